@@ -1,0 +1,193 @@
+"""CPU oracle for the Bitmap Filter self-join -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's
+``cpu_baseline`` / reference leg may import this package.  It shares no code
+with the CUDA library: the arithmetic lives in ``oracle.c`` (plain C, int64),
+loaded here through ctypes; ``expected.py`` holds the paper's closed forms
+(Eq. 4-6) in exact rational / fp64 arithmetic.
+
+Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
+  overlap / similar / self_join -- worked examples of Section 1 and Section 3.1,
+      brute force with Python ``set`` on tiny inputs, the Table 1 identity
+      checked against exact fractions;
+  bitmap (Set/Xor/Next) -- exact binary sets when b covers the universe
+      (Section 3.1), Next's popcount rule (Alg. 3c), order invariance
+      (Section 3.3), Monte Carlo against Eq. 4-5;
+  filter_counts -- window count against a closed form over the size
+      histogram, survivors == results when bitmaps are exact, Theorem 1
+      soundness (results never exceed what brute force finds);
+  join_rows / search -- against self_join / brute force on small inputs.
+  Cutoff point (Section 3.5, Eq. 5 inverted) -- parity unpinned: the paper's
+      Xor figure 4983 does not follow from its own Eq. 5.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+XOR, SET, NEXT, COMBINED = 0, 1, 2, 3
+METHODS = {"xor": XOR, "set": SET, "next": NEXT, "combined": COMBINED}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        i64, i32p, i64p, u64p = C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
+        u32pp = C.POINTER(C.POINTER(C.c_uint32))
+        L.oracle_overlap.argtypes = [i32p, i64, i32p, i64]
+        L.oracle_overlap.restype = i64
+        L.oracle_similar.argtypes = [i64, i64, i64, i64, i64]
+        L.oracle_similar.restype = C.c_int
+        L.oracle_self_join.argtypes = [i64, i64p, i32p, i64, i64, u32pp, u32pp]
+        L.oracle_self_join.restype = i64
+        L.oracle_join_rows.argtypes = [i64, i64p, i32p, i64, i64, i64p, i64, u32pp, u32pp]
+        L.oracle_join_rows.restype = i64
+        L.oracle_search.argtypes = [i32p, i64, i64, i64p, i32p, i64, i64, C.POINTER(i64p)]
+        L.oracle_search.restype = i64
+        L.oracle_bitmap.argtypes = [i32p, i64, C.c_int, C.c_int, u64p]
+        L.oracle_bitmap.restype = None
+        L.oracle_bitmaps.argtypes = [i64, i64p, i32p, C.c_int, C.c_int, u64p]
+        L.oracle_bitmaps.restype = None
+        L.oracle_hamming.argtypes = [u64p, u64p, C.c_int]
+        L.oracle_hamming.restype = i64
+        L.oracle_upper_bound.argtypes = [i64, i64, i64]
+        L.oracle_upper_bound.restype = i64
+        L.oracle_filter_counts.argtypes = [i64, i64p, i32p, i64, i64, C.c_int, C.c_int, i64p]
+        L.oracle_filter_counts.restype = None
+        L.oracle_combined_method.argtypes = [i64, i64]
+        L.oracle_combined_method.restype = C.c_int
+        L.oracle_num_threads.argtypes = []
+        L.oracle_num_threads.restype = C.c_int
+        L.oracle_free.argtypes = [C.c_void_p]
+        L.oracle_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _i32(x):
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+def _i64(x):
+    return np.ascontiguousarray(x, dtype=np.int64)
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def overlap(x, y) -> int:
+    """|x & y| of two strictly increasing token arrays."""
+    x, y = _i32(x), _i32(y)
+    return int(lib().oracle_overlap(_p(x, C.c_int32), len(x), _p(y, C.c_int32), len(y)))
+
+
+def similar(o: int, nx: int, ny: int, p: int, q: int) -> bool:
+    """Jaccard >= p/q given the overlap o and the sizes (Table 1)."""
+    return bool(lib().oracle_similar(o, nx, ny, p, q))
+
+
+def _take_pairs(n, A, B):
+    L = lib()
+    if n < 0:
+        raise MemoryError("oracle allocation failed")
+    if n == 0:
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint32)
+    a = np.ctypeslib.as_array(A, shape=(n,)).copy()
+    b = np.ctypeslib.as_array(B, shape=(n,)).copy()
+    L.oracle_free(C.cast(A, C.c_void_p))
+    L.oracle_free(C.cast(B, C.c_void_p))
+    return a, b
+
+
+def self_join(offsets, tokens, p: int, q: int):
+    """All pairs a<b (original ids) with Jaccard >= p/q, sorted by (a, b)."""
+    off, tok = _i64(offsets), _i32(tokens)
+    A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
+    n = lib().oracle_self_join(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p, q,
+                               C.byref(A), C.byref(B))
+    return _take_pairs(n, A, B)
+
+
+def join_rows(offsets, tokens, p: int, q: int, rows):
+    """Similar pairs (min,max) that touch one of ``rows``, sorted, unique."""
+    off, tok, r = _i64(offsets), _i32(tokens), _i64(rows)
+    A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
+    n = lib().oracle_join_rows(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p, q,
+                               _p(r, C.c_int64), len(r), C.byref(A), C.byref(B))
+    return _take_pairs(n, A, B)
+
+
+def search(probe, offsets, tokens, p: int, q: int):
+    """Ids of the collection's sets with Jaccard(probe, s) >= p/q, ascending."""
+    x, off, tok = _i32(probe), _i64(offsets), _i32(tokens)
+    ids = C.POINTER(C.c_int64)()
+    n = lib().oracle_search(_p(x, C.c_int32), len(x), len(off) - 1, _p(off, C.c_int64),
+                            _p(tok, C.c_int32), p, q, C.byref(ids))
+    if n < 0:
+        raise MemoryError("oracle allocation failed")
+    if n == 0:
+        return np.zeros(0, np.int64)
+    out = np.ctypeslib.as_array(ids, shape=(n,)).copy()
+    lib().oracle_free(C.cast(ids, C.c_void_p))
+    return out
+
+
+def combined_method(p: int, q: int) -> int:
+    """Alg. 4's choice for threshold p/q (switch points on 2p/(p+q))."""
+    return int(lib().oracle_combined_method(p, q))
+
+
+def bitmap(tokens, b: int, method: int):
+    """One set's b-bit bitmap (Alg. 3a/3b/3c) as uint64[b/64]."""
+    x = _i32(tokens)
+    out = np.zeros(b // 64, np.uint64)
+    lib().oracle_bitmap(_p(x, C.c_int32), len(x), b, method, _p(out, C.c_uint64))
+    return out
+
+
+def bitmaps(offsets, tokens, b: int, method: int):
+    """Bitmaps of a collection in original order, uint64[N, b/64]."""
+    off, tok = _i64(offsets), _i32(tokens)
+    n = len(off) - 1
+    out = np.zeros((n, b // 64), np.uint64)
+    lib().oracle_bitmaps(n, _p(off, C.c_int64), _p(tok, C.c_int32), b, method,
+                         _p(out, C.c_uint64))
+    return out
+
+
+def hamming(br, bs) -> int:
+    br, bs = np.ascontiguousarray(br, np.uint64), np.ascontiguousarray(bs, np.uint64)
+    return int(lib().oracle_hamming(_p(br, C.c_uint64), _p(bs, C.c_uint64), 64 * len(br)))
+
+
+def upper_bound(nr: int, ns: int, h: int) -> int:
+    """Eq. 2: floor((|r| + |s| - h) / 2)."""
+    return int(lib().oracle_upper_bound(nr, ns, h))
+
+
+def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int):
+    """(window pairs, survivors, results) of Alg. 6 + host verification."""
+    off, tok = _i64(offsets), _i32(tokens)
+    cnt = np.zeros(3, np.int64)
+    lib().oracle_filter_counts(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p, q,
+                               b, method, _p(cnt, C.c_int64))
+    if cnt[0] < 0:
+        raise MemoryError("oracle allocation failed")
+    return int(cnt[0]), int(cnt[1]), int(cnt[2])
+
+
+__all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "overlap", "similar", "self_join",
+           "join_rows", "search", "bitmap", "bitmaps", "hamming", "upper_bound",
+           "filter_counts", "combined_method", "num_threads", "lib"]

@@ -1,0 +1,392 @@
+/*
+ * oracle.c -- plain CPU oracle for exact set-similarity self-joins and the
+ * Bitmap Filter (Sandes, Teodoro & Melo, "Bitmap Filter: Speeding up Exact
+ * Set Similarity Joins with Bitwise Operations").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may call, link or
+ * include this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header or table with the CUDA
+ * path.  Every function is written as plainly as the definition allows, in
+ * 64-bit integer arithmetic (the method is exact integer work: there is no
+ * floating point anywhere in this file).
+ *
+ * Conventions shared with the paper:
+ *   - a collection is N sets in CSR form: set x holds tokens
+ *     tok[off[x] .. off[x+1]-1], strictly increasing, non-negative
+ *     (sets have no repeated elements, Section 2.1);
+ *   - Jaccard J(x,y) = |x & y| / |x | y| (Table 1); the threshold is the
+ *     rational p/q, and "similar" means J >= p/q (Eq. 1 uses >=).  Since
+ *     |x | y| = |x| + |y| - |x & y|, J >= p/q  <=>  o*(p+q) >= p*(|x|+|y|)
+ *     with o = |x & y|; both sides are exact in int64;
+ *   - bitmaps have b bits, b a multiple of 64, stored as b/64 uint64 words;
+ *     bit k lives in word k/64 at bit position k%64; the hash is
+ *     h(t) = t mod b (Section 5.1).
+ *
+ * Functions:
+ *   oracle_overlap        |x & y| by a plain two-pointer merge (Alg. 1 verify)
+ *   oracle_similar        the integer Jaccard test above
+ *   oracle_self_join      Alg. 1 over all pairs a<b, no filter at all
+ *   oracle_join_rows      Alg. 1 restricted to pairs touching sampled rows
+ *   oracle_search         one probe set against every set of a collection
+ *   oracle_bitmap         Alg. 3a (Set), 3b (Xor), 3c (Next), literally
+ *   oracle_filter_counts  the GPU algorithm (Alg. 6): size order, length
+ *                         window, Eq. 2 bound, then verification -- counted
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { OR_XOR = 0, OR_SET = 1, OR_NEXT = 2, OR_COMBINED = 3 };
+
+/* |x & y| for two strictly increasing token arrays (plain merge). */
+int64_t oracle_overlap(const int32_t *x, int64_t nx, const int32_t *y, int64_t ny)
+{
+    int64_t i = 0, j = 0, o = 0;
+    while (i < nx && j < ny) {
+        if (x[i] == y[j]) { o++; i++; j++; }
+        else if (x[i] < y[j]) i++;
+        else j++;
+    }
+    return o;
+}
+
+/* Jaccard(x,y) >= p/q, as o*(p+q) >= p*(|x|+|y|) (Table 1, Eq. 1). */
+int oracle_similar(int64_t o, int64_t nx, int64_t ny, int64_t p, int64_t q)
+{
+    return o * (p + q) >= p * (nx + ny);
+}
+
+/* Growable pair buffer. */
+typedef struct { uint32_t *a, *b; int64_t n, cap; } pairbuf;
+
+static int pb_push(pairbuf *pb, uint32_t a, uint32_t b)
+{
+    if (pb->n == pb->cap) {
+        int64_t nc = pb->cap ? 2 * pb->cap : 64;
+        uint32_t *na = (uint32_t *)realloc(pb->a, (size_t)nc * sizeof(uint32_t));
+        if (!na) return -1;
+        pb->a = na;
+        uint32_t *nb = (uint32_t *)realloc(pb->b, (size_t)nc * sizeof(uint32_t));
+        if (!nb) return -1;
+        pb->b = nb;
+        pb->cap = nc;
+    }
+    pb->a[pb->n] = a;
+    pb->b[pb->n] = b;
+    pb->n++;
+    return 0;
+}
+
+void oracle_free(void *p) { free(p); }
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/*
+ * Alg. 1 (naive algorithm) for a self-join: every pair a < b of original
+ * ids is verified; the output is every similar pair, in (a, b) order.
+ * Rows are independent, so they are spread over threads (dynamic
+ * schedule); each row's pairs are collected separately and concatenated in
+ * row order, so the output order is the sequential order.
+ * Returns the pair count, or -1 on allocation failure.  *out_a / *out_b are
+ * malloc'd (free with oracle_free); both are NULL when the count is 0.
+ */
+int64_t oracle_self_join(int64_t n, const int64_t *off, const int32_t *tok,
+                         int64_t p, int64_t q, uint32_t **out_a, uint32_t **out_b)
+{
+    *out_a = NULL;
+    *out_b = NULL;
+    if (n <= 1) return 0;
+    pairbuf *rows = (pairbuf *)calloc((size_t)n, sizeof(pairbuf));
+    if (!rows) return -1;
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t a = 0; a < n; a++) {
+        const int32_t *xa = tok + off[a];
+        int64_t na = off[a + 1] - off[a];
+        for (int64_t b = a + 1; b < n; b++) {
+            const int32_t *xb = tok + off[b];
+            int64_t nb = off[b + 1] - off[b];
+            int64_t o = oracle_overlap(xa, na, xb, nb);
+            if (oracle_similar(o, na, nb, p, q))
+                if (pb_push(&rows[a], (uint32_t)a, (uint32_t)b)) failed = 1;
+        }
+    }
+    int64_t total = 0;
+    for (int64_t a = 0; a < n; a++) total += rows[a].n;
+    uint32_t *A = NULL, *B = NULL;
+    if (!failed && total > 0) {
+        A = (uint32_t *)malloc((size_t)total * sizeof(uint32_t));
+        B = (uint32_t *)malloc((size_t)total * sizeof(uint32_t));
+        if (!A || !B) failed = 1;
+    }
+    int64_t k = 0;
+    for (int64_t a = 0; a < n; a++) {
+        if (!failed && rows[a].n) {
+            memcpy(A + k, rows[a].a, (size_t)rows[a].n * sizeof(uint32_t));
+            memcpy(B + k, rows[a].b, (size_t)rows[a].n * sizeof(uint32_t));
+            k += rows[a].n;
+        }
+        free(rows[a].a);
+        free(rows[a].b);
+    }
+    free(rows);
+    if (failed) { free(A); free(B); return -1; }
+    *out_a = A;
+    *out_b = B;
+    return total;
+}
+
+/*
+ * Alg. 1 restricted to the pairs that touch a row in rows[0..k-1] (original
+ * ids, any order, duplicates allowed): for each sampled row r, every other
+ * set s is verified and a similar pair is emitted as (min(r,s), max(r,s)).
+ * The output is sorted by (a, b) with duplicates removed (a pair whose two
+ * ends are both sampled is found twice).  This gives exact parity for a
+ * sample of rows of a join too large for Alg. 1 in full.
+ */
+static int cmp_pair64(const void *x, const void *y)
+{
+    uint64_t u = *(const uint64_t *)x, v = *(const uint64_t *)y;
+    return (u > v) - (u < v);
+}
+
+int64_t oracle_join_rows(int64_t n, const int64_t *off, const int32_t *tok,
+                         int64_t p, int64_t q, const int64_t *rows, int64_t k,
+                         uint32_t **out_a, uint32_t **out_b)
+{
+    *out_a = NULL;
+    *out_b = NULL;
+    if (k <= 0 || n <= 1) return 0;
+    pairbuf *per = (pairbuf *)calloc((size_t)k, sizeof(pairbuf));
+    if (!per) return -1;
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < k; t++) {
+        int64_t r = rows[t];
+        const int32_t *xr = tok + off[r];
+        int64_t nr = off[r + 1] - off[r];
+        for (int64_t s = 0; s < n; s++) {
+            if (s == r) continue;
+            int64_t ns = off[s + 1] - off[s];
+            int64_t o = oracle_overlap(xr, nr, tok + off[s], ns);
+            if (oracle_similar(o, nr, ns, p, q)) {
+                uint32_t a = (uint32_t)(r < s ? r : s), b = (uint32_t)(r < s ? s : r);
+                if (pb_push(&per[t], a, b)) failed = 1;
+            }
+        }
+    }
+    int64_t total = 0;
+    for (int64_t t = 0; t < k; t++) total += per[t].n;
+    uint64_t *keys = NULL;
+    if (!failed && total > 0) {
+        keys = (uint64_t *)malloc((size_t)total * sizeof(uint64_t));
+        if (!keys) failed = 1;
+    }
+    int64_t m = 0;
+    for (int64_t t = 0; t < k; t++) {
+        for (int64_t i = 0; !failed && i < per[t].n; i++)
+            keys[m++] = ((uint64_t)per[t].a[i] << 32) | per[t].b[i];
+        free(per[t].a);
+        free(per[t].b);
+    }
+    free(per);
+    if (failed) { free(keys); return -1; }
+    if (total == 0) return 0;
+    qsort(keys, (size_t)total, sizeof(uint64_t), cmp_pair64);
+    int64_t u = 0;
+    for (int64_t i = 0; i < total; i++)
+        if (i == 0 || keys[i] != keys[i - 1]) keys[u++] = keys[i];
+    uint32_t *A = (uint32_t *)malloc((size_t)u * sizeof(uint32_t));
+    uint32_t *B = (uint32_t *)malloc((size_t)u * sizeof(uint32_t));
+    if (!A || !B) { free(A); free(B); free(keys); return -1; }
+    for (int64_t i = 0; i < u; i++) {
+        A[i] = (uint32_t)(keys[i] >> 32);
+        B[i] = (uint32_t)(keys[i] & 0xffffffffu);
+    }
+    free(keys);
+    *out_a = A;
+    *out_b = B;
+    return u;
+}
+
+/*
+ * One probe set x against every set of the collection (an RS-join with
+ * |R| = 1, Eq. 1): the ids s with J(x, s) >= p/q, ascending.
+ */
+int64_t oracle_search(const int32_t *x, int64_t nx, int64_t n, const int64_t *off,
+                      const int32_t *tok, int64_t p, int64_t q, int64_t **out_ids)
+{
+    *out_ids = NULL;
+    int64_t cnt = 0, cap = 0;
+    int64_t *ids = NULL;
+    for (int64_t s = 0; s < n; s++) {
+        int64_t ns = off[s + 1] - off[s];
+        int64_t o = oracle_overlap(x, nx, tok + off[s], ns);
+        if (oracle_similar(o, nx, ns, p, q)) {
+            if (cnt == cap) {
+                cap = cap ? 2 * cap : 64;
+                int64_t *ni = (int64_t *)realloc(ids, (size_t)cap * sizeof(int64_t));
+                if (!ni) { free(ids); return -1; }
+                ids = ni;
+            }
+            ids[cnt++] = s;
+        }
+    }
+    *out_ids = ids;
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------
+ * Bitmaps (Section 3.2).  Bit k of a b-bit bitmap is word k/64, bit k%64.
+ * ---------------------------------------------------------------------- */
+static int get_bit(const uint64_t *w, int64_t k) { return (int)((w[k / 64] >> (k % 64)) & 1u); }
+static void set_bit(uint64_t *w, int64_t k) { w[k / 64] |= (uint64_t)1 << (k % 64); }
+static void flip_bit(uint64_t *w, int64_t k) { w[k / 64] ^= (uint64_t)1 << (k % 64); }
+
+/*
+ * Alg. 4 (Bitmap-Combined) picks the generation method from the threshold.
+ * The paper's switch points 0.56 and 0.73 are read on the normalised overlap
+ * 2*tj/(1+tj) (the scale of its Figs. 6-7), i.e. 2p/(p+q) for tj = p/q:
+ *   2p/(p+q) <= 0.56 -> Next;  2p/(p+q) >= 0.73 -> Xor;  otherwise Set.
+ */
+int oracle_combined_method(int64_t p, int64_t q)
+{
+    if (2 * p * 100 <= 56 * (p + q)) return OR_NEXT;
+    if (2 * p * 100 >= 73 * (p + q)) return OR_XOR;
+    return OR_SET;
+}
+
+/*
+ * Bitmap of one set x (n tokens) with b bits, written to out[0..b/64-1].
+ *   Set  (Alg. 3a): bit h(t) <- 1 for every token t.
+ *   Xor  (Alg. 3b): bit h(t) <- bit h(t) xor 1 for every token t.
+ *   Next (Alg. 3c): if n >= b all bits are 1; otherwise for every token,
+ *                   starting at i = h(t), step i <- (i+1) mod b while bit i
+ *                   is 1, then set bit i.
+ * method OR_COMBINED is resolved by the caller (it needs the threshold).
+ */
+void oracle_bitmap(const int32_t *x, int64_t n, int b, int method, uint64_t *out)
+{
+    int W = b / 64;
+    for (int w = 0; w < W; w++) out[w] = 0;
+    if (method == OR_SET) {
+        for (int64_t k = 0; k < n; k++) set_bit(out, (int64_t)x[k] % b);
+    } else if (method == OR_XOR) {
+        for (int64_t k = 0; k < n; k++) flip_bit(out, (int64_t)x[k] % b);
+    } else if (method == OR_NEXT) {
+        if (n >= b) {
+            for (int w = 0; w < W; w++) out[w] = ~(uint64_t)0;
+        } else {
+            for (int64_t k = 0; k < n; k++) {
+                int64_t i = (int64_t)x[k] % b;
+                while (get_bit(out, i)) i = (i + 1) % b;
+                set_bit(out, i);
+            }
+        }
+    }
+}
+
+/* Bitmaps of a whole collection, in original set order: out[x*W + w]. */
+void oracle_bitmaps(int64_t n, const int64_t *off, const int32_t *tok, int b, int method,
+                    uint64_t *out)
+{
+    int W = b / 64;
+#pragma omp parallel for schedule(static)
+    for (int64_t x = 0; x < n; x++)
+        oracle_bitmap(tok + off[x], off[x + 1] - off[x], b, method, out + x * W);
+}
+
+static int64_t popcount64(uint64_t v)
+{
+    int64_t c = 0;
+    while (v) { c += (int64_t)(v & 1u); v >>= 1; }
+    return c;
+}
+
+/* Hamming distance popcount(br xor bs) of two b-bit bitmaps. */
+int64_t oracle_hamming(const uint64_t *br, const uint64_t *bs, int b)
+{
+    int64_t h = 0;
+    for (int w = 0; w < b / 64; w++) h += popcount64(br[w] ^ bs[w]);
+    return h;
+}
+
+/* Theorem 1, Eq. 2: |r & s| <= floor((|r| + |s| - popcount(br xor bs)) / 2). */
+int64_t oracle_upper_bound(int64_t nr, int64_t ns, int64_t hamming)
+{
+    int64_t v = nr + ns - hamming;
+    /* v >= 0 always holds (hamming <= |r| + |s|); floor of a non-negative. */
+    return v / 2;
+}
+
+/*
+ * Counts of the GPU algorithm (Alg. 6) with verification (its host code):
+ *   1. order the sets by size, ties by original id (stable);
+ *   2. for sorted index i, j0 = the first sorted index whose size s satisfies
+ *      q*s >= p*|R[i]| (the length filter of Table 2, integer form of
+ *      |R[j]| >= tj*|R[i]|); the window is j in [j0, i);
+ *   3. for every window pair: UB by Eq. 2, the pair survives the Bitmap
+ *      Filter iff UB*(p+q) >= p*(|R[i]|+|R[j]|) (UB reaches the Jaccard
+ *      overlap threshold of Table 1); no cutoff point (the GPU algorithm
+ *      runs without it);
+ *   4. a survivor is a result iff it passes oracle_similar.
+ * method selects the bitmap generation (OR_COMBINED resolved from p/q).
+ * Writes window pairs, survivors and results to counts[0..2].  The sort is a
+ * plain insertion of (size, id) keys through qsort of packed keys.
+ */
+void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int64_t p,
+                          int64_t q, int b, int method, int64_t *counts)
+{
+    counts[0] = counts[1] = counts[2] = 0;
+    if (n <= 1) return;
+    if (method == OR_COMBINED) method = oracle_combined_method(p, q);
+    int W = b / 64;
+    uint64_t *keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int64_t *ord = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *sz = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    uint64_t *bm = (uint64_t *)malloc((size_t)n * (size_t)W * sizeof(uint64_t));
+    if (!keys || !ord || !sz || !bm) {
+        counts[0] = counts[1] = counts[2] = -1;
+        free(keys); free(ord); free(sz); free(bm);
+        return;
+    }
+    for (int64_t x = 0; x < n; x++)
+        keys[x] = ((uint64_t)(off[x + 1] - off[x]) << 32) | (uint64_t)x;
+    qsort(keys, (size_t)n, sizeof(uint64_t), cmp_pair64);
+    for (int64_t i = 0; i < n; i++) {
+        ord[i] = (int64_t)(keys[i] & 0xffffffffu);
+        sz[i] = (int64_t)(keys[i] >> 32);
+        oracle_bitmap(tok + off[ord[i]], sz[i], b, method, bm + i * W);
+    }
+    free(keys);
+    int64_t win = 0, surv = 0, res = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : win, surv, res)
+    for (int64_t i = 0; i < n; i++) {
+        int64_t j0 = 0;
+        while (q * sz[j0] < p * sz[i]) j0++;
+        for (int64_t j = j0; j < i; j++) {
+            win++;
+            int64_t h = oracle_hamming(bm + i * W, bm + j * W, b);
+            int64_t ub = oracle_upper_bound(sz[i], sz[j], h);
+            if (ub * (p + q) >= p * (sz[i] + sz[j])) {
+                surv++;
+                int64_t o = oracle_overlap(tok + off[ord[i]], sz[i], tok + off[ord[j]], sz[j]);
+                if (oracle_similar(o, sz[i], sz[j], p, q)) res++;
+            }
+        }
+    }
+    counts[0] = win;
+    counts[1] = surv;
+    counts[2] = res;
+    free(ord); free(sz); free(bm);
+}

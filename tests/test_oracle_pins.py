@@ -1,0 +1,440 @@
+"""Pins of the CPU oracle to facts the paper and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: values the
+paper prints for a worked example (fixtures under tests/golden/), brute force
+over Python sets with exact fractions, closed forms (Eq. 4-5, the window size
+over a size histogram), invariants (Theorem 1, order invariance of the
+generation functions) and special cases that reduce to exact binary sets.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import expected as E
+from paper_1711_07295_b300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _fixture(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.rstrip("\n").split("\t", 1)
+            out[k] = v
+    return out
+
+
+def _bigrams(s):
+    return {s[i:i + 2] for i in range(len(s) - 1)}
+
+
+def _csr(sets):
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s) for s in sets])
+    tok = np.array([t for s in sets for t in sorted(s)], np.int32)
+    return off, tok
+
+
+def _brute_pairs(sets, p, q):
+    out = []
+    for a, b in itertools.combinations(range(len(sets)), 2):
+        A, B = set(sets[a]), set(sets[b])
+        if Fraction(len(A & B), len(A | B)) >= Fraction(p, q):
+            out.append((a, b))
+    return out
+
+
+# ---------------------------------------------------------------- Section 1
+def test_bigram_example_section1():
+    g = _fixture("bigrams_section1.txt")
+    A, B = _bigrams(g["record_a"]), _bigrams(g["record_b"])
+    vocab = {bg: i for i, bg in enumerate(sorted(A | B))}
+    x = sorted(vocab[t] for t in A)
+    y = sorted(vocab[t] for t in B)
+    o = O.overlap(x, y)
+    assert o == int(g["overlap_ab"]) == 6
+    assert len(_bigrams(g["record_c"])) == int(g["bigrams_c"]) == 13
+    # Jaccard = 6 / (8 + 8 - 6) = 3/5: similar at 3/5 (>= is inclusive), not above it.
+    assert O.similar(o, len(x), len(y), 3, 5)
+    assert not O.similar(o, len(x), len(y), 61, 100)
+    off, tok = _csr([x, y])
+    a, b = O.self_join(off, tok, 3, 5)
+    assert list(zip(a.tolist(), b.tolist())) == [(0, 1)]
+    a, b = O.self_join(off, tok, 61, 100)
+    assert len(a) == 0
+
+
+# -------------------------------------------------------------- Section 3.1
+def test_binary_set_example_section3_1():
+    g = _fixture("binary_sets_section3_1.txt")
+    r = [int(t) for t in g["r"].split()]
+    s = [int(t) for t in g["s"].split()]
+    # Position k (1-based, from the left) of the printed binary set is token k.
+    pr = {k + 1 for k, ch in enumerate(g["b_r"]) if ch == "1"}
+    ps = {k + 1 for k, ch in enumerate(g["b_s"]) if ch == "1"}
+    assert pr == set(r) and ps == set(s)
+    for method in (O.SET, O.XOR, O.NEXT):
+        br, bs = O.bitmap(r, 64, method), O.bitmap(s, 64, method)
+        # No collisions (universe 8 < b = 64): every method gives the exact binary set.
+        assert int(br[0]) == sum(1 << t for t in r)
+        assert int(bs[0]) == sum(1 << t for t in s)
+        assert bin(int(br[0]) & int(bs[0])).count("1") == int(g["and_popcount"]) == 1
+        assert bin(int(br[0]) | int(bs[0])).count("1") == int(g["or_popcount"]) == 6
+        h = O.hamming(br, bs)
+        assert h == 5
+        # Eq. 2 is exact without collisions: floor((3 + 4 - 5) / 2) = 1 = |r & s|.
+        assert O.upper_bound(3, 4, h) == 1 == O.overlap(r, s)
+    j = Fraction(g["jaccard"])
+    assert j == Fraction(1, 6)
+    assert O.similar(1, 3, 4, j.numerator, j.denominator)          # boundary is inclusive
+    assert not O.similar(1, 3, 4, 2, 11)                            # 2/11 > 1/6
+
+
+# ------------------------------------------------------ brute force, Table 1
+@pytest.mark.parametrize("seed,universe,lo,hi,p,q", [
+    (1, 12, 1, 6, 1, 2), (2, 30, 2, 10, 3, 5), (3, 8, 1, 8, 4, 5),
+    (4, 200, 5, 40, 1, 3), (5, 16, 1, 16, 9, 10), (6, 6, 1, 6, 1, 1),
+    (7, 50, 1, 3, 1, 2),
+])
+def test_self_join_brute_force(seed, universe, lo, hi, p, q):
+    rng = np.random.default_rng(seed)
+    sets = []
+    for _ in range(90):
+        n = int(rng.integers(lo, min(hi, universe) + 1))
+        sets.append(sorted(rng.choice(universe, size=n, replace=False).tolist()))
+    off, tok = _csr(sets)
+    a, b = O.self_join(off, tok, p, q)
+    assert list(zip(a.tolist(), b.tolist())) == _brute_pairs(sets, p, q)
+    # overlap against Python set intersection on every pair
+    for x, y in itertools.combinations(range(len(sets)), 2):
+        if (x * 7 + y) % 11 == 0:
+            assert O.overlap(sets[x], sets[y]) == len(set(sets[x]) & set(sets[y]))
+
+
+def test_similar_matches_exact_fractions():
+    rng = np.random.default_rng(11)
+    for _ in range(3000):
+        nx, ny = int(rng.integers(1, 60)), int(rng.integers(1, 60))
+        o = int(rng.integers(0, min(nx, ny) + 1))
+        q = int(rng.integers(1, 40))
+        p = int(rng.integers(1, q + 1))
+        exact = Fraction(o, nx + ny - o) >= Fraction(p, q)
+        assert O.similar(o, nx, ny, p, q) == exact
+
+
+def test_join_rows_and_search_against_brute_force():
+    off, tok = I.random_collection(300, 40, 1, 12, seed=3, planted_frac=0.1)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    p, q = 1, 2
+    full = set(_brute_pairs(sets, p, q))
+    rows = [0, 5, 17, 17, 299, 150]
+    a, b = O.join_rows(off, tok, p, q, rows)
+    got = list(zip(a.tolist(), b.tolist()))
+    assert got == sorted({pr for pr in full if pr[0] in rows or pr[1] in rows})
+    probe = sets[17]
+    ids = O.search(probe, off, tok, p, q)
+    want = [s for s in range(len(sets))
+            if Fraction(len(set(probe) & set(sets[s])), len(set(probe) | set(sets[s]))) >= Fraction(p, q)]
+    assert ids.tolist() == want
+
+
+# ------------------------------------------------------------- Section 3.2
+def test_bitmaps_small_examples():
+    # h(t) = t mod 64: tokens 0 and 64 collide on bit 0, token 1 hits bit 1.
+    x = [0, 1, 64]
+    assert int(O.bitmap(x, 64, O.SET)[0]) == 0b11
+    assert int(O.bitmap(x, 64, O.XOR)[0]) == 0b10                 # 0 and 64 cancel
+    assert int(O.bitmap(x, 64, O.NEXT)[0]) == 0b111               # 64 probes on to bit 1, then 1 to bit 2
+    # Next wraps around the end of the bitmap.
+    assert int(O.bitmap([63, 127], 64, O.NEXT)[0]) == (1 << 63) | 1
+    # n >= b: Next returns all ones (Alg. 3c).
+    full = O.bitmap(list(range(0, 64 * 64, 64)), 64, O.NEXT)
+    assert int(full[0]) == (1 << 64) - 1
+    # Multi-word layout: token 200 with b = 256 is word 3, bit 8.
+    bm = O.bitmap([200], 256, O.XOR)
+    assert bm.tolist() == [0, 0, 0, 1 << 8]
+
+
+@pytest.mark.parametrize("b", [64, 128, 256, 192])
+def test_bitmaps_exact_when_b_covers_universe(b):
+    rng = np.random.default_rng(b)
+    for _ in range(200):
+        n = int(rng.integers(1, b))
+        x = sorted(rng.choice(b, size=n, replace=False).tolist())
+        want = [0] * (b // 64)
+        for t in x:
+            want[t // 64] |= 1 << (t % 64)
+        for m in (O.SET, O.XOR, O.NEXT):
+            assert [int(w) for w in O.bitmap(x, b, m)] == want
+
+
+@pytest.mark.parametrize("b", [64, 128, 256])
+def test_set_and_xor_by_hash_counts(b):
+    # Bit k of Set is "some token hashes to k"; of Xor, "an odd number do".
+    rng = np.random.default_rng(5 + b)
+    for _ in range(300):
+        n = int(rng.integers(1, 4 * b))
+        x = sorted(rng.choice(50 * b, size=n, replace=False).tolist())
+        cnt = np.bincount(np.array(x) % b, minlength=b)
+        bits_set = {k for k in range(b) if cnt[k] > 0}
+        bits_xor = {k for k in range(b) if cnt[k] % 2 == 1}
+
+        def bits(bm):
+            return {w * 64 + i for w in range(b // 64) for i in range(64) if (int(bm[w]) >> i) & 1}
+        assert bits(O.bitmap(x, b, O.SET)) == bits_set
+        assert bits(O.bitmap(x, b, O.XOR)) == bits_xor
+
+
+def _next_by_carry(x, b):
+    """Occupied slots of circular linear probing from hash counts (no probing loop).
+
+    c_k tokens hash to slot k; the overflow carried out of slot k is
+    carry_k = max(0, carry_{k-1} + c_k - 1), and slot k is occupied iff
+    c_k + carry_{k-1} >= 1.  Around the circle the carry into slot 0 is the
+    carry out of slot b-1, so the recurrence is iterated to its fixed point.
+    """
+    n = len(x)
+    if n >= b:
+        return set(range(b))
+    c = np.bincount(np.array(x, dtype=np.int64) % b, minlength=b)
+    carry_in = 0
+    while True:
+        carry = carry_in
+        occ = set()
+        for k in range(b):
+            if c[k] + carry >= 1:
+                occ.add(k)
+            carry = max(0, carry + c[k] - 1)
+        if carry == carry_in:
+            return occ
+        carry_in = carry
+
+
+@pytest.mark.parametrize("b", [64, 128])
+def test_next_against_carry_form_and_order(b):
+    rng = np.random.default_rng(17 + b)
+    for trial in range(300):
+        n = int(rng.integers(1, b + 8))
+        # Adversarial: draw from a few residues so that probing chains are long.
+        base = rng.choice(3 + trial % 5, size=n) + b * rng.choice(10 * b, size=n, replace=False)
+        x = sorted(set(int(t) for t in base))
+        bm = O.bitmap(x, b, O.NEXT)
+        bits = {w * 64 + i for w in range(b // 64) for i in range(64) if (int(bm[w]) >> i) & 1}
+        assert bits == _next_by_carry(x, b)
+        assert len(bits) == min(len(x), b)          # exactly n ones unless n >= b (Alg. 3c)
+        # Order invariance of the generation (Section 3.3): any insertion order.
+        perm = list(x)
+        rng.shuffle(perm)
+        for m in (O.SET, O.XOR, O.NEXT):
+            assert O.bitmap(perm, b, m).tolist() == O.bitmap(x, b, m).tolist()
+
+
+# ------------------------------------------------------ Theorem 1 (Eq. 2)
+@pytest.mark.parametrize("b", [64, 128, 256])
+def test_theorem1_soundness(b):
+    rng = np.random.default_rng(100 + b)
+    for trial in range(1500):
+        nr, ns = int(rng.integers(1, 3 * b)), int(rng.integers(1, 3 * b))
+        if trial % 3 == 0:
+            # Adversarial collisions: every token is congruent to a few residues mod b.
+            pool = (rng.choice(4, size=6 * b) + b * rng.choice(100 * b, size=6 * b)).tolist()
+            pool = sorted(set(pool))
+        else:
+            pool = list(range(4 * b))
+        common = int(rng.integers(0, min(nr, ns) + 1))
+        picks = rng.choice(len(pool), size=min(len(pool), nr + ns - common), replace=False)
+        toks = [pool[i] for i in picks]
+        r = sorted(toks[:nr])
+        s = sorted(toks[:common] + toks[nr:nr + ns - common])
+        o = len(set(r) & set(s))
+        for m in (O.SET, O.XOR, O.NEXT):
+            h = O.hamming(O.bitmap(r, b, m), O.bitmap(s, b, m))
+            assert O.upper_bound(len(r), len(s), h) >= o
+
+
+# ---------------------------------------------------- Section 3.4, Eq. 4-5
+@pytest.mark.parametrize("n", [8, 32, 55, 100])
+def test_expected_upper_bound_monte_carlo(n):
+    b, M = 64, 4000
+    rng = np.random.default_rng(1000 + n)
+    # 2M random n-token sets over a universe far larger than b*M*n, so that
+    # the two sets of a pair share no token and their hashes are uniform.
+    sets = [np.sort(rng.choice(1 << 40, size=n, replace=False) % (1 << 30)) for _ in range(2 * M)]
+    sets = [np.unique(s) for s in sets]
+    sets = [s for s in sets if len(s) == n][: 2 * (len(sets) // 2)]
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(s) for s in sets])
+    tok = np.concatenate(sets).astype(np.int64)
+    assert tok.max() < 2**31
+    tok = tok.astype(np.int32)
+    for m, ef in ((O.SET, E.e_set), (O.XOR, E.e_xor)):
+        bm = O.bitmaps(off, tok, b, m)
+        ub = []
+        for k in range(0, len(sets) - 1, 2):
+            h = O.hamming(bm[k], bm[k + 1])
+            ub.append((2 * n - h) / 2.0)          # Eq. 2 without the floor, as in Eq. 4-6
+        ub = np.array(ub)
+        want = ef(b, n)
+        se = ub.std(ddof=1) / np.sqrt(len(ub))
+        assert abs(ub.mean() - want) <= 4.5 * se + 1e-9, (m, n, ub.mean(), want, se)
+    # Eq. 6 is the paper's approximation for Next: only a loose agreement.
+    bm = O.bitmaps(off, tok, b, O.NEXT)
+    ub = np.mean([(2 * n - O.hamming(bm[k], bm[k + 1])) / 2.0 for k in range(0, len(sets) - 1, 2)])
+    assert abs(ub - E.e_next(b, n)) <= 0.06 * n + 0.1
+
+
+def test_expected_values_quoted_in_text():
+    # Section 3.4: at b = 64, n = 55 the normalised bound of Set and Xor is about 0.72.
+    assert abs(E.e_set(64, 55) / 55 - 0.72) < 0.01
+    assert abs(E.e_xor(64, 55) / 55 - 0.72) < 0.01
+    # With b covering n comfortably the bound tends to 0 (few collisions).
+    assert E.e_set(1 << 20, 4) < 1e-4 and E.e_xor(1 << 20, 4) < 1e-4
+
+
+# --------------------------------------------- Alg. 6 counts (filter oracle)
+def _window_closed_form(sizes, p, q):
+    hist = np.bincount(sizes)
+    total = 0
+    for s in range(1, len(hist)):
+        c = int(hist[s])
+        if c == 0:
+            continue
+        total += c * (c - 1) // 2
+        for t in range(1, s):
+            if q * t >= p * s:
+                total += c * int(hist[t])
+    return total
+
+
+@pytest.mark.parametrize("p,q", [(1, 2), (4, 5), (9, 10), (3, 4), (1, 1), (1, 100)])
+def test_window_count_closed_form(p, q):
+    off, tok = I.random_collection(700, 300, 1, 30, seed=p * 31 + q)
+    sizes = np.diff(off)
+    w, s, r = O.filter_counts(off, tok, p, q, 64, O.XOR)
+    assert w == _window_closed_form(sizes, p, q)
+    assert r <= s <= w
+
+
+@pytest.mark.parametrize("method", [O.SET, O.XOR, O.NEXT])
+def test_exact_bitmaps_survivors_are_results(method):
+    # Universe <= b: bitmaps are the exact binary sets, so the Eq. 2 bound equals
+    # the overlap and the filter passes exactly the similar pairs.
+    off, tok = I.random_collection(400, 64, 1, 20, seed=9, planted_frac=0.2)
+    for p, q in ((1, 2), (3, 5), (4, 5)):
+        w, s, r = O.filter_counts(off, tok, p, q, 64, method)
+        assert s == r
+        assert r == len(O.self_join(off, tok, p, q)[0])
+
+
+@pytest.mark.parametrize("b", [64, 128, 256])
+@pytest.mark.parametrize("method", [O.SET, O.XOR, O.NEXT, O.COMBINED])
+def test_filter_pipeline_loses_no_result(b, method):
+    # Length filter + Bitmap Filter are sound: the verified survivors are
+    # exactly the similar pairs that brute force finds.
+    off, tok = I.random_collection(500, 2000, 1, 60, seed=b + method, planted_frac=0.15)
+    for p, q in ((1, 2), (7, 10), (9, 10)):
+        w, s, r = O.filter_counts(off, tok, p, q, b, method)
+        assert r == len(O.self_join(off, tok, p, q)[0])
+        assert s <= w
+
+
+def test_length_window_is_sound():
+    off, tok = I.random_collection(300, 30, 1, 25, seed=4, planted_frac=0.2)
+    sizes = np.diff(off)
+    for p, q in ((1, 2), (3, 4), (9, 10)):
+        a, b = O.self_join(off, tok, p, q)
+        lo, hi = np.minimum(sizes[a], sizes[b]), np.maximum(sizes[a], sizes[b])
+        assert np.all(q * lo >= p * hi)
+
+
+def test_combined_method_switch_points():
+    # Alg. 4 read on the normalised overlap 2p/(p+q).
+    assert O.combined_method(1, 2) == O.SET       # 0.667: between the switch points
+    assert O.combined_method(4, 5) == O.XOR       # 0.889
+    assert O.combined_method(1, 3) == O.NEXT      # 0.5
+    assert O.combined_method(7, 18) == O.NEXT     # exactly 0.56 -> Next (<=)
+    assert O.combined_method(73, 127) == O.XOR    # exactly 0.73 -> Xor (>=)
+    assert O.combined_method(2, 5) == O.SET       # 0.571
+
+
+def test_degenerate_collections():
+    for n in (0, 1):
+        off = np.zeros(n + 1, np.int64)
+        off[1:] = 3
+        tok = np.array([1, 2, 3][: 3 * n], np.int32)
+        assert len(O.self_join(off, tok, 1, 2)[0]) == 0
+        assert O.filter_counts(off, tok, 1, 2, 64, O.XOR) == (0, 0, 0)
+    # identical sets: every pair is similar at any threshold, including 1/1
+    off = np.arange(0, 6 * 4 + 1, 4, dtype=np.int64)
+    tok = np.tile(np.array([3, 70, 134, 9000], np.int32), 6)
+    tok = np.sort(tok.reshape(6, 4), axis=1).ravel()
+    a, b = O.self_join(off, tok, 1, 1)
+    assert len(a) == 15
+    assert O.filter_counts(off, tok, 1, 1, 64, O.XOR) == (15, 15, 15)
+
+
+# ------------------------------------------- Eq. 2 floor, multi-word Hamming
+def test_upper_bound_floor_of_eq2():
+    # Eq. 2 floors (|r| + |s| - h) / 2: an odd numerator rounds down.
+    assert O.upper_bound(3, 4, 4) == 1
+    assert O.upper_bound(5, 8, 0) == 6
+    assert O.upper_bound(2, 1, 0) == 1
+    assert O.upper_bound(7, 7, 14) == 0
+
+
+@pytest.mark.parametrize("b", [128, 256, 640])
+def test_hamming_is_symmetric_difference_when_exact(b):
+    # With b covering the universe the bitmaps are exact and
+    # popcount(br xor bs) = |r \ s| + |s \ r| over all words.
+    rng = np.random.default_rng(b + 1)
+    for _ in range(300):
+        r = sorted(rng.choice(b, size=int(rng.integers(1, b // 2)), replace=False).tolist())
+        s = sorted(rng.choice(b, size=int(rng.integers(1, b // 2)), replace=False).tolist())
+        for m in (O.SET, O.XOR, O.NEXT):
+            h = O.hamming(O.bitmap(r, b, m), O.bitmap(s, b, m))
+            assert h == len(set(r) ^ set(s))
+
+
+def _bits_by_counts(x, b, method):
+    c = np.bincount(np.asarray(x, dtype=np.int64) % b, minlength=b)
+    if method == O.SET:
+        occ = {k for k in range(b) if c[k] > 0}
+    elif method == O.XOR:
+        occ = {k for k in range(b) if c[k] % 2 == 1}
+    else:
+        occ = _next_by_carry(x, b)
+    return occ
+
+
+@pytest.mark.parametrize("method", [O.SET, O.XOR, O.NEXT])
+@pytest.mark.parametrize("b", [64, 128])
+def test_survivor_count_brute_force(method, b):
+    # Survivors of Alg. 6 recounted over all unordered pairs, without the size
+    # order: the pair is in the length window iff q*min >= p*max, and it
+    # survives iff floor((|r|+|s|-|br ^ bs|)/2) * (p+q) >= p*(|r|+|s|), with
+    # the bitmaps taken from hash counts.
+    off, tok = I.random_collection(160, 6 * b, 1, 2 * b, seed=method * 7 + b, zipf_s=0.8,
+                                   planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    bits = [_bits_by_counts(x, b, method) for x in sets]
+    for p, q in ((1, 2), (2, 3), (4, 5)):
+        win = surv = 0
+        for x, y in itertools.combinations(range(len(sets)), 2):
+            nx, ny = len(sets[x]), len(sets[y])
+            if q * min(nx, ny) < p * max(nx, ny):
+                continue
+            win += 1
+            ub = (nx + ny - len(bits[x] ^ bits[y])) // 2
+            if ub * (p + q) >= p * (nx + ny):
+                surv += 1
+        w, s, r = O.filter_counts(off, tok, p, q, b, method)
+        assert (w, s) == (win, surv)
