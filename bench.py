@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the Bitmap Filter exact self-join on B300.
+
+Workload: self-join of 1,000,000 sets (tokens Zipf(s=1.1) over a 200,000-token
+universe, sizes lognormal(mu=2.3, sigma=0.6) rounded and clipped to [1, 500],
+seed 0), synthetic.  One step = the four joins at Jaccard thresholds 1/2, 3/4,
+9/10 and 19/20, each through the C ABI with the collection resident in HBM:
+size sort, bitmap build, Bitmap Filter over the length window, exact
+verification, canonical result sort.  b = 64 bits, Bitmap-Xor (the fastest
+whole join at every one of these thresholds among b in {64, 128, 256}; the
+--sweep option times the other widths).
+
+Metric: pairs filtered/s = window pairs evaluated by the Bitmap Filter
+(pairs inside the length-filter window, the paper's Alg. 6 inner loop) per
+second of whole-join time.  The filter kernel's own rate goes into the
+roofline object.
+
+--impl reference times the CPU oracle (plain all-pairs join with exact
+integer Jaccard) on a bounded row sample of the same workload, extrapolated
+to the full join, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+THRESHOLDS = ((1, 2), (3, 4), (9, 10), (19, 20))
+METRIC = "pairs filtered/s"
+UNIT = "pairs/s"
+WORKLOAD = ("self-join of 1,000,000 sets, tokens Zipf(s=1.1) over 200,000, sizes "
+            "lognormal(mu=2.3,sigma=0.6) clipped to [1,500], Jaccard 1/2, 3/4, 9/10, 19/20")
+POPC_PER_CLK_PER_SM = 16      # 32-bit population count throughput per SM per clock
+FLUSH_BYTES = 256 << 20       # > 126 MB L2
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--b", type=int, default=64)
+    ap.add_argument("--sweep", action="store_true", help="also time b = 128 and 256")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=12,
+                    help="oracle rows sampled per threshold for the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="bmj_clocks_", suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = list(csv.reader(open(self.path)))
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def profile_traffic(b: int):
+    """DRAM bytes per filter launch from the committed ncu summary, if it was
+    taken on the current kernel source (None otherwise)."""
+    path = os.path.join(ROOT, "profiles", f"filter_1m_b{b}.md")
+    src = os.path.join(ROOT, "paper_1711_07295_b300", "csrc", "kernels.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m_hash = re.search(r"kernels\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_tr = re.search(r"dram bytes per full launch \(tau=1/2\):\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_tr or m_hash.group(1) != digest:
+        return None
+    return float(m_tr.group(1))
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (rank 0 only)
+# ----------------------------------------------------------------------------
+def oracle_rate(off, tok, window_by_thr, rows_per_thr: int, seed: int = 0):
+    """Time the oracle on ``rows_per_thr`` sampled rows per threshold and
+    extrapolate the full self-join time (each sampled row is scanned against
+    all N sets; the full join verifies N(N-1)/2 pairs, i.e. N/2 per row)."""
+    import numpy as np
+    import oracle
+    n = len(off) - 1
+    rng = np.random.default_rng(seed)
+    # enough rows to occupy every oracle thread (rows are its unit of parallelism)
+    rows_per_thr = max(rows_per_thr, 2 * oracle.num_threads())
+    t_full = 0.0
+    t_cpu = 0.0
+    for (p, q) in THRESHOLDS:
+        rows = rng.choice(n, size=rows_per_thr, replace=False)
+        t0 = time.perf_counter()
+        oracle.join_rows(off, tok, p, q, rows)
+        dt = time.perf_counter() - t0
+        t_cpu += dt
+        t_full += dt / rows_per_thr * (n / 2.0)
+    total_window = sum(window_by_thr.values())
+    return total_window / t_full, t_full, t_cpu, min(oracle.num_threads(), rows_per_thr), \
+        rows_per_thr
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1711_07295_b300 import _bmj, inputs
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    off, tok = inputs.gen_collection(inputs.spec_1m(seed=0))
+    d_off = torch.from_numpy(off).to(dev)
+    d_tok = torch.from_numpy(tok).to(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    host_coll = {}
+
+    def join(p, q, b, cap=0, host=False):
+        if host:
+            return _bmj.bmj_self_join(host_coll["off"], host_coll["tok"], p, q, b=b,
+                                      queue_cap=cap)
+        res, _, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True,
+                                        queue_cap=cap, stream=stream.cuda_stream)
+        res.release()
+        return st
+
+    b = args.b
+    caps = {}
+    for _ in range(max(args.warmup, 1)):
+        for (p, q) in THRESHOLDS:
+            st = join(p, q, b, caps.get((p, q), 0))
+            caps[(p, q)] = max(1, st["survivors"])
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K steps, L2 flushed between steps (untimed) ----
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    launches0 = _bmj.bmj_kernel_launches()
+    step_ms = []
+    per_thr = {thr: {"window": 0, "survivors": 0, "results": 0, "ms_filter": 0.0,
+                     "ms_verify": 0.0, "ms_total": 0.0, "ms_prepare": 0.0, "ms_output": 0.0}
+               for thr in THRESHOLDS}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for thr in THRESHOLDS:
+            st = join(thr[0], thr[1], b, caps[thr])
+            d = per_thr[thr]
+            d["window"] = st["window_pairs"]
+            d["survivors"] = st["survivors"]
+            d["results"] = st["results"]
+            for key in ("ms_filter", "ms_verify", "ms_total", "ms_prepare", "ms_output"):
+                d[key] += st[key]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    launches = _bmj.bmj_kernel_launches() - launches0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    window_per_step = sum(per_thr[t]["window"] for t in THRESHOLDS)
+    value = window_per_step * args.steps * world / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (the Bitmap Filter) ----
+    peaks, peak_src = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    popc_per_pair = b // 32
+    filt_ms = sum(per_thr[t]["ms_filter"] for t in THRESHOLDS)
+    popc_ops = window_per_step * args.steps * popc_per_pair
+    achieved = popc_ops / (filt_ms / 1e3) / 1e12
+    peak = sms * POPC_PER_CLK_PER_SM * max_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                "unit": "Tpopc32/s", "frac": round(achieved / peak, 4),
+                "traffic": profile_traffic(b),
+                "kernel": f"k_filter<W={b // 64}> (Bitmap Filter)",
+                "peak_derivation": f"{sms} SMs x {POPC_PER_CLK_PER_SM} POPC/clk/SM x "
+                                   f"{max_mhz:.0f} MHz (max SM clock)",
+                "filter_pairs_per_s": round(window_per_step * args.steps / (filt_ms / 1e3)),
+                "filter_share_of_step": round(filt_ms / sum(step_ms), 4)}
+    if clk.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = round(
+            achieved / (sms * POPC_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / 1e12), 4)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pinned = (torch.from_numpy(off).pin_memory(), torch.from_numpy(tok).pin_memory())
+        host_coll["off"], host_coll["tok"] = pinned[0].numpy(), pinned[1].numpy()
+        join(1, 2, b, caps[(1, 2)], host=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        d2h = 0
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            for thr in THRESHOLDS:
+                a, bb, st = join(thr[0], thr[1], b, caps[thr], host=True)
+                d2h += a.nbytes + bb.nbytes
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = len(THRESHOLDS) * (off.nbytes + tok.nbytes)
+        e2e = {"value": round(window_per_step * args.steps * world / e2e_s), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h // args.steps),
+               "ms_per_step": round(e2e_s * 1e3 / args.steps, 3),
+               "inputs": "pinned host CSR, copied by the library each call"}
+
+    # ---- optional b sweep (outside the headline) ----
+    sweep = None
+    if args.sweep:
+        sweep = {}
+        for bw in (64, 128, 256):
+            tot = 0.0
+            filt = 0.0
+            for thr in THRESHOLDS:
+                st0 = join(thr[0], thr[1], bw)
+                st = join(thr[0], thr[1], bw, max(1, st0["survivors"]))
+                tot += st["ms_total"]
+                filt += st["ms_filter"]
+            sweep[str(bw)] = {"step_ms": round(tot, 3), "filter_ms": round(filt, 3),
+                              "filter_pairs_per_s": round(window_per_step / (filt / 1e3))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        win = {thr: per_thr[thr]["window"] for thr in THRESHOLDS}
+        rate, t_full, t_cpu, cores, nrows = oracle_rate(off, tok, win, args.cpu_rows)
+        cpu = {"value": round(rate), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nrows} random rows per threshold scanned against all "
+                         f"1,000,000 sets ({t_cpu:.1f} s wall on {cores} threads), extrapolated to the "
+                         f"full join ({t_full:.0f} s per step)"}
+
+    if rank == 0:
+        joins = []
+        for thr in THRESHOLDS:
+            d = per_thr[thr]
+            joins.append({"threshold": f"{thr[0]}/{thr[1]}", "window_pairs": d["window"],
+                          "survivors": d["survivors"], "results": d["results"],
+                          "join_ms": round(d["ms_total"] / args.steps, 3),
+                          "filter_ms": round(d["ms_filter"] / args.steps, 3),
+                          "verify_ms": round(d["ms_verify"] / args.steps, 3),
+                          "prepare_ms": round(d["ms_prepare"] / args.steps, 3),
+                          "output_ms": round(d["ms_output"] / args.steps, 3)})
+        out = {"metric": METRIC, "value": round(value), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD, "n_sets": int(len(off) - 1),
+                          "tokens": int(len(tok)), "thresholds": [f"{p}/{q}" for p, q in THRESHOLDS],
+                          "b": b, "method": "xor", "parallelism": f"replicas x{world}",
+                          "l2": "flushed between steps (256 MB write, untimed)",
+                          "inputs": "resident in HBM", "peaks": peak_src},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clk, "joins": joins}
+        if sweep:
+            out["sweep_b"] = sweep
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_1711_07295_b300 import inputs
+    off, tok = inputs.gen_collection(inputs.spec_1m(seed=0))
+    sizes = np.diff(off)
+    # window pairs per threshold from the size histogram (same count the GPU reports)
+    hist = np.bincount(sizes)
+    win = {}
+    cum = np.concatenate([[0], np.cumsum(hist)])
+    for (p, q) in THRESHOLDS:
+        tot = 0
+        for s in range(1, len(hist)):
+            c = int(hist[s])
+            if c == 0:
+                continue
+            lo = -(-p * s // q)
+            tot += c * (c - 1) // 2 + c * int(cum[s] - cum[min(lo, s)])
+        win[(p, q)] = tot
+    rows = max(2, args.cpu_rows // 3)
+    for _ in range(args.warmup):
+        oracle_rate(off, tok, win, rows, seed=1)
+    t_step = []
+    cores = 1
+    t_cpu_total = 0.0
+    for k in range(args.steps):
+        rate, t_full, t_cpu, cores, rows = oracle_rate(off, tok, win, rows, seed=100 + k)
+        t_step.append(t_full)
+        t_cpu_total += t_cpu
+    total_window = sum(win.values())
+    value = total_window * args.steps / sum(t_step)
+    sample = (f"{rows} random rows per threshold per step scanned against all 1,000,000 sets, "
+              f"extrapolated to the full join ({t_cpu_total:.1f} s wall on {cores} threads in total)")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(statistics.mean(t_step) * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_sets": int(len(off) - 1),
+                      "thresholds": [f"{p}/{q}" for p, q in THRESHOLDS],
+                      "impl": "CPU oracle: plain all-pairs merge join, exact integer Jaccard"},
+           "cpu_baseline": {"value": round(value), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * bmj.h -- C ABI of the Bitmap Filter set-similarity self-join on B300 (sm_103a).
+ *
+ * Method: Sandes, Teodoro & Melo, "Bitmap Filter: Speeding up Exact Set
+ * Similarity Joins with Bitwise Operations".  A self-join returns every pair
+ * of sets whose Jaccard similarity reaches the threshold (Section 2.1,
+ * Eq. 1).  The library computes it exactly, on the GPU, in four stages:
+ *   1. one b-bit bitmap per set from hashed tokens (Section 3.2, Alg. 3a-3c,
+ *      hash h(t) = t mod b, Section 5.1);
+ *   2. for every pair inside the length-filter window (Section 2.3.2,
+ *      Table 2) the xor+popcount bound of Theorem 1 (Eq. 2) -- the Bitmap
+ *      Filter -- discards pairs that cannot reach the threshold;
+ *   3. the surviving pairs are verified exactly by merge intersection of
+ *      their sorted token arrays;
+ *   4. the similar pairs are returned as original ids (a < b), sorted.
+ *
+ * Conventions for every entry point:
+ *   - Return value: BMJ_OK (0) or a negative BMJ_ERR_* code; bmj_strerror()
+ *     names it.  No C++ exception crosses this ABI.  On error, outputs are
+ *     left empty (pairs: n = 0, pointers NULL) and nothing is leaked.
+ *   - Collections are borrowed, read-only, and must stay valid until the
+ *     call returns.  Tokens of a set must be non-negative and strictly
+ *     increasing (a set has no repeated element; Bitmap-Xor would cancel a
+ *     repeated token), and no set may be empty (Jaccard of two empty sets is
+ *     undefined).  Violations are detected on the device and reported as
+ *     BMJ_ERR_UNSORTED / BMJ_ERR_NEG_TOKEN / BMJ_ERR_EMPTY_SET.
+ *   - Thresholds are exact rationals p/q with 0 < p <= q; "similar" means
+ *     J(x, y) >= p/q, decided in integers as |x&y|*(p+q) >= p*(|x|+|y|)
+ *     (Table 1).  No floating point is used anywhere on the path.
+ *   - Bitmaps have b bits, b a multiple of 64 in [64, 4096]; bit k of a set's
+ *     bitmap is bit (k % 64) of 64-bit word k / 64.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Calls are stream-ordered on that stream; entry points that
+ *     return host-visible results synchronise it before returning.
+ *   - Device memory for temporaries comes from the CUDA stream-ordered
+ *     allocator of the current device; the calling thread's current device
+ *     must be the one that holds device-resident inputs.
+ */
+#ifndef BMJ_H
+#define BMJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define BMJ_OK                   0
+#define BMJ_ERR_INVALID_ARG     (-1)  /* NULL pointer, q == 0, p == 0, p > q, bad b/method, n < 0 */
+#define BMJ_ERR_UNSORTED        (-2)  /* tokens of a set not strictly increasing, or offsets decreasing */
+#define BMJ_ERR_EMPTY_SET       (-3)  /* a set with no token */
+#define BMJ_ERR_NEG_TOKEN       (-4)  /* a negative token id */
+#define BMJ_ERR_OOM             (-5)  /* device or host allocation failed */
+#define BMJ_ERR_OUTPUT_OVERFLOW (-6)  /* a caller-provided output is too small */
+#define BMJ_ERR_TIMEOUT         (-7)  /* a bounded device-side wait gave up */
+#define BMJ_ERR_CUDA            (-8)  /* a CUDA runtime call failed */
+#define BMJ_ERR_TOO_LARGE       (-9)  /* more than 2^31 - 1 sets, or a set of 2^24 tokens or more */
+
+/* ---- bitmap generation methods (Section 3.2) ---------------------------- */
+#define BMJ_XOR      0   /* Alg. 3b: toggle bit h(t); the paper's GPU default */
+#define BMJ_SET      1   /* Alg. 3a: set bit h(t) */
+#define BMJ_NEXT     2   /* Alg. 3c: set the first unset bit at or after h(t), circularly; all ones if n >= b */
+#define BMJ_COMBINED 3   /* Alg. 4: Next / Set / Xor chosen from the threshold (switch points on 2p/(p+q)) */
+
+/* ---- similarity functions (Table 1) ------------------------------------- */
+#define BMJ_JACCARD  0
+
+/* A collection of n_sets sets in CSR form: set x holds
+ * tokens[offsets[x] .. offsets[x+1]-1].  offsets has n_sets+1 entries and
+ * offsets[0] == 0.  on_device != 0 means both arrays live in device memory;
+ * otherwise they are host memory (pinned or pageable) and are copied in. */
+typedef struct {
+    int64_t        n_sets;
+    const int64_t *offsets;
+    const int32_t *tokens;
+    int32_t        on_device;
+    int32_t        reserved;
+} bmj_collection;
+
+/* A pair list owned by the library until bmj_pairs_free().  Pair k is
+ * (a[k], b[k]) in original 0-based set ids with a[k] < b[k]; pairs are sorted
+ * by (a, b) and unique.  on_device says where a and b live. */
+typedef struct {
+    int64_t   n;
+    uint32_t *a;
+    uint32_t *b;
+    int32_t   on_device;
+    int32_t   reserved;
+} bmj_pairs;
+
+/* Tuning and placement options; bmj_default_options() fills the defaults. */
+typedef struct {
+    int32_t b;                 /* bitmap bits (default 64) */
+    int32_t method;            /* BMJ_XOR (default) / SET / NEXT / COMBINED */
+    int32_t output_on_device;  /* 1: pairs returned in device memory; 0 (default): host memory */
+    int32_t validate;          /* 1 (default): check the collection invariants on the device */
+    int64_t queue_cap;         /* survivor-queue capacity in pairs; 0 (default) = automatic */
+    void   *stream;            /* cudaStream_t; NULL = legacy default stream */
+    int32_t rows_per_thread;   /* filter register blocking: 0 = automatic */
+    int32_t reserved[7];
+} bmj_options;
+
+/* Counters and stage times of one join.  Pair counts are exact and do not
+ * depend on the launch configuration. */
+typedef struct {
+    int64_t window_pairs;   /* pairs (i, j) inside the length-filter window = pairs the Bitmap Filter evaluated */
+    int64_t survivors;      /* pairs that passed the Bitmap Filter (verified exactly) */
+    int64_t results;        /* similar pairs returned */
+    int64_t filter_passes;  /* filter launches over the whole window (1 unless the survivor queue had to grow) */
+    int32_t n_launches;     /* CUDA kernels launched by this call */
+    int32_t b;              /* bitmap bits used */
+    int32_t method;         /* generation method used (COMBINED resolved) */
+    int32_t max_set_size;
+    float   ms_prepare;     /* validation, size sort, sorted-CSR gather and bitmap build */
+    float   ms_filter;      /* Bitmap Filter kernel(s) */
+    float   ms_verify;      /* verification kernel(s) */
+    float   ms_output;      /* result sort, id mapping and output copy */
+    float   ms_total;       /* whole call, device time on the stream */
+    float   reserved_f;
+} bmj_stats;
+
+/* Fills *opt with the defaults listed above.  Never fails. */
+void bmj_default_options(bmj_options *opt);
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *bmj_strerror(int status);
+
+/*
+ * Per-set bitmaps (Section 3.2; Alg. 5 initialisation).
+ *   coll    collection (host or device, see bmj_collection)
+ *   b       bitmap bits, a multiple of 64 in [64, 4096]
+ *   method  BMJ_XOR, BMJ_SET or BMJ_NEXT (BMJ_COMBINED needs a threshold:
+ *           BMJ_ERR_INVALID_ARG)
+ *   out     caller-owned array of n_sets * (b/64) uint64 words, set x at
+ *           out[x*(b/64) .. x*(b/64)+b/64-1], in original set order; it is
+ *           device memory iff coll->on_device, otherwise host memory
+ *   stream  cudaStream_t as void* (NULL = legacy default stream)
+ * The call validates the collection, writes every word of out and, for host
+ * output, synchronises the stream before returning.
+ */
+int bmj_build_bitmaps(const bmj_collection *coll, int b, int method, uint64_t *out,
+                      void *stream);
+
+/*
+ * Exact self-join with the Bitmap Filter (Section 4.2, Alg. 6, with the
+ * verification moved onto the GPU).
+ *   coll    collection (host or device)
+ *   sim     BMJ_JACCARD (the only function implemented)
+ *   p, q    threshold p/q, 0 < p <= q
+ *   opt     options (NULL = defaults)
+ *   out     receives the library-owned, canonical pair list (free it with
+ *           bmj_pairs_free); on error it is left empty
+ *   stats   optional (NULL allowed): counters and stage times
+ * The stream in opt is synchronised before the call returns.
+ */
+int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
+                  const bmj_options *opt, bmj_pairs *out, bmj_stats *stats);
+
+/* Releases a pair list returned by the library and empties *pairs.
+ * Safe on an empty or already freed list. */
+void bmj_pairs_free(bmj_pairs *pairs);
+
+/* Number of CUDA kernels this library has launched in this process (a
+ * monotone counter, for accounting in benchmarks). */
+int64_t bmj_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BMJ_H */

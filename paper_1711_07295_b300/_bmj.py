@@ -1,0 +1,254 @@
+"""ctypes binding of ``libbmj.so`` (the C ABI declared in include/bmj.h).
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  Functions keep the C names.  Arrays may be torch tensors (CUDA or
+CPU) or numpy arrays; CUDA tensors are passed as device pointers on the
+current torch stream, everything else as host pointers.  There is no CPU
+fallback: if the library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbmj.so")
+
+BMJ_OK = 0
+BMJ_ERR_INVALID_ARG = -1
+BMJ_ERR_UNSORTED = -2
+BMJ_ERR_EMPTY_SET = -3
+BMJ_ERR_NEG_TOKEN = -4
+BMJ_ERR_OOM = -5
+BMJ_ERR_OUTPUT_OVERFLOW = -6
+BMJ_ERR_TIMEOUT = -7
+BMJ_ERR_CUDA = -8
+BMJ_ERR_TOO_LARGE = -9
+
+BMJ_XOR, BMJ_SET, BMJ_NEXT, BMJ_COMBINED = 0, 1, 2, 3
+BMJ_JACCARD = 0
+METHODS = {"xor": BMJ_XOR, "set": BMJ_SET, "next": BMJ_NEXT, "combined": BMJ_COMBINED}
+
+
+class bmj_collection(C.Structure):
+    _fields_ = [("n_sets", C.c_int64), ("offsets", C.c_void_p), ("tokens", C.c_void_p),
+                ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bmj_pairs(C.Structure):
+    _fields_ = [("n", C.c_int64), ("a", C.c_void_p), ("b", C.c_void_p),
+                ("on_device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class bmj_options(C.Structure):
+    _fields_ = [("b", C.c_int32), ("method", C.c_int32), ("output_on_device", C.c_int32),
+                ("validate", C.c_int32), ("queue_cap", C.c_int64), ("stream", C.c_void_p),
+                ("rows_per_thread", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class bmj_stats(C.Structure):
+    _fields_ = [("window_pairs", C.c_int64), ("survivors", C.c_int64), ("results", C.c_int64),
+                ("filter_passes", C.c_int64), ("n_launches", C.c_int32), ("b", C.c_int32),
+                ("method", C.c_int32), ("max_set_size", C.c_int32), ("ms_prepare", C.c_float),
+                ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
+                ("ms_total", C.c_float), ("reserved_f", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class BmjError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {bmj_strerror(status)} (status {status})")
+
+
+_lib = None
+
+# Every exported entry point of include/bmj.h with its ctypes signature.
+SIGNATURES = {
+    "bmj_default_options": (None, [C.POINTER(bmj_options)]),
+    "bmj_strerror": (C.c_char_p, [C.c_int]),
+    "bmj_build_bitmaps": (C.c_int, [C.POINTER(bmj_collection), C.c_int, C.c_int, C.c_void_p,
+                                    C.c_void_p]),
+    "bmj_self_join": (C.c_int, [C.POINTER(bmj_collection), C.c_int, C.c_uint32, C.c_uint32,
+                                C.POINTER(bmj_options), C.POINTER(bmj_pairs),
+                                C.POINTER(bmj_stats)]),
+    "bmj_pairs_free": (None, [C.POINTER(bmj_pairs)]),
+    "bmj_kernel_launches": (C.c_int64, []),
+}
+
+
+def lib():
+    """Load ``libbmj.so`` (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------------------
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def _host_array(x, dtype):
+    if hasattr(x, "numpy"):
+        x = x.numpy()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _stream_of(stream, on_device):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    if on_device:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(0)
+
+
+def make_collection(offsets, tokens):
+    """Marshal (offsets, tokens) into a bmj_collection; returns (struct, keepalive)."""
+    if _is_cuda_tensor(offsets) != _is_cuda_tensor(tokens):
+        raise ValueError("offsets and tokens must both be CUDA tensors or both host arrays")
+    on_dev = _is_cuda_tensor(offsets)
+    if on_dev:
+        import torch
+        if offsets.dtype != torch.int64 or tokens.dtype != torch.int32:
+            raise TypeError("offsets must be int64 and tokens int32")
+        offsets, tokens = offsets.contiguous(), tokens.contiguous()
+    else:
+        offsets, tokens = _host_array(offsets, np.int64), _host_array(tokens, np.int32)
+    coll = bmj_collection(len(offsets) - 1, _ptr(offsets), _ptr(tokens), 1 if on_dev else 0, 0)
+    return coll, (offsets, tokens)
+
+
+def bmj_default_options() -> bmj_options:
+    o = bmj_options()
+    lib().bmj_default_options(C.byref(o))
+    return o
+
+
+def bmj_strerror(status: int) -> str:
+    return lib().bmj_strerror(int(status)).decode()
+
+
+def bmj_kernel_launches() -> int:
+    return int(lib().bmj_kernel_launches())
+
+
+def bmj_build_bitmaps(offsets, tokens, b: int = 64, method: int = BMJ_XOR, out=None,
+                      stream=None):
+    """Bitmaps uint64[N, b/64] of a collection in original set order.
+
+    Device tensors in -> device tensor out (torch.int64 viewed as uint64 words);
+    host arrays in -> numpy uint64 out.
+    """
+    coll, keep = make_collection(offsets, tokens)
+    n = coll.n_sets
+    W = b // 64 if b > 0 else 0
+    if out is None:
+        if coll.on_device:
+            import torch
+            out = torch.empty((max(n, 0), max(W, 1)), dtype=torch.int64, device=offsets.device)
+        else:
+            out = np.zeros((max(n, 0), max(W, 1)), np.uint64)
+    st = lib().bmj_build_bitmaps(C.byref(coll), int(b), int(method), _ptr(out),
+                                 _stream_of(stream, coll.on_device))
+    del keep
+    if st != BMJ_OK:
+        raise BmjError(st, "bmj_build_bitmaps")
+    return out
+
+
+class DevicePairs:
+    """Library-owned device pair list; freed with bmj_pairs_free on release()."""
+
+    def __init__(self, pairs: bmj_pairs, device):
+        self._p = pairs
+        self.n = int(pairs.n)
+        self.device = device
+
+    def _view(self, ptr):
+        import torch
+        if self.n == 0:
+            return torch.zeros(0, dtype=torch.int32, device=self.device)
+
+        class _CAI:
+            __cuda_array_interface__ = {"shape": (self.n,), "typestr": "<u4",
+                                        "data": (int(ptr), False), "version": 3}
+        return torch.as_tensor(_CAI(), device=self.device).view(torch.int32)
+
+    @property
+    def a(self):
+        return self._view(self._p.a)
+
+    @property
+    def b(self):
+        return self._view(self._p.b)
+
+    def release(self):
+        if self._p is not None:
+            lib().bmj_pairs_free(C.byref(self._p))
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BMJ_XOR,
+                  output_on_device: bool = False, queue_cap: int = 0, validate: bool = True,
+                  stream=None, sim: int = BMJ_JACCARD):
+    """Exact Jaccard self-join at threshold p/q.
+
+    Returns ``(a, b, stats)``: original ids with a < b sorted by (a, b), as
+    numpy uint32 arrays (host output) or a :class:`DevicePairs` as ``a`` with
+    ``b`` None (device output); ``stats`` is a dict of the bmj_stats fields.
+    """
+    coll, keep = make_collection(offsets, tokens)
+    o = bmj_default_options()
+    o.b = int(b)
+    o.method = int(method)
+    o.output_on_device = 1 if output_on_device else 0
+    o.validate = 1 if validate else 0
+    o.queue_cap = int(queue_cap)
+    o.stream = _stream_of(stream, coll.on_device)
+    pairs = bmj_pairs()
+    st_ = bmj_stats()
+    st = lib().bmj_self_join(C.byref(coll), int(sim), C.c_uint32(int(p)), C.c_uint32(int(q)),
+                             C.byref(o), C.byref(pairs), C.byref(st_))
+    del keep
+    if st != BMJ_OK:
+        raise BmjError(st, "bmj_self_join")
+    stats = st_.as_dict()
+    if output_on_device:
+        dev = offsets.device if hasattr(offsets, "device") else "cuda"
+        return DevicePairs(pairs, dev), None, stats
+    n = int(pairs.n)
+    if n == 0:
+        lib().bmj_pairs_free(C.byref(pairs))
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint32), stats
+    a = np.ctypeslib.as_array(C.cast(pairs.a, C.POINTER(C.c_uint32)), shape=(n,)).copy()
+    bb = np.ctypeslib.as_array(C.cast(pairs.b, C.POINTER(C.c_uint32)), shape=(n,)).copy()
+    lib().bmj_pairs_free(C.byref(pairs))
+    return a, bb, stats

@@ -1,0 +1,515 @@
+// join.cu -- host orchestration of the self-join and the C ABI entry points.
+//
+// bmj_self_join runs the stages of the GPU algorithm (Alg. 6) on one stream:
+//   validate -> size sort -> sorted CSR + bitmaps -> window tiles ->
+//   Bitmap Filter -> exact verification -> canonical result sort -> output.
+// The host reads back three small counters (validation flags and maximum
+// size; survivor count; result count), which size the next allocations.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace bmj {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+void retain_pool_memory(int device) {
+    static std::mutex mu;
+    static bool done[128] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device < 0 || device >= 128 || done[device]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[device] = true;
+}
+
+static int num_sms(int device) {
+    static std::mutex mu;
+    static int cache[128] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device >= 0 && device < 128 && cache[device]) return cache[device];
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+        v = 148;
+    if (device >= 0 && device < 128) cache[device] = v;
+    return v;
+}
+
+static int bit_length(uint64_t v) {
+    int b = 0;
+    while (v) {
+        b++;
+        v >>= 1;
+    }
+    return b;
+}
+
+// Alg. 4 with its switch points read on the normalised overlap 2p/(p+q).
+static int combined_method(uint32_t p, uint32_t q) {
+    const uint64_t P = p, D = (uint64_t)p + q;
+    if (200 * P <= 56 * D) return BMJ_NEXT;
+    if (200 * P >= 73 * D) return BMJ_XOR;
+    return BMJ_SET;
+}
+
+static int flags_to_status(int flags) {
+    if (flags & kFlagTooLarge) return BMJ_ERR_TOO_LARGE;
+    if (flags & kFlagUnsorted) return BMJ_ERR_UNSORTED;
+    if (flags & kFlagNegative) return BMJ_ERR_NEG_TOKEN;
+    if (flags & kFlagEmpty) return BMJ_ERR_EMPTY_SET;
+    return BMJ_OK;
+}
+
+static bool valid_b(int b) { return b >= 64 && b <= 4096 && (b % 64) == 0; }
+
+// Device-resident view of a collection (copied in when it is host memory).
+struct DevColl {
+    const int64_t *off = nullptr;
+    const int32_t *tok = nullptr;
+    int64_t n = 0;
+    int64_t ntok = 0;
+};
+
+static int stage_collection(const bmj_collection *c, Arena &A, cudaStream_t s, DevColl *d) {
+    d->n = c->n_sets;
+    if (c->on_device) {
+        int64_t v = 0;
+        BMJ_CHECK(cudaMemcpyAsync(&v, c->offsets + c->n_sets, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaStreamSynchronize(s));
+        d->off = c->offsets;
+        d->tok = c->tokens;
+        d->ntok = v;
+        if (v < 0) return BMJ_ERR_UNSORTED;
+        return BMJ_OK;
+    }
+    d->ntok = c->offsets[c->n_sets];
+    if (d->ntok < 0) return BMJ_ERR_UNSORTED;
+    int64_t *off = nullptr;
+    int32_t *tok = nullptr;
+    int st = A.alloc(&off, (size_t)(c->n_sets + 1));
+    if (!st) st = A.alloc(&tok, (size_t)d->ntok);
+    if (st) return st;
+    BMJ_CHECK(cudaMemcpyAsync(off, c->offsets, (c->n_sets + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+    if (d->ntok)
+        BMJ_CHECK(cudaMemcpyAsync(tok, c->tokens, d->ntok * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s));
+    d->off = off;
+    d->tok = tok;
+    return BMJ_OK;
+}
+
+// Validation: returns the status and the maximum set size.
+static int validate(const DevColl &d, bool check_tokens, Arena &A, cudaStream_t s,
+                    uint32_t **sizes, uint32_t **ids, int *max_size) {
+    int *info = nullptr;
+    int st = A.alloc(&info, 2);
+    if (!st) st = A.alloc(sizes, (size_t)d.n);
+    if (!st) st = A.alloc(ids, (size_t)d.n);
+    if (st) return st;
+    BMJ_CHECK(cudaMemsetAsync(info, 0, 2 * sizeof(int), s));
+    st = launch_validate(d.off, d.tok, d.n, d.ntok, check_tokens ? 1 : 0, *sizes, *ids, info, s);
+    if (st) return st;
+    int h[2] = {0, 0};
+    BMJ_CHECK(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BMJ_CHECK(cudaStreamSynchronize(s));
+    *max_size = h[1];
+    return flags_to_status(h[0]);
+}
+
+struct Events {
+    cudaEvent_t e[8];
+    int n = 0;
+    Events() {
+        for (auto &x : e) x = nullptr;
+    }
+    int init() {
+        for (int k = 0; k < 8; k++) BMJ_CHECK(cudaEventCreate(&e[k]));
+        n = 8;
+        return BMJ_OK;
+    }
+    ~Events() {
+        for (int k = 0; k < n; k++) cudaEventDestroy(e[k]);
+    }
+    float ms(int a, int b) const {
+        float v = 0.f;
+        if (cudaEventElapsedTime(&v, e[a], e[b]) != cudaSuccess) {
+            cudaGetLastError();
+            return 0.f;
+        }
+        return v;
+    }
+};
+
+static int64_t auto_queue_cap(int64_t window) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = (size_t)8 << 30;
+    }
+    int64_t budget = (int64_t)(free_b / 4 / sizeof(uint2));
+    int64_t cap = window / 128;
+    if (cap < ((int64_t)1 << 20)) cap = (int64_t)1 << 20;
+    if (cap > budget) cap = budget;
+    if (cap > ((int64_t)1 << 32)) cap = (int64_t)1 << 32;
+    if (cap < 1) cap = 1;
+    return cap;
+}
+
+static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
+                          const bmj_options &o, bmj_pairs *out, bmj_stats *stats) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const int64_t launches0 = launches();
+    int dev = 0;
+    BMJ_CHECK(cudaGetDevice(&dev));
+    retain_pool_memory(dev);
+    const int sms = num_sms(dev);
+    bmj_stats stl;
+    memset(&stl, 0, sizeof(stl));
+    const int b = o.b;
+    const int W = b / 64;
+    int method = o.method == BMJ_COMBINED ? combined_method(p, q) : o.method;
+    stl.b = b;
+    stl.method = method;
+
+    Events ev;
+    int st = ev.init();
+    if (st) return st;
+    Arena A(s);
+    BMJ_CHECK(cudaEventRecord(ev.e[0], s));
+    DevColl d;
+    st = stage_collection(coll, A, s, &d);
+    if (st) return st;
+    const int64_t n = d.n;
+
+    uint32_t *sizes = nullptr, *ids = nullptr;
+    int max_size = 0;
+    if (n > 0) {
+        st = validate(d, o.validate != 0, A, s, &sizes, &ids, &max_size);
+        if (st) return st;
+    }
+    stl.max_set_size = max_size;
+
+    uint64_t *keys_sorted = nullptr;
+    int64_t n_res = 0;
+    const int nbits = n > 1 ? bit_length((uint64_t)(n - 1)) : 1;
+    BMJ_CHECK(cudaEventRecord(ev.e[1], s));
+    if (n >= 2) {
+        // ---- size sort (ties by original id) and sorted CSR + bitmaps ----
+        uint32_t *ssz = nullptr, *perm = nullptr;
+        int64_t *soff = nullptr;
+        int32_t *stok = nullptr;
+        uint64_t *bm = nullptr;
+        st = A.alloc(&ssz, (size_t)n);
+        if (!st) st = A.alloc(&perm, (size_t)n);
+        if (!st) st = A.alloc(&soff, (size_t)n);
+        if (!st) st = A.alloc(&stok, (size_t)d.ntok);
+        if (!st) st = A.alloc(&bm, (size_t)n * W);
+        if (st) return st;
+        st = radix_sort_u32_pairs(sizes, ids, ssz, perm, n, bit_length((uint64_t)max_size), A, s);
+        if (st) return st;
+        st = launch_widen(ssz, soff, n, s);
+        if (!st) st = exclusive_scan_i64(soff, soff, n, nullptr, A, s);
+        if (!st)
+            st = launch_gather_build(perm, d.off, d.tok, soff, stok, bm, n, b, method, s);
+        if (st) return st;
+
+        // ---- thresholds per |x|+|y|, window tiles, window size ----
+        const int64_t n_s = 2 * (int64_t)max_size + 1;
+        int32_t *need = nullptr, *lim = nullptr;
+        const int tile_rows = filter_tile_rows(W);
+        const int chunk_cols = W <= 4 ? 4096 : 2048;
+        const int64_t n_tiles = (n + tile_rows - 1) / tile_rows;
+        int32_t *tile_c0 = nullptr;
+        int64_t *tile_off = nullptr;
+        unsigned long long *ctr = nullptr;  // [0] window, [1] survivors, [2] item counter, [3] results
+        st = A.alloc(&need, (size_t)n_s);
+        if (!st) st = A.alloc(&lim, (size_t)n_s);
+        if (!st) st = A.alloc(&tile_c0, (size_t)n_tiles);
+        if (!st) st = A.alloc(&tile_off, (size_t)n_tiles + 1);
+        if (!st) st = A.alloc(&ctr, 4);
+        if (st) return st;
+        BMJ_CHECK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+        st = launch_tables(need, lim, n_s, p, q, s);
+        if (!st)
+            st = launch_tiles(ssz, n, p, q, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s);
+        if (!st) st = exclusive_scan_i64(tile_off, tile_off, n_tiles, tile_off + n_tiles, A, s);
+        if (!st) st = launch_window_count(ssz, n, p, q, &ctr[0], s);
+        if (st) return st;
+        BMJ_CHECK(cudaEventRecord(ev.e[2], s));
+        int64_t hv[2] = {0, 0};
+        BMJ_CHECK(cudaMemcpyAsync(&hv[0], ctr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaMemcpyAsync(&hv[1], tile_off + n_tiles, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaStreamSynchronize(s));
+        stl.window_pairs = hv[0];
+        const int64_t n_items = hv[1];
+
+        // ---- Bitmap Filter ----
+        int64_t qcap = o.queue_cap > 0 ? o.queue_cap : auto_queue_cap(stl.window_pairs);
+        uint2 *queue = nullptr;
+        st = A.alloc(&queue, (size_t)qcap);
+        if (st) return st;
+        FilterArgs fa;
+        fa.bm = bm;
+        fa.ssz = ssz;
+        fa.lim = lim;
+        fa.n = n;
+        fa.p = p;
+        fa.q = q;
+        fa.tile_item_off = tile_off;
+        fa.tile_c0 = tile_c0;
+        fa.n_tiles = n_tiles;
+        fa.n_items = n_items;
+        fa.tile_rows = tile_rows;
+        fa.chunk_cols = chunk_cols;
+        fa.queue = queue;
+        fa.qcount = &ctr[1];
+        fa.qcap = qcap;
+        fa.item_counter = &ctr[2];
+        int64_t n_surv = 0;
+        for (int pass = 0; pass < 2; pass++) {
+            BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+            st = launch_filter(fa, W, sms, s);
+            if (st) return st;
+            BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+            BMJ_CHECK(cudaMemcpyAsync(&n_surv, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaStreamSynchronize(s));
+            stl.filter_passes++;
+            stl.ms_filter += ev.ms(3, 4);
+            if (n_surv <= qcap) break;
+            // The queue was too small: every survivor was counted, so rerun
+            // the filter once with exactly enough room (no pair is dropped).
+            A.free_one(queue);
+            qcap = n_surv;
+            st = A.alloc(&queue, (size_t)qcap);
+            if (st) return st;
+            fa.queue = queue;
+            fa.qcap = qcap;
+            BMJ_CHECK(cudaMemsetAsync(&ctr[1], 0, 2 * sizeof(unsigned long long), s));
+        }
+        stl.survivors = n_surv;
+
+        // ---- exact verification ----
+        uint64_t *keys = nullptr;
+        st = A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1));
+        if (st) return st;
+        BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+        st = launch_verify(queue, n_surv, soff, stok, ssz, perm, need, keys, &ctr[3], nbits, sms, s);
+        if (st) return st;
+        BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+        BMJ_CHECK(cudaMemcpyAsync(&n_res, &ctr[3], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaStreamSynchronize(s));
+        stl.ms_verify = ev.ms(5, 6);
+        A.free_one(queue);
+
+        // ---- canonical order ----
+        if (n_res > 0) {
+            st = A.alloc(&keys_sorted, (size_t)n_res);
+            if (!st) st = radix_sort_u64(keys, keys_sorted, n_res, 2 * nbits, A, s);
+            if (st) return st;
+        }
+    } else {
+        BMJ_CHECK(cudaEventRecord(ev.e[2], s));
+        BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+        BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+    }
+    stl.results = n_res;
+
+    // ---- output ----
+    bmj_pairs res;
+    memset(&res, 0, sizeof(res));
+    res.on_device = o.output_on_device ? 1 : 0;
+    if (n_res > 0) {
+        if (o.output_on_device) {
+            if (cudaMalloc(&res.a, n_res * sizeof(uint32_t)) != cudaSuccess ||
+                cudaMalloc(&res.b, n_res * sizeof(uint32_t)) != cudaSuccess) {
+                cudaGetLastError();
+                if (res.a) cudaFree(res.a);
+                return BMJ_ERR_OOM;
+            }
+            st = launch_unpack(keys_sorted, n_res, nbits, res.a, res.b, s);
+        } else {
+            uint32_t *da = nullptr, *db = nullptr;
+            st = A.alloc(&da, (size_t)n_res);
+            if (!st) st = A.alloc(&db, (size_t)n_res);
+            if (!st) st = launch_unpack(keys_sorted, n_res, nbits, da, db, s);
+            if (!st) {
+                res.a = (uint32_t *)malloc(n_res * sizeof(uint32_t));
+                res.b = (uint32_t *)malloc(n_res * sizeof(uint32_t));
+                if (!res.a || !res.b) st = BMJ_ERR_OOM;
+            }
+            if (!st) {
+                cudaError_t e1 = cudaMemcpyAsync(res.a, da, n_res * sizeof(uint32_t),
+                                                 cudaMemcpyDeviceToHost, s);
+                cudaError_t e2 = cudaMemcpyAsync(res.b, db, n_res * sizeof(uint32_t),
+                                                 cudaMemcpyDeviceToHost, s);
+                if (e1 != cudaSuccess || e2 != cudaSuccess) st = status_of(e1 ? e1 : e2);
+            }
+        }
+        if (st) {
+            bmj_pairs_free(&res);
+            return st;
+        }
+        res.n = n_res;
+    }
+    BMJ_CHECK(cudaEventRecord(ev.e[7], s));
+    A.release();
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        bmj_pairs_free(&res);
+        return status_of(e);
+    }
+    stl.ms_prepare = ev.ms(0, 2);
+    stl.ms_output = ev.ms(6, 7);
+    stl.ms_total = ev.ms(0, 7);
+    stl.n_launches = (int32_t)(launches() - launches0);
+    *out = res;
+    if (stats) *stats = stl;
+    return BMJ_OK;
+}
+
+static int build_bitmaps_impl(const bmj_collection *coll, int b, int method, uint64_t *out,
+                              cudaStream_t s) {
+    int dev = 0;
+    BMJ_CHECK(cudaGetDevice(&dev));
+    retain_pool_memory(dev);
+    Arena A(s);
+    DevColl d;
+    int st = stage_collection(coll, A, s, &d);
+    if (st) return st;
+    if (d.n == 0) return BMJ_OK;
+    uint32_t *sizes = nullptr, *ids = nullptr;
+    int max_size = 0;
+    st = validate(d, true, A, s, &sizes, &ids, &max_size);
+    if (st) return st;
+    const int W = b / 64;
+    uint64_t *dst = out;
+    if (!coll->on_device) {
+        st = A.alloc(&dst, (size_t)d.n * W);
+        if (st) return st;
+    }
+    st = launch_gather_build(nullptr, d.off, d.tok, nullptr, nullptr, dst, d.n, b, method, s);
+    if (st) return st;
+    if (!coll->on_device)
+        BMJ_CHECK(cudaMemcpyAsync(out, dst, (size_t)d.n * W * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, s));
+    A.release();
+    BMJ_CHECK(cudaStreamSynchronize(s));
+    return BMJ_OK;
+}
+
+}  // namespace bmj
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void bmj_default_options(bmj_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->b = 64;
+    opt->method = BMJ_XOR;
+    opt->output_on_device = 0;
+    opt->validate = 1;
+    opt->queue_cap = 0;
+    opt->stream = nullptr;
+    opt->rows_per_thread = 0;
+}
+
+const char *bmj_strerror(int status) {
+    switch (status) {
+        case BMJ_OK: return "ok";
+        case BMJ_ERR_INVALID_ARG: return "invalid argument";
+        case BMJ_ERR_UNSORTED: return "tokens of a set are not strictly increasing (or offsets are inconsistent)";
+        case BMJ_ERR_EMPTY_SET: return "empty set in the collection";
+        case BMJ_ERR_NEG_TOKEN: return "negative token id";
+        case BMJ_ERR_OOM: return "out of memory";
+        case BMJ_ERR_OUTPUT_OVERFLOW: return "output buffer too small";
+        case BMJ_ERR_TIMEOUT: return "bounded device wait timed out";
+        case BMJ_ERR_CUDA: return "CUDA runtime error";
+        case BMJ_ERR_TOO_LARGE: return "collection too large (n_sets >= 2^31 or a set of >= 2^24 tokens)";
+        default: return "unknown status";
+    }
+}
+
+static int check_collection(const bmj_collection *c) {
+    if (!c) return BMJ_ERR_INVALID_ARG;
+    if (c->n_sets < 0) return BMJ_ERR_INVALID_ARG;
+    if (c->n_sets > 0x7fffffffLL) return BMJ_ERR_TOO_LARGE;
+    if (!c->offsets) return BMJ_ERR_INVALID_ARG;
+    if (c->n_sets > 0 && !c->tokens) return BMJ_ERR_INVALID_ARG;
+    return BMJ_OK;
+}
+
+int bmj_build_bitmaps(const bmj_collection *coll, int b, int method, uint64_t *out,
+                      void *stream) {
+    int st = check_collection(coll);
+    if (st) return st;
+    if (!bmj::valid_b(b)) return BMJ_ERR_INVALID_ARG;
+    if (method != BMJ_XOR && method != BMJ_SET && method != BMJ_NEXT) return BMJ_ERR_INVALID_ARG;
+    if (coll->n_sets > 0 && !out) return BMJ_ERR_INVALID_ARG;
+    try {
+        st = bmj::build_bitmaps_impl(coll, b, method, out, (cudaStream_t)stream);
+    } catch (...) {
+        st = BMJ_ERR_OOM;
+    }
+    cudaGetLastError();
+    return st;
+}
+
+int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
+                  const bmj_options *opt, bmj_pairs *out, bmj_stats *stats) {
+    if (!out) return BMJ_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    if (stats) memset(stats, 0, sizeof(*stats));
+    int st = check_collection(coll);
+    if (st) return st;
+    if (sim != BMJ_JACCARD) return BMJ_ERR_INVALID_ARG;
+    if (p == 0 || q == 0 || p > q) return BMJ_ERR_INVALID_ARG;
+    bmj_options o;
+    if (opt) o = *opt;
+    else bmj_default_options(&o);
+    if (!bmj::valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
+    if (o.method < BMJ_XOR || o.method > BMJ_COMBINED) return BMJ_ERR_INVALID_ARG;
+    if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
+    try {
+        st = bmj::self_join_impl(coll, p, q, o, out, stats);
+    } catch (...) {
+        st = BMJ_ERR_OOM;
+    }
+    if (st) {
+        bmj_pairs_free(out);
+        cudaGetLastError();
+    }
+    return st;
+}
+
+void bmj_pairs_free(bmj_pairs *pairs) {
+    if (!pairs) return;
+    if (pairs->on_device) {
+        if (pairs->a) cudaFree(pairs->a);
+        if (pairs->b) cudaFree(pairs->b);
+    } else {
+        free(pairs->a);
+        free(pairs->b);
+    }
+    pairs->a = nullptr;
+    pairs->b = nullptr;
+    pairs->n = 0;
+}
+
+int64_t bmj_kernel_launches(void) { return bmj::launches(); }
+
+}  // extern "C"

@@ -1,0 +1,558 @@
+// kernels.cu -- device kernels of the Bitmap Filter self-join.
+//
+// Stages (each cited where it is defined in the paper):
+//   k_validate       CSR invariants; sizes and ids for the size sort (Section 5
+//                    preprocessing: sets ordered by size)
+//   k_gather_build   sorted CSR gather + b-bit bitmaps (Section 3.2, Alg. 3a/3b/3c,
+//                    h(t) = t mod b as in Section 5.1)
+//   k_tables         need[S] / lim[S]: Jaccard as an overlap threshold (Table 1)
+//                    folded into the Eq. 2 test
+//   k_tiles,
+//   k_window_count   the length filter window j in [j0(i), i) (Table 2; Alg. 6)
+//   k_filter         the Bitmap Filter over every window pair (Alg. 5/6, Eq. 2)
+//   k_verify         exact overlap of the survivors by merge intersection
+//                    (the verification of Alg. 6's host code, moved on the GPU)
+//   k_unpack         canonical output pairs
+#include "kernels.cuh"
+
+namespace bmj {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int warp_inclusive_scan_i(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int u = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += u;
+    }
+    return v;
+}
+
+// First index j in [0, n) with ssz[j] >= v (n if none).
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n, uint64_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((uint64_t)a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Smallest size s' with q*s' >= p*s, i.e. ceil(p*s/q) (Table 2, Jaccard row, integer form).
+__device__ __forceinline__ uint64_t window_low(uint64_t s, uint32_t p, uint32_t q) {
+    return (s * p + q - 1) / q;
+}
+
+// ----------------------------------------------------------------------------
+__global__ void k_validate(const int64_t *__restrict__ off, const int32_t *__restrict__ tok,
+                           int64_t n, int64_t ntok, int check_tokens, uint32_t *__restrict__ sizes,
+                           uint32_t *__restrict__ ids, int *__restrict__ info) {
+    int flags = 0;
+    uint32_t mx = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const int64_t lo = off[x], hi = off[x + 1];
+        int64_t sz = hi - lo;
+        if (x == 0 && lo != 0) flags |= kFlagUnsorted;
+        if (lo < 0 || hi > ntok || sz < 0) {
+            flags |= kFlagUnsorted;
+            sz = 0;
+        } else if (sz == 0) {
+            flags |= kFlagEmpty;
+        } else if (sz > kMaxSetSize) {
+            flags |= kFlagTooLarge;
+            sz = 0;
+        } else if (check_tokens) {
+            int32_t prev = tok[lo];
+            if (prev < 0) flags |= kFlagNegative;
+            for (int64_t k = lo + 1; k < hi; k++) {
+                const int32_t t = tok[k];
+                if (t <= prev) flags |= kFlagUnsorted;
+                if (t < 0) flags |= kFlagNegative;
+                prev = t;
+            }
+        }
+        sizes[x] = (uint32_t)sz;
+        ids[x] = (uint32_t)x;
+        mx = max(mx, (uint32_t)sz);
+    }
+    flags = __reduce_or_sync(kFull, flags);
+    mx = __reduce_max_sync(kFull, mx);
+    if ((threadIdx.x & 31) == 0) {
+        if (flags) atomicOr(&info[0], flags);
+        atomicMax(&info[1], (int)mx);
+    }
+}
+
+__global__ void k_widen(const uint32_t *__restrict__ in, int64_t *__restrict__ out, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = in[i];
+}
+
+// One warp per set.  The bitmap is assembled in shared memory (one 64-word
+// slot per warp, enough for b <= 4096) and written out as whole words.
+constexpr int kBuildWarps = 8;
+
+__global__ void __launch_bounds__(kBuildWarps * 32)
+    k_gather_build(const uint32_t *__restrict__ perm, const int64_t *__restrict__ off,
+                   const int32_t *__restrict__ tok, const int64_t *__restrict__ soff,
+                   int32_t *__restrict__ stok, uint64_t *__restrict__ bm, int64_t n, int b,
+                   int method) {
+    __shared__ unsigned long long sbm[kBuildWarps][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int W = b >> 6;
+    const bool pow2 = (b & (b - 1)) == 0;
+    unsigned long long *mine = sbm[warp];
+    for (int64_t i = (int64_t)blockIdx.x * kBuildWarps + warp; i < n;
+         i += (int64_t)gridDim.x * kBuildWarps) {
+        const int64_t src = perm ? (int64_t)perm[i] : i;
+        const int64_t lo = off[src];
+        const int64_t cnt = off[src + 1] - lo;
+        const int32_t *x = tok + lo;
+        for (int w = lane; w < W; w += 32) mine[w] = 0ull;
+        __syncwarp();
+        if (stok) {
+            int32_t *y = stok + soff[i];
+            for (int64_t k = lane; k < cnt; k += 32) y[k] = x[k];
+        }
+        if (method == BMJ_NEXT) {
+            if (cnt >= b) {
+                for (int w = lane; w < W; w += 32) mine[w] = ~0ull;
+            } else if (lane == 0) {
+                // Alg. 3c: linear probing to the first unset bit at or after
+                // h(t), wrapping around; cnt < b guarantees a free bit, so the
+                // scan ends within W + 1 words.
+                for (int64_t k = 0; k < cnt; k++) {
+                    const uint32_t t = (uint32_t)x[k];
+                    const uint32_t h = pow2 ? (t & (uint32_t)(b - 1)) : (t % (uint32_t)b);
+                    int w = (int)(h >> 6);
+                    unsigned long long m = ~mine[w] & (~0ull << (h & 63));
+                    for (int guard = 0; m == 0ull && guard <= W; guard++) {
+                        w = (w + 1 == W) ? 0 : w + 1;
+                        m = ~mine[w];
+                    }
+                    mine[w] |= m & (~m + 1ull);
+                }
+            }
+        } else {
+            for (int64_t k = lane; k < cnt; k += 32) {
+                const uint32_t t = (uint32_t)x[k];
+                const uint32_t h = pow2 ? (t & (uint32_t)(b - 1)) : (t % (uint32_t)b);
+                const unsigned long long bit = 1ull << (h & 63);
+                if (method == BMJ_XOR) atomicXor(&mine[h >> 6], bit);  // Alg. 3b
+                else atomicOr(&mine[h >> 6], bit);                     // Alg. 3a
+            }
+        }
+        __syncwarp();
+        uint64_t *dst = bm + i * W;
+        for (int w = lane; w < W; w += 32) dst[w] = mine[w];
+        __syncwarp();
+    }
+}
+
+__global__ void k_tables(int32_t *__restrict__ need, int32_t *__restrict__ lim, int64_t n_s,
+                         uint32_t p, uint32_t q) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t d = (uint64_t)p + q;
+    for (int64_t S = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; S < n_s; S += stride) {
+        // Jaccard >= p/q  <=>  o*(p+q) >= p*S  <=>  o >= ceil(p*S/(p+q)) (Table 1).
+        const uint64_t nd = ((uint64_t)S * p + d - 1) / d;
+        need[S] = (int32_t)nd;
+        // floor((S - h)/2) >= nd  <=>  h <= S - 2*nd (Eq. 2 with its floor).
+        lim[S] = (int32_t)((int64_t)S - 2 * (int64_t)nd);
+    }
+}
+
+__global__ void k_tiles(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p, uint32_t q,
+                        int tile_rows, int chunk_cols, int64_t n_tiles,
+                        int32_t *__restrict__ tile_c0, int64_t *__restrict__ tile_items) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
+        const int64_t i0 = t * tile_rows;
+        const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i0], p, q));
+        const int64_t c0 = j0 & ~(int64_t)3;
+        const int64_t c_end = min(i0 + (int64_t)tile_rows, n) - 1;  // columns j < i <= c_end
+        const int64_t cols = c_end - c0;
+        tile_c0[t] = (int32_t)c0;
+        tile_items[t] = cols > 0 ? (cols + chunk_cols - 1) / chunk_cols : 0;
+    }
+}
+
+__global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p,
+                               uint32_t q, unsigned long long *__restrict__ out) {
+    unsigned long long acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i], p, q));
+        if (j0 < i) acc += (unsigned long long)(i - j0);
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(kFull, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// ----------------------------------------------------------------------------
+// Bitmap Filter.
+//
+// A work item is (row tile, column chunk).  A row tile is 32*R consecutive
+// sorted rows held by one warp: lane l owns rows i0 + l + 32k, k < R, with
+// their bitmaps in registers.  The chunk's columns are walked in groups of
+// 32: each lane loads one column (bitmap + size), then every column is
+// broadcast with __shfl_sync and compared against the R rows.
+//
+// For a pair (i, j), with S = |R[i]| + |R[j]| and h = popcount(b_i ^ b_j):
+//   in window  <=>  q*min(|R[i]|,|R[j]|) >= p*max(...)   (Table 2)
+//   survives   <=>  floor((S - h)/2) >= ceil(p*S/(p+q))  (Eq. 2 vs Table 1)
+//              <=>  h <= lim[S]
+// so each row keeps lim (or -1 outside the window) for the current column
+// size, refreshed only when the (warp-uniform) column size changes.  Pairs
+// with j >= i are excluded in the diagonal part of a tile.  Survivors are
+// compacted with one atomicAdd per warp and column group.
+template <int W, int R>
+__global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t *__restrict__ bm = a.bm;
+    const uint32_t *__restrict__ ssz = a.ssz;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= a.n_items) return;
+        int64_t lo = 0, hi = a.n_tiles;  // tile_item_off[lo] <= item < tile_item_off[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((unsigned long long)a.tile_item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int64_t t = lo;
+        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
+        const int64_t i0 = t * a.tile_rows;
+        const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
+        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
+        const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
+
+        uint64_t rb[R][W];
+        uint32_t rs[R];
+        int64_t ri[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const int64_t i = i0 + k * 32 + lane;
+            ri[k] = i;
+            if (i < a.n) {
+                rs[k] = ssz[i];
+#pragma unroll
+                for (int w = 0; w < W; w++) rb[k][w] = bm[i * W + w];
+            } else {
+                rs[k] = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) rb[k][w] = 0;
+            }
+        }
+        int lim[R];
+        uint32_t prev_cs = 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < R; k++) lim[k] = -1;
+
+        for (int64_t j = c0; j < c1; j += 32) {
+            const int gj = (int)min((int64_t)32, c1 - j);
+            uint64_t cb[W];
+            uint32_t cs = 0;
+            if (lane < gj) {
+                cs = ssz[j + lane];
+#pragma unroll
+                for (int w = 0; w < W; w++) cb[w] = bm[(j + lane) * W + w];
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; w++) cb[w] = 0;
+            }
+            const bool diag = (j + gj - 1) >= i0;
+            uint32_t mask[R];
+#pragma unroll
+            for (int k = 0; k < R; k++) mask[k] = 0;
+            uint32_t bit = 1u;
+            for (int cc = 0; cc < gj; cc++, bit <<= 1) {
+                const uint32_t s = __shfl_sync(kFull, cs, cc);
+                uint64_t c[W];
+#pragma unroll
+                for (int w = 0; w < W; w++) c[w] = __shfl_sync(kFull, cb[w], cc);
+                if (s != prev_cs) {  // warp-uniform
+                    prev_cs = s;
+#pragma unroll
+                    for (int k = 0; k < R; k++) {
+                        const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
+                        const bool in_win = rs[k] != 0 &&
+                                            (uint64_t)a.q * mn >= (uint64_t)a.p * mx;
+                        lim[k] = in_win ? a.lim[rs[k] + s] : -1;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < R; k++) {
+                    int h = 0;
+#pragma unroll
+                    for (int w = 0; w < W; w++) h += __popcll(rb[k][w] ^ c[w]);
+                    bool sv = h <= lim[k];
+                    if (diag) sv = sv && (j + cc < ri[k]);
+                    if (sv) mask[k] |= bit;
+                }
+            }
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < R; k++) cnt += __popc(mask[k]);
+            const int total = __reduce_add_sync(kFull, cnt);
+            if (total) {
+                const int excl = warp_inclusive_scan_i(cnt) - cnt;
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.qcount, (unsigned long long)total);
+                base = __shfl_sync(kFull, base, 0);
+                unsigned long long pos = base + excl;
+#pragma unroll
+                for (int k = 0; k < R; k++) {
+                    uint32_t m = mask[k];
+                    while (m) {
+                        const int bpos = __ffs(m) - 1;
+                        m &= m - 1;
+                        if (pos < (unsigned long long)a.qcap)
+                            a.queue[pos] = make_uint2((uint32_t)ri[k], (uint32_t)(j + bpos));
+                        pos++;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Generic-width variant for b not in {64, 128, 256, 512}: one row per lane,
+// bitmaps read from memory word by word.
+__global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int W) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= a.n_items) return;
+        int64_t lo = 0, hi = a.n_tiles;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((unsigned long long)a.tile_item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int64_t t = lo;
+        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
+        const int64_t i0 = t * a.tile_rows;
+        const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
+        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
+        const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
+        const int64_t i = i0 + lane;
+        const uint32_t rs = i < a.n ? a.ssz[i] : 0u;
+        const uint64_t *rowp = a.bm + (i < a.n ? i : 0) * W;
+        for (int64_t j = c0; j < c1; j += 32) {
+            const int gj = (int)min((int64_t)32, c1 - j);
+            uint32_t mask = 0;
+            for (int cc = 0; cc < gj; cc++) {
+                const int64_t jj = j + cc;
+                const uint32_t s = a.ssz[jj];
+                const uint32_t mn = min(rs, s), mx = max(rs, s);
+                const bool in_win = rs != 0 && (uint64_t)a.q * mn >= (uint64_t)a.p * mx;
+                if (!in_win || jj >= i) continue;
+                const uint64_t *colp = a.bm + jj * W;
+                int h = 0;
+                for (int w = 0; w < W; w++) h += __popcll(rowp[w] ^ colp[w]);
+                if (h <= a.lim[rs + s]) mask |= 1u << cc;
+            }
+            const int cnt = __popc(mask);
+            const int total = __reduce_add_sync(kFull, cnt);
+            if (total) {
+                const int excl = warp_inclusive_scan_i(cnt) - cnt;
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.qcount, (unsigned long long)total);
+                base = __shfl_sync(kFull, base, 0);
+                unsigned long long pos = base + excl;
+                uint32_t m = mask;
+                while (m) {
+                    const int bpos = __ffs(m) - 1;
+                    m &= m - 1;
+                    if (pos < (unsigned long long)a.qcap)
+                        a.queue[pos] = make_uint2((uint32_t)i, (uint32_t)(j + bpos));
+                    pos++;
+                }
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Verification: one survivor per thread, exact overlap by a merge of the two
+// sorted token arrays, stopping as soon as the outcome is decided (the overlap
+// reached need[S], or the remaining tokens cannot reach it).
+__global__ void __launch_bounds__(256)
+    k_verify(const uint2 *__restrict__ queue, int64_t n_surv, const int64_t *__restrict__ soff,
+             const int32_t *__restrict__ stok, const uint32_t *__restrict__ ssz,
+             const uint32_t *__restrict__ perm, const int32_t *__restrict__ need,
+             uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount, int nbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int64_t base = gw * 32; base < n_surv; base += warps * 32) {
+        const int64_t idx = base + lane;
+        bool similar = false;
+        uint64_t key = 0;
+        if (idx < n_surv) {
+            const uint2 pr = queue[idx];
+            const uint32_t si = ssz[pr.x], sj = ssz[pr.y];
+            const int nd = need[si + sj];
+            const int32_t *x = stok + soff[pr.x];
+            const int32_t *y = stok + soff[pr.y];
+            int a = 0, b = 0, o = 0;
+            const int na = (int)si, nb = (int)sj;
+            while (a < na && b < nb) {
+                if (o + min(na - a, nb - b) < nd) break;
+                const int32_t xa = x[a], yb = y[b];
+                o += (xa == yb);
+                a += (xa <= yb);
+                b += (yb <= xa);
+                if (o >= nd) break;
+            }
+            similar = o >= nd;
+            if (similar) {
+                const uint64_t u = perm[pr.x], v = perm[pr.y];
+                key = u < v ? ((u << nbits) | v) : ((v << nbits) | u);
+            }
+        }
+        const unsigned ball = __ballot_sync(kFull, similar);
+        if (ball) {
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(rcount, (unsigned long long)__popc(ball));
+            off = __shfl_sync(kFull, off, 0);
+            if (similar) keys[off + __popc(ball & ((1u << lane) - 1u))] = key;
+        }
+    }
+}
+
+__global__ void k_unpack(const uint64_t *__restrict__ keys, int64_t n, int nbits,
+                         uint32_t *__restrict__ a, uint32_t *__restrict__ b) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = keys[i];
+        a[i] = (uint32_t)(k >> nbits);
+        b[i] = (uint32_t)(k & mask);
+    }
+}
+
+unsigned grid_for(int64_t n, int threads, int64_t cap = 148 * 32) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+template <int W, int R>
+int launch_filter_t(const FilterArgs &a, int num_sms, cudaStream_t s) {
+    int per_sm = 0;
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<W, R>, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    int64_t warps_needed = a.n_items;
+    int64_t blocks = (int64_t)num_sms * per_sm;
+    const int64_t need_blocks = (warps_needed + 7) / 8;
+    if (need_blocks < blocks) blocks = need_blocks;
+    if (blocks < 1) blocks = 1;
+    BMJ_LAUNCH((k_filter<W, R>), (unsigned)blocks, 256, 0, s, a);
+    return BMJ_OK;
+}
+
+}  // namespace
+
+int launch_validate(const int64_t *off, const int32_t *tok, int64_t n, int64_t ntok,
+                    int check_tokens, uint32_t *sizes, uint32_t *ids, int *info, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_validate, grid_for(n, 256), 256, 0, s, off, tok, n, ntok, check_tokens, sizes,
+               ids, info);
+    return BMJ_OK;
+}
+
+int launch_widen(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_widen, grid_for(n, 256), 256, 0, s, in, out, n);
+    return BMJ_OK;
+}
+
+int launch_gather_build(const uint32_t *perm, const int64_t *off, const int32_t *tok,
+                        const int64_t *soff, int32_t *stok, uint64_t *bm, int64_t n, int b,
+                        int method, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_gather_build, grid_for(n, kBuildWarps, 148 * 64), kBuildWarps * 32, 0, s, perm,
+               off, tok, soff, stok, bm, n, b, method);
+    return BMJ_OK;
+}
+
+int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, uint32_t p, uint32_t q,
+                  cudaStream_t s) {
+    BMJ_LAUNCH(k_tables, grid_for(n_s, 256), 256, 0, s, need, lim, n_s, p, q);
+    return BMJ_OK;
+}
+
+int launch_tiles(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q, int tile_rows,
+                 int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int64_t *tile_items,
+                 cudaStream_t s) {
+    if (n_tiles <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_tiles, grid_for(n_tiles, 256), 256, 0, s, ssz, n, p, q, tile_rows, chunk_cols,
+               n_tiles, tile_c0, tile_items);
+    return BMJ_OK;
+}
+
+int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
+                        unsigned long long *out, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_window_count, grid_for(n, 256), 256, 0, s, ssz, n, p, q, out);
+    return BMJ_OK;
+}
+
+int filter_tile_rows(int W) {
+    switch (W) {
+        case 1: case 2: case 4: return 32 * 4;
+        case 8: return 32 * 2;
+        default: return 32;
+    }
+}
+
+int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s) {
+    if (a.n_items <= 0) return BMJ_OK;
+    switch (W) {
+        case 1: return launch_filter_t<1, 4>(a, num_sms, s);
+        case 2: return launch_filter_t<2, 4>(a, num_sms, s);
+        case 4: return launch_filter_t<4, 4>(a, num_sms, s);
+        case 8: return launch_filter_t<8, 2>(a, num_sms, s);
+        default: {
+            int per_sm = 0;
+            BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_generic, 256, 0));
+            if (per_sm < 1) per_sm = 1;
+            int64_t blocks = (int64_t)num_sms * per_sm;
+            const int64_t need_blocks = (a.n_items + 7) / 8;
+            if (need_blocks < blocks) blocks = need_blocks;
+            if (blocks < 1) blocks = 1;
+            BMJ_LAUNCH(k_filter_generic, (unsigned)blocks, 256, 0, s, a, W);
+            return BMJ_OK;
+        }
+    }
+}
+
+int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
+                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need, uint64_t *keys,
+                  unsigned long long *rcount, int nbits, int num_sms, cudaStream_t s) {
+    if (n_surv <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_verify, grid_for(n_surv, 256, (int64_t)num_sms * 8), 256, 0, s, queue, n_surv,
+               soff, stok, ssz, perm, need, keys, rcount, nbits);
+    return BMJ_OK;
+}
+
+int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,
+                  cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_unpack, grid_for(n, 256), 256, 0, s, keys, n, nbits, a, b);
+    return BMJ_OK;
+}
+
+}  // namespace bmj

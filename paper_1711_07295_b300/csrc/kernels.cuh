@@ -1,0 +1,83 @@
+// kernels.cuh -- device kernels of the self-join path and their launch helpers.
+#pragma once
+
+#include "bmj_internal.cuh"
+
+namespace bmj {
+
+// Validation flags (bit set on the device, read by the host).
+enum : int {
+    kFlagEmpty = 1,
+    kFlagNegative = 2,
+    kFlagUnsorted = 4,
+    kFlagTooLarge = 8,
+};
+
+constexpr int kMaxSetSize = (1 << 24) - 1;
+
+// Checks the CSR invariants of a collection, writes each set's size (as the
+// sort key) and its id (the sort value), and the maximum size.
+//   info[0] |= flags, info[1] = max size (atomicMax)
+int launch_validate(const int64_t *off, const int32_t *tok, int64_t n, int64_t ntok,
+                    int check_tokens, uint32_t *sizes, uint32_t *ids, int *info, cudaStream_t s);
+
+// Widens sorted uint32 sizes into int64 (input of the offsets scan).
+int launch_widen(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// Per set (in sorted order when perm != nullptr): gathers its tokens into the
+// sorted CSR (when stok != nullptr) and writes its b-bit bitmap to
+// bm[i*(b/64) ..] (Alg. 3a/3b/3c, h(t) = t mod b).
+int launch_gather_build(const uint32_t *perm, const int64_t *off, const int32_t *tok,
+                        const int64_t *soff, int32_t *stok, uint64_t *bm, int64_t n, int b,
+                        int method, cudaStream_t s);
+
+// need[S] = ceil(p*S/(p+q)) (the smallest overlap with Jaccard >= p/q when
+// |x|+|y| = S) and lim[S] = S - 2*need[S] (the largest Hamming distance
+// whose Eq. 2 bound still reaches need[S]), for S in [0, n_s).
+int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, uint32_t p, uint32_t q,
+                  cudaStream_t s);
+
+// Row tiles of `tile_rows` sorted rows: first window column (j0 of the tile's
+// first row, rounded down to a multiple of 4) and the number of column chunks
+// of `chunk_cols` columns.
+int launch_tiles(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q, int tile_rows,
+                 int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int64_t *tile_items,
+                 cudaStream_t s);
+
+// Sum over sorted rows i of (i - j0(i)): the pairs inside the length window.
+int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
+                        unsigned long long *out, cudaStream_t s);
+
+struct FilterArgs {
+    const uint64_t *bm;
+    const uint32_t *ssz;
+    const int32_t *lim;
+    int64_t n;
+    uint32_t p, q;
+    const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
+    const int32_t *tile_c0;
+    int64_t n_tiles;
+    int64_t n_items;
+    int tile_rows;
+    int chunk_cols;
+    uint2 *queue;
+    unsigned long long *qcount;
+    int64_t qcap;
+    unsigned long long *item_counter;
+};
+
+// The Bitmap Filter over every window pair (persistent, warp-level work items).
+int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s);
+int filter_tile_rows(int W);
+
+// Exact verification of the survivors; similar pairs are written as packed
+// keys (min_id << nbits) | max_id in original ids.
+int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
+                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need, uint64_t *keys,
+                  unsigned long long *rcount, int nbits, int num_sms, cudaStream_t s);
+
+// Splits packed keys into the (a, b) arrays of the output.
+int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,
+                  cudaStream_t s);
+
+}  // namespace bmj

@@ -1,0 +1,52 @@
+"""Run one self-join on a synthetic collection (a small driver for profilers).
+
+    python -m paper_1711_07295_b300.profile_join --sets 1000000 --p 19 --q 20 --b 64
+
+The collection is the 1,000,000-set workload shape (Zipf(s=1.1) tokens over
+200,000, sizes lognormal(2.3, 0.6) in [1, 500]) truncated or extended to
+--sets sets (seed 0).  The join runs --repeat times with the survivor queue
+sized from a first call, so that a profiler sees steady-state launches.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sets", type=int, default=1_000_000)
+    ap.add_argument("--p", type=int, default=19)
+    ap.add_argument("--q", type=int, default=20)
+    ap.add_argument("--b", type=int, default=64)
+    ap.add_argument("--method", default="xor")
+    ap.add_argument("--repeat", type=int, default=2)
+    args = ap.parse_args()
+
+    import torch
+    from paper_1711_07295_b300 import _bmj, inputs
+    spec = inputs.spec_1m(seed=0)
+    spec = inputs.CollectionSpec(args.sets, spec.universe, spec.zipf_s, spec.size_dist, seed=0)
+    off, tok = inputs.gen_collection(spec)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    m = _bmj.METHODS[args.method]
+    res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m,
+                                    output_on_device=True)
+    res.release()
+    cap = max(1, st["survivors"])
+    for _ in range(args.repeat):
+        res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m,
+                                        output_on_device=True, queue_cap=cap)
+        res.release()
+    torch.cuda.synchronize()
+    print(json.dumps({"sets": args.sets, "threshold": f"{args.p}/{args.q}", "b": args.b, **st}))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,82 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/bmj.h, and rejects bad arguments before touching CUDA."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1711_07295_b300 import _bmj
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bmj.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(bmj_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bmj_build_bitmaps", "bmj_self_join", "bmj_pairs_free", "bmj_strerror",
+                     "bmj_default_options"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _bmj.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), f"libbmj.so does not export {name}"
+        assert name in _bmj.SIGNATURES, f"binding lacks {name}"
+
+
+def test_strerror_and_defaults():
+    assert _bmj.bmj_strerror(0) == "ok"
+    for code in range(-9, 0):
+        assert _bmj.bmj_strerror(code) != "unknown status"
+    o = _bmj.bmj_default_options()
+    assert (o.b, o.method, o.validate, o.output_on_device, o.queue_cap) == (64, 0, 1, 0, 0)
+
+
+def _join_status(off, tok, p, q, **kw):
+    coll, keep = _bmj.make_collection(off, tok)
+    o = _bmj.bmj_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    pairs = _bmj.bmj_pairs()
+    return _bmj.lib().bmj_self_join(C.byref(coll), 0, p, q, C.byref(o), C.byref(pairs), None)
+
+
+@pytest.mark.parametrize("p,q,kw", [
+    (0, 5, {}), (3, 0, {}), (6, 5, {}), (1, 2, {"b": 100}), (1, 2, {"b": 0}),
+    (1, 2, {"b": 4160}), (1, 2, {"method": 7}), (1, 2, {"queue_cap": -1}),
+])
+def test_invalid_arguments_rejected_on_host(p, q, kw):
+    off = np.array([0, 2, 4], np.int64)
+    tok = np.array([1, 2, 1, 3], np.int32)
+    assert _join_status(off, tok, p, q, **kw) == _bmj.BMJ_ERR_INVALID_ARG
+
+
+def test_null_pointers_rejected():
+    L = _bmj.lib()
+    pairs = _bmj.bmj_pairs()
+    assert L.bmj_self_join(None, 0, 1, 2, None, C.byref(pairs), None) == _bmj.BMJ_ERR_INVALID_ARG
+    coll = _bmj.bmj_collection(-1, None, None, 0, 0)
+    assert L.bmj_self_join(C.byref(coll), 0, 1, 2, None, C.byref(pairs), None) == _bmj.BMJ_ERR_INVALID_ARG
+    coll = _bmj.bmj_collection(1 << 31, None, None, 0, 0)
+    assert L.bmj_self_join(C.byref(coll), 0, 1, 2, None, C.byref(pairs), None) == _bmj.BMJ_ERR_TOO_LARGE
+    assert L.bmj_build_bitmaps(None, 64, 0, None, None) == _bmj.BMJ_ERR_INVALID_ARG
+    off = np.array([0, 1], np.int64)
+    tok = np.array([1], np.int32)
+    coll, keep = _bmj.make_collection(off, tok)
+    assert L.bmj_build_bitmaps(C.byref(coll), 64, _bmj.BMJ_COMBINED, None, None) == _bmj.BMJ_ERR_INVALID_ARG
+    assert L.bmj_build_bitmaps(C.byref(coll), 96, 0, None, None) == _bmj.BMJ_ERR_INVALID_ARG
+    # freeing an empty list is a no-op
+    L.bmj_pairs_free(C.byref(pairs))
+    L.bmj_pairs_free(None)

@@ -1,0 +1,207 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GPU).
+
+Pair lists are compared element by element (bit-exact: the method is integer
+work); window-pair and survivor counts are compared with the oracle's Alg. 6
+counts, which are deterministic.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_07295_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU, skipped by marker
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1711_07295_b300 import _bmj  # noqa: E402
+
+ORACLE_METHOD = {_bmj.BMJ_XOR: O.XOR, _bmj.BMJ_SET: O.SET, _bmj.BMJ_NEXT: O.NEXT,
+                 _bmj.BMJ_COMBINED: O.COMBINED}
+
+
+def dev(off, tok):
+    return torch.from_numpy(np.ascontiguousarray(off)).cuda(), \
+        torch.from_numpy(np.ascontiguousarray(tok)).cuda()
+
+
+def gpu_join(off, tok, p, q, on_device=True, **kw):
+    if on_device:
+        d_off, d_tok = dev(off, tok)
+        return _bmj.bmj_self_join(d_off, d_tok, p, q, **kw)
+    return _bmj.bmj_self_join(off, tok, p, q, **kw)
+
+
+def check_join(off, tok, p, q, b=64, method=_bmj.BMJ_XOR, counts=True, **kw):
+    a, bb, st = gpu_join(off, tok, p, q, b=b, method=method, **kw)
+    ra, rb = O.self_join(off, tok, p, q)
+    assert len(a) == len(ra), (len(a), len(ra))
+    assert np.array_equal(a, ra) and np.array_equal(bb, rb)
+    if counts:
+        w, s, r = O.filter_counts(off, tok, p, q, b, ORACLE_METHOD[method])
+        assert (st["window_pairs"], st["survivors"], st["results"]) == (w, s, r)
+    return st
+
+
+# --------------------------------------------------------------- config 1
+@pytest.mark.parametrize("planted", [False, True])
+def test_small_config_literal_and_planted(planted):
+    # 10,000 sets, Zipf(1.0) over 5,000 tokens, sizes U[5,50], threshold 4/5, b = 64.
+    off, tok = I.gen_collection(I.spec_small(planted=planted))
+    st = check_join(off, tok, 4, 5, b=64, method=_bmj.BMJ_XOR)
+    if planted:
+        assert st["results"] > 0
+
+
+@pytest.mark.parametrize("p,q", [(1, 2), (3, 5), (7, 10), (9, 10)])
+def test_small_config_other_thresholds(p, q):
+    off, tok = I.gen_collection(I.spec_small(planted=True))
+    check_join(off, tok, p, q, b=64)
+
+
+# ------------------------------------------------- methods x bitmap sizes
+@pytest.mark.parametrize("b", [64, 128, 192, 256, 512, 1024, 4096])
+@pytest.mark.parametrize("method", [_bmj.BMJ_XOR, _bmj.BMJ_SET, _bmj.BMJ_NEXT, _bmj.BMJ_COMBINED])
+def test_methods_and_widths(b, method):
+    # 3,001 sets (a ragged last tile), sizes 1..120 so that Next saturates for b = 64.
+    off, tok = I.random_collection(3001, 3000, 1, 120, seed=b + 10 * method, zipf_s=0.9,
+                                   planted_frac=0.1)
+    for p, q in ((1, 2), (4, 5)):
+        check_join(off, tok, p, q, b=b, method=method)
+
+
+@pytest.mark.parametrize("b", [64, 128, 192, 256, 4096])
+@pytest.mark.parametrize("method", [_bmj.BMJ_XOR, _bmj.BMJ_SET, _bmj.BMJ_NEXT])
+def test_build_bitmaps_bit_exact(b, method):
+    off, tok = I.random_collection(1500, 20 * b, 1, b + 40, seed=b * 3 + method, zipf_s=0.7)
+    want = O.bitmaps(off, tok, b, ORACLE_METHOD[method])
+    d_off, d_tok = dev(off, tok)
+    got = _bmj.bmj_build_bitmaps(d_off, d_tok, b=b, method=method)
+    assert np.array_equal(got.cpu().numpy().view(np.uint64), want)
+    got_h = _bmj.bmj_build_bitmaps(off, tok, b=b, method=method)
+    assert np.array_equal(got_h, want)
+
+
+# ------------------------------------------------------ host/device paths
+def test_host_and_device_paths_agree():
+    off, tok = I.random_collection(5000, 2000, 2, 40, seed=5, planted_frac=0.1)
+    a1, b1, _ = gpu_join(off, tok, 3, 5, on_device=False)
+    a2, b2, _ = gpu_join(off, tok, 3, 5, on_device=True)
+    d_off, d_tok = dev(off, tok)
+    dp, _, st = _bmj.bmj_self_join(d_off, d_tok, 3, 5, output_on_device=True)
+    assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+    assert np.array_equal(dp.a.cpu().numpy().view(np.uint32), a1)
+    assert np.array_equal(dp.b.cpu().numpy().view(np.uint32), b1)
+    dp.release()
+
+
+def test_queue_overflow_reruns_exactly():
+    off, tok = I.random_collection(4000, 300, 1, 30, seed=8, planted_frac=0.2)
+    st = check_join(off, tok, 1, 2, b=64, queue_cap=1)
+    assert st["filter_passes"] == 2 and st["survivors"] > 1
+
+
+def test_repeated_calls_are_deterministic():
+    off, tok = I.random_collection(6000, 800, 1, 25, seed=2, planted_frac=0.1)
+    d_off, d_tok = dev(off, tok)
+    first = _bmj.bmj_self_join(d_off, d_tok, 1, 2)
+    for _ in range(3):
+        again = _bmj.bmj_self_join(d_off, d_tok, 1, 2)
+        assert np.array_equal(first[0], again[0]) and np.array_equal(first[1], again[1])
+        assert first[2]["survivors"] == again[2]["survivors"]
+
+
+# ------------------------------------------------------------ edge cases
+def test_empty_and_single():
+    for n in (0, 1):
+        off = np.arange(n + 1, dtype=np.int64) * 3
+        tok = np.tile(np.array([1, 4, 9], np.int32), n)
+        a, b, st = gpu_join(off, tok, 1, 2)
+        assert len(a) == 0 and st["window_pairs"] == 0
+
+
+def test_identical_sets_and_threshold_one():
+    n = 700
+    off = np.arange(n + 1, dtype=np.int64) * 4
+    tok = np.tile(np.array([3, 70, 134, 9000], np.int32), n)
+    a, b, st = gpu_join(off, tok, 1, 1)
+    assert len(a) == n * (n - 1) // 2 == st["results"] == st["window_pairs"]
+    iu = np.triu_indices(n, 1)
+    assert np.array_equal(a, iu[0].astype(np.uint32)) and np.array_equal(b, iu[1].astype(np.uint32))
+
+
+def test_singletons_and_low_threshold():
+    off, tok = I.random_collection(2500, 40, 1, 1, seed=3)
+    check_join(off, tok, 1, 1)
+    off, tok = I.random_collection(1200, 500, 1, 30, seed=4)
+    check_join(off, tok, 1, 100)
+
+
+def test_exact_bitmaps_survivors_equal_results_on_gpu():
+    off, tok = I.random_collection(3000, 64, 1, 30, seed=12, planted_frac=0.1)
+    for m in (_bmj.BMJ_XOR, _bmj.BMJ_SET, _bmj.BMJ_NEXT):
+        st = check_join(off, tok, 3, 5, b=64, method=m)
+        assert st["survivors"] == st["results"]
+
+
+@pytest.mark.parametrize("case,code", [
+    ("unsorted", _bmj.BMJ_ERR_UNSORTED), ("duplicate", _bmj.BMJ_ERR_UNSORTED),
+    ("negative", _bmj.BMJ_ERR_NEG_TOKEN), ("empty", _bmj.BMJ_ERR_EMPTY_SET),
+    ("bad_offsets", _bmj.BMJ_ERR_UNSORTED), ("past_end", _bmj.BMJ_ERR_UNSORTED),
+])
+@pytest.mark.parametrize("on_device", [True, False])
+def test_invalid_collections(case, code, on_device):
+    off = np.array([0, 3, 6, 9], np.int64)
+    tok = np.array([1, 5, 9, 2, 4, 6, 1, 5, 9], np.int32)
+    if case == "unsorted":
+        tok[4], tok[5] = tok[5], tok[4]
+    elif case == "duplicate":
+        tok[5] = tok[4]
+    elif case == "negative":
+        tok[3] = -2
+    elif case == "empty":
+        off = np.array([0, 3, 3, 9], np.int64)
+        tok = np.array([1, 5, 9, 1, 2, 4, 5, 6, 9], np.int32)
+    elif case == "bad_offsets":
+        off = np.array([0, 6, 3, 9], np.int64)
+    elif case == "past_end":
+        off = np.array([0, 3, 12, 9], np.int64)
+    with pytest.raises(_bmj.BmjError) as ei:
+        gpu_join(off, tok, 1, 2, on_device=on_device)
+    assert ei.value.status == code
+    # the context stays usable after a rejected input
+    check_join(*I.random_collection(300, 100, 1, 10, seed=1), 1, 2)
+
+
+# ------------------------------------- full-size configuration, row-sampled
+@pytest.fixture(scope="module")
+def million():
+    return I.gen_collection(I.spec_1m())
+
+
+@pytest.mark.parametrize("p,q,b", [(1, 2, 64), (3, 4, 128), (9, 10, 256), (19, 20, 64)])
+def test_million_sets_row_sampled(million, p, q, b):
+    # 1,000,000 sets, Zipf(1.1) over 200,000, sizes lognormal(2.3, 0.6) in [1, 500];
+    # the launch configuration is the benchmark's.  The oracle scans 40 sampled
+    # rows against all sets; the GPU pairs touching those rows must match exactly.
+    off, tok = million
+    d_off, d_tok = dev(off, tok)
+    a, bb, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b)
+    rng = np.random.default_rng(p * 100 + q + b)
+    sizes = np.diff(off)
+    rows = np.concatenate([rng.choice(len(sizes), 30, replace=False),
+                           np.argsort(sizes)[:5], np.argsort(sizes)[-5:]])
+    ra, rb = O.join_rows(off, tok, p, q, rows)
+    sel = np.isin(a, rows) | np.isin(bb, rows)
+    assert np.array_equal(a[sel], ra) and np.array_equal(bb[sel], rb)
+    # properties that hold at any size
+    assert np.all(a < bb)
+    key = a.astype(np.uint64) << np.uint64(32) | bb.astype(np.uint64)
+    assert np.all(np.diff(key.astype(np.int64)) > 0)
+    assert st["results"] == len(a) <= st["survivors"] <= st["window_pairs"]
+    sa, sb = sizes[a], sizes[bb]
+    assert np.all(q * np.minimum(sa, sb) >= p * np.maximum(sa, sb))
