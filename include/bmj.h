@@ -165,6 +165,54 @@ void bmj_pairs_free(bmj_pairs *pairs);
  * monotone counter, for accounting in benchmarks). */
 int64_t bmj_kernel_launches(void);
 
+/* Size of the device scratch array used by bmj_bitmap_filter_noalloc. */
+#define BMJ_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * bmj_bitmap_filter_noalloc -- the Bitmap Filter alone, without allocating.
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory while they run: code inside a fixed
+ * memory budget owned by another framework's pool, latency-critical serving
+ * loops where cudaMalloc/cudaFree (which can synchronise the device) are not
+ * allowed, and sandboxes that forbid allocator calls altogether.  It calls
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Inputs describe a collection already ordered by set size (the order
+ * bmj_self_join uses internally):
+ *   bitmaps    device, n_sets * (b/64) uint64 words; row i is the bitmap of
+ *              the set at sorted position i (e.g. bmj_build_bitmaps run on
+ *              the size-sorted collection)
+ *   sizes      device, n_sets uint32 set sizes, each >= 1, nondecreasing
+ *   b, p, q    bitmap bits (multiple of 64 in [64, 4096]) and threshold p/q
+ * Output (caller-owned):
+ *   out_pairs  device, 2*out_cap uint32, 8-byte aligned: the surviving pairs
+ *              as (i, j) with j < i in sorted positions, in no particular
+ *              order -- every pair inside the length window whose Eq. 2
+ *              bound reaches the threshold, the same set of pairs that
+ *              bmj_self_join verifies (its stats.survivors counts them)
+ *   out_count  host: the number of survivors.  If it exceeds out_cap, the
+ *              call returns BMJ_ERR_OUTPUT_OVERFLOW, out_count still holds
+ *              the full count and out_pairs holds out_cap of the survivors.
+ * Scratch: one file-scope device array of BMJ_NOALLOC_SCRATCH_BYTES (8 MiB)
+ *   per device that loads the library, held until the process exits.  It
+ *   holds 32 bytes of counters, 4*(2*max_size+1) bytes of thresholds and
+ *   about 12 bytes per 128 sets (per 64 sets when b = 512, per 32 sets for
+ *   other b beyond 256) of window tiles; a collection needing more returns
+ *   BMJ_ERR_TOO_LARGE before any launch.  The counters are cleared on every
+ *   call.  Every call shares the array: calls that overlap on the GPU (other
+ *   streams or host threads) race and must be serialised by the caller.
+ * Set-up: the first call on a device looks up the array's device address
+ *   with that device current (cudaGetSymbolAddress); make that first call
+ *   before any stream capture.
+ * Errors: BMJ_ERR_INVALID_ARG (NULL or misaligned pointers, bad b, p, q),
+ *   BMJ_ERR_UNSORTED (sizes decrease), BMJ_ERR_EMPTY_SET (a size of 0),
+ *   BMJ_ERR_TOO_LARGE, BMJ_ERR_OUTPUT_OVERFLOW, BMJ_ERR_CUDA.  The stream is
+ *   synchronised before the call returns.
+ */
+int bmj_bitmap_filter_noalloc(const uint64_t *bitmaps, const uint32_t *sizes, int64_t n_sets,
+                              int b, uint32_t p, uint32_t q, uint32_t *out_pairs,
+                              int64_t out_cap, int64_t *out_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

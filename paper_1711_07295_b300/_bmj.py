@@ -78,6 +78,9 @@ SIGNATURES = {
                                 C.POINTER(bmj_stats)]),
     "bmj_pairs_free": (None, [C.POINTER(bmj_pairs)]),
     "bmj_kernel_launches": (C.c_int64, []),
+    "bmj_bitmap_filter_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_uint32,
+                                            C.c_uint32, C.c_void_p, C.c_int64,
+                                            C.POINTER(C.c_int64), C.c_void_p]),
 }
 
 
