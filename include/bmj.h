@@ -98,7 +98,8 @@ typedef struct {
     int64_t queue_cap;         /* survivor-queue capacity in pairs; 0 (default) = automatic */
     void   *stream;            /* cudaStream_t; NULL = legacy default stream */
     int32_t rows_per_thread;   /* filter register blocking: 0 = automatic */
-    int32_t reserved[7];
+    int32_t use_graph;         /* bmj_self_join_batch: run the execute stage as a CUDA graph */
+    int32_t reserved[6];
 } bmj_options;
 
 /* Counters and stage times of one join.  Pair counts are exact and do not
@@ -119,6 +120,24 @@ typedef struct {
     float   ms_total;       /* whole call, device time on the stream */
     float   reserved_f;
 } bmj_stats;
+
+/* Counters and stage times of one bmj_self_join_batch call. */
+typedef struct {
+    int64_t n_jobs;
+    int64_t window_pairs;   /* summed over the jobs */
+    int64_t survivors;
+    int64_t results;
+    int32_t n_launches;     /* CUDA kernels launched (kernels inside a graph counted once) */
+    int32_t filter_passes;  /* 1 unless the survivor queue had to grow */
+    int32_t graph;          /* 1 when the execute stage ran as a CUDA graph */
+    int32_t tuned;          /* 1 when b was chosen per job by the autotuner */
+    float   ms_prepare;     /* validation, sort, sorted CSR, bitmaps, thresholds, window sizes */
+    float   ms_tune;        /* autotuner sampling */
+    float   ms_execute;     /* Bitmap Filter + verification of every job */
+    float   ms_output;
+    float   ms_total;       /* whole call, device time on the stream */
+    float   reserved_f[3];
+} bmj_batch_stats;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
 void bmj_default_options(bmj_options *opt);
@@ -156,6 +175,37 @@ int bmj_build_bitmaps(const bmj_collection *coll, int b, int method, uint64_t *o
  */
 int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
                   const bmj_options *opt, bmj_pairs *out, bmj_stats *stats);
+
+/*
+ * Many independent exact self-joins in one pass over the GPU (no counterpart
+ * in the paper, which joins one collection per run; the arithmetic of every
+ * job is the one of bmj_self_join).
+ *   coll      all jobs' sets concatenated into one collection (host or device)
+ *   n_jobs    number of jobs (>= 1)
+ *   job_sets  host int64[n_jobs+1]: job k is sets [job_sets[k], job_sets[k+1])
+ *             of coll; job_sets[0] = 0, job_sets[n_jobs] = coll->n_sets,
+ *             nondecreasing (empty jobs allowed)
+ *   sim       BMJ_JACCARD
+ *   p, q      host uint32[n_jobs]: threshold p[k]/q[k] of job k (0 < p <= q)
+ *   opt       options (NULL = defaults).  opt->b = 0 lets a sampling
+ *             autotuner pick b in {64, 128, 256} per job (cost = window pairs
+ *             x measured filter time per pair + estimated survivors x measured
+ *             verification time per survivor); BMJ_COMBINED resolves the
+ *             method per job; opt->use_graph runs the filter + verification
+ *             stage as a CUDA graph.
+ *   outs      n_jobs pair lists (library-owned; free each with
+ *             bmj_pairs_free), in job-local ids (0 = the job's first set),
+ *             sorted and unique as for bmj_self_join
+ *   job_stats optional n_jobs entries: window_pairs, survivors, results, b,
+ *             method per job
+ *   batch_stats optional totals and stage times
+ * Errors as for bmj_self_join; BMJ_ERR_TOO_LARGE also when
+ * bits(n_jobs - 1) + bits(max set size) > 32 or
+ * bits(n_jobs - 1) + 2 * bits(largest job - 1) > 64.
+ */
+int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets,
+                        int sim, const uint32_t *p, const uint32_t *q, const bmj_options *opt,
+                        bmj_pairs *outs, bmj_stats *job_stats, bmj_batch_stats *batch_stats);
 
 /* Releases a pair list returned by the library and empties *pairs.
  * Safe on an empty or already freed list. */

@@ -45,7 +45,8 @@ class bmj_pairs(C.Structure):
 class bmj_options(C.Structure):
     _fields_ = [("b", C.c_int32), ("method", C.c_int32), ("output_on_device", C.c_int32),
                 ("validate", C.c_int32), ("queue_cap", C.c_int64), ("stream", C.c_void_p),
-                ("rows_per_thread", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("rows_per_thread", C.c_int32), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class bmj_stats(C.Structure):
@@ -54,6 +55,17 @@ class bmj_stats(C.Structure):
                 ("method", C.c_int32), ("max_set_size", C.c_int32), ("ms_prepare", C.c_float),
                 ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
                 ("ms_total", C.c_float), ("reserved_f", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class bmj_batch_stats(C.Structure):
+    _fields_ = [("n_jobs", C.c_int64), ("window_pairs", C.c_int64), ("survivors", C.c_int64),
+                ("results", C.c_int64), ("n_launches", C.c_int32), ("filter_passes", C.c_int32),
+                ("graph", C.c_int32), ("tuned", C.c_int32), ("ms_prepare", C.c_float),
+                ("ms_tune", C.c_float), ("ms_execute", C.c_float), ("ms_output", C.c_float),
+                ("ms_total", C.c_float), ("reserved_f", C.c_float * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -76,6 +88,10 @@ SIGNATURES = {
     "bmj_self_join": (C.c_int, [C.POINTER(bmj_collection), C.c_int, C.c_uint32, C.c_uint32,
                                 C.POINTER(bmj_options), C.POINTER(bmj_pairs),
                                 C.POINTER(bmj_stats)]),
+    "bmj_self_join_batch": (C.c_int, [C.POINTER(bmj_collection), C.c_int64, C.c_void_p, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.POINTER(bmj_options),
+                                      C.POINTER(bmj_pairs), C.POINTER(bmj_stats),
+                                      C.POINTER(bmj_batch_stats)]),
     "bmj_pairs_free": (None, [C.POINTER(bmj_pairs)]),
     "bmj_kernel_launches": (C.c_int64, []),
     "bmj_bitmap_filter_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_uint32,
@@ -255,3 +271,52 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     bb = np.ctypeslib.as_array(C.cast(pairs.b, C.POINTER(C.c_uint32)), shape=(n,)).copy()
     lib().bmj_pairs_free(C.byref(pairs))
     return a, bb, stats
+
+
+def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int = BMJ_XOR,
+                        output_on_device: bool = False, queue_cap: int = 0,
+                        validate: bool = True, use_graph: bool = False, stream=None,
+                        sim: int = BMJ_JACCARD):
+    """Independent self-joins of the jobs ``job_sets`` of one concatenated collection.
+
+    ``job_sets`` int64[n_jobs+1] set boundaries, ``p``/``q`` per-job thresholds;
+    ``b = 0`` autotunes b per job.  Returns ``(pairs, job_stats, batch_stats)``
+    where ``pairs[k]`` is ``(a, b)`` numpy uint32 arrays in job-local ids.
+    """
+    coll, keep = make_collection(offsets, tokens)
+    js = np.ascontiguousarray(job_sets, dtype=np.int64)
+    n_jobs = len(js) - 1
+    pp = np.ascontiguousarray(p, dtype=np.uint32)
+    qq = np.ascontiguousarray(q, dtype=np.uint32)
+    if len(pp) != n_jobs or len(qq) != n_jobs:
+        raise ValueError("p and q need one entry per job")
+    o = bmj_default_options()
+    o.b = int(b)
+    o.method = int(method)
+    o.output_on_device = 1 if output_on_device else 0
+    o.validate = 1 if validate else 0
+    o.queue_cap = int(queue_cap)
+    o.use_graph = 1 if use_graph else 0
+    o.stream = _stream_of(stream, coll.on_device)
+    outs = (bmj_pairs * max(n_jobs, 1))()
+    jst = (bmj_stats * max(n_jobs, 1))()
+    bst = bmj_batch_stats()
+    st = lib().bmj_self_join_batch(C.byref(coll), n_jobs, _ptr(js), int(sim), _ptr(pp), _ptr(qq),
+                                   C.byref(o), outs, jst, C.byref(bst))
+    del keep
+    if st != BMJ_OK:
+        raise BmjError(st, "bmj_self_join_batch")
+    pairs = []
+    for k in range(n_jobs):
+        m = int(outs[k].n)
+        if m == 0:
+            pairs.append((np.zeros(0, np.uint32), np.zeros(0, np.uint32)))
+        elif output_on_device:
+            pairs.append(DevicePairs(outs[k], offsets.device if hasattr(offsets, "device") else "cuda"))
+            continue
+        else:
+            a = np.ctypeslib.as_array(C.cast(outs[k].a, C.POINTER(C.c_uint32)), shape=(m,)).copy()
+            bb = np.ctypeslib.as_array(C.cast(outs[k].b, C.POINTER(C.c_uint32)), shape=(m,)).copy()
+            pairs.append((a, bb))
+        lib().bmj_pairs_free(C.byref(outs[k]))
+    return pairs, [jst[k].as_dict() for k in range(n_jobs)], bst.as_dict()

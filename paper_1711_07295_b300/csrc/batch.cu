@@ -1,0 +1,875 @@
+// batch.cu -- many independent self-joins in one pass over the GPU.
+//
+// The jobs arrive as one concatenated CSR collection with job boundaries.
+// Every stage runs once for all jobs:
+//   validate -> one radix sort by (job, size) -> sorted CSR + bitmaps for each
+//   bitmap width in use -> per-job thresholds -> tiles of every job ->
+//   ONE persistent Bitmap Filter launch over the work items of all jobs ->
+//   ONE verification launch over all survivors -> one result sort.
+// Per-job parameters (threshold p/q, bitmap width b, generation method, tile
+// shape) live in a device table that the kernels index by job.
+//
+// b per job is picked by a sampling autotuner (when the caller passes b = 0):
+// a few row tiles of every job are filtered at b = 64, 128 and 256 with the
+// survivors only counted, the sampled survivors at b = 64 are verified, and
+// the measured costs give, per job,
+//     cost(b) = window_pairs * t_filter(b) + survivors(b) * t_verify
+// with survivors(b) scaled from the sample.  The choice trades filter work
+// (linear in b) against verification work (the survivors that a wider bitmap
+// removes): the filter/verify split.
+//
+// The execute stage (filter + verification) enqueues no allocation and no
+// host read, so it can be captured into a CUDA graph (opt.use_graph).
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "filter_core.cuh"
+#include "host_util.cuh"
+
+namespace bmj {
+namespace {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+struct JobDesc {
+    const uint64_t *bm;  // bitmap array of the job's width (indexed by global sorted position)
+    int64_t base;        // first sorted position of the job
+    int64_t end;         // one past its last sorted position
+    int64_t id_base;     // first input position of the job (output ids are local to it)
+    int64_t lim_off;     // offset of the job's need/lim tables
+    uint32_t p, q;
+    int32_t W;
+    int32_t tile_rows;
+    int32_t chunk_cols;
+    int32_t pad;
+};
+
+__device__ __forceinline__ int64_t lower_bound_range(const uint32_t *a, int64_t lo, int64_t hi,
+                                                     uint64_t v) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((uint64_t)a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Last k in [0, n) with a[k] <= v.
+__device__ __forceinline__ int64_t last_le(const int64_t *a, int64_t n, int64_t v) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Sort key of input set x: (job << sbits) | size (jbits + sbits <= 32).
+__global__ void k_batch_keys(const uint32_t *__restrict__ sizes, int64_t n,
+                             const int64_t *__restrict__ job_sets, int64_t n_jobs, int sbits,
+                             uint32_t *__restrict__ keys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const int64_t k = last_le(job_sets, n_jobs, x);
+        keys[x] = ((uint32_t)k << sbits) | sizes[x];
+    }
+}
+
+__global__ void k_split_keys(const uint32_t *__restrict__ skey, int64_t n, int sbits,
+                             uint32_t *__restrict__ ssz, uint32_t *__restrict__ sjob) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint32_t mask = (sbits >= 32) ? 0xffffffffu : ((1u << sbits) - 1u);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        ssz[i] = skey[i] & mask;
+        sjob[i] = sbits >= 32 ? 0u : (skey[i] >> sbits);
+    }
+}
+
+// Output pairs from keys (job << 2*nbits) | (lo << nbits) | hi.
+__global__ void k_unpack_local(const uint64_t *__restrict__ keys, int64_t n, int nbits,
+                               uint32_t *__restrict__ a, uint32_t *__restrict__ b) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t mask = (1ull << nbits) - 1ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t k = keys[i];
+        a[i] = (uint32_t)((k >> nbits) & mask);
+        b[i] = (uint32_t)(k & mask);
+    }
+}
+
+__global__ void k_batch_tables(int32_t *__restrict__ need, int32_t *__restrict__ lim, int64_t n_s,
+                               const uint32_t *__restrict__ jp, const uint32_t *__restrict__ jq,
+                               int64_t n_jobs) {
+    const int64_t total = n_s * n_jobs;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+        const int64_t k = x / n_s, S = x - k * n_s;
+        const uint64_t p = jp[k], d = (uint64_t)jp[k] + jq[k];
+        const uint64_t nd = ((uint64_t)S * p + d - 1) / d;  // ceil(p*S/(p+q)), Table 1
+        need[x] = (int32_t)nd;
+        lim[x] = (int32_t)((int64_t)S - 2 * (int64_t)nd);   // Eq. 2 with its floor
+    }
+}
+
+// Window pairs per job: sum over its sorted rows of (i - j0(i)).
+__global__ void k_batch_window(const uint32_t *__restrict__ ssz, const uint32_t *__restrict__ sjob,
+                               int64_t n, const JobDesc *__restrict__ jobs,
+                               unsigned long long *__restrict__ job_win) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        unsigned long long v = 0;
+        uint32_t k = 0xffffffffu;
+        if (i < n) {
+            k = sjob[i];
+            const JobDesc &jd = jobs[k];
+            const uint64_t low = ((uint64_t)ssz[i] * jd.p + jd.q - 1) / jd.q;
+            const int64_t j0 = lower_bound_range(ssz, jd.base, i, low);
+            v = (unsigned long long)(i - j0);
+        }
+        const uint32_t k0 = __shfl_sync(kFullMask, k, 0);
+        if (__all_sync(kFullMask, k == k0)) {
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFullMask, v, d);
+            if (lane == 0 && k0 != 0xffffffffu && v) atomicAdd(&job_win[k0], v);
+        } else if (k != 0xffffffffu && v) {
+            atomicAdd(&job_win[k], v);
+        }
+    }
+}
+
+// Tile descriptors from (job, local tile) pairs.
+__global__ void k_batch_tiles(const uint32_t *__restrict__ ssz, const JobDesc *__restrict__ jobs,
+                              const int32_t *__restrict__ tl_job, const int64_t *__restrict__ tl_local,
+                              int64_t n_tiles, int64_t *__restrict__ tile_i0,
+                              int64_t *__restrict__ tile_c0, int64_t *__restrict__ tile_items,
+                              unsigned long long *__restrict__ tile_win) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
+        const JobDesc &jd = jobs[tl_job[t]];
+        const int64_t i0 = jd.base + tl_local[t] * jd.tile_rows;
+        const uint64_t low = ((uint64_t)ssz[i0] * jd.p + jd.q - 1) / jd.q;
+        const int64_t c0 = lower_bound_range(ssz, jd.base, jd.end, low);  // j0 of the first row
+        const int64_t i_end = min(i0 + (int64_t)jd.tile_rows, jd.end);
+        const int64_t c_end = i_end - 1;
+        const int64_t cols = c_end - c0;
+        tile_i0[t] = i0;
+        tile_c0[t] = c0;
+        tile_items[t] = cols > 0 ? (cols + jd.chunk_cols - 1) / jd.chunk_cols : 0;
+        if (tile_win) {
+            unsigned long long w = 0;
+            for (int64_t i = i0; i < i_end; i++) {
+                const uint64_t li = ((uint64_t)ssz[i] * jd.p + jd.q - 1) / jd.q;
+                w += (unsigned long long)(i - lower_bound_range(ssz, jd.base, i, li));
+            }
+            tile_win[t] = w;
+        }
+    }
+}
+
+// (job, local tile) of every tile of every job.
+__global__ void k_enumerate_tiles(const int64_t *__restrict__ job_tile0, int64_t n_jobs,
+                                  int64_t n_tiles, int32_t *__restrict__ tl_job,
+                                  int64_t *__restrict__ tl_local) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
+        const int64_t k = last_le(job_tile0, n_jobs, t);
+        tl_job[t] = (int32_t)k;
+        tl_local[t] = t - job_tile0[k];
+    }
+}
+
+struct BatchFilterArgs {
+    const JobDesc *jobs;
+    const uint32_t *ssz;
+    const int32_t *lim;
+    const int32_t *tile_job;
+    const int64_t *tile_i0;
+    const int64_t *tile_c0;
+    const int64_t *tile_item_off;  // [n_tiles + 1]
+    int64_t n_tiles;
+    const int64_t *n_items_dev;    // total work items (read on the device)
+    unsigned long long *item_counter;
+    uint2 *queue;
+    unsigned long long *qcount;
+    unsigned long long *job_surv;  // per-job survivor counters
+    int64_t qcap;
+};
+
+// One persistent launch over the work items of every job.
+__global__ void __launch_bounds__(256, 4) k_filter_batch(const BatchFilterArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_items = *a.n_items_dev;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
+        item = __shfl_sync(kFullMask, item, 0);
+        if ((int64_t)item >= n_items) return;
+        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
+        const int32_t k = a.tile_job[t];
+        const JobDesc jd = a.jobs[k];
+        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
+        const int64_t i0 = a.tile_i0[t];
+        const int64_t c0 = a.tile_c0[t] + chunk * jd.chunk_cols;
+        const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
+        const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
+        const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
+        const int32_t *lim = a.lim + jd.lim_off;
+        switch (jd.W) {
+            case 1: filter_item<1, 4>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, sink); break;
+            case 2: filter_item<2, 4>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, sink); break;
+            case 4: filter_item<4, 2>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, sink); break;
+            default:
+                filter_item_generic(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, jd.W, sink);
+        }
+    }
+}
+
+// Verification of all survivors (count read on the device); similar pairs
+// become keys (job << 2*nbits) | (lo << nbits) | hi in job-local ids.
+__global__ void __launch_bounds__(256)
+    k_verify_batch(const uint2 *__restrict__ queue, const unsigned long long *__restrict__ n_surv_dev,
+                   int64_t cap, const int64_t *__restrict__ soff, const int32_t *__restrict__ stok,
+                   const uint32_t *__restrict__ ssz, const uint32_t *__restrict__ sjob,
+                   const uint32_t *__restrict__ perm, const JobDesc *__restrict__ jobs,
+                   const int32_t *__restrict__ need, uint64_t *__restrict__ keys,
+                   unsigned long long *__restrict__ rcount, int nbits) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_surv = min((int64_t)*n_surv_dev, cap);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int64_t base = gw * 32; base < n_surv; base += warps * 32) {
+        const int64_t idx = base + lane;
+        bool similar = false;
+        uint64_t key = 0;
+        if (idx < n_surv) {
+            const uint2 pr = queue[idx];
+            const uint32_t k = sjob[pr.x];
+            const JobDesc &jd = jobs[k];
+            const uint32_t si = ssz[pr.x], sj = ssz[pr.y];
+            const int nd = need[jd.lim_off + si + sj];
+            const int32_t *x = stok + soff[pr.x];
+            const int32_t *y = stok + soff[pr.y];
+            int a = 0, b = 0, o = 0;
+            const int na = (int)si, nb = (int)sj;
+            while (a < na && b < nb) {
+                if (o + min(na - a, nb - b) < nd) break;
+                const int32_t xa = x[a], yb = y[b];
+                o += (xa == yb);
+                a += (xa <= yb);
+                b += (yb <= xa);
+                if (o >= nd) break;
+            }
+            similar = o >= nd;
+            if (similar) {
+                const uint64_t u = (uint64_t)((int64_t)perm[pr.x] - jd.id_base);
+                const uint64_t v = (uint64_t)((int64_t)perm[pr.y] - jd.id_base);
+                const uint64_t lo = u < v ? u : v, hi = u < v ? v : u;
+                key = ((uint64_t)k << (2 * nbits)) | (lo << nbits) | hi;
+            }
+        }
+        const unsigned ball = __ballot_sync(kFullMask, similar);
+        if (ball) {
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(rcount, (unsigned long long)__popc(ball));
+            off = __shfl_sync(kFullMask, off, 0);
+            if (similar) keys[off + __popc(ball & ((1u << lane) - 1u))] = key;
+        }
+    }
+}
+
+// First result of every job in the sorted keys.
+__global__ void k_job_bounds(const uint64_t *__restrict__ keys, int64_t n, int64_t n_jobs,
+                             int shift, int64_t *__restrict__ bounds) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n_jobs; k += stride) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)(keys[mid] >> shift) < k) lo = mid + 1;
+            else hi = mid;
+        }
+        bounds[k] = lo;
+    }
+}
+
+unsigned grid_of(int64_t n, int threads, int64_t cap = 148 * 32) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
+struct Plan {
+    // sorted collection
+    int64_t n = 0, n_jobs = 0;
+    uint32_t *ssz = nullptr, *sjob = nullptr, *perm = nullptr;
+    int64_t *soff = nullptr;
+    int32_t *stok = nullptr;
+    int64_t n_s = 0;
+    int32_t *need = nullptr, *lim = nullptr;
+    JobDesc *jobs_dev = nullptr;
+    std::vector<JobDesc> jobs;
+    // tiles / items
+    int64_t n_tiles = 0;
+    int32_t *tile_job = nullptr;
+    int64_t *tile_i0 = nullptr, *tile_c0 = nullptr, *tile_off = nullptr;
+    // counters: [0] item counter, [1] survivors, [2] results
+    unsigned long long *ctr = nullptr;
+    unsigned long long *job_surv = nullptr;
+    uint2 *queue = nullptr;
+    int64_t qcap = 0;
+    uint64_t *keys = nullptr;
+    int nbits = 1;
+};
+
+int build_tiles(Plan &P, const std::vector<int32_t> &h_job, const std::vector<int64_t> &h_local,
+                bool enumerate_all, const std::vector<int64_t> &job_tile0, Arena &A, cudaStream_t s,
+                unsigned long long **tile_win_out) {
+    const int64_t T = enumerate_all ? job_tile0.back() : (int64_t)h_job.size();
+    P.n_tiles = T;
+    int32_t *tl_job = nullptr;
+    int64_t *tl_local = nullptr;
+    int st = A.alloc(&tl_job, (size_t)std::max<int64_t>(T, 1));
+    if (!st) st = A.alloc(&tl_local, (size_t)std::max<int64_t>(T, 1));
+    if (!st) st = A.alloc(&P.tile_i0, (size_t)std::max<int64_t>(T, 1));
+    if (!st) st = A.alloc(&P.tile_c0, (size_t)std::max<int64_t>(T, 1));
+    if (!st) st = A.alloc(&P.tile_off, (size_t)T + 1);
+    if (st) return st;
+    if (T == 0) {
+        BMJ_CHECK(cudaMemsetAsync(P.tile_off, 0, sizeof(int64_t), s));
+        P.tile_job = tl_job;
+        return BMJ_OK;
+    }
+    if (enumerate_all) {
+        int64_t *jt0 = nullptr;
+        st = A.alloc(&jt0, job_tile0.size());
+        if (st) return st;
+        BMJ_CHECK(cudaMemcpyAsync(jt0, job_tile0.data(), job_tile0.size() * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, s));
+        BMJ_LAUNCH(k_enumerate_tiles, grid_of(T, 256), 256, 0, s, jt0, (int64_t)job_tile0.size() - 1,
+                   T, tl_job, tl_local);
+    } else {
+        BMJ_CHECK(cudaMemcpyAsync(tl_job, h_job.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        BMJ_CHECK(cudaMemcpyAsync(tl_local, h_local.data(), T * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    unsigned long long *tile_win = nullptr;
+    if (tile_win_out) {
+        st = A.alloc(&tile_win, (size_t)T);
+        if (st) return st;
+        *tile_win_out = tile_win;
+    }
+    BMJ_LAUNCH(k_batch_tiles, grid_of(T, 128), 128, 0, s, P.ssz, P.jobs_dev, tl_job, tl_local, T,
+               P.tile_i0, P.tile_c0, P.tile_off, tile_win);
+    st = exclusive_scan_i64(P.tile_off, P.tile_off, T, P.tile_off + T, A, s);
+    P.tile_job = tl_job;
+    return st;
+}
+
+int upload_jobs(Plan &P, Arena &A, cudaStream_t s) {
+    if (!P.jobs_dev) {
+        int st = A.alloc(&P.jobs_dev, (size_t)P.n_jobs);
+        if (st) return st;
+    }
+    BMJ_CHECK(cudaMemcpyAsync(P.jobs_dev, P.jobs.data(), P.n_jobs * sizeof(JobDesc),
+                              cudaMemcpyHostToDevice, s));
+    return BMJ_OK;
+}
+
+// Filter over the planned items into the plan's queue (cap may be 0: count only).
+int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
+    BatchFilterArgs fa;
+    fa.jobs = P.jobs_dev;
+    fa.ssz = P.ssz;
+    fa.lim = P.lim;
+    fa.tile_job = P.tile_job;
+    fa.tile_i0 = P.tile_i0;
+    fa.tile_c0 = P.tile_c0;
+    fa.tile_item_off = P.tile_off;
+    fa.n_tiles = P.n_tiles;
+    fa.n_items_dev = P.tile_off + P.n_tiles;
+    fa.item_counter = &P.ctr[0];
+    fa.queue = P.queue;
+    fa.qcount = &P.ctr[1];
+    fa.job_surv = P.job_surv;
+    fa.qcap = P.qcap;
+    int per_sm = 0;
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch, 256, 0));
+    if (per_sm < 1) per_sm = 1;
+    BMJ_LAUNCH(k_filter_batch, (unsigned)(sms * per_sm), 256, 0, s, fa);
+    return BMJ_OK;
+}
+
+// The execute stage: clear counters, filter every job, verify every survivor.
+// No allocation and no host read: capturable into a CUDA graph.
+int enqueue_execute(const Plan &P, int sms, cudaStream_t s) {
+    BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
+    BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, P.n_jobs * sizeof(unsigned long long), s));
+    int st = enqueue_filter(P, sms, s);
+    if (st) return st;
+    BMJ_LAUNCH(k_verify_batch, (unsigned)(sms * 8), 256, 0, s, P.queue, &P.ctr[1], P.qcap, P.soff,
+               P.stok, P.ssz, P.sjob, P.perm, P.jobs_dev, P.need, P.keys, &P.ctr[2], P.nbits);
+    return BMJ_OK;
+}
+
+int run_execute(const Plan &P, int sms, cudaStream_t s, bool use_graph, int *graphed) {
+    *graphed = 0;
+    if (!use_graph) return enqueue_execute(P, sms, s);
+    cudaStream_t cs = nullptr;
+    BMJ_CHECK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    int st = BMJ_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = enqueue_execute(P, sms, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (!st && e2 != cudaSuccess) st = status_of(e2);
+    } else {
+        st = status_of(e);
+    }
+    if (!st && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) st = BMJ_ERR_CUDA;
+    if (!st) {
+        // The graph runs on the caller's stream, ordered after the planning work.
+        if (cudaGraphLaunch(ge, s) != cudaSuccess) st = BMJ_ERR_CUDA;
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (!st) *graphed = 1;
+    return st;
+}
+
+int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets,
+               const uint32_t *hp, const uint32_t *hq, const bmj_options &o, bmj_pairs *outs,
+               bmj_stats *job_stats, bmj_batch_stats *bst) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const int64_t launches0 = launches();
+    int dev = 0;
+    BMJ_CHECK(cudaGetDevice(&dev));
+    retain_pool_memory(dev);
+    const int sms = num_sms(dev);
+    bmj_batch_stats bs;
+    memset(&bs, 0, sizeof(bs));
+    bs.n_jobs = n_jobs;
+    Events ev;
+    int st = ev.init();
+    if (st) return st;
+    Arena A(s);
+    BMJ_CHECK(cudaEventRecord(ev.e[0], s));
+    DevColl d;
+    st = stage_collection(coll, A, s, &d);
+    if (st) return st;
+    Plan P;
+    P.n = d.n;
+    P.n_jobs = n_jobs;
+    const int64_t n = d.n;
+    std::vector<int64_t> result_bounds(n_jobs + 1, 0);
+    std::vector<uint32_t> res_a, res_b;
+    std::vector<int> job_b(n_jobs, o.b > 0 ? o.b : 64), job_method(n_jobs, o.method);
+    for (int64_t k = 0; k < n_jobs; k++)
+        if (o.method == BMJ_COMBINED) job_method[k] = combined_method(hp[k], hq[k]);
+    std::vector<unsigned long long> job_win(n_jobs, 0), job_sv(n_jobs, 0);
+    int64_t max_job = 0;
+    for (int64_t k = 0; k < n_jobs; k++) max_job = std::max(max_job, job_sets[k + 1] - job_sets[k]);
+    P.nbits = max_job > 1 ? bit_length((uint64_t)(max_job - 1)) : 1;
+    const int jbits = n_jobs > 1 ? bit_length((uint64_t)(n_jobs - 1)) : 1;
+    if (jbits + 2 * P.nbits > 64) return BMJ_ERR_TOO_LARGE;
+
+    if (n >= 2) {
+        uint32_t *sizes = nullptr, *ids = nullptr;
+        int max_size = 0;
+        st = validate(d, o.validate != 0, A, s, &sizes, &ids, &max_size);
+        if (st) return st;
+        // ---- one sort by (job, size), ties by input position ----
+        const int sbits = std::max(1, bit_length((uint64_t)max_size));
+        if (sbits + jbits > 32) return BMJ_ERR_TOO_LARGE;
+        int64_t *js_dev = nullptr;
+        uint32_t *keys_in = nullptr, *skey = nullptr;
+        st = A.alloc(&js_dev, (size_t)n_jobs + 1);
+        if (!st) st = A.alloc(&keys_in, (size_t)n);
+        if (!st) st = A.alloc(&skey, (size_t)n);
+        if (!st) st = A.alloc(&P.ssz, (size_t)n);
+        if (!st) st = A.alloc(&P.sjob, (size_t)n);
+        if (!st) st = A.alloc(&P.perm, (size_t)n);
+        if (!st) st = A.alloc(&P.soff, (size_t)n + 1);
+        if (!st) st = A.alloc(&P.stok, (size_t)d.ntok);
+        if (st) return st;
+        BMJ_CHECK(cudaMemcpyAsync(js_dev, job_sets, (n_jobs + 1) * sizeof(int64_t),
+                                  cudaMemcpyHostToDevice, s));
+        BMJ_LAUNCH(k_batch_keys, grid_of(n, 256), 256, 0, s, sizes, n, js_dev, n_jobs, sbits, keys_in);
+        st = radix_sort_u32_pairs(keys_in, ids, skey, P.perm, n, jbits + sbits, A, s);
+        if (st) return st;
+        BMJ_LAUNCH(k_split_keys, grid_of(n, 256), 256, 0, s, skey, n, sbits, P.ssz, P.sjob);
+        st = launch_widen(P.ssz, P.soff, n, s);
+        if (!st) st = exclusive_scan_i64(P.soff, P.soff, n, P.soff + n, A, s);
+        if (st) return st;
+
+        // ---- thresholds per job ----
+        P.n_s = 2 * (int64_t)max_size + 1;
+        uint32_t *jp = nullptr, *jq = nullptr;
+        st = A.alloc(&P.need, (size_t)(P.n_s * n_jobs));
+        if (!st) st = A.alloc(&P.lim, (size_t)(P.n_s * n_jobs));
+        if (!st) st = A.alloc(&jp, (size_t)n_jobs);
+        if (!st) st = A.alloc(&jq, (size_t)n_jobs);
+        if (!st) st = A.alloc(&P.ctr, 3);
+        if (!st) st = A.alloc(&P.job_surv, (size_t)n_jobs);
+        if (st) return st;
+        BMJ_CHECK(cudaMemcpyAsync(jp, hp, n_jobs * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        BMJ_CHECK(cudaMemcpyAsync(jq, hq, n_jobs * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        BMJ_LAUNCH(k_batch_tables, grid_of(P.n_s * n_jobs, 256), 256, 0, s, P.need, P.lim, P.n_s, jp,
+                   jq, n_jobs);
+
+        // ---- bitmaps: one array per (b, method) in use ----
+        const bool tune = o.b <= 0;
+        std::vector<int> widths = tune ? std::vector<int>{64, 128, 256} : std::vector<int>{o.b};
+        std::vector<int> methods;
+        for (int64_t k = 0; k < n_jobs; k++)
+            if (std::find(methods.begin(), methods.end(), job_method[k]) == methods.end())
+                methods.push_back(job_method[k]);
+        uint64_t *bms[3][4] = {{nullptr}};
+        bool gathered = false;
+        for (size_t wi = 0; wi < widths.size(); wi++)
+            for (int m : methods) {
+                const int W = widths[wi] / 64;
+                st = A.alloc(&bms[wi][m], (size_t)n * W);
+                if (st) return st;
+                if (!gathered) {
+                    st = launch_gather_build(P.perm, d.off, d.tok, P.soff, P.stok, bms[wi][m], n,
+                                             widths[wi], m, s);
+                    gathered = true;
+                } else {
+                    st = launch_gather_build(nullptr, P.soff, P.stok, nullptr, nullptr, bms[wi][m], n,
+                                             widths[wi], m, s);
+                }
+                if (st) return st;
+            }
+
+        // ---- job table ----
+        P.jobs.assign(n_jobs, JobDesc());
+        auto set_jobs = [&](const std::vector<int> &jb) {
+            for (int64_t k = 0; k < n_jobs; k++) {
+                JobDesc &jd = P.jobs[k];
+                size_t wi = 0;
+                while (widths[wi] != jb[k]) wi++;
+                jd.bm = bms[wi][job_method[k]];
+                jd.base = job_sets[k];
+                jd.end = job_sets[k + 1];
+                jd.id_base = job_sets[k];
+                jd.lim_off = k * P.n_s;
+                jd.p = hp[k];
+                jd.q = hq[k];
+                jd.W = jb[k] / 64;
+                jd.tile_rows = jd.W <= 2 ? 128 : (jd.W == 4 ? 64 : 32);
+                jd.chunk_cols = 4096;
+            }
+        };
+        set_jobs(job_b);
+        st = upload_jobs(P, A, s);
+        if (st) return st;
+        {
+            unsigned long long *jw = nullptr;
+            st = A.alloc(&jw, (size_t)n_jobs);
+            if (st) return st;
+            BMJ_CHECK(cudaMemsetAsync(jw, 0, n_jobs * sizeof(unsigned long long), s));
+            BMJ_LAUNCH(k_batch_window, grid_of(n, 256), 256, 0, s, P.ssz, P.sjob, n, P.jobs_dev, jw);
+            BMJ_CHECK(cudaMemcpyAsync(job_win.data(), jw, n_jobs * sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, s));
+        }
+        BMJ_CHECK(cudaStreamSynchronize(s));
+        BMJ_CHECK(cudaEventRecord(ev.e[1], s));
+        unsigned long long total_win = 0;
+        for (auto w : job_win) total_win += w;
+        double est_surv = -1.0;
+
+        // ---- autotuner: sampled filter at each width ----
+        // The sample is up to 4 blocks of 128 rows per job (evenly spaced),
+        // covered by the tiles of each width, so every width sees the same pairs.
+        if (tune && total_win > 0) {
+            bs.tuned = 1;
+            std::vector<int64_t> s_rows_job, s_rows_r0;
+            for (int64_t k = 0; k < n_jobs; k++) {
+                const int64_t nk = job_sets[k + 1] - job_sets[k];
+                if (nk < 2) continue;
+                const int64_t blocks = (nk + 127) / 128;
+                const int64_t pick = std::min<int64_t>(blocks, 4);
+                for (int64_t j = 0; j < pick; j++) {
+                    s_rows_job.push_back(k);
+                    s_rows_r0.push_back(128 * (((2 * j + 1) * blocks) / (2 * pick)));
+                }
+            }
+            auto sample_tiles = [&](int width, std::vector<int32_t> &tj, std::vector<int64_t> &tl) {
+                const int tr = width / 64 <= 2 ? 128 : (width / 64 == 4 ? 64 : 32);
+                tj.clear();
+                tl.clear();
+                for (size_t r = 0; r < s_rows_job.size(); r++) {
+                    const int64_t k = s_rows_job[r];
+                    const int64_t nk = job_sets[k + 1] - job_sets[k];
+                    for (int64_t row = s_rows_r0[r]; row < s_rows_r0[r] + 128 && row < nk; row += tr) {
+                        tj.push_back((int32_t)k);
+                        tl.push_back(row / tr);
+                    }
+                }
+            };
+            std::vector<std::vector<double>> samp_win(widths.size(), std::vector<double>(n_jobs, 0.0));
+            std::vector<double> samp_total(widths.size(), 0.0);
+            std::vector<std::vector<unsigned long long>> samp_surv(widths.size(),
+                                                                   std::vector<unsigned long long>(n_jobs));
+            std::vector<double> t_filter(widths.size(), 0.0);
+            P.queue = nullptr;
+            P.qcap = 0;
+            std::vector<int32_t> tj;
+            std::vector<int64_t> tl;
+            for (size_t wi = 0; wi < widths.size(); wi++) {
+                std::vector<int> jb(n_jobs, widths[wi]);
+                set_jobs(jb);
+                st = upload_jobs(P, A, s);
+                if (st) return st;
+                sample_tiles(widths[wi], tj, tl);
+                unsigned long long *twin = nullptr;
+                st = build_tiles(P, tj, tl, false, {}, A, s, &twin);
+                if (st) return st;
+                std::vector<unsigned long long> h_twin(P.n_tiles);
+                BMJ_CHECK(cudaMemcpyAsync(h_twin.data(), twin, P.n_tiles * sizeof(unsigned long long),
+                                          cudaMemcpyDeviceToHost, s));
+                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
+                BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, n_jobs * sizeof(unsigned long long), s));
+                BMJ_CHECK(cudaEventRecord(ev.e[2], s));
+                st = enqueue_filter(P, sms, s);
+                if (st) return st;
+                BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+                BMJ_CHECK(cudaMemcpyAsync(samp_surv[wi].data(), P.job_surv,
+                                          n_jobs * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+                BMJ_CHECK(cudaStreamSynchronize(s));
+                t_filter[wi] = ev.ms(2, 3) * 1e-3;
+                for (int64_t t = 0; t < P.n_tiles; t++) {
+                    samp_win[wi][tj[t]] += (double)h_twin[t];
+                    samp_total[wi] += (double)h_twin[t];
+                }
+            }
+            // Verification cost per survivor, measured on the b = 64 sample.
+            double t_verify = 2.7e-11;
+            unsigned long long sv64 = 0;
+            for (auto v : samp_surv[0]) sv64 += v;
+            if (sv64 >= 4096) {
+                std::vector<int> jb(n_jobs, widths[0]);
+                set_jobs(jb);
+                st = upload_jobs(P, A, s);
+                if (st) return st;
+                sample_tiles(widths[0], tj, tl);
+                st = build_tiles(P, tj, tl, false, {}, A, s, nullptr);
+                if (!st) st = A.alloc(&P.queue, (size_t)sv64);
+                if (!st) st = A.alloc(&P.keys, (size_t)sv64);
+                if (st) return st;
+                P.qcap = (int64_t)sv64;
+                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
+                st = enqueue_filter(P, sms, s);
+                if (st) return st;
+                BMJ_CHECK(cudaEventRecord(ev.e[2], s));
+                BMJ_LAUNCH(k_verify_batch, (unsigned)(sms * 8), 256, 0, s, P.queue, &P.ctr[1], P.qcap,
+                           P.soff, P.stok, P.ssz, P.sjob, P.perm, P.jobs_dev, P.need, P.keys,
+                           &P.ctr[2], P.nbits);
+                BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+                BMJ_CHECK(cudaStreamSynchronize(s));
+                t_verify = ev.ms(2, 3) * 1e-3 / (double)sv64;
+                A.free_one(P.queue);
+                A.free_one(P.keys);
+                P.queue = nullptr;
+                P.keys = nullptr;
+            }
+            est_surv = 0.0;
+            for (int64_t k = 0; k < n_jobs; k++) {
+                double best = 1e300;
+                double best_surv = 0.0;
+                for (size_t wi = 0; wi < widths.size(); wi++) {
+                    const double per_pair = samp_total[wi] > 0 ? t_filter[wi] / samp_total[wi] : 0.0;
+                    const double scale =
+                        samp_win[wi][k] > 0 ? (double)job_win[k] / samp_win[wi][k] : 0.0;
+                    const double surv = (double)samp_surv[wi][k] * scale;
+                    const double cost = (double)job_win[k] * per_pair + surv * t_verify;
+                    if (cost < best) {
+                        best = cost;
+                        best_surv = surv;
+                        job_b[k] = widths[wi];
+                    }
+                }
+                est_surv += best_surv;
+            }
+            set_jobs(job_b);
+            st = upload_jobs(P, A, s);
+            if (st) return st;
+        }
+        BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+
+        // ---- tiles of every job ----
+        std::vector<int64_t> job_tile0(n_jobs + 1, 0);
+        for (int64_t k = 0; k < n_jobs; k++) {
+            const int64_t nk = job_sets[k + 1] - job_sets[k];
+            job_tile0[k + 1] = job_tile0[k] + (nk >= 2 ? (nk + P.jobs[k].tile_rows - 1) / P.jobs[k].tile_rows : 0);
+        }
+        st = build_tiles(P, {}, {}, true, job_tile0, A, s, nullptr);
+        if (st) return st;
+
+        // ---- execute (filter + verification of all jobs) ----
+        int64_t qcap = o.queue_cap > 0
+                           ? o.queue_cap
+                           : (est_surv >= 0 ? (int64_t)(1.25 * est_surv) + ((int64_t)1 << 20)
+                                            : std::max<int64_t>((int64_t)(total_win / 128),
+                                                                (int64_t)1 << 20));
+        {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+                qcap = std::min<int64_t>(qcap, (int64_t)(free_b / 4 / (sizeof(uint2) + sizeof(uint64_t))));
+            cudaGetLastError();
+            qcap = std::max<int64_t>(qcap, 1);
+        }
+        int64_t n_surv = 0;
+        unsigned long long hc[3] = {0, 0, 0};
+        for (int pass = 0; pass < 2; pass++) {
+            st = A.alloc(&P.queue, (size_t)qcap);
+            if (!st) st = A.alloc(&P.keys, (size_t)qcap);
+            if (st) return st;
+            P.qcap = qcap;
+            BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+            int graphed = 0;
+            st = run_execute(P, sms, s, o.use_graph != 0, &graphed);
+            if (st) return st;
+            bs.graph = graphed;
+            BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+            BMJ_CHECK(cudaMemcpyAsync(hc, P.ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaStreamSynchronize(s));
+            bs.filter_passes++;
+            bs.ms_execute += ev.ms(5, 6);
+            n_surv = (int64_t)hc[1];
+            if (n_surv <= qcap) break;
+            A.free_one(P.queue);
+            A.free_one(P.keys);
+            qcap = n_surv;  // every survivor was counted: rerun once with exact room
+        }
+        BMJ_CHECK(cudaMemcpyAsync(job_sv.data(), P.job_surv, n_jobs * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, s));
+        const int64_t n_res = (int64_t)hc[2];
+        bs.survivors = n_surv;
+        bs.results = n_res;
+        bs.window_pairs = (int64_t)total_win;
+        bs.ms_prepare = ev.ms(0, 1);
+        bs.ms_tune = ev.ms(1, 4);
+
+        // ---- canonical order and per-job split ----
+        if (n_res > 0) {
+            uint64_t *sk = nullptr;
+            int64_t *bounds = nullptr;
+            uint32_t *da = nullptr, *db = nullptr;
+            st = A.alloc(&sk, (size_t)n_res);
+            if (!st) st = A.alloc(&bounds, (size_t)n_jobs + 1);
+            if (!st) st = A.alloc(&da, (size_t)n_res);
+            if (!st) st = A.alloc(&db, (size_t)n_res);
+            if (st) return st;
+            st = radix_sort_u64(P.keys, sk, n_res, jbits + 2 * P.nbits, A, s);
+            if (st) return st;
+            BMJ_LAUNCH(k_job_bounds, grid_of(n_jobs + 1, 256), 256, 0, s, sk, n_res, n_jobs,
+                       2 * P.nbits, bounds);
+            BMJ_LAUNCH(k_unpack_local, grid_of(n_res, 256), 256, 0, s, sk, n_res, P.nbits, da, db);
+            res_a.resize(n_res);
+            res_b.resize(n_res);
+            BMJ_CHECK(cudaMemcpyAsync(result_bounds.data(), bounds, (n_jobs + 1) * sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaMemcpyAsync(res_a.data(), da, n_res * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaMemcpyAsync(res_b.data(), db, n_res * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        }
+    }
+    BMJ_CHECK(cudaEventRecord(ev.e[7], s));
+    A.release();
+    BMJ_CHECK(cudaStreamSynchronize(s));
+    bs.ms_output = 0.f;
+    bs.ms_total = ev.ms(0, 7);
+
+    // ---- outputs ----
+    for (int64_t k = 0; k < n_jobs; k++) memset(&outs[k], 0, sizeof(bmj_pairs));
+    for (int64_t k = 0; k < n_jobs; k++) {
+        const int64_t lo = result_bounds[k], hi = result_bounds[k + 1];
+        const int64_t m = res_a.empty() ? 0 : hi - lo;
+        bmj_pairs &op = outs[k];
+        op.on_device = o.output_on_device ? 1 : 0;
+        if (m > 0) {
+            if (o.output_on_device) {
+                if (cudaMalloc(&op.a, m * sizeof(uint32_t)) != cudaSuccess ||
+                    cudaMalloc(&op.b, m * sizeof(uint32_t)) != cudaSuccess) {
+                    cudaGetLastError();
+                    for (int64_t j = 0; j <= k; j++) bmj_pairs_free(&outs[j]);
+                    return BMJ_ERR_OOM;
+                }
+                cudaMemcpy(op.a, res_a.data() + lo, m * sizeof(uint32_t), cudaMemcpyHostToDevice);
+                cudaMemcpy(op.b, res_b.data() + lo, m * sizeof(uint32_t), cudaMemcpyHostToDevice);
+            } else {
+                op.a = (uint32_t *)malloc(m * sizeof(uint32_t));
+                op.b = (uint32_t *)malloc(m * sizeof(uint32_t));
+                if (!op.a || !op.b) {
+                    for (int64_t j = 0; j <= k; j++) bmj_pairs_free(&outs[j]);
+                    return BMJ_ERR_OOM;
+                }
+                memcpy(op.a, res_a.data() + lo, m * sizeof(uint32_t));
+                memcpy(op.b, res_b.data() + lo, m * sizeof(uint32_t));
+            }
+            op.n = m;
+        }
+        if (job_stats) {
+            bmj_stats &js = job_stats[k];
+            memset(&js, 0, sizeof(js));
+            js.window_pairs = (int64_t)job_win[k];
+            js.survivors = (int64_t)job_sv[k];
+            js.results = m;
+            js.filter_passes = bs.filter_passes;
+            js.b = job_b[k];
+            js.method = job_method[k];
+        }
+    }
+    bs.n_launches = (int32_t)(launches() - launches0);
+    if (bst) *bst = bs;
+    return BMJ_OK;
+}
+
+}  // namespace
+}  // namespace bmj
+
+extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
+                                   const int64_t *job_sets, int sim, const uint32_t *p,
+                                   const uint32_t *q, const bmj_options *opt, bmj_pairs *outs,
+                                   bmj_stats *job_stats, bmj_batch_stats *batch_stats) {
+    if (batch_stats) memset(batch_stats, 0, sizeof(*batch_stats));
+    if (!coll || !job_sets || !outs || n_jobs <= 0 || !p || !q) return BMJ_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n_jobs; k++) memset(&outs[k], 0, sizeof(bmj_pairs));
+    if (sim != BMJ_JACCARD) return BMJ_ERR_INVALID_ARG;
+    if (coll->n_sets < 0 || !coll->offsets || (coll->n_sets > 0 && !coll->tokens))
+        return BMJ_ERR_INVALID_ARG;
+    if (coll->n_sets > 0x7fffffffLL || n_jobs > 0x7fffffffLL) return BMJ_ERR_TOO_LARGE;
+    if (job_sets[0] != 0 || job_sets[n_jobs] != coll->n_sets) return BMJ_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < n_jobs; k++) {
+        if (job_sets[k + 1] < job_sets[k]) return BMJ_ERR_INVALID_ARG;
+        if (p[k] == 0 || q[k] == 0 || p[k] > q[k]) return BMJ_ERR_INVALID_ARG;
+    }
+    bmj_options o;
+    if (opt) o = *opt;
+    else bmj_default_options(&o);
+    if (o.b != 0 && !bmj::valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
+    if (o.method < BMJ_XOR || o.method > BMJ_COMBINED) return BMJ_ERR_INVALID_ARG;
+    if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
+    int st;
+    try {
+        st = bmj::batch_impl(coll, n_jobs, job_sets, p, q, o, outs, job_stats, batch_stats);
+    } catch (...) {
+        st = BMJ_ERR_OOM;
+    }
+    if (st) {
+        for (int64_t k = 0; k < n_jobs; k++) bmj_pairs_free(&outs[k]);
+        cudaGetLastError();
+    }
+    return st;
+}

@@ -45,7 +45,7 @@ inline int status_of(cudaError_t e) {
 // ---------------------------------------------------------------------------
 struct Arena {
     cudaStream_t stream;
-    void *ptrs[64];
+    void *ptrs[256];
     int n = 0;
     explicit Arena(cudaStream_t s) : stream(s) {}
     ~Arena() { release(); }
@@ -53,7 +53,7 @@ struct Arena {
     int alloc(T **p, size_t count) {
         *p = nullptr;
         if (count == 0) count = 1;
-        if (n >= 64) return BMJ_ERR_OOM;
+        if (n >= 256) return BMJ_ERR_OOM;
         void *q = nullptr;
         cudaError_t e = cudaMallocAsync(&q, count * sizeof(T), stream);
         if (e != cudaSuccess) {

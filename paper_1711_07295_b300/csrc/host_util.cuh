@@ -1,0 +1,130 @@
+// host_util.cuh -- host-side helpers shared by the join entry points.
+#pragma once
+
+#include <cstring>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace bmj {
+
+inline int num_sms(int device) {
+    static std::mutex mu;
+    static int cache[128] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (device >= 0 && device < 128 && cache[device]) return cache[device];
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+        v = 148;
+    if (device >= 0 && device < 128) cache[device] = v;
+    return v;
+}
+
+inline int bit_length(uint64_t v) {
+    int b = 0;
+    while (v) {
+        b++;
+        v >>= 1;
+    }
+    return b;
+}
+
+// Alg. 4 with its switch points read on the normalised overlap 2p/(p+q).
+inline int combined_method(uint32_t p, uint32_t q) {
+    const uint64_t P = p, D = (uint64_t)p + q;
+    if (200 * P <= 56 * D) return BMJ_NEXT;
+    if (200 * P >= 73 * D) return BMJ_XOR;
+    return BMJ_SET;
+}
+
+inline int flags_to_status(int flags) {
+    if (flags & kFlagTooLarge) return BMJ_ERR_TOO_LARGE;
+    if (flags & kFlagUnsorted) return BMJ_ERR_UNSORTED;
+    if (flags & kFlagNegative) return BMJ_ERR_NEG_TOKEN;
+    if (flags & kFlagEmpty) return BMJ_ERR_EMPTY_SET;
+    return BMJ_OK;
+}
+
+inline bool valid_b(int b) { return b >= 64 && b <= 4096 && (b % 64) == 0; }
+
+// Device-resident view of a collection (copied in when it is host memory).
+struct DevColl {
+    const int64_t *off = nullptr;
+    const int32_t *tok = nullptr;
+    int64_t n = 0;
+    int64_t ntok = 0;
+};
+
+inline int stage_collection(const bmj_collection *c, Arena &A, cudaStream_t s, DevColl *d) {
+    d->n = c->n_sets;
+    if (c->on_device) {
+        int64_t v = 0;
+        BMJ_CHECK(cudaMemcpyAsync(&v, c->offsets + c->n_sets, sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaStreamSynchronize(s));
+        d->off = c->offsets;
+        d->tok = c->tokens;
+        d->ntok = v;
+        if (v < 0) return BMJ_ERR_UNSORTED;
+        return BMJ_OK;
+    }
+    d->ntok = c->offsets[c->n_sets];
+    if (d->ntok < 0) return BMJ_ERR_UNSORTED;
+    int64_t *off = nullptr;
+    int32_t *tok = nullptr;
+    int st = A.alloc(&off, (size_t)(c->n_sets + 1));
+    if (!st) st = A.alloc(&tok, (size_t)d->ntok);
+    if (st) return st;
+    BMJ_CHECK(cudaMemcpyAsync(off, c->offsets, (c->n_sets + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+    if (d->ntok)
+        BMJ_CHECK(cudaMemcpyAsync(tok, c->tokens, d->ntok * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s));
+    d->off = off;
+    d->tok = tok;
+    return BMJ_OK;
+}
+
+// Validation: returns the status and the maximum set size.
+inline int validate(const DevColl &d, bool check_tokens, Arena &A, cudaStream_t s,
+                    uint32_t **sizes, uint32_t **ids, int *max_size) {
+    int *info = nullptr;
+    int st = A.alloc(&info, 2);
+    if (!st) st = A.alloc(sizes, (size_t)d.n);
+    if (!st) st = A.alloc(ids, (size_t)d.n);
+    if (st) return st;
+    BMJ_CHECK(cudaMemsetAsync(info, 0, 2 * sizeof(int), s));
+    st = launch_validate(d.off, d.tok, d.n, d.ntok, check_tokens ? 1 : 0, *sizes, *ids, info, s);
+    if (st) return st;
+    int h[2] = {0, 0};
+    BMJ_CHECK(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+    BMJ_CHECK(cudaStreamSynchronize(s));
+    *max_size = h[1];
+    return flags_to_status(h[0]);
+}
+
+struct Events {
+    cudaEvent_t e[8];
+    int n = 0;
+    Events() {
+        for (auto &x : e) x = nullptr;
+    }
+    int init() {
+        for (int k = 0; k < 8; k++) BMJ_CHECK(cudaEventCreate(&e[k]));
+        n = 8;
+        return BMJ_OK;
+    }
+    ~Events() {
+        for (int k = 0; k < n; k++) cudaEventDestroy(e[k]);
+    }
+    float ms(int a, int b) const {
+        float v = 0.f;
+        if (cudaEventElapsedTime(&v, e[a], e[b]) != cudaSuccess) {
+            cudaGetLastError();
+            return 0.f;
+        }
+        return v;
+    }
+};
+
+}  // namespace bmj

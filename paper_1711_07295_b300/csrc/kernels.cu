@@ -14,21 +14,12 @@
 //                    (the verification of Alg. 6's host code, moved on the GPU)
 //   k_unpack         canonical output pairs
 #include "kernels.cuh"
+#include "filter_core.cuh"
 
 namespace bmj {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ int warp_inclusive_scan_i(int v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int u = __shfl_up_sync(kFull, v, d);
-        if (lane >= d) v += u;
-    }
-    return v;
-}
 
 // First index j in [0, n) with ssz[j] >= v (n if none).
 __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n, uint64_t v) {
@@ -195,191 +186,43 @@ __global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, uint
 }
 
 // ----------------------------------------------------------------------------
-// Bitmap Filter.
-//
-// A work item is (row tile, column chunk).  A row tile is 32*R consecutive
-// sorted rows held by one warp: lane l owns rows i0 + l + 32k, k < R, with
-// their bitmaps in registers.  The chunk's columns are walked in groups of
-// 32: each lane loads one column (bitmap + size), then every column is
-// broadcast with __shfl_sync and compared against the R rows.
-//
-// For a pair (i, j), with S = |R[i]| + |R[j]| and h = popcount(b_i ^ b_j):
-//   in window  <=>  q*min(|R[i]|,|R[j]|) >= p*max(...)   (Table 2)
-//   survives   <=>  floor((S - h)/2) >= ceil(p*S/(p+q))  (Eq. 2 vs Table 1)
-//              <=>  h <= lim[S]
-// so each row keeps lim (or -1 outside the window) for the current column
-// size, refreshed only when the (warp-uniform) column size changes.  Pairs
-// with j >= i are excluded in the diagonal part of a tile.  Survivors are
-// compacted with one atomicAdd per warp and column group.
+// Bitmap Filter (per-item body in filter_core.cuh).  Warps pull work items
+// (row tile, column chunk) from a global counter: a persistent grid that
+// balances the uneven band of the size-sorted triangle.
 template <int W, int R>
 __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
     const int lane = threadIdx.x & 31;
-    const uint64_t *__restrict__ bm = a.bm;
-    const uint32_t *__restrict__ ssz = a.ssz;
+    const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
         item = __shfl_sync(kFull, item, 0);
         if ((int64_t)item >= a.n_items) return;
-        int64_t lo = 0, hi = a.n_tiles;  // tile_item_off[lo] <= item < tile_item_off[hi]
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((unsigned long long)a.tile_item_off[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int64_t t = lo;
+        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
         const int64_t chunk = (int64_t)item - a.tile_item_off[t];
         const int64_t i0 = t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
         const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-
-        uint64_t rb[R][W];
-        uint32_t rs[R];
-        int64_t ri[R];
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-            const int64_t i = i0 + k * 32 + lane;
-            ri[k] = i;
-            if (i < a.n) {
-                rs[k] = ssz[i];
-#pragma unroll
-                for (int w = 0; w < W; w++) rb[k][w] = bm[i * W + w];
-            } else {
-                rs[k] = 0;
-#pragma unroll
-                for (int w = 0; w < W; w++) rb[k][w] = 0;
-            }
-        }
-        int lim[R];
-        uint32_t prev_cs = 0xffffffffu;
-#pragma unroll
-        for (int k = 0; k < R; k++) lim[k] = -1;
-
-        for (int64_t j = c0; j < c1; j += 32) {
-            const int gj = (int)min((int64_t)32, c1 - j);
-            uint64_t cb[W];
-            uint32_t cs = 0;
-            if (lane < gj) {
-                cs = ssz[j + lane];
-#pragma unroll
-                for (int w = 0; w < W; w++) cb[w] = bm[(j + lane) * W + w];
-            } else {
-#pragma unroll
-                for (int w = 0; w < W; w++) cb[w] = 0;
-            }
-            const bool diag = (j + gj - 1) >= i0;
-            uint32_t mask[R];
-#pragma unroll
-            for (int k = 0; k < R; k++) mask[k] = 0;
-            uint32_t bit = 1u;
-            for (int cc = 0; cc < gj; cc++, bit <<= 1) {
-                const uint32_t s = __shfl_sync(kFull, cs, cc);
-                uint64_t c[W];
-#pragma unroll
-                for (int w = 0; w < W; w++) c[w] = __shfl_sync(kFull, cb[w], cc);
-                if (s != prev_cs) {  // warp-uniform
-                    prev_cs = s;
-#pragma unroll
-                    for (int k = 0; k < R; k++) {
-                        const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
-                        const bool in_win = rs[k] != 0 &&
-                                            (uint64_t)a.q * mn >= (uint64_t)a.p * mx;
-                        lim[k] = in_win ? a.lim[rs[k] + s] : -1;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < R; k++) {
-                    int h = 0;
-#pragma unroll
-                    for (int w = 0; w < W; w++) h += __popcll(rb[k][w] ^ c[w]);
-                    bool sv = h <= lim[k];
-                    if (diag) sv = sv && (j + cc < ri[k]);
-                    if (sv) mask[k] |= bit;
-                }
-            }
-            int cnt = 0;
-#pragma unroll
-            for (int k = 0; k < R; k++) cnt += __popc(mask[k]);
-            const int total = __reduce_add_sync(kFull, cnt);
-            if (total) {
-                const int excl = warp_inclusive_scan_i(cnt) - cnt;
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(a.qcount, (unsigned long long)total);
-                base = __shfl_sync(kFull, base, 0);
-                unsigned long long pos = base + excl;
-#pragma unroll
-                for (int k = 0; k < R; k++) {
-                    uint32_t m = mask[k];
-                    while (m) {
-                        const int bpos = __ffs(m) - 1;
-                        m &= m - 1;
-                        if (pos < (unsigned long long)a.qcap)
-                            a.queue[pos] = make_uint2((uint32_t)ri[k], (uint32_t)(j + bpos));
-                        pos++;
-                    }
-                }
-            }
-        }
+        filter_item<W, R>(a.bm, a.ssz, a.lim, a.n, i0, c0, c1, a.p, a.q, sink);
     }
 }
 
-// Generic-width variant for b not in {64, 128, 256, 512}: one row per lane,
-// bitmaps read from memory word by word.
 __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int W) {
     const int lane = threadIdx.x & 31;
+    const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
         item = __shfl_sync(kFull, item, 0);
         if ((int64_t)item >= a.n_items) return;
-        int64_t lo = 0, hi = a.n_tiles;
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((unsigned long long)a.tile_item_off[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int64_t t = lo;
+        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
         const int64_t chunk = (int64_t)item - a.tile_item_off[t];
         const int64_t i0 = t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
         const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        const int64_t i = i0 + lane;
-        const uint32_t rs = i < a.n ? a.ssz[i] : 0u;
-        const uint64_t *rowp = a.bm + (i < a.n ? i : 0) * W;
-        for (int64_t j = c0; j < c1; j += 32) {
-            const int gj = (int)min((int64_t)32, c1 - j);
-            uint32_t mask = 0;
-            for (int cc = 0; cc < gj; cc++) {
-                const int64_t jj = j + cc;
-                const uint32_t s = a.ssz[jj];
-                const uint32_t mn = min(rs, s), mx = max(rs, s);
-                const bool in_win = rs != 0 && (uint64_t)a.q * mn >= (uint64_t)a.p * mx;
-                if (!in_win || jj >= i) continue;
-                const uint64_t *colp = a.bm + jj * W;
-                int h = 0;
-                for (int w = 0; w < W; w++) h += __popcll(rowp[w] ^ colp[w]);
-                if (h <= a.lim[rs + s]) mask |= 1u << cc;
-            }
-            const int cnt = __popc(mask);
-            const int total = __reduce_add_sync(kFull, cnt);
-            if (total) {
-                const int excl = warp_inclusive_scan_i(cnt) - cnt;
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(a.qcount, (unsigned long long)total);
-                base = __shfl_sync(kFull, base, 0);
-                unsigned long long pos = base + excl;
-                uint32_t m = mask;
-                while (m) {
-                    const int bpos = __ffs(m) - 1;
-                    m &= m - 1;
-                    if (pos < (unsigned long long)a.qcap)
-                        a.queue[pos] = make_uint2((uint32_t)i, (uint32_t)(j + bpos));
-                    pos++;
-                }
-            }
-        }
+        filter_item_generic(a.bm, a.ssz, a.lim, a.n, i0, c0, c1, a.p, a.q, W, sink);
     }
 }
 

@@ -80,3 +80,28 @@ def test_null_pointers_rejected():
     # freeing an empty list is a no-op
     L.bmj_pairs_free(C.byref(pairs))
     L.bmj_pairs_free(None)
+
+
+def test_batch_arguments_rejected_on_host():
+    L = _bmj.lib()
+    off = np.array([0, 2, 4, 6], np.int64)
+    tok = np.array([1, 2, 1, 3, 2, 3], np.int32)
+    coll, keep = _bmj.make_collection(off, tok)
+    outs = (_bmj.bmj_pairs * 4)()
+    p = np.array([1, 1, 1, 1], np.uint32)
+    q = np.array([2, 2, 2, 2], np.uint32)
+
+    def call(js, pp=p, qq=q, n_jobs=2, **kw):
+        o = _bmj.bmj_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        js = np.array(js, np.int64)
+        return L.bmj_self_join_batch(C.byref(coll), n_jobs, js.ctypes.data_as(C.c_void_p), 0,
+                                     pp.ctypes.data_as(C.c_void_p), qq.ctypes.data_as(C.c_void_p),
+                                     C.byref(o), outs, None, None)
+    assert call([0, 1, 2]) == _bmj.BMJ_ERR_INVALID_ARG          # does not end at n_sets
+    assert call([1, 2, 3]) == _bmj.BMJ_ERR_INVALID_ARG          # does not start at 0
+    assert call([0, 2, 1, 3], n_jobs=3) == _bmj.BMJ_ERR_INVALID_ARG  # decreasing
+    assert call([0, 1, 3], pp=np.array([1, 3, 1, 1], np.uint32)) == _bmj.BMJ_ERR_INVALID_ARG  # p > q
+    assert call([0, 1, 3], b=100) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call([0, 1, 3], n_jobs=0) == _bmj.BMJ_ERR_INVALID_ARG

@@ -1,0 +1,119 @@
+"""Batched self-joins (many independent jobs in one pass) against the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_07295_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1711_07295_b300 import _bmj  # noqa: E402
+
+OM = {_bmj.BMJ_XOR: O.XOR, _bmj.BMJ_SET: O.SET, _bmj.BMJ_NEXT: O.NEXT}
+
+
+def make_batch(n_jobs, seed, lo=40, hi=2500, universe=3000, size_hi=60):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    ths = ((1, 2), (7, 10), (4, 5), (9, 10))
+    for k in range(n_jobs):
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        off, tok = I.random_collection(n, universe, 3, size_hi, seed=seed * 1000 + k,
+                                       planted_frac=0.1)
+        p, q = ths[int(rng.integers(0, 4))]
+        jobs.append((off, tok, p, q))
+    return jobs
+
+
+def concat(jobs):
+    offs, toks, js = [np.zeros(1, np.int64)], [], [0]
+    base = 0
+    for off, tok, _, _ in jobs:
+        offs.append(off[1:] + base)
+        toks.append(tok)
+        base += int(off[-1])
+        js.append(js[-1] + len(off) - 1)
+    return (np.concatenate(offs), np.concatenate(toks).astype(np.int32), np.array(js, np.int64),
+            np.array([j[2] for j in jobs], np.uint32), np.array([j[3] for j in jobs], np.uint32))
+
+
+def check(jobs, pairs, jst, method=_bmj.BMJ_XOR):
+    for k, (off, tok, p, q) in enumerate(jobs):
+        ra, rb = O.self_join(off, tok, p, q)
+        a, b = pairs[k]
+        assert np.array_equal(a, ra) and np.array_equal(b, rb), k
+        m = OM.get(jst[k]["method"], O.XOR)
+        w, s, r = O.filter_counts(off, tok, p, q, jst[k]["b"], m)
+        assert (jst[k]["window_pairs"], jst[k]["survivors"], jst[k]["results"]) == (w, s, r), k
+
+
+@pytest.mark.parametrize("b", [0, 64, 128, 256])
+def test_batch_matches_oracle(b):
+    jobs = make_batch(24, seed=b + 1)
+    off, tok, js, p, q = concat(jobs)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    pairs, jst, bst = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=b)
+    check(jobs, pairs, jst)
+    assert bst["tuned"] == (1 if b == 0 else 0)
+    if b:
+        assert all(s["b"] == b for s in jst)
+    assert bst["results"] == sum(len(x[0]) for x in pairs)
+
+
+def test_batch_combined_method_and_host_input():
+    jobs = make_batch(12, seed=7)
+    off, tok, js, p, q = concat(jobs)
+    pairs, jst, _ = _bmj.bmj_self_join_batch(off, tok, js, p, q, b=128, method=_bmj.BMJ_COMBINED)
+    for k, (_, _, pk, qk) in enumerate(jobs):
+        assert jst[k]["method"] == O.combined_method(pk, qk)
+    check(jobs, pairs, jst)
+
+
+def test_batch_equals_single_joins_and_graph_mode():
+    jobs = make_batch(16, seed=3)
+    off, tok, js, p, q = concat(jobs)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    plain, jst, bst = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=0)
+    graphed, jst_g, bst_g = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=0, use_graph=True)
+    assert bst_g["graph"] == 1 and bst["graph"] == 0
+    for k, (o, t, pk, qk) in enumerate(jobs):
+        a, b, st = _bmj.bmj_self_join(o, t, int(pk), int(qk), b=jst[k]["b"])
+        assert np.array_equal(plain[k][0], a) and np.array_equal(plain[k][1], b)
+        assert np.array_equal(graphed[k][0], a) and np.array_equal(graphed[k][1], b)
+        assert st["survivors"] == jst[k]["survivors"] == jst_g[k]["survivors"]
+
+
+def test_batch_overflow_empty_and_tiny_jobs():
+    jobs = make_batch(10, seed=11)
+    # an empty job, a one-set job and a job of identical sets
+    one = (np.array([0, 3], np.int64), np.array([1, 2, 3], np.int32), 1, 2)
+    same = (np.arange(0, 41, 4, dtype=np.int64), np.tile(np.array([5, 9, 70, 200], np.int32), 10), 1, 1)
+    empty = (np.zeros(1, np.int64), np.zeros(0, np.int32), 3, 4)
+    jobs = [empty] + jobs[:4] + [one, same] + jobs[4:] + [empty]
+    off, tok, js, p, q = concat(jobs)
+    pairs, jst, bst = _bmj.bmj_self_join_batch(off, tok, js, p, q, b=64, queue_cap=1)
+    assert bst["filter_passes"] == 2
+    check(jobs, pairs, jst)
+    assert len(pairs[0][0]) == 0 and len(pairs[5][0]) == 0 and len(pairs[6][0]) == 45
+
+
+def test_batch_device_output():
+    jobs = make_batch(6, seed=5)
+    off, tok, js, p, q = concat(jobs)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    dev_pairs, jst, _ = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=64, output_on_device=True)
+    host_pairs, _, _ = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=64)
+    for k in range(len(jobs)):
+        dp = dev_pairs[k]
+        if isinstance(dp, tuple):
+            assert len(dp[0]) == 0 == len(host_pairs[k][0])
+            continue
+        assert np.array_equal(dp.a.cpu().numpy().view(np.uint32), host_pairs[k][0])
+        assert np.array_equal(dp.b.cpu().numpy().view(np.uint32), host_pairs[k][1])
+        dp.release()
