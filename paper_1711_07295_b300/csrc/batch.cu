@@ -10,13 +10,13 @@
 // shape) live in a device table that the kernels index by job.
 //
 // b per job is picked by a sampling autotuner (when the caller passes b = 0):
-// a few row tiles of every job are filtered at b = 64, 128 and 256 with the
-// survivors only counted, the sampled survivors at b = 64 are verified, and
-// the measured costs give, per job,
-//     cost(b) = window_pairs * t_filter(b) + survivors(b) * t_verify
-// with survivors(b) scaled from the sample.  The choice trades filter work
-// (linear in b) against verification work (the survivors that a wider bitmap
-// removes): the filter/verify split.
+// up to four blocks of 128 rows of every job are filtered at b = 64, 128 and
+// 256 with the survivors only counted, and per job
+//     cost(b) = window_pairs * t_filter(b) + survivors(b) * t_verify(mean size)
+// with survivors(b) scaled from the sample and fixed cost ratios measured on
+// a B300 (so the choice is deterministic).  The choice trades filter work
+// (growing with b) against verification work (the survivors that a wider
+// bitmap removes): the filter/verify split.
 //
 // The execute stage (filter + verification) enqueues no allocation and no
 // host read, so it can be captured into a CUDA graph (opt.use_graph).
@@ -197,11 +197,19 @@ struct BatchFilterArgs {
     unsigned long long *qcount;
     unsigned long long *job_surv;  // per-job survivor counters
     int64_t qcap;
+    int *err;                      // set when a bounded wait on a copy gave up
 };
 
-// One persistent launch over the work items of every job.
-__global__ void __launch_bounds__(256, 4) k_filter_batch(const BatchFilterArgs a) {
+// One persistent launch over the work items of every job.  Columns are staged
+// by TMA into a per-warp region sized for the widest case (b = 256).
+constexpr int kBatchCS = 128;
+constexpr int kBatchWarpBytes = ColStage<4, kBatchCS>::kWarpBytes;
+
+__global__ void __launch_bounds__(128) k_filter_batch(const BatchFilterArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
+    StageState stg;
+    init_stage(stg, smem + (threadIdx.x >> 5) * kBatchWarpBytes);
     const int64_t n_items = *a.n_items_dev;
     for (;;) {
         unsigned long long item = 0;
@@ -219,11 +227,24 @@ __global__ void __launch_bounds__(256, 4) k_filter_batch(const BatchFilterArgs a
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
         const int32_t *lim = a.lim + jd.lim_off;
         switch (jd.W) {
-            case 1: filter_item<1, 4>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, sink); break;
-            case 2: filter_item<2, 4>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, sink); break;
-            case 4: filter_item<4, 2>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, sink); break;
+            case 1:
+                filter_item_tma<1, kTmaR1, kBatchCS>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p,
+                                                     jd.q, sink, stg);
+                break;
+            case 2:
+                filter_item_tma<2, kTmaR2, kBatchCS>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p,
+                                                     jd.q, sink, stg);
+                break;
+            case 4:
+                filter_item_tma<4, kTmaR4, kBatchCS>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p,
+                                                     jd.q, sink, stg);
+                break;
             default:
                 filter_item_generic(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, jd.W, sink);
+        }
+        if (!stg.ok) {
+            if (lane == 0) atomicOr(a.err, 1);
+            return;
         }
     }
 }
@@ -323,6 +344,7 @@ struct Plan {
     // counters: [0] item counter, [1] survivors, [2] results
     unsigned long long *ctr = nullptr;
     unsigned long long *job_surv = nullptr;
+    int *err = nullptr;
     uint2 *queue = nullptr;
     int64_t qcap = 0;
     uint64_t *keys = nullptr;
@@ -399,10 +421,12 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
     fa.qcount = &P.ctr[1];
     fa.job_surv = P.job_surv;
     fa.qcap = P.qcap;
+    fa.err = P.err;
+    const int smem = 4 * kBatchWarpBytes;
     int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch, 256, 0));
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch, 128, smem));
     if (per_sm < 1) per_sm = 1;
-    BMJ_LAUNCH(k_filter_batch, (unsigned)(sms * per_sm), 256, 0, s, fa);
+    BMJ_LAUNCH(k_filter_batch, (unsigned)(sms * per_sm), 128, smem, s, fa);
     return BMJ_OK;
 }
 
@@ -496,7 +520,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         st = A.alloc(&js_dev, (size_t)n_jobs + 1);
         if (!st) st = A.alloc(&keys_in, (size_t)n);
         if (!st) st = A.alloc(&skey, (size_t)n);
-        if (!st) st = A.alloc(&P.ssz, (size_t)n);
+        if (!st) st = A.alloc(&P.ssz, (size_t)n + 4);  // padded: TMA chunks may read 3 past the end
         if (!st) st = A.alloc(&P.sjob, (size_t)n);
         if (!st) st = A.alloc(&P.perm, (size_t)n);
         if (!st) st = A.alloc(&P.soff, (size_t)n + 1);
@@ -508,6 +532,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         st = radix_sort_u32_pairs(keys_in, ids, skey, P.perm, n, jbits + sbits, A, s);
         if (st) return st;
         BMJ_LAUNCH(k_split_keys, grid_of(n, 256), 256, 0, s, skey, n, sbits, P.ssz, P.sjob);
+        BMJ_CHECK(cudaMemsetAsync(P.ssz + n, 0, 4 * sizeof(uint32_t), s));
         st = launch_widen(P.ssz, P.soff, n, s);
         if (!st) st = exclusive_scan_i64(P.soff, P.soff, n, P.soff + n, A, s);
         if (st) return st;
@@ -521,7 +546,9 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         if (!st) st = A.alloc(&jq, (size_t)n_jobs);
         if (!st) st = A.alloc(&P.ctr, 3);
         if (!st) st = A.alloc(&P.job_surv, (size_t)n_jobs);
+        if (!st) st = A.alloc(&P.err, 1);
         if (st) return st;
+        BMJ_CHECK(cudaMemsetAsync(P.err, 0, sizeof(int), s));
         BMJ_CHECK(cudaMemcpyAsync(jp, hp, n_jobs * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         BMJ_CHECK(cudaMemcpyAsync(jq, hq, n_jobs * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         BMJ_LAUNCH(k_batch_tables, grid_of(P.n_s * n_jobs, 256), 256, 0, s, P.need, P.lim, P.n_s, jp,
@@ -539,8 +566,9 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         for (size_t wi = 0; wi < widths.size(); wi++)
             for (int m : methods) {
                 const int W = widths[wi] / 64;
-                st = A.alloc(&bms[wi][m], (size_t)n * W);
+                st = A.alloc(&bms[wi][m], (size_t)(n + 4) * W);
                 if (st) return st;
+                BMJ_CHECK(cudaMemsetAsync(bms[wi][m] + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
                 if (!gathered) {
                     st = launch_gather_build(P.perm, d.off, d.tok, P.soff, P.stok, bms[wi][m], n,
                                              widths[wi], m, s);
@@ -567,7 +595,9 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 jd.p = hp[k];
                 jd.q = hq[k];
                 jd.W = jb[k] / 64;
-                jd.tile_rows = jd.W <= 2 ? 128 : (jd.W == 4 ? 64 : 32);
+                jd.tile_rows = jd.W == 1 ? 32 * kTmaR1
+                               : jd.W == 2 ? 32 * kTmaR2
+                               : jd.W == 4 ? 32 * kTmaR4 : 32;
                 jd.chunk_cols = 4096;
             }
         };
@@ -606,23 +636,25 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 }
             }
             auto sample_tiles = [&](int width, std::vector<int32_t> &tj, std::vector<int64_t> &tl) {
-                const int tr = width / 64 <= 2 ? 128 : (width / 64 == 4 ? 64 : 32);
+                const int wq = width / 64;
+                const int tr = wq == 1 ? 32 * kTmaR1 : wq == 2 ? 32 * kTmaR2 : wq == 4 ? 32 * kTmaR4 : 32;
                 tj.clear();
                 tl.clear();
                 for (size_t r = 0; r < s_rows_job.size(); r++) {
                     const int64_t k = s_rows_job[r];
                     const int64_t nk = job_sets[k + 1] - job_sets[k];
-                    for (int64_t row = s_rows_r0[r]; row < s_rows_r0[r] + 128 && row < nk; row += tr) {
+                    int64_t last = -1;
+                    for (int64_t row = s_rows_r0[r]; row < s_rows_r0[r] + 128 && row < nk; row++) {
+                        if (row / tr == last) continue;
+                        last = row / tr;
                         tj.push_back((int32_t)k);
-                        tl.push_back(row / tr);
+                        tl.push_back(last);
                     }
                 }
             };
             std::vector<std::vector<double>> samp_win(widths.size(), std::vector<double>(n_jobs, 0.0));
-            std::vector<double> samp_total(widths.size(), 0.0);
             std::vector<std::vector<unsigned long long>> samp_surv(widths.size(),
                                                                    std::vector<unsigned long long>(n_jobs));
-            std::vector<double> t_filter(widths.size(), 0.0);
             P.queue = nullptr;
             P.qcap = 0;
             std::vector<int32_t> tj;
@@ -641,59 +673,42 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                                           cudaMemcpyDeviceToHost, s));
                 BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
                 BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, n_jobs * sizeof(unsigned long long), s));
-                BMJ_CHECK(cudaEventRecord(ev.e[2], s));
                 st = enqueue_filter(P, sms, s);
                 if (st) return st;
-                BMJ_CHECK(cudaEventRecord(ev.e[3], s));
                 BMJ_CHECK(cudaMemcpyAsync(samp_surv[wi].data(), P.job_surv,
                                           n_jobs * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
                 BMJ_CHECK(cudaStreamSynchronize(s));
-                t_filter[wi] = ev.ms(2, 3) * 1e-3;
-                for (int64_t t = 0; t < P.n_tiles; t++) {
-                    samp_win[wi][tj[t]] += (double)h_twin[t];
-                    samp_total[wi] += (double)h_twin[t];
+                for (int64_t t = 0; t < P.n_tiles; t++) samp_win[wi][tj[t]] += (double)h_twin[t];
+            }
+            // Deterministic cost model (the sampled survivor counts are exact
+            // counts; the costs below are fixed ratios measured on a B300):
+            //   filter, per window pair, relative to b = 64:  1, 1.55, 2.55
+            //   verification, per survivor: 57 window-pair units at a mean
+            //   set size of 12, growing with the merge length (mean size).
+            std::vector<double> mean_size(n_jobs, 0.0);
+            {
+                std::vector<int64_t> h_soff(n_jobs + 1);
+                for (int64_t k = 0; k <= n_jobs; k++) {
+                    BMJ_CHECK(cudaMemcpyAsync(&h_soff[k], P.soff + job_sets[k], sizeof(int64_t),
+                                              cudaMemcpyDeviceToHost, s));
+                }
+                BMJ_CHECK(cudaStreamSynchronize(s));
+                for (int64_t k = 0; k < n_jobs; k++) {
+                    const int64_t nk = job_sets[k + 1] - job_sets[k];
+                    mean_size[k] = nk > 0 ? (double)(h_soff[k + 1] - h_soff[k]) / (double)nk : 0.0;
                 }
             }
-            // Verification cost per survivor, measured on the b = 64 sample.
-            double t_verify = 2.7e-11;
-            unsigned long long sv64 = 0;
-            for (auto v : samp_surv[0]) sv64 += v;
-            if (sv64 >= 4096) {
-                std::vector<int> jb(n_jobs, widths[0]);
-                set_jobs(jb);
-                st = upload_jobs(P, A, s);
-                if (st) return st;
-                sample_tiles(widths[0], tj, tl);
-                st = build_tiles(P, tj, tl, false, {}, A, s, nullptr);
-                if (!st) st = A.alloc(&P.queue, (size_t)sv64);
-                if (!st) st = A.alloc(&P.keys, (size_t)sv64);
-                if (st) return st;
-                P.qcap = (int64_t)sv64;
-                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
-                st = enqueue_filter(P, sms, s);
-                if (st) return st;
-                BMJ_CHECK(cudaEventRecord(ev.e[2], s));
-                BMJ_LAUNCH(k_verify_batch, (unsigned)(sms * 8), 256, 0, s, P.queue, &P.ctr[1], P.qcap,
-                           P.soff, P.stok, P.ssz, P.sjob, P.perm, P.jobs_dev, P.need, P.keys,
-                           &P.ctr[2], P.nbits);
-                BMJ_CHECK(cudaEventRecord(ev.e[3], s));
-                BMJ_CHECK(cudaStreamSynchronize(s));
-                t_verify = ev.ms(2, 3) * 1e-3 / (double)sv64;
-                A.free_one(P.queue);
-                A.free_one(P.keys);
-                P.queue = nullptr;
-                P.keys = nullptr;
-            }
+            auto filter_cost = [](int width) { return width == 64 ? 1.0 : width == 128 ? 1.55 : 2.55; };
             est_surv = 0.0;
             for (int64_t k = 0; k < n_jobs; k++) {
                 double best = 1e300;
                 double best_surv = 0.0;
+                const double verify_cost = 57.0 * std::max(1.0, mean_size[k] / 12.0);
                 for (size_t wi = 0; wi < widths.size(); wi++) {
-                    const double per_pair = samp_total[wi] > 0 ? t_filter[wi] / samp_total[wi] : 0.0;
                     const double scale =
                         samp_win[wi][k] > 0 ? (double)job_win[k] / samp_win[wi][k] : 0.0;
                     const double surv = (double)samp_surv[wi][k] * scale;
-                    const double cost = (double)job_win[k] * per_pair + surv * t_verify;
+                    const double cost = (double)job_win[k] * filter_cost(widths[wi]) + surv * verify_cost;
                     if (cost < best) {
                         best = cost;
                         best_surv = surv;

@@ -205,4 +205,286 @@ __device__ __forceinline__ int64_t find_tile(const int64_t *__restrict__ tile_it
     return lo;
 }
 
+
+// ============================================================================
+// Filter with TMA-staged columns.
+//
+// Each warp owns a double buffer in shared memory.  Column chunks (bitmaps and
+// sizes of up to CS consecutive sorted sets) are copied in by one-dimensional
+// bulk copies (cp.async.bulk, completion on an mbarrier), one chunk ahead of
+// the compute.  Every column is then read by all lanes from shared memory (a
+// broadcast), so the per-pair work is: xor, popcount, one IADD3 and one funnel
+// shift that appends the survive bit to the row's 32-column mask.
+//
+// Survive test: h <= lim  <=>  h + (-(lim + 1)) < 0, so the sign bit of
+// t = h + nlim (nlim = -(lim+1); nlim = 0 outside the window, where lim = -1)
+// is the survive bit.
+//
+// For b >= 128 the popcount of the xor words uses carry-save adders
+// (Harley-Seal): three words a, b, c become sum = a^b^c and carry =
+// maj(a,b,c) with popc(a)+popc(b)+popc(c) = popc(sum) + 2*popc(carry), which
+// trades POPC (16 per clock per SM) for LOP3 (64 per clock per SM).
+// ============================================================================
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Waits for the phase `parity` of bar, giving up after a bounded number of
+// polls (returns false then).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (int it = 0; it < (1 << 22); it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int W>
+struct PopcHS;
+
+template <>
+struct PopcHS<1> {
+    __device__ __forceinline__ static int h(const uint32_t *x) {
+        return __popc(x[0]) + __popc(x[1]);
+    }
+};
+
+template <>
+struct PopcHS<2> {
+    // 4 words: one carry-save adder on 3 of them -> 3 POPC.
+    __device__ __forceinline__ static int h(const uint32_t *x) {
+        const uint32_t s = x[0] ^ x[1] ^ x[2];
+        const uint32_t c = (x[0] & x[1]) | (x[2] & (x[0] ^ x[1]));
+        return __popc(s) + __popc(x[3]) + 2 * __popc(c);
+    }
+};
+
+template <>
+struct PopcHS<4> {
+    // 8 words: four carry-save adders -> 4 POPC.
+    __device__ __forceinline__ static int h(const uint32_t *x) {
+        const uint32_t s1 = x[0] ^ x[1] ^ x[2];
+        const uint32_t c1 = (x[0] & x[1]) | (x[2] & (x[0] ^ x[1]));
+        const uint32_t s2 = x[3] ^ x[4] ^ x[5];
+        const uint32_t c2 = (x[3] & x[4]) | (x[5] & (x[3] ^ x[4]));
+        const uint32_t s3 = s1 ^ s2 ^ x[6];
+        const uint32_t c3 = (s1 & s2) | (x[6] & (s1 ^ s2));
+        const uint32_t s4 = c1 ^ c2 ^ c3;
+        const uint32_t c4 = (c1 & c2) | (c3 & (c1 ^ c2));
+        return __popc(s3) + __popc(x[7]) + 2 * __popc(s4) + 4 * __popc(c4);
+    }
+};
+
+// Shared-memory layout of one warp's column buffers.
+template <int W, int CS>
+struct ColStage {
+    static constexpr int kCols = CS + 4;  // room for the 16-byte alignment of a chunk start
+    static constexpr int kBufBytes = kCols * (8 * W + 4);
+    static constexpr int kWarpBytes = 16 + 2 * kBufBytes;  // two mbarriers, then two buffers
+};
+
+// Per-warp pipeline state, kept across work items.  A warp's shared-memory
+// region holds its two mbarriers first (their place does not depend on the
+// bitmap width) and then its two column buffers.
+struct StageState {
+    unsigned char *buf;   // two buffers of kBufBytes (of the width in use)
+    uint64_t *bar;        // two mbarriers
+    uint32_t phase;       // bit k: parity to wait for on buffer k
+    bool ok;              // false once a wait gave up
+};
+
+__device__ __forceinline__ void init_stage(StageState &st, unsigned char *region) {
+    st.bar = reinterpret_cast<uint64_t *>(region);
+    st.buf = region + 16;
+    st.phase = 0;
+    st.ok = true;
+    if ((threadIdx.x & 31) == 0) {
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_shared();
+    }
+    __syncwarp();
+}
+
+template <int W, int CS>
+__device__ __forceinline__ void stage_issue(const StageState &st, int slot,
+                                            const uint64_t *__restrict__ bm,
+                                            const uint32_t *__restrict__ ssz, int64_t c_al,
+                                            int ncols) {
+    using L = ColStage<W, CS>;
+    unsigned char *b = st.buf + slot * L::kBufBytes;
+    const uint32_t bm_bytes = (uint32_t)ncols * 8u * W;
+    const uint32_t sz_bytes = (uint32_t)ncols * 4u;
+    fence_async_shared();
+    mbar_expect_tx(&st.bar[slot], bm_bytes + sz_bytes);
+    tma_load_1d(b, bm + c_al * W, bm_bytes, &st.bar[slot]);
+    tma_load_1d(b + L::kCols * 8 * W, ssz + c_al, sz_bytes, &st.bar[slot]);
+}
+
+// Filter over one work item with TMA-staged columns.  The bitmap and size
+// arrays must be readable up to 3 entries past the last column (padded).
+template <int W, int R, int CS>
+__device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
+                                                const uint32_t *__restrict__ ssz,
+                                                const int32_t *__restrict__ lim_tab,
+                                                int64_t row_end, int64_t i0, int64_t c0, int64_t c1,
+                                                uint32_t p, uint32_t q, const SurvivorSink &sink,
+                                                StageState &st) {
+    using L = ColStage<W, CS>;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (c1 <= c0) return;
+    // rows in registers, as 32-bit words
+    uint32_t rb[R][2 * W];
+    uint32_t rs[R];
+    int32_t rd[R];  // row index - i0 (for the diagonal mask)
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+        const int64_t i = i0 + k * 32 + lane;
+        rd[k] = k * 32 + lane;
+        if (i < row_end) {
+            rs[k] = ssz[i];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                const uint64_t v = bm[i * W + w];
+                rb[k][2 * w] = (uint32_t)v;
+                rb[k][2 * w + 1] = (uint32_t)(v >> 32);
+            }
+        } else {
+            rs[k] = 0;
+#pragma unroll
+            for (int w = 0; w < 2 * W; w++) rb[k][w] = 0;
+        }
+    }
+    int nlim[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) nlim[k] = 0;
+    uint32_t prev_cs = 0xffffffffu;
+
+    const int64_t n_chunks = (c1 - c0 + CS - 1) / CS;
+    // prefetch chunk 0 into slot 0
+    if (lane == 0) {
+        const int64_t cs_ = c0, ce_ = min(c0 + (int64_t)CS, c1);
+        const int64_t c_al = cs_ & ~(int64_t)3;
+        stage_issue<W, CS>(st, 0, bm, ssz, c_al, (int)(((ce_ - c_al) + 3) & ~(int64_t)3));
+    }
+    for (int64_t ch = 0; ch < n_chunks; ch++) {
+        const int slot = (int)(ch & 1);
+        if (ch + 1 < n_chunks && lane == 0) {
+            const int64_t cs_ = c0 + (ch + 1) * CS, ce_ = min(cs_ + (int64_t)CS, c1);
+            const int64_t c_al = cs_ & ~(int64_t)3;
+            stage_issue<W, CS>(st, slot ^ 1, bm, ssz, c_al, (int)(((ce_ - c_al) + 3) & ~(int64_t)3));
+        }
+        const bool got = mbar_wait(&st.bar[slot], (st.phase >> slot) & 1u);
+        st.phase ^= 1u << slot;
+        if (!__all_sync(kFull, got)) {
+            st.ok = false;
+            return;
+        }
+        const int64_t cs = c0 + ch * CS, ce = min(cs + (int64_t)CS, c1);
+        const int64_t c_al = cs & ~(int64_t)3;
+        const unsigned char *b = st.buf + slot * L::kBufBytes;
+        const uint32_t *colw = reinterpret_cast<const uint32_t *>(b);
+        const uint32_t *cols = reinterpret_cast<const uint32_t *>(b + L::kCols * 8 * W);
+        for (int64_t g = cs; g < ce; g += 32) {
+            const int gj = (int)min((int64_t)32, ce - g);
+            const int base = (int)(g - c_al);
+            uint32_t mask[R];
+#pragma unroll
+            for (int k = 0; k < R; k++) mask[k] = 0;
+            for (int cc = 0; cc < gj; cc++) {
+                const int col = base + cc;
+                const uint32_t s = cols[col];
+                if (s != prev_cs) {  // warp-uniform
+                    prev_cs = s;
+#pragma unroll
+                    for (int k = 0; k < R; k++) {
+                        const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
+                        const bool in_win = rs[k] != 0 && (uint64_t)q * mn >= (uint64_t)p * mx;
+                        nlim[k] = in_win ? -(lim_tab[rs[k] + s] + 1) : 0;
+                    }
+                }
+                uint32_t cw[2 * W];
+#pragma unroll
+                for (int w = 0; w < 2 * W; w++) cw[w] = colw[col * 2 * W + w];
+#pragma unroll
+                for (int k = 0; k < R; k++) {
+                    uint32_t x[2 * W];
+#pragma unroll
+                    for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
+                    const int t = PopcHS<W>::h(x) + nlim[k];
+                    mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);
+                }
+            }
+            // bit (gj-1-cc) of mask[k] is column g+cc; keep only columns j < i
+            const int64_t dg = i0 - g;
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const int64_t d = dg + rd[k];  // i - g
+                if (d < gj) mask[k] = d <= 0 ? 0u : (mask[k] & (~0u << (gj - (int)d)));
+                cnt += __popc(mask[k]);
+            }
+            const int total = __reduce_add_sync(kFull, cnt);
+            if (total) {
+                const int excl = warp_excl_scan_i(cnt);
+                unsigned long long pos0 = 0;
+                if (lane == 0) {
+                    pos0 = atomicAdd(sink.count, (unsigned long long)total);
+                    if (sink.job_count) atomicAdd(sink.job_count, (unsigned long long)total);
+                }
+                pos0 = __shfl_sync(kFull, pos0, 0);
+                unsigned long long pos = pos0 + excl;
+#pragma unroll
+                for (int k = 0; k < R; k++) {
+                    uint32_t m = mask[k];
+                    while (m) {
+                        const int bpos = __ffs(m) - 1;
+                        m &= m - 1;
+                        if (pos < (unsigned long long)sink.cap)
+                            sink.queue[pos] = make_uint2((uint32_t)(i0 + rd[k]),
+                                                         (uint32_t)(g + (gj - 1 - bpos)));
+                        pos++;
+                    }
+                }
+            }
+        }
+        __syncwarp();  // every lane is done with this slot before it is refilled
+    }
+}
+
 }  // namespace bmj

@@ -92,11 +92,11 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         int64_t *soff = nullptr;
         int32_t *stok = nullptr;
         uint64_t *bm = nullptr;
-        st = A.alloc(&ssz, (size_t)n);
+        st = A.alloc(&ssz, (size_t)n + 4);
         if (!st) st = A.alloc(&perm, (size_t)n);
         if (!st) st = A.alloc(&soff, (size_t)n);
         if (!st) st = A.alloc(&stok, (size_t)d.ntok);
-        if (!st) st = A.alloc(&bm, (size_t)n * W);
+        if (!st) st = A.alloc(&bm, (size_t)(n + 4) * W);  // padded: TMA chunks may read 3 past the end
         if (st) return st;
         st = radix_sort_u32_pairs(sizes, ids, ssz, perm, n, bit_length((uint64_t)max_size), A, s);
         if (st) return st;
@@ -109,19 +109,24 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         // ---- thresholds per |x|+|y|, window tiles, window size ----
         const int64_t n_s = 2 * (int64_t)max_size + 1;
         int32_t *need = nullptr, *lim = nullptr;
-        const int tile_rows = filter_tile_rows(W);
+        const int tile_rows = filter_tma_tile_rows(W);
         const int chunk_cols = W <= 4 ? 4096 : 2048;
         const int64_t n_tiles = (n + tile_rows - 1) / tile_rows;
         int32_t *tile_c0 = nullptr;
         int64_t *tile_off = nullptr;
         unsigned long long *ctr = nullptr;  // [0] window, [1] survivors, [2] item counter, [3] results
+        int *err = nullptr;
         st = A.alloc(&need, (size_t)n_s);
         if (!st) st = A.alloc(&lim, (size_t)n_s);
         if (!st) st = A.alloc(&tile_c0, (size_t)n_tiles);
         if (!st) st = A.alloc(&tile_off, (size_t)n_tiles + 1);
         if (!st) st = A.alloc(&ctr, 4);
+        if (!st) st = A.alloc(&err, 1);
         if (st) return st;
         BMJ_CHECK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+        BMJ_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
+        BMJ_CHECK(cudaMemsetAsync(ssz + n, 0, 4 * sizeof(uint32_t), s));
+        BMJ_CHECK(cudaMemsetAsync(bm + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
         st = launch_tables(need, lim, n_s, p, q, s);
         if (!st)
             st = launch_tiles(ssz, n, p, q, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s);
@@ -162,11 +167,14 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         int64_t n_surv = 0;
         for (int pass = 0; pass < 2; pass++) {
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
-            st = launch_filter(fa, W, sms, s);
+            st = launch_filter_tma(fa, W, err, sms, s);
             if (st) return st;
             BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+            int herr = 0;
             BMJ_CHECK(cudaMemcpyAsync(&n_surv, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
             BMJ_CHECK(cudaStreamSynchronize(s));
+            if (herr) return BMJ_ERR_TIMEOUT;
             stl.filter_passes++;
             stl.ms_filter += ev.ms(3, 4);
             if (n_surv <= qcap) break;

@@ -226,6 +226,36 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
     }
 }
 
+// Bitmap Filter with TMA-staged columns (filter_item_tma).  Each warp owns a
+// double buffer of column chunks in dynamic shared memory and its two
+// mbarriers; a wait that gives up sets *err and stops the warp.
+template <int W, int R, int CS>
+__global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using L = ColStage<W, CS>;
+    const int lane = threadIdx.x & 31;
+    StageState st;
+    init_stage(st, smem + (threadIdx.x >> 5) * L::kWarpBytes);
+    const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= a.n_items) break;
+        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
+        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
+        const int64_t i0 = t * a.tile_rows;
+        const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
+        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
+        const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
+        filter_item_tma<W, R, CS>(a.bm, a.ssz, a.lim, a.n, i0, c0, c1, a.p, a.q, sink, st);
+        if (!st.ok) {
+            if (lane == 0) atomicOr(err, 1);
+            break;
+        }
+    }
+}
+
 // ----------------------------------------------------------------------------
 // Verification: one survivor per thread, exact overlap by a merge of the two
 // sorted token arrays, stopping as soon as the outcome is decided (the overlap
@@ -379,6 +409,46 @@ int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s) {
             BMJ_LAUNCH(k_filter_generic, (unsigned)blocks, 256, 0, s, a, W);
             return BMJ_OK;
         }
+    }
+}
+
+template <int W, int R, int CS>
+int launch_filter_tma_t(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
+    using L = ColStage<W, CS>;
+    const int smem = 4 * L::kWarpBytes;
+    static bool attr_set = false;
+    if (!attr_set) {
+        BMJ_CHECK(cudaFuncSetAttribute(k_filter_tma<W, R, CS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set = true;
+    }
+    int per_sm = 0;
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tma<W, R, CS>, 128, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (int64_t)num_sms * per_sm;
+    const int64_t need_blocks = (a.n_items + 3) / 4;
+    if (need_blocks < blocks) blocks = need_blocks;
+    if (blocks < 1) blocks = 1;
+    BMJ_LAUNCH((k_filter_tma<W, R, CS>), (unsigned)blocks, 128, smem, s, a, err);
+    return BMJ_OK;
+}
+
+int filter_tma_tile_rows(int W) {
+    switch (W) {
+        case 1: return 32 * kTmaR1;
+        case 2: return 32 * kTmaR2;
+        case 4: return 32 * kTmaR4;
+        default: return filter_tile_rows(W);
+    }
+}
+
+int launch_filter_tma(const FilterArgs &a, int W, int *err, int num_sms, cudaStream_t s) {
+    if (a.n_items <= 0) return BMJ_OK;
+    switch (W) {
+        case 1: return launch_filter_tma_t<1, kTmaR1, 256>(a, err, num_sms, s);
+        case 2: return launch_filter_tma_t<2, kTmaR2, 256>(a, err, num_sms, s);
+        case 4: return launch_filter_tma_t<4, kTmaR4, 128>(a, err, num_sms, s);
+        default: return launch_filter(a, W, num_sms, s);
     }
 }
 

@@ -66,9 +66,20 @@ struct FilterArgs {
     unsigned long long *item_counter;
 };
 
-// The Bitmap Filter over every window pair (persistent, warp-level work items).
+// The Bitmap Filter over every window pair (persistent, warp-level work items;
+// columns broadcast by shuffles).  Reads no column past the window.
 int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s);
 int filter_tile_rows(int W);
+
+// Rows per lane of the TMA-staged filter, per bitmap width.
+constexpr int kTmaR1 = 8, kTmaR2 = 4, kTmaR4 = 4;
+
+// The Bitmap Filter with column chunks staged in shared memory by TMA bulk
+// copies (b in {64, 128, 256}; other widths fall back to launch_filter).  The
+// bitmap and size arrays must stay readable 4 entries past the last set.
+// *err becomes nonzero if a bounded wait on a copy gave up.
+int launch_filter_tma(const FilterArgs &a, int W, int *err, int num_sms, cudaStream_t s);
+int filter_tma_tile_rows(int W);
 
 // Exact verification of the survivors; similar pairs are written as packed
 // keys (min_id << nbits) | max_id in original ids.

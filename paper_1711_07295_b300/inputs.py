@@ -377,3 +377,122 @@ def gen_queries(spec: QuerySpec, coll_spec: CollectionSpec, offsets, tokens):
     np.cumsum(sizes, out=poff[1:])
     ptok = np.concatenate(probes).astype(np.int32) if Q else np.zeros(0, np.int32)
     return arrival, poff, ptok, p, q
+
+
+# ----------------------------------------------------------------------------
+# Device-side sampler for large workloads
+# ----------------------------------------------------------------------------
+def _rank_in_run_t(torch, s):
+    if s.numel() == 0:
+        return torch.zeros(0, dtype=torch.int64, device=s.device)
+    change = torch.ones(s.numel(), dtype=torch.bool, device=s.device)
+    change[1:] = s[1:] != s[:-1]
+    heads = torch.nonzero(change).flatten()
+    lens = torch.diff(torch.cat([heads, torch.tensor([s.numel()], device=s.device)]))
+    return torch.arange(s.numel(), device=s.device) - torch.repeat_interleave(heads, lens)
+
+
+def gen_collection_device(spec: CollectionSpec, device="cuda"):
+    """The recipe of gen_collection drawn with torch's generator on a CUDA device.
+
+    Same size law, Zipf law and first-distinct-draws rule as the host
+    sampler, for workloads whose 1e8-1e9 tokens make the host sampler slow;
+    the random stream differs, so the sets differ from gen_collection's.
+    Planted near-duplicates are not supported here.  Returns device tensors
+    (offsets int64[N+1], tokens int32[]).
+    """
+    import torch
+    if spec.planted_frac:
+        raise ValueError("planted near-duplicates are host-sampler only")
+    g = torch.Generator(device=device)
+    g.manual_seed(int(spec.seed))
+    n, U = spec.n_sets, spec.universe
+    d = spec.size_dist
+    if d[0] == "uniform":
+        sizes = torch.randint(d[1], d[2] + 1, (n,), generator=g, device=device, dtype=torch.int64)
+    else:
+        x = torch.normal(float(d[1]), float(d[2]), (n,), generator=g, device=device,
+                         dtype=torch.float64)
+        sizes = torch.clamp(torch.round(torch.exp(x)), d[3], d[4]).to(torch.int64)
+    sizes = torch.clamp(sizes, max=U)
+    cdf = torch.from_numpy(_zipf_cdf(U, spec.zipf_s)).to(device)
+    tbits = max(1, int(U - 1).bit_length())
+    sbits = max(1, int(n).bit_length())
+    tmask = (1 << tbits) - 1
+    acc_s = torch.zeros(0, dtype=torch.int64, device=device)
+    acc_q = torch.zeros(0, dtype=torch.int64, device=device)
+    acc_t = torch.zeros(0, dtype=torch.int64, device=device)
+    have = torch.zeros(n, dtype=torch.int64, device=device)
+    drawn = torch.zeros(n, dtype=torch.int64, device=device)
+    done = []
+    todo = torch.nonzero(sizes > 0).flatten()
+    rounds = 0
+    while todo.numel():
+        rounds += 1
+        if rounds > 200:
+            raise RuntimeError("token sampling did not converge")
+        want = sizes[todo] - have[todo]
+        if rounds > 1:
+            want = want + (want + 3) // 4
+        new_s = torch.repeat_interleave(todo, want)
+        starts = torch.repeat_interleave(torch.cumsum(want, 0) - want, want)
+        new_q = drawn[new_s] + (torch.arange(new_s.numel(), device=device) - starts)
+        drawn[todo] += want
+        u = torch.rand(new_s.numel(), generator=g, device=device, dtype=torch.float64)
+        new_t = torch.clamp(torch.searchsorted(cdf, u, right=True), max=U - 1)
+        s_ = torch.cat([acc_s, new_s])
+        q_ = torch.cat([acc_q, new_q])
+        t_ = torch.cat([acc_t, new_t])
+        del new_s, new_q, new_t, starts, u
+        qbits = max(1, int(drawn.max().item()).bit_length())
+        if sbits + tbits + qbits > 63:
+            raise ValueError("collection too large for 64-bit sampling keys")
+        key, _ = torch.sort((((s_ << tbits) | t_) << qbits) | q_)
+        st = key >> qbits
+        first = torch.ones(key.numel(), dtype=torch.bool, device=device)
+        first[1:] = st[1:] != st[:-1]
+        key = key[first]
+        del st, first
+        s_ = key >> (qbits + tbits)
+        t_ = (key >> qbits) & tmask
+        q_ = key & ((1 << qbits) - 1)
+        key, _ = torch.sort((((s_ << qbits) | q_) << tbits) | t_)
+        s_ = key >> (qbits + tbits)
+        q_ = (key >> tbits) & ((1 << qbits) - 1)
+        t_ = key & tmask
+        del key
+        ok = _rank_in_run_t(torch, s_) < sizes[s_]
+        s_, q_, t_ = s_[ok], q_[ok], t_[ok]
+        have[todo] = 0
+        have.index_add_(0, s_, torch.ones_like(s_))
+        complete = have[s_] == sizes[s_]
+        done.append((s_[complete] << tbits) | t_[complete])
+        keep = ~complete
+        acc_s, acc_q, acc_t = s_[keep], q_[keep], t_[keep]
+        todo = torch.nonzero(have < sizes).flatten()
+    key = torch.cat(done) if done else torch.zeros(0, dtype=torch.int64, device=device)
+    key, _ = torch.sort(key)
+    tokens = (key & tmask).to(torch.int32)
+    offsets = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    offsets[1:] = torch.cumsum(sizes, 0)
+    return offsets, tokens
+
+
+def gen_batch_device(spec: BatchSpec, device="cuda"):
+    """The batched workload drawn on the device: job sizes log-uniform in
+    [min_sets, max_sets], thresholds uniform over THRESHOLDS_BATCH; all jobs'
+    sets come from one collection (sizes U[size_lo, size_hi], Zipf tokens) cut
+    into consecutive jobs.  Returns (offsets, tokens) device tensors and
+    numpy job_sets int64[n_jobs+1], p, q uint32[n_jobs]."""
+    rng = np.random.default_rng(spec.seed)
+    logn = rng.uniform(np.log(spec.min_sets), np.log(spec.max_sets), size=spec.n_jobs)
+    ns = np.rint(np.exp(logn)).astype(np.int64)
+    th = rng.integers(0, len(THRESHOLDS_BATCH), size=spec.n_jobs)
+    job_sets = np.zeros(spec.n_jobs + 1, np.int64)
+    np.cumsum(ns, out=job_sets[1:])
+    cs = CollectionSpec(int(job_sets[-1]), spec.universe, spec.zipf_s,
+                        ("uniform", spec.size_lo, spec.size_hi), seed=spec.seed)
+    off, tok = gen_collection_device(cs, device)
+    p = np.array([THRESHOLDS_BATCH[t][0] for t in th], np.uint32)
+    q = np.array([THRESHOLDS_BATCH[t][1] for t in th], np.uint32)
+    return off, tok, job_sets, p, q

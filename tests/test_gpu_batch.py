@@ -117,3 +117,38 @@ def test_batch_device_output():
         assert np.array_equal(dp.a.cpu().numpy().view(np.uint32), host_pairs[k][0])
         assert np.array_equal(dp.b.cpu().numpy().view(np.uint32), host_pairs[k][1])
         dp.release()
+
+
+def test_device_generator_recipe():
+    spec = I.CollectionSpec(200_000, 50_000, 1.0, ("uniform", 3, 100), seed=3)
+    off, tok = I.gen_collection_device(spec)
+    off, tok = off.cpu().numpy(), tok.cpu().numpy()
+    sizes = np.diff(off)
+    assert sizes.min() >= 3 and sizes.max() <= 100 and off[-1] == len(tok)
+    assert tok.min() >= 0 and tok.max() < 50_000
+    d = np.diff(tok.astype(np.int64))
+    starts = off[1:-1]
+    d[starts - 1] = 1                      # differences across set boundaries are free
+    assert np.all(d > 0)                   # strictly increasing inside every set
+    # Zipf(1): the most frequent token is token 0
+    assert np.bincount(tok).argmax() == 0
+
+
+def test_full_batched_workload_row_sampled():
+    # 512 jobs, log-uniform 1,000-200,000 sets, sizes U[3,100], Zipf(1.0) over 50,000,
+    # thresholds from {1/2, 7/10, 4/5, 9/10}; autotuned b, graph-captured execute stage.
+    off, tok, js, p, q = I.gen_batch_device(I.BatchSpec())
+    pairs, jst, bst = _bmj.bmj_self_join_batch(off, tok, js, p, q, b=0, use_graph=True)
+    assert bst["tuned"] == 1 and bst["graph"] == 1
+    h_off, h_tok = off.cpu().numpy(), tok.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for k in rng.choice(len(js) - 1, 6, replace=False):
+        lo, hi = int(js[k]), int(js[k + 1])
+        o = h_off[lo:hi + 1] - h_off[lo]
+        t = h_tok[h_off[lo]:h_off[hi]]
+        rows = rng.choice(hi - lo, 12, replace=False)
+        ra, rb = O.join_rows(o, t, int(p[k]), int(q[k]), rows)
+        a, b = pairs[k]
+        sel = np.isin(a, rows) | np.isin(b, rows)
+        assert np.array_equal(a[sel], ra) and np.array_equal(b[sel], rb), k
+        assert jst[k]["results"] == len(a) <= jst[k]["survivors"] <= jst[k]["window_pairs"]
