@@ -207,6 +207,85 @@ int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs, const int64_
                         int sim, const uint32_t *p, const uint32_t *q, const bmj_options *opt,
                         bmj_pairs *outs, bmj_stats *job_stats, bmj_batch_stats *batch_stats);
 
+/* ---- resident index and served queries --------------------------------- */
+
+/* A collection kept resident on the device in size order (sizes, sorted CSR,
+ * b-bit bitmaps), built once and probed many times. */
+typedef struct bmj_index bmj_index;
+
+/* Result of a query batch: the ids of query x are
+ * ids[offsets[x] .. offsets[x+1]-1] (original resident ids, ascending).
+ * Library-owned host memory; free with bmj_id_lists_free. */
+typedef struct {
+    int64_t  n_queries;
+    int64_t *offsets;   /* n_queries + 1 */
+    int64_t *ids;
+} bmj_id_lists;
+
+typedef struct {
+    int32_t n_slots;               /* batches in flight at once (default 4) */
+    int32_t reserved0;
+    int64_t max_batch_queries;     /* queries per batch (default 4096) */
+    int64_t max_batch_window_pairs;/* memory admission: window pairs per batch (default 2^25);
+                                      raised to the largest single query's window */
+    int64_t reserved[4];
+} bmj_serve_options;
+
+typedef struct {
+    int64_t n_queries;
+    int64_t batches;
+    int64_t window_pairs;   /* pairs the Bitmap Filter evaluated */
+    int64_t survivors;
+    int64_t results;
+    double  wall_s;         /* from the first arrival slot to the last completion */
+    double  qps;
+    double  p50_ms, p99_ms, max_ms;  /* latency = completion - arrival */
+    double  reserved[4];
+} bmj_serve_stats;
+
+/*
+ * Builds a resident index of coll (host or device; copied, so the caller may
+ * free coll afterwards) with opt->b and opt->method (BMJ_XOR, BMJ_SET or
+ * BMJ_NEXT; NULL = defaults).  The index is bound to the current device.
+ * Errors as for bmj_self_join.  No counterpart in the paper beyond Alg. 5's
+ * initialisation (bitmaps of every set built once).
+ */
+int bmj_index_create(const bmj_collection *coll, const bmj_options *opt, bmj_index **out);
+void bmj_index_destroy(bmj_index *idx);
+int64_t bmj_index_size(const bmj_index *idx);
+
+/* Fills *opt with the serving defaults listed above. */
+void bmj_default_serve_options(bmj_serve_options *opt);
+
+/*
+ * Probe queries against the index: for every probe set x (host collection,
+ * tokens strictly increasing) the resident sets s with
+ * Jaccard(x, s) >= p[x]/q[x] (an RS-join with |R| = 1, Eq. 1).  Candidates
+ * are the resident sets inside both sides of the length window (Table 2),
+ * filtered by the Eq. 2 bound and verified exactly.  Runs as one batch and
+ * returns when done.  out is filled (free with bmj_id_lists_free); stats
+ * optional.
+ */
+int bmj_index_query(bmj_index *idx, const bmj_collection *probes, const uint32_t *p,
+                    const uint32_t *q, bmj_id_lists *out, bmj_serve_stats *stats);
+
+/*
+ * Serves an arrival stream with continuous batching: query x becomes
+ * available at arrival_s[x] seconds after the call starts (nondecreasing).
+ * Arrived queries are admitted into a free slot (stream + fixed buffers) up
+ * to opt->max_batch_queries and while the batch's exact window-pair count
+ * stays within opt->max_batch_window_pairs (this bounds every buffer of the
+ * batch); up to opt->n_slots batches are in flight and overlap on the device.
+ * Results go to *out (optional), per-query latency in milliseconds to
+ * latency_ms[x] (optional), totals and p50/p99 to *stats (optional).  Each
+ * query's result does not depend on how it was batched.
+ */
+int bmj_serve(bmj_index *idx, const bmj_collection *queries, const double *arrival_s,
+              const uint32_t *p, const uint32_t *q, const bmj_serve_options *opt,
+              bmj_id_lists *out, double *latency_ms, bmj_serve_stats *stats);
+
+void bmj_id_lists_free(bmj_id_lists *lists);
+
 /* Releases a pair list returned by the library and empties *pairs.
  * Safe on an empty or already freed list. */
 void bmj_pairs_free(bmj_pairs *pairs);

@@ -71,6 +71,26 @@ class bmj_batch_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
+class bmj_id_lists(C.Structure):
+    _fields_ = [("n_queries", C.c_int64), ("offsets", C.c_void_p), ("ids", C.c_void_p)]
+
+
+class bmj_serve_options(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("reserved0", C.c_int32),
+                ("max_batch_queries", C.c_int64), ("max_batch_window_pairs", C.c_int64),
+                ("reserved", C.c_int64 * 4)]
+
+
+class bmj_serve_stats(C.Structure):
+    _fields_ = [("n_queries", C.c_int64), ("batches", C.c_int64), ("window_pairs", C.c_int64),
+                ("survivors", C.c_int64), ("results", C.c_int64), ("wall_s", C.c_double),
+                ("qps", C.c_double), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double), ("reserved", C.c_double * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
 class BmjError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -93,6 +113,17 @@ SIGNATURES = {
                                       C.POINTER(bmj_pairs), C.POINTER(bmj_stats),
                                       C.POINTER(bmj_batch_stats)]),
     "bmj_pairs_free": (None, [C.POINTER(bmj_pairs)]),
+    "bmj_index_create": (C.c_int, [C.POINTER(bmj_collection), C.POINTER(bmj_options),
+                                   C.POINTER(C.c_void_p)]),
+    "bmj_index_destroy": (None, [C.c_void_p]),
+    "bmj_index_size": (C.c_int64, [C.c_void_p]),
+    "bmj_default_serve_options": (None, [C.POINTER(bmj_serve_options)]),
+    "bmj_index_query": (C.c_int, [C.c_void_p, C.POINTER(bmj_collection), C.c_void_p, C.c_void_p,
+                                  C.POINTER(bmj_id_lists), C.POINTER(bmj_serve_stats)]),
+    "bmj_serve": (C.c_int, [C.c_void_p, C.POINTER(bmj_collection), C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.POINTER(bmj_serve_options), C.POINTER(bmj_id_lists),
+                            C.c_void_p, C.POINTER(bmj_serve_stats)]),
+    "bmj_id_lists_free": (None, [C.POINTER(bmj_id_lists)]),
     "bmj_kernel_launches": (C.c_int64, []),
     "bmj_bitmap_filter_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_uint32,
                                             C.c_uint32, C.c_void_p, C.c_int64,
@@ -320,3 +351,85 @@ def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int
             pairs.append((a, bb))
         lib().bmj_pairs_free(C.byref(outs[k]))
     return pairs, [jst[k].as_dict() for k in range(n_jobs)], bst.as_dict()
+
+
+def _take_id_lists(lists: bmj_id_lists):
+    n = int(lists.n_queries)
+    if n == 0 or not lists.offsets:
+        lib().bmj_id_lists_free(C.byref(lists))
+        return []
+    off = np.ctypeslib.as_array(C.cast(lists.offsets, C.POINTER(C.c_int64)), shape=(n + 1,)).copy()
+    tot = int(off[-1])
+    ids = (np.ctypeslib.as_array(C.cast(lists.ids, C.POINTER(C.c_int64)), shape=(tot,)).copy()
+           if tot else np.zeros(0, np.int64))
+    lib().bmj_id_lists_free(C.byref(lists))
+    return [ids[off[k]:off[k + 1]] for k in range(n)]
+
+
+class Index:
+    """A resident index (bmj_index_create / bmj_index_destroy)."""
+
+    def __init__(self, offsets, tokens, b: int = 64, method: int = BMJ_XOR, validate: bool = True):
+        coll, keep = make_collection(offsets, tokens)
+        o = bmj_default_options()
+        o.b = int(b)
+        o.method = int(method)
+        o.validate = 1 if validate else 0
+        o.stream = _stream_of(None, coll.on_device)
+        h = C.c_void_p()
+        st = lib().bmj_index_create(C.byref(coll), C.byref(o), C.byref(h))
+        del keep
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_index_create")
+        self._h = h
+
+    def __len__(self):
+        return int(lib().bmj_index_size(self._h))
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().bmj_index_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, offsets, tokens, p, q):
+        """bmj_index_query: per-probe arrays of resident ids (ascending) and stats."""
+        coll, keep = make_collection(offsets, tokens)
+        pp = np.ascontiguousarray(p, dtype=np.uint32)
+        qq = np.ascontiguousarray(q, dtype=np.uint32)
+        out = bmj_id_lists()
+        st_ = bmj_serve_stats()
+        st = lib().bmj_index_query(self._h, C.byref(coll), _ptr(pp), _ptr(qq), C.byref(out),
+                                   C.byref(st_))
+        del keep
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_index_query")
+        return _take_id_lists(out), st_.as_dict()
+
+    def serve(self, offsets, tokens, arrival_s, p, q, n_slots: int = 4,
+              max_batch_queries: int = 4096, max_batch_window_pairs: int = 1 << 25,
+              want_results: bool = True):
+        """bmj_serve: (per-query ids or None, latency_ms array, stats dict)."""
+        coll, keep = make_collection(offsets, tokens)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        pp = np.ascontiguousarray(p, dtype=np.uint32)
+        qq = np.ascontiguousarray(q, dtype=np.uint32)
+        so = bmj_serve_options()
+        lib().bmj_default_serve_options(C.byref(so))
+        so.n_slots = int(n_slots)
+        so.max_batch_queries = int(max_batch_queries)
+        so.max_batch_window_pairs = int(max_batch_window_pairs)
+        lat = np.zeros(len(arr), np.float64)
+        out = bmj_id_lists()
+        st_ = bmj_serve_stats()
+        st = lib().bmj_serve(self._h, C.byref(coll), _ptr(arr), _ptr(pp), _ptr(qq), C.byref(so),
+                             C.byref(out) if want_results else None, _ptr(lat), C.byref(st_))
+        del keep
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_serve")
+        return (_take_id_lists(out) if want_results else None), lat, st_.as_dict()

@@ -1,0 +1,705 @@
+// serve.cu -- a resident index and probe queries with continuous batching.
+//
+// bmj_index_create keeps one collection resident on the device in size order
+// (sizes, sorted CSR, bitmaps).  A probe set x with threshold p/q is an
+// RS-join with |R| = 1 (Eq. 1): its candidates are the resident sets inside
+// both sides of the length window (Table 2: ceil(p|x|/q) <= |s| <= floor(q|x|/p)),
+// filtered by the Eq. 2 bound and verified exactly.
+//
+// A batch of probes runs as:
+//   probe bitmaps + windows -> work items (probe, column chunk) -> filter ->
+//   verification -> sort by (probe, id) -> per-probe id lists.
+// Every batch has its own slot (stream, pinned staging, fixed device buffers),
+// so several batches are in flight at once and overlap on the device.
+//
+// bmj_serve runs an arrival stream through the slots: queries that have
+// arrived are admitted into a free slot while the batch's exact window-pair
+// count (from a host histogram of resident sizes) fits the slot's buffers,
+// which bounds every buffer of the batch (survivors and results cannot
+// exceed window pairs).  Latency of a query = completion - arrival.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "host_util.cuh"
+
+struct bmj_index {
+    int device = 0;
+    int b = 64, W = 1, method = BMJ_XOR;
+    int64_t n = 0;
+    int max_size = 0;
+    uint32_t *ssz = nullptr;  // n + 4
+    uint32_t *perm = nullptr;
+    int64_t *soff = nullptr;  // n + 1
+    int32_t *stok = nullptr;
+    uint64_t *bm = nullptr;   // (n + 4) * W
+    std::vector<int64_t> size_cum;  // size_cum[s] = resident sets with size < s
+};
+
+namespace bmj {
+namespace {
+
+constexpr unsigned kFullQ = 0xffffffffu;
+constexpr int kQueryChunk = 1024;
+
+__device__ __forceinline__ int64_t lb_sizes(const uint32_t *a, int64_t n, uint64_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((uint64_t)a[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Per probe: its window [lo, hi) of resident sorted positions and its number
+// of column chunks.
+__global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
+                                const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
+                                const uint32_t *__restrict__ ssz, int64_t n,
+                                int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
+                                int64_t *__restrict__ items) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nq; x += stride) {
+        const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
+        const uint64_t p = pp[x], q = pq[x];
+        const uint64_t low = (p * sx + q - 1) / q;   // ceil(p|x|/q)
+        const uint64_t high = (q * sx) / p;          // floor(q|x|/p)
+        const int64_t lo = lb_sizes(ssz, n, low);
+        const int64_t hi = lb_sizes(ssz, n, high + 1);
+        wlo[x] = lo;
+        whi[x] = hi;
+        items[x] = hi > lo ? (hi - lo + kQueryChunk - 1) / kQueryChunk : 0;
+    }
+}
+
+// One warp per work item (probe, chunk of columns); lanes take consecutive
+// columns.  Survive iff floor((S - h)/2) * (p+q) >= p * S (Eq. 2, Table 1).
+__global__ void __launch_bounds__(256)
+    k_query_filter(const uint64_t *__restrict__ pbm, const int64_t *__restrict__ poff,
+                   const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
+                   const int64_t *__restrict__ wlo, const int64_t *__restrict__ whi,
+                   const int64_t *__restrict__ item_off, int64_t nq,
+                   const uint64_t *__restrict__ bm, const uint32_t *__restrict__ ssz, int W,
+                   uint2 *__restrict__ queue, unsigned long long *__restrict__ qcount, int64_t qcap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_items = item_off[nq];
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items;
+         item += warps) {
+        int64_t lo = 0, hi = nq;  // probe x with item_off[x] <= item < item_off[x+1]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (item_off[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int64_t x = lo;
+        const int64_t c0 = wlo[x] + (item - item_off[x]) * kQueryChunk;
+        const int64_t c1 = min(c0 + (int64_t)kQueryChunk, whi[x]);
+        const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
+        const uint64_t p = pp[x], pq2 = (uint64_t)pp[x] + pq[x];
+        for (int64_t j0 = c0; j0 < c1; j0 += 32) {
+            const int64_t j = j0 + lane;
+            bool sv = false;
+            if (j < c1) {
+                int h = 0;
+                for (int w = 0; w < W; w++) h += __popcll(pbm[x * W + w] ^ bm[j * W + w]);
+                const uint64_t S = sx + ssz[j];
+                const uint64_t ub = (S - (uint64_t)h) >> 1;
+                sv = ub * pq2 >= p * S;
+            }
+            const unsigned ball = __ballot_sync(kFullQ, sv);
+            if (ball) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(qcount, (unsigned long long)__popc(ball));
+                base = __shfl_sync(kFullQ, base, 0);
+                const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
+                if (sv && pos < (unsigned long long)qcap)
+                    queue[pos] = make_uint2((uint32_t)x, (uint32_t)j);
+            }
+        }
+    }
+}
+
+// Exact verification; similar pairs become keys (probe << 32) | original id.
+__global__ void __launch_bounds__(256)
+    k_query_verify(const uint2 *__restrict__ queue, const unsigned long long *__restrict__ qcount,
+                   int64_t qcap, const int64_t *__restrict__ poff, const int32_t *__restrict__ ptok,
+                   const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
+                   const int64_t *__restrict__ soff, const int32_t *__restrict__ stok,
+                   const uint32_t *__restrict__ ssz, const uint32_t *__restrict__ perm,
+                   uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_surv = min((int64_t)*qcount, qcap);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int64_t base = gw * 32; base < n_surv; base += warps * 32) {
+        const int64_t idx = base + lane;
+        bool similar = false;
+        uint64_t key = 0;
+        if (idx < n_surv) {
+            const uint2 pr = queue[idx];
+            const int32_t *x = ptok + poff[pr.x];
+            const int na = (int)(poff[pr.x + 1] - poff[pr.x]);
+            const int32_t *y = stok + soff[pr.y];
+            const int nb = (int)ssz[pr.y];
+            const uint64_t p = pp[pr.x], d = (uint64_t)pp[pr.x] + pq[pr.x];
+            const int nd = (int)((p * (uint64_t)(na + nb) + d - 1) / d);
+            int a = 0, b = 0, o = 0;
+            while (a < na && b < nb) {
+                if (o + min(na - a, nb - b) < nd) break;
+                const int32_t xa = x[a], yb = y[b];
+                o += (xa == yb);
+                a += (xa <= yb);
+                b += (yb <= xa);
+                if (o >= nd) break;
+            }
+            similar = o >= nd;
+            if (similar) key = ((uint64_t)pr.x << 32) | perm[pr.y];
+        }
+        const unsigned ball = __ballot_sync(kFullQ, similar);
+        if (ball) {
+            unsigned long long off = 0;
+            if (lane == 0) off = atomicAdd(rcount, (unsigned long long)__popc(ball));
+            off = __shfl_sync(kFullQ, off, 0);
+            if (similar) keys[off + __popc(ball & ((1u << lane) - 1u))] = key;
+        }
+    }
+}
+
+__global__ void k_query_bounds(const uint64_t *__restrict__ keys, int64_t n, int64_t nq,
+                               int64_t *__restrict__ bounds) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x <= nq; x += stride) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)(keys[mid] >> 32) < x) lo = mid + 1;
+            else hi = mid;
+        }
+        bounds[x] = lo;
+    }
+}
+
+unsigned grid_q(int64_t n, int threads, int64_t cap = 148 * 16) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ----------------------------------------------------------------------------
+// A slot: everything one in-flight batch needs, allocated once.
+// ----------------------------------------------------------------------------
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    int64_t q_cap = 0, tok_cap = 0, pair_cap = 0;
+    // pinned host staging
+    int64_t *h_off = nullptr;
+    int32_t *h_tok = nullptr;
+    uint32_t *h_p = nullptr, *h_q = nullptr;
+    unsigned long long *h_ctr = nullptr;  // [0] survivors, [1] results
+    uint64_t *h_keys = nullptr;
+    int64_t *h_bounds = nullptr;
+    // device
+    int64_t *d_off = nullptr;
+    int32_t *d_tok = nullptr;
+    uint32_t *d_p = nullptr, *d_q = nullptr;
+    uint64_t *d_pbm = nullptr;
+    int64_t *d_lo = nullptr, *d_hi = nullptr, *d_items = nullptr;
+    uint2 *d_queue = nullptr;
+    uint64_t *d_keys = nullptr, *d_sorted = nullptr;
+    int64_t *d_bounds = nullptr;
+    unsigned long long *d_ctr = nullptr;
+    // in flight
+    int phase = 0;  // 0 free, 1 filter+verify running, 2 sort+copy running
+    std::vector<int64_t> ids;  // query ids of the batch
+    int64_t nq = 0, ntok = 0;
+};
+
+void free_slot(Slot &s) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    cudaFreeHost(s.h_off);
+    cudaFreeHost(s.h_tok);
+    cudaFreeHost(s.h_p);
+    cudaFreeHost(s.h_q);
+    cudaFreeHost(s.h_ctr);
+    cudaFreeHost(s.h_keys);
+    cudaFreeHost(s.h_bounds);
+    cudaFree(s.d_off);
+    cudaFree(s.d_tok);
+    cudaFree(s.d_p);
+    cudaFree(s.d_q);
+    cudaFree(s.d_pbm);
+    cudaFree(s.d_lo);
+    cudaFree(s.d_hi);
+    cudaFree(s.d_items);
+    cudaFree(s.d_queue);
+    cudaFree(s.d_keys);
+    cudaFree(s.d_sorted);
+    cudaFree(s.d_bounds);
+    cudaFree(s.d_ctr);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    cudaGetLastError();
+    s = Slot();
+}
+
+int alloc_slot(Slot &s, int64_t q_cap, int64_t tok_cap, int64_t pair_cap, int W) {
+    s.q_cap = q_cap;
+    s.tok_cap = tok_cap;
+    s.pair_cap = pair_cap;
+    bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess &&
+              cudaMallocHost(&s.h_off, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_tok, std::max<int64_t>(tok_cap, 1) * sizeof(int32_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_p, q_cap * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_q, q_cap * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_ctr, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMallocHost(&s.h_keys, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_bounds, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_off, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_tok, std::max<int64_t>(tok_cap, 1) * sizeof(int32_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_p, q_cap * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_q, q_cap * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_pbm, q_cap * W * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_lo, q_cap * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_hi, q_cap * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_items, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_queue, pair_cap * sizeof(uint2)) == cudaSuccess &&
+              cudaMalloc(&s.d_keys, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_sorted, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_bounds, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_ctr, 2 * sizeof(unsigned long long)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_slot(s);
+        return BMJ_ERR_OOM;
+    }
+    return BMJ_OK;
+}
+
+// Exact number of resident sets inside the window of a probe of size sx.
+int64_t window_of(const bmj_index *idx, int64_t sx, uint32_t p, uint32_t q) {
+    const int64_t low = ((int64_t)p * sx + q - 1) / q;
+    const int64_t high = ((int64_t)q * sx) / p;
+    const int64_t ms = (int64_t)idx->size_cum.size() - 1;
+    auto cum = [&](int64_t s) { return idx->size_cum[(size_t)std::min(std::max<int64_t>(s, 0), ms)]; };
+    return std::max<int64_t>(0, cum(high + 1) - cum(low));
+}
+
+// Phase 1 of a staged batch: copy in, bitmaps, windows, filter, verification,
+// result count back to pinned memory.
+int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
+    cudaStream_t st = s.stream;
+    const int64_t nq = s.nq;
+    BMJ_CHECK(cudaMemcpyAsync(s.d_off, s.h_off, (nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (s.ntok)
+        BMJ_CHECK(cudaMemcpyAsync(s.d_tok, s.h_tok, s.ntok * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    BMJ_CHECK(cudaMemcpyAsync(s.d_p, s.h_p, nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    BMJ_CHECK(cudaMemcpyAsync(s.d_q, s.h_q, nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    BMJ_CHECK(cudaMemsetAsync(s.d_ctr, 0, 2 * sizeof(unsigned long long), st));
+    int rc = launch_gather_build(nullptr, s.d_off, s.d_tok, nullptr, nullptr, s.d_pbm, nq, idx->b,
+                                 idx->method, st);
+    if (rc) return rc;
+    BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q, idx->ssz,
+               idx->n, s.d_lo, s.d_hi, s.d_items);
+    Arena A(st);
+    rc = exclusive_scan_i64(s.d_items, s.d_items, nq, s.d_items + nq, A, st);
+    if (rc) return rc;
+    BMJ_LAUNCH(k_query_filter, (unsigned)(sms * 8), 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
+               s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],
+               s.pair_cap);
+    BMJ_LAUNCH(k_query_verify, (unsigned)(sms * 4), 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
+               s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
+               &s.d_ctr[1]);
+    BMJ_CHECK(cudaMemcpyAsync(s.h_ctr, s.d_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    BMJ_CHECK(cudaEventRecord(s.done, st));
+    A.release();
+    return BMJ_OK;
+}
+
+// Phase 2: sort the results by (probe, id), per-probe bounds, copy out.
+int launch_phase2(Slot &s) {
+    cudaStream_t st = s.stream;
+    const int64_t nres = (int64_t)s.h_ctr[1];
+    const int64_t nq = s.nq;
+    Arena A(st);
+    if (nres > 0) {
+        const int pbits = nq > 1 ? bit_length((uint64_t)(nq - 1)) : 1;
+        int rc = radix_sort_u64(s.d_keys, s.d_sorted, nres, 32 + pbits, A, st);
+        if (rc) return rc;
+        BMJ_LAUNCH(k_query_bounds, grid_q(nq + 1, 128), 128, 0, st, s.d_sorted, nres, nq, s.d_bounds);
+        BMJ_CHECK(cudaMemcpyAsync(s.h_keys, s.d_sorted, nres * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        BMJ_CHECK(cudaMemcpyAsync(s.h_bounds, s.d_bounds, (nq + 1) * sizeof(int64_t),
+                                  cudaMemcpyDeviceToHost, st));
+    } else {
+        memset(s.h_bounds, 0, (nq + 1) * sizeof(int64_t));
+    }
+    BMJ_CHECK(cudaEventRecord(s.done, st));
+    A.release();
+    return BMJ_OK;
+}
+
+// Stages queries ids[0..m) of a host query collection into a slot.
+void stage(Slot &s, const bmj_collection *qc, const uint32_t *p, const uint32_t *q,
+           const int64_t *ids, int64_t m) {
+    s.ids.assign(ids, ids + m);
+    s.nq = m;
+    s.h_off[0] = 0;
+    int64_t t = 0;
+    for (int64_t k = 0; k < m; k++) {
+        const int64_t x = ids[k];
+        const int64_t a = qc->offsets[x], b = qc->offsets[x + 1];
+        memcpy(s.h_tok + t, qc->tokens + a, (b - a) * sizeof(int32_t));
+        t += b - a;
+        s.h_off[k + 1] = t;
+        s.h_p[k] = p[x];
+        s.h_q[k] = q[x];
+    }
+    s.ntok = t;
+}
+
+}  // namespace
+}  // namespace bmj
+
+// ============================================================================
+// C ABI
+// ============================================================================
+using namespace bmj;
+
+extern "C" int bmj_index_create(const bmj_collection *coll, const bmj_options *opt,
+                                bmj_index **out) {
+    if (!out) return BMJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!coll || coll->n_sets < 0 || !coll->offsets || (coll->n_sets > 0 && !coll->tokens))
+        return BMJ_ERR_INVALID_ARG;
+    if (coll->n_sets > 0x7fffffffLL) return BMJ_ERR_TOO_LARGE;
+    bmj_options o;
+    if (opt) o = *opt;
+    else bmj_default_options(&o);
+    if (!valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
+    if (o.method != BMJ_XOR && o.method != BMJ_SET && o.method != BMJ_NEXT) return BMJ_ERR_INVALID_ARG;
+    bmj_index *idx = new (std::nothrow) bmj_index();
+    if (!idx) return BMJ_ERR_OOM;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    int st = BMJ_OK;
+    {
+        Arena A(s);
+        DevColl d;
+        st = stage_collection(coll, A, s, &d);
+        uint32_t *sizes = nullptr, *ids = nullptr;
+        int max_size = 0;
+        if (!st && d.n > 0) st = validate(d, o.validate != 0, A, s, &sizes, &ids, &max_size);
+        if (!st) {
+            cudaGetDevice(&idx->device);
+            idx->b = o.b;
+            idx->W = o.b / 64;
+            idx->method = o.method;
+            idx->n = d.n;
+            idx->max_size = max_size;
+            const int64_t n = d.n;
+            bool ok = cudaMalloc(&idx->ssz, (n + 4) * sizeof(uint32_t)) == cudaSuccess &&
+                      cudaMalloc(&idx->perm, std::max<int64_t>(n, 1) * sizeof(uint32_t)) == cudaSuccess &&
+                      cudaMalloc(&idx->soff, (n + 1) * sizeof(int64_t)) == cudaSuccess &&
+                      cudaMalloc(&idx->stok, std::max<int64_t>(d.ntok, 1) * sizeof(int32_t)) == cudaSuccess &&
+                      cudaMalloc(&idx->bm, (n + 4) * idx->W * sizeof(uint64_t)) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                st = BMJ_ERR_OOM;
+            }
+            if (!st && n > 0) {
+                if (cudaMemsetAsync(idx->ssz + n, 0, 4 * sizeof(uint32_t), s) != cudaSuccess)
+                    st = BMJ_ERR_CUDA;
+                if (!st) st = radix_sort_u32_pairs(sizes, ids, idx->ssz, idx->perm, n,
+                                          std::max(1, bit_length((uint64_t)max_size)), A, s);
+                if (!st) st = launch_widen(idx->ssz, idx->soff, n, s);
+                if (!st) st = exclusive_scan_i64(idx->soff, idx->soff, n, idx->soff + n, A, s);
+                if (!st)
+                    st = launch_gather_build(idx->perm, d.off, d.tok, idx->soff, idx->stok, idx->bm,
+                                             n, idx->b, idx->method, s);
+                if (!st) {
+                    std::vector<uint32_t> h(n);
+                    if (cudaMemcpyAsync(h.data(), idx->ssz, n * sizeof(uint32_t),
+                                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess) {
+                        st = BMJ_ERR_CUDA;
+                    } else {
+                        idx->size_cum.assign((size_t)max_size + 2, 0);
+                        for (int64_t i = 0; i < n; i++) idx->size_cum[h[i] + 1]++;
+                        for (size_t k = 1; k < idx->size_cum.size(); k++)
+                            idx->size_cum[k] += idx->size_cum[k - 1];
+                    }
+                }
+            } else if (!st) {
+                idx->size_cum.assign(2, 0);
+                cudaMemsetAsync(idx->soff, 0, sizeof(int64_t), s);
+            }
+        }
+        A.release();
+        if (cudaStreamSynchronize(s) != cudaSuccess && !st) st = BMJ_ERR_CUDA;
+    }
+    if (st) {
+        bmj_index_destroy(idx);
+        cudaGetLastError();
+        return st;
+    }
+    *out = idx;
+    return BMJ_OK;
+}
+
+extern "C" void bmj_index_destroy(bmj_index *idx) {
+    if (!idx) return;
+    cudaFree(idx->ssz);
+    cudaFree(idx->perm);
+    cudaFree(idx->soff);
+    cudaFree(idx->stok);
+    cudaFree(idx->bm);
+    cudaGetLastError();
+    delete idx;
+}
+
+extern "C" int64_t bmj_index_size(const bmj_index *idx) { return idx ? idx->n : -1; }
+
+static int check_queries(const bmj_collection *qc, const uint32_t *p, const uint32_t *q) {
+    if (!qc || qc->on_device || qc->n_sets < 0 || !qc->offsets || (qc->n_sets > 0 && (!qc->tokens || !p || !q)))
+        return BMJ_ERR_INVALID_ARG;
+    if (qc->offsets[0] != 0) return BMJ_ERR_UNSORTED;
+    for (int64_t x = 0; x < qc->n_sets; x++) {
+        if (p[x] == 0 || q[x] == 0 || p[x] > q[x]) return BMJ_ERR_INVALID_ARG;
+        const int64_t a = qc->offsets[x], b = qc->offsets[x + 1];
+        if (b < a) return BMJ_ERR_UNSORTED;
+        if (b == a) return BMJ_ERR_EMPTY_SET;
+        if (qc->tokens[a] < 0) return BMJ_ERR_NEG_TOKEN;
+        for (int64_t k = a + 1; k < b; k++)
+            if (qc->tokens[k] <= qc->tokens[k - 1]) return BMJ_ERR_UNSORTED;
+    }
+    return BMJ_OK;
+}
+
+static void id_lists_free_impl(bmj_id_lists *l) {
+    if (!l) return;
+    free(l->offsets);
+    free(l->ids);
+    l->offsets = nullptr;
+    l->ids = nullptr;
+    l->n_queries = 0;
+}
+
+extern "C" void bmj_id_lists_free(bmj_id_lists *lists) { id_lists_free_impl(lists); }
+
+// Runs queries through the slots.  arrival_s == NULL: everything is available
+// at once (a plain batched query).  Results are written into *out (optional)
+// and per-query latency into latency_ms (optional).
+static int serve_impl(bmj_index *idx, const bmj_collection *qc, const double *arrival_s,
+                      const uint32_t *p, const uint32_t *q, const bmj_serve_options &so,
+                      bmj_id_lists *out, double *latency_ms, bmj_serve_stats *stats) {
+    using clk = std::chrono::steady_clock;
+    const int64_t Q = qc->n_sets;
+    int dev = 0;
+    BMJ_CHECK(cudaGetDevice(&dev));
+    const int sms = num_sms(dev);
+    const int n_slots = std::max(1, so.n_slots);
+    int64_t max_q = so.max_batch_queries > 0 ? so.max_batch_queries : 4096;
+    int64_t pair_budget = so.max_batch_window_pairs > 0 ? so.max_batch_window_pairs : ((int64_t)1 << 25);
+    int64_t max_tok = 0, max_win = 0;
+    std::vector<int64_t> win(Q);
+    for (int64_t x = 0; x < Q; x++) {
+        const int64_t sx = qc->offsets[x + 1] - qc->offsets[x];
+        max_tok = std::max(max_tok, sx);
+        win[x] = window_of(idx, sx, p[x], q[x]);
+        max_win = std::max(max_win, win[x]);
+    }
+    // A single query always fits a slot on its own.
+    pair_budget = std::max(pair_budget, std::max<int64_t>(max_win, 1));
+    const int64_t tok_cap = max_q * std::max<int64_t>(max_tok, 1);
+    std::vector<Slot> slots(n_slots);
+    for (auto &s : slots) {
+        int rc = alloc_slot(s, max_q, tok_cap, pair_budget, idx->W);
+        if (rc) {
+            for (auto &t : slots) free_slot(t);
+            return rc;
+        }
+    }
+    std::vector<int64_t> counts(Q, 0);
+    std::vector<std::vector<int64_t>> per_q(out ? Q : 0);
+    std::vector<double> lat(Q, 0.0);
+    int64_t next = 0, completed = 0, batches = 0, total_window = 0, total_surv = 0, total_res = 0;
+    std::vector<int64_t> pending;
+    size_t pend_head = 0;
+    int rc = BMJ_OK;
+    const auto t0 = clk::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    while (completed < Q && !rc) {
+        const double now = now_s();
+        while (next < Q && (!arrival_s || arrival_s[next] <= now)) pending.push_back(next++);
+        bool progressed = false;
+        // 1. finished phases
+        for (auto &s : slots) {
+            if (s.phase == 0) continue;
+            const cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess) {
+                rc = status_of(e);
+                break;
+            }
+            progressed = true;
+            if (s.phase == 1) {
+                total_surv += (int64_t)s.h_ctr[0];
+                total_res += (int64_t)s.h_ctr[1];
+                rc = launch_phase2(s);
+                s.phase = 2;
+            } else {
+                const double t_done = now_s();
+                for (int64_t k = 0; k < s.nq; k++) {
+                    const int64_t x = s.ids[k];
+                    lat[x] = (t_done - (arrival_s ? arrival_s[x] : 0.0)) * 1e3;
+                    const int64_t lo = s.h_bounds[k], hi = s.h_bounds[k + 1];
+                    counts[x] = hi - lo;
+                    if (out) {
+                        per_q[x].resize(hi - lo);
+                        for (int64_t r = lo; r < hi; r++)
+                            per_q[x][r - lo] = (int64_t)(s.h_keys[r] & 0xffffffffu);
+                    }
+                }
+                completed += s.nq;
+                s.phase = 0;
+            }
+        }
+        if (rc) break;
+        // 2. admission: arrived queries into free slots, bounded by the slot's
+        //    query, token and window-pair capacities.
+        for (auto &s : slots) {
+            if (pend_head >= pending.size()) break;
+            if (s.phase != 0) continue;
+            std::vector<int64_t> take;
+            int64_t w = 0, t = 0;
+            while (pend_head < pending.size() && (int64_t)take.size() < max_q) {
+                const int64_t x = pending[pend_head];
+                const int64_t sx = qc->offsets[x + 1] - qc->offsets[x];
+                if (!take.empty() && (w + win[x] > pair_budget || t + sx > tok_cap)) break;
+                take.push_back(x);
+                w += win[x];
+                t += sx;
+                pend_head++;
+            }
+            stage(s, qc, p, q, take.data(), (int64_t)take.size());
+            total_window += w;
+            rc = launch_phase1(idx, s, sms);
+            if (rc) break;
+            s.phase = 1;
+            batches++;
+            progressed = true;
+        }
+        if (!progressed) {
+            if (pend_head >= pending.size() && next < Q && arrival_s) {
+                const double wait = arrival_s[next] - now_s();
+                if (wait > 50e-6) std::this_thread::sleep_for(std::chrono::microseconds(20));
+            } else {
+                std::this_thread::yield();
+            }
+        }
+    }
+    const double wall = now_s();
+    for (auto &s : slots) free_slot(s);
+    if (rc) return rc;
+    if (out) {
+        out->n_queries = Q;
+        out->offsets = (int64_t *)malloc((Q + 1) * sizeof(int64_t));
+        int64_t tot = 0;
+        for (int64_t x = 0; x < Q; x++) tot += counts[x];
+        out->ids = (int64_t *)malloc(std::max<int64_t>(tot, 1) * sizeof(int64_t));
+        if (!out->offsets || !out->ids) {
+            id_lists_free_impl(out);
+            return BMJ_ERR_OOM;
+        }
+        out->offsets[0] = 0;
+        for (int64_t x = 0; x < Q; x++) {
+            out->offsets[x + 1] = out->offsets[x] + counts[x];
+            if (counts[x])
+                memcpy(out->ids + out->offsets[x], per_q[x].data(), counts[x] * sizeof(int64_t));
+        }
+    }
+    if (latency_ms) memcpy(latency_ms, lat.data(), Q * sizeof(double));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->n_queries = Q;
+        stats->batches = batches;
+        stats->window_pairs = total_window;
+        stats->survivors = total_surv;
+        stats->results = total_res;
+        stats->wall_s = wall;
+        std::vector<double> sorted = lat;
+        std::sort(sorted.begin(), sorted.end());
+        auto pct = [&](double f) {
+            if (sorted.empty()) return 0.0;
+            size_t k = (size_t)std::min<double>((double)sorted.size() - 1, f * (double)sorted.size());
+            return sorted[k];
+        };
+        stats->p50_ms = pct(0.50);
+        stats->p99_ms = pct(0.99);
+        stats->max_ms = sorted.empty() ? 0.0 : sorted.back();
+        stats->qps = wall > 0 ? (double)Q / wall : 0.0;
+    }
+    return BMJ_OK;
+}
+
+extern "C" void bmj_default_serve_options(bmj_serve_options *so) {
+    if (!so) return;
+    memset(so, 0, sizeof(*so));
+    so->n_slots = 4;
+    so->max_batch_queries = 4096;
+    so->max_batch_window_pairs = (int64_t)1 << 25;
+}
+
+extern "C" int bmj_index_query(bmj_index *idx, const bmj_collection *probes, const uint32_t *p,
+                               const uint32_t *q, bmj_id_lists *out, bmj_serve_stats *stats) {
+    if (!idx || !out) return BMJ_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    int st = check_queries(probes, p, q);
+    if (st) return st;
+    bmj_serve_options so;
+    bmj_default_serve_options(&so);
+    so.n_slots = 1;
+    so.max_batch_queries = std::max<int64_t>(1, std::min<int64_t>(probes->n_sets, 1 << 16));
+    try {
+        st = serve_impl(idx, probes, nullptr, p, q, so, out, nullptr, stats);
+    } catch (...) {
+        st = BMJ_ERR_OOM;
+    }
+    if (st) {
+        id_lists_free_impl(out);
+        cudaGetLastError();
+    }
+    return st;
+}
+
+extern "C" int bmj_serve(bmj_index *idx, const bmj_collection *queries, const double *arrival_s,
+                         const uint32_t *p, const uint32_t *q, const bmj_serve_options *opt,
+                         bmj_id_lists *out, double *latency_ms, bmj_serve_stats *stats) {
+    if (!idx || !arrival_s) return BMJ_ERR_INVALID_ARG;
+    if (out) memset(out, 0, sizeof(*out));
+    int st = check_queries(queries, p, q);
+    if (st) return st;
+    for (int64_t x = 1; x < queries->n_sets; x++)
+        if (arrival_s[x] < arrival_s[x - 1]) return BMJ_ERR_INVALID_ARG;
+    bmj_serve_options so;
+    if (opt) so = *opt;
+    else bmj_default_serve_options(&so);
+    if (so.n_slots < 1 || so.max_batch_queries < 0 || so.max_batch_window_pairs < 0)
+        return BMJ_ERR_INVALID_ARG;
+    try {
+        st = serve_impl(idx, queries, arrival_s, p, q, so, out, latency_ms, stats);
+    } catch (...) {
+        st = BMJ_ERR_OOM;
+    }
+    if (st) {
+        if (out) id_lists_free_impl(out);
+        cudaGetLastError();
+    }
+    return st;
+}

@@ -1,0 +1,95 @@
+"""Resident index and served probe queries against the oracle."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_07295_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1711_07295_b300 import _bmj  # noqa: E402
+
+
+def small_setup(seed=0, n=20_000, nq=400):
+    spec = I.CollectionSpec(n, 3_000, 1.1, ("lognormal", 2.3, 0.6, 1, 200), seed=seed,
+                            planted_frac=0.05)
+    off, tok = I.gen_collection(spec)
+    qs = I.QuerySpec(n_queries=nq, rate_qps=50_000.0, size_lo=2, size_hi=60, seed=seed + 1)
+    arr, qoff, qtok, p, q = I.gen_queries(qs, spec, off, tok)
+    return off, tok, arr, qoff, qtok, p, q
+
+
+@pytest.mark.parametrize("b", [64, 128])
+def test_index_query_matches_oracle(b):
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=b)
+    idx = _bmj.Index(torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda(), b=b)
+    assert len(idx) == len(off) - 1
+    res, st = idx.query(qoff, qtok, p, q)
+    assert st["n_queries"] == len(p) and st["batches"] == 1
+    nonempty = 0
+    for x in range(len(p)):
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
+        assert np.array_equal(res[x], want), x
+        nonempty += len(want) > 0
+    assert nonempty > 50
+    idx.close()
+
+
+def test_each_query_same_alone_and_in_the_mix():
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=3, nq=300)
+    idx = _bmj.Index(off, tok, b=64)
+    mixed, lat, st = idx.serve(qoff, qtok, arr, p, q, n_slots=3, max_batch_queries=64)
+    assert st["n_queries"] == len(p) and st["batches"] >= 2
+    assert np.all(lat > 0) and st["p99_ms"] >= st["p50_ms"] > 0
+    tight, _, st2 = idx.serve(qoff, qtok, arr, p, q, n_slots=2, max_batch_queries=5,
+                              max_batch_window_pairs=1)
+    assert st2["batches"] > st["batches"]
+    for x in range(0, len(p), 7):
+        alone, _ = idx.query(qoff[x:x + 2] - qoff[x], qtok[qoff[x]:qoff[x + 1]], p[x:x + 1], q[x:x + 1])
+        assert np.array_equal(alone[0], mixed[x]) and np.array_equal(alone[0], tight[x]), x
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
+        assert np.array_equal(mixed[x], want)
+    idx.close()
+
+
+def test_invalid_probes_and_empty_batch():
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=5, n=2000, nq=10)
+    idx = _bmj.Index(off, tok)
+    res, st = idx.query(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.uint32),
+                        np.zeros(0, np.uint32))
+    assert res == [] and st["n_queries"] == 0
+    bad = qtok.copy()
+    a = int(qoff[0])
+    if qoff[1] - qoff[0] >= 2:
+        bad[a], bad[a + 1] = bad[a + 1], bad[a]
+        with pytest.raises(_bmj.BmjError) as e:
+            idx.query(qoff, bad, p, q)
+        assert e.value.status == _bmj.BMJ_ERR_UNSORTED
+    with pytest.raises(_bmj.BmjError) as e:
+        idx.query(qoff, qtok, q, p if np.any(p < q) else p)   # p > q somewhere
+    assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
+    idx.close()
+
+
+def test_full_served_workload_sampled():
+    # 2,000,000 resident sets (Zipf 1.1 over 300,000, lognormal(2.3, 0.6)); a Poisson
+    # stream at 20,000 queries/s of probes of size 2..300 (half edited resident copies).
+    spec = I.spec_resident_2m()
+    off_d, tok_d = I.gen_collection_device(spec)
+    off, tok = off_d.cpu().numpy(), tok_d.cpu().numpy()
+    qs = I.QuerySpec(n_queries=4000)
+    arr, qoff, qtok, p, q = I.gen_queries(qs, spec, off, tok)
+    idx = _bmj.Index(off_d, tok_d, b=64)
+    res, lat, st = idx.serve(qoff, qtok, arr, p, q)
+    assert st["n_queries"] == 4000 and st["p99_ms"] > 0
+    rng = np.random.default_rng(0)
+    for x in rng.choice(4000, 24, replace=False):
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
+        assert np.array_equal(res[x], want), x
+    idx.close()
