@@ -132,18 +132,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def filter_source_digest() -> str:
+    """sha256[:16] of the sources the filter kernel is built from."""
+    h = hashlib.sha256()
+    for name in ("filter_core.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1711_07295_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic(b: int):
-    """DRAM bytes per filter launch from the committed ncu summary, if it was
-    taken on the current kernel source (None otherwise)."""
+    """DRAM bytes per filter launch (mean over one step's launches) from the
+    committed ncu summary, if it was taken on the current filter source."""
     path = os.path.join(ROOT, "profiles", f"filter_1m_b{b}.md")
-    src = os.path.join(ROOT, "paper_1711_07295_b300", "csrc", "kernels.cu")
     try:
         text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = filter_source_digest()
     except OSError:
         return None
-    m_hash = re.search(r"kernels\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
-    m_tr = re.search(r"dram bytes per full launch \(tau=1/2\):\s*([0-9.eE+]+)", text)
+    m_hash = re.search(r"filter source sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m_tr = re.search(r"dram bytes per launch, mean over one step:\s*([0-9.eE+]+)", text)
     if not m_hash or not m_tr or m_hash.group(1) != digest:
         return None
     return float(m_tr.group(1))
@@ -262,7 +270,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4),
                 "unit": "Tpopc32/s", "frac": round(achieved / peak, 4),
                 "traffic": profile_traffic(b),
-                "kernel": f"k_filter<W={b // 64}> (Bitmap Filter)",
+                "kernel": f"k_filter_tma<W={b // 64}> (Bitmap Filter, TMA-staged columns)",
                 "peak_derivation": f"{sms} SMs x {POPC_PER_CLK_PER_SM} POPC/clk/SM x "
                                    f"{max_mhz:.0f} MHz (max SM clock)",
                 "filter_pairs_per_s": round(window_per_step * args.steps / (filt_ms / 1e3)),

@@ -170,15 +170,17 @@ __global__ void k_batch_tiles(const uint32_t *__restrict__ ssz, const JobDesc *_
     }
 }
 
-// (job, local tile) of every tile of every job.
-__global__ void k_enumerate_tiles(const int64_t *__restrict__ job_tile0, int64_t n_jobs,
+// (job, local tile) of every tile of every job, jobs taken in the order
+// `order` (grouped by bitmap width) with first tiles job_tile0 in that order.
+__global__ void k_enumerate_tiles(const int64_t *__restrict__ job_tile0,
+                                  const int32_t *__restrict__ order, int64_t n_jobs,
                                   int64_t n_tiles, int32_t *__restrict__ tl_job,
                                   int64_t *__restrict__ tl_local) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
-        const int64_t k = last_le(job_tile0, n_jobs, t);
-        tl_job[t] = (int32_t)k;
-        tl_local[t] = t - job_tile0[k];
+        const int64_t pos = last_le(job_tile0, n_jobs, t);
+        tl_job[t] = order[pos];
+        tl_local[t] = t - job_tile0[pos];
     }
 }
 
@@ -191,8 +193,6 @@ struct BatchFilterArgs {
     const int64_t *tile_c0;
     const int64_t *tile_item_off;  // [n_tiles + 1]
     int64_t n_tiles;
-    const int64_t *n_items_dev;    // total work items (read on the device)
-    unsigned long long *item_counter;
     uint2 *queue;
     unsigned long long *qcount;
     unsigned long long *job_surv;  // per-job survivor counters
@@ -200,23 +200,23 @@ struct BatchFilterArgs {
     int *err;                      // set when a bounded wait on a copy gave up
 };
 
-// One persistent launch over the work items of every job.  Columns are staged
-// by TMA into a per-warp region sized for the widest case (b = 256).
-constexpr int kBatchCS = 128;
-constexpr int kBatchWarpBytes = ColStage<4, kBatchCS>::kWarpBytes;
-
-__global__ void __launch_bounds__(128) k_filter_batch(const BatchFilterArgs a) {
+// The Bitmap Filter over the work items of every job of one bitmap width:
+// tiles [t0, t1) (the jobs of that width are contiguous in the tile list),
+// items pulled from a per-class counter.  Columns are staged by TMA.
+template <int W, int R, int CS>
+__global__ void __launch_bounds__(128) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
+                                                         int64_t t1, unsigned long long *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     StageState stg;
-    init_stage(stg, smem + (threadIdx.x >> 5) * kBatchWarpBytes);
-    const int64_t n_items = *a.n_items_dev;
+    init_stage(stg, smem + (threadIdx.x >> 5) * ColStage<W, CS>::kWarpBytes);
+    const int64_t ibase = a.tile_item_off[t0], iend = a.tile_item_off[t1];
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
+        if (lane == 0) item = (unsigned long long)ibase + atomicAdd(counter, 1ull);
         item = __shfl_sync(kFullMask, item, 0);
-        if ((int64_t)item >= n_items) return;
-        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
+        if ((int64_t)item >= iend) return;
+        const int64_t t = t0 + find_tile(a.tile_item_off + t0, t1 - t0, item);
         const int32_t k = a.tile_job[t];
         const JobDesc jd = a.jobs[k];
         const int64_t chunk = (int64_t)item - a.tile_item_off[t];
@@ -225,27 +225,37 @@ __global__ void __launch_bounds__(128) k_filter_batch(const BatchFilterArgs a) {
         const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
-        const int32_t *lim = a.lim + jd.lim_off;
-        switch (jd.W) {
-            case 1:
-                filter_item_tma<1, kTmaR1, kBatchCS>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p,
-                                                     jd.q, sink, stg);
-                break;
-            case 2:
-                filter_item_tma<2, kTmaR2, kBatchCS>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p,
-                                                     jd.q, sink, stg);
-                break;
-            case 4:
-                filter_item_tma<4, kTmaR4, kBatchCS>(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p,
-                                                     jd.q, sink, stg);
-                break;
-            default:
-                filter_item_generic(jd.bm, a.ssz, lim, jd.end, i0, c0, c1, jd.p, jd.q, jd.W, sink);
-        }
+        filter_item_tma<W, R, CS>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, jd.p,
+                                  jd.q, sink, stg);
         if (!stg.ok) {
             if (lane == 0) atomicOr(a.err, 1);
             return;
         }
+    }
+}
+
+// Other widths: one row per lane, columns read from memory.
+__global__ void __launch_bounds__(256) k_filter_batch_generic(const BatchFilterArgs a, int64_t t0,
+                                                               int64_t t1,
+                                                               unsigned long long *counter) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ibase = a.tile_item_off[t0], iend = a.tile_item_off[t1];
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = (unsigned long long)ibase + atomicAdd(counter, 1ull);
+        item = __shfl_sync(kFullMask, item, 0);
+        if ((int64_t)item >= iend) return;
+        const int64_t t = t0 + find_tile(a.tile_item_off + t0, t1 - t0, item);
+        const int32_t k = a.tile_job[t];
+        const JobDesc jd = a.jobs[k];
+        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
+        const int64_t i0 = a.tile_i0[t];
+        const int64_t c0 = a.tile_c0[t] + chunk * jd.chunk_cols;
+        const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
+        const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
+        const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
+        filter_item_generic(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, jd.p, jd.q,
+                            jd.W, sink);
     }
 }
 
@@ -341,7 +351,9 @@ struct Plan {
     int64_t n_tiles = 0;
     int32_t *tile_job = nullptr;
     int64_t *tile_i0 = nullptr, *tile_c0 = nullptr, *tile_off = nullptr;
-    // counters: [0] item counter, [1] survivors, [2] results
+    // tile ranges of the width classes (b = 64, 128, 256, other), in tile order
+    int64_t class_t0[4] = {0, 0, 0, 0}, class_t1[4] = {0, 0, 0, 0};
+    // counters: [1] survivors, [2] results, [3 + c] item counter of class c
     unsigned long long *ctr = nullptr;
     unsigned long long *job_surv = nullptr;
     int *err = nullptr;
@@ -352,7 +364,8 @@ struct Plan {
 };
 
 int build_tiles(Plan &P, const std::vector<int32_t> &h_job, const std::vector<int64_t> &h_local,
-                bool enumerate_all, const std::vector<int64_t> &job_tile0, Arena &A, cudaStream_t s,
+                bool enumerate_all, const std::vector<int64_t> &job_tile0,
+                const std::vector<int32_t> &order, Arena &A, cudaStream_t s,
                 unsigned long long **tile_win_out) {
     const int64_t T = enumerate_all ? job_tile0.back() : (int64_t)h_job.size();
     P.n_tiles = T;
@@ -371,12 +384,16 @@ int build_tiles(Plan &P, const std::vector<int32_t> &h_job, const std::vector<in
     }
     if (enumerate_all) {
         int64_t *jt0 = nullptr;
+        int32_t *ord = nullptr;
         st = A.alloc(&jt0, job_tile0.size());
+        if (!st) st = A.alloc(&ord, order.size());
         if (st) return st;
         BMJ_CHECK(cudaMemcpyAsync(jt0, job_tile0.data(), job_tile0.size() * sizeof(int64_t),
                                   cudaMemcpyHostToDevice, s));
-        BMJ_LAUNCH(k_enumerate_tiles, grid_of(T, 256), 256, 0, s, jt0, (int64_t)job_tile0.size() - 1,
-                   T, tl_job, tl_local);
+        BMJ_CHECK(cudaMemcpyAsync(ord, order.data(), order.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, s));
+        BMJ_LAUNCH(k_enumerate_tiles, grid_of(T, 256), 256, 0, s, jt0, ord,
+                   (int64_t)job_tile0.size() - 1, T, tl_job, tl_local);
     } else {
         BMJ_CHECK(cudaMemcpyAsync(tl_job, h_job.data(), T * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         BMJ_CHECK(cudaMemcpyAsync(tl_local, h_local.data(), T * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -404,7 +421,23 @@ int upload_jobs(Plan &P, Arena &A, cudaStream_t s) {
     return BMJ_OK;
 }
 
-// Filter over the planned items into the plan's queue (cap may be 0: count only).
+int width_class(int W) { return W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3; }
+
+template <int W, int R, int CS>
+int launch_class(const BatchFilterArgs &fa, int64_t t0, int64_t t1, unsigned long long *counter,
+                 int sms, cudaStream_t s) {
+    const int smem = 4 * ColStage<W, CS>::kWarpBytes;
+    int per_sm = 0;
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_w<W, R, CS>, 128,
+                                                            smem));
+    if (per_sm < 1) per_sm = 1;
+    BMJ_LAUNCH((k_filter_batch_w<W, R, CS>), (unsigned)(sms * per_sm), 128, smem, s, fa, t0, t1,
+               counter);
+    return BMJ_OK;
+}
+
+// Filter over the planned items into the plan's queue (cap may be 0: count
+// only): one persistent launch per width class present.
 int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
     BatchFilterArgs fa;
     fa.jobs = P.jobs_dev;
@@ -415,25 +448,38 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
     fa.tile_c0 = P.tile_c0;
     fa.tile_item_off = P.tile_off;
     fa.n_tiles = P.n_tiles;
-    fa.n_items_dev = P.tile_off + P.n_tiles;
-    fa.item_counter = &P.ctr[0];
     fa.queue = P.queue;
     fa.qcount = &P.ctr[1];
     fa.job_surv = P.job_surv;
     fa.qcap = P.qcap;
     fa.err = P.err;
-    const int smem = 4 * kBatchWarpBytes;
-    int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch, 128, smem));
-    if (per_sm < 1) per_sm = 1;
-    BMJ_LAUNCH(k_filter_batch, (unsigned)(sms * per_sm), 128, smem, s, fa);
+    for (int c = 0; c < 4; c++) {
+        const int64_t t0 = P.class_t0[c], t1 = P.class_t1[c];
+        if (t1 <= t0) continue;
+        unsigned long long *counter = &P.ctr[3 + c];
+        int st = BMJ_OK;
+        switch (c) {
+            case 0: st = launch_class<1, kTmaR1, 256>(fa, t0, t1, counter, sms, s); break;
+            case 1: st = launch_class<2, kTmaR2, 256>(fa, t0, t1, counter, sms, s); break;
+            case 2: st = launch_class<4, kTmaR4, 128>(fa, t0, t1, counter, sms, s); break;
+            default: {
+                int per_sm = 0;
+                BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_generic,
+                                                                        256, 0));
+                if (per_sm < 1) per_sm = 1;
+                BMJ_LAUNCH(k_filter_batch_generic, (unsigned)(sms * per_sm), 256, 0, s, fa, t0, t1,
+                           counter);
+            }
+        }
+        if (st) return st;
+    }
     return BMJ_OK;
 }
 
 // The execute stage: clear counters, filter every job, verify every survivor.
 // No allocation and no host read: capturable into a CUDA graph.
 int enqueue_execute(const Plan &P, int sms, cudaStream_t s) {
-    BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
+    BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 8 * sizeof(unsigned long long), s));
     BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, P.n_jobs * sizeof(unsigned long long), s));
     int st = enqueue_filter(P, sms, s);
     if (st) return st;
@@ -544,7 +590,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         if (!st) st = A.alloc(&P.lim, (size_t)(P.n_s * n_jobs));
         if (!st) st = A.alloc(&jp, (size_t)n_jobs);
         if (!st) st = A.alloc(&jq, (size_t)n_jobs);
-        if (!st) st = A.alloc(&P.ctr, 3);
+        if (!st) st = A.alloc(&P.ctr, 8);
         if (!st) st = A.alloc(&P.job_surv, (size_t)n_jobs);
         if (!st) st = A.alloc(&P.err, 1);
         if (st) return st;
@@ -666,12 +712,14 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 if (st) return st;
                 sample_tiles(widths[wi], tj, tl);
                 unsigned long long *twin = nullptr;
-                st = build_tiles(P, tj, tl, false, {}, A, s, &twin);
+                st = build_tiles(P, tj, tl, false, {}, {}, A, s, &twin);
+                for (int c = 0; c < 4; c++) P.class_t0[c] = P.class_t1[c] = 0;
+                P.class_t1[width_class(widths[wi] / 64)] = P.n_tiles;
                 if (st) return st;
                 std::vector<unsigned long long> h_twin(P.n_tiles);
                 BMJ_CHECK(cudaMemcpyAsync(h_twin.data(), twin, P.n_tiles * sizeof(unsigned long long),
                                           cudaMemcpyDeviceToHost, s));
-                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 3 * sizeof(unsigned long long), s));
+                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 8 * sizeof(unsigned long long), s));
                 BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, n_jobs * sizeof(unsigned long long), s));
                 st = enqueue_filter(P, sms, s);
                 if (st) return st;
@@ -724,12 +772,33 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         BMJ_CHECK(cudaEventRecord(ev.e[4], s));
 
         // ---- tiles of every job ----
+        // jobs grouped by width class, so that each class is one tile range
+        std::vector<int32_t> order(n_jobs);
+        for (int64_t k = 0; k < n_jobs; k++) order[k] = (int32_t)k;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
+            return width_class(P.jobs[a].W) < width_class(P.jobs[c].W);
+        });
         std::vector<int64_t> job_tile0(n_jobs + 1, 0);
-        for (int64_t k = 0; k < n_jobs; k++) {
+        for (int c = 0; c < 4; c++) P.class_t0[c] = P.class_t1[c] = 0;
+        for (int64_t pos = 0; pos < n_jobs; pos++) {
+            const int64_t k = order[pos];
             const int64_t nk = job_sets[k + 1] - job_sets[k];
-            job_tile0[k + 1] = job_tile0[k] + (nk >= 2 ? (nk + P.jobs[k].tile_rows - 1) / P.jobs[k].tile_rows : 0);
+            job_tile0[pos + 1] =
+                job_tile0[pos] + (nk >= 2 ? (nk + P.jobs[k].tile_rows - 1) / P.jobs[k].tile_rows : 0);
         }
-        st = build_tiles(P, {}, {}, true, job_tile0, A, s, nullptr);
+        for (int c = 0; c < 4; c++) {
+            int64_t lo = -1, hi = -1;
+            for (int64_t pos = 0; pos < n_jobs; pos++)
+                if (width_class(P.jobs[order[pos]].W) == c) {
+                    if (lo < 0) lo = job_tile0[pos];
+                    hi = job_tile0[pos + 1];
+                }
+            if (lo >= 0) {
+                P.class_t0[c] = lo;
+                P.class_t1[c] = hi;
+            }
+        }
+        st = build_tiles(P, {}, {}, true, job_tile0, order, A, s, nullptr);
         if (st) return st;
 
         // ---- execute (filter + verification of all jobs) ----
@@ -759,6 +828,12 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
             bs.graph = graphed;
             BMJ_CHECK(cudaEventRecord(ev.e[6], s));
             BMJ_CHECK(cudaMemcpyAsync(hc, P.ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        {
+            int herr = 0;
+            BMJ_CHECK(cudaMemcpyAsync(&herr, P.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaStreamSynchronize(s));
+            if (herr) return BMJ_ERR_TIMEOUT;
+        }
             BMJ_CHECK(cudaStreamSynchronize(s));
             bs.filter_passes++;
             bs.ms_execute += ev.ms(5, 6);
