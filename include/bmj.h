@@ -99,7 +99,10 @@ typedef struct {
     void   *stream;            /* cudaStream_t; NULL = legacy default stream */
     int32_t rows_per_thread;   /* filter register blocking: 0 = automatic */
     int32_t use_graph;         /* bmj_self_join_batch: run the execute stage as a CUDA graph */
-    int32_t reserved[6];
+    int32_t cascade_b;         /* bmj_self_join: width of a second Bitmap Filter applied to the
+                                  survivors before merging (0 = automatic: 256 when b < 256;
+                                  -1 = none; otherwise a valid b larger than b) */
+    int32_t reserved[5];
 } bmj_options;
 
 /* Counters and stage times of one join.  Pair counts are exact and do not
@@ -109,10 +112,13 @@ typedef struct {
     int64_t survivors;      /* pairs that passed the Bitmap Filter (verified exactly) */
     int64_t results;        /* similar pairs returned */
     int64_t filter_passes;  /* filter launches over the whole window (1 unless the survivor queue had to grow) */
+    int64_t verified;       /* survivors that passed the cascade bound and were merged (= survivors without cascade) */
     int32_t n_launches;     /* CUDA kernels launched by this call */
     int32_t b;              /* bitmap bits used */
     int32_t method;         /* generation method used (COMBINED resolved) */
     int32_t max_set_size;
+    int32_t cascade_b;      /* width of the cascade bitmaps, 0 = none */
+    int32_t reserved_i;
     float   ms_prepare;     /* validation, size sort, sorted-CSR gather and bitmap build */
     float   ms_filter;      /* Bitmap Filter kernel(s) */
     float   ms_verify;      /* verification kernel(s) */

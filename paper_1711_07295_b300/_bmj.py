@@ -46,13 +46,14 @@ class bmj_options(C.Structure):
     _fields_ = [("b", C.c_int32), ("method", C.c_int32), ("output_on_device", C.c_int32),
                 ("validate", C.c_int32), ("queue_cap", C.c_int64), ("stream", C.c_void_p),
                 ("rows_per_thread", C.c_int32), ("use_graph", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("cascade_b", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class bmj_stats(C.Structure):
     _fields_ = [("window_pairs", C.c_int64), ("survivors", C.c_int64), ("results", C.c_int64),
-                ("filter_passes", C.c_int64), ("n_launches", C.c_int32), ("b", C.c_int32),
-                ("method", C.c_int32), ("max_set_size", C.c_int32), ("ms_prepare", C.c_float),
+                ("filter_passes", C.c_int64), ("verified", C.c_int64), ("n_launches", C.c_int32),
+                ("b", C.c_int32), ("method", C.c_int32), ("max_set_size", C.c_int32),
+                ("cascade_b", C.c_int32), ("reserved_i", C.c_int32), ("ms_prepare", C.c_float),
                 ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
                 ("ms_total", C.c_float), ("reserved_f", C.c_float)]
 
@@ -268,7 +269,7 @@ class DevicePairs:
 
 def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BMJ_XOR,
                   output_on_device: bool = False, queue_cap: int = 0, validate: bool = True,
-                  stream=None, sim: int = BMJ_JACCARD):
+                  stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0):
     """Exact Jaccard self-join at threshold p/q.
 
     Returns ``(a, b, stats)``: original ids with a < b sorted by (a, b), as
@@ -282,6 +283,7 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     o.output_on_device = 1 if output_on_device else 0
     o.validate = 1 if validate else 0
     o.queue_cap = int(queue_cap)
+    o.cascade_b = int(cascade_b)
     o.stream = _stream_of(stream, coll.on_device)
     pairs = bmj_pairs()
     st_ = bmj_stats()

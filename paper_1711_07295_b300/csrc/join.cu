@@ -98,12 +98,23 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         if (!st) st = A.alloc(&stok, (size_t)d.ntok);
         if (!st) st = A.alloc(&bm, (size_t)(n + 4) * W);  // padded: TMA chunks may read 3 past the end
         if (st) return st;
+        // Second, wider bitmaps for the cascade check in verification.
+        const int b2 = o.cascade_b == 0 ? (b < 256 ? 256 : 0) : (o.cascade_b > b ? o.cascade_b : 0);
+        const int W2 = b2 / 64;
+        uint64_t *bm2 = nullptr;
+        if (b2) {
+            st = A.alloc(&bm2, (size_t)n * W2);
+            if (st) return st;
+        }
+        stl.cascade_b = b2;
         st = radix_sort_u32_pairs(sizes, ids, ssz, perm, n, bit_length((uint64_t)max_size), A, s);
         if (st) return st;
         st = launch_widen(ssz, soff, n, s);
         if (!st) st = exclusive_scan_i64(soff, soff, n, nullptr, A, s);
         if (!st)
             st = launch_gather_build(perm, d.off, d.tok, soff, stok, bm, n, b, method, s);
+        if (!st && b2)
+            st = launch_gather_build(perm, d.off, d.tok, nullptr, nullptr, bm2, n, b2, method, s);
         if (st) return st;
 
         // ---- thresholds per |x|+|y|, window tiles, window size ----
@@ -114,16 +125,18 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         const int64_t n_tiles = (n + tile_rows - 1) / tile_rows;
         int32_t *tile_c0 = nullptr;
         int64_t *tile_off = nullptr;
-        unsigned long long *ctr = nullptr;  // [0] window, [1] survivors, [2] item counter, [3] results
+        // [0] window, [1] queue count, [2] item counter, [3] results, [4] verified,
+        // [5] first-level survivors (cascade)
+        unsigned long long *ctr = nullptr;
         int *err = nullptr;
         st = A.alloc(&need, (size_t)n_s);
         if (!st) st = A.alloc(&lim, (size_t)n_s);
         if (!st) st = A.alloc(&tile_c0, (size_t)n_tiles);
         if (!st) st = A.alloc(&tile_off, (size_t)n_tiles + 1);
-        if (!st) st = A.alloc(&ctr, 4);
+        if (!st) st = A.alloc(&ctr, 6);
         if (!st) st = A.alloc(&err, 1);
         if (st) return st;
-        BMJ_CHECK(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned long long), s));
+        BMJ_CHECK(cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), s));
         BMJ_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
         BMJ_CHECK(cudaMemsetAsync(ssz + n, 0, 4 * sizeof(uint32_t), s));
         BMJ_CHECK(cudaMemsetAsync(bm + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
@@ -195,11 +208,15 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         st = A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1));
         if (st) return st;
         BMJ_CHECK(cudaEventRecord(ev.e[5], s));
-        st = launch_verify(queue, n_surv, soff, stok, ssz, perm, need, keys, &ctr[3], nbits, sms, s);
+        st = launch_verify(queue, n_surv, soff, stok, ssz, perm, need, lim, bm2, W2, keys, &ctr[3],
+                           bm2 ? &ctr[4] : nullptr, nbits, sms, s);
         if (st) return st;
         BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+        int64_t hcas = 0;
         BMJ_CHECK(cudaMemcpyAsync(&n_res, &ctr[3], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaMemcpyAsync(&hcas, &ctr[4], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         BMJ_CHECK(cudaStreamSynchronize(s));
+        stl.verified = bm2 ? hcas : n_surv;
         stl.ms_verify = ev.ms(5, 6);
         A.free_one(queue);
 
@@ -374,6 +391,7 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (!bmj::valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
     if (o.method < BMJ_XOR || o.method > BMJ_COMBINED) return BMJ_ERR_INVALID_ARG;
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
+    if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(coll, p, q, o, out, stats);
     } catch (...) {

@@ -82,10 +82,15 @@ int launch_filter_tma(const FilterArgs &a, int W, int *err, int num_sms, cudaStr
 int filter_tma_tile_rows(int W);
 
 // Exact verification of the survivors; similar pairs are written as packed
-// keys (min_id << nbits) | max_id in original ids.
+// keys (min_id << nbits) | max_id in original ids.  With bm2 (W2 words per
+// set, size order) a survivor first meets the Eq. 2 bound with those wider
+// bitmaps (lim[S] as in the filter); *ccount (optional) counts the survivors
+// that pass it.
 int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
-                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need, uint64_t *keys,
-                  unsigned long long *rcount, int nbits, int num_sms, cudaStream_t s);
+                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need,
+                  const int32_t *lim, const uint64_t *bm2, int W2, uint64_t *keys,
+                  unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
+                  cudaStream_t s);
 
 // Splits packed keys into the (a, b) arrays of the output.
 int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,

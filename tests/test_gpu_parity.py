@@ -205,3 +205,23 @@ def test_million_sets_row_sampled(million, p, q, b):
     assert st["results"] == len(a) <= st["survivors"] <= st["window_pairs"]
     sa, sb = sizes[a], sizes[bb]
     assert np.all(q * np.minimum(sa, sb) >= p * np.maximum(sa, sb))
+
+
+@pytest.mark.parametrize("b", [64, 128, 256])
+def test_cascade_check_changes_nothing_but_merges(b):
+    # The second, wider Bitmap Filter in verification is sound (Theorem 1 for any
+    # b): the pair list and the first-level survivor count stay the oracle's.
+    off, tok = I.random_collection(4000, 1500, 1, 60, seed=31 + b, planted_frac=0.1)
+    d_off, d_tok = dev(off, tok)
+    ra, rb = O.self_join(off, tok, 1, 2)
+    w, s, r = O.filter_counts(off, tok, 1, 2, b, O.XOR)
+    seen = []
+    for cb in (-1, 0, 512, 1024):
+        a, bb, st = _bmj.bmj_self_join(d_off, d_tok, 1, 2, b=b, cascade_b=cb)
+        assert np.array_equal(a, ra) and np.array_equal(bb, rb), cb
+        assert (st["window_pairs"], st["survivors"], st["results"]) == (w, s, r)
+        assert st["results"] <= st["verified"] <= st["survivors"]
+        seen.append(st["verified"])
+        if cb == -1 or (cb == 0 and b >= 256):
+            assert st["cascade_b"] == 0 and st["verified"] == st["survivors"]
+    assert seen[2] <= seen[0]
