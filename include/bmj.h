@@ -198,7 +198,9 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
  *             x measured filter time per pair + estimated survivors x measured
  *             verification time per survivor); BMJ_COMBINED resolves the
  *             method per job; opt->use_graph runs the filter + verification
- *             stage as a CUDA graph.
+ *             stage as a CUDA graph; opt->cascade_b is 0 (jobs with b < 256 get
+ *             the 256-bit check before merging, and the autotuner counts it),
+ *             -1 (none) or 256.
  *   outs      n_jobs pair lists (library-owned; free each with
  *             bmj_pairs_free), in job-local ids (0 = the job's first set),
  *             sorted and unique as for bmj_self_join

@@ -309,7 +309,7 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
 def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int = BMJ_XOR,
                         output_on_device: bool = False, queue_cap: int = 0,
                         validate: bool = True, use_graph: bool = False, stream=None,
-                        sim: int = BMJ_JACCARD):
+                        sim: int = BMJ_JACCARD, cascade_b: int = 0):
     """Independent self-joins of the jobs ``job_sets`` of one concatenated collection.
 
     ``job_sets`` int64[n_jobs+1] set boundaries, ``p``/``q`` per-job thresholds;
@@ -330,6 +330,7 @@ def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int
     o.validate = 1 if validate else 0
     o.queue_cap = int(queue_cap)
     o.use_graph = 1 if use_graph else 0
+    o.cascade_b = int(cascade_b)
     o.stream = _stream_of(stream, coll.on_device)
     outs = (bmj_pairs * max(n_jobs, 1))()
     jst = (bmj_stats * max(n_jobs, 1))()

@@ -35,6 +35,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 struct JobDesc {
     const uint64_t *bm;  // bitmap array of the job's width (indexed by global sorted position)
+    const uint64_t *bm2; // cascade bitmaps (256 bits) checked before a merge, or null
     int64_t base;        // first sorted position of the job
     int64_t end;         // one past its last sorted position
     int64_t id_base;     // first input position of the job (output ids are local to it)
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(256)
                    int64_t cap, const int64_t *__restrict__ soff, const int32_t *__restrict__ stok,
                    const uint32_t *__restrict__ ssz, const uint32_t *__restrict__ sjob,
                    const uint32_t *__restrict__ perm, const JobDesc *__restrict__ jobs,
-                   const int32_t *__restrict__ need, uint64_t *__restrict__ keys,
-                   unsigned long long *__restrict__ rcount, int nbits) {
+                   const int32_t *__restrict__ need, const int32_t *__restrict__ lim,
+                   uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount, int nbits) {
     const int lane = threadIdx.x & 31;
     const int64_t n_surv = min((int64_t)*n_surv_dev, cap);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -281,7 +282,15 @@ __global__ void __launch_bounds__(256)
             const uint32_t k = sjob[pr.x];
             const JobDesc &jd = jobs[k];
             const uint32_t si = ssz[pr.x], sj = ssz[pr.y];
-            const int nd = need[jd.lim_off + si + sj];
+            int nd = need[jd.lim_off + si + sj];
+            if (jd.bm2) {  // cascade: Eq. 2 again with the 256-bit bitmaps (sound for any b)
+                const uint64_t *r2 = jd.bm2 + (int64_t)pr.x * 4;
+                const uint64_t *c2 = jd.bm2 + (int64_t)pr.y * 4;
+                int h2 = 0;
+#pragma unroll
+                for (int w = 0; w < 4; w++) h2 += __popcll(r2[w] ^ c2[w]);
+                if (h2 > lim[jd.lim_off + si + sj]) nd = 0x7fffffff;  // cannot reach the threshold
+            }
             const int32_t *x = stok + soff[pr.x];
             const int32_t *y = stok + soff[pr.y];
             int a = 0, b = 0, o = 0;
@@ -484,7 +493,7 @@ int enqueue_execute(const Plan &P, int sms, cudaStream_t s) {
     int st = enqueue_filter(P, sms, s);
     if (st) return st;
     BMJ_LAUNCH(k_verify_batch, (unsigned)(sms * 8), 256, 0, s, P.queue, &P.ctr[1], P.qcap, P.soff,
-               P.stok, P.ssz, P.sjob, P.perm, P.jobs_dev, P.need, P.keys, &P.ctr[2], P.nbits);
+               P.stok, P.ssz, P.sjob, P.perm, P.jobs_dev, P.need, P.lim, P.keys, &P.ctr[2], P.nbits);
     return BMJ_OK;
 }
 
@@ -602,7 +611,9 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
 
         // ---- bitmaps: one array per (b, method) in use ----
         const bool tune = o.b <= 0;
+        const bool cascade = o.cascade_b != -1;
         std::vector<int> widths = tune ? std::vector<int>{64, 128, 256} : std::vector<int>{o.b};
+        if (cascade && !tune && o.b < 256) widths.push_back(256);
         std::vector<int> methods;
         for (int64_t k = 0; k < n_jobs; k++)
             if (std::find(methods.begin(), methods.end(), job_method[k]) == methods.end())
@@ -634,6 +645,12 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 size_t wi = 0;
                 while (widths[wi] != jb[k]) wi++;
                 jd.bm = bms[wi][job_method[k]];
+                jd.bm2 = nullptr;
+                if (cascade && jb[k] < 256) {
+                    size_t w2 = 0;
+                    while (widths[w2] != 256) w2++;
+                    jd.bm2 = bms[w2][job_method[k]];
+                }
                 jd.base = job_sets[k];
                 jd.end = job_sets[k + 1];
                 jd.id_base = job_sets[k];
@@ -747,16 +764,26 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 }
             }
             auto filter_cost = [](int width) { return width == 64 ? 1.0 : width == 128 ? 1.55 : 2.55; };
+            // with the cascade, a survivor of a narrower filter costs one 256-bit
+            // check (28 pair-units) and is merged only if it passes that too
+            // (about as often as a survivor of the 256-bit filter itself)
+            const size_t w256 = widths.size() - 1;
             est_surv = 0.0;
             for (int64_t k = 0; k < n_jobs; k++) {
                 double best = 1e300;
                 double best_surv = 0.0;
                 const double verify_cost = 57.0 * std::max(1.0, mean_size[k] / 12.0);
+                const double s256 = samp_win[w256][k] > 0
+                                        ? (double)samp_surv[w256][k] * (double)job_win[k] / samp_win[w256][k]
+                                        : 0.0;
                 for (size_t wi = 0; wi < widths.size(); wi++) {
                     const double scale =
                         samp_win[wi][k] > 0 ? (double)job_win[k] / samp_win[wi][k] : 0.0;
                     const double surv = (double)samp_surv[wi][k] * scale;
-                    const double cost = (double)job_win[k] * filter_cost(widths[wi]) + surv * verify_cost;
+                    const bool casc = cascade && widths[wi] < 256;
+                    const double cost = (double)job_win[k] * filter_cost(widths[wi]) +
+                                        (casc ? surv * 28.0 + std::min(surv, s256) * verify_cost
+                                              : surv * verify_cost);
                     if (cost < best) {
                         best = cost;
                         best_surv = surv;
@@ -951,6 +978,7 @@ extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
     if (o.b != 0 && !bmj::valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
     if (o.method < BMJ_XOR || o.method > BMJ_COMBINED) return BMJ_ERR_INVALID_ARG;
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
+    if (o.cascade_b != 0 && o.cascade_b != -1 && o.cascade_b != 256) return BMJ_ERR_INVALID_ARG;
     int st;
     try {
         st = bmj::batch_impl(coll, n_jobs, job_sets, p, q, o, outs, job_stats, batch_stats);

@@ -152,3 +152,14 @@ def test_full_batched_workload_row_sampled():
         sel = np.isin(a, rows) | np.isin(b, rows)
         assert np.array_equal(a[sel], ra) and np.array_equal(b[sel], rb), k
         assert jst[k]["results"] == len(a) <= jst[k]["survivors"] <= jst[k]["window_pairs"]
+
+
+def test_batch_cascade_on_and_off():
+    jobs = make_batch(14, seed=17)
+    off, tok, js, p, q = concat(jobs)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    for b in (0, 64, 128):
+        on, jst_on, _ = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=b)
+        off_, jst_off, _ = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=b, cascade_b=-1)
+        check(jobs, on, jst_on)
+        check(jobs, off_, jst_off)

@@ -225,3 +225,30 @@ def test_cascade_check_changes_nothing_but_merges(b):
         if cb == -1 or (cb == 0 and b >= 256):
             assert st["cascade_b"] == 0 and st["verified"] == st["survivors"]
     assert seen[2] <= seen[0]
+
+
+@pytest.fixture(scope="module")
+def ten_million():
+    # 10,000,000 sets, Zipf(1.0) over 1,000,000 tokens, sizes lognormal(2.0, 0.8) in [1, 1000]
+    off_d, tok_d = I.gen_collection_device(I.spec_10m())
+    return off_d, tok_d, off_d.cpu().numpy(), tok_d.cpu().numpy()
+
+
+@pytest.mark.parametrize("p,q", [(9, 10), (3, 5)])
+def test_ten_million_sets_row_sampled(ten_million, p, q):
+    off_d, tok_d, off, tok = ten_million
+    dp, _, st = _bmj.bmj_self_join(off_d, tok_d, p, q, b=128, output_on_device=True)
+    a = dp.a.cpu().numpy().view(np.uint32)
+    bb = dp.b.cpu().numpy().view(np.uint32)
+    dp.release()
+    assert st["results"] == len(a) <= st["verified"] <= st["survivors"] <= st["window_pairs"]
+    rng = np.random.default_rng(p + q)
+    sizes = np.diff(off)
+    rows = np.concatenate([rng.choice(len(sizes), 10, replace=False), np.argsort(sizes)[-2:],
+                           np.nonzero(sizes == 1)[0][:2]])
+    ra, rb = O.join_rows(off, tok, p, q, rows)
+    sel = np.isin(a, rows) | np.isin(bb, rows)
+    assert np.array_equal(a[sel], ra) and np.array_equal(bb[sel], rb)
+    assert np.all(a < bb)
+    key = a.astype(np.uint64) << np.uint64(32) | bb.astype(np.uint64)
+    assert np.all(key[1:] > key[:-1])
