@@ -102,7 +102,12 @@ typedef struct {
     int32_t cascade_b;         /* bmj_self_join: width of a second Bitmap Filter applied to the
                                   survivors before merging (0 = automatic: 256 when b < 256;
                                   -1 = none; otherwise a valid b larger than b) */
-    int32_t reserved[5];
+    int32_t reserved0;
+    int64_t row_begin;         /* bmj_self_join: join only the pairs whose later set in size order
+                                  (sets ordered by size, ties by id) has its position in */
+    int64_t row_end;           /*   [row_begin, row_end); 0, 0 = every pair.  Bands that cover
+                                  [0, n) give disjoint pair lists whose union is the full join. */
+    int32_t reserved[2];
 } bmj_options;
 
 /* Counters and stage times of one join.  Pair counts are exact and do not

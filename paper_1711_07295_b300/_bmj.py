@@ -46,7 +46,8 @@ class bmj_options(C.Structure):
     _fields_ = [("b", C.c_int32), ("method", C.c_int32), ("output_on_device", C.c_int32),
                 ("validate", C.c_int32), ("queue_cap", C.c_int64), ("stream", C.c_void_p),
                 ("rows_per_thread", C.c_int32), ("use_graph", C.c_int32),
-                ("cascade_b", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("cascade_b", C.c_int32), ("reserved0", C.c_int32), ("row_begin", C.c_int64),
+                ("row_end", C.c_int64), ("reserved", C.c_int32 * 2)]
 
 
 class bmj_stats(C.Structure):
@@ -269,7 +270,8 @@ class DevicePairs:
 
 def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BMJ_XOR,
                   output_on_device: bool = False, queue_cap: int = 0, validate: bool = True,
-                  stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0):
+                  stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0,
+                  row_begin: int = 0, row_end: int = 0):
     """Exact Jaccard self-join at threshold p/q.
 
     Returns ``(a, b, stats)``: original ids with a < b sorted by (a, b), as
@@ -284,6 +286,8 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     o.validate = 1 if validate else 0
     o.queue_cap = int(queue_cap)
     o.cascade_b = int(cascade_b)
+    o.row_begin = int(row_begin)
+    o.row_end = int(row_end)
     o.stream = _stream_of(stream, coll.on_device)
     pairs = bmj_pairs()
     st_ = bmj_stats()

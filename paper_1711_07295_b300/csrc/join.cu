@@ -122,7 +122,11 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         int32_t *need = nullptr, *lim = nullptr;
         const int tile_rows = filter_tma_tile_rows(W);
         const int chunk_cols = W <= 4 ? 4096 : 2048;
-        const int64_t n_tiles = (n + tile_rows - 1) / tile_rows;
+        // rows joined: size-order positions [r0, r1) (all rows unless a band is given)
+        const int64_t r0 = (o.row_begin == 0 && o.row_end == 0) ? 0 : o.row_begin;
+        const int64_t r1 = (o.row_begin == 0 && o.row_end == 0) ? n : o.row_end;
+        if (r0 < 0 || r1 < r0 || r1 > n) return BMJ_ERR_INVALID_ARG;
+        const int64_t n_tiles = (r1 - r0 + tile_rows - 1) / tile_rows;
         int32_t *tile_c0 = nullptr;
         int64_t *tile_off = nullptr;
         // [0] window, [1] queue count, [2] item counter, [3] results, [4] verified,
@@ -131,7 +135,7 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         int *err = nullptr;
         st = A.alloc(&need, (size_t)n_s);
         if (!st) st = A.alloc(&lim, (size_t)n_s);
-        if (!st) st = A.alloc(&tile_c0, (size_t)n_tiles);
+        if (!st) st = A.alloc(&tile_c0, (size_t)(n_tiles > 0 ? n_tiles : 1));
         if (!st) st = A.alloc(&tile_off, (size_t)n_tiles + 1);
         if (!st) st = A.alloc(&ctr, 6);
         if (!st) st = A.alloc(&err, 1);
@@ -142,9 +146,9 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         BMJ_CHECK(cudaMemsetAsync(bm + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
         st = launch_tables(need, lim, n_s, p, q, s);
         if (!st)
-            st = launch_tiles(ssz, n, p, q, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s);
+            st = launch_tiles(ssz, n, p, q, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s, r0, r1);
         if (!st) st = exclusive_scan_i64(tile_off, tile_off, n_tiles, tile_off + n_tiles, A, s);
-        if (!st) st = launch_window_count(ssz, n, p, q, &ctr[0], s);
+        if (!st) st = launch_window_count(ssz, n, p, q, &ctr[0], s, r0, r1);
         if (st) return st;
         BMJ_CHECK(cudaEventRecord(ev.e[2], s));
         int64_t hv[2] = {0, 0};
@@ -165,6 +169,8 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         fa.ssz = ssz;
         fa.lim = lim;
         fa.n = n;
+        fa.row0 = r0;
+        fa.row_end = r1;
         fa.p = p;
         fa.q = q;
         fa.tile_item_off = tile_off;
@@ -392,6 +398,8 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (o.method < BMJ_XOR || o.method > BMJ_COMBINED) return BMJ_ERR_INVALID_ARG;
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
+    if (o.row_begin < 0 || o.row_end < 0 || o.row_end < o.row_begin) return BMJ_ERR_INVALID_ARG;
+    if ((o.row_begin != 0 || o.row_end != 0) && o.row_end > coll->n_sets) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(coll, p, q, o, out, stats);
     } catch (...) {

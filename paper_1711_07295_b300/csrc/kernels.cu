@@ -160,13 +160,14 @@ __global__ void k_tables(int32_t *__restrict__ need, int32_t *__restrict__ lim, 
 
 __global__ void k_tiles(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p, uint32_t q,
                         int tile_rows, int chunk_cols, int64_t n_tiles,
-                        int32_t *__restrict__ tile_c0, int64_t *__restrict__ tile_items) {
+                        int32_t *__restrict__ tile_c0, int64_t *__restrict__ tile_items,
+                        int64_t row0, int64_t row_end) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
-        const int64_t i0 = t * tile_rows;
+        const int64_t i0 = row0 + t * tile_rows;
         const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i0], p, q));
         const int64_t c0 = j0 & ~(int64_t)3;
-        const int64_t c_end = min(i0 + (int64_t)tile_rows, n) - 1;  // columns j < i <= c_end
+        const int64_t c_end = min(i0 + (int64_t)tile_rows, row_end) - 1;  // columns j < i <= c_end
         const int64_t cols = c_end - c0;
         tile_c0[t] = (int32_t)c0;
         tile_items[t] = cols > 0 ? (cols + chunk_cols - 1) / chunk_cols : 0;
@@ -174,10 +175,11 @@ __global__ void k_tiles(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p,
 }
 
 __global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p,
-                               uint32_t q, unsigned long long *__restrict__ out) {
+                               uint32_t q, unsigned long long *__restrict__ out, int64_t row0,
+                               int64_t row_end) {
     unsigned long long acc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int64_t i = row0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < row_end; i += stride) {
         const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i], p, q));
         if (j0 < i) acc += (unsigned long long)(i - j0);
     }
@@ -200,11 +202,12 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
         if ((int64_t)item >= a.n_items) return;
         const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
         const int64_t chunk = (int64_t)item - a.tile_item_off[t];
-        const int64_t i0 = t * a.tile_rows;
+        const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
+        const int64_t i0 = a.row0 + t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
+        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item<W, R>(a.bm, a.ssz, a.lim, a.n, i0, c0, c1, a.p, a.q, sink);
+        filter_item<W, R>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, sink);
     }
 }
 
@@ -218,11 +221,12 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
         if ((int64_t)item >= a.n_items) return;
         const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
         const int64_t chunk = (int64_t)item - a.tile_item_off[t];
-        const int64_t i0 = t * a.tile_rows;
+        const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
+        const int64_t i0 = a.row0 + t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
+        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_generic(a.bm, a.ssz, a.lim, a.n, i0, c0, c1, a.p, a.q, W, sink);
+        filter_item_generic(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, W, sink);
     }
 }
 
@@ -244,11 +248,12 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
         if ((int64_t)item >= a.n_items) break;
         const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
         const int64_t chunk = (int64_t)item - a.tile_item_off[t];
-        const int64_t i0 = t * a.tile_rows;
+        const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
+        const int64_t i0 = a.row0 + t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, a.n) - 1;
+        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_tma<W, R, CS>(a.bm, a.ssz, a.lim, a.n, i0, c0, c1, a.p, a.q, sink, st);
+        filter_item_tma<W, R, CS>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, sink, st);
         if (!st.ok) {
             if (lane == 0) atomicOr(err, 1);
             break;
@@ -395,17 +400,19 @@ int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, uint32_t p, uint32_t
 
 int launch_tiles(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q, int tile_rows,
                  int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int64_t *tile_items,
-                 cudaStream_t s) {
+                 cudaStream_t s, int64_t row0, int64_t row_end) {
     if (n_tiles <= 0) return BMJ_OK;
     BMJ_LAUNCH(k_tiles, grid_for(n_tiles, 256), 256, 0, s, ssz, n, p, q, tile_rows, chunk_cols,
-               n_tiles, tile_c0, tile_items);
+               n_tiles, tile_c0, tile_items, row0, row_end < 0 ? n : row_end);
     return BMJ_OK;
 }
 
 int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
-                        unsigned long long *out, cudaStream_t s) {
-    if (n <= 0) return BMJ_OK;
-    BMJ_LAUNCH(k_window_count, grid_for(n, 256), 256, 0, s, ssz, n, p, q, out);
+                        unsigned long long *out, cudaStream_t s, int64_t row0, int64_t row_end) {
+    if (row_end < 0) row_end = n;
+    if (row_end <= row0) return BMJ_OK;
+    BMJ_LAUNCH(k_window_count, grid_for(row_end - row0, 256), 256, 0, s, ssz, n, p, q, out, row0,
+               row_end);
     return BMJ_OK;
 }
 

@@ -42,17 +42,20 @@ int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, uint32_t p, uint32_t
 // of `chunk_cols` columns.
 int launch_tiles(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q, int tile_rows,
                  int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int64_t *tile_items,
-                 cudaStream_t s);
+                 cudaStream_t s, int64_t row0 = 0, int64_t row_end = -1);
 
 // Sum over sorted rows i of (i - j0(i)): the pairs inside the length window.
 int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
-                        unsigned long long *out, cudaStream_t s);
+                        unsigned long long *out, cudaStream_t s, int64_t row0 = 0,
+                        int64_t row_end = -1);
 
 struct FilterArgs {
     const uint64_t *bm;
     const uint32_t *ssz;
     const int32_t *lim;
     int64_t n;
+    int64_t row0 = 0;       // rows (size-order positions) [row0, row_end) are joined
+    int64_t row_end = -1;   // -1: n
     uint32_t p, q;
     const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
     const int32_t *tile_c0;

@@ -1,0 +1,71 @@
+"""Splitting one self-join across ranks by row bands, and gathering the results.
+
+The size-sorted triangle of window pairs (sets ordered by size, ties by id,
+the order the library joins in) is cut into contiguous row bands with about
+the same number of window pairs each; rank r joins only the pairs whose later
+set lies in its band (bmj_options.row_begin / row_end), over the full
+collection, which every rank holds.  The bands' pair lists are disjoint and
+their union is the full join, so the only exchange is one gather of the pair
+lists at the end, merged into the canonical (a, b) order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def sorted_sizes(offsets) -> np.ndarray:
+    """Set sizes in the join's size order (ties by original id)."""
+    sizes = np.diff(np.asarray(offsets, dtype=np.int64))
+    return sizes[np.argsort(sizes, kind="stable")]
+
+
+def row_window_counts(ssz: np.ndarray, p: int, q: int) -> np.ndarray:
+    """Window pairs per sorted row i: i - j0(i), j0(i) = first j with q*s_j >= p*s_i."""
+    low = -(-(p * ssz) // q)                       # ceil(p*s/q)
+    j0 = np.searchsorted(ssz, low, side="left")
+    return np.arange(len(ssz), dtype=np.int64) - j0
+
+
+def band_split(offsets, p: int, q: int, world: int):
+    """[(row_begin, row_end)] for each rank: contiguous, covering every row,
+    with about the same number of window pairs each."""
+    ssz = sorted_sizes(offsets)
+    n = len(ssz)
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    w = row_window_counts(ssz, p, q)
+    cum = np.concatenate([[0], np.cumsum(w)])
+    total = int(cum[-1])
+    cuts = [0]
+    for r in range(1, world):
+        target = total * r / world
+        cuts.append(int(np.searchsorted(cum, target, side="left")))
+    cuts.append(n)
+    cuts = np.maximum.accumulate(np.clip(cuts, 0, n))
+    return [(int(cuts[r]), int(cuts[r + 1])) for r in range(world)]
+
+
+def merge_pairs(parts):
+    """Union of disjoint pair lists [(a, b), ...] in the canonical (a, b) order."""
+    if not parts:
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint32)
+    a = np.concatenate([np.asarray(x[0], np.uint32) for x in parts])
+    b = np.concatenate([np.asarray(x[1], np.uint32) for x in parts])
+    order = np.lexsort((b, a))
+    return a[order], b[order]
+
+
+def gather_pairs(a, b, group=None):
+    """Gather every rank's pair list (torch.distributed, any backend) and merge."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    out = [None] * world
+    dist.all_gather_object(out, (np.asarray(a, np.uint32), np.asarray(b, np.uint32)), group=group)
+    return merge_pairs(out)
+
+
+def sharded_self_join(offsets, tokens, p: int, q: int, rank: int, world: int, **kw):
+    """This rank's band of the join through the C ABI (bmj_self_join)."""
+    from . import _bmj
+    r0, r1 = band_split(offsets.cpu().numpy() if hasattr(offsets, "cpu") else offsets, p, q, world)[rank]
+    return _bmj.bmj_self_join(offsets, tokens, p, q, row_begin=r0, row_end=r1, **kw)
