@@ -80,13 +80,14 @@ typedef struct {
 
 /* A pair list owned by the library until bmj_pairs_free().  Pair k is
  * (a[k], b[k]) in original 0-based set ids with a[k] < b[k]; pairs are sorted
- * by (a, b) and unique.  on_device says where a and b live. */
+ * by (a, b) and unique.  on_device says where a and b live; host lists of
+ * bmj_self_join are page-locked when possible (host_pinned = 1). */
 typedef struct {
     int64_t   n;
     uint32_t *a;
     uint32_t *b;
     int32_t   on_device;
-    int32_t   reserved;
+    int32_t   host_pinned;   /* set by the library; leave it as returned */
 } bmj_pairs;
 
 /* Tuning and placement options; bmj_default_options() fills the defaults. */

@@ -39,7 +39,32 @@ class bmj_collection(C.Structure):
 
 class bmj_pairs(C.Structure):
     _fields_ = [("n", C.c_int64), ("a", C.c_void_p), ("b", C.c_void_p),
-                ("on_device", C.c_int32), ("reserved", C.c_int32)]
+                ("on_device", C.c_int32), ("host_pinned", C.c_int32)]
+
+
+class _HostPairsOwner:
+    """Keeps a library-owned host pair list alive while numpy views of it exist."""
+
+    def __init__(self, pairs):
+        self.pairs = pairs
+
+    def __del__(self):
+        try:
+            lib().bmj_pairs_free(C.byref(self.pairs))
+        except Exception:
+            pass
+
+
+def _host_views(pairs):
+    """numpy views (no copy) of a host pair list; freed with the last view."""
+    n = int(pairs.n)
+    owner = _HostPairsOwner(pairs)
+    views = []
+    for ptr in (pairs.a, pairs.b):
+        buf = (C.c_uint32 * n).from_address(ptr)
+        buf._owner = owner
+        views.append(np.frombuffer(buf, dtype=np.uint32))
+    return views[0], views[1]
 
 
 class bmj_options(C.Structure):
@@ -304,9 +329,7 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     if n == 0:
         lib().bmj_pairs_free(C.byref(pairs))
         return np.zeros(0, np.uint32), np.zeros(0, np.uint32), stats
-    a = np.ctypeslib.as_array(C.cast(pairs.a, C.POINTER(C.c_uint32)), shape=(n,)).copy()
-    bb = np.ctypeslib.as_array(C.cast(pairs.b, C.POINTER(C.c_uint32)), shape=(n,)).copy()
-    lib().bmj_pairs_free(C.byref(pairs))
+    a, bb = _host_views(pairs)
     return a, bb, stats
 
 

@@ -258,9 +258,18 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             if (!st) st = A.alloc(&db, (size_t)n_res);
             if (!st) st = launch_unpack(keys_sorted, n_res, nbits, da, db, s);
             if (!st) {
-                res.a = (uint32_t *)malloc(n_res * sizeof(uint32_t));
-                res.b = (uint32_t *)malloc(n_res * sizeof(uint32_t));
-                if (!res.a || !res.b) st = BMJ_ERR_OOM;
+                // page-locked host memory, so that the copy out runs at full link speed
+                if (cudaMallocHost(&res.a, n_res * sizeof(uint32_t)) == cudaSuccess &&
+                    cudaMallocHost(&res.b, n_res * sizeof(uint32_t)) == cudaSuccess) {
+                    res.host_pinned = 1;
+                } else {
+                    cudaGetLastError();
+                    if (res.a) cudaFreeHost(res.a);
+                    res.a = (uint32_t *)malloc(n_res * sizeof(uint32_t));
+                    res.b = (uint32_t *)malloc(n_res * sizeof(uint32_t));
+                    res.host_pinned = 0;
+                    if (!res.a || !res.b) st = BMJ_ERR_OOM;
+                }
             }
             if (!st) {
                 cudaError_t e1 = cudaMemcpyAsync(res.a, da, n_res * sizeof(uint32_t),
@@ -417,10 +426,14 @@ void bmj_pairs_free(bmj_pairs *pairs) {
     if (pairs->on_device) {
         if (pairs->a) cudaFree(pairs->a);
         if (pairs->b) cudaFree(pairs->b);
+    } else if (pairs->host_pinned == 1) {  // page-locked host memory
+        if (pairs->a) cudaFreeHost(pairs->a);
+        if (pairs->b) cudaFreeHost(pairs->b);
     } else {
         free(pairs->a);
         free(pairs->b);
     }
+    pairs->host_pinned = 0;
     pairs->a = nullptr;
     pairs->b = nullptr;
     pairs->n = 0;
