@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_filter_batch_w(const BatchFilterArgs a,
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     StageState stg;
-    init_stage(stg, smem + (threadIdx.x >> 5) * ColStage<W, CS>::kWarpBytes);
+    init_stage(stg, smem + (threadIdx.x >> 5) * ColStage<W, CS>::kWarpBytes);  // default bounded waits
     const int64_t ibase = a.tile_item_off[t0], iend = a.tile_item_off[t1];
     for (;;) {
         unsigned long long item = 0;
@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(128) k_filter_batch_w(const BatchFilterArgs a,
         filter_item_tma<W, R, CS>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, jd.p,
                                   jd.q, sink, stg);
         if (!stg.ok) {
+            drain_stage(stg);
             if (lane == 0) atomicOr(a.err, 1);
             return;
         }

@@ -41,6 +41,19 @@ inline int status_of(cudaError_t e) {
     } while (0)
 
 // ---------------------------------------------------------------------------
+// Host-side fault injection (tests): BMJ_FAULT=alloc:K makes the K-th device
+// allocation of a bmj_self_join call fail; BMJ_FAULT=timeout makes one warp of
+// the filter skip one copy, so that its bounded wait runs out.
+// ---------------------------------------------------------------------------
+struct FaultPlan {
+    int alloc_at = 0;   // 0: none
+    bool timeout = false;
+};
+FaultPlan read_fault_plan();      // parses BMJ_FAULT
+void arm_alloc_fault(int k);      // the k-th next Arena allocation fails (0 disarms)
+bool alloc_fault_fires();         // consumed by Arena::alloc
+
+// ---------------------------------------------------------------------------
 // Device arena: stream-ordered allocations released together.
 // ---------------------------------------------------------------------------
 struct Arena {
@@ -54,6 +67,7 @@ struct Arena {
         *p = nullptr;
         if (count == 0) count = 1;
         if (n >= 256) return BMJ_ERR_OOM;
+        if (alloc_fault_fires()) return BMJ_ERR_OOM;
         void *q = nullptr;
         cudaError_t e = cudaMallocAsync(&q, count * sizeof(T), stream);
         if (e != cudaSuccess) {

@@ -254,11 +254,11 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
         : "memory");
 }
 
-// Waits for the phase `parity` of bar, giving up after a bounded number of
-// polls (returns false then).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Waits for the phase `parity` of bar, giving up after `limit` polls
+// (returns false then).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit) {
     const uint32_t addr = smem_u32(bar);
-    for (int it = 0; it < (1 << 22); it++) {
+    for (int it = 0; it < limit; it++) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -324,13 +324,29 @@ struct StageState {
     uint64_t *bar;        // two mbarriers
     uint32_t phase;       // bit k: parity to wait for on buffer k
     bool ok;              // false once a wait gave up
+    int pending;          // after a failed wait: 1 + slot of a copy still in flight, or 0
+    int wait_limit;       // polls before a wait gives up
+    int skip_copy;        // fault injection: issue no copy for the next fill (then 0)
 };
+
+// After a failed wait: waits (bounded) for the copy still in flight, so that
+// no copy targets the warp's shared memory after it stops.
+__device__ __forceinline__ void drain_stage(StageState &st) {
+    if (st.pending) {
+        const int slot = st.pending - 1;
+        mbar_wait(&st.bar[slot], (st.phase >> slot) & 1u, st.wait_limit);
+        st.pending = 0;
+    }
+}
 
 __device__ __forceinline__ void init_stage(StageState &st, unsigned char *region) {
     st.bar = reinterpret_cast<uint64_t *>(region);
     st.buf = region + 16;
     st.phase = 0;
     st.ok = true;
+    st.pending = 0;
+    st.wait_limit = 1 << 22;
+    st.skip_copy = 0;
     if ((threadIdx.x & 31) == 0) {
         mbar_init(&st.bar[0], 1);
         mbar_init(&st.bar[1], 1);
@@ -341,7 +357,7 @@ __device__ __forceinline__ void init_stage(StageState &st, unsigned char *region
 }
 
 template <int W, int CS>
-__device__ __forceinline__ void stage_issue(const StageState &st, int slot,
+__device__ __forceinline__ void stage_issue(StageState &st, int slot,
                                             const uint64_t *__restrict__ bm,
                                             const uint32_t *__restrict__ ssz, int64_t c_al,
                                             int ncols) {
@@ -351,6 +367,10 @@ __device__ __forceinline__ void stage_issue(const StageState &st, int slot,
     const uint32_t sz_bytes = (uint32_t)ncols * 4u;
     fence_async_shared();
     mbar_expect_tx(&st.bar[slot], bm_bytes + sz_bytes);
+    if (st.skip_copy) {  // fault injection: the bytes the barrier expects never arrive
+        st.skip_copy = 0;
+        return;
+    }
     tma_load_1d(b, bm + c_al * W, bm_bytes, &st.bar[slot]);
     tma_load_1d(b + L::kCols * 8 * W, ssz + c_al, sz_bytes, &st.bar[slot]);
 }
@@ -409,10 +429,12 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
             const int64_t c_al = cs_ & ~(int64_t)3;
             stage_issue<W, CS>(st, slot ^ 1, bm, ssz, c_al, (int)(((ce_ - c_al) + 3) & ~(int64_t)3));
         }
-        const bool got = mbar_wait(&st.bar[slot], (st.phase >> slot) & 1u);
+        const bool got = mbar_wait(&st.bar[slot], (st.phase >> slot) & 1u, st.wait_limit);
         st.phase ^= 1u << slot;
         if (!__all_sync(kFull, got)) {
+            // give up; the copy into the other buffer (if any) is drained by the caller
             st.ok = false;
+            st.pending = (ch + 1 < n_chunks) ? (slot ^ 1) + 1 : 0;
             return;
         }
         const int64_t cs = c0 + ch * CS, ce = min(cs + (int64_t)CS, c1);

@@ -19,6 +19,27 @@ static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
+static std::atomic<int> g_alloc_fault{0};
+
+FaultPlan read_fault_plan() {
+    FaultPlan f;
+    const char *e = getenv("BMJ_FAULT");
+    if (!e) return f;
+    if (strncmp(e, "alloc:", 6) == 0) f.alloc_at = atoi(e + 6);
+    if (strcmp(e, "timeout") == 0) f.timeout = true;
+    return f;
+}
+
+void arm_alloc_fault(int k) { g_alloc_fault.store(k > 0 ? k : 0); }
+
+bool alloc_fault_fires() {
+    int v = g_alloc_fault.load();
+    while (v > 0) {
+        if (g_alloc_fault.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+
 void retain_pool_memory(int device) {
     static std::mutex mu;
     static bool done[128] = {false};
@@ -52,6 +73,8 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
                           const bmj_options &o, bmj_pairs *out, bmj_stats *stats) {
     cudaStream_t s = (cudaStream_t)o.stream;
     const int64_t launches0 = launches();
+    const FaultPlan fault = read_fault_plan();
+    arm_alloc_fault(fault.alloc_at);
     int dev = 0;
     BMJ_CHECK(cudaGetDevice(&dev));
     retain_pool_memory(dev);
@@ -183,6 +206,10 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         fa.qcount = &ctr[1];
         fa.qcap = qcap;
         fa.item_counter = &ctr[2];
+        if (fault.timeout) {
+            fa.fault_skip_copy = 1;
+            fa.wait_limit = 1 << 12;
+        }
         int64_t n_surv = 0;
         for (int pass = 0; pass < 2; pass++) {
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
@@ -414,6 +441,7 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     } catch (...) {
         st = BMJ_ERR_OOM;
     }
+    bmj::arm_alloc_fault(0);
     if (st) {
         bmj_pairs_free(out);
         cudaGetLastError();

@@ -233,13 +233,17 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
 // Bitmap Filter with TMA-staged columns (filter_item_tma).  Each warp owns a
 // double buffer of column chunks in dynamic shared memory and its two
 // mbarriers; a wait that gives up sets *err and stops the warp.
-template <int W, int R, int CS>
+template <int W, int R, int CS, bool kFault>
 __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     using L = ColStage<W, CS>;
     const int lane = threadIdx.x & 31;
     StageState st;
     init_stage(st, smem + (threadIdx.x >> 5) * L::kWarpBytes);
+    if (kFault) {  // fault injection: the first warp skips its first copy; short waits
+        st.wait_limit = a.wait_limit;
+        st.skip_copy = (blockIdx.x == 0 && threadIdx.x < 32) ? 1 : 0;
+    }
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
     for (;;) {
         unsigned long long item = 0;
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
         filter_item_tma<W, R, CS>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, sink, st);
         if (!st.ok) {
+            drain_stage(st);
             if (lane == 0) atomicOr(err, 1);
             break;
         }
@@ -445,19 +450,26 @@ int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s) {
     }
 }
 
-template <int W, int R, int CS>
-int launch_filter_tma_t(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
+template <int W, int R, int CS, bool kFault>
+int launch_filter_tma_k(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
     using L = ColStage<W, CS>;
     const int smem = 4 * L::kWarpBytes;
     int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tma<W, R, CS>, 128, smem));
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tma<W, R, CS, kFault>,
+                                                            128, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)num_sms * per_sm;
     const int64_t need_blocks = (a.n_items + 3) / 4;
     if (need_blocks < blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
-    BMJ_LAUNCH((k_filter_tma<W, R, CS>), (unsigned)blocks, 128, smem, s, a, err);
+    BMJ_LAUNCH((k_filter_tma<W, R, CS, kFault>), (unsigned)blocks, 128, smem, s, a, err);
     return BMJ_OK;
+}
+
+template <int W, int R, int CS>
+int launch_filter_tma_t(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
+    return a.fault_skip_copy ? launch_filter_tma_k<W, R, CS, true>(a, err, num_sms, s)
+                             : launch_filter_tma_k<W, R, CS, false>(a, err, num_sms, s);
 }
 
 int filter_tma_tile_rows(int W) {

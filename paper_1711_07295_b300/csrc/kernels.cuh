@@ -56,6 +56,8 @@ struct FilterArgs {
     int64_t n;
     int64_t row0 = 0;       // rows (size-order positions) [row0, row_end) are joined
     int64_t row_end = -1;   // -1: n
+    int wait_limit = 0;     // TMA filter: polls before a copy wait gives up (0: default)
+    int fault_skip_copy = 0;  // fault injection: one warp skips one copy (the wait runs out)
     uint32_t p, q;
     const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
     const int32_t *tile_c0;
