@@ -272,6 +272,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int li
     return false;
 }
 
+// Population count of a 64-bit word (lo, hi) with ALU operations only:
+// pairwise bit sums (2-bit fields), then 4-bit fields, the two halves added,
+// then byte fields summed by a multiply.  Used for one row in eight so that
+// part of the popcount work runs on the ALU and FMA pipes instead of POPC.
+__device__ __forceinline__ int popc64_alu(uint32_t lo, uint32_t hi) {
+    lo = lo - ((lo >> 1) & 0x55555555u);
+    hi = hi - ((hi >> 1) & 0x55555555u);
+    lo = (lo & 0x33333333u) + ((lo >> 2) & 0x33333333u);
+    hi = (hi & 0x33333333u) + ((hi >> 2) & 0x33333333u);
+    uint32_t v = lo + hi;                                      // 4-bit fields, each <= 8
+    v = (v & 0x0F0F0F0Fu) + ((v >> 4) & 0x0F0F0F0Fu);          // byte fields, each <= 16
+    return (int)((v * 0x01010101u) >> 24);                     // sum of the four bytes (<= 64)
+}
+
 template <int W>
 struct PopcHS;
 
@@ -377,7 +391,7 @@ __device__ __forceinline__ void stage_issue(StageState &st, int slot,
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
 // arrays must be readable up to 3 entries past the last column (padded).
-template <int W, int R, int CS>
+template <int W, int R, int CS, int kAluRows = 0>
 __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                                                 const uint32_t *__restrict__ ssz,
                                                 const int32_t *__restrict__ lim_tab,
@@ -468,7 +482,10 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                     uint32_t x[2 * W];
 #pragma unroll
                     for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
-                    const int t = PopcHS<W>::h(x) + nlim[k];
+                    int h;
+                    if (W == 1 && kAluRows > 0 && k >= R - kAluRows) h = popc64_alu(x[0], x[1]);
+                    else h = PopcHS<W>::h(x);
+                    const int t = h + nlim[k];
                     mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);
                 }
             }

@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
         const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_tma<W, R, CS>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, sink, st);
+        filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0)>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1,
+                                                             a.p, a.q, sink, st);
         if (!st.ok) {
             drain_stage(st);
             if (lane == 0) atomicOr(err, 1);

@@ -78,6 +78,11 @@ int filter_tile_rows(int W);
 
 // Rows per lane of the TMA-staged filter, per bitmap width.
 constexpr int kTmaR1 = 8, kTmaR2 = 4, kTmaR4 = 4;
+// At b = 64, rows per lane whose popcount runs on the ALU instead of POPC.
+#ifndef BMJ_ALU_ROWS_W1
+#define BMJ_ALU_ROWS_W1 1
+#endif
+constexpr int kAluRowsW1 = BMJ_ALU_ROWS_W1;
 
 // The Bitmap Filter with column chunks staged in shared memory by TMA bulk
 // copies (b in {64, 128, 256}; other widths fall back to launch_filter).  The
