@@ -461,6 +461,7 @@ def run_batched(args, dev):
             "speedup": round(single_s / batched_s, 3),
             "tuned_b": {str(b): chosen.count(b) for b in (64, 128, 256)},
             "graph": int(last["graph"]), "launches": int(last["n_launches"]),
+            "filter_passes": int(last["filter_passes"]),
             "generation_s": round(gen_s, 2)}
 
 

@@ -620,23 +620,42 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
             if (std::find(methods.begin(), methods.end(), job_method[k]) == methods.end())
                 methods.push_back(job_method[k]);
         uint64_t *bms[3][4] = {{nullptr}};
-        bool gathered = false;
         for (size_t wi = 0; wi < widths.size(); wi++)
             for (int m : methods) {
                 const int W = widths[wi] / 64;
                 st = A.alloc(&bms[wi][m], (size_t)(n + 4) * W);
                 if (st) return st;
                 BMJ_CHECK(cudaMemsetAsync(bms[wi][m] + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
-                if (!gathered) {
-                    st = launch_gather_build(P.perm, d.off, d.tok, P.soff, P.stok, bms[wi][m], n,
-                                             widths[wi], m, s);
-                    gathered = true;
-                } else {
-                    st = launch_gather_build(nullptr, P.soff, P.stok, nullptr, nullptr, bms[wi][m], n,
-                                             widths[wi], m, s);
-                }
-                if (st) return st;
             }
+        bool gathered = false;
+        for (int m : methods) {
+            uint64_t *w64 = nullptr, *w128 = nullptr, *w256 = nullptr;
+            for (size_t wi = 0; wi < widths.size(); wi++) {
+                if (widths[wi] == 64) w64 = bms[wi][m];
+                else if (widths[wi] == 128) w128 = bms[wi][m];
+                else if (widths[wi] == 256) w256 = bms[wi][m];
+            }
+            if ((m == BMJ_XOR || m == BMJ_SET) && (w64 || w128 || w256)) {
+                // one pass over the tokens for every power-of-two width up to 256
+                st = gathered ? launch_build_multi(nullptr, P.soff, P.stok, nullptr, nullptr, n, m,
+                                                   w64, w128, w256, s)
+                              : launch_build_multi(P.perm, d.off, d.tok, P.soff, P.stok, n, m, w64,
+                                                   w128, w256, s);
+                if (st) return st;
+                gathered = true;
+            }
+            for (size_t wi = 0; wi < widths.size(); wi++) {
+                const bool done = (m == BMJ_XOR || m == BMJ_SET) &&
+                                  (widths[wi] == 64 || widths[wi] == 128 || widths[wi] == 256);
+                if (done) continue;
+                st = gathered ? launch_gather_build(nullptr, P.soff, P.stok, nullptr, nullptr,
+                                                    bms[wi][m], n, widths[wi], m, s)
+                              : launch_gather_build(P.perm, d.off, d.tok, P.soff, P.stok, bms[wi][m],
+                                                    n, widths[wi], m, s);
+                if (st) return st;
+                gathered = true;
+            }
+        }
 
         // ---- job table ----
         P.jobs.assign(n_jobs, JobDesc());
@@ -830,11 +849,14 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         if (st) return st;
 
         // ---- execute (filter + verification of all jobs) ----
+        // The sampled estimate can miss clustered survivors (duplicate-heavy rows),
+        // and an overflow reruns the whole filter: size the queue generously
+        // (4x the estimate + 16M entries, at most a quarter of free memory).
         int64_t qcap = o.queue_cap > 0
                            ? o.queue_cap
-                           : (est_surv >= 0 ? (int64_t)(1.25 * est_surv) + ((int64_t)1 << 20)
+                           : (est_surv >= 0 ? (int64_t)(4.0 * est_surv) + ((int64_t)1 << 24)
                                             : std::max<int64_t>((int64_t)(total_win / 128),
-                                                                (int64_t)1 << 20));
+                                                                (int64_t)1 << 24));
         {
             size_t free_b = 0, total_b = 0;
             if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)

@@ -134,10 +134,20 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         if (st) return st;
         st = launch_widen(ssz, soff, n, s);
         if (!st) st = exclusive_scan_i64(soff, soff, n, nullptr, A, s);
-        if (!st)
-            st = launch_gather_build(perm, d.off, d.tok, soff, stok, bm, n, b, method, s);
-        if (!st && b2)
-            st = launch_gather_build(perm, d.off, d.tok, nullptr, nullptr, bm2, n, b2, method, s);
+        if (!st) {
+            const bool multi = (method == BMJ_XOR || method == BMJ_SET) &&
+                               (b == 64 || b == 128 || b == 256) && (b2 == 0 || b2 == 256);
+            if (multi) {  // one pass over the tokens for both widths
+                st = launch_build_multi(perm, d.off, d.tok, soff, stok, n, method,
+                                        b == 64 ? bm : nullptr, b == 128 ? bm : nullptr,
+                                        b == 256 ? bm : (b2 == 256 ? bm2 : nullptr), s);
+            } else {
+                st = launch_gather_build(perm, d.off, d.tok, soff, stok, bm, n, b, method, s);
+                if (!st && b2)
+                    st = launch_gather_build(perm, d.off, d.tok, nullptr, nullptr, bm2, n, b2,
+                                             method, s);
+            }
+        }
         if (st) return st;
 
         // ---- thresholds per |x|+|y|, window tiles, window size ----

@@ -145,6 +145,62 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
     }
 }
 
+// One thread per set: gathers the set's tokens into the sorted CSR (when stok
+// is given) and writes its Xor (Alg. 3b) or Set (Alg. 3a) bitmaps for up to
+// three widths at once (64, 128, 256 bits; a null output skips a width).
+// With b a power of two, h(t) = t mod b selects word (t mod b) / 64 and bit
+// t mod 64 for all three widths.
+__global__ void __launch_bounds__(256)
+    k_build_multi(const uint32_t *__restrict__ perm, const int64_t *__restrict__ off,
+                  const int32_t *__restrict__ tok, const int64_t *__restrict__ soff,
+                  int32_t *__restrict__ stok, int64_t n, int method, uint64_t *__restrict__ bm64,
+                  uint64_t *__restrict__ bm128, uint64_t *__restrict__ bm256) {
+    const bool xr = method == BMJ_XOR;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t src = perm ? (int64_t)perm[i] : i;
+        const int64_t lo = off[src];
+        const int64_t cnt = off[src + 1] - lo;
+        const int32_t *x = tok + lo;
+        int32_t *y = stok ? stok + soff[i] : nullptr;
+        uint64_t a = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        for (int64_t k = 0; k < cnt; k++) {
+            const uint32_t t = (uint32_t)x[k];
+            if (y) y[k] = (int32_t)t;
+            const uint64_t bit = 1ull << (t & 63u);
+            const uint32_t w2 = (t >> 6) & 1u, w4 = (t >> 6) & 3u;
+            if (xr) {
+                a ^= bit;
+                b0 ^= w2 == 0 ? bit : 0ull;
+                b1 ^= w2 == 1 ? bit : 0ull;
+                c0 ^= w4 == 0 ? bit : 0ull;
+                c1 ^= w4 == 1 ? bit : 0ull;
+                c2 ^= w4 == 2 ? bit : 0ull;
+                c3 ^= w4 == 3 ? bit : 0ull;
+            } else {
+                a |= bit;
+                b0 |= w2 == 0 ? bit : 0ull;
+                b1 |= w2 == 1 ? bit : 0ull;
+                c0 |= w4 == 0 ? bit : 0ull;
+                c1 |= w4 == 1 ? bit : 0ull;
+                c2 |= w4 == 2 ? bit : 0ull;
+                c3 |= w4 == 3 ? bit : 0ull;
+            }
+        }
+        if (bm64) bm64[i] = a;
+        if (bm128) {
+            bm128[2 * i] = b0;
+            bm128[2 * i + 1] = b1;
+        }
+        if (bm256) {
+            bm256[4 * i] = c0;
+            bm256[4 * i + 1] = c1;
+            bm256[4 * i + 2] = c2;
+            bm256[4 * i + 3] = c3;
+        }
+    }
+}
+
 __global__ void k_tables(int32_t *__restrict__ need, int32_t *__restrict__ lim, int64_t n_s,
                          uint32_t p, uint32_t q) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -395,6 +451,15 @@ int launch_gather_build(const uint32_t *perm, const int64_t *off, const int32_t 
     if (n <= 0) return BMJ_OK;
     BMJ_LAUNCH(k_gather_build, grid_for(n, kBuildWarps, 148 * 64), kBuildWarps * 32, 0, s, perm,
                off, tok, soff, stok, bm, n, b, method);
+    return BMJ_OK;
+}
+
+int launch_build_multi(const uint32_t *perm, const int64_t *off, const int32_t *tok,
+                       const int64_t *soff, int32_t *stok, int64_t n, int method, uint64_t *bm64,
+                       uint64_t *bm128, uint64_t *bm256, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_build_multi, grid_for(n, 256, 148 * 16), 256, 0, s, perm, off, tok, soff, stok, n,
+               method, bm64, bm128, bm256);
     return BMJ_OK;
 }
 

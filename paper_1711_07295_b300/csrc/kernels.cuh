@@ -31,6 +31,13 @@ int launch_gather_build(const uint32_t *perm, const int64_t *off, const int32_t 
                         const int64_t *soff, int32_t *stok, uint64_t *bm, int64_t n, int b,
                         int method, cudaStream_t s);
 
+// Xor or Set bitmaps (method BMJ_XOR / BMJ_SET) of up to three widths at once,
+// one thread per set, with the sorted-CSR gather fused as in
+// launch_gather_build; bm64 / bm128 / bm256 may be null.
+int launch_build_multi(const uint32_t *perm, const int64_t *off, const int32_t *tok,
+                       const int64_t *soff, int32_t *stok, int64_t n, int method, uint64_t *bm64,
+                       uint64_t *bm128, uint64_t *bm256, cudaStream_t s);
+
 // need[S] = ceil(p*S/(p+q)) (the smallest overlap with Jaccard >= p/q when
 // |x|+|y| = S) and lim[S] = S - 2*need[S] (the largest Hamming distance
 // whose Eq. 2 bound still reaches need[S]), for S in [0, n_s).
@@ -77,7 +84,10 @@ int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s);
 int filter_tile_rows(int W);
 
 // Rows per lane of the TMA-staged filter, per bitmap width.
-constexpr int kTmaR1 = 8, kTmaR2 = 4, kTmaR4 = 4;
+#ifndef BMJ_TMA_R1
+#define BMJ_TMA_R1 8
+#endif
+constexpr int kTmaR1 = BMJ_TMA_R1, kTmaR2 = 4, kTmaR4 = 4;
 // At b = 64, rows per lane whose popcount runs on the ALU instead of POPC.
 #ifndef BMJ_ALU_ROWS_W1
 #define BMJ_ALU_ROWS_W1 1
