@@ -81,7 +81,10 @@ typedef struct {
 /* A pair list owned by the library until bmj_pairs_free().  Pair k is
  * (a[k], b[k]) in original 0-based set ids with a[k] < b[k]; pairs are sorted
  * by (a, b) and unique.  on_device says where a and b live; host lists of
- * bmj_self_join are page-locked when possible (host_pinned = 1). */
+ * bmj_self_join are page-locked when possible (host_pinned = 1): then a and b
+ * share one block that bmj_pairs_free returns to a reuse pool of the library
+ * (at most 8 idle blocks and 4 GiB are kept), so that the next call does not
+ * pin pages again. */
 typedef struct {
     int64_t   n;
     uint32_t *a;

@@ -95,6 +95,12 @@ struct Arena {
 // Keeps the stream-ordered pool's memory between calls (set once per device).
 void retain_pool_memory(int device);
 
+// Page-locked host blocks reused between calls (host_pool.cu).  pinned_alloc
+// returns nullptr when the driver refuses; pinned_release returns false for a
+// pointer that is not a live block of the pool.
+void *pinned_alloc(size_t bytes);
+bool pinned_release(void *p);
+
 // ---------------------------------------------------------------------------
 // Device-wide primitives (scan_sort.cu)
 // ---------------------------------------------------------------------------

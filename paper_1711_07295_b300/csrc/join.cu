@@ -295,13 +295,14 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             if (!st) st = A.alloc(&db, (size_t)n_res);
             if (!st) st = launch_unpack(keys_sorted, n_res, nbits, da, db, s);
             if (!st) {
-                // page-locked host memory, so that the copy out runs at full link speed
-                if (cudaMallocHost(&res.a, n_res * sizeof(uint32_t)) == cudaSuccess &&
-                    cudaMallocHost(&res.b, n_res * sizeof(uint32_t)) == cudaSuccess) {
+                // one page-locked block (a, then b) from the reuse pool, so that the
+                // copy out runs at full link speed without pinning pages every call
+                uint32_t *blk = (uint32_t *)pinned_alloc(2 * (size_t)n_res * sizeof(uint32_t));
+                if (blk) {
+                    res.a = blk;
+                    res.b = blk + n_res;
                     res.host_pinned = 1;
                 } else {
-                    cudaGetLastError();
-                    if (res.a) cudaFreeHost(res.a);
                     res.a = (uint32_t *)malloc(n_res * sizeof(uint32_t));
                     res.b = (uint32_t *)malloc(n_res * sizeof(uint32_t));
                     res.host_pinned = 0;
@@ -464,9 +465,8 @@ void bmj_pairs_free(bmj_pairs *pairs) {
     if (pairs->on_device) {
         if (pairs->a) cudaFree(pairs->a);
         if (pairs->b) cudaFree(pairs->b);
-    } else if (pairs->host_pinned == 1) {  // page-locked host memory
-        if (pairs->a) cudaFreeHost(pairs->a);
-        if (pairs->b) cudaFreeHost(pairs->b);
+    } else if (pairs->host_pinned == 1) {  // one pooled page-locked block holding a and b
+        bmj::pinned_release(pairs->a);
     } else {
         free(pairs->a);
         free(pairs->b);

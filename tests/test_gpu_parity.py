@@ -99,6 +99,26 @@ def test_host_and_device_paths_agree():
     dp.release()
 
 
+def test_pooled_host_lists_are_reused_without_aliasing():
+    """Freed page-locked lists go back to the library's pool; a list still held is never reused."""
+    off, tok = I.random_collection(5000, 1500, 2, 40, seed=6, planted_frac=0.1)
+    ra, rb = O.self_join(off, tok, 1, 2)
+    a1, b1, _ = _bmj.bmj_self_join(off, tok, 1, 2)
+    keep_a, keep_b = a1.copy(), b1.copy()
+    a2, b2, _ = _bmj.bmj_self_join(off, tok, 1, 2)
+    span = lambda x: (x.ctypes.data, x.ctypes.data + x.nbytes)  # noqa: E731
+    lo1, hi1 = min(span(a1)[0], span(b1)[0]), max(span(a1)[1], span(b1)[1])
+    for s0, s1 in (span(a2), span(b2)):
+        assert s1 <= lo1 or s0 >= hi1, "a live list was handed out again"
+    addr2 = a2.ctypes.data
+    del a2, b2  # the last views of the second list: its block goes back to the pool
+    a3, b3, _ = _bmj.bmj_self_join(off, tok, 1, 2)
+    assert a3.ctypes.data == addr2, "the freed block was not reused"
+    assert np.array_equal(a1, keep_a) and np.array_equal(b1, keep_b)
+    assert np.array_equal(a1, ra) and np.array_equal(b1, rb)
+    assert np.array_equal(a3, ra) and np.array_equal(b3, rb)
+
+
 def test_queue_overflow_reruns_exactly():
     off, tok = I.random_collection(4000, 300, 1, 30, seed=8, planted_frac=0.2)
     st = check_join(off, tok, 1, 2, b=64, queue_cap=1)
