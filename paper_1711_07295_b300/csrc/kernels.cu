@@ -10,9 +10,7 @@
 //   k_tiles,
 //   k_window_count   the length filter window j in [j0(i), i) (Table 2; Alg. 6)
 //   k_filter         the Bitmap Filter over every window pair (Alg. 5/6, Eq. 2)
-//   k_verify         exact overlap of the survivors by merge intersection
-//                    (the verification of Alg. 6's host code, moved on the GPU)
-//   k_unpack         canonical output pairs
+// Verification and the output kernels are in verify.cu.
 #include "kernels.cuh"
 #include "filter_core.cuh"
 
@@ -323,91 +321,6 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
     }
 }
 
-// ----------------------------------------------------------------------------
-// Verification: one survivor per thread.  When a second, wider bitmap array is
-// given (cascade), the survivor first meets the Eq. 2 bound again with those
-// bitmaps -- Theorem 1 holds for any b, so this drops no similar pair -- and
-// only pairs that pass it are merged.  The merge of the two sorted token
-// arrays stops as soon as the outcome is decided (the overlap reached need[S],
-// or the remaining tokens cannot reach it).
-__global__ void __launch_bounds__(256)
-    k_verify(const uint2 *__restrict__ queue, int64_t n_surv, const int64_t *__restrict__ soff,
-             const int32_t *__restrict__ stok, const uint32_t *__restrict__ ssz,
-             const uint32_t *__restrict__ perm, const int32_t *__restrict__ need,
-             const int32_t *__restrict__ lim, const uint64_t *__restrict__ bm2, int W2,
-             uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount,
-             unsigned long long *__restrict__ ccount, int nbits) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    unsigned n_passed = 0;
-    for (int64_t base = gw * 32; base < n_surv; base += warps * 32) {
-        const int64_t idx = base + lane;
-        bool similar = false, passed = false;
-        uint64_t key = 0;
-        if (idx < n_surv) {
-            const uint2 pr = queue[idx];
-            const uint32_t si = ssz[pr.x], sj = ssz[pr.y];
-            passed = true;
-            if (bm2) {
-                const uint64_t *a = bm2 + (int64_t)pr.x * W2;
-                const uint64_t *c = bm2 + (int64_t)pr.y * W2;
-                int h = 0;
-                for (int w = 0; w < W2; w++) h += __popcll(a[w] ^ c[w]);
-                passed = h <= lim[si + sj];
-            }
-            if (passed) {
-                const int nd = need[si + sj];
-                const int32_t *x = stok + soff[pr.x];
-                const int32_t *y = stok + soff[pr.y];
-                int a = 0, b = 0, o = 0;
-                const int na = (int)si, nb = (int)sj;
-                while (a < na && b < nb) {
-                    if (o + min(na - a, nb - b) < nd) break;
-                    const int32_t xa = x[a], yb = y[b];
-                    o += (xa == yb);
-                    a += (xa <= yb);
-                    b += (yb <= xa);
-                    if (o >= nd) break;
-                }
-                similar = o >= nd;
-                if (similar) {
-                    const uint64_t u = perm[pr.x], v = perm[pr.y];
-                    key = u < v ? ((u << nbits) | v) : ((v << nbits) | u);
-                }
-            }
-        }
-        n_passed += passed ? 1u : 0u;
-        const unsigned ball = __ballot_sync(kFull, similar);
-        if (ball) {
-            unsigned long long off = 0;
-            if (lane == 0) off = atomicAdd(rcount, (unsigned long long)__popc(ball));
-            off = __shfl_sync(kFull, off, 0);
-            if (similar) keys[off + __popc(ball & ((1u << lane) - 1u))] = key;
-        }
-    }
-    if (ccount) {  // one atomic per block
-        __shared__ unsigned long long block_passed;
-        if (threadIdx.x == 0) block_passed = 0;
-        __syncthreads();
-        const unsigned v = __reduce_add_sync(kFull, n_passed);
-        if (lane == 0 && v) atomicAdd(&block_passed, (unsigned long long)v);
-        __syncthreads();
-        if (threadIdx.x == 0 && block_passed) atomicAdd(ccount, block_passed);
-    }
-}
-
-__global__ void k_unpack(const uint64_t *__restrict__ keys, int64_t n, int nbits,
-                         uint32_t *__restrict__ a, uint32_t *__restrict__ b) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t mask = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint64_t k = keys[i];
-        a[i] = (uint32_t)(k >> nbits);
-        b[i] = (uint32_t)(k & mask);
-    }
-}
-
 unsigned grid_for(int64_t n, int threads, int64_t cap = 148 * 32) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -555,24 +468,6 @@ int launch_filter_tma(const FilterArgs &a, int W, int *err, int num_sms, cudaStr
         case 4: return launch_filter_tma_t<4, kTmaR4, 128>(a, err, num_sms, s);
         default: return launch_filter(a, W, num_sms, s);
     }
-}
-
-int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
-                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need,
-                  const int32_t *lim, const uint64_t *bm2, int W2, uint64_t *keys,
-                  unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
-                  cudaStream_t s) {
-    if (n_surv <= 0) return BMJ_OK;
-    BMJ_LAUNCH(k_verify, grid_for(n_surv, 256, (int64_t)num_sms * 8), 256, 0, s, queue, n_surv,
-               soff, stok, ssz, perm, need, lim, bm2, W2, keys, rcount, ccount, nbits);
-    return BMJ_OK;
-}
-
-int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,
-                  cudaStream_t s) {
-    if (n <= 0) return BMJ_OK;
-    BMJ_LAUNCH(k_unpack, grid_for(n, 256), 256, 0, s, keys, n, nbits, a, b);
-    return BMJ_OK;
 }
 
 }  // namespace bmj
