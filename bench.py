@@ -165,12 +165,16 @@ def profile_traffic(b: int):
 # ----------------------------------------------------------------------------
 # CPU oracle timing (rank 0 only)
 # ----------------------------------------------------------------------------
-def oracle_rate(off, tok, window_by_thr, rows_per_thr: int, seed: int = 0):
+def oracle_rate(off, tok, window_by_thr, rows_per_thr: int, seed: int = 0, windowed=False):
     """Time the oracle on ``rows_per_thr`` sampled rows per threshold and
     extrapolate the full self-join time (each sampled row is scanned against
-    all N sets; the full join verifies N(N-1)/2 pairs, i.e. N/2 per row)."""
+    all N sets; the full join verifies N(N-1)/2 pairs, i.e. N/2 per row).
+    ``windowed``: the row scan with the length filter of Table 2 instead
+    (each row against its two-sided size window; every window pair of the
+    full join is met from both ends, so again half of the rows' sum)."""
     import numpy as np
     import oracle
+    scan = oracle.join_rows_window if windowed else oracle.join_rows
     n = len(off) - 1
     rng = np.random.default_rng(seed)
     # enough rows to occupy every oracle thread (rows are its unit of parallelism)
@@ -180,7 +184,7 @@ def oracle_rate(off, tok, window_by_thr, rows_per_thr: int, seed: int = 0):
     for (p, q) in THRESHOLDS:
         rows = rng.choice(n, size=rows_per_thr, replace=False)
         t0 = time.perf_counter()
-        oracle.join_rows(off, tok, p, q, rows)
+        scan(off, tok, p, q, rows)
         dt = time.perf_counter() - t0
         t_cpu += dt
         t_full += dt / rows_per_thr * (n / 2.0)
@@ -363,16 +367,28 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         win = {thr: per_thr[thr]["window"] for thr in THRESHOLDS}
-        rate, t_full, t_cpu, cores, nrows = oracle_rate(off, tok, win, args.cpu_rows)
-        if t_cpu < args.cpu_seconds / 2:  # calibration run: scale the sample to the target time
-            rows = int(nrows * args.cpu_seconds / max(t_cpu, 1e-3))
-            rows = max(nrows, min(rows, 64 * nrows))
-            rate, t_full, t_cpu2, cores, nrows = oracle_rate(off, tok, win, rows, seed=1)
-            t_cpu = t_cpu2
+
+        def sampled(windowed, budget_s):
+            rate, t_full, t_cpu, cores, nrows = oracle_rate(off, tok, win, args.cpu_rows,
+                                                            windowed=windowed)
+            if t_cpu < budget_s / 2:  # calibration run: scale the sample to the budget
+                rows = int(nrows * budget_s / max(t_cpu, 1e-3))
+                rows = max(nrows, min(rows, 256 * nrows, (len(off) - 1) // 2))
+                rate, t_full, t_cpu, cores, nrows = oracle_rate(off, tok, win, rows, seed=1,
+                                                                windowed=windowed)
+            return rate, t_full, t_cpu, cores, nrows
+
+        rate, t_full, t_cpu, cores, nrows = sampled(False, args.cpu_seconds)
+        w_rate, w_full, w_cpu, _, w_rows = sampled(True, args.cpu_seconds / 3)
         cpu = {"value": round(rate), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{nrows} random rows per threshold scanned against all "
                          f"1,000,000 sets ({t_cpu:.1f} s wall on {cores} threads), extrapolated to the "
-                         f"full join ({t_full:.0f} s per step)"}
+                         f"full join ({t_full:.0f} s per step)",
+               "with_length_filter": {
+                   "value": round(w_rate), "unit": UNIT,
+                   "sample": f"{w_rows} random rows per threshold, each against the sets of its "
+                             f"Table 2 size window ({w_cpu:.1f} s wall), extrapolated to the full "
+                             f"join ({w_full:.0f} s per step)"}}
 
     if rank == 0:
         joins = []

@@ -49,6 +49,8 @@ def lib():
         L.oracle_self_join.restype = i64
         L.oracle_join_rows.argtypes = [i64, i64p, i32p, i64, i64, i64p, i64, u32pp, u32pp]
         L.oracle_join_rows.restype = i64
+        L.oracle_join_rows_window.argtypes = [i64, i64p, i32p, i64, i64, i64p, i64, u32pp, u32pp]
+        L.oracle_join_rows_window.restype = i64
         L.oracle_search.argtypes = [i32p, i64, i64, i64p, i32p, i64, i64, C.POINTER(i64p)]
         L.oracle_search.restype = i64
         L.oracle_bitmap.argtypes = [i32p, i64, C.c_int, C.c_int, u64p]
@@ -129,6 +131,15 @@ def join_rows(offsets, tokens, p: int, q: int, rows):
     return _take_pairs(n, A, B)
 
 
+def join_rows_window(offsets, tokens, p: int, q: int, rows):
+    """join_rows with the length filter (Table 2): same output, fewer pairs verified."""
+    off, tok, r = _i64(offsets), _i32(tokens), _i64(rows)
+    A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
+    n = lib().oracle_join_rows_window(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p,
+                                      q, _p(r, C.c_int64), len(r), C.byref(A), C.byref(B))
+    return _take_pairs(n, A, B)
+
+
 def search(probe, offsets, tokens, p: int, q: int):
     """Ids of the collection's sets with Jaccard(probe, s) >= p/q, ascending."""
     x, off, tok = _i32(probe), _i64(offsets), _i32(tokens)
@@ -189,5 +200,5 @@ def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int):
 
 
 __all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "overlap", "similar", "self_join",
-           "join_rows", "search", "bitmap", "bitmaps", "hamming", "upper_bound",
+           "join_rows", "join_rows_window", "search", "bitmap", "bitmaps", "hamming", "upper_bound",
            "filter_counts", "combined_method", "num_threads", "lib"]

@@ -27,6 +27,7 @@
  *   oracle_similar        the integer Jaccard test above
  *   oracle_self_join      Alg. 1 over all pairs a<b, no filter at all
  *   oracle_join_rows      Alg. 1 restricted to pairs touching sampled rows
+ *   oracle_join_rows_window  the same with the length filter of Table 2
  *   oracle_search         one probe set against every set of a collection
  *   oracle_bitmap         Alg. 3a (Set), 3b (Xor), 3c (Next), literally
  *   oracle_filter_counts  the GPU algorithm (Alg. 6): size order, length
@@ -185,6 +186,96 @@ int64_t oracle_join_rows(int64_t n, const int64_t *off, const int32_t *tok,
             }
         }
     }
+    int64_t total = 0;
+    for (int64_t t = 0; t < k; t++) total += per[t].n;
+    uint64_t *keys = NULL;
+    if (!failed && total > 0) {
+        keys = (uint64_t *)malloc((size_t)total * sizeof(uint64_t));
+        if (!keys) failed = 1;
+    }
+    int64_t m = 0;
+    for (int64_t t = 0; t < k; t++) {
+        for (int64_t i = 0; !failed && i < per[t].n; i++)
+            keys[m++] = ((uint64_t)per[t].a[i] << 32) | per[t].b[i];
+        free(per[t].a);
+        free(per[t].b);
+    }
+    free(per);
+    if (failed) { free(keys); return -1; }
+    if (total == 0) return 0;
+    qsort(keys, (size_t)total, sizeof(uint64_t), cmp_pair64);
+    int64_t u = 0;
+    for (int64_t i = 0; i < total; i++)
+        if (i == 0 || keys[i] != keys[i - 1]) keys[u++] = keys[i];
+    uint32_t *A = (uint32_t *)malloc((size_t)u * sizeof(uint32_t));
+    uint32_t *B = (uint32_t *)malloc((size_t)u * sizeof(uint32_t));
+    if (!A || !B) { free(A); free(B); free(keys); return -1; }
+    for (int64_t i = 0; i < u; i++) {
+        A[i] = (uint32_t)(keys[i] >> 32);
+        B[i] = (uint32_t)(keys[i] & 0xffffffffu);
+    }
+    free(keys);
+    *out_a = A;
+    *out_b = B;
+    return u;
+}
+
+/*
+ * oracle_join_rows with the length filter (Section 2.3.2, Table 2, Jaccard
+ * row): a sampled row r is verified only against the sets s whose size lies
+ * in [ceil(p|r|/q), floor(q|r|/p)] -- outside that range J(r,s) < p/q for
+ * any contents, so the output equals oracle_join_rows'.  The sets are
+ * visited through size buckets built once per call (a counting sort of the
+ * ids by size).  It exists to time the plain join with the paper's cheapest
+ * filter beside the plain definition.
+ */
+int64_t oracle_join_rows_window(int64_t n, const int64_t *off, const int32_t *tok,
+                                int64_t p, int64_t q, const int64_t *rows, int64_t k,
+                                uint32_t **out_a, uint32_t **out_b)
+{
+    *out_a = NULL;
+    *out_b = NULL;
+    if (k <= 0 || n <= 1) return 0;
+    int64_t max_size = 0;
+    for (int64_t s = 0; s < n; s++)
+        if (off[s + 1] - off[s] > max_size) max_size = off[s + 1] - off[s];
+    /* bucket[z] .. bucket[z+1]-1: positions in by_size of the sets of size z */
+    int64_t *bucket = (int64_t *)calloc((size_t)max_size + 2, sizeof(int64_t));
+    int64_t *by_size = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    pairbuf *per = (pairbuf *)calloc((size_t)k, sizeof(pairbuf));
+    if (!bucket || !by_size || !per) { free(bucket); free(by_size); free(per); return -1; }
+    for (int64_t s = 0; s < n; s++) bucket[off[s + 1] - off[s] + 1]++;
+    for (int64_t z = 0; z <= max_size; z++) bucket[z + 1] += bucket[z];
+    {
+        int64_t *fill = (int64_t *)malloc((size_t)(max_size + 1) * sizeof(int64_t));
+        if (!fill) { free(bucket); free(by_size); free(per); return -1; }
+        memcpy(fill, bucket, (size_t)(max_size + 1) * sizeof(int64_t));
+        for (int64_t s = 0; s < n; s++) by_size[fill[off[s + 1] - off[s]]++] = s;
+        free(fill);
+    }
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t t = 0; t < k; t++) {
+        int64_t r = rows[t];
+        const int32_t *xr = tok + off[r];
+        int64_t nr = off[r + 1] - off[r];
+        int64_t lo = (p * nr + q - 1) / q;    /* ceil(p|r|/q) */
+        int64_t hi = (q * nr) / p;            /* floor(q|r|/p) */
+        if (hi > max_size) hi = max_size;
+        for (int64_t z = lo; z <= hi; z++) {
+            for (int64_t x = bucket[z]; x < bucket[z + 1]; x++) {
+                int64_t s = by_size[x];
+                if (s == r) continue;
+                int64_t o = oracle_overlap(xr, nr, tok + off[s], z);
+                if (oracle_similar(o, nr, z, p, q)) {
+                    uint32_t a = (uint32_t)(r < s ? r : s), b = (uint32_t)(r < s ? s : r);
+                    if (pb_push(&per[t], a, b)) failed = 1;
+                }
+            }
+        }
+    }
+    free(bucket);
+    free(by_size);
     int64_t total = 0;
     for (int64_t t = 0; t < k; t++) total += per[t].n;
     uint64_t *keys = NULL;

@@ -140,6 +140,28 @@ def test_join_rows_and_search_against_brute_force():
     a, b = O.join_rows(off, tok, p, q, rows)
     got = list(zip(a.tolist(), b.tolist()))
     assert got == sorted({pr for pr in full if pr[0] in rows or pr[1] in rows})
+    a2, b2 = O.join_rows_window(off, tok, p, q, rows)
+    assert list(zip(a2.tolist(), b2.tolist())) == got
+
+
+@pytest.mark.parametrize("p,q", [(1, 2), (3, 5), (9, 10), (1, 1), (1, 7)])
+def test_length_filtered_rows_against_brute_force(p, q):
+    # Table 2's size window only drops pairs that cannot be similar: the windowed row
+    # scan returns exactly the brute-force pairs of the sampled rows (sizes 1..25, so
+    # windows are cut at both ends and at the largest size).
+    off, tok = I.random_collection(400, 60, 1, 25, seed=p * 31 + q, planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    full = set(_brute_pairs(sets, p, q))
+    rows = list(range(0, 400, 7)) + [399]
+    a, b = O.join_rows_window(off, tok, p, q, rows)
+    assert list(zip(a.tolist(), b.tolist())) == sorted(
+        {pr for pr in full if pr[0] in rows or pr[1] in rows})
+
+
+def test_search_against_brute_force():
+    off, tok = I.random_collection(300, 40, 1, 12, seed=3, planted_frac=0.1)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    p, q = 1, 2
     probe = sets[17]
     ids = O.search(probe, off, tok, p, q)
     want = [s for s in range(len(sets))
