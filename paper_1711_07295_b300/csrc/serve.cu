@@ -9,6 +9,9 @@
 // A batch of probes runs as:
 //   probe bitmaps + windows -> work items (probe, column chunk) -> filter ->
 //   verification -> sort by (probe, id) -> per-probe id lists.
+// The counters and the first 2048 result keys come back together; a batch
+// with no more results than that is sorted on the host (one round trip), a
+// larger one is radix-sorted on the device in a second phase.
 // Every batch has its own slot (stream, pinned staging, fixed device buffers),
 // so several batches are in flight at once and overlap on the device.
 //
@@ -44,6 +47,8 @@ namespace {
 
 constexpr unsigned kFullQ = 0xffffffffu;
 constexpr int kQueryChunk = 1024;
+// Result keys copied back with a batch's counters (16 KB).
+constexpr int64_t kEagerKeys = 2048;
 
 __device__ __forceinline__ int64_t lb_sizes(const uint32_t *a, int64_t n, uint64_t v) {
     int64_t lo = 0, hi = n;
@@ -318,9 +323,29 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
                s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
                &s.d_ctr[1]);
     BMJ_CHECK(cudaMemcpyAsync(s.h_ctr, s.d_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    // the first keys come back with the counters: a batch with few results then
+    // finishes on the host without a second round trip (finish_on_host)
+    BMJ_CHECK(cudaMemcpyAsync(s.h_keys, s.d_keys, std::min(s.pair_cap, kEagerKeys) * sizeof(uint64_t),
+                              cudaMemcpyDeviceToHost, st));
     BMJ_CHECK(cudaEventRecord(s.done, st));
     A.release();
     return BMJ_OK;
+}
+
+// After phase 1: a batch whose results all came back with its counters is
+// sorted by (probe, id) on the host and gets its per-probe bounds there.
+// Returns false when the batch has more results than that (phase 2 sorts them
+// on the device).
+bool finish_on_host(Slot &s) {
+    const int64_t nres = (int64_t)s.h_ctr[1];
+    if (nres > std::min(s.pair_cap, kEagerKeys)) return false;
+    std::sort(s.h_keys, s.h_keys + nres);
+    int64_t r = 0;
+    for (int64_t k = 0; k <= s.nq; k++) {
+        while (r < nres && (int64_t)(s.h_keys[r] >> 32) < k) r++;
+        s.h_bounds[k] = r;
+    }
+    return true;
 }
 
 // Phase 2: sort the results by (probe, id), per-probe bounds, copy out.
@@ -548,12 +573,18 @@ static int serve_impl(bmj_index *idx, const bmj_collection *qc, const double *ar
                 break;
             }
             progressed = true;
+            bool finished = s.phase == 2;
             if (s.phase == 1) {
                 total_surv += (int64_t)s.h_ctr[0];
                 total_res += (int64_t)s.h_ctr[1];
-                rc = launch_phase2(s);
-                s.phase = 2;
-            } else {
+                if (finish_on_host(s)) {
+                    finished = true;
+                } else {
+                    rc = launch_phase2(s);
+                    s.phase = 2;
+                }
+            }
+            if (finished) {
                 const double t_done = now_s();
                 for (int64_t k = 0; k < s.nq; k++) {
                     const int64_t x = s.ids[k];
