@@ -62,6 +62,8 @@ def parse_args():
                     help="target wall time of the CPU baseline's sample (rows are scaled to it)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-joins comparison (512 jobs)")
+    ap.add_argument("--no-10m", action="store_true",
+                    help="skip the 10,000,000-set joins (b = 128, thresholds 3/5 and 9/10)")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the served-queries measurement (2,000,000 resident sets)")
     ap.add_argument("--shard", choices=("replicas", "bands"), default="replicas",
@@ -140,7 +142,7 @@ class ClockSampler:
 def filter_source_digest() -> str:
     """sha256[:16] of the sources the filter kernel is built from."""
     h = hashlib.sha256()
-    for name in ("filter_core.cuh", "kernels.cuh", "kernels.cu"):
+    for name in ("filter_core.cuh", "kernels.cuh", "filter.cu"):
         with open(os.path.join(ROOT, "paper_1711_07295_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -356,6 +358,13 @@ def run_ours(args):
         except Exception as e:  # reported, never fatal to the headline line
             batched = {"error": f"{type(e).__name__}: {e}"}
 
+    ten_m = None
+    if not args.no_10m:
+        try:
+            ten_m = run_ten_million(args, dev)
+        except Exception as e:  # reported, never fatal to the headline line
+            ten_m = {"error": f"{type(e).__name__}: {e}"}
+
     served = None
     if not args.no_served:
         try:
@@ -418,6 +427,8 @@ def run_ours(args):
             out["sweep_b"] = sweep
         if batched:
             out["batched"] = batched
+        if ten_m:
+            out["ten_million"] = ten_m
         if served:
             out["served"] = served
         print(json.dumps(out), flush=True)
@@ -489,6 +500,38 @@ def run_batched(args, dev):
             "graph": int(last["graph"]), "launches": int(last["n_launches"]),
             "filter_passes": int(last["filter_passes"]),
             "generation_s": round(gen_s, 2)}
+
+
+def run_ten_million(args, dev):
+    """The 10,000,000-set workload (Zipf(1.0) over 1,000,000 tokens, sizes
+    lognormal(2.0,0.8) in [1,1000], CSR in HBM) joined at 3/5 and 9/10 with
+    b = 128: one untimed join, then each threshold once (CUDA-event stage
+    times reported by the library)."""
+    import torch
+    from paper_1711_07295_b300 import _bmj, inputs
+    t0 = time.perf_counter()
+    off, tok = inputs.gen_collection_device(inputs.spec_10m(), device=dev)
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    r, _, _ = _bmj.bmj_self_join(off, tok, 9, 10, b=128, output_on_device=True,
+                                 stream=stream.cuda_stream)
+    r.release()
+    out = []
+    for p, q in ((3, 5), (9, 10)):
+        r, _, st = _bmj.bmj_self_join(off, tok, p, q, b=128, output_on_device=True,
+                                      stream=stream.cuda_stream)
+        r.release()
+        out.append({"threshold": f"{p}/{q}", "window_pairs": st["window_pairs"],
+                    "survivors": st["survivors"], "results": st["results"],
+                    "join_ms": round(st["ms_total"], 2), "filter_ms": round(st["ms_filter"], 2),
+                    "verify_ms": round(st["ms_verify"], 2),
+                    "pairs_per_s": round(st["window_pairs"] / (st["ms_total"] / 1e3)),
+                    "filter_pairs_per_s": round(st["window_pairs"] / (st["ms_filter"] / 1e3))})
+    del off, tok
+    torch.cuda.empty_cache()
+    return {"workload": "self-join of 10,000,000 sets, tokens Zipf(s=1.0) over 1,000,000, sizes "
+                        "lognormal(mu=2.0,sigma=0.8) clipped to [1,1000], b = 128, inputs in HBM",
+            "joins": out, "generation_s": round(gen_s, 2)}
 
 
 def run_served(args, dev):

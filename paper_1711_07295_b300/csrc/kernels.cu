@@ -1,4 +1,4 @@
-// kernels.cu -- device kernels of the Bitmap Filter self-join.
+// kernels.cu -- preparation kernels of the Bitmap Filter self-join.
 //
 // Stages (each cited where it is defined in the paper):
 //   k_validate       CSR invariants; sizes and ids for the size sort (Section 5
@@ -7,12 +7,11 @@
 //                    h(t) = t mod b as in Section 5.1)
 //   k_tables         need[S] / lim[S]: Jaccard as an overlap threshold (Table 1)
 //                    folded into the Eq. 2 test
+//   k_build_multi    the same for 64-, 128- and 256-bit Xor/Set bitmaps in one pass
 //   k_tiles,
 //   k_window_count   the length filter window j in [j0(i), i) (Table 2; Alg. 6)
-//   k_filter         the Bitmap Filter over every window pair (Alg. 5/6, Eq. 2)
-// Verification and the output kernels are in verify.cu.
+// The Bitmap Filter is in filter.cu, verification and output in verify.cu.
 #include "kernels.cuh"
-#include "filter_core.cuh"
 
 namespace bmj {
 namespace {
@@ -143,28 +142,33 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
     }
 }
 
-// One thread per set: gathers the set's tokens into the sorted CSR (when stok
-// is given) and writes its Xor (Alg. 3b) or Set (Alg. 3a) bitmaps for up to
-// three widths at once (64, 128, 256 bits; a null output skips a width).
-// With b a power of two, h(t) = t mod b selects word (t mod b) / 64 and bit
-// t mod 64 for all three widths.
+// One thread per set: writes its Xor (Alg. 3b) or Set (Alg. 3a) bitmaps for
+// up to three widths at once (64, 128, 256 bits; a null output skips a
+// width).  With b a power of two, h(t) = t mod b selects word (t mod b) / 64
+// and bit t mod 64 for all three widths.  When stok is given the warp then
+// gathers its 32 sets' tokens into the sorted CSR together, one set at a
+// time with consecutive lanes on consecutive tokens, so that the writes are
+// whole sectors (per-thread writes left partial sectors that DRAM had to
+// merge, doubling the traffic).
 __global__ void __launch_bounds__(256)
     k_build_multi(const uint32_t *__restrict__ perm, const int64_t *__restrict__ off,
                   const int32_t *__restrict__ tok, const int64_t *__restrict__ soff,
                   int32_t *__restrict__ stok, int64_t n, int method, uint64_t *__restrict__ bm64,
                   uint64_t *__restrict__ bm128, uint64_t *__restrict__ bm256) {
     const bool xr = method == BMJ_XOR;
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t src = perm ? (int64_t)perm[i] : i;
-        const int64_t lo = off[src];
-        const int64_t cnt = off[src + 1] - lo;
+    // whole warps iterate together (the gather below is warp-wide)
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const int64_t i = i0 + lane;
+        const bool live = i < n;
+        const int64_t src = live ? (perm ? (int64_t)perm[i] : i) : 0;
+        const int64_t lo = live ? off[src] : 0;
+        const int64_t cnt = live ? off[src + 1] - lo : 0;
         const int32_t *x = tok + lo;
-        int32_t *y = stok ? stok + soff[i] : nullptr;
         uint64_t a = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0;
         for (int64_t k = 0; k < cnt; k++) {
             const uint32_t t = (uint32_t)x[k];
-            if (y) y[k] = (int32_t)t;
             const uint64_t bit = 1ull << (t & 63u);
             const uint32_t w2 = (t >> 6) & 1u, w4 = (t >> 6) & 3u;
             if (xr) {
@@ -185,16 +189,28 @@ __global__ void __launch_bounds__(256)
                 c3 |= w4 == 3 ? bit : 0ull;
             }
         }
-        if (bm64) bm64[i] = a;
-        if (bm128) {
-            bm128[2 * i] = b0;
-            bm128[2 * i + 1] = b1;
+        if (live) {
+            if (bm64) bm64[i] = a;
+            if (bm128) {
+                bm128[2 * i] = b0;
+                bm128[2 * i + 1] = b1;
+            }
+            if (bm256) {
+                bm256[4 * i] = c0;
+                bm256[4 * i + 1] = c1;
+                bm256[4 * i + 2] = c2;
+                bm256[4 * i + 3] = c3;
+            }
         }
-        if (bm256) {
-            bm256[4 * i] = c0;
-            bm256[4 * i + 1] = c1;
-            bm256[4 * i + 2] = c2;
-            bm256[4 * i + 3] = c3;
+        if (stok) {
+            const int64_t dst = live ? soff[i] : 0;
+            const int nl = (int)min((int64_t)32, n - i0);
+            for (int l = 0; l < nl; l++) {
+                const int64_t lo_l = __shfl_sync(kFull, lo, l);
+                const int64_t cnt_l = __shfl_sync(kFull, cnt, l);
+                const int64_t dst_l = __shfl_sync(kFull, dst, l);
+                for (int64_t k = lane; k < cnt_l; k += 32) stok[dst_l + k] = tok[lo_l + k];
+            }
         }
     }
 }
@@ -241,105 +257,11 @@ __global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, uint
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
-// ----------------------------------------------------------------------------
-// Bitmap Filter (per-item body in filter_core.cuh).  Warps pull work items
-// (row tile, column chunk) from a global counter: a persistent grid that
-// balances the uneven band of the size-sorted triangle.
-template <int W, int R>
-__global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
-    const int lane = threadIdx.x & 31;
-    const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
-        item = __shfl_sync(kFull, item, 0);
-        if ((int64_t)item >= a.n_items) return;
-        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
-        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
-        const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
-        const int64_t i0 = a.row0 + t * a.tile_rows;
-        const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
-        const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item<W, R>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, sink);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int W) {
-    const int lane = threadIdx.x & 31;
-    const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
-        item = __shfl_sync(kFull, item, 0);
-        if ((int64_t)item >= a.n_items) return;
-        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
-        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
-        const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
-        const int64_t i0 = a.row0 + t * a.tile_rows;
-        const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
-        const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_generic(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, W, sink);
-    }
-}
-
-// Bitmap Filter with TMA-staged columns (filter_item_tma).  Each warp owns a
-// double buffer of column chunks in dynamic shared memory and its two
-// mbarriers; a wait that gives up sets *err and stops the warp.
-template <int W, int R, int CS, bool kFault>
-__global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    using L = ColStage<W, CS>;
-    const int lane = threadIdx.x & 31;
-    StageState st;
-    init_stage(st, smem + (threadIdx.x >> 5) * L::kWarpBytes);
-    if (kFault) {  // fault injection: the first warp skips its first copy; short waits
-        st.wait_limit = a.wait_limit;
-        st.skip_copy = (blockIdx.x == 0 && threadIdx.x < 32) ? 1 : 0;
-    }
-    const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
-        item = __shfl_sync(kFull, item, 0);
-        if ((int64_t)item >= a.n_items) break;
-        const int64_t t = find_tile(a.tile_item_off, a.n_tiles, item);
-        const int64_t chunk = (int64_t)item - a.tile_item_off[t];
-        const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
-        const int64_t i0 = a.row0 + t * a.tile_rows;
-        const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
-        const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0)>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1,
-                                                             a.p, a.q, sink, st);
-        if (!st.ok) {
-            drain_stage(st);
-            if (lane == 0) atomicOr(err, 1);
-            break;
-        }
-    }
-}
-
 unsigned grid_for(int64_t n, int threads, int64_t cap = 148 * 32) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
     if (g > cap) g = cap;
     return (unsigned)g;
-}
-
-template <int W, int R>
-int launch_filter_t(const FilterArgs &a, int num_sms, cudaStream_t s) {
-    int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<W, R>, 256, 0));
-    if (per_sm < 1) per_sm = 1;
-    int64_t warps_needed = a.n_items;
-    int64_t blocks = (int64_t)num_sms * per_sm;
-    const int64_t need_blocks = (warps_needed + 7) / 8;
-    if (need_blocks < blocks) blocks = need_blocks;
-    if (blocks < 1) blocks = 1;
-    BMJ_LAUNCH((k_filter<W, R>), (unsigned)blocks, 256, 0, s, a);
-    return BMJ_OK;
 }
 
 }  // namespace
@@ -398,76 +320,6 @@ int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
     BMJ_LAUNCH(k_window_count, grid_for(row_end - row0, 256), 256, 0, s, ssz, n, p, q, out, row0,
                row_end);
     return BMJ_OK;
-}
-
-int filter_tile_rows(int W) {
-    switch (W) {
-        case 1: case 2: case 4: return 32 * 4;
-        case 8: return 32 * 2;
-        default: return 32;
-    }
-}
-
-int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s) {
-    if (a.n_items <= 0) return BMJ_OK;
-    switch (W) {
-        case 1: return launch_filter_t<1, 4>(a, num_sms, s);
-        case 2: return launch_filter_t<2, 4>(a, num_sms, s);
-        case 4: return launch_filter_t<4, 4>(a, num_sms, s);
-        case 8: return launch_filter_t<8, 2>(a, num_sms, s);
-        default: {
-            int per_sm = 0;
-            BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_generic, 256, 0));
-            if (per_sm < 1) per_sm = 1;
-            int64_t blocks = (int64_t)num_sms * per_sm;
-            const int64_t need_blocks = (a.n_items + 7) / 8;
-            if (need_blocks < blocks) blocks = need_blocks;
-            if (blocks < 1) blocks = 1;
-            BMJ_LAUNCH(k_filter_generic, (unsigned)blocks, 256, 0, s, a, W);
-            return BMJ_OK;
-        }
-    }
-}
-
-template <int W, int R, int CS, bool kFault>
-int launch_filter_tma_k(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
-    using L = ColStage<W, CS>;
-    const int smem = 4 * L::kWarpBytes;
-    int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tma<W, R, CS, kFault>,
-                                                            128, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (int64_t)num_sms * per_sm;
-    const int64_t need_blocks = (a.n_items + 3) / 4;
-    if (need_blocks < blocks) blocks = need_blocks;
-    if (blocks < 1) blocks = 1;
-    BMJ_LAUNCH((k_filter_tma<W, R, CS, kFault>), (unsigned)blocks, 128, smem, s, a, err);
-    return BMJ_OK;
-}
-
-template <int W, int R, int CS>
-int launch_filter_tma_t(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
-    return a.fault_skip_copy ? launch_filter_tma_k<W, R, CS, true>(a, err, num_sms, s)
-                             : launch_filter_tma_k<W, R, CS, false>(a, err, num_sms, s);
-}
-
-int filter_tma_tile_rows(int W) {
-    switch (W) {
-        case 1: return 32 * kTmaR1;
-        case 2: return 32 * kTmaR2;
-        case 4: return 32 * kTmaR4;
-        default: return filter_tile_rows(W);
-    }
-}
-
-int launch_filter_tma(const FilterArgs &a, int W, int *err, int num_sms, cudaStream_t s) {
-    if (a.n_items <= 0) return BMJ_OK;
-    switch (W) {
-        case 1: return launch_filter_tma_t<1, kTmaR1, 256>(a, err, num_sms, s);
-        case 2: return launch_filter_tma_t<2, kTmaR2, 256>(a, err, num_sms, s);
-        case 4: return launch_filter_tma_t<4, kTmaR4, 128>(a, err, num_sms, s);
-        default: return launch_filter(a, W, num_sms, s);
-    }
 }
 
 }  // namespace bmj
