@@ -62,6 +62,8 @@ def parse_args():
                     help="target wall time of the CPU baseline's sample (rows are scaled to it)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-joins comparison (512 jobs)")
+    ap.add_argument("--no-combined", action="store_true",
+                    help="skip the step with Alg. 4's generation function per threshold")
     ap.add_argument("--no-10m", action="store_true",
                     help="skip the 10,000,000-set joins (b = 128, thresholds 3/5 and 9/10)")
     ap.add_argument("--no-served", action="store_true",
@@ -220,14 +222,14 @@ def run_ours(args):
         for (p, q) in THRESHOLDS:
             bands[(p, q)] = shard.band_split(off, p, q, world)[rank]
 
-    def join(p, q, b, cap=0, host=False):
+    def join(p, q, b, cap=0, host=False, method=_bmj.BMJ_XOR):
         r0, r1 = bands.get((p, q), (0, 0))
         if host:
             return _bmj.bmj_self_join(host_coll["off"], host_coll["tok"], p, q, b=b,
-                                      queue_cap=cap, row_begin=r0, row_end=r1)
+                                      queue_cap=cap, row_begin=r0, row_end=r1, method=method)
         res, _, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True,
                                         queue_cap=cap, stream=stream.cuda_stream,
-                                        row_begin=r0, row_end=r1)
+                                        row_begin=r0, row_end=r1, method=method)
         res.release()
         return st
 
@@ -336,6 +338,30 @@ def run_ours(args):
                "ms_per_step": round(e2e_s * 1e3 / args.steps, 3),
                "inputs": "pinned host CSR, copied by the library each call"}
 
+    # ---- the same step with Alg. 4's choice of generation function ----
+    # (the paper's GPU runs use Bitmap-Xor, as the headline does; Alg. 4 picks
+    # Bitmap-Set at 1/2, which leaves fewer survivors for verification)
+    combined = None
+    if not args.no_combined:
+        ccaps = {}
+        for thr in THRESHOLDS:
+            st = join(thr[0], thr[1], b, method=_bmj.BMJ_COMBINED)
+            ccaps[thr] = max(1, st["survivors"])
+        flush.fill_(7)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        surv, meth = {}, {}
+        for thr in THRESHOLDS:
+            st = join(thr[0], thr[1], b, ccaps[thr], method=_bmj.BMJ_COMBINED)
+            surv[f"{thr[0]}/{thr[1]}"] = st["survivors"]
+            meth[f"{thr[0]}/{thr[1]}"] = ("xor", "set", "next")[st["method"]]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        c_ms = ev0.elapsed_time(ev1)
+        combined = {"method": meth, "ms_per_step": round(c_ms, 3),
+                    "value": round(window_per_step / (c_ms / 1e3)), "unit": UNIT,
+                    "survivors": surv, "steps": 1}
+
     # ---- optional b sweep (outside the headline) ----
     sweep = None
     if args.sweep:
@@ -425,6 +451,8 @@ def run_ours(args):
                "gpu_launches": int(launches), "clocks": clk, "joins": joins}
         if sweep:
             out["sweep_b"] = sweep
+        if combined:
+            out["combined_method"] = combined
         if batched:
             out["batched"] = batched
         if ten_m:

@@ -307,6 +307,12 @@ void bmj_id_lists_free(bmj_id_lists *lists);
  * Safe on an empty or already freed list. */
 void bmj_pairs_free(bmj_pairs *pairs);
 
+/* Gives every idle page-locked block of the library's reuse pool back to the
+ * CUDA driver and returns the number of bytes released.  Lists still held by
+ * the caller are untouched (they return to the pool when freed).  Calls no
+ * CUDA function when the pool is empty. */
+int64_t bmj_host_pool_trim(void);
+
 /* Number of CUDA kernels this library has launched in this process (a
  * monotone counter, for accounting in benchmarks). */
 int64_t bmj_kernel_launches(void);

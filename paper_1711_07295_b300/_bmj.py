@@ -152,6 +152,7 @@ SIGNATURES = {
                             C.c_void_p, C.POINTER(bmj_serve_stats)]),
     "bmj_id_lists_free": (None, [C.POINTER(bmj_id_lists)]),
     "bmj_kernel_launches": (C.c_int64, []),
+    "bmj_host_pool_trim": (C.c_int64, []),
     "bmj_bitmap_filter_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_uint32,
                                             C.c_uint32, C.c_void_p, C.c_int64,
                                             C.POINTER(C.c_int64), C.c_void_p]),
@@ -229,6 +230,11 @@ def bmj_strerror(status: int) -> str:
 
 def bmj_kernel_launches() -> int:
     return int(lib().bmj_kernel_launches())
+
+
+def bmj_host_pool_trim() -> int:
+    """Releases the idle page-locked blocks the library keeps for host pair lists (bytes freed)."""
+    return int(lib().bmj_host_pool_trim())
 
 
 def bmj_build_bitmaps(offsets, tokens, b: int = 64, method: int = BMJ_XOR, out=None,

@@ -96,7 +96,7 @@ struct Arena {
 void retain_pool_memory(int device);
 
 // Page-locked host blocks reused between calls (host_pool.cu).  pinned_alloc
-// returns nullptr when the driver refuses; pinned_release returns false for a
+// returns nullptr when the CUDA driver refuses; pinned_release returns false for a
 // pointer that is not a live block of the pool.
 void *pinned_alloc(size_t bytes);
 bool pinned_release(void *p);

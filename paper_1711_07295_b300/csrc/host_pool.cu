@@ -3,9 +3,9 @@
 // Pinning pages costs about as much time per byte as copying them over the
 // link, so a pair list returned in page-locked memory goes back to this pool
 // when it is freed and the next call with a result of similar size takes it
-// again instead of asking the driver.  Blocks in use are never handed out; the
+// again instead of asking the CUDA driver.  Blocks in use are never handed out; the
 // pool keeps at most kMaxFree idle blocks and kMaxFreeBytes idle bytes and
-// gives the oldest idle blocks back to the driver beyond that.
+// gives the oldest idle blocks back to the CUDA driver beyond that.
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -31,7 +31,7 @@ struct Pool {
     size_t idle_bytes = 0;
 };
 
-// Never destroyed: at process exit the driver reclaims the pages, and a
+// Never destroyed: at process exit the CUDA driver reclaims the pages, and a
 // destructor running after the CUDA runtime has shut down must not free them.
 Pool &pool() {
     static Pool *p = new Pool();
@@ -95,3 +95,19 @@ bool pinned_release(void *p) {
 }
 
 }  // namespace bmj
+
+extern "C" int64_t bmj_host_pool_trim(void) {
+    bmj::Pool &P = bmj::pool();
+    std::vector<bmj::Block> drop;
+    {
+        std::lock_guard<std::mutex> g(P.mu);
+        drop.swap(P.idle);
+        P.idle_bytes = 0;
+    }
+    int64_t bytes = 0;
+    for (const auto &b : drop) {
+        cudaFreeHost(b.ptr);
+        bytes += (int64_t)b.cap;
+    }
+    return bytes;
+}

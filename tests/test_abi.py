@@ -36,6 +36,11 @@ def test_library_exports_every_declared_symbol():
         assert name in _bmj.SIGNATURES, f"binding lacks {name}"
 
 
+def test_host_pool_trim_on_an_empty_pool():
+    # nothing has been returned to the pool in this process on the CPU: no CUDA call is made
+    assert _bmj.bmj_host_pool_trim() == 0
+
+
 def test_strerror_and_defaults():
     assert _bmj.bmj_strerror(0) == "ok"
     for code in range(-9, 0):

@@ -117,6 +117,11 @@ def test_pooled_host_lists_are_reused_without_aliasing():
     assert np.array_equal(a1, keep_a) and np.array_equal(b1, keep_b)
     assert np.array_equal(a1, ra) and np.array_equal(b1, rb)
     assert np.array_equal(a3, ra) and np.array_equal(b3, rb)
+    # trimming frees idle blocks only: the held lists stay valid
+    del a3, b3
+    assert _bmj.bmj_host_pool_trim() > 0
+    assert _bmj.bmj_host_pool_trim() == 0
+    assert np.array_equal(a1, keep_a) and np.array_equal(b1, keep_b)
 
 
 def test_queue_overflow_reruns_exactly():
