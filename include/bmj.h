@@ -99,7 +99,13 @@ typedef struct {
     int32_t method;            /* BMJ_XOR (default) / SET / NEXT / COMBINED */
     int32_t output_on_device;  /* 1: pairs returned in device memory; 0 (default): host memory */
     int32_t validate;          /* 1 (default): check the collection invariants on the device */
-    int64_t queue_cap;         /* survivor-queue capacity in pairs; 0 (default) = automatic */
+    int64_t queue_cap;         /* survivor-queue capacity in pairs; 0 (default) = automatic.
+                                  bmj_self_join never drops a survivor: when they exceed the
+                                  queue, an automatic queue is regrown to the exact count if
+                                  that fits in a quarter of free memory; otherwise (and always
+                                  for a caller-given capacity) the filter's work items run in
+                                  consecutive ranges whose survivors fit, each verified before
+                                  the next (stats.filter_passes counts the passes) */
     void   *stream;            /* cudaStream_t; NULL = legacy default stream */
     int32_t rows_per_thread;   /* filter register blocking: 0 = automatic */
     int32_t use_graph;         /* bmj_self_join_batch: run the execute stage as a CUDA graph */

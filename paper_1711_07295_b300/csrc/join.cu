@@ -5,6 +5,7 @@
 //   Bitmap Filter -> exact verification -> canonical result sort -> output.
 // The host reads back three small counters (validation flags and maximum
 // size; survivor count; result count), which size the next allocations.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -192,8 +193,14 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         stl.window_pairs = hv[0];
         const int64_t n_items = hv[1];
 
-        // ---- Bitmap Filter ----
-        int64_t qcap = o.queue_cap > 0 ? o.queue_cap : auto_queue_cap(stl.window_pairs);
+        // ---- Bitmap Filter + exact verification ----
+        // The filter's queue counts every survivor, also past its capacity.  When
+        // the first pass over all work items overflows, the filter reruns with
+        // exact room if that fits (automatic capacity), else the items run in
+        // consecutive ranges whose survivors fit the queue, each verified before
+        // the next; no pair is ever dropped.
+        const bool user_cap = o.queue_cap > 0;
+        int64_t qcap = user_cap ? o.queue_cap : auto_queue_cap(stl.window_pairs);
         uint2 *queue = nullptr;
         st = A.alloc(&queue, (size_t)qcap);
         if (st) return st;
@@ -220,47 +227,125 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             fa.fault_skip_copy = 1;
             fa.wait_limit = 1 << 12;
         }
-        int64_t n_surv = 0;
-        for (int pass = 0; pass < 2; pass++) {
+        // Filters work items [lo, hi) into the queue; *count = their survivors.
+        auto run_filter = [&](int64_t lo, int64_t hi, int64_t *count) -> int {
+            const unsigned long long init[2] = {0ull, (unsigned long long)lo};
+            BMJ_CHECK(cudaMemcpyAsync(&ctr[1], init, sizeof(init), cudaMemcpyHostToDevice, s));
+            fa.n_items = hi;
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
-            st = launch_filter_tma(fa, W, err, sms, s);
-            if (st) return st;
+            int rc = launch_filter_tma(fa, W, err, sms, s);
+            if (rc) return rc;
             BMJ_CHECK(cudaEventRecord(ev.e[4], s));
             int herr = 0;
-            BMJ_CHECK(cudaMemcpyAsync(&n_surv, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaMemcpyAsync(count, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             BMJ_CHECK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
             BMJ_CHECK(cudaStreamSynchronize(s));
             if (herr) return BMJ_ERR_TIMEOUT;
             stl.filter_passes++;
             stl.ms_filter += ev.ms(3, 4);
-            if (n_surv <= qcap) break;
-            // The queue was too small: every survivor was counted, so rerun
-            // the filter once with exactly enough room (no pair is dropped).
-            A.free_one(queue);
-            qcap = n_surv;
-            st = A.alloc(&queue, (size_t)qcap);
-            if (st) return st;
-            fa.queue = queue;
-            fa.qcap = qcap;
-            BMJ_CHECK(cudaMemsetAsync(&ctr[1], 0, 2 * sizeof(unsigned long long), s));
-        }
-        stl.survivors = n_surv;
+            return BMJ_OK;
+        };
+        // Verifies the m survivors in the queue into out_keys; adds to n_res.
+        auto run_verify = [&](int64_t m, uint64_t *out_keys, int64_t *n_out) -> int {
+            BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
+            BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+            int rc = launch_verify(queue, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
+                                   &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms, s);
+            if (rc) return rc;
+            BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+            int64_t hv2[2] = {0, 0};
+            BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaStreamSynchronize(s));
+            *n_out = hv2[0];
+            stl.verified += bm2 ? hv2[1] : m;
+            stl.ms_verify += ev.ms(5, 6);
+            return BMJ_OK;
+        };
 
-        // ---- exact verification ----
+        int64_t n_surv = 0;
+        st = run_filter(0, n_items, &n_surv);
+        if (st) return st;
+        stl.survivors = n_surv;
+        bool banded = false;
+        if (n_surv > qcap) {
+            uint2 *exact = nullptr;
+            if (!user_cap && A.alloc(&exact, (size_t)n_surv) == BMJ_OK) {
+                A.free_one(queue);
+                queue = exact;
+                qcap = n_surv;
+                fa.queue = queue;
+                fa.qcap = qcap;
+                int64_t again = 0;
+                st = run_filter(0, n_items, &again);
+                if (st) return st;
+            } else {
+                banded = true;
+            }
+        }
         uint64_t *keys = nullptr;
-        st = A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1));
-        if (st) return st;
-        BMJ_CHECK(cudaEventRecord(ev.e[5], s));
-        st = launch_verify(queue, n_surv, soff, stok, ssz, perm, need, lim, bm2, W2, keys, &ctr[3],
-                           bm2 ? &ctr[4] : nullptr, nbits, sms, s);
-        if (st) return st;
-        BMJ_CHECK(cudaEventRecord(ev.e[6], s));
-        int64_t hcas = 0;
-        BMJ_CHECK(cudaMemcpyAsync(&n_res, &ctr[3], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        BMJ_CHECK(cudaMemcpyAsync(&hcas, &ctr[4], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        BMJ_CHECK(cudaStreamSynchronize(s));
-        stl.verified = bm2 ? hcas : n_surv;
-        stl.ms_verify = ev.ms(5, 6);
+        if (!banded) {
+            st = A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1));
+            if (st) return st;
+            st = run_verify(n_surv, keys, &n_res);
+            if (st) return st;
+        } else {
+            // Item ranges sized from the measured survivor density; a range that
+            // still overflows is split again, and a single item that overflows
+            // gets a queue of exactly its size.
+            uint64_t *bkeys = nullptr;
+            st = A.alloc(&bkeys, (size_t)qcap);
+            if (st) return st;
+            int64_t res_cap = std::max<int64_t>(qcap, 1), lo = 0;
+            st = A.alloc(&keys, (size_t)res_cap);
+            if (st) return st;
+            double density = (double)n_surv / (double)std::max<int64_t>(n_items, 1);
+            while (lo < n_items) {
+                int64_t step = (int64_t)(0.8 * (double)qcap / std::max(density, 1e-12));
+                step = std::max<int64_t>(1, std::min(step, n_items - lo));
+                int64_t c = 0;
+                st = run_filter(lo, lo + step, &c);
+                if (st) return st;
+                if (c > qcap) {
+                    if (step > 1) {  // too dense here: retry a shorter range
+                        density = std::max(density, (double)c / (double)step);
+                        continue;
+                    }
+                    // one work item alone overflows: give the queue its exact size
+                    A.free_one(queue);
+                    A.free_one(bkeys);
+                    qcap = c;
+                    st = A.alloc(&queue, (size_t)qcap);
+                    if (!st) st = A.alloc(&bkeys, (size_t)qcap);
+                    if (st) return st;
+                    fa.queue = queue;
+                    fa.qcap = qcap;
+                    st = run_filter(lo, lo + 1, &c);
+                    if (st) return st;
+                }
+                int64_t r = 0;
+                st = run_verify(c, bkeys, &r);
+                if (st) return st;
+                if (n_res + r > res_cap) {  // grow the result buffer
+                    int64_t ncap = std::max(2 * res_cap, n_res + r);
+                    uint64_t *grown = nullptr;
+                    st = A.alloc(&grown, (size_t)ncap);
+                    if (st) return st;
+                    if (n_res)
+                        BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
+                                                  cudaMemcpyDeviceToDevice, s));
+                    A.free_one(keys);
+                    keys = grown;
+                    res_cap = ncap;
+                }
+                if (r)
+                    BMJ_CHECK(cudaMemcpyAsync(keys + n_res, bkeys, r * sizeof(uint64_t),
+                                              cudaMemcpyDeviceToDevice, s));
+                n_res += r;
+                lo += step;
+                if (c > 0) density = 0.5 * density + 0.5 * (double)c / (double)step;
+            }
+            A.free_one(bkeys);
+        }
         A.free_one(queue);
 
         // ---- canonical order ----

@@ -125,9 +125,24 @@ def test_pooled_host_lists_are_reused_without_aliasing():
 
 
 def test_queue_overflow_reruns_exactly():
+    # A one-entry queue: the work items run in ranges, and an item whose survivors
+    # alone overflow the queue gets a queue of exactly its size.
     off, tok = I.random_collection(4000, 300, 1, 30, seed=8, planted_frac=0.2)
     st = check_join(off, tok, 1, 2, b=64, queue_cap=1)
-    assert st["filter_passes"] == 2 and st["survivors"] > 1
+    assert st["filter_passes"] >= 2 and st["survivors"] > 1
+
+
+@pytest.mark.parametrize("b", [64, 128])
+def test_survivors_beyond_the_queue_run_in_item_ranges(b):
+    # The survivors need several queue fills: each range of work items is filtered and
+    # verified before the next; pairs, window and survivor counts stay exact.
+    off, tok = I.random_collection(12000, 3000, 2, 60, seed=21 + b, zipf_s=1.1, planted_frac=0.1)
+    full = check_join(off, tok, 1, 2, b=b)   # automatic queue: one pass, or two with exact room
+    cap = max(64, full["survivors"] // 7)
+    st = check_join(off, tok, 1, 2, b=b, queue_cap=cap)
+    assert st["filter_passes"] >= 8
+    assert (st["survivors"], st["results"], st["verified"]) == \
+        (full["survivors"], full["results"], full["verified"])
 
 
 def test_repeated_calls_are_deterministic():
