@@ -43,11 +43,14 @@ inline int status_of(cudaError_t e) {
 // ---------------------------------------------------------------------------
 // Host-side fault injection (tests): BMJ_FAULT=alloc:K makes the K-th device
 // allocation of a bmj_self_join call fail; BMJ_FAULT=timeout makes one warp of
-// the filter skip one copy, so that its bounded wait runs out.
+// the filter skip one copy, so that its bounded wait runs out;
+// BMJ_FAULT=keys refuses the result-key buffer as long as the survivor queue,
+// so that verification runs over the queue in slices.
 // ---------------------------------------------------------------------------
 struct FaultPlan {
     int alloc_at = 0;   // 0: none
     bool timeout = false;
+    bool keys = false;
 };
 FaultPlan read_fault_plan();      // parses BMJ_FAULT
 void arm_alloc_fault(int k);      // the k-th next Arena allocation fails (0 disarms)

@@ -28,6 +28,7 @@ FaultPlan read_fault_plan() {
     if (!e) return f;
     if (strncmp(e, "alloc:", 6) == 0) f.alloc_at = atoi(e + 6);
     if (strcmp(e, "timeout") == 0) f.timeout = true;
+    if (strcmp(e, "keys") == 0) f.keys = true;
     return f;
 }
 
@@ -245,11 +246,12 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             stl.ms_filter += ev.ms(3, 4);
             return BMJ_OK;
         };
-        // Verifies the m survivors in the queue into out_keys; adds to n_res.
-        auto run_verify = [&](int64_t m, uint64_t *out_keys, int64_t *n_out) -> int {
+        // Verifies the m survivors at qptr into out_keys (*n_out results).
+        auto run_verify = [&](const uint2 *qptr, int64_t m, uint64_t *out_keys,
+                              int64_t *n_out) -> int {
             BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
             BMJ_CHECK(cudaEventRecord(ev.e[5], s));
-            int rc = launch_verify(queue, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
+            int rc = launch_verify(qptr, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
                                    &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms, s);
             if (rc) return rc;
             BMJ_CHECK(cudaEventRecord(ev.e[6], s));
@@ -283,11 +285,45 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             }
         }
         uint64_t *keys = nullptr;
-        if (!banded) {
-            st = A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1));
+        int64_t res_cap = 0;
+        // Appends r result keys from src to the growing result buffer.
+        auto append = [&](const uint64_t *src, int64_t r) -> int {
+            if (n_res + r > res_cap) {
+                const int64_t ncap = std::max(2 * res_cap, n_res + r);
+                uint64_t *grown = nullptr;
+                int rc = A.alloc(&grown, (size_t)ncap);
+                if (rc) return rc;
+                if (n_res)
+                    BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
+                                              cudaMemcpyDeviceToDevice, s));
+                if (keys) A.free_one(keys);
+                keys = grown;
+                res_cap = ncap;
+            }
+            if (r)
+                BMJ_CHECK(cudaMemcpyAsync(keys + n_res, src, r * sizeof(uint64_t),
+                                          cudaMemcpyDeviceToDevice, s));
+            n_res += r;
+            return BMJ_OK;
+        };
+        if (!banded && !fault.keys && A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1)) == BMJ_OK) {
+            st = run_verify(queue, n_surv, keys, &n_res);
             if (st) return st;
-            st = run_verify(n_surv, keys, &n_res);
+        } else if (!banded) {
+            // every survivor is queued but a key buffer as long as the queue does
+            // not fit: verify the queue in slices (results <= survivors per slice)
+            const int64_t slice = std::max<int64_t>(
+                1, std::min<int64_t>(fault.keys ? (n_surv + 4) / 5 : n_surv, (int64_t)1 << 26));
+            uint64_t *bkeys = nullptr;
+            st = A.alloc(&bkeys, (size_t)slice);
             if (st) return st;
+            for (int64_t at = 0; at < n_surv; at += slice) {
+                int64_t r = 0;
+                st = run_verify(queue + at, std::min(slice, n_surv - at), bkeys, &r);
+                if (!st) st = append(bkeys, r);
+                if (st) return st;
+            }
+            A.free_one(bkeys);
         } else {
             // Item ranges sized from the measured survivor density; a range that
             // still overflows is split again, and a single item that overflows
@@ -295,9 +331,7 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             uint64_t *bkeys = nullptr;
             st = A.alloc(&bkeys, (size_t)qcap);
             if (st) return st;
-            int64_t res_cap = std::max<int64_t>(qcap, 1), lo = 0;
-            st = A.alloc(&keys, (size_t)res_cap);
-            if (st) return st;
+            int64_t lo = 0;
             double density = (double)n_surv / (double)std::max<int64_t>(n_items, 1);
             while (lo < n_items) {
                 int64_t step = (int64_t)(0.8 * (double)qcap / std::max(density, 1e-12));
@@ -323,24 +357,9 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
                     if (st) return st;
                 }
                 int64_t r = 0;
-                st = run_verify(c, bkeys, &r);
+                st = run_verify(queue, c, bkeys, &r);
+                if (!st) st = append(bkeys, r);
                 if (st) return st;
-                if (n_res + r > res_cap) {  // grow the result buffer
-                    int64_t ncap = std::max(2 * res_cap, n_res + r);
-                    uint64_t *grown = nullptr;
-                    st = A.alloc(&grown, (size_t)ncap);
-                    if (st) return st;
-                    if (n_res)
-                        BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
-                                                  cudaMemcpyDeviceToDevice, s));
-                    A.free_one(keys);
-                    keys = grown;
-                    res_cap = ncap;
-                }
-                if (r)
-                    BMJ_CHECK(cudaMemcpyAsync(keys + n_res, bkeys, r * sizeof(uint64_t),
-                                              cudaMemcpyDeviceToDevice, s));
-                n_res += r;
                 lo += step;
                 if (c > 0) density = 0.5 * density + 0.5 * (double)c / (double)step;
             }

@@ -36,3 +36,16 @@ def test_injected_timeout_and_allocation_failures(monkeypatch):
     ra, rb = O.self_join(off, tok, 1, 2)
     assert np.array_equal(a, ra) and np.array_equal(b, rb)
     torch.cuda.synchronize()
+
+
+def test_refused_key_buffer_verifies_the_queue_in_slices(monkeypatch):
+    # A key buffer as long as the survivor queue is refused: verification runs over
+    # the queue in slices and appends their results; the pairs and counts are exact.
+    off, tok = I.random_collection(6_000, 1_500, 1, 40, seed=78, planted_frac=0.1)
+    ra, rb = O.self_join(off, tok, 1, 2)
+    w, s, r = O.filter_counts(off, tok, 1, 2, 64, O.XOR)
+    monkeypatch.setenv("BMJ_FAULT", "keys")
+    a, b, st = _bmj.bmj_self_join(off, tok, 1, 2, b=64)
+    monkeypatch.delenv("BMJ_FAULT")
+    assert np.array_equal(a, ra) and np.array_equal(b, rb)
+    assert (st["window_pairs"], st["survivors"], st["results"]) == (w, s, r) and s >= 5
