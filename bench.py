@@ -307,6 +307,12 @@ def run_ours(args):
                 "frac_of_xu_plus_alu": round(achieved / mixed, 4),
                 "filter_pairs_per_s": round(window_per_step * args.steps / (filt_ms / 1e3)),
                 "filter_share_of_step": round(filt_ms / sum(step_ms), 4)}
+    try:  # the same peak measured by a POPC-only loop on this device (untimed region)
+        popc_meas = _bmj.bmj_measure_popc_rate(stream.cuda_stream) / 1e12
+        roofline["peak_measured"] = round(popc_meas, 4)
+        roofline["frac_of_measured"] = round(achieved / popc_meas, 4)
+    except Exception as e:  # reported, never fatal to the headline line
+        roofline["peak_measured"] = f"unavailable: {type(e).__name__}: {e}"
     if clk.get("sm_mhz"):
         roofline["frac_at_median_clock"] = round(
             achieved / (sms * POPC_PER_CLK_PER_SM * clk["sm_mhz"] * 1e6 / 1e12), 4)

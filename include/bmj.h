@@ -323,6 +323,14 @@ int64_t bmj_host_pool_trim(void);
  * monotone counter, for accounting in benchmarks). */
 int64_t bmj_kernel_launches(void);
 
+/* Measures the device's 32-bit population-count throughput (popcounts per
+ * second over all SMs, a 65,536-iteration loop of independent popcounts on
+ * every resident thread; about 40 ms on a B300) on `stream` (cudaStream_t,
+ * NULL = legacy default stream).  This is the peak of the Bitmap Filter's
+ * roofline, which needs b/32 popcounts per window pair.  Returns a BMJ status;
+ * *popc_per_s is 0 on error. */
+int bmj_measure_popc_rate(void *stream, double *popc_per_s);
+
 /* Size of the device scratch array used by bmj_bitmap_filter_noalloc. */
 #define BMJ_NOALLOC_SCRATCH_BYTES (8u << 20)
 

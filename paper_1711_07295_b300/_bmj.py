@@ -153,6 +153,7 @@ SIGNATURES = {
     "bmj_id_lists_free": (None, [C.POINTER(bmj_id_lists)]),
     "bmj_kernel_launches": (C.c_int64, []),
     "bmj_host_pool_trim": (C.c_int64, []),
+    "bmj_measure_popc_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "bmj_bitmap_filter_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_uint32,
                                             C.c_uint32, C.c_void_p, C.c_int64,
                                             C.POINTER(C.c_int64), C.c_void_p]),
@@ -230,6 +231,15 @@ def bmj_strerror(status: int) -> str:
 
 def bmj_kernel_launches() -> int:
     return int(lib().bmj_kernel_launches())
+
+
+def bmj_measure_popc_rate(stream=None) -> float:
+    """32-bit popcounts per second of the device (the Bitmap Filter's roofline peak)."""
+    out = C.c_double(0.0)
+    st = lib().bmj_measure_popc_rate(_stream_of(stream, True), C.byref(out))
+    if st != BMJ_OK:
+        raise BmjError(st, "bmj_measure_popc_rate")
+    return float(out.value)
 
 
 def bmj_host_pool_trim() -> int:
