@@ -292,3 +292,12 @@ def test_ten_million_sets_row_sampled(ten_million, p, q):
     assert np.all(a < bb)
     key = a.astype(np.uint64) << np.uint64(32) | bb.astype(np.uint64)
     assert np.all(key[1:] > key[:-1])
+
+
+def test_measured_popc_rate_matches_the_unit_count():
+    # 16 POPC per clock per SM at up to 2032 MHz: the measured rate may fall short of
+    # that under a lower clock, never above it by more than timing noise.
+    rate = _bmj.bmj_measure_popc_rate()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 16 * 2032e6
+    assert 0.5 * nominal < rate < 1.05 * nominal, (rate, nominal)
