@@ -979,6 +979,135 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
 }  // namespace
 }  // namespace bmj
 
+namespace bmj {
+namespace {
+
+__global__ void k_rebase(const int64_t *__restrict__ in, int64_t n, int64_t base,
+                         int64_t *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = in[i] - base;
+}
+
+void add_batch_stats(bmj_batch_stats &t, const bmj_batch_stats &u) {
+    t.n_jobs += u.n_jobs;
+    t.window_pairs += u.window_pairs;
+    t.survivors += u.survivors;
+    t.results += u.results;
+    t.n_launches += u.n_launches;
+    t.filter_passes += u.filter_passes;
+    t.graph = t.graph || u.graph;
+    t.tuned = t.tuned || u.tuned;
+    t.ms_prepare += u.ms_prepare;
+    t.ms_tune += u.ms_tune;
+    t.ms_execute += u.ms_execute;
+    t.ms_output += u.ms_output;
+    t.ms_total += u.ms_total;
+}
+
+// Jobs [k0, k1) of the batch as a collection of their own: offsets rebased to
+// start at 0 (a device copy for a device collection), tokens borrowed.
+struct SubColl {
+    bmj_collection c{};
+    std::vector<int64_t> host_off;
+    int64_t *dev_off = nullptr;
+    cudaStream_t s = nullptr;
+    ~SubColl() {
+        if (dev_off) cudaFreeAsync(dev_off, s);
+    }
+};
+
+int make_sub(const bmj_collection *coll, int64_t s0, int64_t s1, cudaStream_t s, SubColl &sub) {
+    sub.s = s;
+    const int64_t m = s1 - s0;
+    int64_t base = 0;
+    if (coll->on_device) {
+        BMJ_CHECK(cudaMemcpyAsync(&base, coll->offsets + s0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        BMJ_CHECK(cudaStreamSynchronize(s));
+        BMJ_CHECK(cudaMallocAsync(&sub.dev_off, (m + 1) * sizeof(int64_t), s));
+        k_rebase<<<(unsigned)std::min<int64_t>((m + 256) / 256, 148 * 8), 256, 0, s>>>(
+            coll->offsets + s0, m + 1, base, sub.dev_off);
+        count_launch();
+        BMJ_CHECK(cudaGetLastError());
+        sub.c.offsets = sub.dev_off;
+    } else {
+        base = coll->offsets[s0];
+        sub.host_off.resize(m + 1);
+        for (int64_t i = 0; i <= m; i++) sub.host_off[i] = coll->offsets[s0 + i] - base;
+        sub.c.offsets = sub.host_off.data();
+    }
+    sub.c.n_sets = m;
+    sub.c.tokens = coll->tokens + base;
+    sub.c.on_device = coll->on_device;
+    return BMJ_OK;
+}
+
+// After an out-of-memory batch: the jobs run in two halves (recursively); a
+// single job that still does not fit runs as bmj_self_join, whose survivor
+// handling never needs all survivors in memory at once.
+int batch_in_parts(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets,
+                   const uint32_t *hp, const uint32_t *hq, const bmj_options &o, bmj_pairs *outs,
+                   bmj_stats *job_stats, bmj_batch_stats *bst) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    if (n_jobs == 1) {
+        SubColl sub;
+        int st = make_sub(coll, job_sets[0], job_sets[1], s, sub);
+        if (st) return st;
+        bmj_options so = o;
+        if (so.b == 0) so.b = 256;  // the widest tuned width leaves the fewest survivors
+        so.use_graph = 0;
+        bmj_stats js;
+        memset(&js, 0, sizeof(js));
+        st = bmj_self_join(&sub.c, BMJ_JACCARD, hp[0], hq[0], &so, &outs[0], &js);
+        if (st) return st;
+        if (job_stats) job_stats[0] = js;
+        bmj_batch_stats u;
+        memset(&u, 0, sizeof(u));
+        u.n_jobs = 1;
+        u.window_pairs = js.window_pairs;
+        u.survivors = js.survivors;
+        u.results = js.results;
+        u.n_launches = js.n_launches;
+        u.filter_passes = (int32_t)js.filter_passes;
+        u.ms_prepare = js.ms_prepare;
+        u.ms_execute = js.ms_filter + js.ms_verify;
+        u.ms_output = js.ms_output;
+        u.ms_total = js.ms_total;
+        add_batch_stats(*bst, u);
+        return BMJ_OK;
+    }
+    const int64_t half = n_jobs / 2;
+    for (int part = 0; part < 2; part++) {
+        const int64_t k0 = part ? half : 0, k1 = part ? n_jobs : half;
+        SubColl sub;
+        int st = make_sub(coll, job_sets[k0], job_sets[k1], s, sub);
+        if (st) return st;
+        std::vector<int64_t> js(k1 - k0 + 1);
+        for (int64_t k = k0; k <= k1; k++) js[k - k0] = job_sets[k] - job_sets[k0];
+        bmj_batch_stats u;
+        memset(&u, 0, sizeof(u));
+        try {
+            st = batch_impl(&sub.c, k1 - k0, js.data(), hp + k0, hq + k0, o, outs + k0,
+                            job_stats ? job_stats + k0 : nullptr, &u);
+        } catch (...) {
+            st = BMJ_ERR_OOM;
+        }
+        if (st == BMJ_ERR_OOM) {
+            for (int64_t k = k0; k < k1; k++) bmj_pairs_free(&outs[k]);
+            cudaGetLastError();
+            memset(&u, 0, sizeof(u));
+            st = batch_in_parts(&sub.c, k1 - k0, js.data(), hp + k0, hq + k0, o, outs + k0,
+                                job_stats ? job_stats + k0 : nullptr, &u);
+        }
+        if (st) return st;
+        add_batch_stats(*bst, u);
+    }
+    return BMJ_OK;
+}
+
+}  // namespace
+}  // namespace bmj
+
 extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
                                    const int64_t *job_sets, int sim, const uint32_t *p,
                                    const uint32_t *q, const bmj_options *opt, bmj_pairs *outs,
@@ -1003,11 +1132,26 @@ extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
     if (o.cascade_b != 0 && o.cascade_b != -1 && o.cascade_b != 256) return BMJ_ERR_INVALID_ARG;
     int st;
+    bmj_batch_stats bs;
+    memset(&bs, 0, sizeof(bs));
+    bmj::arm_alloc_fault(bmj::read_fault_plan().alloc_at);  // tests: BMJ_FAULT=alloc:K
     try {
-        st = bmj::batch_impl(coll, n_jobs, job_sets, p, q, o, outs, job_stats, batch_stats);
+        st = bmj::batch_impl(coll, n_jobs, job_sets, p, q, o, outs, job_stats, &bs);
     } catch (...) {
         st = BMJ_ERR_OOM;
     }
+    bmj::arm_alloc_fault(0);
+    if (st == BMJ_ERR_OOM) {  // retry in parts: halves of the job list, then single joins
+        for (int64_t k = 0; k < n_jobs; k++) bmj_pairs_free(&outs[k]);
+        cudaGetLastError();
+        memset(&bs, 0, sizeof(bs));
+        try {
+            st = bmj::batch_in_parts(coll, n_jobs, job_sets, p, q, o, outs, job_stats, &bs);
+        } catch (...) {
+            st = BMJ_ERR_OOM;
+        }
+    }
+    if (!st && batch_stats) *batch_stats = bs;
     if (st) {
         for (int64_t k = 0; k < n_jobs; k++) bmj_pairs_free(&outs[k]);
         cudaGetLastError();

@@ -163,3 +163,19 @@ def test_batch_cascade_on_and_off():
         off_, jst_off, _ = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=b, cascade_b=-1)
         check(jobs, on, jst_on)
         check(jobs, off_, jst_off)
+
+
+@pytest.mark.parametrize("k,on_device", [(1, True), (4, True), (9, False)])
+def test_out_of_memory_batch_retries_in_parts(monkeypatch, k, on_device):
+    # An allocation refused inside the batch (injected on the host): the jobs run again
+    # in halves of the job list (offsets rebased per part) with the same exact results.
+    jobs = make_batch(12, seed=31)
+    off, tok, js, p, q = concat(jobs)
+    if on_device:
+        off, tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    monkeypatch.setenv("BMJ_FAULT", f"alloc:{k}")
+    pairs, jst, bst = _bmj.bmj_self_join_batch(off, tok, js, p, q, b=0)
+    monkeypatch.delenv("BMJ_FAULT")
+    check(jobs, pairs, jst)
+    assert bst["n_jobs"] == 12 and bst["results"] == sum(len(x[0]) for x in pairs)
+    assert bst["filter_passes"] >= 2   # the two halves ran (one pass or more each)
