@@ -17,6 +17,10 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
       histogram, survivors == results when bitmaps are exact, Theorem 1
       soundness (results never exceed what brute force finds);
   join_rows / search -- against self_join / brute force on small inputs.
+  similar_sim / in_window (Cosine, Dice, Overlap; Table 1 and Table 2) --
+      Table 1 evaluated with exact fractions and 60-digit square roots, the
+      bounds printed in Table 2, the Dice-Jaccard threshold equivalence, brute
+      force joins, window counts from the size histogram.
   Cutoff point (Section 3.5, Eq. 5 inverted) -- parity unpinned: the paper's
       Xor figure 4983 does not follow from its own Eq. 5.
 """
@@ -29,6 +33,7 @@ import numpy as np
 from . import build as _build
 
 XOR, SET, NEXT, COMBINED = 0, 1, 2, 3
+JACCARD, COSINE, DICE, OVERLAP = 0, 1, 2, 3   # similarity functions (Table 1)
 METHODS = {"xor": XOR, "set": SET, "next": NEXT, "combined": COMBINED}
 
 _lib = None
@@ -45,13 +50,18 @@ def lib():
         L.oracle_overlap.restype = i64
         L.oracle_similar.argtypes = [i64, i64, i64, i64, i64]
         L.oracle_similar.restype = C.c_int
-        L.oracle_self_join.argtypes = [i64, i64p, i32p, i64, i64, u32pp, u32pp]
+        L.oracle_similar_sim.argtypes = [C.c_int, i64, i64, i64, i64, i64]
+        L.oracle_similar_sim.restype = C.c_int
+        L.oracle_in_window.argtypes = [C.c_int, i64, i64, i64, i64]
+        L.oracle_in_window.restype = C.c_int
+        L.oracle_self_join.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, u32pp, u32pp]
         L.oracle_self_join.restype = i64
-        L.oracle_join_rows.argtypes = [i64, i64p, i32p, i64, i64, i64p, i64, u32pp, u32pp]
+        L.oracle_join_rows.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, i64p, i64, u32pp, u32pp]
         L.oracle_join_rows.restype = i64
-        L.oracle_join_rows_window.argtypes = [i64, i64p, i32p, i64, i64, i64p, i64, u32pp, u32pp]
+        L.oracle_join_rows_window.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, i64p, i64, u32pp,
+                                              u32pp]
         L.oracle_join_rows_window.restype = i64
-        L.oracle_search.argtypes = [i32p, i64, i64, i64p, i32p, i64, i64, C.POINTER(i64p)]
+        L.oracle_search.argtypes = [i32p, i64, i64, i64p, i32p, C.c_int, i64, i64, C.POINTER(i64p)]
         L.oracle_search.restype = i64
         L.oracle_bitmap.argtypes = [i32p, i64, C.c_int, C.c_int, u64p]
         L.oracle_bitmap.restype = None
@@ -61,7 +71,8 @@ def lib():
         L.oracle_hamming.restype = i64
         L.oracle_upper_bound.argtypes = [i64, i64, i64]
         L.oracle_upper_bound.restype = i64
-        L.oracle_filter_counts.argtypes = [i64, i64p, i32p, i64, i64, C.c_int, C.c_int, i64p]
+        L.oracle_filter_counts.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, C.c_int, C.c_int,
+                                           i64p]
         L.oracle_filter_counts.restype = None
         L.oracle_combined_method.argtypes = [i64, i64]
         L.oracle_combined_method.restype = C.c_int
@@ -100,6 +111,16 @@ def similar(o: int, nx: int, ny: int, p: int, q: int) -> bool:
     return bool(lib().oracle_similar(o, nx, ny, p, q))
 
 
+def similar_sim(sim: int, o: int, nx: int, ny: int, p: int, q: int) -> bool:
+    """sim >= p/q for Jaccard, Cosine, Dice or Overlap given o and the sizes (Table 1)."""
+    return bool(lib().oracle_similar_sim(sim, o, nx, ny, p, q))
+
+
+def in_window(sim: int, a: int, b: int, p: int, q: int) -> bool:
+    """Sizes a <= b inside the length filter's window (Table 2)."""
+    return bool(lib().oracle_in_window(sim, a, b, p, q))
+
+
 def _take_pairs(n, A, B):
     L = lib()
     if n < 0:
@@ -113,39 +134,39 @@ def _take_pairs(n, A, B):
     return a, b
 
 
-def self_join(offsets, tokens, p: int, q: int):
-    """All pairs a<b (original ids) with Jaccard >= p/q, sorted by (a, b)."""
+def self_join(offsets, tokens, p: int, q: int, sim: int = JACCARD):
+    """All pairs a<b (original ids) with sim >= p/q, sorted by (a, b)."""
     off, tok = _i64(offsets), _i32(tokens)
     A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
-    n = lib().oracle_self_join(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p, q,
+    n = lib().oracle_self_join(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim, p, q,
                                C.byref(A), C.byref(B))
     return _take_pairs(n, A, B)
 
 
-def join_rows(offsets, tokens, p: int, q: int, rows):
+def join_rows(offsets, tokens, p: int, q: int, rows, sim: int = JACCARD):
     """Similar pairs (min,max) that touch one of ``rows``, sorted, unique."""
     off, tok, r = _i64(offsets), _i32(tokens), _i64(rows)
     A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
-    n = lib().oracle_join_rows(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p, q,
+    n = lib().oracle_join_rows(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim, p, q,
                                _p(r, C.c_int64), len(r), C.byref(A), C.byref(B))
     return _take_pairs(n, A, B)
 
 
-def join_rows_window(offsets, tokens, p: int, q: int, rows):
+def join_rows_window(offsets, tokens, p: int, q: int, rows, sim: int = JACCARD):
     """join_rows with the length filter (Table 2): same output, fewer pairs verified."""
     off, tok, r = _i64(offsets), _i32(tokens), _i64(rows)
     A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
-    n = lib().oracle_join_rows_window(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p,
-                                      q, _p(r, C.c_int64), len(r), C.byref(A), C.byref(B))
+    n = lib().oracle_join_rows_window(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim,
+                                      p, q, _p(r, C.c_int64), len(r), C.byref(A), C.byref(B))
     return _take_pairs(n, A, B)
 
 
-def search(probe, offsets, tokens, p: int, q: int):
-    """Ids of the collection's sets with Jaccard(probe, s) >= p/q, ascending."""
+def search(probe, offsets, tokens, p: int, q: int, sim: int = JACCARD):
+    """Ids of the collection's sets with sim(probe, s) >= p/q, ascending."""
     x, off, tok = _i32(probe), _i64(offsets), _i32(tokens)
     ids = C.POINTER(C.c_int64)()
     n = lib().oracle_search(_p(x, C.c_int32), len(x), len(off) - 1, _p(off, C.c_int64),
-                            _p(tok, C.c_int32), p, q, C.byref(ids))
+                            _p(tok, C.c_int32), sim, p, q, C.byref(ids))
     if n < 0:
         raise MemoryError("oracle allocation failed")
     if n == 0:
@@ -188,17 +209,18 @@ def upper_bound(nr: int, ns: int, h: int) -> int:
     return int(lib().oracle_upper_bound(nr, ns, h))
 
 
-def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int):
+def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int = JACCARD):
     """(window pairs, survivors, results) of Alg. 6 + host verification."""
     off, tok = _i64(offsets), _i32(tokens)
     cnt = np.zeros(3, np.int64)
-    lib().oracle_filter_counts(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), p, q,
+    lib().oracle_filter_counts(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim, p, q,
                                b, method, _p(cnt, C.c_int64))
     if cnt[0] < 0:
         raise MemoryError("oracle allocation failed")
     return int(cnt[0]), int(cnt[1]), int(cnt[2])
 
 
-__all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "overlap", "similar", "self_join",
+__all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "JACCARD", "COSINE", "DICE", "OVERLAP",
+           "overlap", "similar", "similar_sim", "in_window", "self_join",
            "join_rows", "join_rows_window", "search", "bitmap", "bitmaps", "hamming", "upper_bound",
            "filter_counts", "combined_method", "num_threads", "lib"]

@@ -25,6 +25,8 @@
  * Functions:
  *   oracle_overlap        |x & y| by a plain two-pointer merge (Alg. 1 verify)
  *   oracle_similar        the integer Jaccard test above
+ *   oracle_similar_sim    the same for Jaccard, Cosine, Dice and Overlap (Table 1)
+ *   oracle_in_window      the length filter of Table 2 for any of them
  *   oracle_self_join      Alg. 1 over all pairs a<b, no filter at all
  *   oracle_join_rows      Alg. 1 restricted to pairs touching sampled rows
  *   oracle_join_rows_window  the same with the length filter of Table 2
@@ -41,6 +43,7 @@
 #endif
 
 enum { OR_XOR = 0, OR_SET = 1, OR_NEXT = 2, OR_COMBINED = 3 };
+enum { OR_JACCARD = 0, OR_COSINE = 1, OR_DICE = 2, OR_OVERLAP = 3 };
 
 /* |x & y| for two strictly increasing token arrays (plain merge). */
 int64_t oracle_overlap(const int32_t *x, int64_t nx, const int32_t *y, int64_t ny)
@@ -58,6 +61,40 @@ int64_t oracle_overlap(const int32_t *x, int64_t nx, const int32_t *y, int64_t n
 int oracle_similar(int64_t o, int64_t nx, int64_t ny, int64_t p, int64_t q)
 {
     return o * (p + q) >= p * (nx + ny);
+}
+
+/*
+ * sim(x,y) >= p/q for the four functions of Table 1, each cleared of its
+ * fraction (and of the square root for Cosine) so that the test is exact in
+ * integers (128-bit where a product of four 32-bit factors can occur):
+ *   Jaccard  o / (|x|+|y|-o) >= p/q   <=>  o*(p+q)     >= p*(|x|+|y|)
+ *   Cosine   o / sqrt(|x||y|) >= p/q  <=>  o^2*q^2     >= p^2*|x|*|y|
+ *   Dice     2o / (|x|+|y|) >= p/q    <=>  2*o*q       >= p*(|x|+|y|)
+ *   Overlap  o >= p/q                 <=>  o*q         >= p
+ */
+int oracle_similar_sim(int sim, int64_t o, int64_t nx, int64_t ny, int64_t p, int64_t q)
+{
+    switch (sim) {
+    case OR_JACCARD: return oracle_similar(o, nx, ny, p, q);
+    case OR_COSINE: {
+        __int128 lhs = (__int128)o * o * q * q;
+        __int128 rhs = (__int128)p * p * nx * ny;
+        return lhs >= rhs;
+    }
+    case OR_DICE: return 2 * o * q >= p * (nx + ny);
+    case OR_OVERLAP: return o * q >= p;
+    }
+    return 0;
+}
+
+/*
+ * The length filter of Table 2 for sizes a <= b: a pair of sizes (a, b) can
+ * reach the threshold only if the overlap min(a,b) = a does, i.e. if
+ * sim(a, b) with o = a passes.  Returns 1 when (a, b) is inside the window.
+ */
+int oracle_in_window(int sim, int64_t a, int64_t b, int64_t p, int64_t q)
+{
+    return oracle_similar_sim(sim, a, a, b, p, q);
 }
 
 /* Growable pair buffer. */
@@ -101,7 +138,7 @@ int oracle_num_threads(void)
  * Returns the pair count, or -1 on allocation failure.  *out_a / *out_b are
  * malloc'd (free with oracle_free); both are NULL when the count is 0.
  */
-int64_t oracle_self_join(int64_t n, const int64_t *off, const int32_t *tok,
+int64_t oracle_self_join(int64_t n, const int64_t *off, const int32_t *tok, int sim,
                          int64_t p, int64_t q, uint32_t **out_a, uint32_t **out_b)
 {
     *out_a = NULL;
@@ -118,7 +155,7 @@ int64_t oracle_self_join(int64_t n, const int64_t *off, const int32_t *tok,
             const int32_t *xb = tok + off[b];
             int64_t nb = off[b + 1] - off[b];
             int64_t o = oracle_overlap(xa, na, xb, nb);
-            if (oracle_similar(o, na, nb, p, q))
+            if (oracle_similar_sim(sim, o, na, nb, p, q))
                 if (pb_push(&rows[a], (uint32_t)a, (uint32_t)b)) failed = 1;
         }
     }
@@ -161,7 +198,7 @@ static int cmp_pair64(const void *x, const void *y)
     return (u > v) - (u < v);
 }
 
-int64_t oracle_join_rows(int64_t n, const int64_t *off, const int32_t *tok,
+int64_t oracle_join_rows(int64_t n, const int64_t *off, const int32_t *tok, int sim,
                          int64_t p, int64_t q, const int64_t *rows, int64_t k,
                          uint32_t **out_a, uint32_t **out_b)
 {
@@ -180,7 +217,7 @@ int64_t oracle_join_rows(int64_t n, const int64_t *off, const int32_t *tok,
             if (s == r) continue;
             int64_t ns = off[s + 1] - off[s];
             int64_t o = oracle_overlap(xr, nr, tok + off[s], ns);
-            if (oracle_similar(o, nr, ns, p, q)) {
+            if (oracle_similar_sim(sim, o, nr, ns, p, q)) {
                 uint32_t a = (uint32_t)(r < s ? r : s), b = (uint32_t)(r < s ? s : r);
                 if (pb_push(&per[t], a, b)) failed = 1;
             }
@@ -221,15 +258,15 @@ int64_t oracle_join_rows(int64_t n, const int64_t *off, const int32_t *tok,
 }
 
 /*
- * oracle_join_rows with the length filter (Section 2.3.2, Table 2, Jaccard
- * row): a sampled row r is verified only against the sets s whose size lies
- * in [ceil(p|r|/q), floor(q|r|/p)] -- outside that range J(r,s) < p/q for
- * any contents, so the output equals oracle_join_rows'.  The sets are
- * visited through size buckets built once per call (a counting sort of the
- * ids by size).  It exists to time the plain join with the paper's cheapest
- * filter beside the plain definition.
+ * oracle_join_rows with the length filter (Section 2.3.2, Table 2): a sampled
+ * row r is verified only against the sets s whose size is inside its window
+ * (oracle_in_window; for Jaccard [ceil(p|r|/q), floor(q|r|/p)]) -- outside it
+ * sim(r,s) < p/q for any contents, so the output equals oracle_join_rows'.
+ * The sets are visited through size buckets built once per call (a counting
+ * sort of the ids by size).  It exists to time the plain join with the
+ * paper's cheapest filter beside the plain definition.
  */
-int64_t oracle_join_rows_window(int64_t n, const int64_t *off, const int32_t *tok,
+int64_t oracle_join_rows_window(int64_t n, const int64_t *off, const int32_t *tok, int sim,
                                 int64_t p, int64_t q, const int64_t *rows, int64_t k,
                                 uint32_t **out_a, uint32_t **out_b)
 {
@@ -259,15 +296,14 @@ int64_t oracle_join_rows_window(int64_t n, const int64_t *off, const int32_t *to
         int64_t r = rows[t];
         const int32_t *xr = tok + off[r];
         int64_t nr = off[r + 1] - off[r];
-        int64_t lo = (p * nr + q - 1) / q;    /* ceil(p|r|/q) */
-        int64_t hi = (q * nr) / p;            /* floor(q|r|/p) */
-        if (hi > max_size) hi = max_size;
-        for (int64_t z = lo; z <= hi; z++) {
+        for (int64_t z = 0; z <= max_size; z++) {
+            if (bucket[z] == bucket[z + 1]) continue;
+            if (!oracle_in_window(sim, z < nr ? z : nr, z < nr ? nr : z, p, q)) continue;
             for (int64_t x = bucket[z]; x < bucket[z + 1]; x++) {
                 int64_t s = by_size[x];
                 if (s == r) continue;
                 int64_t o = oracle_overlap(xr, nr, tok + off[s], z);
-                if (oracle_similar(o, nr, z, p, q)) {
+                if (oracle_similar_sim(sim, o, nr, z, p, q)) {
                     uint32_t a = (uint32_t)(r < s ? r : s), b = (uint32_t)(r < s ? s : r);
                     if (pb_push(&per[t], a, b)) failed = 1;
                 }
@@ -315,7 +351,7 @@ int64_t oracle_join_rows_window(int64_t n, const int64_t *off, const int32_t *to
  * |R| = 1, Eq. 1): the ids s with J(x, s) >= p/q, ascending.
  */
 int64_t oracle_search(const int32_t *x, int64_t nx, int64_t n, const int64_t *off,
-                      const int32_t *tok, int64_t p, int64_t q, int64_t **out_ids)
+                      const int32_t *tok, int sim, int64_t p, int64_t q, int64_t **out_ids)
 {
     *out_ids = NULL;
     int64_t cnt = 0, cap = 0;
@@ -323,7 +359,7 @@ int64_t oracle_search(const int32_t *x, int64_t nx, int64_t n, const int64_t *of
     for (int64_t s = 0; s < n; s++) {
         int64_t ns = off[s + 1] - off[s];
         int64_t o = oracle_overlap(x, nx, tok + off[s], ns);
-        if (oracle_similar(o, nx, ns, p, q)) {
+        if (oracle_similar_sim(sim, o, nx, ns, p, q)) {
             if (cnt == cap) {
                 cap = cap ? 2 * cap : 64;
                 int64_t *ni = (int64_t *)realloc(ids, (size_t)cap * sizeof(int64_t));
@@ -435,7 +471,7 @@ int64_t oracle_upper_bound(int64_t nr, int64_t ns, int64_t hamming)
  * Writes window pairs, survivors and results to counts[0..2].  The sort is a
  * plain insertion of (size, id) keys through qsort of packed keys.
  */
-void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int64_t p,
+void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int sim, int64_t p,
                           int64_t q, int b, int method, int64_t *counts)
 {
     counts[0] = counts[1] = counts[2] = 0;
@@ -464,15 +500,16 @@ void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : win, surv, res)
     for (int64_t i = 0; i < n; i++) {
         int64_t j0 = 0;
-        while (q * sz[j0] < p * sz[i]) j0++;
+        while (j0 < i && !oracle_in_window(sim, sz[j0], sz[i], p, q)) j0++;
         for (int64_t j = j0; j < i; j++) {
             win++;
             int64_t h = oracle_hamming(bm + i * W, bm + j * W, b);
             int64_t ub = oracle_upper_bound(sz[i], sz[j], h);
-            if (ub * (p + q) >= p * (sz[i] + sz[j])) {
+            /* the bound passes iff the similarity of an overlap of ub passes */
+            if (oracle_similar_sim(sim, ub, sz[i], sz[j], p, q)) {
                 surv++;
                 int64_t o = oracle_overlap(tok + off[ord[i]], sz[i], tok + off[ord[j]], sz[j]);
-                if (oracle_similar(o, sz[i], sz[j], p, q)) res++;
+                if (oracle_similar_sim(sim, o, sz[i], sz[j], p, q)) res++;
             }
         }
     }

@@ -460,3 +460,120 @@ def test_survivor_count_brute_force(method, b):
                 surv += 1
         w, s, r = O.filter_counts(off, tok, p, q, b, method)
         assert (w, s) == (win, surv)
+
+
+# ------------------------------------------------ Table 1 / Table 2: other functions
+SIMS = (O.JACCARD, O.COSINE, O.DICE, O.OVERLAP)
+
+
+def _sim_value(sim, o, x, y):
+    """Table 1 evaluated independently: exact fractions, the square root of Cosine
+    in 60-digit decimal arithmetic (exact whenever x*y is a perfect square)."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    if sim == O.JACCARD:
+        return Fraction(o, x + y - o)
+    if sim == O.DICE:
+        return Fraction(2 * o, x + y)
+    if sim == O.OVERLAP:
+        return Fraction(o)
+    return Decimal(o) / (Decimal(x) * Decimal(y)).sqrt()
+
+
+def _passes(sim, o, x, y, p, q):
+    v = _sim_value(sim, o, x, y)
+    if sim == O.COSINE:
+        from decimal import Decimal
+        return v >= Decimal(p) / Decimal(q)
+    return v >= Fraction(p, q)
+
+
+def _brute_pairs_sim(sets, sim, p, q):
+    out = []
+    for a, b in itertools.combinations(range(len(sets)), 2):
+        A, B = set(sets[a]), set(sets[b])
+        if _passes(sim, len(A & B), len(A), len(B), p, q):
+            out.append((a, b))
+    return out
+
+
+@pytest.mark.parametrize("sim", SIMS)
+def test_similarity_functions_of_table1(sim):
+    rng = np.random.default_rng(40 + sim)
+    for _ in range(4000):
+        x, y = int(rng.integers(1, 90)), int(rng.integers(1, 90))
+        o = int(rng.integers(0, min(x, y) + 1))
+        q = int(rng.integers(1, 30))
+        p = int(rng.integers(1, 3 * q if sim == O.OVERLAP else q + 1))
+        assert O.similar_sim(sim, o, x, y, p, q) == _passes(sim, o, x, y, p, q), (sim, o, x, y, p, q)
+    # boundary cases that hit the threshold exactly
+    assert O.similar_sim(O.COSINE, 6, 9, 16, 1, 2) and not O.similar_sim(O.COSINE, 5, 9, 16, 1, 2)
+    assert O.similar_sim(O.DICE, 3, 4, 8, 1, 2) and not O.similar_sim(O.DICE, 2, 4, 8, 1, 2)
+    assert O.similar_sim(O.OVERLAP, 3, 5, 5, 3, 1) and not O.similar_sim(O.OVERLAP, 2, 5, 5, 3, 1)
+    assert O.similar_sim(O.JACCARD, 4, 6, 6, 1, 2) and not O.similar_sim(O.JACCARD, 3, 6, 6, 1, 2)
+
+
+@pytest.mark.parametrize("sim", SIMS)
+def test_length_window_is_table2(sim):
+    # in_window(a, b) for sizes a <= b against the lower bounds printed in Table 2
+    # (the larger set r = b): Overlap tau, Jaccard |r| tau_j, Cosine |r| tau_c^2,
+    # Dice |r| tau_d / (2 - tau_d).
+    for q in (1, 2, 3, 5, 10, 20):
+        for p in range(1, (3 * q if sim == O.OVERLAP else q) + 1):
+            t = Fraction(p, q)
+            lower = {O.OVERLAP: lambda b: t, O.JACCARD: lambda b: b * t,
+                     O.COSINE: lambda b: b * t * t, O.DICE: lambda b: b * t / (2 - t)}[sim]
+            for b in range(1, 40):
+                for a in range(1, b + 1):
+                    assert O.in_window(sim, a, b, p, q) == (a >= lower(b)), (sim, p, q, a, b)
+
+
+def test_dice_and_jaccard_thresholds_are_equivalent():
+    # Dice = 2J / (1 + J) is increasing in J, so Dice >= 2t/(1+t) <=> Jaccard >= t:
+    # with t = p/q the Dice threshold is 2p/(p+q) (Table 1's equivalences).
+    off, tok = I.random_collection(600, 200, 1, 25, seed=61, planted_frac=0.2)
+    for p, q in ((1, 2), (3, 5), (4, 5), (9, 10)):
+        ja, jb = O.self_join(off, tok, p, q, sim=O.JACCARD)
+        da, db = O.self_join(off, tok, 2 * p, p + q, sim=O.DICE)
+        assert np.array_equal(ja, da) and np.array_equal(jb, db) and len(ja) > 0
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.COSINE, 1, 2), (O.COSINE, 4, 5), (O.DICE, 3, 5),
+                                     (O.DICE, 9, 10), (O.OVERLAP, 3, 1), (O.OVERLAP, 7, 2)])
+def test_other_functions_brute_force(sim, p, q):
+    off, tok = I.random_collection(160, 50, 1, 14, seed=sim * 10 + p, planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    want = _brute_pairs_sim(sets, sim, p, q)
+    a, b = O.self_join(off, tok, p, q, sim=sim)
+    assert list(zip(a.tolist(), b.tolist())) == want and len(want) > 0
+    rows = [0, 7, 59, 159]
+    ra, rb = O.join_rows(off, tok, p, q, rows, sim=sim)
+    wa, wb = O.join_rows_window(off, tok, p, q, rows, sim=sim)
+    sel = sorted(pr for pr in want if pr[0] in rows or pr[1] in rows)
+    assert list(zip(ra.tolist(), rb.tolist())) == sel == list(zip(wa.tolist(), wb.tolist()))
+    ids = O.search(sets[7], off, tok, p, q, sim=sim)
+    assert ids.tolist() == [s for s in range(len(sets))
+                            if _passes(sim, len(set(sets[7]) & set(sets[s])), len(sets[7]),
+                                       len(sets[s]), p, q)]
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.COSINE, 3, 5), (O.DICE, 7, 10), (O.OVERLAP, 4, 1),
+                                     (O.JACCARD, 1, 2)])
+def test_filter_counts_other_functions(sim, p, q):
+    # window pairs = pairs j < i (size order) inside Table 2's window, counted from
+    # the size histogram; results = brute force; survivors between the two; exact
+    # bitmaps (universe <= b) pass exactly the similar pairs.
+    off, tok = I.random_collection(500, 60, 1, 24, seed=70 + sim, planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    sizes = sorted(np.diff(off).tolist())
+    t = Fraction(p, q)
+    lower = {O.OVERLAP: lambda b: t, O.JACCARD: lambda b: b * t,
+             O.COSINE: lambda b: b * t * t, O.DICE: lambda b: b * t / (2 - t)}[sim]
+    win = sum(1 for i in range(len(sizes)) for j in range(i) if sizes[j] >= lower(sizes[i]))
+    n_res = len(_brute_pairs_sim(sets, sim, p, q))
+    for method in (O.XOR, O.SET):
+        w, s, r = O.filter_counts(off, tok, p, q, 64, method, sim=sim)
+        assert w == win and r == n_res and r <= s <= w
+        assert s == r   # universe 60 <= b: the bitmaps are exact
+    w, s, r = O.filter_counts(off, tok, p, q, 128, O.XOR, sim=sim)
+    assert (w, r) == (win, n_res) and s == r
