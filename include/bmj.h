@@ -64,7 +64,16 @@ extern "C" {
 #define BMJ_COMBINED 3   /* Alg. 4: Next / Set / Xor chosen from the threshold (switch points on 2p/(p+q)) */
 
 /* ---- similarity functions (Table 1) ------------------------------------- */
+/* A threshold is p/q; every test is exact in integers:
+ *   BMJ_JACCARD  |x&y| / |x|y|          >= p/q   (0 < p <= q)
+ *   BMJ_COSINE   |x&y| / sqrt(|x||y|)   >= p/q   (0 < p <= q <= 65535)
+ *   BMJ_DICE     2|x&y| / (|x|+|y|)     >= p/q   (0 < p <= q)
+ *   BMJ_OVERLAP  |x&y|                  >= p/q   (p, q >= 1; p/q counts tokens)
+ * p, q < 2^31.  The length window of each function is the one of Table 2. */
 #define BMJ_JACCARD  0
+#define BMJ_COSINE   1
+#define BMJ_DICE     2
+#define BMJ_OVERLAP  3
 
 /* A collection of n_sets sets in CSR form: set x holds
  * tokens[offsets[x] .. offsets[x+1]-1].  offsets has n_sets+1 entries and
@@ -112,7 +121,9 @@ typedef struct {
     int32_t cascade_b;         /* bmj_self_join: width of a second Bitmap Filter applied to the
                                   survivors before merging (0 = automatic: 256 when b < 256;
                                   -1 = none; otherwise a valid b larger than b) */
-    int32_t reserved0;
+    int32_t sim;               /* bmj_index_create: similarity function of every query on the
+                                  index (default BMJ_JACCARD); bmj_self_join and
+                                  bmj_self_join_batch take it as an argument instead */
     int64_t row_begin;         /* bmj_self_join: join only the pairs whose later set in size order
                                   (sets ordered by size, ties by id) has its position in */
     int64_t row_end;           /*   [row_begin, row_end); 0, 0 = every pair.  Bands that cover
@@ -186,8 +197,8 @@ int bmj_build_bitmaps(const bmj_collection *coll, int b, int method, uint64_t *o
  * Exact self-join with the Bitmap Filter (Section 4.2, Alg. 6, with the
  * verification moved onto the GPU).
  *   coll    collection (host or device)
- *   sim     BMJ_JACCARD (the only function implemented)
- *   p, q    threshold p/q, 0 < p <= q
+ *   sim     BMJ_JACCARD, BMJ_COSINE, BMJ_DICE or BMJ_OVERLAP
+ *   p, q    threshold p/q (ranges above; BMJ_ERR_INVALID_ARG outside them)
  *   opt     options (NULL = defaults)
  *   out     receives the library-owned, canonical pair list (free it with
  *           bmj_pairs_free); on error it is left empty
@@ -283,7 +294,9 @@ void bmj_default_serve_options(bmj_serve_options *opt);
 /*
  * Probe queries against the index: for every probe set x (host collection,
  * tokens strictly increasing) the resident sets s with
- * Jaccard(x, s) >= p[x]/q[x] (an RS-join with |R| = 1, Eq. 1).  Candidates
+ * sim(x, s) >= p[x]/q[x] (an RS-join with |R| = 1, Eq. 1), sim being the
+ * index's function (bmj_options.sim at creation; thresholds outside its range
+ * give BMJ_ERR_INVALID_ARG).  Candidates
  * are the resident sets inside both sides of the length window (Table 2),
  * filtered by the Eq. 2 bound and verified exactly.  Runs as one batch and
  * returns when done.  out is filled (free with bmj_id_lists_free); stats

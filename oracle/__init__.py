@@ -76,6 +76,8 @@ def lib():
         L.oracle_filter_counts.restype = None
         L.oracle_combined_method.argtypes = [i64, i64]
         L.oracle_combined_method.restype = C.c_int
+        L.oracle_combined_method_sim.argtypes = [C.c_int, i64, i64]
+        L.oracle_combined_method_sim.restype = C.c_int
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         L.oracle_free.argtypes = [C.c_void_p]
@@ -176,9 +178,10 @@ def search(probe, offsets, tokens, p: int, q: int, sim: int = JACCARD):
     return out
 
 
-def combined_method(p: int, q: int) -> int:
-    """Alg. 4's choice for threshold p/q (switch points on 2p/(p+q))."""
-    return int(lib().oracle_combined_method(p, q))
+def combined_method(p: int, q: int, sim: int = JACCARD) -> int:
+    """Alg. 4's choice for threshold p/q (switch points on the normalised overlap:
+    2p/(p+q) for Jaccard, p/q for Dice and Cosine; Xor for Overlap)."""
+    return int(lib().oracle_combined_method_sim(sim, p, q))
 
 
 def bitmap(tokens, b: int, method: int):

@@ -393,6 +393,18 @@ int oracle_combined_method(int64_t p, int64_t q)
     return OR_SET;
 }
 
+/* Alg. 4 for the other functions: the normalised overlap at the threshold of
+ * two sets of equal size n is tau*n/n = p/q for Dice and Cosine; an Overlap
+ * threshold counts tokens, so it keeps Xor (the paper's GPU choice). */
+int oracle_combined_method_sim(int sim, int64_t p, int64_t q)
+{
+    if (sim == OR_JACCARD) return oracle_combined_method(p, q);
+    if (sim == OR_OVERLAP) return OR_XOR;
+    if (p * 100 <= 56 * q) return OR_NEXT;
+    if (p * 100 >= 73 * q) return OR_XOR;
+    return OR_SET;
+}
+
 /*
  * Bitmap of one set x (n tokens) with b bits, written to out[0..b/64-1].
  *   Set  (Alg. 3a): bit h(t) <- 1 for every token t.

@@ -28,7 +28,7 @@ BMJ_ERR_CUDA = -8
 BMJ_ERR_TOO_LARGE = -9
 
 BMJ_XOR, BMJ_SET, BMJ_NEXT, BMJ_COMBINED = 0, 1, 2, 3
-BMJ_JACCARD = 0
+BMJ_JACCARD, BMJ_COSINE, BMJ_DICE, BMJ_OVERLAP = 0, 1, 2, 3   # similarity functions (Table 1)
 METHODS = {"xor": BMJ_XOR, "set": BMJ_SET, "next": BMJ_NEXT, "combined": BMJ_COMBINED}
 
 
@@ -71,7 +71,7 @@ class bmj_options(C.Structure):
     _fields_ = [("b", C.c_int32), ("method", C.c_int32), ("output_on_device", C.c_int32),
                 ("validate", C.c_int32), ("queue_cap", C.c_int64), ("stream", C.c_void_p),
                 ("rows_per_thread", C.c_int32), ("use_graph", C.c_int32),
-                ("cascade_b", C.c_int32), ("reserved0", C.c_int32), ("row_begin", C.c_int64),
+                ("cascade_b", C.c_int32), ("sim", C.c_int32), ("row_begin", C.c_int64),
                 ("row_end", C.c_int64), ("reserved", C.c_int32 * 2)]
 
 
@@ -415,11 +415,13 @@ def _take_id_lists(lists: bmj_id_lists):
 class Index:
     """A resident index (bmj_index_create / bmj_index_destroy)."""
 
-    def __init__(self, offsets, tokens, b: int = 64, method: int = BMJ_XOR, validate: bool = True):
+    def __init__(self, offsets, tokens, b: int = 64, method: int = BMJ_XOR, validate: bool = True,
+                 sim: int = BMJ_JACCARD):
         coll, keep = make_collection(offsets, tokens)
         o = bmj_default_options()
         o.b = int(b)
         o.method = int(method)
+        o.sim = int(sim)
         o.validate = 1 if validate else 0
         o.stream = _stream_of(None, coll.on_device)
         h = C.c_void_p()

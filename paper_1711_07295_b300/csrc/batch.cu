@@ -44,6 +44,8 @@ struct JobDesc {
     int32_t W;
     int32_t tile_rows;
     int32_t chunk_cols;
+    int32_t sim;         // similarity function of the threshold p/q
+    SimWindow win;       // its length window (Table 2)
     int32_t pad;
 };
 
@@ -103,15 +105,15 @@ __global__ void k_unpack_local(const uint64_t *__restrict__ keys, int64_t n, int
 
 __global__ void k_batch_tables(int32_t *__restrict__ need, int32_t *__restrict__ lim, int64_t n_s,
                                const uint32_t *__restrict__ jp, const uint32_t *__restrict__ jq,
-                               int64_t n_jobs) {
+                               int64_t n_jobs, int sim) {
     const int64_t total = n_s * n_jobs;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
         const int64_t k = x / n_s, S = x - k * n_s;
-        const uint64_t p = jp[k], d = (uint64_t)jp[k] + jq[k];
-        const uint64_t nd = ((uint64_t)S * p + d - 1) / d;  // ceil(p*S/(p+q)), Table 1
+        // e.g. Jaccard: ceil(p*S/(p+q)) (Table 1); Cosine computes it per pair
+        const int64_t nd = sim == BMJ_COSINE ? 0 : need_of_sum(sim, jp[k], jq[k], S);
         need[x] = (int32_t)nd;
-        lim[x] = (int32_t)((int64_t)S - 2 * (int64_t)nd);   // Eq. 2 with its floor
+        lim[x] = (int32_t)(S - 2 * nd);   // Eq. 2 with its floor
     }
 }
 
@@ -128,7 +130,7 @@ __global__ void k_batch_window(const uint32_t *__restrict__ ssz, const uint32_t 
         if (i < n) {
             k = sjob[i];
             const JobDesc &jd = jobs[k];
-            const uint64_t low = ((uint64_t)ssz[i] * jd.p + jd.q - 1) / jd.q;
+            const uint64_t low = window_low(ssz[i], jd.win);
             const int64_t j0 = lower_bound_range(ssz, jd.base, i, low);
             v = (unsigned long long)(i - j0);
         }
@@ -152,7 +154,7 @@ __global__ void k_batch_tiles(const uint32_t *__restrict__ ssz, const JobDesc *_
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
         const JobDesc &jd = jobs[tl_job[t]];
         const int64_t i0 = jd.base + tl_local[t] * jd.tile_rows;
-        const uint64_t low = ((uint64_t)ssz[i0] * jd.p + jd.q - 1) / jd.q;
+        const uint64_t low = window_low(ssz[i0], jd.win);
         const int64_t c0 = lower_bound_range(ssz, jd.base, jd.end, low);  // j0 of the first row
         const int64_t i_end = min(i0 + (int64_t)jd.tile_rows, jd.end);
         const int64_t c_end = i_end - 1;
@@ -163,7 +165,7 @@ __global__ void k_batch_tiles(const uint32_t *__restrict__ ssz, const JobDesc *_
         if (tile_win) {
             unsigned long long w = 0;
             for (int64_t i = i0; i < i_end; i++) {
-                const uint64_t li = ((uint64_t)ssz[i] * jd.p + jd.q - 1) / jd.q;
+                const uint64_t li = window_low(ssz[i], jd.win);
                 w += (unsigned long long)(i - lower_bound_range(ssz, jd.base, i, li));
             }
             tile_win[t] = w;
@@ -199,12 +201,13 @@ struct BatchFilterArgs {
     unsigned long long *job_surv;  // per-job survivor counters
     int64_t qcap;
     int *err;                      // set when a bounded wait on a copy gave up
+    int sim;                       // similarity function of every job
 };
 
 // The Bitmap Filter over the work items of every job of one bitmap width:
 // tiles [t0, t1) (the jobs of that width are contiguous in the tile list),
 // items pulled from a per-class counter.  Columns are staged by TMA.
-template <int W, int R, int CS>
+template <int W, int R, int CS, bool kCos>
 __global__ void __launch_bounds__(128) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
                                                          int64_t t1, unsigned long long *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -226,8 +229,9 @@ __global__ void __launch_bounds__(128) k_filter_batch_w(const BatchFilterArgs a,
         const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
-        filter_item_tma<W, R, CS>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, jd.p,
-                                  jd.q, sink, stg);
+        const SimArgs sa{jd.win, jd.p, jd.q};
+        filter_item_tma<W, R, CS, 0, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, sa,
+                                           sink, stg);
         if (!stg.ok) {
             drain_stage(stg);
             if (lane == 0) atomicOr(a.err, 1);
@@ -256,8 +260,13 @@ __global__ void __launch_bounds__(256) k_filter_batch_generic(const BatchFilterA
         const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
-        filter_item_generic(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, jd.p, jd.q,
-                            jd.W, sink);
+        const SimArgs sa{jd.win, jd.p, jd.q};
+        if (jd.sim == BMJ_COSINE)
+            filter_item_generic<true>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, sa,
+                                      jd.W, sink);
+        else
+            filter_item_generic<false>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, sa,
+                                       jd.W, sink);
     }
 }
 
@@ -283,14 +292,16 @@ __global__ void __launch_bounds__(256)
             const uint32_t k = sjob[pr.x];
             const JobDesc &jd = jobs[k];
             const uint32_t si = ssz[pr.x], sj = ssz[pr.y];
-            int nd = need[jd.lim_off + si + sj];
+            const bool cosine = jd.sim == BMJ_COSINE;
+            int nd = cosine ? (int)cosine_need(jd.p, jd.q, si, sj) : need[jd.lim_off + si + sj];
             if (jd.bm2) {  // cascade: Eq. 2 again with the 256-bit bitmaps (sound for any b)
                 const uint64_t *r2 = jd.bm2 + (int64_t)pr.x * 4;
                 const uint64_t *c2 = jd.bm2 + (int64_t)pr.y * 4;
                 int h2 = 0;
 #pragma unroll
                 for (int w = 0; w < 4; w++) h2 += __popcll(r2[w] ^ c2[w]);
-                if (h2 > lim[jd.lim_off + si + sj]) nd = 0x7fffffff;  // cannot reach the threshold
+                const int l2 = cosine ? (int)si + (int)sj - 2 * nd : lim[jd.lim_off + si + sj];
+                if (h2 > l2) nd = 0x7fffffff;  // cannot reach the threshold
             }
             const int32_t *x = stok + soff[pr.x];
             const int32_t *y = stok + soff[pr.y];
@@ -354,6 +365,7 @@ struct Plan {
     int64_t *soff = nullptr;
     int32_t *stok = nullptr;
     int64_t n_s = 0;
+    int sim = BMJ_JACCARD;
     int32_t *need = nullptr, *lim = nullptr;
     JobDesc *jobs_dev = nullptr;
     std::vector<JobDesc> jobs;
@@ -433,23 +445,31 @@ int upload_jobs(Plan &P, Arena &A, cudaStream_t s) {
 
 int width_class(int W) { return W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3; }
 
+template <int W, int R, int CS, bool kCos>
+int launch_class_c(const BatchFilterArgs &fa, int64_t t0, int64_t t1, unsigned long long *counter,
+                   int sms, cudaStream_t s) {
+    const int smem = 4 * ColStage<W, CS>::kWarpBytes;
+    int per_sm = 0;
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_w<W, R, CS, kCos>,
+                                                            128, smem));
+    if (per_sm < 1) per_sm = 1;
+    BMJ_LAUNCH((k_filter_batch_w<W, R, CS, kCos>), (unsigned)(sms * per_sm), 128, smem, s, fa, t0,
+               t1, counter);
+    return BMJ_OK;
+}
+
 template <int W, int R, int CS>
 int launch_class(const BatchFilterArgs &fa, int64_t t0, int64_t t1, unsigned long long *counter,
                  int sms, cudaStream_t s) {
-    const int smem = 4 * ColStage<W, CS>::kWarpBytes;
-    int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_w<W, R, CS>, 128,
-                                                            smem));
-    if (per_sm < 1) per_sm = 1;
-    BMJ_LAUNCH((k_filter_batch_w<W, R, CS>), (unsigned)(sms * per_sm), 128, smem, s, fa, t0, t1,
-               counter);
-    return BMJ_OK;
+    return fa.sim == BMJ_COSINE ? launch_class_c<W, R, CS, true>(fa, t0, t1, counter, sms, s)
+                                : launch_class_c<W, R, CS, false>(fa, t0, t1, counter, sms, s);
 }
 
 // Filter over the planned items into the plan's queue (cap may be 0: count
 // only): one persistent launch per width class present.
 int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
     BatchFilterArgs fa;
+    fa.sim = P.sim;
     fa.jobs = P.jobs_dev;
     fa.ssz = P.ssz;
     fa.lim = P.lim;
@@ -527,7 +547,7 @@ int run_execute(const Plan &P, int sms, cudaStream_t s, bool use_graph, int *gra
     return st;
 }
 
-int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets,
+int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets, int sim,
                const uint32_t *hp, const uint32_t *hq, const bmj_options &o, bmj_pairs *outs,
                bmj_stats *job_stats, bmj_batch_stats *bst) {
     cudaStream_t s = (cudaStream_t)o.stream;
@@ -550,12 +570,13 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
     Plan P;
     P.n = d.n;
     P.n_jobs = n_jobs;
+    P.sim = sim;
     const int64_t n = d.n;
     std::vector<int64_t> result_bounds(n_jobs + 1, 0);
     std::vector<uint32_t> res_a, res_b;
     std::vector<int> job_b(n_jobs, o.b > 0 ? o.b : 64), job_method(n_jobs, o.method);
     for (int64_t k = 0; k < n_jobs; k++)
-        if (o.method == BMJ_COMBINED) job_method[k] = combined_method(hp[k], hq[k]);
+        if (o.method == BMJ_COMBINED) job_method[k] = combined_method(sim, hp[k], hq[k]);
     std::vector<unsigned long long> job_win(n_jobs, 0), job_sv(n_jobs, 0);
     int64_t max_job = 0;
     for (int64_t k = 0; k < n_jobs; k++) max_job = std::max(max_job, job_sets[k + 1] - job_sets[k]);
@@ -608,7 +629,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         BMJ_CHECK(cudaMemcpyAsync(jp, hp, n_jobs * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         BMJ_CHECK(cudaMemcpyAsync(jq, hq, n_jobs * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         BMJ_LAUNCH(k_batch_tables, grid_of(P.n_s * n_jobs, 256), 256, 0, s, P.need, P.lim, P.n_s, jp,
-                   jq, n_jobs);
+                   jq, n_jobs, sim);
 
         // ---- bitmaps: one array per (b, method) in use ----
         const bool tune = o.b <= 0;
@@ -677,6 +698,8 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 jd.lim_off = k * P.n_s;
                 jd.p = hp[k];
                 jd.q = hq[k];
+                jd.sim = sim;
+                jd.win = sim_window(sim, hp[k], hq[k]);
                 jd.W = jb[k] / 64;
                 jd.tile_rows = jd.W == 1 ? 32 * kTmaR1
                                : jd.W == 2 ? 32 * kTmaR2
@@ -1045,7 +1068,7 @@ int make_sub(const bmj_collection *coll, int64_t s0, int64_t s1, cudaStream_t s,
 // After an out-of-memory batch: the jobs run in two halves (recursively); a
 // single job that still does not fit runs as bmj_self_join, whose survivor
 // handling never needs all survivors in memory at once.
-int batch_in_parts(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets,
+int batch_in_parts(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets, int sim,
                    const uint32_t *hp, const uint32_t *hq, const bmj_options &o, bmj_pairs *outs,
                    bmj_stats *job_stats, bmj_batch_stats *bst) {
     cudaStream_t s = (cudaStream_t)o.stream;
@@ -1058,7 +1081,7 @@ int batch_in_parts(const bmj_collection *coll, int64_t n_jobs, const int64_t *jo
         so.use_graph = 0;
         bmj_stats js;
         memset(&js, 0, sizeof(js));
-        st = bmj_self_join(&sub.c, BMJ_JACCARD, hp[0], hq[0], &so, &outs[0], &js);
+        st = bmj_self_join(&sub.c, sim, hp[0], hq[0], &so, &outs[0], &js);
         if (st) return st;
         if (job_stats) job_stats[0] = js;
         bmj_batch_stats u;
@@ -1087,7 +1110,7 @@ int batch_in_parts(const bmj_collection *coll, int64_t n_jobs, const int64_t *jo
         bmj_batch_stats u;
         memset(&u, 0, sizeof(u));
         try {
-            st = batch_impl(&sub.c, k1 - k0, js.data(), hp + k0, hq + k0, o, outs + k0,
+            st = batch_impl(&sub.c, k1 - k0, js.data(), sim, hp + k0, hq + k0, o, outs + k0,
                             job_stats ? job_stats + k0 : nullptr, &u);
         } catch (...) {
             st = BMJ_ERR_OOM;
@@ -1096,7 +1119,7 @@ int batch_in_parts(const bmj_collection *coll, int64_t n_jobs, const int64_t *jo
             for (int64_t k = k0; k < k1; k++) bmj_pairs_free(&outs[k]);
             cudaGetLastError();
             memset(&u, 0, sizeof(u));
-            st = batch_in_parts(&sub.c, k1 - k0, js.data(), hp + k0, hq + k0, o, outs + k0,
+            st = batch_in_parts(&sub.c, k1 - k0, js.data(), sim, hp + k0, hq + k0, o, outs + k0,
                                 job_stats ? job_stats + k0 : nullptr, &u);
         }
         if (st) return st;
@@ -1115,14 +1138,14 @@ extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
     if (batch_stats) memset(batch_stats, 0, sizeof(*batch_stats));
     if (!coll || !job_sets || !outs || n_jobs <= 0 || !p || !q) return BMJ_ERR_INVALID_ARG;
     for (int64_t k = 0; k < n_jobs; k++) memset(&outs[k], 0, sizeof(bmj_pairs));
-    if (sim != BMJ_JACCARD) return BMJ_ERR_INVALID_ARG;
+    if (sim < BMJ_JACCARD || sim > BMJ_OVERLAP) return BMJ_ERR_INVALID_ARG;
     if (coll->n_sets < 0 || !coll->offsets || (coll->n_sets > 0 && !coll->tokens))
         return BMJ_ERR_INVALID_ARG;
     if (coll->n_sets > 0x7fffffffLL || n_jobs > 0x7fffffffLL) return BMJ_ERR_TOO_LARGE;
     if (job_sets[0] != 0 || job_sets[n_jobs] != coll->n_sets) return BMJ_ERR_INVALID_ARG;
     for (int64_t k = 0; k < n_jobs; k++) {
         if (job_sets[k + 1] < job_sets[k]) return BMJ_ERR_INVALID_ARG;
-        if (p[k] == 0 || q[k] == 0 || p[k] > q[k]) return BMJ_ERR_INVALID_ARG;
+        if (!bmj::sim_valid(sim, p[k], q[k])) return BMJ_ERR_INVALID_ARG;
     }
     bmj_options o;
     if (opt) o = *opt;
@@ -1136,7 +1159,7 @@ extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
     memset(&bs, 0, sizeof(bs));
     bmj::arm_alloc_fault(bmj::read_fault_plan().alloc_at);  // tests: BMJ_FAULT=alloc:K
     try {
-        st = bmj::batch_impl(coll, n_jobs, job_sets, p, q, o, outs, job_stats, &bs);
+        st = bmj::batch_impl(coll, n_jobs, job_sets, sim, p, q, o, outs, job_stats, &bs);
     } catch (...) {
         st = BMJ_ERR_OOM;
     }
@@ -1146,7 +1169,7 @@ extern "C" int bmj_self_join_batch(const bmj_collection *coll, int64_t n_jobs,
         cudaGetLastError();
         memset(&bs, 0, sizeof(bs));
         try {
-            st = bmj::batch_in_parts(coll, n_jobs, job_sets, p, q, o, outs, job_stats, &bs);
+            st = bmj::batch_in_parts(coll, n_jobs, job_sets, sim, p, q, o, outs, job_stats, &bs);
         } catch (...) {
             st = BMJ_ERR_OOM;
         }

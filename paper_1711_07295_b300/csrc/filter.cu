@@ -16,10 +16,11 @@ constexpr unsigned kFull = 0xffffffffu;
 // Bitmap Filter (per-item body in filter_core.cuh).  Warps pull work items
 // (row tile, column chunk) from a global counter: a persistent grid that
 // balances the uneven band of the size-sorted triangle.
-template <int W, int R>
+template <int W, int R, bool kCos>
 __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
     const int lane = threadIdx.x & 31;
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -32,13 +33,14 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
         const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item<W, R>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, sink);
+        filter_item<W, R, kCos>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, sa, sink);
     }
 }
 
 __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int W) {
     const int lane = threadIdx.x & 31;
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -51,14 +53,17 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
         const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_generic(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, a.p, a.q, W, sink);
+        if (a.sim == BMJ_COSINE)
+            filter_item_generic<true>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, sa, W, sink);
+        else
+            filter_item_generic<false>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, sa, W, sink);
     }
 }
 
 // Bitmap Filter with TMA-staged columns (filter_item_tma).  Each warp owns a
 // double buffer of column chunks in dynamic shared memory and its two
 // mbarriers; a wait that gives up sets *err and stops the warp.
-template <int W, int R, int CS, bool kFault>
+template <int W, int R, int CS, bool kFault, bool kCos>
 __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     using L = ColStage<W, CS>;
@@ -70,6 +75,7 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
         st.skip_copy = (blockIdx.x == 0 && threadIdx.x < 32) ? 1 : 0;
     }
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -82,8 +88,8 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
         const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0)>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1,
-                                                             a.p, a.q, sink, st);
+        filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0), kCos>(a.bm, a.ssz, a.lim, row_end, i0,
+                                                                   c0, c1, sa, sink, st);
         if (!st.ok) {
             drain_stage(st);
             if (lane == 0) atomicOr(err, 1);
@@ -92,18 +98,24 @@ __global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err
     }
 }
 
-template <int W, int R>
-int launch_filter_t(const FilterArgs &a, int num_sms, cudaStream_t s) {
+template <int W, int R, bool kCos>
+int launch_filter_c(const FilterArgs &a, int num_sms, cudaStream_t s) {
     int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<W, R>, 256, 0));
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter<W, R, kCos>, 256, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t warps_needed = a.n_items;
     int64_t blocks = (int64_t)num_sms * per_sm;
     const int64_t need_blocks = (warps_needed + 7) / 8;
     if (need_blocks < blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
-    BMJ_LAUNCH((k_filter<W, R>), (unsigned)blocks, 256, 0, s, a);
+    BMJ_LAUNCH((k_filter<W, R, kCos>), (unsigned)blocks, 256, 0, s, a);
     return BMJ_OK;
+}
+
+template <int W, int R>
+int launch_filter_t(const FilterArgs &a, int num_sms, cudaStream_t s) {
+    return a.sim == BMJ_COSINE ? launch_filter_c<W, R, true>(a, num_sms, s)
+                               : launch_filter_c<W, R, false>(a, num_sms, s);
 }
 
 }  // namespace
@@ -137,26 +149,28 @@ int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s) {
     }
 }
 
-template <int W, int R, int CS, bool kFault>
+template <int W, int R, int CS, bool kFault, bool kCos>
 int launch_filter_tma_k(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
     using L = ColStage<W, CS>;
     const int smem = 4 * L::kWarpBytes;
     int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_tma<W, R, CS, kFault>,
-                                                            128, smem));
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_filter_tma<W, R, CS, kFault, kCos>, 128, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)num_sms * per_sm;
     const int64_t need_blocks = (a.n_items + 3) / 4;
     if (need_blocks < blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
-    BMJ_LAUNCH((k_filter_tma<W, R, CS, kFault>), (unsigned)blocks, 128, smem, s, a, err);
+    BMJ_LAUNCH((k_filter_tma<W, R, CS, kFault, kCos>), (unsigned)blocks, 128, smem, s, a, err);
     return BMJ_OK;
 }
 
 template <int W, int R, int CS>
 int launch_filter_tma_t(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
-    return a.fault_skip_copy ? launch_filter_tma_k<W, R, CS, true>(a, err, num_sms, s)
-                             : launch_filter_tma_k<W, R, CS, false>(a, err, num_sms, s);
+    if (a.sim == BMJ_COSINE)  // (fault injection is exercised with the other functions)
+        return launch_filter_tma_k<W, R, CS, false, true>(a, err, num_sms, s);
+    return a.fault_skip_copy ? launch_filter_tma_k<W, R, CS, true, false>(a, err, num_sms, s)
+                             : launch_filter_tma_k<W, R, CS, false, false>(a, err, num_sms, s);
 }
 
 int filter_tma_tile_rows(int W) {

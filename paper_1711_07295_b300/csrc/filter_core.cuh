@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sim.cuh"
+
 namespace bmj {
 
 __device__ __forceinline__ int warp_excl_scan_i(int v) {
@@ -43,12 +45,27 @@ struct SurvivorSink {
     int64_t cap;
 };
 
-template <int W, int R>
+// The similarity function's window (Table 2) and threshold.
+struct SimArgs {
+    SimWindow win;
+    uint32_t p, q;
+};
+
+// Eq. 2 limit of a pair of sizes: from the table indexed by |x|+|y| (Jaccard,
+// Dice, Overlap), or computed (Cosine, whose limit depends on |x|*|y|).
+template <bool kCos>
+__device__ __forceinline__ int32_t pair_lim(const int32_t *__restrict__ lim_tab, uint32_t x,
+                                            uint32_t y, const SimArgs &sa) {
+    if (kCos) return (int32_t)sim_lim(BMJ_COSINE, sa.p, sa.q, x, y);
+    return lim_tab[x + y];
+}
+
+template <int W, int R, bool kCos = false>
 __device__ __forceinline__ void filter_item(const uint64_t *__restrict__ bm,
                                             const uint32_t *__restrict__ ssz,
                                             const int32_t *__restrict__ lim_tab, int64_t row_end,
-                                            int64_t i0, int64_t c0, int64_t c1, uint32_t p,
-                                            uint32_t q, const SurvivorSink &sink) {
+                                            int64_t i0, int64_t c0, int64_t c1, const SimArgs &sa,
+                                            const SurvivorSink &sink) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     uint64_t rb[R][W];
@@ -100,8 +117,8 @@ __device__ __forceinline__ void filter_item(const uint64_t *__restrict__ bm,
 #pragma unroll
                 for (int k = 0; k < R; k++) {
                     const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
-                    const bool in_win = rs[k] != 0 && (uint64_t)q * mn >= (uint64_t)p * mx;
-                    lim[k] = in_win ? lim_tab[rs[k] + s] : -1;
+                    const bool in_win = rs[k] != 0 && in_window(mn, mx, sa.win);
+                    lim[k] = in_win ? pair_lim<kCos>(lim_tab, rs[k], s, sa) : -1;
                 }
             }
 #pragma unroll
@@ -144,11 +161,12 @@ __device__ __forceinline__ void filter_item(const uint64_t *__restrict__ bm,
 
 // Generic width (b not in {64,128,256,512}): one row per lane, bitmaps read
 // word by word from memory.
+template <bool kCos = false>
 __device__ __forceinline__ void filter_item_generic(const uint64_t *__restrict__ bm,
                                                     const uint32_t *__restrict__ ssz,
                                                     const int32_t *__restrict__ lim_tab,
                                                     int64_t row_end, int64_t i0, int64_t c0,
-                                                    int64_t c1, uint32_t p, uint32_t q, int W,
+                                                    int64_t c1, const SimArgs &sa, int W,
                                                     const SurvivorSink &sink) {
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -162,12 +180,12 @@ __device__ __forceinline__ void filter_item_generic(const uint64_t *__restrict__
             const int64_t jj = j + cc;
             const uint32_t s = ssz[jj];
             const uint32_t mn = min(rs, s), mx = max(rs, s);
-            const bool in_win = rs != 0 && (uint64_t)q * mn >= (uint64_t)p * mx;
+            const bool in_win = rs != 0 && in_window(mn, mx, sa.win);
             if (!in_win || jj >= i) continue;
             const uint64_t *colp = bm + jj * W;
             int h = 0;
             for (int w = 0; w < W; w++) h += __popcll(rowp[w] ^ colp[w]);
-            if (h <= lim_tab[rs + s]) mask |= 1u << cc;
+            if (h <= pair_lim<kCos>(lim_tab, rs, s, sa)) mask |= 1u << cc;
         }
         const int cnt = __popc(mask);
         const int total = __reduce_add_sync(kFull, cnt);
@@ -391,12 +409,12 @@ __device__ __forceinline__ void stage_issue(StageState &st, int slot,
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
 // arrays must be readable up to 3 entries past the last column (padded).
-template <int W, int R, int CS, int kAluRows = 0>
+template <int W, int R, int CS, int kAluRows = 0, bool kCos = false>
 __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                                                 const uint32_t *__restrict__ ssz,
                                                 const int32_t *__restrict__ lim_tab,
                                                 int64_t row_end, int64_t i0, int64_t c0, int64_t c1,
-                                                uint32_t p, uint32_t q, const SurvivorSink &sink,
+                                                const SimArgs &sa, const SurvivorSink &sink,
                                                 StageState &st) {
     using L = ColStage<W, CS>;
     constexpr unsigned kFull = 0xffffffffu;
@@ -470,8 +488,8 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
 #pragma unroll
                     for (int k = 0; k < R; k++) {
                         const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
-                        const bool in_win = rs[k] != 0 && (uint64_t)q * mn >= (uint64_t)p * mx;
-                        nlim[k] = in_win ? -(lim_tab[rs[k] + s] + 1) : 0;
+                        const bool in_win = rs[k] != 0 && in_window(mn, mx, sa.win);
+                        nlim[k] = in_win ? -(pair_lim<kCos>(lim_tab, rs[k], s, sa) + 1) : 0;
                     }
                 }
                 uint32_t cw[2 * W];

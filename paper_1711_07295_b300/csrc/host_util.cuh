@@ -37,6 +37,19 @@ inline int combined_method(uint32_t p, uint32_t q) {
     return BMJ_SET;
 }
 
+// Alg. 4 for any function: the switch points apply to the normalised overlap of
+// two equal-sized sets at the threshold (Jaccard 2p/(p+q) above; Dice and Cosine
+// p/q itself); an Overlap threshold counts tokens and is not normalised, so Xor
+// (the paper's GPU choice) is kept.
+inline int combined_method(int sim, uint32_t p, uint32_t q) {
+    if (sim == BMJ_JACCARD) return combined_method(p, q);
+    if (sim == BMJ_OVERLAP) return BMJ_XOR;
+    const uint64_t P = p, Q = q;
+    if (100 * P <= 56 * Q) return BMJ_NEXT;
+    if (100 * P >= 73 * Q) return BMJ_XOR;
+    return BMJ_SET;
+}
+
 inline int flags_to_status(int flags) {
     if (flags & kFlagTooLarge) return BMJ_ERR_TOO_LARGE;
     if (flags & kFlagUnsorted) return BMJ_ERR_UNSORTED;

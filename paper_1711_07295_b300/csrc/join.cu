@@ -71,7 +71,7 @@ static int64_t auto_queue_cap(int64_t window) {
     return cap;
 }
 
-static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
+static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
                           const bmj_options &o, bmj_pairs *out, bmj_stats *stats) {
     cudaStream_t s = (cudaStream_t)o.stream;
     const int64_t launches0 = launches();
@@ -85,7 +85,7 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
     memset(&stl, 0, sizeof(stl));
     const int b = o.b;
     const int W = b / 64;
-    int method = o.method == BMJ_COMBINED ? combined_method(p, q) : o.method;
+    int method = o.method == BMJ_COMBINED ? combined_method(sim, p, q) : o.method;
     stl.b = b;
     stl.method = method;
 
@@ -154,6 +154,7 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
 
         // ---- thresholds per |x|+|y|, window tiles, window size ----
         const int64_t n_s = 2 * (int64_t)max_size + 1;
+        const SimWindow win = sim_window(sim, p, q);
         int32_t *need = nullptr, *lim = nullptr;
         const int tile_rows = filter_tma_tile_rows(W);
         const int chunk_cols = W <= 4 ? 4096 : 2048;
@@ -179,11 +180,12 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         BMJ_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
         BMJ_CHECK(cudaMemsetAsync(ssz + n, 0, 4 * sizeof(uint32_t), s));
         BMJ_CHECK(cudaMemsetAsync(bm + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
-        st = launch_tables(need, lim, n_s, p, q, s);
+        st = launch_tables(need, lim, n_s, sim, p, q, s);
         if (!st)
-            st = launch_tiles(ssz, n, p, q, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s, r0, r1);
+            st = launch_tiles(ssz, n, win, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s, r0,
+                              r1);
         if (!st) st = exclusive_scan_i64(tile_off, tile_off, n_tiles, tile_off + n_tiles, A, s);
-        if (!st) st = launch_window_count(ssz, n, p, q, &ctr[0], s, r0, r1);
+        if (!st) st = launch_window_count(ssz, n, win, &ctr[0], s, r0, r1);
         if (st) return st;
         BMJ_CHECK(cudaEventRecord(ev.e[2], s));
         int64_t hv[2] = {0, 0};
@@ -213,6 +215,7 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
         fa.row0 = r0;
         fa.row_end = r1;
         fa.p = p;
+        fa.sim = sim;
         fa.q = q;
         fa.tile_item_off = tile_off;
         fa.tile_c0 = tile_c0;
@@ -252,7 +255,7 @@ static int self_join_impl(const bmj_collection *coll, uint32_t p, uint32_t q,
             BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
             BMJ_CHECK(cudaEventRecord(ev.e[5], s));
             int rc = launch_verify(qptr, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
-                                   &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms, s);
+                                   &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms, s, sim, p, q);
             if (rc) return rc;
             BMJ_CHECK(cudaEventRecord(ev.e[6], s));
             int64_t hv2[2] = {0, 0};
@@ -540,8 +543,7 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (stats) memset(stats, 0, sizeof(*stats));
     int st = check_collection(coll);
     if (st) return st;
-    if (sim != BMJ_JACCARD) return BMJ_ERR_INVALID_ARG;
-    if (p == 0 || q == 0 || p > q) return BMJ_ERR_INVALID_ARG;
+    if (!bmj::sim_valid(sim, p, q)) return BMJ_ERR_INVALID_ARG;
     bmj_options o;
     if (opt) o = *opt;
     else bmj_default_options(&o);
@@ -552,7 +554,7 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (o.row_begin < 0 || o.row_end < 0 || o.row_end < o.row_begin) return BMJ_ERR_INVALID_ARG;
     if ((o.row_begin != 0 || o.row_end != 0) && o.row_end > coll->n_sets) return BMJ_ERR_INVALID_ARG;
     try {
-        st = bmj::self_join_impl(coll, p, q, o, out, stats);
+        st = bmj::self_join_impl(coll, sim, p, q, o, out, stats);
     } catch (...) {
         st = BMJ_ERR_OOM;
     }

@@ -29,10 +29,6 @@ __device__ __forceinline__ int64_t lower_bound_u32(const uint32_t *a, int64_t n,
     return lo;
 }
 
-// Smallest size s' with q*s' >= p*s, i.e. ceil(p*s/q) (Table 2, Jaccard row, integer form).
-__device__ __forceinline__ uint64_t window_low(uint64_t s, uint32_t p, uint32_t q) {
-    return (s * p + q - 1) / q;
-}
 
 // ----------------------------------------------------------------------------
 __global__ void k_validate(const int64_t *__restrict__ off, const int32_t *__restrict__ tok,
@@ -215,27 +211,28 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// need[S] / lim[S] for the functions whose smallest passing overlap depends on
+// S = |x|+|y| alone (Jaccard, Dice, Overlap; Cosine computes them per pair).
 __global__ void k_tables(int32_t *__restrict__ need, int32_t *__restrict__ lim, int64_t n_s,
-                         uint32_t p, uint32_t q) {
+                         int sim, uint32_t p, uint32_t q) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t d = (uint64_t)p + q;
     for (int64_t S = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; S < n_s; S += stride) {
-        // Jaccard >= p/q  <=>  o*(p+q) >= p*S  <=>  o >= ceil(p*S/(p+q)) (Table 1).
-        const uint64_t nd = ((uint64_t)S * p + d - 1) / d;
+        // e.g. Jaccard >= p/q  <=>  o*(p+q) >= p*S  <=>  o >= ceil(p*S/(p+q)) (Table 1).
+        const int64_t nd = sim == BMJ_COSINE ? 0 : need_of_sum(sim, p, q, S);
         need[S] = (int32_t)nd;
         // floor((S - h)/2) >= nd  <=>  h <= S - 2*nd (Eq. 2 with its floor).
-        lim[S] = (int32_t)((int64_t)S - 2 * (int64_t)nd);
+        lim[S] = (int32_t)(S - 2 * nd);
     }
 }
 
-__global__ void k_tiles(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p, uint32_t q,
+__global__ void k_tiles(const uint32_t *__restrict__ ssz, int64_t n, SimWindow win,
                         int tile_rows, int chunk_cols, int64_t n_tiles,
                         int32_t *__restrict__ tile_c0, int64_t *__restrict__ tile_items,
                         int64_t row0, int64_t row_end) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
         const int64_t i0 = row0 + t * tile_rows;
-        const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i0], p, q));
+        const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i0], win));
         const int64_t c0 = j0 & ~(int64_t)3;
         const int64_t c_end = min(i0 + (int64_t)tile_rows, row_end) - 1;  // columns j < i <= c_end
         const int64_t cols = c_end - c0;
@@ -244,13 +241,13 @@ __global__ void k_tiles(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p,
     }
 }
 
-__global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, uint32_t p,
-                               uint32_t q, unsigned long long *__restrict__ out, int64_t row0,
+__global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, SimWindow win,
+                               unsigned long long *__restrict__ out, int64_t row0,
                                int64_t row_end) {
     unsigned long long acc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = row0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < row_end; i += stride) {
-        const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i], p, q));
+        const int64_t j0 = lower_bound_u32(ssz, n, window_low(ssz[i], win));
         if (j0 < i) acc += (unsigned long long)(i - j0);
     }
     for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(kFull, acc, d);
@@ -298,26 +295,26 @@ int launch_build_multi(const uint32_t *perm, const int64_t *off, const int32_t *
     return BMJ_OK;
 }
 
-int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, uint32_t p, uint32_t q,
+int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, int sim, uint32_t p, uint32_t q,
                   cudaStream_t s) {
-    BMJ_LAUNCH(k_tables, grid_for(n_s, 256), 256, 0, s, need, lim, n_s, p, q);
+    BMJ_LAUNCH(k_tables, grid_for(n_s, 256), 256, 0, s, need, lim, n_s, sim, p, q);
     return BMJ_OK;
 }
 
-int launch_tiles(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q, int tile_rows,
+int launch_tiles(const uint32_t *ssz, int64_t n, SimWindow win, int tile_rows,
                  int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int64_t *tile_items,
                  cudaStream_t s, int64_t row0, int64_t row_end) {
     if (n_tiles <= 0) return BMJ_OK;
-    BMJ_LAUNCH(k_tiles, grid_for(n_tiles, 256), 256, 0, s, ssz, n, p, q, tile_rows, chunk_cols,
+    BMJ_LAUNCH(k_tiles, grid_for(n_tiles, 256), 256, 0, s, ssz, n, win, tile_rows, chunk_cols,
                n_tiles, tile_c0, tile_items, row0, row_end < 0 ? n : row_end);
     return BMJ_OK;
 }
 
-int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
+int launch_window_count(const uint32_t *ssz, int64_t n, SimWindow win,
                         unsigned long long *out, cudaStream_t s, int64_t row0, int64_t row_end) {
     if (row_end < 0) row_end = n;
     if (row_end <= row0) return BMJ_OK;
-    BMJ_LAUNCH(k_window_count, grid_for(row_end - row0, 256), 256, 0, s, ssz, n, p, q, out, row0,
+    BMJ_LAUNCH(k_window_count, grid_for(row_end - row0, 256), 256, 0, s, ssz, n, win, out, row0,
                row_end);
     return BMJ_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "bmj_internal.cuh"
+#include "sim.cuh"
 
 namespace bmj {
 
@@ -41,18 +42,18 @@ int launch_build_multi(const uint32_t *perm, const int64_t *off, const int32_t *
 // need[S] = ceil(p*S/(p+q)) (the smallest overlap with Jaccard >= p/q when
 // |x|+|y| = S) and lim[S] = S - 2*need[S] (the largest Hamming distance
 // whose Eq. 2 bound still reaches need[S]), for S in [0, n_s).
-int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, uint32_t p, uint32_t q,
+int launch_tables(int32_t *need, int32_t *lim, int64_t n_s, int sim, uint32_t p, uint32_t q,
                   cudaStream_t s);
 
 // Row tiles of `tile_rows` sorted rows: first window column (j0 of the tile's
 // first row, rounded down to a multiple of 4) and the number of column chunks
 // of `chunk_cols` columns.
-int launch_tiles(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q, int tile_rows,
+int launch_tiles(const uint32_t *ssz, int64_t n, SimWindow win, int tile_rows,
                  int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int64_t *tile_items,
                  cudaStream_t s, int64_t row0 = 0, int64_t row_end = -1);
 
 // Sum over sorted rows i of (i - j0(i)): the pairs inside the length window.
-int launch_window_count(const uint32_t *ssz, int64_t n, uint32_t p, uint32_t q,
+int launch_window_count(const uint32_t *ssz, int64_t n, SimWindow win,
                         unsigned long long *out, cudaStream_t s, int64_t row0 = 0,
                         int64_t row_end = -1);
 
@@ -66,6 +67,7 @@ struct FilterArgs {
     int wait_limit = 0;     // TMA filter: polls before a copy wait gives up (0: default)
     int fault_skip_copy = 0;  // fault injection: one warp skips one copy (the wait runs out)
     uint32_t p, q;
+    int sim = BMJ_JACCARD;  // similarity function of the threshold p/q
     const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
     const int32_t *tile_c0;
     int64_t n_tiles;
@@ -110,7 +112,7 @@ int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const
                   const uint32_t *ssz, const uint32_t *perm, const int32_t *need,
                   const int32_t *lim, const uint64_t *bm2, int W2, uint64_t *keys,
                   unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
-                  cudaStream_t s);
+                  cudaStream_t s, int sim = BMJ_JACCARD, uint32_t p = 0, uint32_t q = 0);
 
 // Splits packed keys into the (a, b) arrays of the output.
 int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,

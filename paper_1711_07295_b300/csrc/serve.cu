@@ -31,7 +31,7 @@
 
 struct bmj_index {
     int device = 0;
-    int b = 64, W = 1, method = BMJ_XOR;
+    int b = 64, W = 1, method = BMJ_XOR, sim = BMJ_JACCARD;
     int64_t n = 0;
     int max_size = 0;
     uint32_t *ssz = nullptr;  // n + 4
@@ -66,15 +66,15 @@ __global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
                                 const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
                                 const uint32_t *__restrict__ ssz, int64_t n,
                                 int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
-                                int64_t *__restrict__ items) {
+                                int64_t *__restrict__ items, int sim) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nq; x += stride) {
         const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
-        const uint64_t p = pp[x], q = pq[x];
-        const uint64_t low = (p * sx + q - 1) / q;   // ceil(p|x|/q)
-        const uint64_t high = (q * sx) / p;          // floor(q|x|/p)
+        const SimWindow w = sim_window(sim, pp[x], pq[x]);
+        const uint64_t low = window_low(sx, w);     // e.g. Jaccard: ceil(p|x|/q)
+        const uint64_t high = window_high(sx, w);   // e.g. Jaccard: floor(q|x|/p); ~0: none
         const int64_t lo = lb_sizes(ssz, n, low);
-        const int64_t hi = lb_sizes(ssz, n, high + 1);
+        const int64_t hi = high == ~0ull ? n : lb_sizes(ssz, n, high + 1);
         wlo[x] = lo;
         whi[x] = hi;
         items[x] = hi > lo ? (hi - lo + kQueryChunk - 1) / kQueryChunk : 0;
@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256)
                    const int64_t *__restrict__ wlo, const int64_t *__restrict__ whi,
                    const int64_t *__restrict__ item_off, int64_t nq,
                    const uint64_t *__restrict__ bm, const uint32_t *__restrict__ ssz, int W,
-                   uint2 *__restrict__ queue, unsigned long long *__restrict__ qcount, int64_t qcap) {
+                   uint2 *__restrict__ queue, unsigned long long *__restrict__ qcount, int64_t qcap,
+                   int sim) {
     const int lane = threadIdx.x & 31;
     const int64_t n_items = item_off[nq];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256)
         const int64_t c0 = wlo[x] + (item - item_off[x]) * kQueryChunk;
         const int64_t c1 = min(c0 + (int64_t)kQueryChunk, whi[x]);
         const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
-        const uint64_t p = pp[x], pq2 = (uint64_t)pp[x] + pq[x];
+        const uint32_t p = pp[x], q = pq[x];
         for (int64_t j0 = c0; j0 < c1; j0 += 32) {
             const int64_t j = j0 + lane;
             bool sv = false;
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(256)
                 int h = 0;
                 for (int w = 0; w < W; w++) h += __popcll(pbm[x * W + w] ^ bm[j * W + w]);
                 const uint64_t S = sx + ssz[j];
-                const uint64_t ub = (S - (uint64_t)h) >> 1;
-                sv = ub * pq2 >= p * S;
+                const int64_t ub = (int64_t)((S - (uint64_t)h) >> 1);   // Eq. 2
+                sv = ub >= sim_need(sim, p, q, (int64_t)sx, (int64_t)ssz[j]);
             }
             const unsigned ball = __ballot_sync(kFullQ, sv);
             if (ball) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256)
                    const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
                    const int64_t *__restrict__ soff, const int32_t *__restrict__ stok,
                    const uint32_t *__restrict__ ssz, const uint32_t *__restrict__ perm,
-                   uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount) {
+                   uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount, int sim) {
     const int lane = threadIdx.x & 31;
     const int64_t n_surv = min((int64_t)*qcount, qcap);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -151,8 +152,7 @@ __global__ void __launch_bounds__(256)
             const int na = (int)(poff[pr.x + 1] - poff[pr.x]);
             const int32_t *y = stok + soff[pr.y];
             const int nb = (int)ssz[pr.y];
-            const uint64_t p = pp[pr.x], d = (uint64_t)pp[pr.x] + pq[pr.x];
-            const int nd = (int)((p * (uint64_t)(na + nb) + d - 1) / d);
+            const int nd = (int)sim_need(sim, pp[pr.x], pq[pr.x], na, nb);
             int a = 0, b = 0, o = 0;
             while (a < na && b < nb) {
                 if (o + min(na - a, nb - b) < nd) break;
@@ -290,9 +290,11 @@ int alloc_slot(Slot &s, int64_t q_cap, int64_t tok_cap, int64_t pair_cap, int W)
 
 // Exact number of resident sets inside the window of a probe of size sx.
 int64_t window_of(const bmj_index *idx, int64_t sx, uint32_t p, uint32_t q) {
-    const int64_t low = ((int64_t)p * sx + q - 1) / q;
-    const int64_t high = ((int64_t)q * sx) / p;
+    const SimWindow w = sim_window(idx->sim, p, q);
+    const uint64_t lo_u = window_low((uint64_t)sx, w), hi_u = window_high((uint64_t)sx, w);
     const int64_t ms = (int64_t)idx->size_cum.size() - 1;
+    const int64_t low = (int64_t)std::min<uint64_t>(lo_u, (uint64_t)ms);
+    const int64_t high = (int64_t)std::min<uint64_t>(hi_u, (uint64_t)ms);
     auto cum = [&](int64_t s) { return idx->size_cum[(size_t)std::min(std::max<int64_t>(s, 0), ms)]; };
     return std::max<int64_t>(0, cum(high + 1) - cum(low));
 }
@@ -312,16 +314,16 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
                                  idx->method, st);
     if (rc) return rc;
     BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q, idx->ssz,
-               idx->n, s.d_lo, s.d_hi, s.d_items);
+               idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim);
     Arena A(st);
     rc = exclusive_scan_i64(s.d_items, s.d_items, nq, s.d_items + nq, A, st);
     if (rc) return rc;
     BMJ_LAUNCH(k_query_filter, (unsigned)(sms * 8), 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
                s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],
-               s.pair_cap);
+               s.pair_cap, idx->sim);
     BMJ_LAUNCH(k_query_verify, (unsigned)(sms * 4), 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
                s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
-               &s.d_ctr[1]);
+               &s.d_ctr[1], idx->sim);
     BMJ_CHECK(cudaMemcpyAsync(s.h_ctr, s.d_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     // the first keys come back with the counters: a batch with few results then
     // finishes on the host without a second round trip (finish_on_host)
@@ -409,6 +411,7 @@ extern "C" int bmj_index_create(const bmj_collection *coll, const bmj_options *o
     else bmj_default_options(&o);
     if (!valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
     if (o.method != BMJ_XOR && o.method != BMJ_SET && o.method != BMJ_NEXT) return BMJ_ERR_INVALID_ARG;
+    if (o.sim < BMJ_JACCARD || o.sim > BMJ_OVERLAP) return BMJ_ERR_INVALID_ARG;
     bmj_index *idx = new (std::nothrow) bmj_index();
     if (!idx) return BMJ_ERR_OOM;
     cudaStream_t s = (cudaStream_t)o.stream;
@@ -425,6 +428,7 @@ extern "C" int bmj_index_create(const bmj_collection *coll, const bmj_options *o
             idx->b = o.b;
             idx->W = o.b / 64;
             idx->method = o.method;
+            idx->sim = o.sim;
             idx->n = d.n;
             idx->max_size = max_size;
             const int64_t n = d.n;
@@ -490,12 +494,13 @@ extern "C" void bmj_index_destroy(bmj_index *idx) {
 
 extern "C" int64_t bmj_index_size(const bmj_index *idx) { return idx ? idx->n : -1; }
 
-static int check_queries(const bmj_collection *qc, const uint32_t *p, const uint32_t *q) {
+static int check_queries(const bmj_index *idx, const bmj_collection *qc, const uint32_t *p,
+                         const uint32_t *q) {
     if (!qc || qc->on_device || qc->n_sets < 0 || !qc->offsets || (qc->n_sets > 0 && (!qc->tokens || !p || !q)))
         return BMJ_ERR_INVALID_ARG;
     if (qc->offsets[0] != 0) return BMJ_ERR_UNSORTED;
     for (int64_t x = 0; x < qc->n_sets; x++) {
-        if (p[x] == 0 || q[x] == 0 || p[x] > q[x]) return BMJ_ERR_INVALID_ARG;
+        if (!sim_valid(idx->sim, p[x], q[x])) return BMJ_ERR_INVALID_ARG;
         const int64_t a = qc->offsets[x], b = qc->offsets[x + 1];
         if (b < a) return BMJ_ERR_UNSORTED;
         if (b == a) return BMJ_ERR_EMPTY_SET;
@@ -691,7 +696,7 @@ extern "C" int bmj_index_query(bmj_index *idx, const bmj_collection *probes, con
                                const uint32_t *q, bmj_id_lists *out, bmj_serve_stats *stats) {
     if (!idx || !out) return BMJ_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
-    int st = check_queries(probes, p, q);
+    int st = check_queries(idx, probes, p, q);
     if (st) return st;
     bmj_serve_options so;
     bmj_default_serve_options(&so);
@@ -714,7 +719,7 @@ extern "C" int bmj_serve(bmj_index *idx, const bmj_collection *queries, const do
                          bmj_id_lists *out, double *latency_ms, bmj_serve_stats *stats) {
     if (!idx || !arrival_s) return BMJ_ERR_INVALID_ARG;
     if (out) memset(out, 0, sizeof(*out));
-    int st = check_queries(queries, p, q);
+    int st = check_queries(idx, queries, p, q);
     if (st) return st;
     for (int64_t x = 1; x < queries->n_sets; x++)
         if (arrival_s[x] < arrival_s[x - 1]) return BMJ_ERR_INVALID_ARG;

@@ -8,6 +8,25 @@
 //   k_unpack         canonical output pairs
 #include "kernels.cuh"
 
+namespace bmj {
+namespace {
+// need / lim of a pair of sizes: the tables indexed by |x|+|y|, or computed for
+// Cosine (whose smallest passing overlap depends on |x|*|y|).
+struct PairTest {
+    const int32_t *need, *lim;
+    uint32_t p, q;
+};
+template <bool kCos>
+__device__ __forceinline__ int pair_need(const PairTest &t, uint32_t x, uint32_t y) {
+    return kCos ? (int)cosine_need(t.p, t.q, x, y) : t.need[x + y];
+}
+template <bool kCos>
+__device__ __forceinline__ int pair_limit(const PairTest &t, uint32_t x, uint32_t y) {
+    return kCos ? (int)((int64_t)x + y - 2 * cosine_need(t.p, t.q, x, y)) : t.lim[x + y];
+}
+}  // namespace
+}  // namespace bmj
+
 // Survivors per thread of the verification with the 256-bit cascade (2 was
 // fastest on the 1M-set workload at threshold 1/2: 13.3 ms, against 13.9 ms
 // for 1, 16.5 ms for 4 and 17.8 ms for k_verify).
@@ -27,11 +46,12 @@ constexpr unsigned kFull = 0xffffffffu;
 // only pairs that pass it are merged.  The merge of the two sorted token
 // arrays stops as soon as the outcome is decided (the overlap reached need[S],
 // or the remaining tokens cannot reach it).
+template <bool kCos>
 __global__ void __launch_bounds__(256)
     k_verify(const uint2 *__restrict__ queue, int64_t n_surv, const int64_t *__restrict__ soff,
              const int32_t *__restrict__ stok, const uint32_t *__restrict__ ssz,
-             const uint32_t *__restrict__ perm, const int32_t *__restrict__ need,
-             const int32_t *__restrict__ lim, const uint64_t *__restrict__ bm2, int W2,
+             const uint32_t *__restrict__ perm, const PairTest pt,
+             const uint64_t *__restrict__ bm2, int W2,
              uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount,
              unsigned long long *__restrict__ ccount, int nbits) {
     const int lane = threadIdx.x & 31;
@@ -51,10 +71,10 @@ __global__ void __launch_bounds__(256)
                 const uint64_t *c = bm2 + (int64_t)pr.y * W2;
                 int h = 0;
                 for (int w = 0; w < W2; w++) h += __popcll(a[w] ^ c[w]);
-                passed = h <= lim[si + sj];
+                passed = h <= pair_limit<kCos>(pt, si, sj);
             }
             if (passed) {
-                const int nd = need[si + sj];
+                const int nd = pair_need<kCos>(pt, si, sj);
                 const int32_t *x = stok + soff[pr.x];
                 const int32_t *y = stok + soff[pr.y];
                 int a = 0, b = 0, o = 0;
@@ -99,12 +119,12 @@ __global__ void __launch_bounds__(256)
 // 16-byte loads, with SPT survivors per thread whose loads are all issued
 // before any of them is used, so that a thread keeps several independent L2
 // requests in flight (the kernel is bound by L2 latency, not bandwidth).
-template <int SPT>
+template <int SPT, bool kCos>
 __global__ void __launch_bounds__(256)
     k_verify_c256(const uint2 *__restrict__ queue, int64_t n_surv, const int64_t *__restrict__ soff,
                   const int32_t *__restrict__ stok, const uint32_t *__restrict__ ssz,
-                  const uint32_t *__restrict__ perm, const int32_t *__restrict__ need,
-                  const int32_t *__restrict__ lim, const uint4 *__restrict__ bm2,
+                  const uint32_t *__restrict__ perm, const PairTest pt,
+                  const uint4 *__restrict__ bm2,
                   uint64_t *__restrict__ keys, unsigned long long *__restrict__ rcount,
                   unsigned long long *__restrict__ ccount, int nbits) {
     const int lane = threadIdx.x & 31;
@@ -136,11 +156,11 @@ __global__ void __launch_bounds__(256)
                           __popc(x0[u].z ^ y0[u].z) + __popc(x0[u].w ^ y0[u].w) +
                           __popc(x1[u].x ^ y1[u].x) + __popc(x1[u].y ^ y1[u].y) +
                           __popc(x1[u].z ^ y1[u].z) + __popc(x1[u].w ^ y1[u].w);
-            const bool passed = idx < n_surv && h <= lim[si[u] + sj[u]];
+            const bool passed = idx < n_surv && h <= pair_limit<kCos>(pt, si[u], sj[u]);
             bool similar = false;
             uint64_t key = 0;
             if (passed) {
-                const int nd = need[si[u] + sj[u]];
+                const int nd = pair_need<kCos>(pt, si[u], sj[u]);
                 const int32_t *x = stok + soff[pr[u].x];
                 const int32_t *y = stok + soff[pr[u].y];
                 int a = 0, b = 0, o = 0;
@@ -200,27 +220,43 @@ unsigned grid_for(int64_t n, int threads, int64_t cap) {
 
 }  // namespace
 
-int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
-                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need,
-                  const int32_t *lim, const uint64_t *bm2, int W2, uint64_t *keys,
-                  unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
-                  cudaStream_t s) {
+template <bool kCos>
+int launch_verify_t(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
+                    const uint32_t *ssz, const uint32_t *perm, const int32_t *need,
+                    const int32_t *lim, const uint64_t *bm2, int W2, uint64_t *keys,
+                    unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
+                    cudaStream_t s, uint32_t p, uint32_t q) {
     if (n_surv <= 0) return BMJ_OK;
+    const PairTest pt{need, lim, p, q};
 #if BMJ_VERIFY_SPT > 0
     if (bm2 && W2 == 4) {
         constexpr int kSpt = BMJ_VERIFY_SPT;
         int per_sm = 0;
-        BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_verify_c256<kSpt>, 256, 0));
+        BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_verify_c256<kSpt, kCos>,
+                                                                256, 0));
         if (per_sm < 1) per_sm = 1;
-        BMJ_LAUNCH(k_verify_c256<kSpt>, grid_for(n_surv, 256 * kSpt, (int64_t)num_sms * per_sm),
-                   256, 0, s, queue, n_surv, soff, stok, ssz, perm, need, lim,
-                   reinterpret_cast<const uint4 *>(bm2), keys, rcount, ccount, nbits);
+        BMJ_LAUNCH((k_verify_c256<kSpt, kCos>),
+                   grid_for(n_surv, 256 * kSpt, (int64_t)num_sms * per_sm), 256, 0, s, queue,
+                   n_surv, soff, stok, ssz, perm, pt, reinterpret_cast<const uint4 *>(bm2), keys,
+                   rcount, ccount, nbits);
         return BMJ_OK;
     }
 #endif
-    BMJ_LAUNCH(k_verify, grid_for(n_surv, 256, (int64_t)num_sms * 8), 256, 0, s, queue, n_surv,
-               soff, stok, ssz, perm, need, lim, bm2, W2, keys, rcount, ccount, nbits);
+    BMJ_LAUNCH((k_verify<kCos>), grid_for(n_surv, 256, (int64_t)num_sms * 8), 256, 0, s, queue,
+               n_surv, soff, stok, ssz, perm, pt, bm2, W2, keys, rcount, ccount, nbits);
     return BMJ_OK;
+}
+
+int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const int32_t *stok,
+                  const uint32_t *ssz, const uint32_t *perm, const int32_t *need,
+                  const int32_t *lim, const uint64_t *bm2, int W2, uint64_t *keys,
+                  unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
+                  cudaStream_t s, int sim, uint32_t p, uint32_t q) {
+    return sim == BMJ_COSINE
+               ? launch_verify_t<true>(queue, n_surv, soff, stok, ssz, perm, need, lim, bm2, W2,
+                                       keys, rcount, ccount, nbits, num_sms, s, p, q)
+               : launch_verify_t<false>(queue, n_surv, soff, stok, ssz, perm, need, lim, bm2, W2,
+                                        keys, rcount, ccount, nbits, num_sms, s, p, q);
 }
 
 int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,

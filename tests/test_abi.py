@@ -68,6 +68,25 @@ def test_invalid_arguments_rejected_on_host(p, q, kw):
     assert _join_status(off, tok, p, q, **kw) == _bmj.BMJ_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("sim,p,q,ok", [
+    (_bmj.BMJ_COSINE, 3, 4, True), (_bmj.BMJ_COSINE, 1, 70000, False), (_bmj.BMJ_COSINE, 5, 4, False),
+    (_bmj.BMJ_DICE, 9, 10, True), (_bmj.BMJ_DICE, 11, 10, False), (_bmj.BMJ_OVERLAP, 7, 2, True),
+    (_bmj.BMJ_OVERLAP, 0, 1, False), (4, 1, 2, False), (-1, 1, 2, False),
+])
+def test_similarity_function_thresholds_checked_on_host(sim, p, q, ok):
+    off = np.array([0, 2, 4], np.int64)
+    tok = np.array([1, 3, 1, 3], np.int32)
+    coll, keep = _bmj.make_collection(off, tok)
+    o = _bmj.bmj_default_options()
+    o.validate = 0
+    st = _bmj.lib().bmj_self_join(C.byref(coll), sim, p, q, C.byref(o), C.byref(_bmj.bmj_pairs()),
+                                  None)
+    if ok:
+        assert st != _bmj.BMJ_ERR_INVALID_ARG   # without a GPU the call fails later, not here
+    else:
+        assert st == _bmj.BMJ_ERR_INVALID_ARG
+
+
 def test_null_pointers_rejected():
     L = _bmj.lib()
     pairs = _bmj.bmj_pairs()

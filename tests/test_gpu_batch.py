@@ -43,13 +43,13 @@ def concat(jobs):
             np.array([j[2] for j in jobs], np.uint32), np.array([j[3] for j in jobs], np.uint32))
 
 
-def check(jobs, pairs, jst, method=_bmj.BMJ_XOR):
+def check(jobs, pairs, jst, method=_bmj.BMJ_XOR, sim=_bmj.BMJ_JACCARD):
     for k, (off, tok, p, q) in enumerate(jobs):
-        ra, rb = O.self_join(off, tok, p, q)
+        ra, rb = O.self_join(off, tok, p, q, sim=sim)
         a, b = pairs[k]
         assert np.array_equal(a, ra) and np.array_equal(b, rb), k
         m = OM.get(jst[k]["method"], O.XOR)
-        w, s, r = O.filter_counts(off, tok, p, q, jst[k]["b"], m)
+        w, s, r = O.filter_counts(off, tok, p, q, jst[k]["b"], m, sim=sim)
         assert (jst[k]["window_pairs"], jst[k]["survivors"], jst[k]["results"]) == (w, s, r), k
 
 
@@ -179,3 +179,16 @@ def test_out_of_memory_batch_retries_in_parts(monkeypatch, k, on_device):
     check(jobs, pairs, jst)
     assert bst["n_jobs"] == 12 and bst["results"] == sum(len(x[0]) for x in pairs)
     assert bst["filter_passes"] >= 2   # the two halves ran (one pass or more each)
+
+
+@pytest.mark.parametrize("sim,b", [(_bmj.BMJ_COSINE, 0), (_bmj.BMJ_DICE, 0), (_bmj.BMJ_COSINE, 128),
+                                   (_bmj.BMJ_OVERLAP, 64)])
+def test_batch_other_similarity_functions(sim, b):
+    jobs = make_batch(16, seed=50 + sim)
+    if sim == _bmj.BMJ_OVERLAP:   # token-count thresholds
+        jobs = [(off, tok, [3, 5, 8][k % 3], 1) for k, (off, tok, _, _) in enumerate(jobs)]
+    off, tok, js, p, q = concat(jobs)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    pairs, jst, bst = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=b, sim=sim)
+    check(jobs, pairs, jst, sim=sim)
+    assert bst["results"] == sum(len(x[0]) for x in pairs) > 0

@@ -36,13 +36,15 @@ def gpu_join(off, tok, p, q, on_device=True, **kw):
     return _bmj.bmj_self_join(off, tok, p, q, **kw)
 
 
-def check_join(off, tok, p, q, b=64, method=_bmj.BMJ_XOR, counts=True, **kw):
-    a, bb, st = gpu_join(off, tok, p, q, b=b, method=method, **kw)
-    ra, rb = O.self_join(off, tok, p, q)
+def check_join(off, tok, p, q, b=64, method=_bmj.BMJ_XOR, counts=True, sim=_bmj.BMJ_JACCARD, **kw):
+    a, bb, st = gpu_join(off, tok, p, q, b=b, method=method, sim=sim, **kw)
+    ra, rb = O.self_join(off, tok, p, q, sim=sim)
     assert len(a) == len(ra), (len(a), len(ra))
     assert np.array_equal(a, ra) and np.array_equal(bb, rb)
     if counts:
-        w, s, r = O.filter_counts(off, tok, p, q, b, ORACLE_METHOD[method])
+        m = O.combined_method(p, q, sim) if method == _bmj.BMJ_COMBINED else ORACLE_METHOD[method]
+        assert st["method"] == m or method != _bmj.BMJ_COMBINED
+        w, s, r = O.filter_counts(off, tok, p, q, b, m, sim=sim)
         assert (st["window_pairs"], st["survivors"], st["results"]) == (w, s, r)
     return st
 
@@ -84,6 +86,28 @@ def test_build_bitmaps_bit_exact(b, method):
     assert np.array_equal(got.cpu().numpy().view(np.uint64), want)
     got_h = _bmj.bmj_build_bitmaps(off, tok, b=b, method=method)
     assert np.array_equal(got_h, want)
+
+
+# ------------------------------------- other similarity functions (Table 1)
+@pytest.mark.parametrize("b", [64, 128, 256, 192])
+@pytest.mark.parametrize("sim,p,q", [(_bmj.BMJ_COSINE, 1, 2), (_bmj.BMJ_COSINE, 4, 5),
+                                     (_bmj.BMJ_DICE, 3, 5), (_bmj.BMJ_DICE, 9, 10),
+                                     (_bmj.BMJ_OVERLAP, 3, 1), (_bmj.BMJ_OVERLAP, 9, 2)])
+def test_other_similarity_functions(sim, p, q, b):
+    # 3,001 sets (a ragged last tile), sizes 1..80; the pair list and the window,
+    # survivor and result counts equal the oracle's for the function's window (Table 2)
+    # and limit (Cosine: per pair of sizes, the others per size sum).
+    off, tok = I.random_collection(3001, 2500, 1, 80, seed=b + 7 * sim + p, zipf_s=0.9,
+                                   planted_frac=0.15)
+    st = check_join(off, tok, p, q, b=b, sim=sim)
+    assert st["results"] > 0
+
+
+@pytest.mark.parametrize("sim", [_bmj.BMJ_COSINE, _bmj.BMJ_DICE])
+def test_other_functions_combined_method_and_host_input(sim):
+    off, tok = I.random_collection(2500, 1200, 1, 50, seed=90 + sim, planted_frac=0.1)
+    for p, q in ((1, 2), (3, 5), (9, 10)):
+        check_join(off, tok, p, q, b=64, sim=sim, method=_bmj.BMJ_COMBINED, on_device=False)
 
 
 # ------------------------------------------------------ host/device paths

@@ -117,3 +117,28 @@ def test_full_served_workload_sampled():
         want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
         assert np.array_equal(res[x], want), x
     idx.close()
+
+
+@pytest.mark.parametrize("sim", [_bmj.BMJ_COSINE, _bmj.BMJ_DICE, _bmj.BMJ_OVERLAP])
+def test_index_other_similarity_functions(sim):
+    # The index's function (set at creation) decides the two-sided window (Table 2),
+    # the Eq. 2 limit per pair and the exact test; every probe equals the oracle's
+    # search, alone and in the continuous mix.
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=20 + sim, nq=200)
+    if sim == _bmj.BMJ_OVERLAP:          # token-count thresholds
+        p = (3 + np.arange(len(p)) % 6).astype(np.uint32)
+        q = np.ones(len(p), np.uint32)
+    idx = _bmj.Index(torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda(), b=64, sim=sim)
+    res, st = idx.query(qoff, qtok, p, q)
+    mixed, lat, _ = idx.serve(qoff, qtok, arr, p, q, n_slots=3, max_batch_queries=32)
+    nonempty = 0
+    for x in range(len(p)):
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]), sim=sim)
+        assert np.array_equal(res[x], want) and np.array_equal(mixed[x], want), x
+        nonempty += len(want) > 0
+    assert nonempty > 20
+    if sim != _bmj.BMJ_OVERLAP:
+        with pytest.raises(_bmj.BmjError) as e:   # p > q is no valid threshold for it
+            idx.query(qoff[:2], qtok[:int(qoff[1])], np.array([5], np.uint32), np.array([4], np.uint32))
+        assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
+    idx.close()

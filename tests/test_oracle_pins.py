@@ -577,3 +577,16 @@ def test_filter_counts_other_functions(sim, p, q):
         assert s == r   # universe 60 <= b: the bitmaps are exact
     w, s, r = O.filter_counts(off, tok, p, q, 128, O.XOR, sim=sim)
     assert (w, r) == (win, n_res) and s == r
+
+
+def test_combined_method_of_other_functions():
+    # switch points 0.56 / 0.73 on the normalised overlap at the threshold: p/q itself
+    # for Dice and Cosine (tau*n / n for two sets of size n); Xor for Overlap
+    for sim in (O.DICE, O.COSINE):
+        assert O.combined_method(1, 2, sim) == O.NEXT        # 0.50
+        assert O.combined_method(14, 25, sim) == O.NEXT      # 0.56
+        assert O.combined_method(3, 5, sim) == O.SET         # 0.60
+        assert O.combined_method(73, 100, sim) == O.XOR      # 0.73
+        assert O.combined_method(9, 10, sim) == O.XOR
+    assert O.combined_method(7, 2, O.OVERLAP) == O.XOR
+    assert O.combined_method(1, 2, O.JACCARD) == O.SET       # 2/3 normalised
