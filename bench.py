@@ -62,6 +62,8 @@ def parse_args():
                     help="target wall time of the CPU baseline's sample (rows are scaled to it)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-joins comparison (512 jobs)")
+    ap.add_argument("--no-sims", action="store_true",
+                    help="skip the joins with Cosine, Dice and Overlap similarity")
     ap.add_argument("--no-combined", action="store_true",
                     help="skip the step with Alg. 4's generation function per threshold")
     ap.add_argument("--no-10m", action="store_true",
@@ -368,6 +370,30 @@ def run_ours(args):
                     "value": round(window_per_step / (c_ms / 1e3)), "unit": UNIT,
                     "survivors": surv, "steps": 1}
 
+    # ---- the other similarity functions of Table 1 on the same collection ----
+    sims = None
+    if not args.no_sims:
+        sims = {}
+        cases = (("cosine", _bmj.BMJ_COSINE, THRESHOLDS), ("dice", _bmj.BMJ_DICE, THRESHOLDS),
+                 ("overlap", _bmj.BMJ_OVERLAP, ((10, 1), (20, 1))))
+        for name, sim, thr_list in cases:
+            rows = []
+            for (p, q) in thr_list:
+                st0 = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, sim=sim, output_on_device=True,
+                                         stream=stream.cuda_stream)
+                st0[0].release()
+                r, _, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, sim=sim,
+                                              output_on_device=True, stream=stream.cuda_stream)
+                r.release()
+                rows.append({"threshold": f"{p}/{q}", "window_pairs": st["window_pairs"],
+                             "survivors": st["survivors"], "results": st["results"],
+                             "filter_passes": st["filter_passes"],
+                             "join_ms": round(st["ms_total"], 3),
+                             "pairs_per_s": round(st["window_pairs"] / (st["ms_total"] / 1e3)),
+                             "filter_pairs_per_s": round(st["window_pairs"] /
+                                                         max(st["ms_filter"] / 1e3, 1e-9))})
+            sims[name] = rows
+
     # ---- optional b sweep (outside the headline) ----
     sweep = None
     if args.sweep:
@@ -459,6 +485,10 @@ def run_ours(args):
             out["sweep_b"] = sweep
         if combined:
             out["combined_method"] = combined
+        if sims:
+            out["similarity_functions"] = {
+                "workload": "the 1,000,000-set collection at b = " + str(b) + ", one join per "
+                            "threshold (Overlap thresholds count tokens)", **sims}
         if batched:
             out["batched"] = batched
         if ten_m:

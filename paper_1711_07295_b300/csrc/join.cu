@@ -206,6 +206,11 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
         int64_t qcap = user_cap ? o.queue_cap : auto_queue_cap(stl.window_pairs);
         uint2 *queue = nullptr;
         st = A.alloc(&queue, (size_t)qcap);
+        if (st == BMJ_ERR_OOM && user_cap) {  // a requested capacity that does not fit: the
+            cudaGetLastError();                // automatic one, drained in item ranges
+            qcap = std::min(qcap, auto_queue_cap(stl.window_pairs));
+            st = A.alloc(&queue, (size_t)qcap);
+        }
         if (st) return st;
         FilterArgs fa;
         fa.bm = bm;
