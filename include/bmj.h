@@ -362,7 +362,7 @@ int bmj_measure_popc_rate(void *stream, double *popc_per_s);
  *              the set at sorted position i (e.g. bmj_build_bitmaps run on
  *              the size-sorted collection)
  *   sizes      device, n_sets uint32 set sizes, each >= 1, nondecreasing
- *   b, p, q    bitmap bits (multiple of 64 in [64, 4096]) and threshold p/q
+ *   b, p, q    bitmap bits (multiple of 64 in [64, 4096]) and Jaccard threshold p/q
  * Output (caller-owned):
  *   out_pairs  device, 2*out_cap uint32, 8-byte aligned: the surviving pairs
  *              as (i, j) with j < i in sorted positions, in no particular

@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--q", type=int, default=20)
     ap.add_argument("--b", type=int, default=64)
     ap.add_argument("--method", default="xor")
+    ap.add_argument("--sim", default="jaccard", choices=("jaccard", "cosine", "dice", "overlap"))
     ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
 
@@ -36,16 +37,19 @@ def main():
     off, tok = inputs.gen_collection(spec)
     d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
     m = _bmj.METHODS[args.method]
-    res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m,
+    sim = {"jaccard": _bmj.BMJ_JACCARD, "cosine": _bmj.BMJ_COSINE, "dice": _bmj.BMJ_DICE,
+           "overlap": _bmj.BMJ_OVERLAP}[args.sim]
+    res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m, sim=sim,
                                     output_on_device=True)
     res.release()
     cap = max(1, st["survivors"])
     for _ in range(args.repeat):
-        res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m,
+        res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m, sim=sim,
                                         output_on_device=True, queue_cap=cap)
         res.release()
     torch.cuda.synchronize()
-    print(json.dumps({"sets": args.sets, "threshold": f"{args.p}/{args.q}", "b": args.b, **st}))
+    print(json.dumps({"sets": args.sets, "threshold": f"{args.p}/{args.q}", "b": args.b,
+                      "sim": args.sim, **st}))
 
 
 if __name__ == "__main__":
