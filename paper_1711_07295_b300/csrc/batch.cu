@@ -208,12 +208,13 @@ struct BatchFilterArgs {
 // tiles [t0, t1) (the jobs of that width are contiguous in the tile list),
 // items pulled from a per-class counter.  Columns are staged by TMA.
 template <int W, int R, int CS, bool kCos>
-__global__ void __launch_bounds__(128) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
+__global__ void __launch_bounds__(128, kCos ? 6 : 7) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
                                                          int64_t t1, unsigned long long *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     StageState stg;
-    init_stage(stg, smem + (threadIdx.x >> 5) * ColStage<W, CS>::kWarpBytes);  // default bounded waits
+    init_stage(stg, smem + (threadIdx.x >> 5) * ColStage<W, CS>::kWarpBytes,
+               ColStage<W, CS>::kStageOff);  // default bounded waits
     const int64_t ibase = a.tile_item_off[t0], iend = a.tile_item_off[t1];
     for (;;) {
         unsigned long long item = 0;

@@ -63,13 +63,15 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
 // Bitmap Filter with TMA-staged columns (filter_item_tma).  Each warp owns a
 // double buffer of column chunks in dynamic shared memory and its two
 // mbarriers; a wait that gives up sets *err and stops the warp.
+// Eight 4-warp blocks per SM (64 registers) for the production variants; the
+// Cosine variant's per-pair limit needs more registers.
 template <int W, int R, int CS, bool kFault, bool kCos>
-__global__ void __launch_bounds__(128) k_filter_tma(const FilterArgs a, int *err) {
+__global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterArgs a, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     using L = ColStage<W, CS>;
     const int lane = threadIdx.x & 31;
     StageState st;
-    init_stage(st, smem + (threadIdx.x >> 5) * L::kWarpBytes);
+    init_stage(st, smem + (threadIdx.x >> 5) * L::kWarpBytes, L::kStageOff);
     if (kFault) {  // fault injection: the first warp skips its first copy; short waits
         st.wait_limit = a.wait_limit;
         st.skip_copy = (blockIdx.x == 0 && threadIdx.x < 32) ? 1 : 0;

@@ -345,13 +345,17 @@ template <int W, int CS>
 struct ColStage {
     static constexpr int kCols = CS + 4;  // room for the 16-byte alignment of a chunk start
     static constexpr int kBufBytes = kCols * (8 * W + 4);
-    static constexpr int kWarpBytes = 16 + 2 * kBufBytes;  // two mbarriers, then two buffers
+    static constexpr int kStage = 64;     // survivor masks staged per round (see flush_masks)
+    static constexpr int kStageOff = 16 + 2 * kBufBytes;
+    // two mbarriers, two column buffers, then the survivor-mask staging area
+    static constexpr int kWarpBytes = kStageOff + kStage * 8;
 };
 
 // Per-warp pipeline state, kept across work items.  A warp's shared-memory
 // region holds its two mbarriers first (their place does not depend on the
 // bitmap width) and then its two column buffers.
 struct StageState {
+    uint2 *stage;         // kStage (row offset, mask) entries: survivor masks of one group
     unsigned char *buf;   // two buffers of kBufBytes (of the width in use)
     uint64_t *bar;        // two mbarriers
     uint32_t phase;       // bit k: parity to wait for on buffer k
@@ -371,7 +375,8 @@ __device__ __forceinline__ void drain_stage(StageState &st) {
     }
 }
 
-__device__ __forceinline__ void init_stage(StageState &st, unsigned char *region) {
+__device__ __forceinline__ void init_stage(StageState &st, unsigned char *region, int stage_off) {
+    st.stage = reinterpret_cast<uint2 *>(region + stage_off);
     st.bar = reinterpret_cast<uint64_t *>(region);
     st.buf = region + 16;
     st.phase = 0;
@@ -405,6 +410,67 @@ __device__ __forceinline__ void stage_issue(StageState &st, int slot,
     }
     tma_load_1d(b, bm + c_al * W, bm_bytes, &st.bar[slot]);
     tma_load_1d(b + L::kCols * 8 * W, ssz + c_al, sz_bytes, &st.bar[slot]);
+}
+
+// Writes the survivors of one 32-column group to the queue.  A lane's masks are
+// sparse (at threshold 1/2 about one survivor per lane and group), so looping
+// over each lane's own bits leaves most lanes idle for most iterations.
+// Instead the warp stages its nonzero masks (row offset, mask) in shared memory,
+// kStage per round, and each lane expands two of them: the loop runs for the
+// largest number of bits in two masks, not the largest over eight.  Bit b of a
+// mask is column col_hi - b.  One atomicAdd per round reserves the queue slots.
+template <int R, int kStage>
+__device__ __forceinline__ void flush_masks(const uint32_t (&mask)[R], const int32_t (&rd)[R], int nz,
+                                            int n_masks, int64_t i0, int64_t col_hi,
+                                            const SurvivorSink &sink, uint2 *stage) {
+    static_assert(kStage == 64, "two staged masks per lane");
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int first = warp_excl_scan_i(nz);  // index of this lane's first nonzero mask
+    for (int base = 0; base < n_masks; base += kStage) {  // warp-uniform; one round usually
+        int e = first;
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            if (mask[k]) {
+                if (e >= base && e < base + kStage)
+                    stage[e - base] = make_uint2((uint32_t)rd[k], mask[k]);
+                e++;
+            }
+        }
+        __syncwarp();
+        const int n_e = min(kStage, n_masks - base);
+        const uint2 ea = lane < n_e ? stage[lane] : make_uint2(0u, 0u);
+        const uint2 eb = lane + 32 < n_e ? stage[lane + 32] : make_uint2(0u, 0u);
+        __syncwarp();  // the staging area may be rewritten in the next round
+        const int c = __popc(ea.y) + __popc(eb.y);
+        const int total = __reduce_add_sync(kFull, c);
+        const int excl = warp_excl_scan_i(c);
+        unsigned long long pos0 = 0;
+        if (lane == 0) {
+            pos0 = atomicAdd(sink.count, (unsigned long long)total);
+            if (sink.job_count) atomicAdd(sink.job_count, (unsigned long long)total);
+        }
+        pos0 = __shfl_sync(kFull, pos0, 0);
+        unsigned long long pos = pos0 + excl;
+        uint32_t m = ea.y;
+        uint32_t row = (uint32_t)(i0 + ea.x);
+        while (m) {
+            const int bpos = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < (unsigned long long)sink.cap)
+                sink.queue[pos] = make_uint2(row, (uint32_t)(col_hi - bpos));
+            pos++;
+        }
+        m = eb.y;
+        row = (uint32_t)(i0 + eb.x);
+        while (m) {
+            const int bpos = __ffs(m) - 1;
+            m &= m - 1;
+            if (pos < (unsigned long long)sink.cap)
+                sink.queue[pos] = make_uint2(row, (uint32_t)(col_hi - bpos));
+            pos++;
+        }
+    }
 }
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
@@ -509,36 +575,15 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
             }
             // bit (gj-1-cc) of mask[k] is column g+cc; keep only columns j < i
             const int64_t dg = i0 - g;
-            int cnt = 0;
+            int nz = 0;
 #pragma unroll
             for (int k = 0; k < R; k++) {
                 const int64_t d = dg + rd[k];  // i - g
                 if (d < gj) mask[k] = d <= 0 ? 0u : (mask[k] & (~0u << (gj - (int)d)));
-                cnt += __popc(mask[k]);
+                nz += mask[k] != 0u;
             }
-            const int total = __reduce_add_sync(kFull, cnt);
-            if (total) {
-                const int excl = warp_excl_scan_i(cnt);
-                unsigned long long pos0 = 0;
-                if (lane == 0) {
-                    pos0 = atomicAdd(sink.count, (unsigned long long)total);
-                    if (sink.job_count) atomicAdd(sink.job_count, (unsigned long long)total);
-                }
-                pos0 = __shfl_sync(kFull, pos0, 0);
-                unsigned long long pos = pos0 + excl;
-#pragma unroll
-                for (int k = 0; k < R; k++) {
-                    uint32_t m = mask[k];
-                    while (m) {
-                        const int bpos = __ffs(m) - 1;
-                        m &= m - 1;
-                        if (pos < (unsigned long long)sink.cap)
-                            sink.queue[pos] = make_uint2((uint32_t)(i0 + rd[k]),
-                                                         (uint32_t)(g + (gj - 1 - bpos)));
-                        pos++;
-                    }
-                }
-            }
+            const int n_masks = __reduce_add_sync(kFull, nz);
+            if (n_masks) flush_masks<R, L::kStage>(mask, rd, nz, n_masks, i0, g + gj - 1, sink, st.stage);
         }
         __syncwarp();  // every lane is done with this slot before it is refilled
     }
