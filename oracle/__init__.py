@@ -74,6 +74,9 @@ def lib():
         L.oracle_filter_counts.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, C.c_int, C.c_int,
                                            i64p]
         L.oracle_filter_counts.restype = None
+        L.oracle_prefix_counts.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, C.c_int, C.c_int,
+                                           i64p]
+        L.oracle_prefix_counts.restype = None
         L.oracle_combined_method.argtypes = [i64, i64]
         L.oracle_combined_method.restype = C.c_int
         L.oracle_combined_method_sim.argtypes = [C.c_int, i64, i64]
@@ -212,6 +215,17 @@ def upper_bound(nr: int, ns: int, h: int) -> int:
     return int(lib().oracle_upper_bound(nr, ns, h))
 
 
+def prefix_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int = JACCARD):
+    """(candidates, survivors, results) with the prefix filter choosing the candidates."""
+    off, tok = _i64(offsets), _i32(tokens)
+    cnt = np.zeros(3, np.int64)
+    lib().oracle_prefix_counts(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim, p, q,
+                               b, method, _p(cnt, C.c_int64))
+    if cnt[0] < 0:
+        raise MemoryError("oracle allocation failed")
+    return int(cnt[0]), int(cnt[1]), int(cnt[2])
+
+
 def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int = JACCARD):
     """(window pairs, survivors, results) of Alg. 6 + host verification."""
     off, tok = _i64(offsets), _i32(tokens)
@@ -226,4 +240,4 @@ def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int
 __all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "JACCARD", "COSINE", "DICE", "OVERLAP",
            "overlap", "similar", "similar_sim", "in_window", "self_join",
            "join_rows", "join_rows_window", "search", "bitmap", "bitmaps", "hamming", "upper_bound",
-           "filter_counts", "combined_method", "num_threads", "lib"]
+           "filter_counts", "prefix_counts", "combined_method", "num_threads", "lib"]

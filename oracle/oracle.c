@@ -34,6 +34,8 @@
  *   oracle_bitmap         Alg. 3a (Set), 3b (Xor), 3c (Next), literally
  *   oracle_filter_counts  the GPU algorithm (Alg. 6): size order, length
  *                         window, Eq. 2 bound, then verification -- counted
+ *   oracle_prefix_counts  the same with the prefix filter (Section 2.2)
+ *                         choosing the candidates inside the window
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -529,4 +531,125 @@ void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int
     counts[1] = surv;
     counts[2] = res;
     free(ord); free(sz); free(bm);
+}
+
+/*
+ * The prefix filter (Section 2.2) as a candidate generator for the Bitmap
+ * Filter.  Tokens are ordered globally by frequency (rarest first, ties by
+ * token id); the prefix of a set of size x is its x - low(x) + 1 first tokens
+ * in that order, where low(x) is the smallest partner size inside the length
+ * window (oracle_in_window), which is also the smallest overlap any similar
+ * partner can have.  Two similar sets share a prefix token, so the pairs of the
+ * window whose prefixes intersect (the candidates) contain every result.
+ * counts[0] = candidates (pairs j < i in size order inside the window with
+ * intersecting prefixes), counts[1] = candidates passing Eq. 2 with the
+ * b-bit bitmaps of `method`, counts[2] = results among them.
+ */
+static int cmp_i64(const void *x, const void *y)
+{
+    int64_t u = *(const int64_t *)x, v = *(const int64_t *)y;
+    return (u > v) - (u < v);
+}
+
+void oracle_prefix_counts(int64_t n, const int64_t *off, const int32_t *tok, int sim, int64_t p,
+                          int64_t q, int b, int method, int64_t *counts)
+{
+    counts[0] = counts[1] = counts[2] = 0;
+    if (n <= 1) return;
+    if (method == OR_COMBINED) method = oracle_combined_method_sim(sim, p, q);
+    const int64_t ntok = off[n];
+    const int W = b / 64;
+    /* global token order: distinct tokens with their counts, sorted by (count, token) */
+    int64_t *all = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *ukey = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *utok = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *rank_of = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    uint64_t *keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int64_t *ord = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *sz = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *poff = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    uint64_t *bm = (uint64_t *)malloc((size_t)n * (size_t)W * sizeof(uint64_t));
+    if (!all || !ukey || !utok || !rank_of || !keys || !ord || !sz || !poff || !bm) {
+        counts[0] = counts[1] = counts[2] = -1;
+        free(all); free(ukey); free(utok); free(rank_of); free(keys); free(ord); free(sz);
+        free(poff); free(bm);
+        return;
+    }
+    for (int64_t k = 0; k < ntok; k++) all[k] = tok[k];
+    qsort(all, (size_t)ntok, sizeof(int64_t), cmp_i64);
+    int64_t nu = 0;
+    for (int64_t k = 0; k < ntok;) {
+        int64_t e = k;
+        while (e < ntok && all[e] == all[k]) e++;
+        utok[nu] = all[k];                       /* ascending token ids */
+        ukey[nu] = ((e - k) << 32) | nu;         /* (count, index into utok) */
+        nu++;
+        k = e;
+    }
+    qsort(ukey, (size_t)nu, sizeof(int64_t), cmp_i64);  /* by count, then token id */
+    for (int64_t r = 0; r < nu; r++) rank_of[ukey[r] & 0xffffffff] = r;  /* rank per utok index */
+    /* size order */
+    for (int64_t x = 0; x < n; x++)
+        keys[x] = ((uint64_t)(off[x + 1] - off[x]) << 32) | (uint64_t)x;
+    qsort(keys, (size_t)n, sizeof(uint64_t), cmp_pair64);
+    /* prefixes: the ranks of each set's tokens, sorted, first x - low(x) + 1 of them */
+    poff[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        ord[i] = (int64_t)(keys[i] & 0xffffffffu);
+        sz[i] = (int64_t)(keys[i] >> 32);
+        int64_t low = 1;
+        while (low <= sz[i] && !oracle_in_window(sim, low, sz[i], p, q)) low++;
+        int64_t len = sz[i] - low + 1;
+        if (len < 0) len = 0;
+        poff[i + 1] = poff[i] + len;
+        oracle_bitmap(tok + off[ord[i]], sz[i], b, method, bm + i * W);
+    }
+    int64_t *pre = (int64_t *)malloc((size_t)(poff[n] > 0 ? poff[n] : 1) * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    if (!pre || !tmp) {
+        counts[0] = counts[1] = counts[2] = -1;
+    } else {
+        for (int64_t i = 0; i < n; i++) {
+            const int32_t *x = tok + off[ord[i]];
+            for (int64_t k = 0; k < sz[i]; k++) {
+                /* rank of token x[k]: binary search in the ascending distinct tokens */
+                int64_t lo = 0, hi = nu - 1;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) / 2;
+                    if (utok[mid] < x[k]) lo = mid + 1; else hi = mid;
+                }
+                tmp[k] = rank_of[lo];
+            }
+            qsort(tmp, (size_t)sz[i], sizeof(int64_t), cmp_i64);
+            for (int64_t k = 0; k < poff[i + 1] - poff[i]; k++) pre[poff[i] + k] = tmp[k];
+        }
+        int64_t cand = 0, surv = 0, res = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : cand, surv, res)
+        for (int64_t i = 0; i < n; i++) {
+            for (int64_t j = 0; j < i; j++) {
+                if (!oracle_in_window(sim, sz[j], sz[i], p, q)) continue;
+                /* do the two sorted prefixes share a rank? */
+                int64_t a = poff[i], ae = poff[i + 1], c = poff[j], ce = poff[j + 1];
+                int share = 0;
+                while (a < ae && c < ce) {
+                    if (pre[a] == pre[c]) { share = 1; break; }
+                    if (pre[a] < pre[c]) a++; else c++;
+                }
+                if (!share) continue;
+                cand++;
+                int64_t h = oracle_hamming(bm + i * W, bm + j * W, b);
+                if (!oracle_similar_sim(sim, oracle_upper_bound(sz[i], sz[j], h), sz[i], sz[j], p, q))
+                    continue;
+                surv++;
+                int64_t o = oracle_overlap(tok + off[ord[i]], sz[i], tok + off[ord[j]], sz[j]);
+                if (oracle_similar_sim(sim, o, sz[i], sz[j], p, q)) res++;
+            }
+        }
+        counts[0] = cand;
+        counts[1] = surv;
+        counts[2] = res;
+    }
+    free(pre); free(tmp);
+    free(all); free(ukey); free(utok); free(rank_of); free(keys); free(ord); free(sz); free(poff);
+    free(bm);
 }

@@ -590,3 +590,42 @@ def test_combined_method_of_other_functions():
         assert O.combined_method(9, 10, sim) == O.XOR
     assert O.combined_method(7, 2, O.OVERLAP) == O.XOR
     assert O.combined_method(1, 2, O.JACCARD) == O.SET       # 2/3 normalised
+
+
+# --------------------------------------- Section 2.2: the prefix filter as candidates
+def _prefix_candidates_brute(sets, sim, p, q):
+    """Candidates by the definition: tokens ranked by (frequency, id), a set's prefix is
+    its x - low(x) + 1 lowest-ranked tokens with low(x) the smallest overlap any similar
+    partner can have (found here from Table 1 by search); pairs inside Table 2's window
+    whose prefixes intersect."""
+    from collections import Counter
+    freq = Counter(t for s in sets for t in s)
+    rank = {t: r for r, t in enumerate(sorted(freq, key=lambda t: (freq[t], t)))}
+
+    def low(x):   # smallest partner size y <= x that can still reach the threshold
+        for y in range(1, x + 1):
+            if _passes(sim, y, y, x, p, q):
+                return y
+        return x + 1
+
+    pre = [set(sorted(rank[t] for t in s)[:max(0, len(s) - low(len(s)) + 1)]) for s in sets]
+    cand = 0
+    for a, b in itertools.combinations(range(len(sets)), 2):
+        x, y = sorted((len(sets[a]), len(sets[b])))
+        if not _passes(sim, x, x, y, p, q):
+            continue
+        if pre[a] & pre[b]:
+            cand += 1
+    return cand
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 4, 5), (O.COSINE, 3, 5),
+                                     (O.DICE, 7, 10), (O.OVERLAP, 3, 1)])
+def test_prefix_filter_candidates(sim, p, q):
+    off, tok = I.random_collection(220, 90, 1, 16, seed=80 + p + sim, planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    c, s, r = O.prefix_counts(off, tok, p, q, 64, O.XOR, sim=sim)
+    assert c == _prefix_candidates_brute(sets, sim, p, q)
+    # the prefix filter is exact: every similar pair is a candidate
+    w, s_w, r_w = O.filter_counts(off, tok, p, q, 64, O.XOR, sim=sim)
+    assert r == r_w == len(_brute_pairs_sim(sets, sim, p, q)) and r <= s <= s_w and c <= w
