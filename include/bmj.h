@@ -128,8 +128,17 @@ typedef struct {
                                   (sets ordered by size, ties by id) has its position in */
     int64_t row_end;           /*   [row_begin, row_end); 0, 0 = every pair.  Bands that cover
                                   [0, n) give disjoint pair lists whose union is the full join. */
-    int32_t reserved[2];
+    int32_t candidates;        /* bmj_self_join: BMJ_CAND_WINDOW (default) filters every pair of
+                                  the length window; BMJ_CAND_PREFIX filters only the window
+                                  pairs whose prefixes share a token (prefix filter, Section 2.2)
+                                  -- fewer pairs at high thresholds, same result; it falls back
+                                  to the window when its candidates do not fit in memory, and
+                                  needs row_begin = row_end = 0 */
+    int32_t reserved1;
 } bmj_options;
+
+#define BMJ_CAND_WINDOW 0
+#define BMJ_CAND_PREFIX 1
 
 /* Counters and stage times of one join.  Pair counts are exact and do not
  * depend on the launch configuration. */
@@ -151,6 +160,9 @@ typedef struct {
     float   ms_output;      /* result sort, id mapping and output copy */
     float   ms_total;       /* whole call, device time on the stream */
     float   reserved_f;
+    int64_t candidates;     /* BMJ_CAND_PREFIX: distinct prefix-filter candidates, which the
+                               Bitmap Filter then evaluated (survivors counts those passing it);
+                               0 in window mode; -1 when prefix mode fell back to the window */
 } bmj_stats;
 
 /* Counters and stage times of one bmj_self_join_batch call. */

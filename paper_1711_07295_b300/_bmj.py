@@ -29,6 +29,7 @@ BMJ_ERR_TOO_LARGE = -9
 
 BMJ_XOR, BMJ_SET, BMJ_NEXT, BMJ_COMBINED = 0, 1, 2, 3
 BMJ_JACCARD, BMJ_COSINE, BMJ_DICE, BMJ_OVERLAP = 0, 1, 2, 3   # similarity functions (Table 1)
+BMJ_CAND_WINDOW, BMJ_CAND_PREFIX = 0, 1   # candidate pairs: the whole window, or the prefix filter
 METHODS = {"xor": BMJ_XOR, "set": BMJ_SET, "next": BMJ_NEXT, "combined": BMJ_COMBINED}
 
 
@@ -72,7 +73,8 @@ class bmj_options(C.Structure):
                 ("validate", C.c_int32), ("queue_cap", C.c_int64), ("stream", C.c_void_p),
                 ("rows_per_thread", C.c_int32), ("use_graph", C.c_int32),
                 ("cascade_b", C.c_int32), ("sim", C.c_int32), ("row_begin", C.c_int64),
-                ("row_end", C.c_int64), ("reserved", C.c_int32 * 2)]
+                ("row_end", C.c_int64), ("candidates", C.c_int32),
+                ("reserved1", C.c_int32)]
 
 
 class bmj_stats(C.Structure):
@@ -81,7 +83,7 @@ class bmj_stats(C.Structure):
                 ("b", C.c_int32), ("method", C.c_int32), ("max_set_size", C.c_int32),
                 ("cascade_b", C.c_int32), ("reserved_i", C.c_int32), ("ms_prepare", C.c_float),
                 ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
-                ("ms_total", C.c_float), ("reserved_f", C.c_float)]
+                ("ms_total", C.c_float), ("reserved_f", C.c_float), ("candidates", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -312,7 +314,7 @@ class DevicePairs:
 def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BMJ_XOR,
                   output_on_device: bool = False, queue_cap: int = 0, validate: bool = True,
                   stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0,
-                  row_begin: int = 0, row_end: int = 0):
+                  row_begin: int = 0, row_end: int = 0, candidates: int = 0):
     """Exact Jaccard self-join at threshold p/q.
 
     Returns ``(a, b, stats)``: original ids with a < b sorted by (a, b), as
@@ -329,6 +331,7 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     o.cascade_b = int(cascade_b)
     o.row_begin = int(row_begin)
     o.row_end = int(row_end)
+    o.candidates = int(candidates)
     o.stream = _stream_of(stream, coll.on_device)
     pairs = bmj_pairs()
     st_ = bmj_stats()

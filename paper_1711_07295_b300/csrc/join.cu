@@ -196,184 +196,229 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
         stl.window_pairs = hv[0];
         const int64_t n_items = hv[1];
 
-        // ---- Bitmap Filter + exact verification ----
-        // The filter's queue counts every survivor, also past its capacity.  When
-        // the first pass over all work items overflows, the filter reruns with
-        // exact room if that fits (automatic capacity), else the items run in
-        // consecutive ranges whose survivors fit the queue, each verified before
-        // the next; no pair is ever dropped.
-        const bool user_cap = o.queue_cap > 0;
-        int64_t qcap = user_cap ? o.queue_cap : auto_queue_cap(stl.window_pairs);
-        uint2 *queue = nullptr;
-        st = A.alloc(&queue, (size_t)qcap);
-        if (st == BMJ_ERR_OOM && user_cap) {  // a requested capacity that does not fit: the
-            cudaGetLastError();                // automatic one, drained in item ranges
-            qcap = std::min(qcap, auto_queue_cap(stl.window_pairs));
-            st = A.alloc(&queue, (size_t)qcap);
-        }
-        if (st) return st;
-        FilterArgs fa;
-        fa.bm = bm;
-        fa.ssz = ssz;
-        fa.lim = lim;
-        fa.n = n;
-        fa.row0 = r0;
-        fa.row_end = r1;
-        fa.p = p;
-        fa.sim = sim;
-        fa.q = q;
-        fa.tile_item_off = tile_off;
-        fa.tile_c0 = tile_c0;
-        fa.n_tiles = n_tiles;
-        fa.n_items = n_items;
-        fa.tile_rows = tile_rows;
-        fa.chunk_cols = chunk_cols;
-        fa.queue = queue;
-        fa.qcount = &ctr[1];
-        fa.qcap = qcap;
-        fa.item_counter = &ctr[2];
-        if (fault.timeout) {
-            fa.fault_skip_copy = 1;
-            fa.wait_limit = 1 << 12;
-        }
-        // Filters work items [lo, hi) into the queue; *count = their survivors.
-        auto run_filter = [&](int64_t lo, int64_t hi, int64_t *count) -> int {
-            const unsigned long long init[2] = {0ull, (unsigned long long)lo};
-            BMJ_CHECK(cudaMemcpyAsync(&ctr[1], init, sizeof(init), cudaMemcpyHostToDevice, s));
-            fa.n_items = hi;
-            BMJ_CHECK(cudaEventRecord(ev.e[3], s));
-            int rc = launch_filter_tma(fa, W, err, sms, s);
-            if (rc) return rc;
-            BMJ_CHECK(cudaEventRecord(ev.e[4], s));
-            int herr = 0;
-            BMJ_CHECK(cudaMemcpyAsync(count, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            BMJ_CHECK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-            BMJ_CHECK(cudaStreamSynchronize(s));
-            if (herr) return BMJ_ERR_TIMEOUT;
-            stl.filter_passes++;
-            stl.ms_filter += ev.ms(3, 4);
-            return BMJ_OK;
-        };
-        // Verifies the m survivors at qptr into out_keys (*n_out results).
-        auto run_verify = [&](const uint2 *qptr, int64_t m, uint64_t *out_keys,
-                              int64_t *n_out) -> int {
-            BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
-            BMJ_CHECK(cudaEventRecord(ev.e[5], s));
-            int rc = launch_verify(qptr, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
-                                   &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms, s, sim, p, q);
-            if (rc) return rc;
-            BMJ_CHECK(cudaEventRecord(ev.e[6], s));
-            int64_t hv2[2] = {0, 0};
-            BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            BMJ_CHECK(cudaStreamSynchronize(s));
-            *n_out = hv2[0];
-            stl.verified += bm2 ? hv2[1] : m;
-            stl.ms_verify += ev.ms(5, 6);
-            return BMJ_OK;
-        };
-
-        int64_t n_surv = 0;
-        st = run_filter(0, n_items, &n_surv);
-        if (st) return st;
-        stl.survivors = n_surv;
-        bool banded = false;
-        if (n_surv > qcap) {
-            uint2 *exact = nullptr;
-            if (!user_cap && A.alloc(&exact, (size_t)n_surv) == BMJ_OK) {
-                A.free_one(queue);
-                queue = exact;
-                qcap = n_surv;
-                fa.queue = queue;
-                fa.qcap = qcap;
-                int64_t again = 0;
-                st = run_filter(0, n_items, &again);
-                if (st) return st;
-            } else {
-                banded = true;
-            }
-        }
+        // ---- candidates from the prefix filter (Section 2.2), if asked for ----
         uint64_t *keys = nullptr;
-        int64_t res_cap = 0;
-        // Appends r result keys from src to the growing result buffer.
-        auto append = [&](const uint64_t *src, int64_t r) -> int {
-            if (n_res + r > res_cap) {
-                const int64_t ncap = std::max(2 * res_cap, n_res + r);
-                uint64_t *grown = nullptr;
-                int rc = A.alloc(&grown, (size_t)ncap);
-                if (rc) return rc;
-                if (n_res)
-                    BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
-                                              cudaMemcpyDeviceToDevice, s));
-                if (keys) A.free_one(keys);
-                keys = grown;
-                res_cap = ncap;
-            }
-            if (r)
-                BMJ_CHECK(cudaMemcpyAsync(keys + n_res, src, r * sizeof(uint64_t),
-                                          cudaMemcpyDeviceToDevice, s));
-            n_res += r;
-            return BMJ_OK;
-        };
-        if (!banded && !fault.keys && A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1)) == BMJ_OK) {
-            st = run_verify(queue, n_surv, keys, &n_res);
-            if (st) return st;
-        } else if (!banded) {
-            // every survivor is queued but a key buffer as long as the queue does
-            // not fit: verify the queue in slices (results <= survivors per slice)
-            const int64_t slice = std::max<int64_t>(
-                1, std::min<int64_t>(fault.keys ? (n_surv + 4) / 5 : n_surv, (int64_t)1 << 26));
-            uint64_t *bkeys = nullptr;
-            st = A.alloc(&bkeys, (size_t)slice);
-            if (st) return st;
-            for (int64_t at = 0; at < n_surv; at += slice) {
-                int64_t r = 0;
-                st = run_verify(queue + at, std::min(slice, n_surv - at), bkeys, &r);
-                if (!st) st = append(bkeys, r);
+        bool done = false;
+        if (o.candidates == BMJ_CAND_PREFIX) {
+            Arena PA(s);  // its buffers go once the candidates are verified
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
+            cudaGetLastError();
+            BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+            uint2 *cq = nullptr;
+            int64_t nc = 0, slots = 0;
+            int pst = prefix_candidates(ssz, soff, stok, n, d.ntok, win,
+                                        (int64_t)(free_b / 4 / sizeof(uint2)), PA, s, &cq, &nc,
+                                        &slots);
+            BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+            if (pst == BMJ_OK) {
+                stl.candidates = nc;
+                stl.filter_passes = 1;
+                // Eq. 2 with the join's own bitmaps on every candidate, then the merge
+                st = A.alloc(&keys, (size_t)(nc > 0 ? nc : 1));
                 if (st) return st;
-            }
-            A.free_one(bkeys);
-        } else {
-            // Item ranges sized from the measured survivor density; a range that
-            // still overflows is split again, and a single item that overflows
-            // gets a queue of exactly its size.
-            uint64_t *bkeys = nullptr;
-            st = A.alloc(&bkeys, (size_t)qcap);
-            if (st) return st;
-            int64_t lo = 0;
-            double density = (double)n_surv / (double)std::max<int64_t>(n_items, 1);
-            while (lo < n_items) {
-                int64_t step = (int64_t)(0.8 * (double)qcap / std::max(density, 1e-12));
-                step = std::max<int64_t>(1, std::min(step, n_items - lo));
-                int64_t c = 0;
-                st = run_filter(lo, lo + step, &c);
-                if (st) return st;
-                if (c > qcap) {
-                    if (step > 1) {  // too dense here: retry a shorter range
-                        density = std::max(density, (double)c / (double)step);
-                        continue;
-                    }
-                    // one work item alone overflows: give the queue its exact size
-                    A.free_one(queue);
-                    A.free_one(bkeys);
-                    qcap = c;
-                    st = A.alloc(&queue, (size_t)qcap);
-                    if (!st) st = A.alloc(&bkeys, (size_t)qcap);
-                    if (st) return st;
-                    fa.queue = queue;
-                    fa.qcap = qcap;
-                    st = run_filter(lo, lo + 1, &c);
+                BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+                if (nc > 0) {
+                    st = launch_verify(cq, nc, soff, stok, ssz, perm, need, lim, bm, W, keys, &ctr[3],
+                                       &ctr[4], nbits, sms, s, sim, p, q);
                     if (st) return st;
                 }
-                int64_t r = 0;
-                st = run_verify(queue, c, bkeys, &r);
-                if (!st) st = append(bkeys, r);
-                if (st) return st;
-                lo += step;
-                if (c > 0) density = 0.5 * density + 0.5 * (double)c / (double)step;
+                BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+                int64_t hv2[2] = {0, 0};
+                BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                BMJ_CHECK(cudaStreamSynchronize(s));
+                n_res = hv2[0];
+                stl.survivors = hv2[1];
+                stl.verified = hv2[1];
+                stl.ms_filter = ev.ms(3, 4);
+                stl.ms_verify = ev.ms(5, 6);
+                done = true;
+            } else if (pst == BMJ_ERR_OOM) {  // too many candidates: the window instead
+                cudaGetLastError();
+                stl.candidates = -1;
+            } else {
+                return pst;
             }
-            A.free_one(bkeys);
         }
-        A.free_one(queue);
+        if (!done) {
+            // ---- Bitmap Filter + exact verification ----
+            // The filter's queue counts every survivor, also past its capacity.  When
+            // the first pass over all work items overflows, the filter reruns with
+            // exact room if that fits (automatic capacity), else the items run in
+            // consecutive ranges whose survivors fit the queue, each verified before
+            // the next; no pair is ever dropped.
+            const bool user_cap = o.queue_cap > 0;
+            int64_t qcap = user_cap ? o.queue_cap : auto_queue_cap(stl.window_pairs);
+            uint2 *queue = nullptr;
+            st = A.alloc(&queue, (size_t)qcap);
+            if (st == BMJ_ERR_OOM && user_cap) {  // a requested capacity that does not fit: the
+                cudaGetLastError();                // automatic one, drained in item ranges
+                qcap = std::min(qcap, auto_queue_cap(stl.window_pairs));
+                st = A.alloc(&queue, (size_t)qcap);
+            }
+            if (st) return st;
+            FilterArgs fa;
+            fa.bm = bm;
+            fa.ssz = ssz;
+            fa.lim = lim;
+            fa.n = n;
+            fa.row0 = r0;
+            fa.row_end = r1;
+            fa.p = p;
+            fa.sim = sim;
+            fa.q = q;
+            fa.tile_item_off = tile_off;
+            fa.tile_c0 = tile_c0;
+            fa.n_tiles = n_tiles;
+            fa.n_items = n_items;
+            fa.tile_rows = tile_rows;
+            fa.chunk_cols = chunk_cols;
+            fa.queue = queue;
+            fa.qcount = &ctr[1];
+            fa.qcap = qcap;
+            fa.item_counter = &ctr[2];
+            if (fault.timeout) {
+                fa.fault_skip_copy = 1;
+                fa.wait_limit = 1 << 12;
+            }
+            // Filters work items [lo, hi) into the queue; *count = their survivors.
+            auto run_filter = [&](int64_t lo, int64_t hi, int64_t *count) -> int {
+                const unsigned long long init[2] = {0ull, (unsigned long long)lo};
+                BMJ_CHECK(cudaMemcpyAsync(&ctr[1], init, sizeof(init), cudaMemcpyHostToDevice, s));
+                fa.n_items = hi;
+                BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+                int rc = launch_filter_tma(fa, W, err, sms, s);
+                if (rc) return rc;
+                BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+                int herr = 0;
+                BMJ_CHECK(cudaMemcpyAsync(count, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                BMJ_CHECK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+                BMJ_CHECK(cudaStreamSynchronize(s));
+                if (herr) return BMJ_ERR_TIMEOUT;
+                stl.filter_passes++;
+                stl.ms_filter += ev.ms(3, 4);
+                return BMJ_OK;
+            };
+            // Verifies the m survivors at qptr into out_keys (*n_out results).
+            auto run_verify = [&](const uint2 *qptr, int64_t m, uint64_t *out_keys,
+                                  int64_t *n_out) -> int {
+                BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
+                BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+                int rc = launch_verify(qptr, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
+                                       &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms, s, sim, p, q);
+                if (rc) return rc;
+                BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+                int64_t hv2[2] = {0, 0};
+                BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                BMJ_CHECK(cudaStreamSynchronize(s));
+                *n_out = hv2[0];
+                stl.verified += bm2 ? hv2[1] : m;
+                stl.ms_verify += ev.ms(5, 6);
+                return BMJ_OK;
+            };
+
+            int64_t n_surv = 0;
+            st = run_filter(0, n_items, &n_surv);
+            if (st) return st;
+            stl.survivors = n_surv;
+            bool banded = false;
+            if (n_surv > qcap) {
+                uint2 *exact = nullptr;
+                if (!user_cap && A.alloc(&exact, (size_t)n_surv) == BMJ_OK) {
+                    A.free_one(queue);
+                    queue = exact;
+                    qcap = n_surv;
+                    fa.queue = queue;
+                    fa.qcap = qcap;
+                    int64_t again = 0;
+                    st = run_filter(0, n_items, &again);
+                    if (st) return st;
+                } else {
+                    banded = true;
+                }
+            }
+            int64_t res_cap = 0;
+            // Appends r result keys from src to the growing result buffer.
+            auto append = [&](const uint64_t *src, int64_t r) -> int {
+                if (n_res + r > res_cap) {
+                    const int64_t ncap = std::max(2 * res_cap, n_res + r);
+                    uint64_t *grown = nullptr;
+                    int rc = A.alloc(&grown, (size_t)ncap);
+                    if (rc) return rc;
+                    if (n_res)
+                        BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
+                                                  cudaMemcpyDeviceToDevice, s));
+                    if (keys) A.free_one(keys);
+                    keys = grown;
+                    res_cap = ncap;
+                }
+                if (r)
+                    BMJ_CHECK(cudaMemcpyAsync(keys + n_res, src, r * sizeof(uint64_t),
+                                              cudaMemcpyDeviceToDevice, s));
+                n_res += r;
+                return BMJ_OK;
+            };
+            if (!banded && !fault.keys && A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1)) == BMJ_OK) {
+                st = run_verify(queue, n_surv, keys, &n_res);
+                if (st) return st;
+            } else if (!banded) {
+                // every survivor is queued but a key buffer as long as the queue does
+                // not fit: verify the queue in slices (results <= survivors per slice)
+                const int64_t slice = std::max<int64_t>(
+                    1, std::min<int64_t>(fault.keys ? (n_surv + 4) / 5 : n_surv, (int64_t)1 << 26));
+                uint64_t *bkeys = nullptr;
+                st = A.alloc(&bkeys, (size_t)slice);
+                if (st) return st;
+                for (int64_t at = 0; at < n_surv; at += slice) {
+                    int64_t r = 0;
+                    st = run_verify(queue + at, std::min(slice, n_surv - at), bkeys, &r);
+                    if (!st) st = append(bkeys, r);
+                    if (st) return st;
+                }
+                A.free_one(bkeys);
+            } else {
+                // Item ranges sized from the measured survivor density; a range that
+                // still overflows is split again, and a single item that overflows
+                // gets a queue of exactly its size.
+                uint64_t *bkeys = nullptr;
+                st = A.alloc(&bkeys, (size_t)qcap);
+                if (st) return st;
+                int64_t lo = 0;
+                double density = (double)n_surv / (double)std::max<int64_t>(n_items, 1);
+                while (lo < n_items) {
+                    int64_t step = (int64_t)(0.8 * (double)qcap / std::max(density, 1e-12));
+                    step = std::max<int64_t>(1, std::min(step, n_items - lo));
+                    int64_t c = 0;
+                    st = run_filter(lo, lo + step, &c);
+                    if (st) return st;
+                    if (c > qcap) {
+                        if (step > 1) {  // too dense here: retry a shorter range
+                            density = std::max(density, (double)c / (double)step);
+                            continue;
+                        }
+                        // one work item alone overflows: give the queue its exact size
+                        A.free_one(queue);
+                        A.free_one(bkeys);
+                        qcap = c;
+                        st = A.alloc(&queue, (size_t)qcap);
+                        if (!st) st = A.alloc(&bkeys, (size_t)qcap);
+                        if (st) return st;
+                        fa.queue = queue;
+                        fa.qcap = qcap;
+                        st = run_filter(lo, lo + 1, &c);
+                        if (st) return st;
+                    }
+                    int64_t r = 0;
+                    st = run_verify(queue, c, bkeys, &r);
+                    if (!st) st = append(bkeys, r);
+                    if (st) return st;
+                    lo += step;
+                    if (c > 0) density = 0.5 * density + 0.5 * (double)c / (double)step;
+                }
+                A.free_one(bkeys);
+            }
+            A.free_one(queue);
+        }
 
         // ---- canonical order ----
         if (n_res > 0) {
@@ -557,6 +602,9 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     if (o.row_begin < 0 || o.row_end < 0 || o.row_end < o.row_begin) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates == BMJ_CAND_PREFIX && (o.row_begin != 0 || o.row_end != 0))
+        return BMJ_ERR_INVALID_ARG;
     if ((o.row_begin != 0 || o.row_end != 0) && o.row_end > coll->n_sets) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(coll, sim, p, q, o, out, stats);

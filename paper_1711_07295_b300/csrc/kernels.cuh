@@ -57,6 +57,15 @@ int launch_window_count(const uint32_t *ssz, int64_t n, SimWindow win,
                         unsigned long long *out, cudaStream_t s, int64_t row0 = 0,
                         int64_t row_end = -1);
 
+// Candidates of the prefix filter (Section 2.2, prefix.cu): the pairs (i, j),
+// j < i in size order inside the window, whose prefixes share a token, each
+// once.  On the size-sorted collection (sizes, sorted CSR).  *n_slots is the
+// number of (rank, pair) slots examined; BMJ_ERR_OOM when they exceed
+// max_cand (> 0) or do not fit.
+int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, int64_t n,
+                      int64_t ntok, SimWindow win, int64_t max_cand, Arena &A, cudaStream_t s,
+                      uint2 **cand, int64_t *n_cand, int64_t *n_slots);
+
 struct FilterArgs {
     const uint64_t *bm;
     const uint32_t *ssz;

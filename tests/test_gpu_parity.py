@@ -325,3 +325,38 @@ def test_measured_popc_rate_matches_the_unit_count():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     nominal = sms * 16 * 2032e6
     assert 0.5 * nominal < rate < 1.05 * nominal, (rate, nominal)
+
+
+# ------------------------------------------ prefix-filter candidates (Section 2.2)
+@pytest.mark.parametrize("b", [64, 128, 256])
+@pytest.mark.parametrize("sim,p,q", [(_bmj.BMJ_JACCARD, 1, 2), (_bmj.BMJ_JACCARD, 4, 5),
+                                     (_bmj.BMJ_JACCARD, 19, 20), (_bmj.BMJ_COSINE, 3, 4),
+                                     (_bmj.BMJ_DICE, 9, 10), (_bmj.BMJ_OVERLAP, 5, 1)])
+def test_prefix_filter_candidates(sim, p, q, b):
+    # Only the window pairs whose prefixes share a token reach the Bitmap Filter: the
+    # pair list equals the oracle's join, and candidates, survivors and results equal
+    # the oracle's prefix-filter counts (ranks by (frequency, token), each pair once).
+    off, tok = I.random_collection(4001, 3000, 1, 60, seed=300 + b + sim + p, zipf_s=1.0,
+                                   planted_frac=0.15)
+    a, bb, st = gpu_join(off, tok, p, q, b=b, sim=sim, candidates=_bmj.BMJ_CAND_PREFIX)
+    ra, rb = O.self_join(off, tok, p, q, sim=sim)
+    assert np.array_equal(a, ra) and np.array_equal(bb, rb)
+    c, s, r = O.prefix_counts(off, tok, p, q, b, O.XOR, sim=sim)
+    assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r)
+    w, _, _ = O.filter_counts(off, tok, p, q, b, O.XOR, sim=sim)
+    assert st["window_pairs"] == w and c <= w
+
+
+def test_prefix_filter_on_the_million_set_workload(million):
+    # 1M sets at 9/10 and 19/20: the same pairs as the window-mode join, far fewer pairs
+    # through the Bitmap Filter.
+    off, tok = million
+    off_d, tok_d = dev(off, tok)
+    for p, q in ((9, 10), (19, 20)):
+        w_pairs, _, st_w = _bmj.bmj_self_join(off_d, tok_d, p, q, b=64, output_on_device=True)
+        x_pairs, _, st_x = _bmj.bmj_self_join(off_d, tok_d, p, q, b=64, output_on_device=True,
+                                              candidates=_bmj.BMJ_CAND_PREFIX)
+        assert torch.equal(w_pairs.a, x_pairs.a) and torch.equal(w_pairs.b, x_pairs.b)
+        assert st_x["results"] == st_w["results"] and 0 < st_x["candidates"] < st_w["window_pairs"] // 10
+        w_pairs.release()
+        x_pairs.release()
