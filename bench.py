@@ -62,6 +62,8 @@ def parse_args():
                     help="target wall time of the CPU baseline's sample (rows are scaled to it)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-joins comparison (512 jobs)")
+    ap.add_argument("--no-prefix", action="store_true",
+                    help="skip the prefix-filter candidate joins")
     ap.add_argument("--no-sims", action="store_true",
                     help="skip the joins with Cosine, Dice and Overlap similarity")
     ap.add_argument("--no-combined", action="store_true",
@@ -394,6 +396,26 @@ def run_ours(args):
                                                          max(st["ms_filter"] / 1e3, 1e-9))})
             sims[name] = rows
 
+    # ---- prefix-filter candidates (Section 2.2) against the whole window ----
+    prefix = None
+    if not args.no_prefix:
+        prefix = []
+        for (p, q) in THRESHOLDS:
+            r, _, _ = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True,
+                                         candidates=_bmj.BMJ_CAND_PREFIX, stream=stream.cuda_stream)
+            r.release()
+            r, _, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True,
+                                          candidates=_bmj.BMJ_CAND_PREFIX,
+                                          stream=stream.cuda_stream)
+            r.release()
+            wj = per_thr[(p, q)]["ms_total"] / args.steps
+            prefix.append({"threshold": f"{p}/{q}", "window_pairs": st["window_pairs"],
+                           "candidates": st["candidates"], "survivors": st["survivors"],
+                           "results": st["results"], "join_ms": round(st["ms_total"], 3),
+                           "candidate_ms": round(st["ms_filter"], 3),
+                           "window_join_ms": round(wj, 3),
+                           "speedup_vs_window": round(wj / st["ms_total"], 3)})
+
     # ---- optional b sweep (outside the headline) ----
     sweep = None
     if args.sweep:
@@ -485,6 +507,11 @@ def run_ours(args):
             out["sweep_b"] = sweep
         if combined:
             out["combined_method"] = combined
+        if prefix:
+            out["prefix_filter"] = {"workload": "the 1,000,000-set collection at b = " + str(b) +
+                                                ", candidates from the prefix filter, one join "
+                                                "per threshold, against the step's window joins",
+                                    "joins": prefix}
         if sims:
             out["similarity_functions"] = {
                 "workload": "the 1,000,000-set collection at b = " + str(b) + ", one join per "
@@ -591,6 +618,15 @@ def run_ten_million(args, dev):
                     "verify_ms": round(st["ms_verify"], 2),
                     "pairs_per_s": round(st["window_pairs"] / (st["ms_total"] / 1e3)),
                     "filter_pairs_per_s": round(st["window_pairs"] / (st["ms_filter"] / 1e3))})
+    for p, q in ((3, 5), (9, 10)):   # the same joins with prefix-filter candidates
+        r, _, st = _bmj.bmj_self_join(off, tok, p, q, b=128, output_on_device=True,
+                                      candidates=_bmj.BMJ_CAND_PREFIX, stream=stream.cuda_stream)
+        r.release()
+        win = next(x for x in out if x["threshold"] == f"{p}/{q}")
+        win["prefix_filter"] = {"candidates": st["candidates"], "survivors": st["survivors"],
+                                "results": st["results"], "join_ms": round(st["ms_total"], 2),
+                                "candidate_ms": round(st["ms_filter"], 2),
+                                "speedup_vs_window": round(win["join_ms"] / st["ms_total"], 3)}
     del off, tok
     torch.cuda.empty_cache()
     return {"workload": "self-join of 10,000,000 sets, tokens Zipf(s=1.0) over 1,000,000, sizes "
