@@ -35,10 +35,17 @@ unsigned grid_p(int64_t n, int threads, int64_t cap = 148 * 32) {
     return (unsigned)g;
 }
 
-__global__ void k_tok_keys(const int32_t *__restrict__ tok, int64_t T, uint64_t *__restrict__ out) {
+// Token values as sort keys, and their maximum (for the number of key bits).
+__global__ void k_tok_keys(const int32_t *__restrict__ tok, int64_t T, uint64_t *__restrict__ out,
+                           unsigned int *__restrict__ max_tok) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T; k += stride)
+    unsigned int m = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T; k += stride) {
         out[k] = (uint64_t)(uint32_t)tok[k];
+        m = max(m, (unsigned int)tok[k]);
+    }
+    m = __reduce_max_sync(kFullP, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(max_tok, m);
 }
 
 // 1 where a run of equal sorted tokens starts.
@@ -61,18 +68,23 @@ __global__ void k_run_write(const uint64_t *__restrict__ st, int64_t T,
         }
 }
 
-// (count << 32) | distinct-token index: sorted, this is the rank order.
-__global__ void k_rank_keys(const int64_t *__restrict__ ustart, int64_t nu, uint64_t *__restrict__ key) {
+// (count << ubits) | distinct-token index: sorted, this is the rank order.
+// Keys pack their fields into as few bits as the sizes need, which saves
+// radix-sort passes (ubits = bits of a distinct-token index or rank, sbits =
+// bits of a set position).
+__global__ void k_rank_keys(const int64_t *__restrict__ ustart, int64_t nu, int ubits,
+                            uint64_t *__restrict__ key) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += stride)
-        key[u] = ((uint64_t)(ustart[u + 1] - ustart[u]) << 32) | (uint64_t)u;
+        key[u] = ((uint64_t)(ustart[u + 1] - ustart[u]) << ubits) | (uint64_t)u;
 }
 
-__global__ void k_rank_scatter(const uint64_t *__restrict__ skey, int64_t nu,
+__global__ void k_rank_scatter(const uint64_t *__restrict__ skey, int64_t nu, int ubits,
                                uint32_t *__restrict__ rank_of) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t umask = (1ull << ubits) - 1;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nu; r += stride)
-        rank_of[(uint32_t)skey[r]] = (uint32_t)r;
+        rank_of[skey[r] & umask] = (uint32_t)r;
 }
 
 __device__ __forceinline__ int64_t lb_u32(const uint32_t *a, int64_t n, uint32_t v) {
@@ -85,18 +97,19 @@ __device__ __forceinline__ int64_t lb_u32(const uint32_t *a, int64_t n, uint32_t
     return lo;
 }
 
-// (set << 32) | rank for every token occurrence of the sorted CSR; one thread
-// per set (its keys are contiguous at soff[i]).
+// (set << ubits) | rank for every token occurrence of the sorted CSR; one
+// thread per set (its keys are contiguous at soff[i]).
 __global__ void k_set_keys(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
                            const int32_t *__restrict__ stok, int64_t n,
                            const uint32_t *__restrict__ utok, int64_t nu,
-                           const uint32_t *__restrict__ rank_of, uint64_t *__restrict__ keys) {
+                           const uint32_t *__restrict__ rank_of, int ubits,
+                           uint64_t *__restrict__ keys) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int64_t o = soff[i];
         for (uint32_t k = 0; k < ssz[i]; k++) {
             const int64_t u = lb_u32(utok, nu, (uint32_t)stok[o + k]);
-            keys[o + k] = ((uint64_t)i << 32) | rank_of[u];
+            keys[o + k] = ((uint64_t)i << ubits) | rank_of[u];
         }
     }
 }
@@ -113,38 +126,41 @@ __global__ void k_prefix_len(const uint32_t *__restrict__ ssz, int64_t n, SimWin
         plen[i] = prefix_len(ssz[i], win);
 }
 
-// (rank << 32) | set for the prefix tokens of every set.
+// (rank << sbits) | set for the prefix tokens of every set.
 __global__ void k_prefix_emit(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
                               const uint64_t *__restrict__ srank, int64_t n, SimWindow win,
-                              const int64_t *__restrict__ pofs, uint64_t *__restrict__ idx) {
+                              const int64_t *__restrict__ pofs, int ubits, int sbits,
+                              uint64_t *__restrict__ idx) {
+    const uint64_t umask = (1ull << ubits) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int64_t len = prefix_len(ssz[i], win);
         for (int64_t k = 0; k < len; k++)
-            idx[pofs[i] + k] = ((uint64_t)(uint32_t)srank[soff[i] + k] << 32) | (uint64_t)i;
+            idx[pofs[i] + k] = ((srank[soff[i] + k] & umask) << sbits) | (uint64_t)i;
     }
 }
 
 // Per index entry k = (rank r, set i): the entries of r's list before k (earlier
 // sets in size order) whose size is inside i's window form [lo, k).
 __global__ void k_cand_count(const uint64_t *__restrict__ idx, int64_t P,
-                             const uint32_t *__restrict__ ssz, SimWindow win,
+                             const uint32_t *__restrict__ ssz, SimWindow win, int sbits,
                              int64_t *__restrict__ lo_out, int64_t *__restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t smask = (1ull << sbits) - 1;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += stride) {
         const uint64_t key = idx[k];
-        const uint64_t head = key & 0xffffffff00000000ull;
+        const uint64_t head = key & ~smask;
         int64_t a = 0, b = k;  // first entry of the rank's list
         while (a < b) {
             const int64_t m = (a + b) >> 1;
             if (idx[m] < head) a = m + 1;
             else b = m;
         }
-        const uint64_t low = window_low(ssz[(uint32_t)key], win);
+        const uint64_t low = window_low(ssz[key & smask], win);
         b = k;  // first entry of the list with a size inside the window
         while (a < b) {
             const int64_t m = (a + b) >> 1;
-            if (ssz[(uint32_t)idx[m]] < low) a = m + 1;
+            if (ssz[idx[m] & smask] < low) a = m + 1;
             else b = m;
         }
         lo_out[k] = a;
@@ -160,9 +176,10 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                               const int64_t *__restrict__ cand_off, const int64_t *__restrict__ lo,
                               int64_t C, const uint32_t *__restrict__ ssz,
                               const int64_t *__restrict__ soff, const uint64_t *__restrict__ srank,
-                              SimWindow win, uint2 *__restrict__ out,
+                              SimWindow win, int ubits, int sbits, uint2 *__restrict__ out,
                               unsigned long long *__restrict__ count) {
     const int lane = threadIdx.x & 31;
+    const uint64_t umask = (1ull << ubits) - 1, smask = (1ull << sbits) - 1;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (int64_t base = gw * 32; base < C; base += warps * 32) {
@@ -178,16 +195,16 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
             }
             const int64_t k = a;
             const uint64_t key = idx[k];
-            const uint32_t r = (uint32_t)(key >> 32);
-            i = (uint32_t)key;
-            j = (uint32_t)idx[lo[k] + (o - cand_off[k])];
+            const uint32_t r = (uint32_t)(key >> sbits);
+            i = (uint32_t)(key & smask);
+            j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] & smask);
             const uint64_t *pi = srank + soff[i];
             const uint64_t *pj = srank + soff[j];
             const int64_t ni = prefix_len(ssz[i], win), nj = prefix_len(ssz[j], win);
             int64_t x = 0, y = 0;
             keep = true;
             while (x < ni && y < nj) {
-                const uint32_t rx = (uint32_t)pi[x], ry = (uint32_t)pj[y];
+                const uint32_t rx = (uint32_t)(pi[x] & umask), ry = (uint32_t)(pj[y] & umask);
                 if (rx >= r || ry >= r) break;
                 if (rx == ry) {
                     keep = false;
@@ -216,19 +233,25 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     *n_cand = 0;
     *n_slots = 0;
     if (n < 2 || ntok <= 0) return BMJ_OK;
-    if (ntok >= ((int64_t)1 << 32)) return BMJ_ERR_TOO_LARGE;  // token counts are 32-bit
+    if (ntok >= ((int64_t)1 << 32)) return BMJ_ERR_TOO_LARGE;  // counts and ranks are 32-bit
     const int nbits_set = std::max(1, bit_length((uint64_t)(n - 1)));
     // ---- rank the distinct tokens ----
     uint64_t *tk = nullptr, *st = nullptr;
     int64_t *flag = nullptr, *pos = nullptr, *ustart = nullptr, *tot = nullptr;
+    unsigned int *max_tok = nullptr;
     int rc = A.alloc(&tk, (size_t)ntok);
     if (!rc) rc = A.alloc(&st, (size_t)ntok);
     if (!rc) rc = A.alloc(&flag, (size_t)ntok);
     if (!rc) rc = A.alloc(&pos, (size_t)ntok);
     if (!rc) rc = A.alloc(&tot, 2);
+    if (!rc) rc = A.alloc(&max_tok, 1);
     if (rc) return rc;
-    BMJ_LAUNCH(k_tok_keys, grid_p(ntok, 256), 256, 0, s, stok, ntok, tk);
-    rc = radix_sort_u64(tk, st, ntok, 31, A, s);
+    BMJ_CHECK(cudaMemsetAsync(max_tok, 0, sizeof(unsigned int), s));
+    BMJ_LAUNCH(k_tok_keys, grid_p(ntok, 256), 256, 0, s, stok, ntok, tk, max_tok);
+    unsigned int hmax = 0;
+    BMJ_CHECK(cudaMemcpyAsync(&hmax, max_tok, sizeof(hmax), cudaMemcpyDeviceToHost, s));
+    BMJ_CHECK(cudaStreamSynchronize(s));
+    rc = radix_sort_u64(tk, st, ntok, std::max(1, bit_length((uint64_t)hmax)), A, s);
     if (rc) return rc;
     BMJ_LAUNCH(k_run_heads, grid_p(ntok, 256), 256, 0, s, st, ntok, flag);
     rc = exclusive_scan_i64(flag, pos, ntok, tot, A, s);
@@ -246,17 +269,20 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     if (rc) return rc;
     BMJ_LAUNCH(k_run_write, grid_p(ntok, 256), 256, 0, s, st, ntok, flag, pos, utok, ustart);
     BMJ_CHECK(cudaMemcpyAsync(ustart + nu, &ntok, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    BMJ_LAUNCH(k_rank_keys, grid_p(nu, 256), 256, 0, s, ustart, nu, rkey);
-    rc = radix_sort_u64(rkey, rkey_s, nu, 64, A, s);
+    const int ubits = std::max(1, bit_length((uint64_t)(nu - 1)));
+    const int cbits = std::max(1, bit_length((uint64_t)ntok));
+    BMJ_LAUNCH(k_rank_keys, grid_p(nu, 256), 256, 0, s, ustart, nu, ubits, rkey);
+    rc = radix_sort_u64(rkey, rkey_s, nu, cbits + ubits, A, s);
     if (rc) return rc;
-    BMJ_LAUNCH(k_rank_scatter, grid_p(nu, 256), 256, 0, s, rkey_s, nu, rank_of);
+    BMJ_LAUNCH(k_rank_scatter, grid_p(nu, 256), 256, 0, s, rkey_s, nu, ubits, rank_of);
     A.free_one(flag);
     A.free_one(pos);
     A.free_one(rkey);
     A.free_one(rkey_s);
     // ---- order every set by rank ----
-    BMJ_LAUNCH(k_set_keys, grid_p(n, 256), 256, 0, s, ssz, soff, stok, n, utok, nu, rank_of, tk);
-    rc = radix_sort_u64(tk, st, ntok, 32 + nbits_set, A, s);  // st: (set, rank) in order
+    BMJ_LAUNCH(k_set_keys, grid_p(n, 256), 256, 0, s, ssz, soff, stok, n, utok, nu, rank_of, ubits,
+               tk);
+    rc = radix_sort_u64(tk, st, ntok, ubits + nbits_set, A, s);  // st: (set, rank) in order
     if (rc) return rc;
     A.free_one(tk);
     // ---- index the prefixes by rank ----
@@ -274,8 +300,9 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     rc = A.alloc(&ix, (size_t)P);
     if (!rc) rc = A.alloc(&idx, (size_t)P);
     if (rc) return rc;
-    BMJ_LAUNCH(k_prefix_emit, grid_p(n, 256), 256, 0, s, ssz, soff, st, n, win, plen, ix);
-    rc = radix_sort_u64(ix, idx, P, 64, A, s);
+    BMJ_LAUNCH(k_prefix_emit, grid_p(n, 256), 256, 0, s, ssz, soff, st, n, win, plen, ubits,
+               nbits_set, ix);
+    rc = radix_sort_u64(ix, idx, P, ubits + nbits_set, A, s);
     if (rc) return rc;
     A.free_one(ix);
     // ---- count, then expand the candidates ----
@@ -283,7 +310,7 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     rc = A.alloc(&lo, (size_t)P);
     if (!rc) rc = A.alloc(&coff, (size_t)P + 1);
     if (rc) return rc;
-    BMJ_LAUNCH(k_cand_count, grid_p(P, 256), 256, 0, s, idx, P, ssz, win, lo, coff);
+    BMJ_LAUNCH(k_cand_count, grid_p(P, 256), 256, 0, s, idx, P, ssz, win, nbits_set, lo, coff);
     rc = exclusive_scan_i64(coff, coff, P, coff + P, A, s);
     if (rc) return rc;
     int64_t C = 0;
@@ -299,7 +326,7 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     if (rc) return rc;
     BMJ_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
     BMJ_LAUNCH(k_cand_expand, grid_p(C, 256, 148 * 16), 256, 0, s, idx, P, coff, lo, C, ssz, soff,
-               st, win, out, cnt);
+               st, win, ubits, nbits_set, out, cnt);
     unsigned long long nc = 0;
     BMJ_CHECK(cudaMemcpyAsync(&nc, cnt, sizeof(nc), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));

@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--b", type=int, default=64)
     ap.add_argument("--method", default="xor")
     ap.add_argument("--sim", default="jaccard", choices=("jaccard", "cosine", "dice", "overlap"))
+    ap.add_argument("--candidates", default="window", choices=("window", "prefix"))
     ap.add_argument("--repeat", type=int, default=2)
     args = ap.parse_args()
 
@@ -39,13 +40,14 @@ def main():
     m = _bmj.METHODS[args.method]
     sim = {"jaccard": _bmj.BMJ_JACCARD, "cosine": _bmj.BMJ_COSINE, "dice": _bmj.BMJ_DICE,
            "overlap": _bmj.BMJ_OVERLAP}[args.sim]
+    cand = _bmj.BMJ_CAND_PREFIX if args.candidates == "prefix" else _bmj.BMJ_CAND_WINDOW
     res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m, sim=sim,
-                                    output_on_device=True)
+                                    output_on_device=True, candidates=cand)
     res.release()
     cap = max(1, st["survivors"])
     for _ in range(args.repeat):
         res, _, st = _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, b=args.b, method=m, sim=sim,
-                                        output_on_device=True, queue_cap=cap)
+                                        output_on_device=True, queue_cap=cap, candidates=cand)
         res.release()
     torch.cuda.synchronize()
     print(json.dumps({"sets": args.sets, "threshold": f"{args.p}/{args.q}", "b": args.b,
