@@ -97,19 +97,30 @@ __device__ __forceinline__ int64_t lb_u32(const uint32_t *a, int64_t n, uint32_t
     return lo;
 }
 
+// Rank of every token value, for token universes small enough to index
+// directly (rank_map[token]); larger ones search the distinct tokens instead.
+__global__ void k_rank_map(const uint32_t *__restrict__ utok, const uint32_t *__restrict__ rank_of,
+                           int64_t nu, uint32_t *__restrict__ rank_map) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += stride)
+        rank_map[utok[u]] = rank_of[u];
+}
+
 // (set << ubits) | rank for every token occurrence of the sorted CSR; one
 // thread per set (its keys are contiguous at soff[i]).
 __global__ void k_set_keys(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
                            const int32_t *__restrict__ stok, int64_t n,
                            const uint32_t *__restrict__ utok, int64_t nu,
-                           const uint32_t *__restrict__ rank_of, int ubits,
+                           const uint32_t *__restrict__ rank_of,
+                           const uint32_t *__restrict__ rank_map, int ubits,
                            uint64_t *__restrict__ keys) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const int64_t o = soff[i];
         for (uint32_t k = 0; k < ssz[i]; k++) {
-            const int64_t u = lb_u32(utok, nu, (uint32_t)stok[o + k]);
-            keys[o + k] = ((uint64_t)i << ubits) | rank_of[u];
+            const uint32_t t = (uint32_t)stok[o + k];
+            const uint32_t r = rank_map ? rank_map[t] : rank_of[lb_u32(utok, nu, t)];
+            keys[o + k] = ((uint64_t)i << ubits) | r;
         }
     }
 }
@@ -280,8 +291,14 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     A.free_one(rkey);
     A.free_one(rkey_s);
     // ---- order every set by rank ----
-    BMJ_LAUNCH(k_set_keys, grid_p(n, 256), 256, 0, s, ssz, soff, stok, n, utok, nu, rank_of, ubits,
-               tk);
+    uint32_t *rank_map = nullptr;
+    if (hmax < (1u << 26)) {  // a direct map of at most 256 MB
+        rc = A.alloc(&rank_map, (size_t)hmax + 1);
+        if (rc) return rc;
+        BMJ_LAUNCH(k_rank_map, grid_p(nu, 256), 256, 0, s, utok, rank_of, nu, rank_map);
+    }
+    BMJ_LAUNCH(k_set_keys, grid_p(n, 256), 256, 0, s, ssz, soff, stok, n, utok, nu, rank_of,
+               rank_map, ubits, tk);
     rc = radix_sort_u64(tk, st, ntok, ubits + nbits_set, A, s);  // st: (set, rank) in order
     if (rc) return rc;
     A.free_one(tk);
