@@ -17,6 +17,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
       histogram, survivors == results when bitmaps are exact, Theorem 1
       soundness (results never exceed what brute force finds);
   join_rows / search -- against self_join / brute force on small inputs.
+  rs_join / rs_filter_counts (Section 2.1) -- brute force with Python ``set``
+      and exact fractions; the cross pairs of the self-join of R and S
+      concatenated; the self-join itself when S is R (pairs r < s); window
+      counts from the two size histograms; survivors == results with exact
+      bitmaps.
   similar_sim / in_window (Cosine, Dice, Overlap; Table 1 and Table 2) --
       Table 1 evaluated with exact fractions and 60-digit square roots, the
       bounds printed in Table 2, the Dice-Jaccard threshold equivalence, brute
@@ -81,6 +86,12 @@ def lib():
         L.oracle_combined_method.restype = C.c_int
         L.oracle_combined_method_sim.argtypes = [C.c_int, i64, i64]
         L.oracle_combined_method_sim.restype = C.c_int
+        L.oracle_rs_join.argtypes = [i64, i64p, i32p, i64, i64p, i32p, C.c_int, i64, i64, u32pp,
+                                     u32pp]
+        L.oracle_rs_join.restype = i64
+        L.oracle_rs_filter_counts.argtypes = [i64, i64p, i32p, i64, i64p, i32p, C.c_int, i64, i64,
+                                              C.c_int, C.c_int, i64p]
+        L.oracle_rs_filter_counts.restype = None
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         L.oracle_free.argtypes = [C.c_void_p]
@@ -146,6 +157,29 @@ def self_join(offsets, tokens, p: int, q: int, sim: int = JACCARD):
     n = lib().oracle_self_join(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim, p, q,
                                C.byref(A), C.byref(B))
     return _take_pairs(n, A, B)
+
+
+def rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, sim: int = JACCARD):
+    """All pairs (r, s) of R x S with sim >= p/q (Eq. 1, an RS-join), sorted by (r, s)."""
+    ro, rt, so, st = _i64(r_offsets), _i32(r_tokens), _i64(s_offsets), _i32(s_tokens)
+    A, B = C.POINTER(C.c_uint32)(), C.POINTER(C.c_uint32)()
+    n = lib().oracle_rs_join(len(ro) - 1, _p(ro, C.c_int64), _p(rt, C.c_int32), len(so) - 1,
+                             _p(so, C.c_int64), _p(st, C.c_int32), sim, p, q, C.byref(A),
+                             C.byref(B))
+    return _take_pairs(n, A, B)
+
+
+def rs_filter_counts(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int,
+                     method: int, sim: int = JACCARD):
+    """(window pairs, survivors, results) of an RS-join with the Bitmap Filter."""
+    ro, rt, so, st = _i64(r_offsets), _i32(r_tokens), _i64(s_offsets), _i32(s_tokens)
+    cnt = np.zeros(3, np.int64)
+    lib().oracle_rs_filter_counts(len(ro) - 1, _p(ro, C.c_int64), _p(rt, C.c_int32), len(so) - 1,
+                                  _p(so, C.c_int64), _p(st, C.c_int32), sim, p, q, b, method,
+                                  _p(cnt, C.c_int64))
+    if cnt[0] < 0:
+        raise MemoryError("oracle allocation failed")
+    return int(cnt[0]), int(cnt[1]), int(cnt[2])
 
 
 def join_rows(offsets, tokens, p: int, q: int, rows, sim: int = JACCARD):
@@ -239,5 +273,6 @@ def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int
 
 __all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "JACCARD", "COSINE", "DICE", "OVERLAP",
            "overlap", "similar", "similar_sim", "in_window", "self_join",
-           "join_rows", "join_rows_window", "search", "bitmap", "bitmaps", "hamming", "upper_bound",
+           "join_rows", "join_rows_window", "rs_join", "rs_filter_counts", "search", "bitmap",
+           "bitmaps", "hamming", "upper_bound",
            "filter_counts", "prefix_counts", "combined_method", "num_threads", "lib"]

@@ -36,6 +36,11 @@
  *                         window, Eq. 2 bound, then verification -- counted
  *   oracle_prefix_counts  the same with the prefix filter (Section 2.2)
  *                         choosing the candidates inside the window
+ *   oracle_rs_join        Eq. 1 between two collections R and S (an RS-join,
+ *                         Section 2.1): every pair (r, s) verified
+ *   oracle_rs_filter_counts  window pairs, Bitmap Filter survivors and
+ *                         results of an RS-join (length window of Table 2,
+ *                         Eq. 2), counted over every pair of R x S
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -652,4 +657,105 @@ void oracle_prefix_counts(int64_t n, const int64_t *off, const int32_t *tok, int
     free(pre); free(tmp);
     free(all); free(ukey); free(utok); free(rank_of); free(keys); free(ord); free(sz); free(poff);
     free(bm);
+}
+
+/*
+ * RS-join (Section 2.1, Eq. 1 with R and S two collections): every pair
+ * (r, s) of R x S is verified; the output is every similar pair as (r, s)
+ * with r an id of R and s an id of S, in (r, s) order.  Rows of R are spread
+ * over threads and concatenated in row order.  Returns the pair count, or -1
+ * on allocation failure (*out_a / *out_b as for oracle_self_join).
+ */
+int64_t oracle_rs_join(int64_t nr, const int64_t *offr, const int32_t *tokr, int64_t ns,
+                       const int64_t *offs, const int32_t *toks, int sim, int64_t p, int64_t q,
+                       uint32_t **out_a, uint32_t **out_b)
+{
+    *out_a = NULL;
+    *out_b = NULL;
+    if (nr <= 0 || ns <= 0) return 0;
+    pairbuf *rows = (pairbuf *)calloc((size_t)nr, sizeof(pairbuf));
+    if (!rows) return -1;
+    int failed = 0;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < nr; r++) {
+        const int32_t *xr = tokr + offr[r];
+        int64_t lr = offr[r + 1] - offr[r];
+        for (int64_t t = 0; t < ns; t++) {
+            int64_t lt = offs[t + 1] - offs[t];
+            int64_t o = oracle_overlap(xr, lr, toks + offs[t], lt);
+            if (oracle_similar_sim(sim, o, lr, lt, p, q))
+                if (pb_push(&rows[r], (uint32_t)r, (uint32_t)t)) failed = 1;
+        }
+    }
+    int64_t total = 0;
+    for (int64_t r = 0; r < nr; r++) total += rows[r].n;
+    uint32_t *A = NULL, *B = NULL;
+    if (!failed && total > 0) {
+        A = (uint32_t *)malloc((size_t)total * sizeof(uint32_t));
+        B = (uint32_t *)malloc((size_t)total * sizeof(uint32_t));
+        if (!A || !B) failed = 1;
+    }
+    int64_t k = 0;
+    for (int64_t r = 0; r < nr; r++) {
+        if (!failed && rows[r].n) {
+            memcpy(A + k, rows[r].a, (size_t)rows[r].n * sizeof(uint32_t));
+            memcpy(B + k, rows[r].b, (size_t)rows[r].n * sizeof(uint32_t));
+            k += rows[r].n;
+        }
+        free(rows[r].a);
+        free(rows[r].b);
+    }
+    free(rows);
+    if (failed) { free(A); free(B); return -1; }
+    *out_a = A;
+    *out_b = B;
+    return total;
+}
+
+/*
+ * Counts of an RS-join run as the GPU algorithm runs a self-join: a pair
+ * (r, s) is in the window when its sizes, smaller first, pass the length
+ * filter of Table 2; a window pair survives the Bitmap Filter when the Eq. 2
+ * bound of its bitmaps passes the similarity test, and a survivor is a result
+ * when its exact overlap does.  Every pair of R x S is looked at, so no order
+ * of the sets is involved.  Writes window pairs, survivors and results to
+ * counts[0..2] (-1 on allocation failure).
+ */
+void oracle_rs_filter_counts(int64_t nr, const int64_t *offr, const int32_t *tokr, int64_t ns,
+                             const int64_t *offs, const int32_t *toks, int sim, int64_t p,
+                             int64_t q, int b, int method, int64_t *counts)
+{
+    counts[0] = counts[1] = counts[2] = 0;
+    if (nr <= 0 || ns <= 0) return;
+    if (method == OR_COMBINED) method = oracle_combined_method_sim(sim, p, q);
+    int W = b / 64;
+    uint64_t *bmr = (uint64_t *)malloc((size_t)nr * (size_t)W * sizeof(uint64_t));
+    uint64_t *bms = (uint64_t *)malloc((size_t)ns * (size_t)W * sizeof(uint64_t));
+    if (!bmr || !bms) {
+        counts[0] = counts[1] = counts[2] = -1;
+        free(bmr); free(bms);
+        return;
+    }
+    oracle_bitmaps(nr, offr, tokr, b, method, bmr);
+    oracle_bitmaps(ns, offs, toks, b, method, bms);
+    int64_t win = 0, surv = 0, res = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : win, surv, res)
+    for (int64_t r = 0; r < nr; r++) {
+        int64_t lr = offr[r + 1] - offr[r];
+        for (int64_t t = 0; t < ns; t++) {
+            int64_t lt = offs[t + 1] - offs[t];
+            int64_t mn = lr < lt ? lr : lt, mx = lr < lt ? lt : lr;
+            if (!oracle_in_window(sim, mn, mx, p, q)) continue;
+            win++;
+            int64_t h = oracle_hamming(bmr + r * W, bms + t * W, b);
+            if (!oracle_similar_sim(sim, oracle_upper_bound(lr, lt, h), lr, lt, p, q)) continue;
+            surv++;
+            int64_t o = oracle_overlap(tokr + offr[r], lr, toks + offs[t], lt);
+            if (oracle_similar_sim(sim, o, lr, lt, p, q)) res++;
+        }
+    }
+    counts[0] = win;
+    counts[1] = surv;
+    counts[2] = res;
+    free(bmr); free(bms);
 }

@@ -629,3 +629,81 @@ def test_prefix_filter_candidates(sim, p, q):
     # the prefix filter is exact: every similar pair is a candidate
     w, s_w, r_w = O.filter_counts(off, tok, p, q, 64, O.XOR, sim=sim)
     assert r == r_w == len(_brute_pairs_sim(sets, sim, p, q)) and r <= s <= s_w and c <= w
+
+
+# ------------------------------------------------- Section 2.1: the RS-join (Eq. 1)
+def _split(off, tok, n_r):
+    """The first n_r sets of a collection as R, the rest as S (each its own CSR)."""
+    ro = off[:n_r + 1].copy()
+    so = off[n_r:] - off[n_r]
+    return ro, tok[:off[n_r]].copy(), so, tok[off[n_r]:].copy()
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 4, 5), (O.COSINE, 3, 5),
+                                     (O.DICE, 7, 10), (O.OVERLAP, 3, 1)])
+def test_rs_join_brute_force(sim, p, q):
+    # every (r, s) of R x S against Table 1 evaluated with Python sets and exact
+    # fractions; R and S of different sizes and token mixes
+    off, tok = I.random_collection(150, 45, 1, 14, seed=90 + sim * 7 + p, planted_frac=0.25)
+    ro, rt, so, st = _split(off, tok, 60)
+    R = [set(rt[ro[i]:ro[i + 1]].tolist()) for i in range(len(ro) - 1)]
+    S = [set(st[so[j]:so[j + 1]].tolist()) for j in range(len(so) - 1)]
+    want = [(i, j) for i in range(len(R)) for j in range(len(S))
+            if _passes(sim, len(R[i] & S[j]), len(R[i]), len(S[j]), p, q)]
+    a, b = O.rs_join(ro, rt, so, st, p, q, sim=sim)
+    assert list(zip(a.tolist(), b.tolist())) == want and len(want) > 0
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 3, 5), (O.DICE, 4, 5), (O.COSINE, 1, 2),
+                                     (O.OVERLAP, 5, 2)])
+def test_rs_join_is_the_cross_part_of_the_self_join(sim, p, q):
+    # the self-join of R and S concatenated holds three kinds of pairs; the ones
+    # with one end in each collection are exactly the RS-join (ids of S shifted)
+    off, tok = I.random_collection(400, 150, 1, 20, seed=120 + sim, planted_frac=0.2)
+    n_r = 170
+    ro, rt, so, st = _split(off, tok, n_r)
+    sa, sb = O.self_join(off, tok, p, q, sim=sim)
+    cross = (sa < n_r) & (sb >= n_r)
+    a, b = O.rs_join(ro, rt, so, st, p, q, sim=sim)
+    assert np.array_equal(a, sa[cross]) and np.array_equal(b, sb[cross] - n_r) and len(a) > 0
+    # and swapping R and S swaps the pairs
+    a2, b2 = O.rs_join(so, st, ro, rt, p, q, sim=sim)
+    order = np.lexsort((a, b))
+    assert np.array_equal(a2, b[order]) and np.array_equal(b2, a[order])
+
+
+def test_rs_join_of_a_collection_with_itself():
+    # S = R: the pairs r < s are the self-join, every (r, r) passes (similarity 1),
+    # and the pair list is symmetric
+    off, tok = I.random_collection(250, 120, 1, 18, seed=131, planted_frac=0.2)
+    for p, q in ((1, 2), (4, 5)):
+        a, b = O.rs_join(off, tok, off, tok, p, q)
+        sa, sb = O.self_join(off, tok, p, q)
+        up = a < b
+        assert np.array_equal(a[up], sa) and np.array_equal(b[up], sb)
+        assert np.count_nonzero(a == b) == len(off) - 1
+        assert len(a) == 2 * len(sa) + len(off) - 1
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 9, 10), (O.COSINE, 3, 5),
+                                     (O.DICE, 7, 10), (O.OVERLAP, 4, 1)])
+def test_rs_filter_counts(sim, p, q):
+    # window pairs from the two size histograms and Table 2's bounds; results =
+    # the RS-join's length; exact bitmaps (universe <= b) pass exactly the results
+    off, tok = I.random_collection(420, 60, 1, 24, seed=140 + sim, planted_frac=0.2)
+    ro, rt, so, st = _split(off, tok, 150)
+    t = Fraction(p, q)
+    lower = {O.OVERLAP: lambda b: t, O.JACCARD: lambda b: b * t,
+             O.COSINE: lambda b: b * t * t, O.DICE: lambda b: b * t / (2 - t)}[sim]
+    hr, hs = np.bincount(np.diff(ro)), np.bincount(np.diff(so))
+    win = sum(int(hr[x]) * int(hs[y]) for x in range(len(hr)) for y in range(len(hs))
+              if hr[x] and hs[y] and min(x, y) >= lower(max(x, y)))
+    n_res = len(O.rs_join(ro, rt, so, st, p, q, sim=sim)[0])
+    for method in (O.XOR, O.SET, O.NEXT):
+        w, s, r = O.rs_filter_counts(ro, rt, so, st, p, q, 64, method, sim=sim)
+        assert (w, r) == (win, n_res) and s == r
+    # a small universe against b = 64 exceeded: survivors between results and window
+    off2, tok2 = I.random_collection(420, 3000, 1, 40, seed=141 + sim, planted_frac=0.3)
+    ro, rt, so, st = _split(off2, tok2, 200)
+    w, s, r = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
+    assert r == len(O.rs_join(ro, rt, so, st, p, q, sim=sim)[0]) and r <= s <= w
