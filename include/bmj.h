@@ -221,6 +221,25 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
                   const bmj_options *opt, bmj_pairs *out, bmj_stats *stats);
 
 /*
+ * Exact RS-join (Section 2.1, Eq. 1 with R and S two collections): every pair
+ * (r, s) of R x S with sim(r, s) >= p/q, by the algorithm of bmj_self_join
+ * (length window of Table 2 with both of its bounds, Bitmap Filter, exact
+ * verification).
+ *   r, s    the two collections (host or device, independently); each must
+ *           start at offset 0; r->n_sets + s->n_sets < 2^31
+ *           (BMJ_ERR_TOO_LARGE otherwise)
+ *   sim, p, q, opt, stats  as for bmj_self_join; opt->row_begin / row_end
+ *           must be 0 and opt->candidates BMJ_CAND_WINDOW
+ *           (BMJ_ERR_INVALID_ARG otherwise)
+ *   out     library-owned pairs (free with bmj_pairs_free): a = id in R, b = id
+ *           in S, sorted by (a, b); every pair appears once
+ * Either collection empty gives an empty result.  The stream in opt is
+ * synchronised before the call returns.
+ */
+int bmj_rs_join(const bmj_collection *r, const bmj_collection *s, int sim, uint32_t p, uint32_t q,
+                const bmj_options *opt, bmj_pairs *out, bmj_stats *stats);
+
+/*
  * Many independent exact self-joins in one pass over the GPU (no counterpart
  * in the paper, which joins one collection per run; the arithmetic of every
  * job is the one of bmj_self_join).

@@ -9,7 +9,7 @@ loudly when it is missing.
 from importlib import import_module
 
 _BINDING = {
-    "bmj_build_bitmaps", "bmj_self_join", "bmj_default_options", "bmj_strerror",
+    "bmj_build_bitmaps", "bmj_self_join", "bmj_rs_join", "bmj_default_options", "bmj_strerror",
     "bmj_kernel_launches", "BmjError", "DevicePairs", "BMJ_XOR", "BMJ_SET", "BMJ_NEXT",
     "BMJ_COMBINED", "BMJ_JACCARD", "METHODS", "lib",
 }

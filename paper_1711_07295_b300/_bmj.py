@@ -137,6 +137,9 @@ SIGNATURES = {
     "bmj_self_join": (C.c_int, [C.POINTER(bmj_collection), C.c_int, C.c_uint32, C.c_uint32,
                                 C.POINTER(bmj_options), C.POINTER(bmj_pairs),
                                 C.POINTER(bmj_stats)]),
+    "bmj_rs_join": (C.c_int, [C.POINTER(bmj_collection), C.POINTER(bmj_collection), C.c_int,
+                              C.c_uint32, C.c_uint32, C.POINTER(bmj_options), C.POINTER(bmj_pairs),
+                              C.POINTER(bmj_stats)]),
     "bmj_self_join_batch": (C.c_int, [C.POINTER(bmj_collection), C.c_int64, C.c_void_p, C.c_int,
                                       C.c_void_p, C.c_void_p, C.POINTER(bmj_options),
                                       C.POINTER(bmj_pairs), C.POINTER(bmj_stats),
@@ -340,9 +343,12 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     del keep
     if st != BMJ_OK:
         raise BmjError(st, "bmj_self_join")
-    stats = st_.as_dict()
+    return _pairs_out(pairs, st_.as_dict(), output_on_device, offsets)
+
+
+def _pairs_out(pairs, stats, output_on_device, like):
     if output_on_device:
-        dev = offsets.device if hasattr(offsets, "device") else "cuda"
+        dev = like.device if hasattr(like, "device") else "cuda"
         return DevicePairs(pairs, dev), None, stats
     n = int(pairs.n)
     if n == 0:
@@ -350,6 +356,37 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
         return np.zeros(0, np.uint32), np.zeros(0, np.uint32), stats
     a, bb = _host_views(pairs)
     return a, bb, stats
+
+
+def bmj_rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int = 64,
+                method: int = BMJ_XOR, output_on_device: bool = False, queue_cap: int = 0,
+                validate: bool = True, stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0,
+                candidates: int = 0):
+    """Exact RS-join of R = (r_offsets, r_tokens) and S = (s_offsets, s_tokens) at p/q.
+
+    Returns ``(a, b, stats)`` as :func:`bmj_self_join` does, with ``a`` ids of R
+    and ``b`` ids of S, sorted by (a, b).
+    """
+    rc, keep_r = make_collection(r_offsets, r_tokens)
+    sc, keep_s = make_collection(s_offsets, s_tokens)
+    o = bmj_default_options()
+    o.b = int(b)
+    o.method = int(method)
+    o.output_on_device = 1 if output_on_device else 0
+    o.validate = 1 if validate else 0
+    o.queue_cap = int(queue_cap)
+    o.cascade_b = int(cascade_b)
+    o.candidates = int(candidates)
+    o.stream = _stream_of(stream, rc.on_device or sc.on_device)
+    pairs = bmj_pairs()
+    st_ = bmj_stats()
+    st = lib().bmj_rs_join(C.byref(rc), C.byref(sc), int(sim), C.c_uint32(int(p)),
+                           C.c_uint32(int(q)), C.byref(o), C.byref(pairs), C.byref(st_))
+    del keep_r, keep_s
+    if st != BMJ_OK:
+        raise BmjError(st, "bmj_rs_join")
+    like = r_offsets if hasattr(r_offsets, "device") else s_offsets
+    return _pairs_out(pairs, st_.as_dict(), output_on_device, like)
 
 
 def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int = BMJ_XOR,

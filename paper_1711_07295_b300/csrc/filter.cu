@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
         const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
         const int64_t i0 = a.row0 + t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
+        const int64_t c_end =
+            a.tile_c1 ? (int64_t)a.tile_c1[t] : min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
         filter_item<W, R, kCos>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, sa, sink);
     }
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
         const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
         const int64_t i0 = a.row0 + t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
+        const int64_t c_end =
+            a.tile_c1 ? (int64_t)a.tile_c1[t] : min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
         if (a.sim == BMJ_COSINE)
             filter_item_generic<true>(a.bm, a.ssz, a.lim, row_end, i0, c0, c1, sa, W, sink);
@@ -88,7 +90,8 @@ __global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterAr
         const int64_t row_end = a.row_end < 0 ? a.n : a.row_end;
         const int64_t i0 = a.row0 + t * a.tile_rows;
         const int64_t c0 = (int64_t)a.tile_c0[t] + chunk * a.chunk_cols;
-        const int64_t c_end = min(i0 + (int64_t)a.tile_rows, row_end) - 1;
+        const int64_t c_end =
+            a.tile_c1 ? (int64_t)a.tile_c1[t] : min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
         filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0), kCos>(a.bm, a.ssz, a.lim, row_end, i0,
                                                                    c0, c1, sa, sink, st);

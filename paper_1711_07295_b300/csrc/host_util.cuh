@@ -98,6 +98,54 @@ inline int stage_collection(const bmj_collection *c, Arena &A, cudaStream_t s, D
     return BMJ_OK;
 }
 
+// The two collections of an RS-join as one device CSR, R's sets first: set x
+// of S becomes set n_r + x.  Each input must start at offset 0.
+inline int stage_two(const bmj_collection *r, const bmj_collection *c, Arena &A, cudaStream_t s,
+                     DevColl *d) {
+    int64_t ends[2][2] = {{0, 0}, {0, 0}};  // first and last offset of R and of S
+    const bmj_collection *in[2] = {r, c};
+    for (int k = 0; k < 2; k++) {
+        const bmj_collection *x = in[k];
+        if (x->on_device) {
+            BMJ_CHECK(cudaMemcpyAsync(&ends[k][0], x->offsets, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaMemcpyAsync(&ends[k][1], x->offsets + x->n_sets, sizeof(int64_t),
+                                      cudaMemcpyDeviceToHost, s));
+        } else {
+            ends[k][0] = x->offsets[0];
+            ends[k][1] = x->offsets[x->n_sets];
+        }
+    }
+    BMJ_CHECK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 2; k++)
+        if (ends[k][0] != 0 || ends[k][1] < 0) return BMJ_ERR_UNSORTED;
+    const int64_t nr = r->n_sets, ns = c->n_sets, tr = ends[0][1], ts = ends[1][1];
+    d->n = nr + ns;
+    d->ntok = tr + ts;
+    int64_t *off = nullptr;
+    int32_t *tok = nullptr;
+    int st = A.alloc(&off, (size_t)(d->n + 1));
+    if (!st) st = A.alloc(&tok, (size_t)(d->ntok > 0 ? d->ntok : 1));
+    if (st) return st;
+    BMJ_CHECK(cudaMemcpyAsync(off, r->offsets, (nr + 1) * sizeof(int64_t),
+                              r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    BMJ_CHECK(cudaMemcpyAsync(off + nr, c->offsets, (ns + 1) * sizeof(int64_t),
+                              c->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    st = launch_add_i64(off + nr, ns + 1, tr, s);
+    if (st) return st;
+    if (tr)
+        BMJ_CHECK(cudaMemcpyAsync(tok, r->tokens, tr * sizeof(int32_t),
+                                  r->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  s));
+    if (ts)
+        BMJ_CHECK(cudaMemcpyAsync(tok + tr, c->tokens, ts * sizeof(int32_t),
+                                  c->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  s));
+    d->off = off;
+    d->tok = tok;
+    return BMJ_OK;
+}
+
 // Validation: returns the status and the maximum set size.
 inline int validate(const DevColl &d, bool check_tokens, Arena &A, cudaStream_t s,
                     uint32_t **sizes, uint32_t **ids, int *max_size) {

@@ -3,6 +3,8 @@
 // bmj_self_join runs the stages of the GPU algorithm (Alg. 6) on one stream:
 //   validate -> size sort -> sorted CSR + bitmaps -> window tiles ->
 //   Bitmap Filter -> exact verification -> canonical result sort -> output.
+// bmj_rs_join runs the same stages on R and S held in one size-sorted array
+// (S first): the rows are R's sets, the columns S's inside each row's window.
 // The host reads back three small counters (validation flags and maximum
 // size; survivor count; result count), which size the next allocations.
 #include <algorithm>
@@ -71,8 +73,11 @@ static int64_t auto_queue_cap(int64_t window) {
     return cap;
 }
 
-static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
-                          const bmj_options &o, bmj_pairs *out, bmj_stats *stats) {
+// coll_s == nullptr: the self-join of coll; else the RS-join of R = coll and
+// S = coll_s.
+static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll_s, int sim,
+                          uint32_t p, uint32_t q, const bmj_options &o, bmj_pairs *out,
+                          bmj_stats *stats) {
     cudaStream_t s = (cudaStream_t)o.stream;
     const int64_t launches0 = launches();
     const FaultPlan fault = read_fault_plan();
@@ -95,9 +100,13 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
     Arena A(s);
     BMJ_CHECK(cudaEventRecord(ev.e[0], s));
     DevColl d;
-    st = stage_collection(coll, A, s, &d);
+    const bool rs = coll_s != nullptr;
+    st = rs ? stage_two(coll, coll_s, A, s, &d) : stage_collection(coll, A, s, &d);
     if (st) return st;
     const int64_t n = d.n;
+    // RS-join: R's sets are ids [0, n_r) of the staged collection and sort after
+    // S's, which fill size-order positions [0, n_sc)
+    const int64_t n_r = rs ? coll->n_sets : 0, n_sc = rs ? coll_s->n_sets : 0;
 
     uint32_t *sizes = nullptr, *ids = nullptr;
     int max_size = 0;
@@ -111,7 +120,7 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
     int64_t n_res = 0;
     const int nbits = n > 1 ? bit_length((uint64_t)(n - 1)) : 1;
     BMJ_CHECK(cudaEventRecord(ev.e[1], s));
-    if (n >= 2) {
+    if (rs ? (n_r > 0 && n_sc > 0) : n >= 2) {
         // ---- size sort (ties by original id) and sorted CSR + bitmaps ----
         uint32_t *ssz = nullptr, *perm = nullptr;
         int64_t *soff = nullptr;
@@ -132,7 +141,10 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
             if (st) return st;
         }
         stl.cascade_b = b2;
-        st = radix_sort_u32_pairs(sizes, ids, ssz, perm, n, bit_length((uint64_t)max_size), A, s);
+        const int sbits = bit_length((uint64_t)max_size);
+        if (rs) st = launch_or_bits(sizes, n_r, 1u << sbits, s);  // R after S
+        if (!st) st = radix_sort_u32_pairs(sizes, ids, ssz, perm, n, sbits + (rs ? 1 : 0), A, s);
+        if (!st && rs) st = launch_and_bits(ssz, n, (1u << sbits) - 1u, s);
         if (st) return st;
         st = launch_widen(ssz, soff, n, s);
         if (!st) st = exclusive_scan_i64(soff, soff, n, nullptr, A, s);
@@ -159,11 +171,11 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
         const int tile_rows = filter_tma_tile_rows(W);
         const int chunk_cols = W <= 4 ? 4096 : 2048;
         // rows joined: size-order positions [r0, r1) (all rows unless a band is given)
-        const int64_t r0 = (o.row_begin == 0 && o.row_end == 0) ? 0 : o.row_begin;
-        const int64_t r1 = (o.row_begin == 0 && o.row_end == 0) ? n : o.row_end;
+        const int64_t r0 = rs ? n_sc : (o.row_begin == 0 && o.row_end == 0) ? 0 : o.row_begin;
+        const int64_t r1 = rs ? n : (o.row_begin == 0 && o.row_end == 0) ? n : o.row_end;
         if (r0 < 0 || r1 < r0 || r1 > n) return BMJ_ERR_INVALID_ARG;
         const int64_t n_tiles = (r1 - r0 + tile_rows - 1) / tile_rows;
-        int32_t *tile_c0 = nullptr;
+        int32_t *tile_c0 = nullptr, *tile_c1 = nullptr;
         int64_t *tile_off = nullptr;
         // [0] window, [1] queue count, [2] item counter, [3] results, [4] verified,
         // [5] first-level survivors (cascade)
@@ -173,6 +185,7 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
         if (!st) st = A.alloc(&lim, (size_t)n_s);
         if (!st) st = A.alloc(&tile_c0, (size_t)(n_tiles > 0 ? n_tiles : 1));
         if (!st) st = A.alloc(&tile_off, (size_t)n_tiles + 1);
+        if (!st && rs) st = A.alloc(&tile_c1, (size_t)(n_tiles > 0 ? n_tiles : 1));
         if (!st) st = A.alloc(&ctr, 6);
         if (!st) st = A.alloc(&err, 1);
         if (st) return st;
@@ -181,11 +194,15 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
         BMJ_CHECK(cudaMemsetAsync(ssz + n, 0, 4 * sizeof(uint32_t), s));
         BMJ_CHECK(cudaMemsetAsync(bm + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
         st = launch_tables(need, lim, n_s, sim, p, q, s);
-        if (!st)
+        if (!st && rs)
+            st = launch_rs_tiles(ssz, n_sc, win, tile_rows, chunk_cols, n_tiles, tile_c0, tile_c1,
+                                 tile_off, r0, r1, s);
+        else if (!st)
             st = launch_tiles(ssz, n, win, tile_rows, chunk_cols, n_tiles, tile_c0, tile_off, s, r0,
                               r1);
         if (!st) st = exclusive_scan_i64(tile_off, tile_off, n_tiles, tile_off + n_tiles, A, s);
-        if (!st) st = launch_window_count(ssz, n, win, &ctr[0], s, r0, r1);
+        if (!st && rs) st = launch_rs_window_count(ssz, n_sc, win, &ctr[0], r0, r1, s);
+        else if (!st) st = launch_window_count(ssz, n, win, &ctr[0], s, r0, r1);
         if (st) return st;
         BMJ_CHECK(cudaEventRecord(ev.e[2], s));
         int64_t hv[2] = {0, 0};
@@ -269,6 +286,7 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
             fa.q = q;
             fa.tile_item_off = tile_off;
             fa.tile_c0 = tile_c0;
+            fa.tile_c1 = tile_c1;
             fa.n_tiles = n_tiles;
             fa.n_items = n_items;
             fa.tile_rows = tile_rows;
@@ -445,12 +463,12 @@ static int self_join_impl(const bmj_collection *coll, int sim, uint32_t p, uint3
                 if (res.a) cudaFree(res.a);
                 return BMJ_ERR_OOM;
             }
-            st = launch_unpack(keys_sorted, n_res, nbits, res.a, res.b, s);
+            st = launch_unpack(keys_sorted, n_res, nbits, res.a, res.b, s, (uint32_t)n_r);
         } else {
             uint32_t *da = nullptr, *db = nullptr;
             st = A.alloc(&da, (size_t)n_res);
             if (!st) st = A.alloc(&db, (size_t)n_res);
-            if (!st) st = launch_unpack(keys_sorted, n_res, nbits, da, db, s);
+            if (!st) st = launch_unpack(keys_sorted, n_res, nbits, da, db, s, (uint32_t)n_r);
             if (!st) {
                 // one page-locked block (a, then b) from the reuse pool, so that the
                 // copy out runs at full link speed without pinning pages every call
@@ -607,7 +625,39 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
         return BMJ_ERR_INVALID_ARG;
     if ((o.row_begin != 0 || o.row_end != 0) && o.row_end > coll->n_sets) return BMJ_ERR_INVALID_ARG;
     try {
-        st = bmj::self_join_impl(coll, sim, p, q, o, out, stats);
+        st = bmj::self_join_impl(coll, nullptr, sim, p, q, o, out, stats);
+    } catch (...) {
+        st = BMJ_ERR_OOM;
+    }
+    bmj::arm_alloc_fault(0);
+    if (st) {
+        bmj_pairs_free(out);
+        cudaGetLastError();
+    }
+    return st;
+}
+
+int bmj_rs_join(const bmj_collection *r, const bmj_collection *s, int sim, uint32_t p, uint32_t q,
+                const bmj_options *opt, bmj_pairs *out, bmj_stats *stats) {
+    if (!out) return BMJ_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    if (stats) memset(stats, 0, sizeof(*stats));
+    int st = check_collection(r);
+    if (!st) st = check_collection(s);
+    if (st) return st;
+    if (r->n_sets + s->n_sets > 0x7fffffffLL) return BMJ_ERR_TOO_LARGE;
+    if (!bmj::sim_valid(sim, p, q)) return BMJ_ERR_INVALID_ARG;
+    bmj_options o;
+    if (opt) o = *opt;
+    else bmj_default_options(&o);
+    if (!bmj::valid_b(o.b)) return BMJ_ERR_INVALID_ARG;
+    if (o.method < BMJ_XOR || o.method > BMJ_COMBINED) return BMJ_ERR_INVALID_ARG;
+    if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
+    if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
+    if (o.row_begin != 0 || o.row_end != 0) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates != BMJ_CAND_WINDOW) return BMJ_ERR_INVALID_ARG;
+    try {
+        st = bmj::self_join_impl(r, s, sim, p, q, o, out, stats);
     } catch (...) {
         st = BMJ_ERR_OOM;
     }

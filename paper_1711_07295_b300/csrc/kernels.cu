@@ -10,6 +10,9 @@
 //   k_build_multi    the same for 64-, 128- and 256-bit Xor/Set bitmaps in one pass
 //   k_tiles,
 //   k_window_count   the length filter window j in [j0(i), i) (Table 2; Alg. 6)
+//   k_rs_tiles,
+//   k_rs_window_count  the same for an RS-join: the columns of S in a row's
+//                    window (both bounds of Table 2)
 // The Bitmap Filter is in filter.cu, verification and output in verify.cu.
 #include "kernels.cuh"
 
@@ -254,6 +257,65 @@ __global__ void k_window_count(const uint32_t *__restrict__ ssz, int64_t n, SimW
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+// ---- RS-join (R and S in one size-sorted array: S at [0, n_cols), R after) ----
+// The columns of S inside the window of a row of size x: sizes in
+// [window_low(x), window_high(x)], a contiguous range [lo, hi) of the sorted S.
+__device__ __forceinline__ void rs_cols(const uint32_t *__restrict__ ssz, int64_t n_cols,
+                                        uint64_t x_lo, uint64_t x_hi, SimWindow win, int64_t *lo,
+                                        int64_t *hi) {
+    *lo = lower_bound_u32(ssz, n_cols, window_low(x_lo, win));
+    const uint64_t top = window_high(x_hi, win);
+    *hi = top == ~0ull ? n_cols : lower_bound_u32(ssz, n_cols, top + 1);
+}
+
+__global__ void k_rs_tiles(const uint32_t *__restrict__ ssz, int64_t n_cols, SimWindow win,
+                           int tile_rows, int chunk_cols, int64_t n_tiles,
+                           int32_t *__restrict__ tile_c0, int32_t *__restrict__ tile_c1,
+                           int64_t *__restrict__ tile_items, int64_t row0, int64_t row_end) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) {
+        const int64_t i0 = row0 + t * tile_rows;
+        const int64_t i1 = min(i0 + (int64_t)tile_rows, row_end) - 1;
+        int64_t lo, hi;
+        rs_cols(ssz, n_cols, ssz[i0], ssz[i1], win, &lo, &hi);  // union of the rows' windows
+        const int64_t c0 = lo & ~(int64_t)3;
+        const int64_t cols = hi - c0;
+        tile_c0[t] = (int32_t)c0;
+        tile_c1[t] = (int32_t)(hi > c0 ? hi : c0);
+        tile_items[t] = (hi > lo && cols > 0) ? (cols + chunk_cols - 1) / chunk_cols : 0;
+    }
+}
+
+__global__ void k_rs_window_count(const uint32_t *__restrict__ ssz, int64_t n_cols, SimWindow win,
+                                  unsigned long long *__restrict__ out, int64_t row0,
+                                  int64_t row_end) {
+    unsigned long long acc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = row0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < row_end; i += stride) {
+        int64_t lo, hi;
+        rs_cols(ssz, n_cols, ssz[i], ssz[i], win, &lo, &hi);
+        if (hi > lo) acc += (unsigned long long)(hi - lo);
+    }
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(kFull, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// v[i] |= bit for i in [0, n) (marks the sort keys of R so that R sorts after S).
+__global__ void k_or_bits(uint32_t *__restrict__ v, int64_t n, uint32_t bit) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] |= bit;
+}
+
+__global__ void k_and_bits(uint32_t *__restrict__ v, int64_t n, uint32_t mask) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] &= mask;
+}
+
+__global__ void k_add_i64(int64_t *__restrict__ v, int64_t n, int64_t add) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) v[i] += add;
+}
+
 unsigned grid_for(int64_t n, int threads, int64_t cap = 148 * 32) {
     int64_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -316,6 +378,42 @@ int launch_window_count(const uint32_t *ssz, int64_t n, SimWindow win,
     if (row_end <= row0) return BMJ_OK;
     BMJ_LAUNCH(k_window_count, grid_for(row_end - row0, 256), 256, 0, s, ssz, n, win, out, row0,
                row_end);
+    return BMJ_OK;
+}
+
+int launch_rs_tiles(const uint32_t *ssz, int64_t n_cols, SimWindow win, int tile_rows,
+                    int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int32_t *tile_c1,
+                    int64_t *tile_items, int64_t row0, int64_t row_end, cudaStream_t s) {
+    if (n_tiles <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_rs_tiles, grid_for(n_tiles, 256), 256, 0, s, ssz, n_cols, win, tile_rows,
+               chunk_cols, n_tiles, tile_c0, tile_c1, tile_items, row0, row_end);
+    return BMJ_OK;
+}
+
+int launch_rs_window_count(const uint32_t *ssz, int64_t n_cols, SimWindow win,
+                           unsigned long long *out, int64_t row0, int64_t row_end,
+                           cudaStream_t s) {
+    if (row_end <= row0) return BMJ_OK;
+    BMJ_LAUNCH(k_rs_window_count, grid_for(row_end - row0, 256), 256, 0, s, ssz, n_cols, win, out,
+               row0, row_end);
+    return BMJ_OK;
+}
+
+int launch_or_bits(uint32_t *v, int64_t n, uint32_t bit, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_or_bits, grid_for(n, 256), 256, 0, s, v, n, bit);
+    return BMJ_OK;
+}
+
+int launch_and_bits(uint32_t *v, int64_t n, uint32_t mask, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_and_bits, grid_for(n, 256), 256, 0, s, v, n, mask);
+    return BMJ_OK;
+}
+
+int launch_add_i64(int64_t *v, int64_t n, int64_t add, cudaStream_t s) {
+    if (n <= 0) return BMJ_OK;
+    BMJ_LAUNCH(k_add_i64, grid_for(n, 256), 256, 0, s, v, n, add);
     return BMJ_OK;
 }
 

@@ -57,6 +57,22 @@ int launch_window_count(const uint32_t *ssz, int64_t n, SimWindow win,
                         unsigned long long *out, cudaStream_t s, int64_t row0 = 0,
                         int64_t row_end = -1);
 
+// RS-join: R and S share one size-sorted array, S at [0, n_cols) and R at
+// [row0, row_end).  Per tile of tile_rows rows of R, the columns of S inside
+// the union of its rows' windows, [tile_c0 (rounded down to a multiple of 4),
+// tile_c1), and their number of chunks.
+int launch_rs_tiles(const uint32_t *ssz, int64_t n_cols, SimWindow win, int tile_rows,
+                    int chunk_cols, int64_t n_tiles, int32_t *tile_c0, int32_t *tile_c1,
+                    int64_t *tile_items, int64_t row0, int64_t row_end, cudaStream_t s);
+// Sum over rows of R of the columns of S inside the row's window.
+int launch_rs_window_count(const uint32_t *ssz, int64_t n_cols, SimWindow win,
+                           unsigned long long *out, int64_t row0, int64_t row_end,
+                           cudaStream_t s);
+// v[i] |= bit, v[i] &= mask, v[i] += add over [0, n).
+int launch_or_bits(uint32_t *v, int64_t n, uint32_t bit, cudaStream_t s);
+int launch_and_bits(uint32_t *v, int64_t n, uint32_t mask, cudaStream_t s);
+int launch_add_i64(int64_t *v, int64_t n, int64_t add, cudaStream_t s);
+
 // Candidates of the prefix filter (Section 2.2, prefix.cu): the pairs (i, j),
 // j < i in size order inside the window, whose prefixes share a token, each
 // once.  On the size-sorted collection (sizes, sorted CSR).  *n_slots is the
@@ -79,6 +95,7 @@ struct FilterArgs {
     int sim = BMJ_JACCARD;  // similarity function of the threshold p/q
     const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
     const int32_t *tile_c0;
+    const int32_t *tile_c1 = nullptr;  // RS-join: end of each tile's columns (else the diagonal)
     int64_t n_tiles;
     int64_t n_items;
     int tile_rows;
@@ -123,8 +140,9 @@ int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const
                   unsigned long long *rcount, unsigned long long *ccount, int nbits, int num_sms,
                   cudaStream_t s, int sim = BMJ_JACCARD, uint32_t p = 0, uint32_t q = 0);
 
-// Splits packed keys into the (a, b) arrays of the output.
+// Splits packed keys into the (a, b) arrays of the output; b_sub is taken off
+// every b (an RS-join's S ids follow R's in its packed keys).
 int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,
-                  cudaStream_t s);
+                  cudaStream_t s, uint32_t b_sub = 0);
 
 }  // namespace bmj

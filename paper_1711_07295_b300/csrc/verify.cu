@@ -201,13 +201,13 @@ __global__ void __launch_bounds__(256)
 }
 
 __global__ void k_unpack(const uint64_t *__restrict__ keys, int64_t n, int nbits,
-                         uint32_t *__restrict__ a, uint32_t *__restrict__ b) {
+                         uint32_t *__restrict__ a, uint32_t *__restrict__ b, uint32_t b_sub) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const uint64_t mask = (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint64_t k = keys[i];
         a[i] = (uint32_t)(k >> nbits);
-        b[i] = (uint32_t)(k & mask);
+        b[i] = (uint32_t)(k & mask) - b_sub;
     }
 }
 
@@ -260,9 +260,9 @@ int launch_verify(const uint2 *queue, int64_t n_surv, const int64_t *soff, const
 }
 
 int launch_unpack(const uint64_t *keys, int64_t n, int nbits, uint32_t *a, uint32_t *b,
-                  cudaStream_t s) {
+                  cudaStream_t s, uint32_t b_sub) {
     if (n <= 0) return BMJ_OK;
-    BMJ_LAUNCH(k_unpack, grid_for(n, 256, 148 * 32), 256, 0, s, keys, n, nbits, a, b);
+    BMJ_LAUNCH(k_unpack, grid_for(n, 256, 148 * 32), 256, 0, s, keys, n, nbits, a, b, b_sub);
     return BMJ_OK;
 }
 
