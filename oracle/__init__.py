@@ -26,8 +26,13 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
       Table 1 evaluated with exact fractions and 60-digit square roots, the
       bounds printed in Table 2, the Dice-Jaccard threshold equivalence, brute
       force joins, window counts from the size histogram.
-  Cutoff point (Section 3.5, Eq. 5 inverted) -- parity unpinned: the paper's
-      Xor figure 4983 does not follow from its own Eq. 5.
+  expected.cutoff (Section 3.5, Eq. 4-6 inverted) -- the values the text
+      quotes (55 at b = 64; Set 2129 and the Xor/Set ratios 2.3 and 1.47 at
+      b = 1024) and Alg. 4's switch points 0.56 / 0.73; the paper's Xor figure
+      4983 does not follow from its own Eq. 5: parity unpinned for it.
+  filter_counts / rs_filter_counts with a cutoff -- against the counts
+      without one: the window and the results are unchanged, the survivors
+      grow by exactly the bound-rejected pairs whose larger set is above it.
 """
 from __future__ import annotations
 
@@ -77,7 +82,7 @@ def lib():
         L.oracle_upper_bound.argtypes = [i64, i64, i64]
         L.oracle_upper_bound.restype = i64
         L.oracle_filter_counts.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, C.c_int, C.c_int,
-                                           i64p]
+                                           i64, i64p]
         L.oracle_filter_counts.restype = None
         L.oracle_prefix_counts.argtypes = [i64, i64p, i32p, C.c_int, i64, i64, C.c_int, C.c_int,
                                            i64p]
@@ -90,7 +95,7 @@ def lib():
                                      u32pp]
         L.oracle_rs_join.restype = i64
         L.oracle_rs_filter_counts.argtypes = [i64, i64p, i32p, i64, i64p, i32p, C.c_int, i64, i64,
-                                              C.c_int, C.c_int, i64p]
+                                              C.c_int, C.c_int, i64, i64p]
         L.oracle_rs_filter_counts.restype = None
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
@@ -170,13 +175,14 @@ def rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, sim: int =
 
 
 def rs_filter_counts(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int,
-                     method: int, sim: int = JACCARD):
-    """(window pairs, survivors, results) of an RS-join with the Bitmap Filter."""
+                     method: int, sim: int = JACCARD, cutoff: int = 0):
+    """(window pairs, survivors, results) of an RS-join with the Bitmap Filter (pairs whose
+    larger set exceeds ``cutoff`` > 0 tokens skip the bound)."""
     ro, rt, so, st = _i64(r_offsets), _i32(r_tokens), _i64(s_offsets), _i32(s_tokens)
     cnt = np.zeros(3, np.int64)
     lib().oracle_rs_filter_counts(len(ro) - 1, _p(ro, C.c_int64), _p(rt, C.c_int32), len(so) - 1,
                                   _p(so, C.c_int64), _p(st, C.c_int32), sim, p, q, b, method,
-                                  _p(cnt, C.c_int64))
+                                  cutoff, _p(cnt, C.c_int64))
     if cnt[0] < 0:
         raise MemoryError("oracle allocation failed")
     return int(cnt[0]), int(cnt[1]), int(cnt[2])
@@ -260,12 +266,14 @@ def prefix_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int
     return int(cnt[0]), int(cnt[1]), int(cnt[2])
 
 
-def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int = JACCARD):
-    """(window pairs, survivors, results) of Alg. 6 + host verification."""
+def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int = JACCARD,
+                  cutoff: int = 0):
+    """(window pairs, survivors, results) of Alg. 6 + host verification; pairs whose larger
+    set exceeds ``cutoff`` > 0 tokens skip the bound (Section 3.5)."""
     off, tok = _i64(offsets), _i32(tokens)
     cnt = np.zeros(3, np.int64)
     lib().oracle_filter_counts(len(off) - 1, _p(off, C.c_int64), _p(tok, C.c_int32), sim, p, q,
-                               b, method, _p(cnt, C.c_int64))
+                               b, method, cutoff, _p(cnt, C.c_int64))
     if cnt[0] < 0:
         raise MemoryError("oracle allocation failed")
     return int(cnt[0]), int(cnt[1]), int(cnt[2])

@@ -487,11 +487,14 @@ int64_t oracle_upper_bound(int64_t nr, int64_t ns, int64_t hamming)
  *      runs without it);
  *   4. a survivor is a result iff it passes oracle_similar.
  * method selects the bitmap generation (OR_COMBINED resolved from p/q).
+ * cutoff > 0 is the cutoff point of Section 3.5: a pair whose larger set has
+ * more than cutoff tokens skips the bound (Alg. 5) and is a survivor as it is;
+ * cutoff <= 0 applies the bound to every pair (the GPU algorithm's setting).
  * Writes window pairs, survivors and results to counts[0..2].  The sort is a
  * plain insertion of (size, id) keys through qsort of packed keys.
  */
 void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int sim, int64_t p,
-                          int64_t q, int b, int method, int64_t *counts)
+                          int64_t q, int b, int method, int64_t cutoff, int64_t *counts)
 {
     counts[0] = counts[1] = counts[2] = 0;
     if (n <= 1) return;
@@ -524,8 +527,10 @@ void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int
             win++;
             int64_t h = oracle_hamming(bm + i * W, bm + j * W, b);
             int64_t ub = oracle_upper_bound(sz[i], sz[j], h);
-            /* the bound passes iff the similarity of an overlap of ub passes */
-            if (oracle_similar_sim(sim, ub, sz[i], sz[j], p, q)) {
+            /* the bound passes iff the similarity of an overlap of ub passes;
+               sz[i] >= sz[j] is the larger size (size order) */
+            int skip = cutoff > 0 && sz[i] > cutoff;
+            if (skip || oracle_similar_sim(sim, ub, sz[i], sz[j], p, q)) {
                 surv++;
                 int64_t o = oracle_overlap(tok + off[ord[i]], sz[i], tok + off[ord[j]], sz[j]);
                 if (oracle_similar_sim(sim, o, sz[i], sz[j], p, q)) res++;
@@ -718,12 +723,13 @@ int64_t oracle_rs_join(int64_t nr, const int64_t *offr, const int32_t *tokr, int
  * filter of Table 2; a window pair survives the Bitmap Filter when the Eq. 2
  * bound of its bitmaps passes the similarity test, and a survivor is a result
  * when its exact overlap does.  Every pair of R x S is looked at, so no order
- * of the sets is involved.  Writes window pairs, survivors and results to
+ * of the sets is involved.  cutoff as for oracle_filter_counts (on the larger
+ * of the two sizes).  Writes window pairs, survivors and results to
  * counts[0..2] (-1 on allocation failure).
  */
 void oracle_rs_filter_counts(int64_t nr, const int64_t *offr, const int32_t *tokr, int64_t ns,
                              const int64_t *offs, const int32_t *toks, int sim, int64_t p,
-                             int64_t q, int b, int method, int64_t *counts)
+                             int64_t q, int b, int method, int64_t cutoff, int64_t *counts)
 {
     counts[0] = counts[1] = counts[2] = 0;
     if (nr <= 0 || ns <= 0) return;
@@ -748,7 +754,9 @@ void oracle_rs_filter_counts(int64_t nr, const int64_t *offr, const int32_t *tok
             if (!oracle_in_window(sim, mn, mx, p, q)) continue;
             win++;
             int64_t h = oracle_hamming(bmr + r * W, bms + t * W, b);
-            if (!oracle_similar_sim(sim, oracle_upper_bound(lr, lt, h), lr, lt, p, q)) continue;
+            int skip = cutoff > 0 && mx > cutoff;
+            if (!skip && !oracle_similar_sim(sim, oracle_upper_bound(lr, lt, h), lr, lt, p, q))
+                continue;
             surv++;
             int64_t o = oracle_overlap(tokr + offr[r], lr, toks + offs[t], lt);
             if (oracle_similar_sim(sim, o, lr, lt, p, q)) res++;

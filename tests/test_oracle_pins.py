@@ -707,3 +707,77 @@ def test_rs_filter_counts(sim, p, q):
     ro, rt, so, st = _split(off2, tok2, 200)
     w, s, r = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
     assert r == len(O.rs_join(ro, rt, so, st, p, q, sim=sim)[0]) and r <= s <= w
+
+
+# ------------------------------------------------- Section 3.5: the cutoff point
+def test_cutoff_closed_forms_equal_eq4_and_eq5():
+    # the fp64 closed forms used for the cutoff search against the exact sums
+    for b in (64, 128, 256, 1024):
+        for n in (1, 2, 5, 17, 55, 100, 300):
+            assert abs(E.e_set_closed(b, n) - E.e_set(b, n)) <= 1e-9 * max(1, n)
+            assert abs(E.e_xor_closed(b, n) - E.e_xor(b, n)) <= 1e-9 * max(1, n)
+
+
+def test_cutoff_values_quoted_in_text():
+    # Section 3.5: omega(64, 0.72) = 55; at b = 1024 and Jaccard 0.9 the Set cutoff is
+    # 2129 and Xor's is 2.3 times it, at Jaccard 0.8 1.47 times (the normalised
+    # threshold of a Jaccard threshold t is 2t/(1+t)).  The paper's Xor value 4983
+    # does not follow from Eq. 5 (which gives 4863): parity unpinned for it.
+    assert E.cutoff(64, 0.72, "xor") == 55
+    u9, u8 = 2 * 0.9 / 1.9, 2 * 0.8 / 1.8
+    s9, x9 = E.cutoff(1024, u9, "set"), E.cutoff(1024, u9, "xor")
+    assert abs(s9 - 2129) <= 1
+    assert round(x9 / s9, 1) == 2.3
+    assert round(E.cutoff(1024, u8, "xor") / E.cutoff(1024, u8, "set"), 2) == 1.47
+
+
+@pytest.mark.parametrize("b", [256, 1024, 4096])
+def test_combined_switch_points_follow_from_the_cutoffs(b):
+    # Alg. 4 picks the method with the highest cutoff: Next up to 0.56, Set up to
+    # 0.73, Xor above (on the normalised threshold), for any b above 64
+    def best(u):
+        c = {m: E.cutoff(b, u, m) for m in ("set", "xor", "next")}
+        return max(c, key=c.get)
+    for u in (0.50, 0.53, 0.55):
+        assert best(u) == "next", u
+    for u in (0.58, 0.62, 0.66, 0.70, 0.72):
+        assert best(u) == "set", u
+    for u in (0.74, 0.8, 0.9):
+        assert best(u) == "xor", u
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 4, 5), (O.COSINE, 3, 5),
+                                     (O.DICE, 7, 10)])
+def test_filter_counts_with_a_cutoff(sim, p, q):
+    # a cutoff changes neither the window nor the results; survivors grow by exactly
+    # the pairs above it that the bound rejected (counted by brute force per pair)
+    off, tok = I.random_collection(600, 3000, 1, 60, seed=150 + sim + p, planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]] for i in range(len(off) - 1)]
+    bms = O.bitmaps(off, tok, 64, O.XOR)
+    sizes = np.diff(off)
+    t = Fraction(p, q)
+    lower = {O.JACCARD: lambda b: b * t, O.COSINE: lambda b: b * t * t,
+             O.DICE: lambda b: b * t / (2 - t)}[sim]
+    w0, s0, r0 = O.filter_counts(off, tok, p, q, 64, O.XOR, sim=sim)
+    for cut in (10, 30, 59):
+        extra = 0
+        for a, b in itertools.combinations(range(len(sets)), 2):
+            x, y = int(sizes[a]), int(sizes[b])
+            if max(x, y) <= cut or min(x, y) < lower(max(x, y)):
+                continue
+            ub = O.upper_bound(x, y, O.hamming(bms[a], bms[b]))
+            extra += not O.similar_sim(sim, ub, x, y, p, q)
+        w, s, r = O.filter_counts(off, tok, p, q, 64, O.XOR, sim=sim, cutoff=cut)
+        assert (w, r) == (w0, r0) and s == s0 + extra
+        assert extra > 0 or cut == 59
+    # RS-join of the first 300 sets with the rest: with cutoff 1 only pairs of two
+    # single-token sets still meet the bound
+    ro, rt = off[:301].copy(), tok[:off[300]].copy()
+    so, st = off[300:] - off[300], tok[off[300]:].copy()
+    w0, s0, r0 = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
+    w, s, r = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim, cutoff=1)
+    ones = [a for a in range(len(sets)) if sizes[a] == 1]
+    kept = sum(1 for a in ones if a < 300 for b in ones if b >= 300
+               and O.similar_sim(sim, O.upper_bound(1, 1, O.hamming(bms[a], bms[b])), 1, 1, p, q))
+    n1r, n1s = sum(1 for a in ones if a < 300), sum(1 for a in ones if a >= 300)
+    assert (w, r) == (w0, r0) and s == w - (n1r * n1s - kept) and s > s0
