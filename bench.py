@@ -64,6 +64,8 @@ def parse_args():
                     help="skip the batched-joins comparison (512 jobs)")
     ap.add_argument("--no-prefix", action="store_true",
                     help="skip the prefix-filter candidate joins")
+    ap.add_argument("--no-cutoff", action="store_true",
+                    help="skip the joins with the cutoff point of Section 3.5")
     ap.add_argument("--no-rs", action="store_true",
                     help="skip the RS-joins of two 1,000,000-set collections")
     ap.add_argument("--no-sims", action="store_true",
@@ -418,6 +420,25 @@ def run_ours(args):
                            "window_join_ms": round(wj, 3),
                            "speedup_vs_window": round(wj / st["ms_total"], 3)})
 
+    # ---- the cutoff point (Section 3.5): pairs above it skip the filter ----
+    cutoff = None
+    if not args.no_cutoff:
+        cutoff = []
+        for (p, q) in THRESHOLDS:
+            for rep in range(2):
+                r, _, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True,
+                                              cutoff=_bmj.BMJ_CUTOFF_AUTO,
+                                              stream=stream.cuda_stream)
+                r.release()
+            wj = per_thr[(p, q)]["ms_total"] / args.steps
+            cutoff.append({"threshold": f"{p}/{q}", "cutoff": st["cutoff"],
+                           "window_pairs": st["window_pairs"], "survivors": st["survivors"],
+                           "survivors_without": per_thr[(p, q)]["survivors"],
+                           "results": st["results"], "join_ms": round(st["ms_total"], 3),
+                           "verify_ms": round(st["ms_verify"], 3),
+                           "window_join_ms": round(wj, 3),
+                           "speedup_vs_no_cutoff": round(wj / st["ms_total"], 3)})
+
     # ---- RS-join (Section 2.1): the collection against a second one of its kind ----
     rs = None
     if not args.no_rs:
@@ -533,6 +554,11 @@ def run_ours(args):
                                                 ", candidates from the prefix filter, one join "
                                                 "per threshold, against the step's window joins",
                                     "joins": prefix}
+        if cutoff:
+            out["cutoff_point"] = {"workload": "the 1,000,000-set collection at b = " + str(b) +
+                                               ", cutoff from Eq. 4-6 (Xor, normalised threshold "
+                                               "2p/(p+q)), against the step's joins",
+                                   "joins": cutoff}
         if rs:
             out["rs_join"] = {"workload": "R = the 1,000,000-set collection, S = a second one "
                                           "(same recipe, seed 1), b = " + str(b) +
@@ -653,6 +679,17 @@ def run_ten_million(args, dev):
                                 "results": st["results"], "join_ms": round(st["ms_total"], 2),
                                 "candidate_ms": round(st["ms_filter"], 2),
                                 "speedup_vs_window": round(win["join_ms"] / st["ms_total"], 3)}
+    # the cutoff point of Section 3.5 (Eq. 4-6) on the long size tail at 3/5
+    if not args.no_cutoff:
+        r, _, st = _bmj.bmj_self_join(off, tok, 3, 5, b=128, output_on_device=True,
+                                      cutoff=_bmj.BMJ_CUTOFF_AUTO, stream=stream.cuda_stream)
+        r.release()
+        win = next(x for x in out if x["threshold"] == "3/5")
+        win["cutoff_point"] = {"cutoff": st["cutoff"], "survivors": st["survivors"],
+                               "results": st["results"], "join_ms": round(st["ms_total"], 2),
+                               "filter_ms": round(st["ms_filter"], 2),
+                               "verify_ms": round(st["ms_verify"], 2),
+                               "speedup_vs_no_cutoff": round(win["join_ms"] / st["ms_total"], 3)}
     del off, tok
     torch.cuda.empty_cache()
     return {"workload": "self-join of 10,000,000 sets, tokens Zipf(s=1.0) over 1,000,000, sizes "

@@ -134,9 +134,16 @@ typedef struct {
                                   -- fewer pairs at high thresholds, same result; it falls back
                                   to the window when its candidates do not fit in memory, and
                                   needs row_begin = row_end = 0 */
-    int32_t reserved1;
+    int32_t cutoff;            /* bmj_self_join, bmj_rs_join: the cutoff point of Section 3.5.
+                                  0 (default) = none, every window pair meets the Bitmap Filter
+                                  (the paper's GPU setting); n > 0 = a pair whose larger set has
+                                  more than n tokens skips the filter and is verified directly;
+                                  BMJ_CUTOFF_AUTO = n from Eq. 4-6 for b, the method used and the
+                                  normalised threshold (Jaccard 2p/(p+q), Dice and Cosine p/q;
+                                  none for Overlap).  With BMJ_CAND_PREFIX it must be 0. */
 } bmj_options;
 
+#define BMJ_CUTOFF_AUTO (-1)
 #define BMJ_CAND_WINDOW 0
 #define BMJ_CAND_PREFIX 1
 
@@ -153,7 +160,7 @@ typedef struct {
     int32_t method;         /* generation method used (COMBINED resolved) */
     int32_t max_set_size;
     int32_t cascade_b;      /* width of the cascade bitmaps, 0 = none */
-    int32_t reserved_i;
+    int32_t cutoff;         /* cutoff point applied (set size), 0 = none */
     float   ms_prepare;     /* validation, size sort, sorted-CSR gather and bitmap build */
     float   ms_filter;      /* Bitmap Filter kernel(s) */
     float   ms_verify;      /* verification kernel(s) */

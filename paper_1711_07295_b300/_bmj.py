@@ -30,6 +30,7 @@ BMJ_ERR_TOO_LARGE = -9
 BMJ_XOR, BMJ_SET, BMJ_NEXT, BMJ_COMBINED = 0, 1, 2, 3
 BMJ_JACCARD, BMJ_COSINE, BMJ_DICE, BMJ_OVERLAP = 0, 1, 2, 3   # similarity functions (Table 1)
 BMJ_CAND_WINDOW, BMJ_CAND_PREFIX = 0, 1   # candidate pairs: the whole window, or the prefix filter
+BMJ_CUTOFF_AUTO = -1   # bmj_options.cutoff: the cutoff point from Eq. 4-6 (Section 3.5)
 METHODS = {"xor": BMJ_XOR, "set": BMJ_SET, "next": BMJ_NEXT, "combined": BMJ_COMBINED}
 
 
@@ -74,14 +75,14 @@ class bmj_options(C.Structure):
                 ("rows_per_thread", C.c_int32), ("use_graph", C.c_int32),
                 ("cascade_b", C.c_int32), ("sim", C.c_int32), ("row_begin", C.c_int64),
                 ("row_end", C.c_int64), ("candidates", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("cutoff", C.c_int32)]
 
 
 class bmj_stats(C.Structure):
     _fields_ = [("window_pairs", C.c_int64), ("survivors", C.c_int64), ("results", C.c_int64),
                 ("filter_passes", C.c_int64), ("verified", C.c_int64), ("n_launches", C.c_int32),
                 ("b", C.c_int32), ("method", C.c_int32), ("max_set_size", C.c_int32),
-                ("cascade_b", C.c_int32), ("reserved_i", C.c_int32), ("ms_prepare", C.c_float),
+                ("cascade_b", C.c_int32), ("cutoff", C.c_int32), ("ms_prepare", C.c_float),
                 ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
                 ("ms_total", C.c_float), ("reserved_f", C.c_float), ("candidates", C.c_int64)]
 
@@ -317,7 +318,7 @@ class DevicePairs:
 def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BMJ_XOR,
                   output_on_device: bool = False, queue_cap: int = 0, validate: bool = True,
                   stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0,
-                  row_begin: int = 0, row_end: int = 0, candidates: int = 0):
+                  row_begin: int = 0, row_end: int = 0, candidates: int = 0, cutoff: int = 0):
     """Exact Jaccard self-join at threshold p/q.
 
     Returns ``(a, b, stats)``: original ids with a < b sorted by (a, b), as
@@ -335,6 +336,7 @@ def bmj_self_join(offsets, tokens, p: int, q: int, b: int = 64, method: int = BM
     o.row_begin = int(row_begin)
     o.row_end = int(row_end)
     o.candidates = int(candidates)
+    o.cutoff = int(cutoff)
     o.stream = _stream_of(stream, coll.on_device)
     pairs = bmj_pairs()
     st_ = bmj_stats()
@@ -361,7 +363,7 @@ def _pairs_out(pairs, stats, output_on_device, like):
 def bmj_rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int = 64,
                 method: int = BMJ_XOR, output_on_device: bool = False, queue_cap: int = 0,
                 validate: bool = True, stream=None, sim: int = BMJ_JACCARD, cascade_b: int = 0,
-                candidates: int = 0):
+                candidates: int = 0, cutoff: int = 0):
     """Exact RS-join of R = (r_offsets, r_tokens) and S = (s_offsets, s_tokens) at p/q.
 
     Returns ``(a, b, stats)`` as :func:`bmj_self_join` does, with ``a`` ids of R
@@ -377,6 +379,7 @@ def bmj_rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int
     o.queue_cap = int(queue_cap)
     o.cascade_b = int(cascade_b)
     o.candidates = int(candidates)
+    o.cutoff = int(cutoff)
     o.stream = _stream_of(stream, rc.on_device or sc.on_device)
     pairs = bmj_pairs()
     st_ = bmj_stats()

@@ -20,7 +20,7 @@ template <int W, int R, bool kCos>
 __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
     const int lane = threadIdx.x & 31;
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
 __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int W) {
     const int lane = threadIdx.x & 31;
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -66,8 +66,9 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
 // double buffer of column chunks in dynamic shared memory and its two
 // mbarriers; a wait that gives up sets *err and stops the warp.
 // Eight 4-warp blocks per SM (64 registers) for the production variants; the
-// Cosine variant's per-pair limit needs more registers.
-template <int W, int R, int CS, bool kFault, bool kCos>
+// Cosine variant's per-pair limit needs more registers.  kCut: pairs whose
+// larger set is above the cutoff point skip Eq. 2 (Section 3.5).
+template <int W, int R, int CS, bool kFault, bool kCos, bool kCut>
 __global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterArgs a, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     using L = ColStage<W, CS>;
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterAr
         st.skip_copy = (blockIdx.x == 0 && threadIdx.x < 32) ? 1 : 0;
     }
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -93,8 +94,8 @@ __global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterAr
         const int64_t c_end =
             a.tile_c1 ? (int64_t)a.tile_c1[t] : min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0), kCos>(a.bm, a.ssz, a.lim, row_end, i0,
-                                                                   c0, c1, sa, sink, st);
+        filter_item_tma<W, R, CS, (W == 1 ? kAluRowsW1 : 0), kCos, kCut>(a.bm, a.ssz, a.lim, row_end,
+                                                                         i0, c0, c1, sa, sink, st);
         if (!st.ok) {
             drain_stage(st);
             if (lane == 0) atomicOr(err, 1);
@@ -154,28 +155,32 @@ int launch_filter(const FilterArgs &a, int W, int num_sms, cudaStream_t s) {
     }
 }
 
-template <int W, int R, int CS, bool kFault, bool kCos>
+template <int W, int R, int CS, bool kFault, bool kCos, bool kCut>
 int launch_filter_tma_k(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
     using L = ColStage<W, CS>;
     const int smem = 4 * L::kWarpBytes;
     int per_sm = 0;
     BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, k_filter_tma<W, R, CS, kFault, kCos>, 128, smem));
+        &per_sm, k_filter_tma<W, R, CS, kFault, kCos, kCut>, 128, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t blocks = (int64_t)num_sms * per_sm;
     const int64_t need_blocks = (a.n_items + 3) / 4;
     if (need_blocks < blocks) blocks = need_blocks;
     if (blocks < 1) blocks = 1;
-    BMJ_LAUNCH((k_filter_tma<W, R, CS, kFault, kCos>), (unsigned)blocks, 128, smem, s, a, err);
+    BMJ_LAUNCH((k_filter_tma<W, R, CS, kFault, kCos, kCut>), (unsigned)blocks, 128, smem, s, a,
+               err);
     return BMJ_OK;
 }
 
 template <int W, int R, int CS>
 int launch_filter_tma_t(const FilterArgs &a, int *err, int num_sms, cudaStream_t s) {
+    const bool cut = a.cut != 0xffffffffu;
     if (a.sim == BMJ_COSINE)  // (fault injection is exercised with the other functions)
-        return launch_filter_tma_k<W, R, CS, false, true>(a, err, num_sms, s);
-    return a.fault_skip_copy ? launch_filter_tma_k<W, R, CS, true, false>(a, err, num_sms, s)
-                             : launch_filter_tma_k<W, R, CS, false, false>(a, err, num_sms, s);
+        return cut ? launch_filter_tma_k<W, R, CS, false, true, true>(a, err, num_sms, s)
+                   : launch_filter_tma_k<W, R, CS, false, true, false>(a, err, num_sms, s);
+    if (cut) return launch_filter_tma_k<W, R, CS, false, false, true>(a, err, num_sms, s);
+    return a.fault_skip_copy ? launch_filter_tma_k<W, R, CS, true, false, false>(a, err, num_sms, s)
+                             : launch_filter_tma_k<W, R, CS, false, false, false>(a, err, num_sms, s);
 }
 
 int filter_tma_tile_rows(int W) {

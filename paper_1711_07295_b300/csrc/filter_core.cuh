@@ -49,6 +49,7 @@ struct SurvivorSink {
 struct SimArgs {
     SimWindow win;
     uint32_t p, q;
+    uint32_t cut = 0xffffffffu;  // cutoff point: a pair whose larger size exceeds it skips Eq. 2
 };
 
 // Eq. 2 limit of a pair of sizes: from the table indexed by |x|+|y| (Jaccard,
@@ -118,7 +119,7 @@ __device__ __forceinline__ void filter_item(const uint64_t *__restrict__ bm,
                 for (int k = 0; k < R; k++) {
                     const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
                     const bool in_win = rs[k] != 0 && in_window(mn, mx, sa.win);
-                    lim[k] = in_win ? pair_lim<kCos>(lim_tab, rs[k], s, sa) : -1;
+                    lim[k] = !in_win ? -1 : mx > sa.cut ? (1 << 30) : pair_lim<kCos>(lim_tab, rs[k], s, sa);
                 }
             }
 #pragma unroll
@@ -185,7 +186,7 @@ __device__ __forceinline__ void filter_item_generic(const uint64_t *__restrict__
             const uint64_t *colp = bm + jj * W;
             int h = 0;
             for (int w = 0; w < W; w++) h += __popcll(rowp[w] ^ colp[w]);
-            if (h <= pair_lim<kCos>(lim_tab, rs, s, sa)) mask |= 1u << cc;
+            if (mx > sa.cut || h <= pair_lim<kCos>(lim_tab, rs, s, sa)) mask |= 1u << cc;
         }
         const int cnt = __popc(mask);
         const int total = __reduce_add_sync(kFull, cnt);
@@ -475,7 +476,7 @@ __device__ __forceinline__ void flush_masks(const uint32_t (&mask)[R], const int
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
 // arrays must be readable up to 3 entries past the last column (padded).
-template <int W, int R, int CS, int kAluRows = 0, bool kCos = false>
+template <int W, int R, int CS, int kAluRows = 0, bool kCos = false, bool kCut = false>
 __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                                                 const uint32_t *__restrict__ ssz,
                                                 const int32_t *__restrict__ lim_tab,
@@ -555,7 +556,8 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                     for (int k = 0; k < R; k++) {
                         const uint32_t mn = min(rs[k], s), mx = max(rs[k], s);
                         const bool in_win = rs[k] != 0 && in_window(mn, mx, sa.win);
-                        nlim[k] = in_win ? -(pair_lim<kCos>(lim_tab, rs[k], s, sa) + 1) : 0;
+                        if (kCut && in_win && mx > sa.cut) nlim[k] = -(1 << 30);  // skips Eq. 2
+                        else nlim[k] = in_win ? -(pair_lim<kCos>(lim_tab, rs[k], s, sa) + 1) : 0;
                     }
                 }
                 uint32_t cw[2 * W];

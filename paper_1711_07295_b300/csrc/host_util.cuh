@@ -1,6 +1,7 @@
 // host_util.cuh -- host-side helpers shared by the join entry points.
 #pragma once
 
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -48,6 +49,42 @@ inline int combined_method(int sim, uint32_t p, uint32_t q) {
     if (100 * P <= 56 * Q) return BMJ_NEXT;
     if (100 * P >= 73 * Q) return BMJ_XOR;
     return BMJ_SET;
+}
+
+// Section 3.5: the expected Eq. 2 bound of two random n-token sets hashed into
+// b bits -- Eq. 4 (Set) as n + b r^2 - b r with r = (1 - 1/b)^n, Eq. 5 (Xor)
+// with its sum of odd binomial terms in closed form, Eq. 6 (Next).
+inline double expected_bound(int b, int method, double n) {
+    const double bb = (double)b;
+    if (method == BMJ_SET) {
+        const double r = pow(1.0 - 1.0 / bb, n);
+        return n + bb * r * r - bb * r;
+    }
+    if (method == BMJ_NEXT) return fmin(n * n / bb, n);
+    return n - bb / 4.0 * (1.0 - pow(1.0 - 2.0 / bb, 2.0 * n));
+}
+
+// The cutoff point: the largest set size n whose expected normalised bound
+// E(b, n)/n is still at most the normalised threshold (Jaccard 2p/(p+q), Dice
+// and Cosine p/q), at least 1; 0 when there is none (Overlap, whose threshold
+// is not normalised, or a threshold no size reaches below the largest size).
+inline int64_t cutoff_point(int b, int method, int sim, uint32_t p, uint32_t q) {
+    if (sim == BMJ_OVERLAP) return 0;
+    const double u = sim == BMJ_JACCARD ? 2.0 * p / ((double)p + (double)q) : (double)p / (double)q;
+    auto above = [&](int64_t n) { return expected_bound(b, method, (double)n) / (double)n > u; };
+    int64_t hi = 2;
+    while (!above(hi)) {
+        if (hi > kMaxSetSize) return 0;
+        hi *= 2;
+    }
+    int64_t lo = 1;  // E/n grows with n: the answer lies in [lo, hi)
+    if (above(lo)) return 1;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (above(mid)) hi = mid;
+        else lo = mid;
+    }
+    return lo;
 }
 
 inline int flags_to_status(int flags) {

@@ -93,6 +93,14 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
     int method = o.method == BMJ_COMBINED ? combined_method(sim, p, q) : o.method;
     stl.b = b;
     stl.method = method;
+    // cutoff point (Section 3.5): pairs whose larger set exceeds it skip Eq. 2
+    uint32_t cut = 0xffffffffu;
+    if (o.cutoff > 0) cut = (uint32_t)o.cutoff;
+    else if (o.cutoff == BMJ_CUTOFF_AUTO) {
+        const int64_t w = cutoff_point(b, method, sim, p, q);
+        if (w > 0) cut = (uint32_t)w;
+    }
+    stl.cutoff = cut == 0xffffffffu ? 0 : (int32_t)cut;
 
     Events ev;
     int st = ev.init();
@@ -287,6 +295,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
             fa.tile_item_off = tile_off;
             fa.tile_c0 = tile_c0;
             fa.tile_c1 = tile_c1;
+            fa.cut = cut;
             fa.n_tiles = n_tiles;
             fa.n_items = n_items;
             fa.tile_rows = tile_rows;
@@ -621,8 +630,9 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     if (o.row_begin < 0 || o.row_end < 0 || o.row_end < o.row_begin) return BMJ_ERR_INVALID_ARG;
     if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX) return BMJ_ERR_INVALID_ARG;
-    if (o.candidates == BMJ_CAND_PREFIX && (o.row_begin != 0 || o.row_end != 0))
+    if (o.candidates == BMJ_CAND_PREFIX && (o.row_begin != 0 || o.row_end != 0 || o.cutoff != 0))
         return BMJ_ERR_INVALID_ARG;
+    if (o.cutoff < BMJ_CUTOFF_AUTO) return BMJ_ERR_INVALID_ARG;
     if ((o.row_begin != 0 || o.row_end != 0) && o.row_end > coll->n_sets) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(coll, nullptr, sim, p, q, o, out, stats);
@@ -656,6 +666,7 @@ int bmj_rs_join(const bmj_collection *r, const bmj_collection *s, int sim, uint3
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     if (o.row_begin != 0 || o.row_end != 0) return BMJ_ERR_INVALID_ARG;
     if (o.candidates != BMJ_CAND_WINDOW) return BMJ_ERR_INVALID_ARG;
+    if (o.cutoff < BMJ_CUTOFF_AUTO) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(r, s, sim, p, q, o, out, stats);
     } catch (...) {

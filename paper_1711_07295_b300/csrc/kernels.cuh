@@ -93,6 +93,7 @@ struct FilterArgs {
     int fault_skip_copy = 0;  // fault injection: one warp skips one copy (the wait runs out)
     uint32_t p, q;
     int sim = BMJ_JACCARD;  // similarity function of the threshold p/q
+    uint32_t cut = 0xffffffffu;  // cutoff point (Section 3.5); all ones: none
     const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
     const int32_t *tile_c0;
     const int32_t *tile_c1 = nullptr;  // RS-join: end of each tile's columns (else the diagonal)

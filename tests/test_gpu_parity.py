@@ -110,6 +110,59 @@ def test_other_functions_combined_method_and_host_input(sim):
         check_join(off, tok, p, q, b=64, sim=sim, method=_bmj.BMJ_COMBINED, on_device=False)
 
 
+# ------------------------------------------------- cutoff point (Section 3.5)
+def _normalised(sim, p, q):
+    return 2 * p / (p + q) if sim == _bmj.BMJ_JACCARD else p / q
+
+
+@pytest.mark.parametrize("b", [64, 128, 256, 1024])
+def test_automatic_cutoff_is_the_oracles(b):
+    # the library's cutoff point from Eq. 4-6 equals the oracle's, for every method
+    # and several functions and thresholds (read from the stats of a two-set join)
+    from oracle import expected as E
+    off, tok = np.array([0, 2, 4], np.int64), np.array([1, 2, 1, 3], np.int32)
+    names = {_bmj.BMJ_SET: "set", _bmj.BMJ_XOR: "xor", _bmj.BMJ_NEXT: "next"}
+    for method, name in names.items():
+        for sim, p, q in ((_bmj.BMJ_JACCARD, 1, 2), (_bmj.BMJ_JACCARD, 3, 4),
+                          (_bmj.BMJ_JACCARD, 9, 10), (_bmj.BMJ_DICE, 7, 10),
+                          (_bmj.BMJ_COSINE, 3, 5)):
+            _, _, st = _bmj.bmj_self_join(off, tok, p, q, b=b, method=method, sim=sim,
+                                          cutoff=_bmj.BMJ_CUTOFF_AUTO)
+            assert st["cutoff"] == E.cutoff(b, _normalised(sim, p, q), name), (b, name, sim, p, q)
+    _, _, st = _bmj.bmj_self_join(off, tok, 2, 1, sim=_bmj.BMJ_OVERLAP, cutoff=_bmj.BMJ_CUTOFF_AUTO)
+    assert st["cutoff"] == 0      # Overlap thresholds are not normalised: no cutoff
+
+
+@pytest.mark.parametrize("b", [64, 128, 256, 192])
+@pytest.mark.parametrize("sim,p,q", [(_bmj.BMJ_JACCARD, 1, 2), (_bmj.BMJ_JACCARD, 3, 4),
+                                     (_bmj.BMJ_COSINE, 3, 5), (_bmj.BMJ_DICE, 7, 10)])
+def test_cutoff_point_parity(sim, p, q, b):
+    # pairs whose larger set is above the cutoff skip Eq. 2: same pairs, survivors as
+    # the oracle's counts with that cutoff (explicit values and the automatic one)
+    off, tok = I.random_collection(3001, 2500, 1, 120, seed=b + 3 * sim + q, zipf_s=0.9,
+                                   planted_frac=0.15)
+    ra, rb = O.self_join(off, tok, p, q, sim=sim)
+    base = None
+    for cut in (20, 75, _bmj.BMJ_CUTOFF_AUTO):
+        a, bb, st = gpu_join(off, tok, p, q, b=b, sim=sim, cutoff=cut)
+        assert np.array_equal(a, ra) and np.array_equal(bb, rb)
+        w = st["cutoff"]
+        assert w == cut or (cut == _bmj.BMJ_CUTOFF_AUTO and w > 0)
+        counts = O.filter_counts(off, tok, p, q, b, O.XOR, sim=sim, cutoff=w)
+        assert (st["window_pairs"], st["survivors"], st["results"]) == counts
+        if base is None:
+            base = O.filter_counts(off, tok, p, q, b, O.XOR, sim=sim)
+        assert st["survivors"] >= base[1]
+
+
+def test_cutoff_invalid_combinations():
+    off, tok = I.random_collection(200, 100, 1, 10, seed=3)
+    for kw in ({"cutoff": -2}, {"cutoff": 5, "candidates": _bmj.BMJ_CAND_PREFIX}):
+        with pytest.raises(_bmj.BmjError) as e:
+            _bmj.bmj_self_join(off, tok, 1, 2, **kw)
+        assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
+
+
 # ------------------------------------------------------ host/device paths
 def test_host_and_device_paths_agree():
     off, tok = I.random_collection(5000, 2000, 2, 40, seed=5, planted_frac=0.1)

@@ -127,6 +127,21 @@ def test_rs_join_queue_overflow_is_exact():
     assert st["survivors"] > 4096 and st["filter_passes"] >= 2
 
 
+@pytest.mark.parametrize("b", [64, 128])
+def test_rs_join_with_a_cutoff(b):
+    # pairs whose larger set exceeds the cutoff skip Eq. 2 (Section 3.5)
+    off, tok = I.random_collection(3000, 2000, 1, 100, seed=91 + b, planted_frac=0.2)
+    ro, rt, so, st_ = split(off, tok, 1300)
+    for cut in (30, _bmj.BMJ_CUTOFF_AUTO):
+        a, bb, st = _bmj.bmj_rs_join(*dev(ro, rt), *dev(so, st_), 1, 2, b=b, cutoff=cut)
+        wa, wb = O.rs_join(ro, rt, so, st_, 1, 2)
+        assert np.array_equal(a, wa) and np.array_equal(bb, wb)
+        w = st["cutoff"]
+        assert w > 0 and (w == cut or cut == _bmj.BMJ_CUTOFF_AUTO)
+        counts = O.rs_filter_counts(ro, rt, so, st_, 1, 2, b, O.XOR, cutoff=w)
+        assert (st["window_pairs"], st["survivors"], st["results"]) == counts
+
+
 def test_rs_join_invalid_arguments():
     off, tok = I.random_collection(100, 100, 1, 10, seed=81)
     ro, rt, so, st_ = split(off, tok, 50)
