@@ -264,7 +264,8 @@ int bmj_rs_join(const bmj_collection *r, const bmj_collection *s, int sim, uint3
  *             method per job; opt->use_graph runs the filter + verification
  *             stage as a CUDA graph; opt->cascade_b is 0 (jobs with b < 256 get
  *             the 256-bit check before merging, and the autotuner counts it),
- *             -1 (none) or 256.
+ *             -1 (none) or 256; row_begin, row_end, candidates and cutoff must
+ *             be 0 (BMJ_ERR_INVALID_ARG otherwise).
  *   outs      n_jobs pair lists (library-owned; free each with
  *             bmj_pairs_free), in job-local ids (0 = the job's first set),
  *             sorted and unique as for bmj_self_join

@@ -129,3 +129,34 @@ def test_batch_arguments_rejected_on_host():
     assert call([0, 1, 3], pp=np.array([1, 3, 1, 1], np.uint32)) == _bmj.BMJ_ERR_INVALID_ARG  # p > q
     assert call([0, 1, 3], b=100) == _bmj.BMJ_ERR_INVALID_ARG
     assert call([0, 1, 3], n_jobs=0) == _bmj.BMJ_ERR_INVALID_ARG
+    for kw in ({"cutoff": 5}, {"candidates": _bmj.BMJ_CAND_PREFIX}, {"row_end": 2}):
+        assert call([0, 1, 3], **kw) == _bmj.BMJ_ERR_INVALID_ARG   # single-join options
+
+
+def test_rs_join_arguments_rejected_on_host():
+    L = _bmj.lib()
+    off = np.array([0, 2, 4], np.int64)
+    tok = np.array([1, 2, 1, 3], np.int32)
+    r, keep_r = _bmj.make_collection(off, tok)
+    s, keep_s = _bmj.make_collection(off, tok)
+    pairs = _bmj.bmj_pairs()
+
+    def call(p=1, q=2, sim=0, rr=r, ss=s, **kw):
+        o = _bmj.bmj_default_options()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return L.bmj_rs_join(C.byref(rr) if rr is not None else None,
+                             C.byref(ss) if ss is not None else None, sim, p, q, C.byref(o),
+                             C.byref(pairs), None)
+    assert call(rr=None) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(ss=None) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(p=3, q=2) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(b=100) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(candidates=_bmj.BMJ_CAND_PREFIX) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(row_begin=0, row_end=1) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(cutoff=-2) == _bmj.BMJ_ERR_INVALID_ARG
+    big = _bmj.bmj_collection(1 << 30, off.ctypes.data_as(C.c_void_p), tok.ctypes.data_as(C.c_void_p), 0, 0)
+    assert call(rr=big, ss=big) == _bmj.BMJ_ERR_TOO_LARGE       # |R| + |S| >= 2^31
+    assert _join_status(off, tok, 1, 2, cutoff=-2) == _bmj.BMJ_ERR_INVALID_ARG
+    assert _join_status(off, tok, 1, 2, cutoff=3, candidates=_bmj.BMJ_CAND_PREFIX) == \
+        _bmj.BMJ_ERR_INVALID_ARG

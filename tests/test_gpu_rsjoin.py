@@ -80,6 +80,12 @@ def test_rs_join_host_and_device_inputs():
         check_rs(R, S, 3, 5, r_dev=r_dev, s_dev=s_dev)
     st = check_rs(R, S, 3, 5, output_on_device=False, cascade_b=-1)
     assert st["results"] > 0
+    # pairs left on the device
+    dp, _, _ = _bmj.bmj_rs_join(*dev(*R), *dev(*S), 3, 5, output_on_device=True)
+    wa, wb = O.rs_join(*R, *S, 3, 5)
+    assert np.array_equal(dp.a.cpu().numpy().view(np.uint32), wa)
+    assert np.array_equal(dp.b.cpu().numpy().view(np.uint32), wb)
+    dp.release()
 
 
 def test_rs_join_swapped_and_self():
