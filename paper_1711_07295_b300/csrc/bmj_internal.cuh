@@ -120,8 +120,11 @@ int radix_sort_u32_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint3
                          uint32_t *vals_out, int64_t n, int key_bits, Arena &arena,
                          cudaStream_t s);
 
-// LSD radix sort of 64-bit keys by their low `key_bits` bits.  The sorted
-// keys end in keys_out.
+// Stable LSD radix sorts of 32-bit and 64-bit keys by their low `key_bits`
+// bits rounded up to whole 8-bit digits (keys equal in those bits keep their
+// input order).  The sorted keys end in keys_out.
+int radix_sort_u32(const uint32_t *keys_in, uint32_t *keys_out, int64_t n, int key_bits,
+                   Arena &arena, cudaStream_t s);
 int radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, int64_t n, int key_bits,
                    Arena &arena, cudaStream_t s);
 

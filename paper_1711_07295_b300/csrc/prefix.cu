@@ -13,7 +13,10 @@
 // Steps (all on the device, in size order):
 //   rank the distinct tokens        sort the token occurrences, run lengths,
 //                                   sort (count, token index)
-//   order each set by rank          sort (set, rank) keys
+//   every set's prefix by rank      one thread per set selects it (sets of up
+//                                   to 32 tokens); one warp per set ranks its
+//                                   tokens by counting in shared memory (up to
+//                                   2048); a sort of (set, rank) keys beyond
 //   index the prefixes              sort (rank, set) entries of every prefix
 //   count and expand candidates     per index entry, the earlier sets of its
 //                                   rank's list inside the window; one thread
@@ -35,13 +38,20 @@ unsigned grid_p(int64_t n, int threads, int64_t cap = 148 * 32) {
     return (unsigned)g;
 }
 
+// Sets of up to kThreadSetMax tokens have their prefix selected by one thread,
+// sets of up to kWarpSetMax tokens by one warp in shared memory; larger ones
+// by a sort.
+constexpr int kThreadSetMax = 32;
+constexpr int kWarpSetMax = 2048;
+constexpr int kPrefWarps = 4;
+
 // Token values as sort keys, and their maximum (for the number of key bits).
-__global__ void k_tok_keys(const int32_t *__restrict__ tok, int64_t T, uint64_t *__restrict__ out,
+__global__ void k_tok_keys(const int32_t *__restrict__ tok, int64_t T, uint32_t *__restrict__ out,
                            unsigned int *__restrict__ max_tok) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned int m = 0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T; k += stride) {
-        out[k] = (uint64_t)(uint32_t)tok[k];
+        out[k] = (uint32_t)tok[k];
         m = max(m, (unsigned int)tok[k]);
     }
     m = __reduce_max_sync(kFullP, m);
@@ -49,42 +59,52 @@ __global__ void k_tok_keys(const int32_t *__restrict__ tok, int64_t T, uint64_t 
 }
 
 // 1 where a run of equal sorted tokens starts.
-__global__ void k_run_heads(const uint64_t *__restrict__ st, int64_t T, int64_t *__restrict__ flag) {
+__device__ __forceinline__ bool run_head(const uint32_t *st, int64_t k) {
+    return k == 0 || st[k] != st[k - 1];
+}
+
+__global__ void k_run_heads(const uint32_t *__restrict__ st, int64_t T, uint32_t *__restrict__ flag) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T; k += stride)
-        flag[k] = (k == 0 || st[k] != st[k - 1]) ? 1 : 0;
+        flag[k] = run_head(st, k) ? 1u : 0u;
+}
+
+// The number of runs, from the exclusive scan of the head flags (one thread).
+__global__ void k_run_total(const uint32_t *__restrict__ st, const uint32_t *__restrict__ pos,
+                            int64_t T, int64_t *__restrict__ total) {
+    total[0] = (int64_t)pos[T - 1] + (run_head(st, T - 1) ? 1 : 0);
 }
 
 // Distinct tokens (ascending) and the start of each run; pos is the exclusive
-// scan of the head flags, recomputed here from the flags.
-__global__ void k_run_write(const uint64_t *__restrict__ st, int64_t T,
-                            const int64_t *__restrict__ flag, const int64_t *__restrict__ pos,
-                            uint32_t *__restrict__ utok, int64_t *__restrict__ ustart) {
+// scan of the head flags.
+__global__ void k_run_write(const uint32_t *__restrict__ st, int64_t T,
+                            const uint32_t *__restrict__ pos, uint32_t *__restrict__ utok,
+                            int64_t *__restrict__ ustart) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < T; k += stride)
-        if (flag[k]) {
-            utok[pos[k]] = (uint32_t)st[k];
+        if (run_head(st, k)) {
+            utok[pos[k]] = st[k];
             ustart[pos[k]] = k;
         }
 }
 
-// (count << ubits) | distinct-token index: sorted, this is the rank order.
-// Keys pack their fields into as few bits as the sizes need, which saves
-// radix-sort passes (ubits = bits of a distinct-token index or rank, sbits =
-// bits of a set position).
-__global__ void k_rank_keys(const int64_t *__restrict__ ustart, int64_t nu, int ubits,
+// (distinct-token index << cshift) | count, in index order: a stable sort by
+// the count digits (the low cshift bits, a whole number of 8-bit radix digits)
+// leaves equal counts in index order, which is the rank order.  Keys pack their
+// fields into as few digits as the sizes need, and sorts touch only the digits
+// they order by, which saves radix-sort passes.
+__global__ void k_rank_keys(const int64_t *__restrict__ ustart, int64_t nu, int cshift,
                             uint64_t *__restrict__ key) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += stride)
-        key[u] = ((uint64_t)(ustart[u + 1] - ustart[u]) << ubits) | (uint64_t)u;
+        key[u] = ((uint64_t)u << cshift) | (uint64_t)(ustart[u + 1] - ustart[u]);
 }
 
-__global__ void k_rank_scatter(const uint64_t *__restrict__ skey, int64_t nu, int ubits,
+__global__ void k_rank_scatter(const uint64_t *__restrict__ skey, int64_t nu, int cshift,
                                uint32_t *__restrict__ rank_of) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t umask = (1ull << ubits) - 1;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nu; r += stride)
-        rank_of[skey[r] & umask] = (uint32_t)r;
+        rank_of[skey[r] >> cshift] = (uint32_t)r;
 }
 
 __device__ __forceinline__ int64_t lb_u32(const uint32_t *a, int64_t n, uint32_t v) {
@@ -97,8 +117,7 @@ __device__ __forceinline__ int64_t lb_u32(const uint32_t *a, int64_t n, uint32_t
     return lo;
 }
 
-// Rank of every token value, for token universes small enough to index
-// directly (rank_map[token]); larger ones search the distinct tokens instead.
+// rank_map[token] = rank, for token values small enough to index directly.
 __global__ void k_rank_map(const uint32_t *__restrict__ utok, const uint32_t *__restrict__ rank_of,
                            int64_t nu, uint32_t *__restrict__ rank_map) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -106,28 +125,124 @@ __global__ void k_rank_map(const uint32_t *__restrict__ utok, const uint32_t *__
         rank_map[utok[u]] = rank_of[u];
 }
 
-// (set << ubits) | rank for every token occurrence of the sorted CSR; one
-// thread per set (its keys are contiguous at soff[i]).
-__global__ void k_set_keys(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
-                           const int32_t *__restrict__ stok, int64_t n,
-                           const uint32_t *__restrict__ utok, int64_t nu,
-                           const uint32_t *__restrict__ rank_of,
-                           const uint32_t *__restrict__ rank_map, int ubits,
-                           uint64_t *__restrict__ keys) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t o = soff[i];
-        for (uint32_t k = 0; k < ssz[i]; k++) {
-            const uint32_t t = (uint32_t)stok[o + k];
-            const uint32_t r = rank_map ? rank_map[t] : rank_of[lb_u32(utok, nu, t)];
-            keys[o + k] = ((uint64_t)i << ubits) | r;
-        }
+// The rank of a token value: a direct map (token values below 2^26), else a
+// binary search of the distinct tokens.
+struct RankLookup {
+    const uint32_t *map;
+    const uint32_t *utok, *rank_of;
+    int64_t nu;
+    __device__ __forceinline__ uint32_t operator()(uint32_t t) const {
+        return map ? map[t] : rank_of[lb_u32(utok, nu, t)];
     }
-}
+};
 
 __device__ __forceinline__ int64_t prefix_len(uint32_t x, SimWindow win) {
     const uint64_t low = window_low(x, win);
     return low > x ? 0 : (int64_t)(x - low + 1);
+}
+
+// In size order: the first set with more than kThreadSetMax tokens, the first
+// with more than kWarpSetMax, and the position of the latter's first token
+// (one thread).
+__global__ void k_size_bounds(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
+                              int64_t n, int64_t ntok, int64_t *__restrict__ out) {
+    const uint32_t lim[2] = {(uint32_t)kThreadSetMax, (uint32_t)kWarpSetMax};
+    for (int k = 0; k < 2; k++) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t m = (lo + hi) >> 1;
+            if (ssz[m] <= lim[k]) lo = m + 1;
+            else hi = m;
+        }
+        out[k] = lo;
+        if (k == 1) out[2] = lo < n ? soff[lo] : ntok;
+    }
+}
+
+// The prefix of every set of at most kThreadSetMax tokens, in rank order: one
+// thread per set keeps its ranks in a local array and selects the smallest,
+// the next smallest, and so on, prefix-length times (ranks are distinct within
+// a set).
+__global__ void k_prefix_small(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
+                               const int32_t *__restrict__ stok, int64_t n1, SimWindow win,
+                               const int64_t *__restrict__ pofs, const RankLookup rl,
+                               uint32_t *__restrict__ pref) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride) {
+        const int x = (int)ssz[i];
+        const int L = (int)prefix_len((uint32_t)x, win);
+        if (L == 0) continue;
+        uint32_t r[kThreadSetMax];
+        const int64_t o = soff[i];
+        for (int e = 0; e < x; e++) r[e] = rl((uint32_t)stok[o + e]);
+        uint32_t *dst = pref + pofs[i];
+        int64_t prev = -1;
+        for (int k = 0; k < L; k++) {
+            uint32_t m = 0xffffffffu;
+            for (int e = 0; e < x; e++)
+                if ((int64_t)r[e] > prev && r[e] < m) m = r[e];
+            dst[k] = m;
+            prev = m;
+        }
+    }
+}
+
+// The prefix of every set of kThreadSetMax + 1 to kWarpSetMax tokens (sets
+// [n1, n2) in size order), in rank order: one warp per set loads its tokens' ranks into shared memory; a rank's position
+// in the set is the number of smaller ranks (ranks are distinct within a set),
+// and the positions below the prefix length are written to pref[pofs[i] ..].
+__global__ void __launch_bounds__(32 * kPrefWarps)
+    k_prefix_rank(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
+                  const int32_t *__restrict__ stok, int64_t n1, int64_t n2, SimWindow win,
+                  const int64_t *__restrict__ pofs, const RankLookup rl,
+                  uint32_t *__restrict__ pref) {
+    __shared__ uint32_t buf[kPrefWarps][kWarpSetMax];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t *b = buf[w];
+    const int64_t warps = (int64_t)gridDim.x * kPrefWarps;
+    for (int64_t i = n1 + (int64_t)blockIdx.x * kPrefWarps + w; i < n2; i += warps) {
+        const int x = (int)ssz[i];
+        const int L = (int)prefix_len((uint32_t)x, win);
+        if (L == 0) continue;  // warp-uniform
+        const int64_t o = soff[i];
+        for (int e = lane; e < x; e += 32) b[e] = rl((uint32_t)stok[o + e]);
+        __syncwarp();
+        uint32_t *dst = pref + pofs[i];
+        for (int e = lane; e < x; e += 32) {
+            const uint32_t re = b[e];
+            int c = 0;
+            for (int f = 0; f < x && c < L; f++) c += b[f] < re;
+            if (c < L) dst[c] = re;
+        }
+        __syncwarp();  // the buffer is reused for the next set
+    }
+}
+
+// (set - i0) << ubits | rank for the tokens of the sets [i0, n) (their tokens
+// are the suffix of the sorted CSR from soff[i0] = t0); one thread per set.
+__global__ void k_set_keys(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
+                           const int32_t *__restrict__ stok, int64_t i0, int64_t n, int64_t t0,
+                           const RankLookup rl, int ubits, uint64_t *__restrict__ keys) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t o = soff[i];
+        for (uint32_t k = 0; k < ssz[i]; k++)
+            keys[o - t0 + k] = ((uint64_t)(i - i0) << ubits) | rl((uint32_t)stok[o + k]);
+    }
+}
+
+// The prefixes of the sets [i0, n) from their (set, rank) keys sorted.
+__global__ void k_prefix_big(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
+                             const uint64_t *__restrict__ sorted, int64_t i0, int64_t n,
+                             int64_t t0, SimWindow win, const int64_t *__restrict__ pofs,
+                             int ubits, uint32_t *__restrict__ pref) {
+    const uint64_t umask = (1ull << ubits) - 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t len = prefix_len(ssz[i], win);
+        for (int64_t k = 0; k < len; k++)
+            pref[pofs[i] + k] = (uint32_t)(sorted[soff[i] - t0 + k] & umask);
+    }
 }
 
 __global__ void k_prefix_len(const uint32_t *__restrict__ ssz, int64_t n, SimWindow win,
@@ -137,41 +252,40 @@ __global__ void k_prefix_len(const uint32_t *__restrict__ ssz, int64_t n, SimWin
         plen[i] = prefix_len(ssz[i], win);
 }
 
-// (rank << sbits) | set for the prefix tokens of every set.
-__global__ void k_prefix_emit(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
-                              const uint64_t *__restrict__ srank, int64_t n, SimWindow win,
-                              const int64_t *__restrict__ pofs, int ubits, int sbits,
+// (set << rshift) | rank for the prefix tokens of every set, in set order; a
+// stable sort by the rank digits (the low rshift bits) then gives every rank's
+// list in size order.
+__global__ void k_prefix_emit(const uint32_t *__restrict__ ssz, const uint32_t *__restrict__ pref,
+                              int64_t n, SimWindow win, const int64_t *__restrict__ pofs, int rshift,
                               uint64_t *__restrict__ idx) {
-    const uint64_t umask = (1ull << ubits) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t len = prefix_len(ssz[i], win);
-        for (int64_t k = 0; k < len; k++)
-            idx[pofs[i] + k] = ((srank[soff[i] + k] & umask) << sbits) | (uint64_t)i;
+        const int64_t len = prefix_len(ssz[i], win), o = pofs[i];
+        for (int64_t k = 0; k < len; k++) idx[o + k] = ((uint64_t)i << rshift) | pref[o + k];
     }
 }
 
 // Per index entry k = (rank r, set i): the entries of r's list before k (earlier
 // sets in size order) whose size is inside i's window form [lo, k).
 __global__ void k_cand_count(const uint64_t *__restrict__ idx, int64_t P,
-                             const uint32_t *__restrict__ ssz, SimWindow win, int sbits,
+                             const uint32_t *__restrict__ ssz, SimWindow win, int rshift,
                              int64_t *__restrict__ lo_out, int64_t *__restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const uint64_t smask = (1ull << sbits) - 1;
+    const uint64_t umask = (1ull << rshift) - 1;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += stride) {
         const uint64_t key = idx[k];
-        const uint64_t head = key & ~smask;
+        const uint64_t r = key & umask;
         int64_t a = 0, b = k;  // first entry of the rank's list
         while (a < b) {
             const int64_t m = (a + b) >> 1;
-            if (idx[m] < head) a = m + 1;
+            if ((idx[m] & umask) < r) a = m + 1;
             else b = m;
         }
-        const uint64_t low = window_low(ssz[key & smask], win);
+        const uint64_t low = window_low(ssz[key >> rshift], win);
         b = k;  // first entry of the list with a size inside the window
         while (a < b) {
             const int64_t m = (a + b) >> 1;
-            if (ssz[idx[m] & smask] < low) a = m + 1;
+            if (ssz[idx[m] >> rshift] < low) a = m + 1;
             else b = m;
         }
         lo_out[k] = a;
@@ -181,16 +295,16 @@ __global__ void k_cand_count(const uint64_t *__restrict__ idx, int64_t P,
 
 // One candidate slot per thread: slot o belongs to entry k (cand_off[k] <= o <
 // cand_off[k+1]); the pair (i, j) is kept when no rank below the entry's is in
-// both prefixes (sorted ranks of a prefix: srank[soff[x] ..]).  Kept pairs are
+// both prefixes (sorted ranks of a prefix: pref[pofs[x] ..]).  Kept pairs are
 // appended with one atomicAdd per warp.
 __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                               const int64_t *__restrict__ cand_off, const int64_t *__restrict__ lo,
                               int64_t C, const uint32_t *__restrict__ ssz,
-                              const int64_t *__restrict__ soff, const uint64_t *__restrict__ srank,
-                              SimWindow win, int ubits, int sbits, uint2 *__restrict__ out,
+                              const int64_t *__restrict__ pofs, const uint32_t *__restrict__ pref,
+                              SimWindow win, int rshift, uint2 *__restrict__ out,
                               unsigned long long *__restrict__ count) {
     const int lane = threadIdx.x & 31;
-    const uint64_t umask = (1ull << ubits) - 1, smask = (1ull << sbits) - 1;
+    const uint64_t umask = (1ull << rshift) - 1;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (int64_t base = gw * 32; base < C; base += warps * 32) {
@@ -206,16 +320,16 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
             }
             const int64_t k = a;
             const uint64_t key = idx[k];
-            const uint32_t r = (uint32_t)(key >> sbits);
-            i = (uint32_t)(key & smask);
-            j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] & smask);
-            const uint64_t *pi = srank + soff[i];
-            const uint64_t *pj = srank + soff[j];
+            const uint32_t r = (uint32_t)(key & umask);
+            i = (uint32_t)(key >> rshift);
+            j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
+            const uint32_t *pi = pref + pofs[i];
+            const uint32_t *pj = pref + pofs[j];
             const int64_t ni = prefix_len(ssz[i], win), nj = prefix_len(ssz[j], win);
             int64_t x = 0, y = 0;
             keep = true;
             while (x < ni && y < nj) {
-                const uint32_t rx = (uint32_t)(pi[x] & umask), ry = (uint32_t)(pj[y] & umask);
+                const uint32_t rx = pi[x], ry = pj[y];
                 if (rx >= r || ry >= r) break;
                 if (rx == ry) {
                     keep = false;
@@ -245,28 +359,31 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     *n_slots = 0;
     if (n < 2 || ntok <= 0) return BMJ_OK;
     if (ntok >= ((int64_t)1 << 32)) return BMJ_ERR_TOO_LARGE;  // counts and ranks are 32-bit
-    const int nbits_set = std::max(1, bit_length((uint64_t)(n - 1)));
-    // ---- rank the distinct tokens ----
-    uint64_t *tk = nullptr, *st = nullptr;
-    int64_t *flag = nullptr, *pos = nullptr, *ustart = nullptr, *tot = nullptr;
+    // ---- rank the distinct tokens: (occurrences, token value), rarest first ----
+    // Sort the occurrences; run lengths give each distinct token's count; sort
+    // the (count, token index) pairs.
     unsigned int *max_tok = nullptr;
-    int rc = A.alloc(&tk, (size_t)ntok);
-    if (!rc) rc = A.alloc(&st, (size_t)ntok);
-    if (!rc) rc = A.alloc(&flag, (size_t)ntok);
-    if (!rc) rc = A.alloc(&pos, (size_t)ntok);
+    int64_t *tot = nullptr;
+    uint32_t *tk = nullptr, *st = nullptr;
+    uint32_t *pos = nullptr;
+    int64_t *ustart = nullptr;
+    int rc = A.alloc(&max_tok, 1);
     if (!rc) rc = A.alloc(&tot, 2);
-    if (!rc) rc = A.alloc(&max_tok, 1);
+    if (!rc) rc = A.alloc(&tk, (size_t)ntok);
+    if (!rc) rc = A.alloc(&st, (size_t)ntok);
+    if (!rc) rc = A.alloc(&pos, (size_t)ntok);
     if (rc) return rc;
     BMJ_CHECK(cudaMemsetAsync(max_tok, 0, sizeof(unsigned int), s));
     BMJ_LAUNCH(k_tok_keys, grid_p(ntok, 256), 256, 0, s, stok, ntok, tk, max_tok);
     unsigned int hmax = 0;
     BMJ_CHECK(cudaMemcpyAsync(&hmax, max_tok, sizeof(hmax), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
-    rc = radix_sort_u64(tk, st, ntok, std::max(1, bit_length((uint64_t)hmax)), A, s);
+    rc = radix_sort_u32(tk, st, ntok, std::max(1, bit_length((uint64_t)hmax)), A, s);
     if (rc) return rc;
-    BMJ_LAUNCH(k_run_heads, grid_p(ntok, 256), 256, 0, s, st, ntok, flag);
-    rc = exclusive_scan_i64(flag, pos, ntok, tot, A, s);
+    BMJ_LAUNCH(k_run_heads, grid_p(ntok, 256), 256, 0, s, st, ntok, pos);
+    rc = exclusive_scan_u32(pos, pos, ntok, A, s);  // (ntok < 2^32)
     if (rc) return rc;
+    BMJ_LAUNCH(k_run_total, 1, 1, 0, s, st, pos, ntok, tot);
     int64_t nu = 0;
     BMJ_CHECK(cudaMemcpyAsync(&nu, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
@@ -278,48 +395,77 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     if (!rc) rc = A.alloc(&rkey, (size_t)nu);
     if (!rc) rc = A.alloc(&rkey_s, (size_t)nu);
     if (rc) return rc;
-    BMJ_LAUNCH(k_run_write, grid_p(ntok, 256), 256, 0, s, st, ntok, flag, pos, utok, ustart);
+    BMJ_LAUNCH(k_run_write, grid_p(ntok, 256), 256, 0, s, st, ntok, pos, utok, ustart);
     BMJ_CHECK(cudaMemcpyAsync(ustart + nu, &ntok, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     const int ubits = std::max(1, bit_length((uint64_t)(nu - 1)));
-    const int cbits = std::max(1, bit_length((uint64_t)ntok));
-    BMJ_LAUNCH(k_rank_keys, grid_p(nu, 256), 256, 0, s, ustart, nu, ubits, rkey);
-    rc = radix_sort_u64(rkey, rkey_s, nu, cbits + ubits, A, s);
+    const int cbits = std::max(1, bit_length((uint64_t)n));  // a token occurs at most once per set
+    const int cshift = 8 * ((cbits + 7) / 8);  // the count in whole radix digits
+    BMJ_LAUNCH(k_rank_keys, grid_p(nu, 256), 256, 0, s, ustart, nu, cshift, rkey);
+    rc = radix_sort_u64(rkey, rkey_s, nu, cshift, A, s);  // by count; ties stay in token order
     if (rc) return rc;
-    BMJ_LAUNCH(k_rank_scatter, grid_p(nu, 256), 256, 0, s, rkey_s, nu, ubits, rank_of);
-    A.free_one(flag);
+    BMJ_LAUNCH(k_rank_scatter, grid_p(nu, 256), 256, 0, s, rkey_s, nu, cshift, rank_of);
+    A.free_one(tk);
+    A.free_one(st);
     A.free_one(pos);
     A.free_one(rkey);
     A.free_one(rkey_s);
-    // ---- order every set by rank ----
-    uint32_t *rank_map = nullptr;
+    RankLookup rl{nullptr, utok, rank_of, nu};
     if (hmax < (1u << 26)) {  // a direct map of at most 256 MB
+        uint32_t *rank_map = nullptr;
         rc = A.alloc(&rank_map, (size_t)hmax + 1);
         if (rc) return rc;
         BMJ_LAUNCH(k_rank_map, grid_p(nu, 256), 256, 0, s, utok, rank_of, nu, rank_map);
+        rl.map = rank_map;
     }
-    BMJ_LAUNCH(k_set_keys, grid_p(n, 256), 256, 0, s, ssz, soff, stok, n, utok, nu, rank_of,
-               rank_map, ubits, tk);
-    rc = radix_sort_u64(tk, st, ntok, ubits + nbits_set, A, s);  // st: (set, rank) in order
+    // ---- prefix lengths and offsets; where the set sizes cross the size classes ----
+    int64_t *pofs = nullptr, *bounds = nullptr;
+    rc = A.alloc(&pofs, (size_t)n);
+    if (!rc) rc = A.alloc(&bounds, 3);
     if (rc) return rc;
-    A.free_one(tk);
-    // ---- index the prefixes by rank ----
-    int64_t *plen = nullptr;
-    rc = A.alloc(&plen, (size_t)n);
+    BMJ_LAUNCH(k_prefix_len, grid_p(n, 256), 256, 0, s, ssz, n, win, pofs);
+    rc = exclusive_scan_i64(pofs, pofs, n, tot, A, s);  // pofs: the prefix offsets
     if (rc) return rc;
-    BMJ_LAUNCH(k_prefix_len, grid_p(n, 256), 256, 0, s, ssz, n, win, plen);
-    rc = exclusive_scan_i64(plen, plen, n, tot, A, s);  // plen becomes the prefix offsets
-    if (rc) return rc;
-    int64_t P = 0;
-    BMJ_CHECK(cudaMemcpyAsync(&P, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BMJ_LAUNCH(k_size_bounds, 1, 1, 0, s, ssz, soff, n, ntok, bounds);
+    int64_t hv[4] = {0, 0, 0, 0};  // P, first set above one thread, above one warp, its token
+    BMJ_CHECK(cudaMemcpyAsync(&hv[0], tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BMJ_CHECK(cudaMemcpyAsync(&hv[1], bounds, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
+    const int64_t P = hv[0], n1 = hv[1], n_small = hv[2], t0 = hv[3];
     if (P == 0) return BMJ_OK;
+    // ---- every set's prefix in rank order ----
+    uint32_t *pref = nullptr;
+    rc = A.alloc(&pref, (size_t)P);
+    if (rc) return rc;
+    if (n1 > 0)
+        BMJ_LAUNCH(k_prefix_small, grid_p(n1, 128, 148 * 64), 128, 0, s, ssz, soff, stok, n1, win,
+                   pofs, rl, pref);
+    if (n_small > n1)
+        BMJ_LAUNCH(k_prefix_rank, grid_p(n_small - n1, kPrefWarps, 148 * 16), 32 * kPrefWarps, 0, s,
+                   ssz, soff, stok, n1, n_small, win, pofs, rl, pref);
+    if (n_small < n) {  // sets of more than kWarpSetMax tokens: sort their (set, rank) keys
+        const int64_t tb = ntok - t0;
+        const int bbits = std::max(1, bit_length((uint64_t)(n - n_small - 1)));
+        uint64_t *bk = nullptr, *bs = nullptr;
+        rc = A.alloc(&bk, (size_t)tb);
+        if (!rc) rc = A.alloc(&bs, (size_t)tb);
+        if (rc) return rc;
+        BMJ_LAUNCH(k_set_keys, grid_p(n - n_small, 128), 128, 0, s, ssz, soff, stok, n_small, n, t0,
+                   rl, ubits, bk);
+        rc = radix_sort_u64(bk, bs, tb, ubits + bbits, A, s);
+        if (rc) return rc;
+        BMJ_LAUNCH(k_prefix_big, grid_p(n - n_small, 128), 128, 0, s, ssz, soff, bs, n_small, n, t0,
+                   win, pofs, ubits, pref);
+        A.free_one(bk);
+        A.free_one(bs);
+    }
+    // ---- index the prefixes by (rank, set) ----
     uint64_t *ix = nullptr, *idx = nullptr;
     rc = A.alloc(&ix, (size_t)P);
     if (!rc) rc = A.alloc(&idx, (size_t)P);
     if (rc) return rc;
-    BMJ_LAUNCH(k_prefix_emit, grid_p(n, 256), 256, 0, s, ssz, soff, st, n, win, plen, ubits,
-               nbits_set, ix);
-    rc = radix_sort_u64(ix, idx, P, ubits + nbits_set, A, s);
+    const int rshift = 8 * ((ubits + 7) / 8);  // the rank in whole radix digits
+    BMJ_LAUNCH(k_prefix_emit, grid_p(n, 256), 256, 0, s, ssz, pref, n, win, pofs, rshift, ix);
+    rc = radix_sort_u64(ix, idx, P, rshift, A, s);  // by rank; each list stays in size order
     if (rc) return rc;
     A.free_one(ix);
     // ---- count, then expand the candidates ----
@@ -327,7 +473,7 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     rc = A.alloc(&lo, (size_t)P);
     if (!rc) rc = A.alloc(&coff, (size_t)P + 1);
     if (rc) return rc;
-    BMJ_LAUNCH(k_cand_count, grid_p(P, 256), 256, 0, s, idx, P, ssz, win, nbits_set, lo, coff);
+    BMJ_LAUNCH(k_cand_count, grid_p(P, 256), 256, 0, s, idx, P, ssz, win, rshift, lo, coff);
     rc = exclusive_scan_i64(coff, coff, P, coff + P, A, s);
     if (rc) return rc;
     int64_t C = 0;
@@ -337,15 +483,15 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     if (C == 0) return BMJ_OK;
     if (max_cand > 0 && C > max_cand) return BMJ_ERR_OOM;  // more slots than the caller allows
     uint2 *out = nullptr;
-    unsigned long long *cnt = nullptr;
+    unsigned long long *cnt2 = nullptr;
     rc = A.alloc(&out, (size_t)C);
-    if (!rc) rc = A.alloc(&cnt, 1);
+    if (!rc) rc = A.alloc(&cnt2, 1);
     if (rc) return rc;
-    BMJ_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
-    BMJ_LAUNCH(k_cand_expand, grid_p(C, 256, 148 * 16), 256, 0, s, idx, P, coff, lo, C, ssz, soff,
-               st, win, ubits, nbits_set, out, cnt);
+    BMJ_CHECK(cudaMemsetAsync(cnt2, 0, sizeof(unsigned long long), s));
+    BMJ_LAUNCH(k_cand_expand, grid_p(C, 256, 148 * 16), 256, 0, s, idx, P, coff, lo, C, ssz, pofs,
+               pref, win, rshift, out, cnt2);
     unsigned long long nc = 0;
-    BMJ_CHECK(cudaMemcpyAsync(&nc, cnt, sizeof(nc), cudaMemcpyDeviceToHost, s));
+    BMJ_CHECK(cudaMemcpyAsync(&nc, cnt2, sizeof(nc), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
     *cand = out;
     *n_cand = (int64_t)nc;

@@ -243,6 +243,12 @@ int radix_sort_u32_pairs(const uint32_t *keys_in, const uint32_t *vals_in, uint3
                                                 arena, s);
 }
 
+int radix_sort_u32(const uint32_t *keys_in, uint32_t *keys_out, int64_t n, int key_bits,
+                   Arena &arena, cudaStream_t s) {
+    return radix_impl<uint32_t, uint32_t, false>(keys_in, nullptr, keys_out, nullptr, n, key_bits,
+                                                 arena, s);
+}
+
 int radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, int64_t n, int key_bits,
                    Arena &arena, cudaStream_t s) {
     return radix_impl<uint64_t, uint32_t, false>(keys_in, nullptr, keys_out, nullptr, n, key_bits,

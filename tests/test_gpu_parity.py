@@ -251,6 +251,29 @@ def test_identical_sets_and_threshold_one():
     assert np.array_equal(a, iu[0].astype(np.uint32)) and np.array_equal(b, iu[1].astype(np.uint32))
 
 
+def test_very_large_sets_among_small_ones():
+    # 2,000 small sets plus sets of up to 1,000,000 tokens (near-duplicate pairs among
+    # them): 32-bit overlap counts, long merges and saturated bitmaps in one join
+    rng = np.random.default_rng(77)
+    small_off, small_tok = I.random_collection(2000, 5000, 1, 30, seed=78)
+    h1 = np.sort(rng.choice(3_000_000, 1_000_000, replace=False))
+    keep = rng.random(len(h1)) > 0.05
+    h2 = np.sort(np.concatenate([h1[keep], 3_000_000 + rng.choice(100_000, 20_000, replace=False)]))
+    h3 = np.sort(rng.choice(3_000_000, 200_000, replace=False))
+    h4 = h3[rng.random(len(h3)) > 0.4]
+    h5 = np.arange(5000)
+    sets = [small_tok[small_off[i]:small_off[i + 1]] for i in range(len(small_off) - 1)]
+    for k, h in enumerate((h1, h2, h3, h4, h5)):
+        sets.insert(300 * k + 7, h.astype(np.int32))
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in sets])
+    tok = np.concatenate(sets).astype(np.int32)
+    for p, q in ((1, 2), (9, 10), (1, 1000)):
+        for b in (64, 256):
+            st = check_join(off, tok, p, q, b=b)
+            assert st["max_set_size"] == 1_000_000 and st["results"] > 0
+
+
 def test_singletons_and_low_threshold():
     off, tok = I.random_collection(2500, 40, 1, 1, seed=3)
     check_join(off, tok, 1, 1)
@@ -398,6 +421,30 @@ def test_prefix_filter_candidates(sim, p, q, b):
     assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r)
     w, _, _ = O.filter_counts(off, tok, p, q, b, O.XOR, sim=sim)
     assert st["window_pairs"] == w and c <= w
+
+
+@pytest.mark.parametrize("large_values", [False, True])
+def test_prefix_filter_large_sets_and_token_values(large_values):
+    # sets of 2,049 to 6,000 tokens among small ones (their prefixes are ordered by a
+    # sort instead of one warp each), and token values of up to 2^30 (ranked by a sort of
+    # the occurrences instead of a histogram): same candidates as the oracle
+    rng = np.random.default_rng(91 + large_values)
+    small_off, small_tok = I.random_collection(1500, 4000, 1, 40, seed=92, planted_frac=0.2)
+    sets = [small_tok[small_off[i]:small_off[i + 1]] for i in range(len(small_off) - 1)]
+    base = np.sort(rng.choice(20000, 6000, replace=False))
+    for k, x in enumerate((2049, 2300, 3000, 3100, 6000)):
+        sets.append(np.sort(rng.choice(base[:max(x + 200, 2400)], x, replace=False)))
+    if large_values:   # spread the token values up to 2^30, keeping every set sorted
+        sets = [(x.astype(np.int64) * 53687 + 7).astype(np.int32) for x in sets]
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in sets])
+    tok = np.concatenate(sets).astype(np.int32)
+    for p, q in ((4, 5), (1, 2)):
+        a, bb, st = gpu_join(off, tok, p, q, b=64, candidates=_bmj.BMJ_CAND_PREFIX)
+        ra, rb = O.self_join(off, tok, p, q)
+        assert np.array_equal(a, ra) and np.array_equal(bb, rb)
+        c, s, r = O.prefix_counts(off, tok, p, q, 64, O.XOR)
+        assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r) and r > 0
 
 
 def test_prefix_filter_on_the_million_set_workload(million):
