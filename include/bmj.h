@@ -109,20 +109,21 @@ typedef struct {
     int32_t output_on_device;  /* 1: pairs returned in device memory; 0 (default): host memory */
     int32_t validate;          /* 1 (default): check the collection invariants on the device */
     int64_t queue_cap;         /* survivor-queue capacity in pairs; 0 (default) = automatic.
-                                  bmj_self_join never drops a survivor: when they exceed the
-                                  queue, an automatic queue is regrown to the exact count if
-                                  that fits in a quarter of free memory; otherwise (and always
-                                  for a caller-given capacity) the filter's work items run in
-                                  consecutive ranges whose survivors fit, each verified before
-                                  the next (stats.filter_passes counts the passes) */
+                                  bmj_self_join and bmj_rs_join never drop a survivor: when
+                                  they exceed the queue, an automatic queue is regrown to the
+                                  exact count if that fits in a quarter of free memory;
+                                  otherwise (and always for a caller-given capacity) the
+                                  filter's work items run in consecutive ranges whose
+                                  survivors fit, each verified before the next
+                                  (stats.filter_passes counts the passes) */
     void   *stream;            /* cudaStream_t; NULL = legacy default stream */
     int32_t rows_per_thread;   /* filter register blocking: 0 = automatic */
     int32_t use_graph;         /* bmj_self_join_batch: run the execute stage as a CUDA graph */
-    int32_t cascade_b;         /* bmj_self_join: width of a second Bitmap Filter applied to the
-                                  survivors before merging (0 = automatic: 256 when b < 256;
-                                  -1 = none; otherwise a valid b larger than b) */
+    int32_t cascade_b;         /* bmj_self_join, bmj_rs_join: width of a second Bitmap Filter
+                                  applied to the survivors before merging (0 = automatic: 256
+                                  when b < 256; -1 = none; otherwise a valid b larger than b) */
     int32_t sim;               /* bmj_index_create: similarity function of every query on the
-                                  index (default BMJ_JACCARD); bmj_self_join and
+                                  index (default BMJ_JACCARD); bmj_self_join, bmj_rs_join and
                                   bmj_self_join_batch take it as an argument instead */
     int64_t row_begin;         /* bmj_self_join: join only the pairs whose later set in size order
                                   (sets ordered by size, ties by id) has its position in */
