@@ -212,8 +212,15 @@ struct BatchFilterArgs {
 template <int W>
 constexpr int kBatchAlu = W == 1 ? kAluRowsW1 : 0;
 
+// Resident 4-warp blocks per SM of the batched filter at b = 64: eight (64
+// registers, 8 bytes spilled) ran the 512-job execute stage in 248.2 ms against
+// 249.6 ms with seven.
+#ifndef BMJ_BATCH_W1_BLOCKS
+#define BMJ_BATCH_W1_BLOCKS 8
+#endif
+
 template <int W, int R, int CS, bool kCos>
-__global__ void __launch_bounds__(128, kCos ? 6 : 7) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
+__global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS : 7)) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
                                                          int64_t t1, unsigned long long *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
