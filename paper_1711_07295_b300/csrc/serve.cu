@@ -40,6 +40,7 @@ struct bmj_index {
     int32_t *stok = nullptr;
     uint64_t *bm = nullptr;   // (n + 4) * W
     std::vector<int64_t> size_cum;  // size_cum[s] = resident sets with size < s
+    int64_t *d_size_cum = nullptr;  // the same on the device (max_size + 2 entries)
 };
 
 namespace bmj {
@@ -50,35 +51,71 @@ constexpr int kQueryChunk = 1024;
 // Result keys copied back with a batch's counters (16 KB).
 constexpr int64_t kEagerKeys = 2048;
 
-__device__ __forceinline__ int64_t lb_sizes(const uint32_t *a, int64_t n, uint64_t v) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if ((uint64_t)a[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
+// First resident position with a size >= v: size_cum[v] = the resident sets
+// of size below v (max_size + 2 entries, the last equal to n).
+__device__ __forceinline__ int64_t lb_sizes(const int64_t *size_cum, int max_size, int64_t n,
+                                            uint64_t v) {
+    return v > (uint64_t)max_size ? n : size_cum[v];
 }
 
-// Per probe: its window [lo, hi) of resident sorted positions and its number
-// of column chunks.
+// Per probe x: its window [lo, hi) of resident sorted positions (Table 2, both
+// bounds) and its number of column chunks.
+__device__ __forceinline__ int64_t probe_window(const int64_t *poff, const uint32_t *pp,
+                                                const uint32_t *pq, const int64_t *size_cum,
+                                                int max_size, int64_t n, int sim, int64_t x,
+                                                int64_t *lo, int64_t *hi) {
+    const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
+    const SimWindow w = sim_window(sim, pp[x], pq[x]);
+    const uint64_t low = window_low(sx, w);     // e.g. Jaccard: ceil(p|x|/q)
+    const uint64_t high = window_high(sx, w);   // e.g. Jaccard: floor(q|x|/p); ~0: none
+    *lo = lb_sizes(size_cum, max_size, n, low);
+    *hi = high == ~0ull ? n : lb_sizes(size_cum, max_size, n, high + 1);
+    return *hi > *lo ? (*hi - *lo + kQueryChunk - 1) / kQueryChunk : 0;
+}
+
+// Per probe: its window and its number of column chunks (items[x]).
 __global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
                                 const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
-                                const uint32_t *__restrict__ ssz, int64_t n,
+                                const int64_t *__restrict__ size_cum, int max_size, int64_t n,
                                 int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
                                 int64_t *__restrict__ items, int sim) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nq; x += stride) {
-        const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
-        const SimWindow w = sim_window(sim, pp[x], pq[x]);
-        const uint64_t low = window_low(sx, w);     // e.g. Jaccard: ceil(p|x|/q)
-        const uint64_t high = window_high(sx, w);   // e.g. Jaccard: floor(q|x|/p); ~0: none
-        const int64_t lo = lb_sizes(ssz, n, low);
-        const int64_t hi = high == ~0ull ? n : lb_sizes(ssz, n, high + 1);
-        wlo[x] = lo;
-        whi[x] = hi;
-        items[x] = hi > lo ? (hi - lo + kQueryChunk - 1) / kQueryChunk : 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nq; x += stride)
+        items[x] = probe_window(poff, pp, pq, size_cum, max_size, n, sim, x, &wlo[x], &whi[x]);
+}
+
+// The same for a batch of at most kScanProbes probes in one block, with the
+// exclusive scan of the chunk counts (items[nq] = their total) done in place.
+constexpr int kScanProbes = 1024;
+__global__ void __launch_bounds__(kScanProbes)
+    k_probe_windows_scan(const int64_t *__restrict__ poff, int64_t nq,
+                         const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
+                         const int64_t *__restrict__ size_cum, int max_size, int64_t n,
+                         int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
+                         int64_t *__restrict__ items, int sim) {
+    __shared__ int64_t warp_sum[kScanProbes / 32];
+    const int x = threadIdx.x, lane = x & 31, w = x >> 5;
+    int64_t c = 0;
+    if (x < nq) c = probe_window(poff, pp, pq, size_cum, max_size, n, sim, x, &wlo[x], &whi[x]);
+    int64_t incl = c;  // inclusive scan within the warp
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t v = __shfl_up_sync(kFullQ, incl, d);
+        if (lane >= d) incl += v;
     }
+    if (lane == 31) warp_sum[w] = incl;
+    __syncthreads();
+    if (w == 0) {  // scan of the warp totals
+        int64_t t = lane < kScanProbes / 32 ? warp_sum[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t v = __shfl_up_sync(kFullQ, t, d);
+            if (lane >= d) t += v;
+        }
+        warp_sum[lane] = t;  // inclusive totals up to warp `lane`
+    }
+    __syncthreads();
+    const int64_t excl = incl - c + (w > 0 ? warp_sum[w - 1] : 0);
+    if (x < nq) items[x] = excl;
+    if (x == 0) items[nq] = warp_sum[kScanProbes / 32 - 1];
 }
 
 // One warp per work item (probe, chunk of columns); lanes take consecutive
@@ -313,11 +350,16 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     int rc = launch_gather_build(nullptr, s.d_off, s.d_tok, nullptr, nullptr, s.d_pbm, nq, idx->b,
                                  idx->method, st);
     if (rc) return rc;
-    BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q, idx->ssz,
-               idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim);
     Arena A(st);
-    rc = exclusive_scan_i64(s.d_items, s.d_items, nq, s.d_items + nq, A, st);
-    if (rc) return rc;
+    if (nq <= kScanProbes) {  // windows and their scan in one launch
+        BMJ_LAUNCH(k_probe_windows_scan, 1, kScanProbes, 0, st, s.d_off, nq, s.d_p, s.d_q,
+                   idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim);
+    } else {
+        BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q,
+                   idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim);
+        rc = exclusive_scan_i64(s.d_items, s.d_items, nq, s.d_items + nq, A, st);
+        if (rc) return rc;
+    }
     BMJ_LAUNCH(k_query_filter, (unsigned)(sms * 8), 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
                s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],
                s.pair_cap, idx->sim);
@@ -468,6 +510,16 @@ extern "C" int bmj_index_create(const bmj_collection *coll, const bmj_options *o
                 idx->size_cum.assign(2, 0);
                 cudaMemsetAsync(idx->soff, 0, sizeof(int64_t), s);
             }
+            if (!st) {  // the window lookup table on the device
+                const size_t bytes = idx->size_cum.size() * sizeof(int64_t);
+                if (cudaMalloc(&idx->d_size_cum, bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    st = BMJ_ERR_OOM;
+                } else if (cudaMemcpyAsync(idx->d_size_cum, idx->size_cum.data(), bytes,
+                                           cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                    st = BMJ_ERR_CUDA;
+                }
+            }
         }
         A.release();
         if (cudaStreamSynchronize(s) != cudaSuccess && !st) st = BMJ_ERR_CUDA;
@@ -488,6 +540,7 @@ extern "C" void bmj_index_destroy(bmj_index *idx) {
     cudaFree(idx->soff);
     cudaFree(idx->stok);
     cudaFree(idx->bm);
+    cudaFree(idx->d_size_cum);
     cudaGetLastError();
     delete idx;
 }
