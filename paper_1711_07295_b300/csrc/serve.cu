@@ -259,6 +259,7 @@ struct Slot {
     unsigned long long *d_ctr = nullptr;
     // in flight
     int phase = 0;  // 0 free, 1 filter+verify running, 2 sort+copy running
+    int64_t win = 0;  // window pairs of the batch (exact, from the host size histogram)
     std::vector<int64_t> ids;  // query ids of the batch
     int64_t nq = 0, ntok = 0;
 };
@@ -360,10 +361,17 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
         rc = exclusive_scan_i64(s.d_items, s.d_items, nq, s.d_items + nq, A, st);
         if (rc) return rc;
     }
-    BMJ_LAUNCH(k_query_filter, (unsigned)(sms * 8), 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
+    // grids no larger than the batch's work: a probe's window of w sets is
+    // ceil(w / kQueryChunk) work items, and every survivor is a window pair
+    const int64_t items_ub = s.win / kQueryChunk + nq;
+    const unsigned fblocks =
+        (unsigned)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, (items_ub + 7) / 8));
+    const unsigned vblocks =
+        (unsigned)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (s.win + 255) / 256));
+    BMJ_LAUNCH(k_query_filter, fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
                s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],
                s.pair_cap, idx->sim);
-    BMJ_LAUNCH(k_query_verify, (unsigned)(sms * 4), 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
+    BMJ_LAUNCH(k_query_verify, vblocks, 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
                s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
                &s.d_ctr[1], idx->sim);
     BMJ_CHECK(cudaMemcpyAsync(s.h_ctr, s.d_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -677,6 +685,7 @@ static int serve_impl(bmj_index *idx, const bmj_collection *qc, const double *ar
                 pend_head++;
             }
             stage(s, qc, p, q, take.data(), (int64_t)take.size());
+            s.win = w;
             total_window += w;
             rc = launch_phase1(idx, s, sms);
             if (rc) break;
@@ -685,12 +694,15 @@ static int serve_impl(bmj_index *idx, const bmj_collection *qc, const double *ar
             progressed = true;
         }
         if (!progressed) {
-            if (pend_head >= pending.size() && next < Q && arrival_s) {
-                const double wait = arrival_s[next] - now_s();
-                if (wait > 50e-6) std::this_thread::sleep_for(std::chrono::microseconds(20));
-            } else {
+            // sleep only through long gaps (the wake-up can come tens of
+            // microseconds late); otherwise keep polling arrivals and events
+            const double wait = (pend_head >= pending.size() && next < Q && arrival_s)
+                                    ? arrival_s[next] - now_s()
+                                    : 0.0;
+            if (wait > 1e-3)
+                std::this_thread::sleep_for(std::chrono::microseconds((int64_t)((wait - 5e-4) * 1e6)));
+            else
                 std::this_thread::yield();
-            }
         }
     }
     const double wall = now_s();
