@@ -47,7 +47,11 @@ namespace bmj {
 namespace {
 
 constexpr unsigned kFullQ = 0xffffffffu;
+// Columns per work item of the query filter: kQueryChunk, halved down to
+// kQueryChunkMin while a batch has fewer items than the GPU has warp slots
+// (a single probe's window then spreads over many warps).
 constexpr int kQueryChunk = 1024;
+constexpr int kQueryChunkMin = 64;
 // Result keys copied back with a batch's counters (16 KB).
 constexpr int64_t kEagerKeys = 2048;
 
@@ -62,15 +66,15 @@ __device__ __forceinline__ int64_t lb_sizes(const int64_t *size_cum, int max_siz
 // bounds) and its number of column chunks.
 __device__ __forceinline__ int64_t probe_window(const int64_t *poff, const uint32_t *pp,
                                                 const uint32_t *pq, const int64_t *size_cum,
-                                                int max_size, int64_t n, int sim, int64_t x,
-                                                int64_t *lo, int64_t *hi) {
+                                                int max_size, int64_t n, int sim, int chunk,
+                                                int64_t x, int64_t *lo, int64_t *hi) {
     const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
     const SimWindow w = sim_window(sim, pp[x], pq[x]);
     const uint64_t low = window_low(sx, w);     // e.g. Jaccard: ceil(p|x|/q)
     const uint64_t high = window_high(sx, w);   // e.g. Jaccard: floor(q|x|/p); ~0: none
     *lo = lb_sizes(size_cum, max_size, n, low);
     *hi = high == ~0ull ? n : lb_sizes(size_cum, max_size, n, high + 1);
-    return *hi > *lo ? (*hi - *lo + kQueryChunk - 1) / kQueryChunk : 0;
+    return *hi > *lo ? (*hi - *lo + chunk - 1) / chunk : 0;
 }
 
 // Per probe: its window and its number of column chunks (items[x]).
@@ -78,10 +82,11 @@ __global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
                                 const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
                                 const int64_t *__restrict__ size_cum, int max_size, int64_t n,
                                 int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
-                                int64_t *__restrict__ items, int sim) {
+                                int64_t *__restrict__ items, int sim, int chunk) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nq; x += stride)
-        items[x] = probe_window(poff, pp, pq, size_cum, max_size, n, sim, x, &wlo[x], &whi[x]);
+        items[x] = probe_window(poff, pp, pq, size_cum, max_size, n, sim, chunk, x, &wlo[x],
+                                &whi[x]);
 }
 
 // The same for a batch of at most kScanProbes probes in one block, with the
@@ -92,11 +97,12 @@ __global__ void __launch_bounds__(kScanProbes)
                          const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
                          const int64_t *__restrict__ size_cum, int max_size, int64_t n,
                          int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
-                         int64_t *__restrict__ items, int sim) {
+                         int64_t *__restrict__ items, int sim, int chunk) {
     __shared__ int64_t warp_sum[kScanProbes / 32];
     const int x = threadIdx.x, lane = x & 31, w = x >> 5;
     int64_t c = 0;
-    if (x < nq) c = probe_window(poff, pp, pq, size_cum, max_size, n, sim, x, &wlo[x], &whi[x]);
+    if (x < nq)
+        c = probe_window(poff, pp, pq, size_cum, max_size, n, sim, chunk, x, &wlo[x], &whi[x]);
     int64_t incl = c;  // inclusive scan within the warp
     for (int d = 1; d < 32; d <<= 1) {
         const int64_t v = __shfl_up_sync(kFullQ, incl, d);
@@ -127,7 +133,7 @@ __global__ void __launch_bounds__(256)
                    const int64_t *__restrict__ item_off, int64_t nq,
                    const uint64_t *__restrict__ bm, const uint32_t *__restrict__ ssz, int W,
                    uint2 *__restrict__ queue, unsigned long long *__restrict__ qcount, int64_t qcap,
-                   int sim) {
+                   int sim, int chunk) {
     const int lane = threadIdx.x & 31;
     const int64_t n_items = item_off[nq];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -140,8 +146,8 @@ __global__ void __launch_bounds__(256)
             else hi = mid;
         }
         const int64_t x = lo;
-        const int64_t c0 = wlo[x] + (item - item_off[x]) * kQueryChunk;
-        const int64_t c1 = min(c0 + (int64_t)kQueryChunk, whi[x]);
+        const int64_t c0 = wlo[x] + (item - item_off[x]) * chunk;
+        const int64_t c1 = min(c0 + (int64_t)chunk, whi[x]);
         const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
         const uint32_t p = pp[x], q = pq[x];
         for (int64_t j0 = c0; j0 < c1; j0 += 32) {
@@ -352,25 +358,29 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
                                  idx->method, st);
     if (rc) return rc;
     Arena A(st);
+    int chunk = kQueryChunk;
+    while (chunk > kQueryChunkMin && s.win / chunk < (int64_t)sms * 32) chunk >>= 1;
     if (nq <= kScanProbes) {  // windows and their scan in one launch
         BMJ_LAUNCH(k_probe_windows_scan, 1, kScanProbes, 0, st, s.d_off, nq, s.d_p, s.d_q,
-                   idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim);
+                   idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim,
+                   chunk);
     } else {
         BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q,
-                   idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim);
+                   idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim,
+                   chunk);
         rc = exclusive_scan_i64(s.d_items, s.d_items, nq, s.d_items + nq, A, st);
         if (rc) return rc;
     }
     // grids no larger than the batch's work: a probe's window of w sets is
-    // ceil(w / kQueryChunk) work items, and every survivor is a window pair
-    const int64_t items_ub = s.win / kQueryChunk + nq;
+    // ceil(w / chunk) work items, and every survivor is a window pair
+    const int64_t items_ub = s.win / chunk + nq;
     const unsigned fblocks =
         (unsigned)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, (items_ub + 7) / 8));
     const unsigned vblocks =
         (unsigned)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (s.win + 255) / 256));
     BMJ_LAUNCH(k_query_filter, fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
                s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],
-               s.pair_cap, idx->sim);
+               s.pair_cap, idx->sim, chunk);
     BMJ_LAUNCH(k_query_verify, vblocks, 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
                s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
                &s.d_ctr[1], idx->sim);
