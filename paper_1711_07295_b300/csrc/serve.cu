@@ -126,6 +126,11 @@ __global__ void __launch_bounds__(kScanProbes)
 
 // One warp per work item (probe, chunk of columns); lanes take consecutive
 // columns.  Survive iff floor((S - h)/2) * (p+q) >= p * S (Eq. 2, Table 1).
+// kW > 0: the probe's bitmap of kW words stays in registers and every lane
+// takes four columns per step, their loads issued together; kW = 0: any width,
+// one column per lane and step.  A lane recomputes the smallest passing overlap
+// only when its column's size changes (sizes ascend along the window).
+template <int kW>
 __global__ void __launch_bounds__(256)
     k_query_filter(const uint64_t *__restrict__ pbm, const int64_t *__restrict__ poff,
                    const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
@@ -134,6 +139,7 @@ __global__ void __launch_bounds__(256)
                    const uint64_t *__restrict__ bm, const uint32_t *__restrict__ ssz, int W,
                    uint2 *__restrict__ queue, unsigned long long *__restrict__ qcount, int64_t qcap,
                    int sim, int chunk) {
+    constexpr int U = kW > 0 ? 4 : 1;  // columns per lane and step
     const int lane = threadIdx.x & 31;
     const int64_t n_items = item_off[nq];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -150,24 +156,50 @@ __global__ void __launch_bounds__(256)
         const int64_t c1 = min(c0 + (int64_t)chunk, whi[x]);
         const uint64_t sx = (uint64_t)(poff[x + 1] - poff[x]);
         const uint32_t p = pp[x], q = pq[x];
-        for (int64_t j0 = c0; j0 < c1; j0 += 32) {
-            const int64_t j = j0 + lane;
-            bool sv = false;
-            if (j < c1) {
-                int h = 0;
-                for (int w = 0; w < W; w++) h += __popcll(pbm[x * W + w] ^ bm[j * W + w]);
-                const uint64_t S = sx + ssz[j];
-                const int64_t ub = (int64_t)((S - (uint64_t)h) >> 1);   // Eq. 2
-                sv = ub >= sim_need(sim, p, q, (int64_t)sx, (int64_t)ssz[j]);
+        uint64_t pb[kW > 0 ? kW : 1];
+#pragma unroll
+        for (int w = 0; w < kW; w++) pb[w] = pbm[x * kW + w];
+        uint32_t last_s = 0xffffffffu;
+        int64_t last_need = 0;
+        for (int64_t j0 = c0; j0 < c1; j0 += 32 * U) {
+            uint32_t cs[U];
+            uint64_t cb[U][kW > 0 ? kW : 1];
+#pragma unroll
+            for (int u = 0; u < U; u++) {  // all loads of the step first
+                const int64_t j = j0 + u * 32 + lane;
+                cs[u] = j < c1 ? ssz[j] : 0u;
+#pragma unroll
+                for (int w = 0; w < kW; w++) cb[u][w] = j < c1 ? bm[j * kW + w] : 0ull;
             }
-            const unsigned ball = __ballot_sync(kFullQ, sv);
-            if (ball) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(qcount, (unsigned long long)__popc(ball));
-                base = __shfl_sync(kFullQ, base, 0);
-                const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
-                if (sv && pos < (unsigned long long)qcap)
-                    queue[pos] = make_uint2((uint32_t)x, (uint32_t)j);
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t j = j0 + u * 32 + lane;
+                bool sv = false;
+                if (j < c1) {
+                    int h = 0;
+                    if (kW > 0) {
+#pragma unroll
+                        for (int w = 0; w < kW; w++) h += __popcll(pb[w] ^ cb[u][w]);
+                    } else {
+                        for (int w = 0; w < W; w++) h += __popcll(pbm[x * W + w] ^ bm[j * W + w]);
+                    }
+                    if (cs[u] != last_s) {
+                        last_s = cs[u];
+                        last_need = sim_need(sim, p, q, (int64_t)sx, (int64_t)cs[u]);
+                    }
+                    const uint64_t S = sx + cs[u];
+                    const int64_t ub = (int64_t)((S - (uint64_t)h) >> 1);   // Eq. 2
+                    sv = ub >= last_need;
+                }
+                const unsigned ball = __ballot_sync(kFullQ, sv);
+                if (ball) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(qcount, (unsigned long long)__popc(ball));
+                    base = __shfl_sync(kFullQ, base, 0);
+                    const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
+                    if (sv && pos < (unsigned long long)qcap)
+                        queue[pos] = make_uint2((uint32_t)x, (uint32_t)j);
+                }
             }
         }
     }
@@ -378,9 +410,17 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
         (unsigned)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, (items_ub + 7) / 8));
     const unsigned vblocks =
         (unsigned)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (s.win + 255) / 256));
-    BMJ_LAUNCH(k_query_filter, fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,
-               s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],
-               s.pair_cap, idx->sim, chunk);
+#define BMJ_QUERY_FILTER(KW)                                                                  \
+    BMJ_LAUNCH(k_query_filter<KW>, fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q, s.d_lo,   \
+               s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],          \
+               s.pair_cap, idx->sim, chunk)
+    switch (idx->W) {
+        case 1: BMJ_QUERY_FILTER(1); break;
+        case 2: BMJ_QUERY_FILTER(2); break;
+        case 4: BMJ_QUERY_FILTER(4); break;
+        default: BMJ_QUERY_FILTER(0); break;
+    }
+#undef BMJ_QUERY_FILTER
     BMJ_LAUNCH(k_query_verify, vblocks, 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
                s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
                &s.d_ctr[1], idx->sim);
