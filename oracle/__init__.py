@@ -30,6 +30,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
       quotes (55 at b = 64; Set 2129 and the Xor/Set ratios 2.3 and 1.47 at
       b = 1024) and Alg. 4's switch points 0.56 / 0.73; the paper's Xor figure
       4983 does not follow from its own Eq. 5: parity unpinned for it.
+  rs_prefix_counts -- candidates by the definition over Python sets (ranks by
+      frequency over R and S), results equal to the RS-join's.
   filter_counts / rs_filter_counts with a cutoff -- against the counts
       without one: the window and the results are unchanged, the survivors
       grow by exactly the bound-rejected pairs whose larger set is above it.
@@ -97,6 +99,9 @@ def lib():
         L.oracle_rs_filter_counts.argtypes = [i64, i64p, i32p, i64, i64p, i32p, C.c_int, i64, i64,
                                               C.c_int, C.c_int, i64, i64p]
         L.oracle_rs_filter_counts.restype = None
+        L.oracle_rs_prefix_counts.argtypes = [i64, i64p, i32p, i64, i64p, i32p, C.c_int, i64, i64,
+                                              C.c_int, C.c_int, i64p]
+        L.oracle_rs_prefix_counts.restype = None
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         L.oracle_free.argtypes = [C.c_void_p]
@@ -183,6 +188,19 @@ def rs_filter_counts(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b
     lib().oracle_rs_filter_counts(len(ro) - 1, _p(ro, C.c_int64), _p(rt, C.c_int32), len(so) - 1,
                                   _p(so, C.c_int64), _p(st, C.c_int32), sim, p, q, b, method,
                                   cutoff, _p(cnt, C.c_int64))
+    if cnt[0] < 0:
+        raise MemoryError("oracle allocation failed")
+    return int(cnt[0]), int(cnt[1]), int(cnt[2])
+
+
+def rs_prefix_counts(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int,
+                     method: int, sim: int = JACCARD):
+    """(candidates, survivors, results) of an RS-join with prefix-filter candidates."""
+    ro, rt, so, st = _i64(r_offsets), _i32(r_tokens), _i64(s_offsets), _i32(s_tokens)
+    cnt = np.zeros(3, np.int64)
+    lib().oracle_rs_prefix_counts(len(ro) - 1, _p(ro, C.c_int64), _p(rt, C.c_int32), len(so) - 1,
+                                  _p(so, C.c_int64), _p(st, C.c_int32), sim, p, q, b, method,
+                                  _p(cnt, C.c_int64))
     if cnt[0] < 0:
         raise MemoryError("oracle allocation failed")
     return int(cnt[0]), int(cnt[1]), int(cnt[2])
@@ -281,6 +299,7 @@ def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int
 
 __all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "JACCARD", "COSINE", "DICE", "OVERLAP",
            "overlap", "similar", "similar_sim", "in_window", "self_join",
-           "join_rows", "join_rows_window", "rs_join", "rs_filter_counts", "search", "bitmap",
+           "join_rows", "join_rows_window", "rs_join", "rs_filter_counts", "rs_prefix_counts",
+           "search", "bitmap",
            "bitmaps", "hamming", "upper_bound",
            "filter_counts", "prefix_counts", "combined_method", "num_threads", "lib"]

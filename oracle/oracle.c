@@ -41,6 +41,8 @@
  *   oracle_rs_filter_counts  window pairs, Bitmap Filter survivors and
  *                         results of an RS-join (length window of Table 2,
  *                         Eq. 2), counted over every pair of R x S
+ *   oracle_rs_prefix_counts  the same with the prefix filter choosing the
+ *                         candidates among the window pairs of R x S
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -766,4 +768,114 @@ void oracle_rs_filter_counts(int64_t nr, const int64_t *offr, const int32_t *tok
     counts[1] = surv;
     counts[2] = res;
     free(bmr); free(bms);
+}
+
+/*
+ * The prefix filter (Section 2.2) for an RS-join: tokens are ranked by their
+ * frequency over R and S together (rarest first, ties by token id); every set
+ * of R and of S keeps its x - low(x) + 1 lowest-ranked tokens as its prefix,
+ * low(x) being the smallest partner size inside the length window (the
+ * smallest overlap a similar partner can have, whichever collection it is
+ * in).  A pair (r, s) of the window is a candidate when the two prefixes share
+ * a rank.  counts[0] = candidates, counts[1] = candidates passing Eq. 2 with
+ * the b-bit bitmaps of `method`, counts[2] = results among them (-1 on
+ * allocation failure).
+ */
+void oracle_rs_prefix_counts(int64_t nr, const int64_t *offr, const int32_t *tokr, int64_t ns,
+                             const int64_t *offs, const int32_t *toks, int sim, int64_t p,
+                             int64_t q, int b, int method, int64_t *counts)
+{
+    counts[0] = counts[1] = counts[2] = 0;
+    if (nr <= 0 || ns <= 0) return;
+    if (method == OR_COMBINED) method = oracle_combined_method_sim(sim, p, q);
+    const int64_t n = nr + ns, tr = offr[nr], ntok = offr[nr] + offs[ns];
+    const int W = b / 64;
+    /* R and S as one list of sets: set x < nr is r_x, set nr + y is s_y */
+    int64_t *off = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int32_t *tok = (int32_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int32_t));
+    int64_t *all = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *ukey = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *utok = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *rank_of = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    int64_t *poff = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)(ntok > 0 ? ntok : 1) * sizeof(int64_t));
+    uint64_t *bm = (uint64_t *)malloc((size_t)n * (size_t)W * sizeof(uint64_t));
+    int64_t *pre = NULL;
+    int64_t nu = 0;
+    if (off && tok && all && ukey && utok && rank_of && poff && tmp && bm) {
+        for (int64_t x = 0; x <= nr; x++) off[x] = offr[x];
+        for (int64_t y = 1; y <= ns; y++) off[nr + y] = tr + offs[y];
+        memcpy(tok, tokr, (size_t)tr * sizeof(int32_t));
+        memcpy(tok + tr, toks, (size_t)offs[ns] * sizeof(int32_t));
+        /* global token order: distinct tokens with their counts, sorted by (count, token) */
+        for (int64_t k = 0; k < ntok; k++) all[k] = tok[k];
+        qsort(all, (size_t)ntok, sizeof(int64_t), cmp_i64);
+        for (int64_t k = 0; k < ntok;) {
+            int64_t e = k;
+            while (e < ntok && all[e] == all[k]) e++;
+            utok[nu] = all[k];                   /* ascending token ids */
+            ukey[nu] = ((e - k) << 32) | nu;     /* (count, index into utok) */
+            nu++;
+            k = e;
+        }
+        qsort(ukey, (size_t)nu, sizeof(int64_t), cmp_i64);
+        for (int64_t r = 0; r < nu; r++) rank_of[ukey[r] & 0xffffffff] = r;
+        /* prefix lengths x - low(x) + 1 and the bitmaps */
+        poff[0] = 0;
+        for (int64_t x = 0; x < n; x++) {
+            const int64_t sx = off[x + 1] - off[x];
+            int64_t low = 1;
+            while (low <= sx && !oracle_in_window(sim, low, sx, p, q)) low++;
+            poff[x + 1] = poff[x] + (sx - low + 1 > 0 ? sx - low + 1 : 0);
+            oracle_bitmap(tok + off[x], sx, b, method, bm + x * W);
+        }
+        pre = (int64_t *)malloc((size_t)(poff[n] > 0 ? poff[n] : 1) * sizeof(int64_t));
+    }
+    if (!pre) {
+        counts[0] = counts[1] = counts[2] = -1;
+    } else {
+        /* each set's prefix: the ranks of its tokens, sorted, first poff[x+1]-poff[x] */
+        for (int64_t x = 0; x < n; x++) {
+            const int64_t sx = off[x + 1] - off[x];
+            for (int64_t k = 0; k < sx; k++) {
+                int64_t lo = 0, hi = nu - 1;   /* the token among the ascending distinct ones */
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) / 2;
+                    if (utok[mid] < tok[off[x] + k]) lo = mid + 1; else hi = mid;
+                }
+                tmp[k] = rank_of[lo];
+            }
+            qsort(tmp, (size_t)sx, sizeof(int64_t), cmp_i64);
+            for (int64_t k = 0; k < poff[x + 1] - poff[x]; k++) pre[poff[x] + k] = tmp[k];
+        }
+        int64_t cand = 0, surv = 0, res = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : cand, surv, res)
+        for (int64_t r = 0; r < nr; r++) {
+            const int64_t lr = off[r + 1] - off[r];
+            for (int64_t y = 0; y < ns; y++) {
+                const int64_t t = nr + y, lt = off[t + 1] - off[t];
+                const int64_t mn = lr < lt ? lr : lt, mx = lr < lt ? lt : lr;
+                if (!oracle_in_window(sim, mn, mx, p, q)) continue;
+                /* do the two sorted prefixes share a rank? */
+                int64_t a = poff[r], ae = poff[r + 1], c = poff[t], ce = poff[t + 1];
+                int share = 0;
+                while (a < ae && c < ce) {
+                    if (pre[a] == pre[c]) { share = 1; break; }
+                    if (pre[a] < pre[c]) a++; else c++;
+                }
+                if (!share) continue;
+                cand++;
+                int64_t h = oracle_hamming(bm + r * W, bm + t * W, b);
+                if (!oracle_similar_sim(sim, oracle_upper_bound(lr, lt, h), lr, lt, p, q)) continue;
+                surv++;
+                int64_t o = oracle_overlap(tok + off[r], lr, tok + off[t], lt);
+                if (oracle_similar_sim(sim, o, lr, lt, p, q)) res++;
+            }
+        }
+        counts[0] = cand;
+        counts[1] = surv;
+        counts[2] = res;
+    }
+    free(off); free(tok); free(all); free(ukey); free(utok); free(rank_of); free(poff); free(tmp);
+    free(bm); free(pre);
 }

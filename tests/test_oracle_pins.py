@@ -781,3 +781,40 @@ def test_filter_counts_with_a_cutoff(sim, p, q):
                and O.similar_sim(sim, O.upper_bound(1, 1, O.hamming(bms[a], bms[b])), 1, 1, p, q))
     n1r, n1s = sum(1 for a in ones if a < 300), sum(1 for a in ones if a >= 300)
     assert (w, r) == (w0, r0) and s == w - (n1r * n1s - kept) and s > s0
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 4, 5), (O.COSINE, 3, 5),
+                                     (O.DICE, 7, 10), (O.OVERLAP, 3, 1)])
+def test_rs_prefix_filter_candidates(sim, p, q):
+    # RS-join candidates by the definition: ranks by (frequency over R and S, id); each
+    # set's prefix as in the self-join; pairs (r, s) inside Table 2's window whose
+    # prefixes intersect.  Every similar pair is a candidate.
+    from collections import Counter
+    off, tok = I.random_collection(240, 90, 1, 16, seed=170 + p + sim, planted_frac=0.25)
+    ro, rt, so, st = _split(off, tok, 100)
+    R = [rt[ro[i]:ro[i + 1]].tolist() for i in range(len(ro) - 1)]
+    S = [st[so[j]:so[j + 1]].tolist() for j in range(len(so) - 1)]
+    freq = Counter(t for x in R + S for t in x)
+    rank = {t: r for r, t in enumerate(sorted(freq, key=lambda t: (freq[t], t)))}
+
+    def low(x):   # smallest partner size y <= x that can still reach the threshold
+        for y in range(1, x + 1):
+            if _passes(sim, y, y, x, p, q):
+                return y
+        return x + 1
+
+    def prefix(x):
+        return set(sorted(rank[t] for t in x)[:max(0, len(x) - low(len(x)) + 1)])
+
+    pr, ps = [prefix(x) for x in R], [prefix(y) for y in S]
+    want = 0
+    for i in range(len(R)):
+        for j in range(len(S)):
+            a, b = sorted((len(R[i]), len(S[j])))
+            if _passes(sim, a, a, b, p, q) and pr[i] & ps[j]:
+                want += 1
+    c, s, r = O.rs_prefix_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
+    assert c == want
+    w, s_w, r_w = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
+    assert r == r_w == len(O.rs_join(ro, rt, so, st, p, q, sim=sim)[0]) and r > 0
+    assert r <= s <= s_w and c <= w
