@@ -450,12 +450,21 @@ def run_ours(args):
                 r, _, st = _bmj.bmj_rs_join(d_off, d_tok, ds_off, ds_tok, p, q, b=b,
                                             output_on_device=True, stream=stream.cuda_stream)
                 r.release()
+            for rep in range(2):
+                r, _, sx = _bmj.bmj_rs_join(d_off, d_tok, ds_off, ds_tok, p, q, b=b,
+                                            output_on_device=True, stream=stream.cuda_stream,
+                                            candidates=_bmj.BMJ_CAND_PREFIX)
+                r.release()
             rs.append({"threshold": f"{p}/{q}", "window_pairs": st["window_pairs"],
                        "survivors": st["survivors"], "results": st["results"],
                        "join_ms": round(st["ms_total"], 3), "filter_ms": round(st["ms_filter"], 3),
                        "pairs_per_s": round(st["window_pairs"] / (st["ms_total"] / 1e3)),
                        "filter_pairs_per_s": round(st["window_pairs"] /
-                                                   max(st["ms_filter"] / 1e3, 1e-9))})
+                                                   max(st["ms_filter"] / 1e3, 1e-9)),
+                       "prefix_filter": {"candidates": sx["candidates"], "results": sx["results"],
+                                         "join_ms": round(sx["ms_total"], 3),
+                                         "speedup_vs_window": round(st["ms_total"] /
+                                                                    sx["ms_total"], 3)}})
         del ds_off, ds_tok
 
     # ---- optional b sweep (outside the headline) ----

@@ -129,12 +129,12 @@ typedef struct {
                                   (sets ordered by size, ties by id) has its position in */
     int64_t row_end;           /*   [row_begin, row_end); 0, 0 = every pair.  Bands that cover
                                   [0, n) give disjoint pair lists whose union is the full join. */
-    int32_t candidates;        /* bmj_self_join: BMJ_CAND_WINDOW (default) filters every pair of
-                                  the length window; BMJ_CAND_PREFIX filters only the window
+    int32_t candidates;        /* bmj_self_join, bmj_rs_join: BMJ_CAND_WINDOW (default) filters
+                                  every pair of the length window; BMJ_CAND_PREFIX filters only the window
                                   pairs whose prefixes share a token (prefix filter, Section 2.2)
                                   -- fewer pairs at high thresholds, same result; it falls back
                                   to the window when its candidates do not fit in memory, and
-                                  needs row_begin = row_end = 0 */
+                                  needs row_begin = row_end = 0 and cutoff = 0 */
     int32_t cutoff;            /* bmj_self_join, bmj_rs_join: the cutoff point of Section 3.5.
                                   0 (default) = none, every window pair meets the Bitmap Filter
                                   (the paper's GPU setting); n > 0 = a pair whose larger set has
@@ -237,8 +237,10 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
  *           start at offset 0; r->n_sets + s->n_sets < 2^31
  *           (BMJ_ERR_TOO_LARGE otherwise)
  *   sim, p, q, opt, stats  as for bmj_self_join; opt->row_begin / row_end
- *           must be 0 and opt->candidates BMJ_CAND_WINDOW
- *           (BMJ_ERR_INVALID_ARG otherwise)
+ *           must be 0 (BMJ_ERR_INVALID_ARG otherwise); with
+ *           opt->candidates = BMJ_CAND_PREFIX the candidates are the window
+ *           pairs whose prefixes share a token, tokens ranked by their
+ *           frequency over R and S together
  *   out     library-owned pairs (free with bmj_pairs_free): a = id in R, b = id
  *           in S, sorted by (a, b); every pair appears once
  * Either collection empty gives an empty result.  The stream in opt is

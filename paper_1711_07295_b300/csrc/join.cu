@@ -232,7 +232,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
             uint2 *cq = nullptr;
             int64_t nc = 0, slots = 0;
-            int pst = prefix_candidates(ssz, soff, stok, n, d.ntok, win,
+            int pst = prefix_candidates(ssz, soff, stok, n, d.ntok, rs ? n_sc : 0, win,
                                         (int64_t)(free_b / 4 / sizeof(uint2)), PA, s, &cq, &nc,
                                         &slots);
             BMJ_CHECK(cudaEventRecord(ev.e[4], s));
@@ -665,8 +665,9 @@ int bmj_rs_join(const bmj_collection *r, const bmj_collection *s, int sim, uint3
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     if (o.row_begin != 0 || o.row_end != 0) return BMJ_ERR_INVALID_ARG;
-    if (o.candidates != BMJ_CAND_WINDOW) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX) return BMJ_ERR_INVALID_ARG;
     if (o.cutoff < BMJ_CUTOFF_AUTO) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates == BMJ_CAND_PREFIX && o.cutoff != 0) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(r, s, sim, p, q, o, out, stats);
     } catch (...) {

@@ -141,22 +141,24 @@ __device__ __forceinline__ int64_t prefix_len(uint32_t x, SimWindow win) {
     return low > x ? 0 : (int64_t)(x - low + 1);
 }
 
-// In size order: the first set with more than kThreadSetMax tokens, the first
-// with more than kWarpSetMax, and the position of the latter's first token
-// (one thread).
+// Within the size-ordered sets [i0, i1): the first set with more than
+// kThreadSetMax tokens, the first with more than kWarpSetMax, the position of
+// the latter's first token and the end of the range's tokens (one thread).
 __global__ void k_size_bounds(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
-                              int64_t n, int64_t ntok, int64_t *__restrict__ out) {
+                              int64_t i0, int64_t i1, int64_t n, int64_t ntok,
+                              int64_t *__restrict__ out) {
     const uint32_t lim[2] = {(uint32_t)kThreadSetMax, (uint32_t)kWarpSetMax};
     for (int k = 0; k < 2; k++) {
-        int64_t lo = 0, hi = n;
+        int64_t lo = i0, hi = i1;
         while (lo < hi) {
             const int64_t m = (lo + hi) >> 1;
             if (ssz[m] <= lim[k]) lo = m + 1;
             else hi = m;
         }
         out[k] = lo;
-        if (k == 1) out[2] = lo < n ? soff[lo] : ntok;
     }
+    out[2] = out[1] < n ? soff[out[1]] : ntok;
+    out[3] = i1 < n ? soff[i1] : ntok;
 }
 
 // The prefix of every set of at most kThreadSetMax tokens, in rank order: one
@@ -164,11 +166,11 @@ __global__ void k_size_bounds(const uint32_t *__restrict__ ssz, const int64_t *_
 // the next smallest, and so on, prefix-length times (ranks are distinct within
 // a set).
 __global__ void k_prefix_small(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
-                               const int32_t *__restrict__ stok, int64_t n1, SimWindow win,
-                               const int64_t *__restrict__ pofs, const RankLookup rl,
-                               uint32_t *__restrict__ pref) {
+                               const int32_t *__restrict__ stok, int64_t i0, int64_t n1,
+                               SimWindow win, const int64_t *__restrict__ pofs,
+                               const RankLookup rl, uint32_t *__restrict__ pref) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride) {
         const int x = (int)ssz[i];
         const int L = (int)prefix_len((uint32_t)x, win);
         if (L == 0) continue;
@@ -218,27 +220,27 @@ __global__ void __launch_bounds__(32 * kPrefWarps)
     }
 }
 
-// (set - i0) << ubits | rank for the tokens of the sets [i0, n) (their tokens
-// are the suffix of the sorted CSR from soff[i0] = t0); one thread per set.
+// (set - i0) << ubits | rank for the tokens of the sets [i0, i1) (their tokens
+// are contiguous in the sorted CSR from soff[i0] = t0); one thread per set.
 __global__ void k_set_keys(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
-                           const int32_t *__restrict__ stok, int64_t i0, int64_t n, int64_t t0,
+                           const int32_t *__restrict__ stok, int64_t i0, int64_t i1, int64_t t0,
                            const RankLookup rl, int ubits, uint64_t *__restrict__ keys) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += stride) {
         const int64_t o = soff[i];
         for (uint32_t k = 0; k < ssz[i]; k++)
             keys[o - t0 + k] = ((uint64_t)(i - i0) << ubits) | rl((uint32_t)stok[o + k]);
     }
 }
 
-// The prefixes of the sets [i0, n) from their (set, rank) keys sorted.
+// The prefixes of the sets [i0, i1) from their (set, rank) keys sorted.
 __global__ void k_prefix_big(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ soff,
-                             const uint64_t *__restrict__ sorted, int64_t i0, int64_t n,
+                             const uint64_t *__restrict__ sorted, int64_t i0, int64_t i1,
                              int64_t t0, SimWindow win, const int64_t *__restrict__ pofs,
                              int ubits, uint32_t *__restrict__ pref) {
     const uint64_t umask = (1ull << ubits) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    for (int64_t i = i0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < i1; i += stride) {
         const int64_t len = prefix_len(ssz[i], win);
         for (int64_t k = 0; k < len; k++)
             pref[pofs[i] + k] = (uint32_t)(sorted[soff[i] - t0 + k] & umask);
@@ -266,30 +268,61 @@ __global__ void k_prefix_emit(const uint32_t *__restrict__ ssz, const uint32_t *
 }
 
 // Per index entry k = (rank r, set i): the entries of r's list before k (earlier
-// sets in size order) whose size is inside i's window form [lo, k).
+// sets in size order) whose size is inside i's window form [lo, k).  RS-join
+// (n_cols > 0: S holds positions [0, n_cols), R the rest): an entry of S owns
+// no candidates; an entry of R owns the entries of S in its rank's list whose
+// size lies between i's window bounds (S's sets precede R's in every list).
 __global__ void k_cand_count(const uint64_t *__restrict__ idx, int64_t P,
                              const uint32_t *__restrict__ ssz, SimWindow win, int rshift,
-                             int64_t *__restrict__ lo_out, int64_t *__restrict__ cnt) {
+                             int64_t n_cols, int64_t *__restrict__ lo_out,
+                             int64_t *__restrict__ cnt) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const uint64_t umask = (1ull << rshift) - 1;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < P; k += stride) {
         const uint64_t key = idx[k];
         const uint64_t r = key & umask;
+        const int64_t i = (int64_t)(key >> rshift);
+        if (n_cols > 0 && i < n_cols) {
+            lo_out[k] = k;
+            cnt[k] = 0;
+            continue;
+        }
         int64_t a = 0, b = k;  // first entry of the rank's list
         while (a < b) {
             const int64_t m = (a + b) >> 1;
             if ((idx[m] & umask) < r) a = m + 1;
             else b = m;
         }
-        const uint64_t low = window_low(ssz[key >> rshift], win);
-        b = k;  // first entry of the list with a size inside the window
+        int64_t e = k;  // end of the candidate partners: k, or (RS) the first entry of R
+        if (n_cols > 0) {
+            int64_t c = a;
+            while (c < e) {
+                const int64_t m = (c + e) >> 1;
+                if ((int64_t)(idx[m] >> rshift) < n_cols) c = m + 1;
+                else e = m;
+            }
+        }
+        const uint64_t low = window_low(ssz[i], win);
+        b = e;  // first entry with a size inside the window
         while (a < b) {
             const int64_t m = (a + b) >> 1;
             if (ssz[idx[m] >> rshift] < low) a = m + 1;
             else b = m;
         }
+        if (n_cols > 0) {  // (RS) past the last entry with a size below the upper bound
+            const uint64_t high = window_high(ssz[i], win);
+            if (high != ~0ull) {
+                int64_t c = a, d = e;
+                while (c < d) {
+                    const int64_t m = (c + d) >> 1;
+                    if ((uint64_t)ssz[idx[m] >> rshift] <= high) c = m + 1;
+                    else d = m;
+                }
+                e = c;
+            }
+        }
         lo_out[k] = a;
-        cnt[k] = k - a;
+        cnt[k] = e > a ? e - a : 0;
     }
 }
 
@@ -352,8 +385,8 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
 }  // namespace
 
 int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, int64_t n,
-                      int64_t ntok, SimWindow win, int64_t max_cand, Arena &A, cudaStream_t s,
-                      uint2 **cand, int64_t *n_cand, int64_t *n_slots) {
+                      int64_t ntok, int64_t n_cols, SimWindow win, int64_t max_cand, Arena &A,
+                      cudaStream_t s, uint2 **cand, int64_t *n_cand, int64_t *n_slots) {
     *cand = nullptr;
     *n_cand = 0;
     *n_slots = 0;
@@ -417,47 +450,67 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
         BMJ_LAUNCH(k_rank_map, grid_p(nu, 256), 256, 0, s, utok, rank_of, nu, rank_map);
         rl.map = rank_map;
     }
-    // ---- prefix lengths and offsets; where the set sizes cross the size classes ----
+    // ---- prefix lengths and offsets ----
     int64_t *pofs = nullptr, *bounds = nullptr;
     rc = A.alloc(&pofs, (size_t)n);
-    if (!rc) rc = A.alloc(&bounds, 3);
+    if (!rc) rc = A.alloc(&bounds, 4);
     if (rc) return rc;
     BMJ_LAUNCH(k_prefix_len, grid_p(n, 256), 256, 0, s, ssz, n, win, pofs);
     rc = exclusive_scan_i64(pofs, pofs, n, tot, A, s);  // pofs: the prefix offsets
     if (rc) return rc;
-    BMJ_LAUNCH(k_size_bounds, 1, 1, 0, s, ssz, soff, n, ntok, bounds);
-    int64_t hv[4] = {0, 0, 0, 0};  // P, first set above one thread, above one warp, its token
+    const int64_t run0_end = n_cols > 0 ? n_cols : n;
+    BMJ_LAUNCH(k_size_bounds, 1, 1, 0, s, ssz, soff, (int64_t)0, run0_end, n, ntok, bounds);
+    int64_t hv[5] = {0, 0, 0, 0, 0};  // P, then the first run's size-class bounds
     BMJ_CHECK(cudaMemcpyAsync(&hv[0], tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    BMJ_CHECK(cudaMemcpyAsync(&hv[1], bounds, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BMJ_CHECK(cudaMemcpyAsync(&hv[1], bounds, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
-    const int64_t P = hv[0], n1 = hv[1], n_small = hv[2], t0 = hv[3];
+    const int64_t P = hv[0];
     if (P == 0) return BMJ_OK;
-    // ---- every set's prefix in rank order ----
+    // ---- every set's prefix in rank order, per run of sets in size order (one
+    //      run for a self-join; S's run and R's run for an RS-join) ----
     uint32_t *pref = nullptr;
     rc = A.alloc(&pref, (size_t)P);
     if (rc) return rc;
-    if (n1 > 0)
-        BMJ_LAUNCH(k_prefix_small, grid_p(n1, 128, 148 * 64), 128, 0, s, ssz, soff, stok, n1, win,
-                   pofs, rl, pref);
-    if (n_small > n1)
-        BMJ_LAUNCH(k_prefix_rank, grid_p(n_small - n1, kPrefWarps, 148 * 16), 32 * kPrefWarps, 0, s,
-                   ssz, soff, stok, n1, n_small, win, pofs, rl, pref);
-    if (n_small < n) {  // sets of more than kWarpSetMax tokens: sort their (set, rank) keys
-        const int64_t tb = ntok - t0;
-        const int bbits = std::max(1, bit_length((uint64_t)(n - n_small - 1)));
-        uint64_t *bk = nullptr, *bs = nullptr;
-        rc = A.alloc(&bk, (size_t)tb);
-        if (!rc) rc = A.alloc(&bs, (size_t)tb);
-        if (rc) return rc;
-        BMJ_LAUNCH(k_set_keys, grid_p(n - n_small, 128), 128, 0, s, ssz, soff, stok, n_small, n, t0,
-                   rl, ubits, bk);
-        rc = radix_sort_u64(bk, bs, tb, ubits + bbits, A, s);
-        if (rc) return rc;
-        BMJ_LAUNCH(k_prefix_big, grid_p(n - n_small, 128), 128, 0, s, ssz, soff, bs, n_small, n, t0,
-                   win, pofs, ubits, pref);
-        A.free_one(bk);
-        A.free_one(bs);
-    }
+    // hb: the run's first set above one thread, above one warp, its first token,
+    // the run's end token (read back with P for the first run)
+    auto prefix_run = [&](int64_t i0, int64_t i1, const int64_t *known) -> int {
+        if (i1 <= i0) return BMJ_OK;
+        int64_t hb[4] = {0, 0, 0, 0};
+        if (known) {
+            for (int k = 0; k < 4; k++) hb[k] = known[k];
+        } else {
+            BMJ_LAUNCH(k_size_bounds, 1, 1, 0, s, ssz, soff, i0, i1, n, ntok, bounds);
+            BMJ_CHECK(cudaMemcpyAsync(hb, bounds, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BMJ_CHECK(cudaStreamSynchronize(s));
+        }
+        const int64_t n1 = hb[0], n2 = hb[1], t0 = hb[2], t1 = hb[3];
+        if (n1 > i0)
+            BMJ_LAUNCH(k_prefix_small, grid_p(n1 - i0, 128, 148 * 64), 128, 0, s, ssz, soff, stok, i0,
+                       n1, win, pofs, rl, pref);
+        if (n2 > n1)
+            BMJ_LAUNCH(k_prefix_rank, grid_p(n2 - n1, kPrefWarps, 148 * 16), 32 * kPrefWarps, 0, s,
+                       ssz, soff, stok, n1, n2, win, pofs, rl, pref);
+        if (n2 < i1) {  // sets of more than kWarpSetMax tokens: sort their (set, rank) keys
+            const int64_t tb = t1 - t0;
+            const int bbits = std::max(1, bit_length((uint64_t)(i1 - n2 - 1)));
+            uint64_t *bk = nullptr, *bs = nullptr;
+            int r2 = A.alloc(&bk, (size_t)tb);
+            if (!r2) r2 = A.alloc(&bs, (size_t)tb);
+            if (r2) return r2;
+            BMJ_LAUNCH(k_set_keys, grid_p(i1 - n2, 128), 128, 0, s, ssz, soff, stok, n2, i1, t0, rl,
+                       ubits, bk);
+            r2 = radix_sort_u64(bk, bs, tb, ubits + bbits, A, s);
+            if (r2) return r2;
+            BMJ_LAUNCH(k_prefix_big, grid_p(i1 - n2, 128), 128, 0, s, ssz, soff, bs, n2, i1, t0, win,
+                       pofs, ubits, pref);
+            A.free_one(bk);
+            A.free_one(bs);
+        }
+        return BMJ_OK;
+    };
+    rc = prefix_run(0, run0_end, &hv[1]);
+    if (!rc && n_cols > 0) rc = prefix_run(n_cols, n, nullptr);
+    if (rc) return rc;
     // ---- index the prefixes by (rank, set) ----
     uint64_t *ix = nullptr, *idx = nullptr;
     rc = A.alloc(&ix, (size_t)P);
@@ -473,7 +526,8 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     rc = A.alloc(&lo, (size_t)P);
     if (!rc) rc = A.alloc(&coff, (size_t)P + 1);
     if (rc) return rc;
-    BMJ_LAUNCH(k_cand_count, grid_p(P, 256), 256, 0, s, idx, P, ssz, win, rshift, lo, coff);
+    BMJ_LAUNCH(k_cand_count, grid_p(P, 256), 256, 0, s, idx, P, ssz, win, rshift, n_cols, lo,
+               coff);
     rc = exclusive_scan_i64(coff, coff, P, coff + P, A, s);
     if (rc) return rc;
     int64_t C = 0;

@@ -152,7 +152,8 @@ def test_rs_join_arguments_rejected_on_host():
     assert call(ss=None) == _bmj.BMJ_ERR_INVALID_ARG
     assert call(p=3, q=2) == _bmj.BMJ_ERR_INVALID_ARG
     assert call(b=100) == _bmj.BMJ_ERR_INVALID_ARG
-    assert call(candidates=_bmj.BMJ_CAND_PREFIX) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(candidates=_bmj.BMJ_CAND_PREFIX, cutoff=4) == _bmj.BMJ_ERR_INVALID_ARG
+    assert call(candidates=7) == _bmj.BMJ_ERR_INVALID_ARG
     assert call(row_begin=0, row_end=1) == _bmj.BMJ_ERR_INVALID_ARG
     assert call(cutoff=-2) == _bmj.BMJ_ERR_INVALID_ARG
     big = _bmj.bmj_collection(1 << 30, off.ctypes.data_as(C.c_void_p), tok.ctypes.data_as(C.c_void_p), 0, 0)

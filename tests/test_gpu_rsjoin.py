@@ -164,8 +164,8 @@ def test_rs_join_invalid_arguments():
     with pytest.raises(_bmj.BmjError) as e:
         _bmj.bmj_rs_join(ro, rt, so, unsorted, 1, 2)
     assert e.value.status == _bmj.BMJ_ERR_UNSORTED
-    with pytest.raises(_bmj.BmjError) as e:   # the prefix filter joins one collection only
-        _bmj.bmj_rs_join(ro, rt, so, st_, 1, 2, candidates=_bmj.BMJ_CAND_PREFIX)
+    with pytest.raises(_bmj.BmjError) as e:   # prefix candidates and a cutoff do not combine
+        _bmj.bmj_rs_join(ro, rt, so, st_, 1, 2, candidates=_bmj.BMJ_CAND_PREFIX, cutoff=5)
     assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
     check_rs((ro, rt), (so, st_), 1, 2)   # the context stays usable
 
@@ -193,3 +193,48 @@ def test_rs_join_of_two_million_set_collections_row_sampled():
         assert st["results"] == len(a) <= st["survivors"] <= st["window_pairs"]
         x, y = sizes[a], np.diff(so)[bb]
         assert np.all(q * np.minimum(x, y) >= p * np.maximum(x, y))
+
+
+@pytest.mark.parametrize("b", [64, 128, 256])
+@pytest.mark.parametrize("sim,p,q", [(_bmj.BMJ_JACCARD, 1, 2), (_bmj.BMJ_JACCARD, 4, 5),
+                                     (_bmj.BMJ_COSINE, 3, 5), (_bmj.BMJ_DICE, 9, 10),
+                                     (_bmj.BMJ_OVERLAP, 4, 1)])
+def test_rs_join_prefix_candidates(sim, p, q, b):
+    # prefix-filter candidates of R x S (ranks over R and S together): same pairs, and
+    # candidates, survivors and results equal to the oracle's counts
+    off, tok = I.random_collection(3200, 2500, 1, 60, seed=400 + b + sim + p, zipf_s=1.0,
+                                   planted_frac=0.2)
+    ro, rt, so, st_ = split(off, tok, 1300)
+    a, bb, st = _bmj.bmj_rs_join(*dev(ro, rt), *dev(so, st_), p, q, b=b, sim=sim,
+                                 candidates=_bmj.BMJ_CAND_PREFIX)
+    wa, wb = O.rs_join(ro, rt, so, st_, p, q, sim=sim)
+    assert np.array_equal(a, wa) and np.array_equal(bb, wb) and len(a) > 0
+    c, s, r = O.rs_prefix_counts(ro, rt, so, st_, p, q, b, O.XOR, sim=sim)
+    assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r)
+    w, _, _ = O.rs_filter_counts(ro, rt, so, st_, p, q, b, O.XOR, sim=sim)
+    assert st["window_pairs"] == w and c <= w
+
+
+def test_rs_join_prefix_candidates_with_large_sets():
+    # sets of 33 to 6,000 tokens on both sides: every size class of the prefix selection
+    # (one thread, one warp, a sort) runs on both of R's and S's size-ordered runs
+    rng = np.random.default_rng(97)
+    base = np.sort(rng.choice(30000, 8000, replace=False))
+
+    def coll(n_small, bigs, seed):
+        o, t = I.random_collection(n_small, 4000, 1, 60, seed=seed, planted_frac=0.2)
+        sets = [t[o[i]:o[i + 1]] for i in range(len(o) - 1)]
+        sets += [np.sort(rng.choice(base[:x + 400], x, replace=False)) for x in bigs]
+        off = np.zeros(len(sets) + 1, np.int64)
+        off[1:] = np.cumsum([len(x) for x in sets])
+        return off, np.concatenate(sets).astype(np.int32)
+
+    ro, rt = coll(900, (40, 500, 2049, 3000, 6000), 98)
+    so, st_ = coll(1200, (33, 2100, 2500, 5900), 99)
+    for p, q in ((4, 5), (1, 2)):
+        a, bb, st = _bmj.bmj_rs_join(*dev(ro, rt), *dev(so, st_), p, q,
+                                     candidates=_bmj.BMJ_CAND_PREFIX)
+        wa, wb = O.rs_join(ro, rt, so, st_, p, q)
+        assert np.array_equal(a, wa) and np.array_equal(bb, wb) and len(a) > 0
+        c, s, r = O.rs_prefix_counts(ro, rt, so, st_, p, q, 64, O.XOR)
+        assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r)
