@@ -92,6 +92,14 @@ __global__ void k_split_keys(const uint32_t *__restrict__ skey, int64_t n, int s
 }
 
 // Output pairs from keys (job << 2*nbits) | (lo << nbits) | hi.
+// out[k] = src[idx[k]] for k < m.
+__global__ void k_gather_at(const int64_t *__restrict__ src, const int64_t *__restrict__ idx,
+                            int64_t m, int64_t *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += stride)
+        out[k] = src[idx[k]];
+}
+
 __global__ void k_unpack_local(const uint64_t *__restrict__ keys, int64_t n, int nbits,
                                uint32_t *__restrict__ a, uint32_t *__restrict__ b) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -808,11 +816,18 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
             //   set size of 12, growing with the merge length (mean size).
             std::vector<double> mean_size(n_jobs, 0.0);
             {
+                // each job's first token position in the sorted CSR, gathered at once
                 std::vector<int64_t> h_soff(n_jobs + 1);
-                for (int64_t k = 0; k <= n_jobs; k++) {
-                    BMJ_CHECK(cudaMemcpyAsync(&h_soff[k], P.soff + job_sets[k], sizeof(int64_t),
-                                              cudaMemcpyDeviceToHost, s));
-                }
+                int64_t *jsd = nullptr, *jso = nullptr;
+                st = A.alloc(&jsd, (size_t)n_jobs + 1);
+                if (!st) st = A.alloc(&jso, (size_t)n_jobs + 1);
+                if (st) return st;
+                BMJ_CHECK(cudaMemcpyAsync(jsd, job_sets, (n_jobs + 1) * sizeof(int64_t),
+                                          cudaMemcpyHostToDevice, s));
+                BMJ_LAUNCH(k_gather_at, grid_of(n_jobs + 1, 256), 256, 0, s, P.soff, jsd,
+                           n_jobs + 1, jso);
+                BMJ_CHECK(cudaMemcpyAsync(h_soff.data(), jso, (n_jobs + 1) * sizeof(int64_t),
+                                          cudaMemcpyDeviceToHost, s));
                 BMJ_CHECK(cudaStreamSynchronize(s));
                 for (int64_t k = 0; k < n_jobs; k++) {
                     const int64_t nk = job_sets[k + 1] - job_sets[k];
