@@ -15,6 +15,7 @@
 
 #include "kernels.cuh"
 #include "host_util.cuh"
+#include "prefix.cuh"
 
 namespace bmj {
 

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "host_util.cuh"
+#include "prefix.cuh"
 
 namespace bmj {
 namespace {
