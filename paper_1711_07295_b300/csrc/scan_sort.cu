@@ -7,7 +7,7 @@
 //          scan of the tile totals, then a pass that adds the tile offsets;
 //   sort:  per pass an 8-bit digit histogram per tile, an exclusive scan of
 //          the digit-major histogram, then a stable scatter in which every
-//          warp ranks its items with __match_any_sync and a per-warp
+//          warp ranks its items by ballots over the digit bits and a per-warp
 //          histogram in shared memory.
 #include "bmj_internal.cuh"
 
@@ -148,7 +148,15 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const K *keys_in, co
             if (kHasVals) val[it] = vals_in[i];
             d = (uint32_t)(key[it] >> shift) & 255u;
         }
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // the lanes holding the same digit: one ballot per digit bit (a little
+        // faster than __match_any_sync here); an invalid lane is a group alone
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int bit = 0; bit < 8; bit++) {
+            const unsigned bal = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+            peers &= ((d >> bit) & 1u) ? bal : ~bal;
+        }
+        if (!valid) peers = 1u << lane;
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
         if (lane == leader) {
