@@ -330,6 +330,16 @@ int bmj_index_create(const bmj_collection *coll, const bmj_options *opt, bmj_ind
 void bmj_index_destroy(bmj_index *idx);
 int64_t bmj_index_size(const bmj_index *idx);
 
+/*
+ * Errors stick to an index: once a call on it fails with BMJ_ERR_CUDA or
+ * BMJ_ERR_TIMEOUT (its device state is then in doubt), every later
+ * bmj_index_query / bmj_serve on it returns that status without running, and
+ * only bmj_index_destroy remains useful.  Argument errors and BMJ_ERR_OOM do
+ * not stick.  bmj_index_status returns the sticky status (BMJ_OK while the
+ * index is usable; BMJ_ERR_INVALID_ARG for NULL).
+ */
+int bmj_index_status(const bmj_index *idx);
+
 /* Fills *opt with the serving defaults listed above. */
 void bmj_default_serve_options(bmj_serve_options *opt);
 

@@ -150,6 +150,7 @@ SIGNATURES = {
                                    C.POINTER(C.c_void_p)]),
     "bmj_index_destroy": (None, [C.c_void_p]),
     "bmj_index_size": (C.c_int64, [C.c_void_p]),
+    "bmj_index_status": (C.c_int, [C.c_void_p]),
     "bmj_default_serve_options": (None, [C.POINTER(bmj_serve_options)]),
     "bmj_index_query": (C.c_int, [C.c_void_p, C.POINTER(bmj_collection), C.c_void_p, C.c_void_p,
                                   C.POINTER(bmj_id_lists), C.POINTER(bmj_serve_stats)]),
@@ -487,6 +488,10 @@ class Index:
             self.close()
         except Exception:
             pass
+
+    def status(self) -> int:
+        """bmj_index_status: BMJ_OK, or the device failure that stuck to the index."""
+        return int(lib().bmj_index_status(self._h))
 
     def query(self, offsets, tokens, p, q):
         """bmj_index_query: per-probe arrays of resident ids (ascending) and stats."""

@@ -51,6 +51,7 @@ struct FaultPlan {
     int alloc_at = 0;   // 0: none
     bool timeout = false;
     bool keys = false;
+    bool serve = false;  // a call on an index fails as a CUDA runtime error would
 };
 FaultPlan read_fault_plan();      // parses BMJ_FAULT
 void arm_alloc_fault(int k);      // the k-th next Arena allocation fails (0 disarms)

@@ -32,6 +32,7 @@ FaultPlan read_fault_plan() {
     if (strncmp(e, "alloc:", 6) == 0) f.alloc_at = atoi(e + 6);
     if (strcmp(e, "timeout") == 0) f.timeout = true;
     if (strcmp(e, "keys") == 0) f.keys = true;
+    if (strcmp(e, "serve") == 0) f.serve = true;
     return f;
 }
 

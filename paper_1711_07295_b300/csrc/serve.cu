@@ -41,6 +41,7 @@ struct bmj_index {
     uint64_t *bm = nullptr;   // (n + 4) * W
     std::vector<int64_t> size_cum;  // size_cum[s] = resident sets with size < s
     int64_t *d_size_cum = nullptr;  // the same on the device (max_size + 2 entries)
+    int sticky = 0;  // a CUDA runtime or timeout failure of an earlier call (then every call fails)
 };
 
 namespace bmj {
@@ -807,12 +808,26 @@ extern "C" void bmj_default_serve_options(bmj_serve_options *so) {
     so->max_batch_window_pairs = (int64_t)1 << 25;
 }
 
+// A device-level failure (CUDA runtime error, bounded wait given up) leaves the
+// index's device state in doubt: it sticks to the handle.  Argument errors and
+// out-of-memory do not.
+static int stick(bmj_index *idx, int st) {
+    if (st == BMJ_ERR_CUDA || st == BMJ_ERR_TIMEOUT) idx->sticky = st;
+    return st;
+}
+
+extern "C" int bmj_index_status(const bmj_index *idx) {
+    return idx ? idx->sticky : BMJ_ERR_INVALID_ARG;
+}
+
 extern "C" int bmj_index_query(bmj_index *idx, const bmj_collection *probes, const uint32_t *p,
                                const uint32_t *q, bmj_id_lists *out, bmj_serve_stats *stats) {
     if (!idx || !out) return BMJ_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
+    if (idx->sticky) return idx->sticky;
     int st = check_queries(idx, probes, p, q);
     if (st) return st;
+    if (bmj::read_fault_plan().serve) return stick(idx, BMJ_ERR_CUDA);
     bmj_serve_options so;
     bmj_default_serve_options(&so);
     so.n_slots = 1;
@@ -826,7 +841,7 @@ extern "C" int bmj_index_query(bmj_index *idx, const bmj_collection *probes, con
         id_lists_free_impl(out);
         cudaGetLastError();
     }
-    return st;
+    return stick(idx, st);
 }
 
 extern "C" int bmj_serve(bmj_index *idx, const bmj_collection *queries, const double *arrival_s,
@@ -834,8 +849,10 @@ extern "C" int bmj_serve(bmj_index *idx, const bmj_collection *queries, const do
                          bmj_id_lists *out, double *latency_ms, bmj_serve_stats *stats) {
     if (!idx || !arrival_s) return BMJ_ERR_INVALID_ARG;
     if (out) memset(out, 0, sizeof(*out));
+    if (idx->sticky) return idx->sticky;
     int st = check_queries(idx, queries, p, q);
     if (st) return st;
+    if (bmj::read_fault_plan().serve) return stick(idx, BMJ_ERR_CUDA);
     for (int64_t x = 1; x < queries->n_sets; x++)
         if (arrival_s[x] < arrival_s[x - 1]) return BMJ_ERR_INVALID_ARG;
     bmj_serve_options so;
@@ -852,5 +869,5 @@ extern "C" int bmj_serve(bmj_index *idx, const bmj_collection *queries, const do
         if (out) id_lists_free_impl(out);
         cudaGetLastError();
     }
-    return st;
+    return stick(idx, st);
 }

@@ -89,6 +89,7 @@ def test_similarity_function_thresholds_checked_on_host(sim, p, q, ok):
 
 def test_null_pointers_rejected():
     L = _bmj.lib()
+    assert L.bmj_index_status(None) == _bmj.BMJ_ERR_INVALID_ARG
     pairs = _bmj.bmj_pairs()
     assert L.bmj_self_join(None, 0, 1, 2, None, C.byref(pairs), None) == _bmj.BMJ_ERR_INVALID_ARG
     coll = _bmj.bmj_collection(-1, None, None, 0, 0)

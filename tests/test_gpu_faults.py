@@ -49,3 +49,35 @@ def test_refused_key_buffer_verifies_the_queue_in_slices(monkeypatch):
     monkeypatch.delenv("BMJ_FAULT")
     assert np.array_equal(a, ra) and np.array_equal(b, rb)
     assert (st["window_pairs"], st["survivors"], st["results"]) == (w, s, r) and s >= 5
+
+
+def test_device_failures_stick_to_an_index(monkeypatch):
+    # a call on an index that fails as a CUDA runtime error would (injected on the
+    # host) leaves every later call on that index failing with the same status;
+    # argument errors do not stick, and a fresh index is unaffected
+    off, tok = I.random_collection(5000, 1000, 1, 30, seed=78, planted_frac=0.1)
+    qoff, qtok = off[:41].copy(), tok[:off[40]].copy()
+    p, q = np.full(40, 3, np.uint32), np.full(40, 4, np.uint32)
+    idx = _bmj.Index(off, tok, b=64)
+    want, _ = idx.query(qoff, qtok, p, q)
+    with pytest.raises(_bmj.BmjError) as e:      # an argument error: not sticky
+        idx.query(qoff, qtok, np.full(40, 5, np.uint32), q)
+    assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG and idx.status() == _bmj.BMJ_OK
+    monkeypatch.setenv("BMJ_FAULT", "serve")
+    with pytest.raises(_bmj.BmjError) as e:
+        idx.query(qoff, qtok, p, q)
+    assert e.value.status == _bmj.BMJ_ERR_CUDA
+    monkeypatch.delenv("BMJ_FAULT")
+    assert idx.status() == _bmj.BMJ_ERR_CUDA
+    with pytest.raises(_bmj.BmjError) as e:      # sticky: the fault is gone, the status stays
+        idx.query(qoff, qtok, p, q)
+    assert e.value.status == _bmj.BMJ_ERR_CUDA
+    with pytest.raises(_bmj.BmjError) as e:
+        idx.serve(qoff, qtok, np.zeros(40), p, q)
+    assert e.value.status == _bmj.BMJ_ERR_CUDA
+    idx.close()
+    fresh = _bmj.Index(off, tok, b=64)
+    got, _ = fresh.query(qoff, qtok, p, q)
+    assert fresh.status() == _bmj.BMJ_OK
+    assert len(got) == len(want) and all(np.array_equal(x, y) for x, y in zip(got, want))
+    fresh.close()
