@@ -1,4 +1,4 @@
-"""Splitting one self-join across ranks by row bands, and gathering the results.
+"""Splitting one self-join (or RS-join) across ranks, and gathering the results.
 
 The size-sorted triangle of window pairs (sets ordered by size, ties by id,
 the order the library joins in) is cut into contiguous row bands with about
@@ -7,6 +7,10 @@ set lies in its band (bmj_options.row_begin / row_end), over the full
 collection, which every rank holds.  The bands' pair lists are disjoint and
 their union is the full join, so the only exchange is one gather of the pair
 lists at the end, merged into the canonical (a, b) order.
+
+An RS-join splits by R: rank r joins a contiguous range of R's sets (about the
+same number of window pairs each) with all of S, and its R ids are offset by
+the range's start before the same gather.
 """
 from __future__ import annotations
 
@@ -69,3 +73,45 @@ def sharded_self_join(offsets, tokens, p: int, q: int, rank: int, world: int, **
     from . import _bmj
     r0, r1 = band_split(offsets.cpu().numpy() if hasattr(offsets, "cpu") else offsets, p, q, world)[rank]
     return _bmj.bmj_self_join(offsets, tokens, p, q, row_begin=r0, row_end=r1, **kw)
+
+
+def rs_row_windows(r_offsets, s_offsets, p: int, q: int) -> np.ndarray:
+    """Window pairs of every set of R (original order) against S, for the Jaccard
+    threshold p/q: the sets of S with ceil(p*x/q) <= size <= floor(q*x/p)."""
+    rs = np.diff(np.asarray(r_offsets, dtype=np.int64))
+    ss = np.sort(np.diff(np.asarray(s_offsets, dtype=np.int64)))
+    low = -(-(p * rs) // q)
+    high = (q * rs) // p
+    return np.searchsorted(ss, high, side="right") - np.searchsorted(ss, low, side="left")
+
+
+def rs_split(r_offsets, s_offsets, p: int, q: int, world: int):
+    """[(r_begin, r_end)] for each rank: contiguous ranges of R's sets (original
+    order) covering R, with about the same number of window pairs each."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    w = rs_row_windows(r_offsets, s_offsets, p, q)
+    n = len(w)
+    cum = np.concatenate([[0], np.cumsum(w)])
+    cuts = [0] + [int(np.searchsorted(cum, cum[-1] * r / world, side="left")) for r in range(1, world)]
+    cuts.append(n)
+    cuts = np.maximum.accumulate(np.clip(cuts, 0, n))
+    return [(int(cuts[r]), int(cuts[r + 1])) for r in range(world)]
+
+
+def rs_part(r_offsets, r_tokens, r0: int, r1: int):
+    """The sets [r0, r1) of R as a collection of their own (offsets rebased)."""
+    off = np.asarray(r_offsets, dtype=np.int64)
+    tok = np.asarray(r_tokens)
+    return off[r0:r1 + 1] - off[r0], tok[off[r0]:off[r1]]
+
+
+def sharded_rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, rank: int, world: int,
+                    **kw):
+    """This rank's range of R joined with all of S through the C ABI (bmj_rs_join);
+    the R ids it returns are ids of the whole R."""
+    from . import _bmj
+    r0, r1 = rs_split(r_offsets, s_offsets, p, q, world)[rank]
+    po, pt = rs_part(r_offsets, r_tokens, r0, r1)
+    a, b, st = _bmj.bmj_rs_join(po, pt, s_offsets, s_tokens, p, q, **kw)
+    return (np.asarray(a, np.uint32) + np.uint32(r0)), b, st

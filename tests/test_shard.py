@@ -46,6 +46,31 @@ def test_bands_partition_the_oracle_join():
     assert np.array_equal(ma, a) and np.array_equal(mb, b)
 
 
+@pytest.mark.parametrize("world", [1, 2, 5])
+def test_rs_split_partitions_the_oracle_rs_join(world):
+    # the ranks' ranges of R cover R, carry about equal window pairs, and their
+    # RS-joins with all of S (R ids offset back) merge into the full RS-join
+    off, tok = I.random_collection(1500, 300, 1, 25, seed=20 + world, planted_frac=0.2)
+    ro, rt = off[:601].copy(), tok[:off[600]].copy()
+    so, st = off[600:] - off[600], tok[off[600]:].copy()
+    parts_r = shard.rs_split(ro, so, 3, 5, world)
+    assert parts_r[0][0] == 0 and parts_r[-1][1] == 600
+    assert all(parts_r[k][1] == parts_r[k + 1][0] for k in range(world - 1))
+    w = shard.rs_row_windows(ro, so, 3, 5)
+    assert w.sum() == O.rs_filter_counts(ro, rt, so, st, 3, 5, 64, O.XOR)[0]
+    if world > 1:
+        loads = [w[a:b].sum() for a, b in parts_r]
+        assert max(loads) <= 1.05 * (w.sum() / world) + w.max()
+    parts = []
+    for r0, r1 in parts_r:
+        po, pt = shard.rs_part(ro, rt, r0, r1)
+        a, b = O.rs_join(po, pt, so, st, 3, 5)
+        parts.append((a + np.uint32(r0), b))
+    ma, mb = shard.merge_pairs(parts)
+    fa, fb = O.rs_join(ro, rt, so, st, 3, 5)
+    assert np.array_equal(ma, fa) and np.array_equal(mb, fb) and len(fa) > 0
+
+
 def _gloo_worker(rank, world, port, result_path):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -95,3 +120,24 @@ def test_gpu_bands_merge_to_full_join():
         assert (win, surv) == (fst["window_pairs"], fst["survivors"])
     with pytest.raises(_bmj.BmjError):
         _bmj.bmj_self_join(d_off, d_tok, 1, 2, row_begin=5, row_end=4)
+
+
+@pytest.mark.gpu
+def test_gpu_rs_parts_merge_to_full_rs_join():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1711_07295_b300 import _bmj
+    off, tok = I.random_collection(9000, 2000, 1, 50, seed=13, planted_frac=0.15)
+    ro, rt = off[:4001].copy(), tok[:off[4000]].copy()
+    so, st_ = off[4000:] - off[4000], tok[off[4000]:].copy()
+    fa, fb, fst = _bmj.bmj_rs_join(ro, rt, so, st_, 3, 5)
+    for world in (2, 3):
+        parts, win = [], 0
+        for r in range(world):
+            a, b, st = shard.sharded_rs_join(ro, rt, so, st_, 3, 5, r, world)
+            parts.append((a, b))
+            win += st["window_pairs"]
+        ma, mb = shard.merge_pairs(parts)
+        assert np.array_equal(ma, fa) and np.array_equal(mb, fb) and len(fa) > 0
+        assert win == fst["window_pairs"]
