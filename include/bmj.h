@@ -3,8 +3,10 @@
  *
  * Method: Sandes, Teodoro & Melo, "Bitmap Filter: Speeding up Exact Set
  * Similarity Joins with Bitwise Operations".  A self-join returns every pair
- * of sets whose Jaccard similarity reaches the threshold (Section 2.1,
- * Eq. 1).  The library computes it exactly, on the GPU, in four stages:
+ * of sets whose similarity (Jaccard by default; Cosine, Dice, Overlap,
+ * Table 1) reaches the threshold (Section 2.1, Eq. 1); an RS-join every pair
+ * of two collections.  The library computes them exactly, on the GPU, in
+ * four stages:
  *   1. one b-bit bitmap per set from hashed tokens (Section 3.2, Alg. 3a-3c,
  *      hash h(t) = t mod b, Section 5.1);
  *   2. for every pair inside the length-filter window (Section 2.3.2,
@@ -24,9 +26,12 @@
  *     repeated token), and no set may be empty (Jaccard of two empty sets is
  *     undefined).  Violations are detected on the device and reported as
  *     BMJ_ERR_UNSORTED / BMJ_ERR_NEG_TOKEN / BMJ_ERR_EMPTY_SET.
- *   - Thresholds are exact rationals p/q with 0 < p <= q; "similar" means
- *     J(x, y) >= p/q, decided in integers as |x&y|*(p+q) >= p*(|x|+|y|)
- *     (Table 1).  No floating point is used anywhere on the path.
+ *   - Thresholds are exact rationals p/q (0 < p <= q; Overlap counts tokens
+ *     and allows p > q); "similar" means sim(x, y) >= p/q, decided in
+ *     integers, e.g. Jaccard as |x&y|*(p+q) >= p*(|x|+|y|) (Table 1).  Only
+ *     Cosine's smallest passing overlap starts from a floating-point estimate,
+ *     which exact 128-bit integer arithmetic then corrects, so every decision
+ *     is exact.
  *   - Bitmaps have b bits, b a multiple of 64 in [64, 4096]; bit k of a set's
  *     bitmap is bit (k % 64) of 64-bit word k / 64.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
