@@ -25,8 +25,10 @@ def small_setup(seed=0, n=20_000, nq=400):
     return off, tok, arr, qoff, qtok, p, q
 
 
-@pytest.mark.parametrize("b", [64, 128])
+@pytest.mark.parametrize("b", [64, 128, 256, 192])
 def test_index_query_matches_oracle(b):
+    # b = 64, 128, 256 keep the probe's bitmap in registers in the query filter;
+    # b = 192 takes the filter's path for any width
     off, tok, arr, qoff, qtok, p, q = small_setup(seed=b)
     idx = _bmj.Index(torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda(), b=b)
     assert len(idx) == len(off) - 1
