@@ -228,8 +228,9 @@ constexpr int kBatchAlu = W == 1 ? kAluRowsW1 : 0;
 #endif
 
 template <int W, int R, int CS, bool kCos>
-__global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS : 7)) k_filter_batch_w(const BatchFilterArgs a, int64_t t0,
-                                                         int64_t t1, unsigned long long *counter) {
+__global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS : 7))
+    k_filter_batch_w(const BatchFilterArgs a, int64_t t0, int64_t t1,
+                     unsigned long long *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     StageState stg;
