@@ -126,12 +126,16 @@ template <typename K, typename V, bool kHasVals>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const K *keys_in, const V *vals_in,
                                                             K *keys_out, V *vals_out, int64_t n,
                                                             int shift,
-                                                            const uint32_t *digit_offsets) {
+                                                            const uint32_t *digit_offsets,
+                                                            const uint32_t *chunk_offsets) {
     __shared__ uint32_t warp_hist[kWarps][257];
     __shared__ uint32_t block_base[256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = threadIdx.x; k < kWarps * 257; k += kThreads) (&warp_hist[0][0])[k] = 0;
-    block_base[threadIdx.x] = digit_offsets[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+    {  // this block's start for its digit: the chunk-local scan plus its chunk's offset
+        const int64_t h = (int64_t)threadIdx.x * gridDim.x + blockIdx.x;
+        block_base[threadIdx.x] = digit_offsets[h] + (chunk_offsets ? chunk_offsets[h / kTile] : 0u);
+    }
     __syncthreads();
     const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)warp * 32 * kItems;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -212,6 +216,8 @@ int radix_impl(const K *keys_in, const V *vals_in, K *keys_out, V *vals_out, int
     int st = arena.alloc(&tk, (size_t)n);
     if (!st && kHasVals) st = arena.alloc(&tv, (size_t)n);
     if (!st) st = arena.alloc(&hist, (size_t)tiles * 256);
+    uint32_t *csum = nullptr;  // totals of the histogram's scan chunks
+    if (!st) st = arena.alloc(&csum, (size_t)((tiles * 256 + kTile - 1) / kTile));
     if (st) return st;
     const K *src_k = keys_in;
     const V *src_v = vals_in;
@@ -222,10 +228,20 @@ int radix_impl(const K *keys_in, const V *vals_in, K *keys_out, V *vals_out, int
         V *dst_v = to_out ? vals_out : tv;
         const int shift = 8 * pass;
         BMJ_LAUNCH(k_radix_hist<K>, (unsigned)tiles, kThreads, 0, s, src_k, n, shift, hist);
-        st = scan_impl<uint32_t>(hist, hist, tiles * 256, nullptr, arena, s);
-        if (st) return st;
+        // The digit-major histogram is scanned in chunks of kTile entries; the
+        // chunk totals are scanned on their own, and the scatter adds a chunk's
+        // offset itself (one launch fewer per pass than a full scan).
+        const int64_t m = tiles * 256;
+        if (m <= kTile) {
+            BMJ_LAUNCH(k_scan_tiles<uint32_t>, 1u, kThreads, 0, s, hist, hist, m, csum);
+        } else {
+            BMJ_LAUNCH(k_scan_tiles<uint32_t>, (unsigned)((m + kTile - 1) / kTile), kThreads, 0, s,
+                       hist, hist, m, csum);
+            st = scan_impl<uint32_t>(csum, csum, (m + kTile - 1) / kTile, nullptr, arena, s);
+            if (st) return st;
+        }
         BMJ_LAUNCH((k_radix_scatter<K, V, kHasVals>), (unsigned)tiles, kThreads, 0, s, src_k,
-                   src_v, dst_k, dst_v, n, shift, hist);
+                   src_v, dst_k, dst_v, n, shift, hist, m <= kTile ? nullptr : csum);
         src_k = dst_k;
         src_v = dst_v;
     }
