@@ -98,9 +98,11 @@ __global__ void __launch_bounds__(kScanProbes)
                          const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
                          const int64_t *__restrict__ size_cum, int max_size, int64_t n,
                          int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
-                         int64_t *__restrict__ items, int sim, int chunk) {
+                         int64_t *__restrict__ items, int sim, int chunk,
+                         unsigned long long *__restrict__ ctr) {
     __shared__ int64_t warp_sum[kScanProbes / 32];
     const int x = threadIdx.x, lane = x & 31, w = x >> 5;
+    if (x < 2) ctr[x] = 0;  // the batch's survivor and result counters
     int64_t c = 0;
     if (x < nq)
         c = probe_window(poff, pp, pq, size_cum, max_size, n, sim, chunk, x, &wlo[x], &whi[x]);
@@ -279,7 +281,11 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     int64_t q_cap = 0, tok_cap = 0, pair_cap = 0;
-    // pinned host staging
+    // pinned host staging: a batch's offsets, thresholds and tokens packed
+    // into h_in, copied to d_in in one transfer (the pointers below point into
+    // them, laid out for the batch by stage)
+    unsigned char *h_in = nullptr, *d_in = nullptr;
+    int64_t in_bytes = 0;
     int64_t *h_off = nullptr;
     int32_t *h_tok = nullptr;
     uint32_t *h_p = nullptr, *h_q = nullptr;
@@ -305,17 +311,11 @@ struct Slot {
 
 void free_slot(Slot &s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    cudaFreeHost(s.h_off);
-    cudaFreeHost(s.h_tok);
-    cudaFreeHost(s.h_p);
-    cudaFreeHost(s.h_q);
+    cudaFreeHost(s.h_in);
     cudaFreeHost(s.h_ctr);
     cudaFreeHost(s.h_keys);
     cudaFreeHost(s.h_bounds);
-    cudaFree(s.d_off);
-    cudaFree(s.d_tok);
-    cudaFree(s.d_p);
-    cudaFree(s.d_q);
+    cudaFree(s.d_in);
     cudaFree(s.d_pbm);
     cudaFree(s.d_lo);
     cudaFree(s.d_hi);
@@ -335,19 +335,15 @@ int alloc_slot(Slot &s, int64_t q_cap, int64_t tok_cap, int64_t pair_cap, int W)
     s.q_cap = q_cap;
     s.tok_cap = tok_cap;
     s.pair_cap = pair_cap;
+    const size_t in_cap = (size_t)(q_cap + 1) * sizeof(int64_t) + 2 * (size_t)q_cap * sizeof(uint32_t) +
+                          (size_t)std::max<int64_t>(tok_cap, 1) * sizeof(int32_t);
     bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess &&
-              cudaMallocHost(&s.h_off, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
-              cudaMallocHost(&s.h_tok, std::max<int64_t>(tok_cap, 1) * sizeof(int32_t)) == cudaSuccess &&
-              cudaMallocHost(&s.h_p, q_cap * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMallocHost(&s.h_q, q_cap * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_in, in_cap) == cudaSuccess &&
               cudaMallocHost(&s.h_ctr, 2 * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&s.h_keys, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
               cudaMallocHost(&s.h_bounds, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
-              cudaMalloc(&s.d_off, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
-              cudaMalloc(&s.d_tok, std::max<int64_t>(tok_cap, 1) * sizeof(int32_t)) == cudaSuccess &&
-              cudaMalloc(&s.d_p, q_cap * sizeof(uint32_t)) == cudaSuccess &&
-              cudaMalloc(&s.d_q, q_cap * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_in, in_cap) == cudaSuccess &&
               cudaMalloc(&s.d_pbm, q_cap * W * sizeof(uint64_t)) == cudaSuccess &&
               cudaMalloc(&s.d_lo, q_cap * sizeof(int64_t)) == cudaSuccess &&
               cudaMalloc(&s.d_hi, q_cap * sizeof(int64_t)) == cudaSuccess &&
@@ -381,12 +377,9 @@ int64_t window_of(const bmj_index *idx, int64_t sx, uint32_t p, uint32_t q) {
 int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     cudaStream_t st = s.stream;
     const int64_t nq = s.nq;
-    BMJ_CHECK(cudaMemcpyAsync(s.d_off, s.h_off, (nq + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    if (s.ntok)
-        BMJ_CHECK(cudaMemcpyAsync(s.d_tok, s.h_tok, s.ntok * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    BMJ_CHECK(cudaMemcpyAsync(s.d_p, s.h_p, nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    BMJ_CHECK(cudaMemcpyAsync(s.d_q, s.h_q, nq * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    BMJ_CHECK(cudaMemsetAsync(s.d_ctr, 0, 2 * sizeof(unsigned long long), st));
+    BMJ_CHECK(cudaMemcpyAsync(s.d_in, s.h_in, s.in_bytes, cudaMemcpyHostToDevice, st));
+    if (nq > kScanProbes)  // (the one-block window kernel clears them otherwise)
+        BMJ_CHECK(cudaMemsetAsync(s.d_ctr, 0, 2 * sizeof(unsigned long long), st));
     int rc = launch_gather_build(nullptr, s.d_off, s.d_tok, nullptr, nullptr, s.d_pbm, nq, idx->b,
                                  idx->method, st);
     if (rc) return rc;
@@ -396,7 +389,7 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     if (nq <= kScanProbes) {  // windows and their scan in one launch
         BMJ_LAUNCH(k_probe_windows_scan, 1, kScanProbes, 0, st, s.d_off, nq, s.d_p, s.d_q,
                    idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim,
-                   chunk);
+                   chunk, s.d_ctr);
     } else {
         BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q,
                    idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim,
@@ -478,6 +471,17 @@ void stage(Slot &s, const bmj_collection *qc, const uint32_t *p, const uint32_t 
            const int64_t *ids, int64_t m) {
     s.ids.assign(ids, ids + m);
     s.nq = m;
+    // packed layout: offsets (m + 1 int64), p (m), q (m), then the tokens
+    const size_t o_p = (size_t)(m + 1) * sizeof(int64_t), o_q = o_p + m * sizeof(uint32_t),
+                 o_t = o_q + m * sizeof(uint32_t);
+    s.h_off = reinterpret_cast<int64_t *>(s.h_in);
+    s.h_p = reinterpret_cast<uint32_t *>(s.h_in + o_p);
+    s.h_q = reinterpret_cast<uint32_t *>(s.h_in + o_q);
+    s.h_tok = reinterpret_cast<int32_t *>(s.h_in + o_t);
+    s.d_off = reinterpret_cast<int64_t *>(s.d_in);
+    s.d_p = reinterpret_cast<uint32_t *>(s.d_in + o_p);
+    s.d_q = reinterpret_cast<uint32_t *>(s.d_in + o_q);
+    s.d_tok = reinterpret_cast<int32_t *>(s.d_in + o_t);
     s.h_off[0] = 0;
     int64_t t = 0;
     for (int64_t k = 0; k < m; k++) {
@@ -490,6 +494,7 @@ void stage(Slot &s, const bmj_collection *qc, const uint32_t *p, const uint32_t 
         s.h_q[k] = q[x];
     }
     s.ntok = t;
+    s.in_bytes = (int64_t)(o_t + t * sizeof(int32_t));
 }
 
 }  // namespace
