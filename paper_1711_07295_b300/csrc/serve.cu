@@ -312,8 +312,7 @@ struct Slot {
 void free_slot(Slot &s) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     cudaFreeHost(s.h_in);
-    cudaFreeHost(s.h_ctr);
-    cudaFreeHost(s.h_keys);
+    cudaFreeHost(s.h_ctr);  // (h_keys lives in the same block)
     cudaFreeHost(s.h_bounds);
     cudaFree(s.d_in);
     cudaFree(s.d_pbm);
@@ -321,10 +320,9 @@ void free_slot(Slot &s) {
     cudaFree(s.d_hi);
     cudaFree(s.d_items);
     cudaFree(s.d_queue);
-    cudaFree(s.d_keys);
+    cudaFree(s.d_ctr);  // (d_keys lives in the same block)
     cudaFree(s.d_sorted);
     cudaFree(s.d_bounds);
-    cudaFree(s.d_ctr);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
     cudaGetLastError();
@@ -340,8 +338,7 @@ int alloc_slot(Slot &s, int64_t q_cap, int64_t tok_cap, int64_t pair_cap, int W)
     bool ok = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) == cudaSuccess &&
               cudaMallocHost(&s.h_in, in_cap) == cudaSuccess &&
-              cudaMallocHost(&s.h_ctr, 2 * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMallocHost(&s.h_keys, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMallocHost(&s.h_ctr, (2 + pair_cap) * sizeof(uint64_t)) == cudaSuccess &&
               cudaMallocHost(&s.h_bounds, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
               cudaMalloc(&s.d_in, in_cap) == cudaSuccess &&
               cudaMalloc(&s.d_pbm, q_cap * W * sizeof(uint64_t)) == cudaSuccess &&
@@ -349,15 +346,17 @@ int alloc_slot(Slot &s, int64_t q_cap, int64_t tok_cap, int64_t pair_cap, int W)
               cudaMalloc(&s.d_hi, q_cap * sizeof(int64_t)) == cudaSuccess &&
               cudaMalloc(&s.d_items, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
               cudaMalloc(&s.d_queue, pair_cap * sizeof(uint2)) == cudaSuccess &&
-              cudaMalloc(&s.d_keys, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMalloc(&s.d_ctr, (2 + pair_cap) * sizeof(uint64_t)) == cudaSuccess &&
               cudaMalloc(&s.d_sorted, pair_cap * sizeof(uint64_t)) == cudaSuccess &&
-              cudaMalloc(&s.d_bounds, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess &&
-              cudaMalloc(&s.d_ctr, 2 * sizeof(unsigned long long)) == cudaSuccess;
+              cudaMalloc(&s.d_bounds, (q_cap + 1) * sizeof(int64_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_slot(s);
         return BMJ_ERR_OOM;
     }
+    // the result keys follow the two counters in the same block, host and device
+    s.h_keys = reinterpret_cast<uint64_t *>(s.h_ctr + 2);
+    s.d_keys = reinterpret_cast<uint64_t *>(s.d_ctr + 2);
     return BMJ_OK;
 }
 
@@ -418,10 +417,11 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     BMJ_LAUNCH(k_query_verify, vblocks, 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
                s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
                &s.d_ctr[1], idx->sim);
-    BMJ_CHECK(cudaMemcpyAsync(s.h_ctr, s.d_ctr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    // the first keys come back with the counters: a batch with few results then
-    // finishes on the host without a second round trip (finish_on_host)
-    BMJ_CHECK(cudaMemcpyAsync(s.h_keys, s.d_keys, std::min(s.pair_cap, kEagerKeys) * sizeof(uint64_t),
+    // the counters and the first result keys, adjacent on both sides, come back in
+    // one copy: a batch with few results then finishes on the host without a
+    // second round trip (finish_on_host)
+    BMJ_CHECK(cudaMemcpyAsync(s.h_ctr, s.d_ctr,
+                              (2 + std::min(s.pair_cap, kEagerKeys)) * sizeof(uint64_t),
                               cudaMemcpyDeviceToHost, st));
     BMJ_CHECK(cudaEventRecord(s.done, st));
     A.release();
