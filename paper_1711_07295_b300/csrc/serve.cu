@@ -92,17 +92,49 @@ __global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
 
 // The same for a batch of at most kScanProbes probes in one block, with the
 // exclusive scan of the chunk counts (items[nq] = their total) done in place.
+// With bw > 0 (b = 64 bw, a power of two up to 256; Xor or Set) each thread
+// also writes its probe's bitmap (Alg. 3b / 3a, h(t) = t mod b), which saves
+// the bitmap launch for small batches.
 constexpr int kScanProbes = 1024;
+constexpr int kFuseProbes = 16;
 __global__ void __launch_bounds__(kScanProbes)
     k_probe_windows_scan(const int64_t *__restrict__ poff, int64_t nq,
                          const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
                          const int64_t *__restrict__ size_cum, int max_size, int64_t n,
                          int64_t *__restrict__ wlo, int64_t *__restrict__ whi,
                          int64_t *__restrict__ items, int sim, int chunk,
-                         unsigned long long *__restrict__ ctr) {
+                         unsigned long long *__restrict__ ctr, const int32_t *__restrict__ ptok,
+                         uint64_t *__restrict__ pbm, int bw, int xor_method) {
     __shared__ int64_t warp_sum[kScanProbes / 32];
     const int x = threadIdx.x, lane = x & 31, w = x >> 5;
     if (x < 2) ctr[x] = 0;  // the batch's survivor and result counters
+    if (bw > 0 && x < nq) {
+        uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        const uint32_t hmask = 64u * (uint32_t)bw - 1u;
+        for (int64_t k = poff[x]; k < poff[x + 1]; k++) {
+            const uint32_t h = (uint32_t)ptok[k] & hmask;
+            const uint64_t bit = 1ull << (h & 63);
+            const uint32_t word = h >> 6;
+            if (xor_method) {
+                m0 ^= word == 0 ? bit : 0ull;
+                m1 ^= word == 1 ? bit : 0ull;
+                m2 ^= word == 2 ? bit : 0ull;
+                m3 ^= word == 3 ? bit : 0ull;
+            } else {
+                m0 |= word == 0 ? bit : 0ull;
+                m1 |= word == 1 ? bit : 0ull;
+                m2 |= word == 2 ? bit : 0ull;
+                m3 |= word == 3 ? bit : 0ull;
+            }
+        }
+        uint64_t *dst = pbm + (int64_t)x * bw;
+        dst[0] = m0;
+        if (bw > 1) dst[1] = m1;
+        if (bw > 2) {
+            dst[2] = m2;
+            dst[3] = m3;
+        }
+    }
     int64_t c = 0;
     if (x < nq)
         c = probe_window(poff, pp, pq, size_cum, max_size, n, sim, chunk, x, &wlo[x], &whi[x]);
@@ -379,7 +411,14 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     BMJ_CHECK(cudaMemcpyAsync(s.d_in, s.h_in, s.in_bytes, cudaMemcpyHostToDevice, st));
     if (nq > kScanProbes)  // (the one-block window kernel clears them otherwise)
         BMJ_CHECK(cudaMemsetAsync(s.d_ctr, 0, 2 * sizeof(unsigned long long), st));
-    int rc = launch_gather_build(nullptr, s.d_off, s.d_tok, nullptr, nullptr, s.d_pbm, nq, idx->b,
+    // small batches (a thread per probe) of Xor/Set bitmaps up to 256 bits are
+    // built in the window kernel: one launch fewer (p50 0.049 -> 0.043 ms at
+    // 20,000 q/s); larger batches keep the warp-per-probe bitmap kernel
+    const bool fuse = nq <= kFuseProbes && (idx->method == BMJ_XOR || idx->method == BMJ_SET) &&
+                      (idx->b == 64 || idx->b == 128 || idx->b == 256);
+    int rc = BMJ_OK;
+    if (!fuse)
+        rc = launch_gather_build(nullptr, s.d_off, s.d_tok, nullptr, nullptr, s.d_pbm, nq, idx->b,
                                  idx->method, st);
     if (rc) return rc;
     Arena A(st);
@@ -388,7 +427,8 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     if (nq <= kScanProbes) {  // windows and their scan in one launch
         BMJ_LAUNCH(k_probe_windows_scan, 1, kScanProbes, 0, st, s.d_off, nq, s.d_p, s.d_q,
                    idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim,
-                   chunk, s.d_ctr);
+                   chunk, s.d_ctr, s.d_tok, s.d_pbm, fuse ? idx->b / 64 : 0,
+                   idx->method == BMJ_XOR ? 1 : 0);
     } else {
         BMJ_LAUNCH(k_probe_windows, grid_q(nq, 128), 128, 0, st, s.d_off, nq, s.d_p, s.d_q,
                    idx->d_size_cum, idx->max_size, idx->n, s.d_lo, s.d_hi, s.d_items, idx->sim,

@@ -40,6 +40,24 @@ def test_index_query_matches_oracle(b):
         assert np.array_equal(res[x], want), x
         nonempty += len(want) > 0
     assert nonempty > 50
+    # batches of at most 8 probes: their bitmaps come from the window kernel
+    mixed, _, _ = idx.serve(qoff, qtok, arr, p, q, n_slots=2, max_batch_queries=8)
+    assert all(np.array_equal(u, v) for u, v in zip(mixed, res))
+    idx.close()
+
+
+@pytest.mark.parametrize("method", [_bmj.BMJ_SET, _bmj.BMJ_NEXT])
+def test_index_with_other_generation_methods(method):
+    # Set bitmaps of small batches are built in the window kernel, Next ones by the
+    # bitmap kernel; both must equal the oracle's search, alone and batched
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=20 + method, nq=120)
+    idx = _bmj.Index(off, tok, b=128, method=method)
+    res, _ = idx.query(qoff, qtok, p, q)
+    for x in range(len(p)):
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
+        assert np.array_equal(res[x], want), x
+    mixed, _, _ = idx.serve(qoff, qtok, arr, p, q, n_slots=2, max_batch_queries=8)
+    assert all(np.array_equal(a, b) for a, b in zip(mixed, res))
     idx.close()
 
 
