@@ -46,6 +46,29 @@ def test_bands_partition_the_oracle_join():
     assert np.array_equal(ma, a) and np.array_equal(mb, b)
 
 
+def test_size_buckets_are_row_bands_of_the_larger_set():
+    # the precision-by-size study joins one row band per size bucket: the bands
+    # tile the rows, and a pair lies in a bucket's band exactly when its larger
+    # set's size is in the bucket
+    from paper_1711_07295_b300.study_filter_ratio import size_band_rows
+    off, tok = I.random_collection(1_500, 300, 1, 40, seed=6, planted_frac=0.3)
+    sizes = np.diff(off)
+    bands = size_band_rows(sizes, (1, 4, 9, 10, 25, 60))
+    assert bands[0][2] == 0 and bands[-1][3] == len(sizes)
+    assert all(bands[k][3] == bands[k + 1][2] for k in range(len(bands) - 1))
+    a, b = O.self_join(off, tok, 1, 2)
+    larger = np.maximum(sizes[a], sizes[b])
+    total = 0
+    for lo, hi, r0, r1 in bands:
+        ba, bb = _band_of_pairs(off, a, b, r0, r1)
+        lb = np.maximum(sizes[ba], sizes[bb])
+        assert np.all(lb >= lo) and (hi is None or np.all(lb < hi))
+        want = np.count_nonzero((larger >= lo) & ((larger < hi) if hi is not None else True))
+        assert len(ba) == want
+        total += len(ba)
+    assert total == len(a) > 0
+
+
 @pytest.mark.parametrize("world", [1, 2, 5])
 def test_rs_split_partitions_the_oracle_rs_join(world):
     # the ranks' ranges of R cover R, carry about equal window pairs, and their
