@@ -165,7 +165,10 @@ __global__ void __launch_bounds__(kScanProbes)
 // takes four columns per step, their loads issued together; kW = 0: any width,
 // one column per lane and step.  A lane recomputes the smallest passing overlap
 // only when its column's size changes (sizes ascend along the window).
-template <int kW>
+// kV: a survivor is verified at once by its lane (the merge of k_query_verify)
+// and only similar pairs leave the kernel, as keys; the survivor queue is not
+// written (small batches, which then skip the verification launch).
+template <int kW, bool kV>
 __global__ void __launch_bounds__(256)
     k_query_filter(const uint64_t *__restrict__ pbm, const int64_t *__restrict__ poff,
                    const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
@@ -173,7 +176,10 @@ __global__ void __launch_bounds__(256)
                    const int64_t *__restrict__ item_off, int64_t nq,
                    const uint64_t *__restrict__ bm, const uint32_t *__restrict__ ssz, int W,
                    uint2 *__restrict__ queue, unsigned long long *__restrict__ qcount, int64_t qcap,
-                   int sim, int chunk) {
+                   int sim, int chunk, const int32_t *__restrict__ ptok,
+                   const int64_t *__restrict__ soff, const int32_t *__restrict__ stok,
+                   const uint32_t *__restrict__ perm, uint64_t *__restrict__ keys,
+                   unsigned long long *__restrict__ rcount) {
     constexpr int U = kW > 0 ? 4 : 1;  // columns per lane and step
     const int lane = threadIdx.x & 31;
     const int64_t n_items = item_off[nq];
@@ -232,8 +238,36 @@ __global__ void __launch_bounds__(256)
                     if (lane == 0) base = atomicAdd(qcount, (unsigned long long)__popc(ball));
                     base = __shfl_sync(kFullQ, base, 0);
                     const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
-                    if (sv && pos < (unsigned long long)qcap)
+                    if (!kV && sv && pos < (unsigned long long)qcap)
                         queue[pos] = make_uint2((uint32_t)x, (uint32_t)j);
+                    if (kV) {
+                        bool similar = false;
+                        uint64_t key = 0;
+                        if (sv) {
+                            const int32_t *xt = ptok + poff[x];
+                            const int32_t *yt = stok + soff[j];
+                            const int na = (int)sx, nb = (int)cs[u], nd = (int)last_need;
+                            int a = 0, b = 0, o = 0;
+                            while (a < na && b < nb) {
+                                if (o + min(na - a, nb - b) < nd) break;
+                                const int32_t xa = xt[a], yb = yt[b];
+                                o += (xa == yb);
+                                a += (xa <= yb);
+                                b += (yb <= xa);
+                                if (o >= nd) break;
+                            }
+                            similar = o >= nd;
+                            if (similar) key = ((uint64_t)x << 32) | perm[j];
+                        }
+                        const unsigned rb = __ballot_sync(kFullQ, similar);
+                        if (rb) {
+                            unsigned long long rbase = 0;
+                            if (lane == 0) rbase = atomicAdd(rcount, (unsigned long long)__popc(rb));
+                            rbase = __shfl_sync(kFullQ, rbase, 0);
+                            const unsigned long long rpos = rbase + __popc(rb & ((1u << lane) - 1u));
+                            if (similar && rpos < (unsigned long long)qcap) keys[rpos] = key;
+                        }
+                    }
                 }
             }
         }
@@ -443,20 +477,31 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
         (unsigned)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, (items_ub + 7) / 8));
     const unsigned vblocks =
         (unsigned)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (s.win + 255) / 256));
-#define BMJ_QUERY_FILTER(KW)                                                                  \
-    BMJ_LAUNCH(k_query_filter<KW>, fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q, s.d_lo,   \
-               s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],          \
-               s.pair_cap, idx->sim, chunk)
-    switch (idx->W) {
-        case 1: BMJ_QUERY_FILTER(1); break;
-        case 2: BMJ_QUERY_FILTER(2); break;
-        case 4: BMJ_QUERY_FILTER(4); break;
-        default: BMJ_QUERY_FILTER(0); break;
+    // a batch of at most kFuseProbes probes verifies its survivors inside the
+    // filter (one launch fewer); larger ones keep the thread-per-survivor kernel
+    const bool inline_verify = nq <= kFuseProbes;
+#define BMJ_QUERY_FILTER(KW, KV)                                                               \
+    BMJ_LAUNCH((k_query_filter<KW, KV>), fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,   \
+               s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],  \
+               s.pair_cap, idx->sim, chunk, s.d_tok, idx->soff, idx->stok, idx->perm, s.d_keys,   \
+               &s.d_ctr[1])
+    switch (idx->W * 2 + (inline_verify ? 1 : 0)) {
+        case 2: BMJ_QUERY_FILTER(1, false); break;
+        case 3: BMJ_QUERY_FILTER(1, true); break;
+        case 4: BMJ_QUERY_FILTER(2, false); break;
+        case 5: BMJ_QUERY_FILTER(2, true); break;
+        case 8: BMJ_QUERY_FILTER(4, false); break;
+        case 9: BMJ_QUERY_FILTER(4, true); break;
+        default:
+            if (inline_verify) BMJ_QUERY_FILTER(0, true);
+            else BMJ_QUERY_FILTER(0, false);
+            break;
     }
 #undef BMJ_QUERY_FILTER
-    BMJ_LAUNCH(k_query_verify, vblocks, 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
-               s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm, s.d_keys,
-               &s.d_ctr[1], idx->sim);
+    if (!inline_verify)
+        BMJ_LAUNCH(k_query_verify, vblocks, 256, 0, st, s.d_queue, &s.d_ctr[0], s.pair_cap,
+                   s.d_off, s.d_tok, s.d_p, s.d_q, idx->soff, idx->stok, idx->ssz, idx->perm,
+                   s.d_keys, &s.d_ctr[1], idx->sim);
     // the counters and the first result keys, adjacent on both sides, come back in
     // one copy: a batch with few results then finishes on the host without a
     // second round trip (finish_on_host)
