@@ -92,11 +92,12 @@ __global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
 
 // The same for a batch of at most kScanProbes probes in one block, with the
 // exclusive scan of the chunk counts (items[nq] = their total) done in place.
-// With bw > 0 (b = 64 bw, a power of two up to 256; Xor or Set) each thread
-// also writes its probe's bitmap (Alg. 3b / 3a, h(t) = t mod b), which saves
-// the bitmap launch for small batches.
+// With bw > 0 (b = 64 bw, a power of two up to 256; Xor or Set; at most
+// kFuseProbes probes) warp w also writes probe w's bitmap (Alg. 3b / 3a,
+// h(t) = t mod b), which saves the bitmap launch for small batches.
 constexpr int kScanProbes = 1024;
 constexpr int kFuseProbes = 16;
+static_assert(kFuseProbes <= kScanProbes / 32, "a warp per fused probe");
 __global__ void __launch_bounds__(kScanProbes)
     k_probe_windows_scan(const int64_t *__restrict__ poff, int64_t nq,
                          const uint32_t *__restrict__ pp, const uint32_t *__restrict__ pq,
@@ -108,10 +109,10 @@ __global__ void __launch_bounds__(kScanProbes)
     __shared__ int64_t warp_sum[kScanProbes / 32];
     const int x = threadIdx.x, lane = x & 31, w = x >> 5;
     if (x < 2) ctr[x] = 0;  // the batch's survivor and result counters
-    if (bw > 0 && x < nq) {
+    if (bw > 0 && w < nq) {  // warp w builds probe w's bitmap (nq <= kFuseProbes < 32 warps)
         uint64_t m0 = 0, m1 = 0, m2 = 0, m3 = 0;
         const uint32_t hmask = 64u * (uint32_t)bw - 1u;
-        for (int64_t k = poff[x]; k < poff[x + 1]; k++) {
+        for (int64_t k = poff[w] + lane; k < poff[w + 1]; k += 32) {
             const uint32_t h = (uint32_t)ptok[k] & hmask;
             const uint64_t bit = 1ull << (h & 63);
             const uint32_t word = h >> 6;
@@ -127,12 +128,26 @@ __global__ void __launch_bounds__(kScanProbes)
                 m3 |= word == 3 ? bit : 0ull;
             }
         }
-        uint64_t *dst = pbm + (int64_t)x * bw;
-        dst[0] = m0;
-        if (bw > 1) dst[1] = m1;
-        if (bw > 2) {
-            dst[2] = m2;
-            dst[3] = m3;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {  // Xor (Alg. 3b) and Or (Alg. 3a) are associative
+            const uint64_t o0 = __shfl_xor_sync(0xffffffffu, m0, d);
+            const uint64_t o1 = __shfl_xor_sync(0xffffffffu, m1, d);
+            const uint64_t o2 = __shfl_xor_sync(0xffffffffu, m2, d);
+            const uint64_t o3 = __shfl_xor_sync(0xffffffffu, m3, d);
+            if (xor_method) {
+                m0 ^= o0; m1 ^= o1; m2 ^= o2; m3 ^= o3;
+            } else {
+                m0 |= o0; m1 |= o1; m2 |= o2; m3 |= o3;
+            }
+        }
+        if (lane == 0) {
+            uint64_t *dst = pbm + (int64_t)w * bw;
+            dst[0] = m0;
+            if (bw > 1) dst[1] = m1;
+            if (bw > 2) {
+                dst[2] = m2;
+                dst[3] = m3;
+            }
         }
     }
     int64_t c = 0;
