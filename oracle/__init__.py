@@ -17,6 +17,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
       histogram, survivors == results when bitmaps are exact, Theorem 1
       soundness (results never exceed what brute force finds);
   join_rows / search -- against self_join / brute force on small inputs.
+  window_pairs -- against the window count of filter_counts and a brute-force
+      count over every pair of sizes with Python integers, for every function.
   rs_join / rs_filter_counts (Section 2.1) -- brute force with Python ``set``
       and exact fractions; the cross pairs of the self-join of R and S
       concatenated; the self-join itself when S is R (pairs r < s); window
@@ -102,6 +104,8 @@ def lib():
         L.oracle_rs_prefix_counts.argtypes = [i64, i64p, i32p, i64, i64p, i32p, C.c_int, i64, i64,
                                               C.c_int, C.c_int, i64p]
         L.oracle_rs_prefix_counts.restype = None
+        L.oracle_window_pairs_hist.argtypes = [i64p, i64, C.c_int, i64, i64]
+        L.oracle_window_pairs_hist.restype = i64
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         L.oracle_free.argtypes = [C.c_void_p]
@@ -297,9 +301,22 @@ def filter_counts(offsets, tokens, p: int, q: int, b: int, method: int, sim: int
     return int(cnt[0]), int(cnt[1]), int(cnt[2])
 
 
+def window_pairs(sizes, p: int, q: int, sim: int = JACCARD) -> int:
+    """Pairs inside the length window (Table 2) of a self-join of sets with these sizes:
+    the window count of ``filter_counts``, from the size histogram alone."""
+    sizes = np.asarray(sizes, dtype=np.int64)
+    if len(sizes) == 0:
+        return 0
+    hist = np.bincount(sizes).astype(np.int64)
+    w = int(lib().oracle_window_pairs_hist(_p(hist, C.c_int64), len(hist), sim, p, q))
+    if w < 0:
+        raise ValueError("negative size")
+    return w
+
+
 __all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "JACCARD", "COSINE", "DICE", "OVERLAP",
            "overlap", "similar", "similar_sim", "in_window", "self_join",
            "join_rows", "join_rows_window", "rs_join", "rs_filter_counts", "rs_prefix_counts",
            "search", "bitmap",
            "bitmaps", "hamming", "upper_bound",
-           "filter_counts", "prefix_counts", "combined_method", "num_threads", "lib"]
+           "filter_counts", "prefix_counts", "window_pairs", "combined_method", "num_threads", "lib"]

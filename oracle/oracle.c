@@ -34,6 +34,8 @@
  *   oracle_bitmap         Alg. 3a (Set), 3b (Xor), 3c (Next), literally
  *   oracle_filter_counts  the GPU algorithm (Alg. 6): size order, length
  *                         window, Eq. 2 bound, then verification -- counted
+ *   oracle_window_pairs_hist  the window count of oracle_filter_counts from the
+ *                         size histogram alone (Table 2)
  *   oracle_prefix_counts  the same with the prefix filter (Section 2.2)
  *                         choosing the candidates inside the window
  *   oracle_rs_join        Eq. 1 between two collections R and S (an RS-join,
@@ -543,6 +545,28 @@ void oracle_filter_counts(int64_t n, const int64_t *off, const int32_t *tok, int
     counts[1] = surv;
     counts[2] = res;
     free(ord); free(sz); free(bm);
+}
+
+/*
+ * Window pairs of a self-join from its size histogram alone (the count of
+ * step 2 of oracle_filter_counts, Alg. 6's inner loop, without the sets):
+ * hist[s] sets have size s (0 <= s < n_sizes).  Two sets of sizes t <= s form
+ * a window pair iff oracle_in_window(t, s) (Table 2); sets of equal size pair
+ * C(hist[s], 2) times when the size is in its own window, sets of different
+ * sizes hist[t] * hist[s] times.  Returns -1 on a negative count.
+ */
+int64_t oracle_window_pairs_hist(const int64_t *hist, int64_t n_sizes, int sim, int64_t p,
+                                 int64_t q)
+{
+    int64_t total = 0;
+    for (int64_t s = 1; s < n_sizes; s++) {
+        if (hist[s] < 0) return -1;
+        if (hist[s] == 0) continue;
+        if (oracle_in_window(sim, s, s, p, q)) total += hist[s] * (hist[s] - 1) / 2;
+        for (int64_t t = 1; t < s; t++)
+            if (hist[t] > 0 && oracle_in_window(sim, t, s, p, q)) total += hist[t] * hist[s];
+    }
+    return total;
 }
 
 /*

@@ -818,3 +818,36 @@ def test_rs_prefix_filter_candidates(sim, p, q):
     w, s_w, r_w = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
     assert r == r_w == len(O.rs_join(ro, rt, so, st, p, q, sim=sim)[0]) and r > 0
     assert r <= s <= s_w and c <= w
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 3, 5), (O.JACCARD, 19, 20),
+                                     (O.JACCARD, 1, 1), (O.COSINE, 3, 4), (O.DICE, 7, 10),
+                                     (O.OVERLAP, 4, 1), (O.OVERLAP, 1, 3)])
+def test_window_pairs_from_the_size_histogram(sim, p, q):
+    # The closed form counts, for every pair of sizes t <= s, the set pairs those sizes
+    # give; pinned to (1) every pair of sets compared against Table 2's lower bound in
+    # exact fractions, (2) the window count of filter_counts (which walks the sets in
+    # size order), and (3) the empty and one-set collections.
+    off, tok = I.random_collection(450, 80, 1, 40, seed=80 + sim + p, planted_frac=0.1)
+    sizes = np.diff(off).tolist()
+    t = Fraction(p, q)
+    lower = {O.OVERLAP: lambda b: t, O.JACCARD: lambda b: b * t,
+             O.COSINE: lambda b: b * t * t, O.DICE: lambda b: b * t / (2 - t)}[sim]
+    brute = sum(1 for x, y in itertools.combinations(sizes, 2)
+                if min(x, y) >= lower(max(x, y)))
+    assert O.window_pairs(sizes, p, q, sim) == brute
+    w, _, _ = O.filter_counts(off, tok, p, q, 64, O.XOR, sim=sim)
+    assert w == brute
+    assert O.window_pairs([], p, q, sim) == 0 and O.window_pairs([7], p, q, sim) == 0
+
+
+def test_window_pairs_of_equal_sizes_and_large_counts():
+    # n sets of one size are all inside each other's window: C(n, 2) pairs, also for
+    # counts whose product needs more than 32 bits
+    assert O.window_pairs([5] * 1000, 1, 2) == 1000 * 999 // 2
+    sizes = np.concatenate([np.full(3_000_000, 10), np.full(2_000_000, 12)])
+    # 10 and 12 pair at 4/5 (10 >= 9.6), not at 9/10 (10 < 10.8)
+    n10, n12 = 3_000_000, 2_000_000
+    same = n10 * (n10 - 1) // 2 + n12 * (n12 - 1) // 2
+    assert O.window_pairs(sizes, 4, 5) == same + n10 * n12
+    assert O.window_pairs(sizes, 9, 10) == same
