@@ -19,6 +19,8 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   join_rows / search -- against self_join / brute force on small inputs.
   window_pairs -- against the window count of filter_counts and a brute-force
       count over every pair of sizes with Python integers, for every function.
+  rs_window_pairs -- against the window count of rs_filter_counts and a
+      brute-force count over every pair of R x S with exact fractions.
   rs_join / rs_filter_counts (Section 2.1) -- brute force with Python ``set``
       and exact fractions; the cross pairs of the self-join of R and S
       concatenated; the self-join itself when S is R (pairs r < s); window
@@ -106,6 +108,8 @@ def lib():
         L.oracle_rs_prefix_counts.restype = None
         L.oracle_window_pairs_hist.argtypes = [i64p, i64, C.c_int, i64, i64]
         L.oracle_window_pairs_hist.restype = i64
+        L.oracle_rs_window_pairs_hist.argtypes = [i64p, i64, i64p, i64, C.c_int, i64, i64]
+        L.oracle_rs_window_pairs_hist.restype = i64
         L.oracle_num_threads.argtypes = []
         L.oracle_num_threads.restype = C.c_int
         L.oracle_free.argtypes = [C.c_void_p]
@@ -314,9 +318,24 @@ def window_pairs(sizes, p: int, q: int, sim: int = JACCARD) -> int:
     return w
 
 
+
+def rs_window_pairs(sizes_r, sizes_s, p: int, q: int, sim: int = JACCARD) -> int:
+    """Pairs of R x S inside the length window (Table 2), from the two size histograms:
+    the window count of ``rs_filter_counts`` (and of probe queries against a collection)."""
+    sr, ss = np.asarray(sizes_r, dtype=np.int64), np.asarray(sizes_s, dtype=np.int64)
+    if len(sr) == 0 or len(ss) == 0:
+        return 0
+    hr, hs = np.bincount(sr).astype(np.int64), np.bincount(ss).astype(np.int64)
+    w = int(lib().oracle_rs_window_pairs_hist(_p(hr, C.c_int64), len(hr), _p(hs, C.c_int64),
+                                              len(hs), sim, p, q))
+    if w < 0:
+        raise ValueError("negative size")
+    return w
+
+
 __all__ = ["XOR", "SET", "NEXT", "COMBINED", "METHODS", "JACCARD", "COSINE", "DICE", "OVERLAP",
            "overlap", "similar", "similar_sim", "in_window", "self_join",
            "join_rows", "join_rows_window", "rs_join", "rs_filter_counts", "rs_prefix_counts",
            "search", "bitmap",
            "bitmaps", "hamming", "upper_bound",
-           "filter_counts", "prefix_counts", "window_pairs", "combined_method", "num_threads", "lib"]
+           "filter_counts", "prefix_counts", "window_pairs", "rs_window_pairs", "combined_method", "num_threads", "lib"]

@@ -36,6 +36,7 @@
  *                         window, Eq. 2 bound, then verification -- counted
  *   oracle_window_pairs_hist  the window count of oracle_filter_counts from the
  *                         size histogram alone (Table 2)
+ *   oracle_rs_window_pairs_hist  the same for the pairs of R x S
  *   oracle_prefix_counts  the same with the prefix filter (Section 2.2)
  *                         choosing the candidates inside the window
  *   oracle_rs_join        Eq. 1 between two collections R and S (an RS-join,
@@ -565,6 +566,30 @@ int64_t oracle_window_pairs_hist(const int64_t *hist, int64_t n_sizes, int sim, 
         if (oracle_in_window(sim, s, s, p, q)) total += hist[s] * (hist[s] - 1) / 2;
         for (int64_t t = 1; t < s; t++)
             if (hist[t] > 0 && oracle_in_window(sim, t, s, p, q)) total += hist[t] * hist[s];
+    }
+    return total;
+}
+
+/*
+ * Window pairs of an RS-join (or of probe queries against a collection) from
+ * the two size histograms: hist_r[a] sets of R and hist_s[c] sets of S have
+ * sizes a and c; every pair of sizes inside the window of Table 2
+ * (oracle_in_window of the smaller and the larger size) gives
+ * hist_r[a] * hist_s[c] pairs.  Returns -1 on a negative count.
+ */
+int64_t oracle_rs_window_pairs_hist(const int64_t *hist_r, int64_t nr, const int64_t *hist_s,
+                                    int64_t ns, int sim, int64_t p, int64_t q)
+{
+    int64_t total = 0;
+    for (int64_t a = 1; a < nr; a++) {
+        if (hist_r[a] < 0) return -1;
+        if (hist_r[a] == 0) continue;
+        for (int64_t c = 1; c < ns; c++) {
+            if (hist_s[c] < 0) return -1;
+            if (hist_s[c] == 0) continue;
+            int64_t lo = a < c ? a : c, hi = a < c ? c : a;
+            if (oracle_in_window(sim, lo, hi, p, q)) total += hist_r[a] * hist_s[c];
+        }
     }
     return total;
 }

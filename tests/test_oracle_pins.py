@@ -851,3 +851,21 @@ def test_window_pairs_of_equal_sizes_and_large_counts():
     same = n10 * (n10 - 1) // 2 + n12 * (n12 - 1) // 2
     assert O.window_pairs(sizes, 4, 5) == same + n10 * n12
     assert O.window_pairs(sizes, 9, 10) == same
+
+
+@pytest.mark.parametrize("sim,p,q", [(O.JACCARD, 1, 2), (O.JACCARD, 9, 10), (O.COSINE, 3, 5),
+                                     (O.DICE, 3, 4), (O.OVERLAP, 3, 1)])
+def test_rs_window_pairs_from_the_size_histograms(sim, p, q):
+    # every pair of R x S compared against Table 2's lower bound in exact fractions, and
+    # the window count of rs_filter_counts
+    off, tok = I.random_collection(420, 90, 1, 45, seed=95 + sim + q, planted_frac=0.1)
+    ro, rt, so, st = _split(off, tok, 150)
+    sr, ss = np.diff(ro).tolist(), np.diff(so).tolist()
+    t = Fraction(p, q)
+    lower = {O.OVERLAP: lambda b: t, O.JACCARD: lambda b: b * t,
+             O.COSINE: lambda b: b * t * t, O.DICE: lambda b: b * t / (2 - t)}[sim]
+    brute = sum(1 for x in sr for y in ss if min(x, y) >= lower(max(x, y)))
+    assert O.rs_window_pairs(sr, ss, p, q, sim) == brute > 0
+    w, _, _ = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
+    assert w == brute
+    assert O.rs_window_pairs([], ss, p, q, sim) == 0 == O.rs_window_pairs(sr, [], p, q, sim)
