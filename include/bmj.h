@@ -438,8 +438,10 @@ int bmj_measure_popc_rate(void *stream, double *popc_per_s);
  *   call.  Every call shares the array: calls that overlap on the GPU (other
  *   streams or host threads) race and must be serialised by the caller.
  * Set-up: the first call on a device looks up the array's device address
- *   with that device current (cudaGetSymbolAddress); make that first call
- *   before any stream capture.
+ *   with that device current (cudaGetSymbolAddress).
+ * Synchronisation: every call copies the counters back and synchronises
+ *   `stream` before it returns, so it must not be called while a stream is
+ *   being captured into a CUDA graph.
  * Errors: BMJ_ERR_INVALID_ARG (NULL or misaligned pointers, bad b, p, q),
  *   BMJ_ERR_UNSORTED (sizes decrease), BMJ_ERR_EMPTY_SET (a size of 0),
  *   BMJ_ERR_TOO_LARGE, BMJ_ERR_OUTPUT_OVERFLOW, BMJ_ERR_CUDA.  The stream is

@@ -152,6 +152,12 @@ def test_full_batched_workload_row_sampled():
         sel = np.isin(a, rows) | np.isin(b, rows)
         assert np.array_equal(a[sel], ra) and np.array_equal(b[sel], rb), k
         assert jst[k]["results"] == len(a) <= jst[k]["survivors"] <= jst[k]["window_pairs"]
+    # every job's window pairs equal the oracle's count from its size histogram
+    sizes = np.diff(h_off)
+    for k in range(len(js) - 1):
+        lo, hi = int(js[k]), int(js[k + 1])
+        assert jst[k]["window_pairs"] == O.window_pairs(sizes[lo:hi], int(p[k]), int(q[k])), k
+    assert bst["window_pairs"] == sum(s["window_pairs"] for s in jst)
 
 
 def test_batch_cascade_on_and_off():

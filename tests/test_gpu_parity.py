@@ -343,8 +343,24 @@ def test_million_sets_row_sampled(million, p, q, b):
     key = a.astype(np.uint64) << np.uint64(32) | bb.astype(np.uint64)
     assert np.all(np.diff(key.astype(np.int64)) > 0)
     assert st["results"] == len(a) <= st["survivors"] <= st["window_pairs"]
+    assert st["window_pairs"] == O.window_pairs(sizes, p, q)
     sa, sb = sizes[a], sizes[bb]
     assert np.all(q * np.minimum(sa, sb) >= p * np.maximum(sa, sb))
+
+
+@pytest.mark.parametrize("b", [64, 128, 256])
+def test_million_sets_window_pairs_closed_form(million, b):
+    # The headline's numerator: the window pairs the Bitmap Filter evaluated at every
+    # threshold of the 1M workload equal the oracle's count from the size histogram
+    # (Table 2), at each bitmap width the benchmark times.
+    off, tok = million
+    d_off, d_tok = dev(off, tok)
+    sizes = np.diff(off)
+    for p, q in ((1, 2), (3, 4), (9, 10), (19, 20)):
+        r, _, st = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True)
+        r.release()
+        assert st["window_pairs"] == O.window_pairs(sizes, p, q), (p, q, b)
+        assert st["results"] <= st["survivors"] <= st["window_pairs"]
 
 
 @pytest.mark.parametrize("b", [64, 128, 256])
@@ -384,6 +400,8 @@ def test_ten_million_sets_row_sampled(ten_million, p, q):
     assert st["results"] == len(a) <= st["verified"] <= st["survivors"] <= st["window_pairs"]
     rng = np.random.default_rng(p + q)
     sizes = np.diff(off)
+    # the headline's numerator at its full size: 1.8e13 / 3.9e12 window pairs
+    assert st["window_pairs"] == O.window_pairs(sizes, p, q)
     rows = np.concatenate([rng.choice(len(sizes), 10, replace=False), np.argsort(sizes)[-2:],
                            np.nonzero(sizes == 1)[0][:2]])
     ra, rb = O.join_rows(off, tok, p, q, rows)

@@ -132,6 +132,12 @@ def test_full_served_workload_sampled():
     idx = _bmj.Index(off_d, tok_d, b=64)
     res, lat, st = idx.serve(qoff, qtok, arr, p, q)
     assert st["n_queries"] == 4000 and st["p99_ms"] > 0
+    # window pairs = every (probe, resident set) pair inside Table 2's two-sided window,
+    # counted by the oracle from the size histograms, one threshold at a time
+    psz, rsz = np.diff(qoff), np.diff(off)
+    want_win = sum(O.rs_window_pairs(psz[(p == pk) & (q == qk)], rsz, int(pk), int(qk))
+                   for pk, qk in set(zip(p.tolist(), q.tolist())))
+    assert st["window_pairs"] == want_win
     rng = np.random.default_rng(0)
     for x in rng.choice(4000, 24, replace=False):
         want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))

@@ -5,10 +5,12 @@ inside a fixed memory budget owned by another framework's pool, or a
 latency-critical serving loop where cudaMalloc/cudaFree and the device
 synchronisation they can cause are not allowed.  For them the library runs
 the same filter kernel as bmj_self_join with its scratch in a fixed device
-array.  This file checks that entry point through the C ABI against the
-existing bmj_self_join: the same survivor count, and after exact
-verification the same similar pairs, on two calls in a row (the second call
-reuses the scratch left by the first).  It is named to be collected last.
+array.  This file checks that entry point through the C ABI, on two calls in
+a row (the second call reuses the scratch left by the first), against the
+CPU oracle -- its survivor count equals the oracle's Bitmap Filter count
+(Alg. 6 with the Eq. 2 bound) and the survivors, verified exactly, give the
+oracle's pair list -- and against the existing bmj_self_join, which must
+agree with both.  It is named to be collected last.
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1711_07295_b300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -53,18 +56,24 @@ def call_noalloc(bm, d_sizes, n, b, p, q, cap):
 
 
 @pytest.mark.parametrize("b,p,q", [(64, 1, 2), (128, 4, 5), (256, 3, 5)])
-def test_noalloc_filter_matches_self_join_twice(b, p, q):
+def test_noalloc_filter_matches_oracle_twice(b, p, q):
     off, tok = I.random_collection(6000, 1500, 1, 40, seed=21 + b, planted_frac=0.1)
     sets = [tok[off[i]:off[i + 1]] for i in range(len(off) - 1)]
     order, bm, d_sizes = size_sorted(off, tok, b)
+    # the oracle's counts and pairs (Alg. 6 with Eq. 2; Eq. 1 over all pairs)
+    win, surv, res = O.filter_counts(off, tok, p, q, b, O.XOR)
+    oa, ob = O.self_join(off, tok, p, q)
+    want = set(zip(oa.tolist(), ob.tolist()))
+    assert res == len(want) > 0
+    # the existing entry point agrees with the oracle on the same collection
     ref_a, ref_b, ref_st = _bmj.bmj_self_join(off, tok, p, q, b=b, method=_bmj.BMJ_XOR)
-    want = set(zip(ref_a.tolist(), ref_b.tolist()))
-    cap = ref_st["survivors"] + 64
+    assert ref_st["survivors"] == surv and set(zip(ref_a.tolist(), ref_b.tolist())) == want
+    cap = surv + 64
     previous = None
     for _call in range(2):
         st, count, out = call_noalloc(bm, d_sizes, len(order), b, p, q, cap)
         assert st == _bmj.BMJ_OK, _bmj.bmj_strerror(st)
-        assert count == ref_st["survivors"]
+        assert count == surv == ref_st["survivors"]
         pairs = out[:2 * count].cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
         assert np.all(pairs[:, 1] < pairs[:, 0])
         oi, oj = order[pairs[:, 0]], order[pairs[:, 1]]
@@ -86,8 +95,9 @@ def test_noalloc_filter_errors():
     off, tok = I.random_collection(3000, 800, 1, 30, seed=5, planted_frac=0.1)
     order, bm, d_sizes = size_sorted(off, tok, 64)
     n = len(order)
-    _, _, ref = _bmj.bmj_self_join(off, tok, 1, 2, b=64)
-    assert ref["survivors"] > 10
+    _, surv, _ = O.filter_counts(off, tok, 1, 2, 64, O.XOR)
+    ref = {"survivors": surv}
+    assert surv > 10
     # output too small: full count reported, first out_cap pairs written
     st, count, out = call_noalloc(bm, d_sizes, n, 64, 1, 2, 10)
     assert st == _bmj.BMJ_ERR_OUTPUT_OVERFLOW and count == ref["survivors"]
