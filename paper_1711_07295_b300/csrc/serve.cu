@@ -97,6 +97,9 @@ __global__ void k_probe_windows(const int64_t *__restrict__ poff, int64_t nq,
 // h(t) = t mod b), which saves the bitmap launch for small batches.
 constexpr int kScanProbes = 1024;
 constexpr int kFuseProbes = 16;
+// window pairs of a small batch up to which its survivors are verified in the
+// filter's lanes (about two probes of the typical size against 2,000,000 sets)
+constexpr int64_t kInlineVerifyWindow = int64_t(1) << 22;
 static_assert(kFuseProbes <= kScanProbes / 32, "a warp per fused probe");
 __global__ void __launch_bounds__(kScanProbes)
     k_probe_windows_scan(const int64_t *__restrict__ poff, int64_t nq,
@@ -460,9 +463,9 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
     BMJ_CHECK(cudaMemcpyAsync(s.d_in, s.h_in, s.in_bytes, cudaMemcpyHostToDevice, st));
     if (nq > kScanProbes)  // (the one-block window kernel clears them otherwise)
         BMJ_CHECK(cudaMemsetAsync(s.d_ctr, 0, 2 * sizeof(unsigned long long), st));
-    // small batches (a thread per probe) of Xor/Set bitmaps up to 256 bits are
-    // built in the window kernel: one launch fewer (p50 0.049 -> 0.043 ms at
-    // 20,000 q/s); larger batches keep the warp-per-probe bitmap kernel
+    // the bitmaps of small batches (Xor/Set, up to 256 bits) are built in the
+    // window kernel, a warp per probe: one launch fewer (p50 0.049 -> 0.043 ms
+    // at 20,000 q/s); larger batches keep the separate warp-per-probe kernel
     const bool fuse = nq <= kFuseProbes && (idx->method == BMJ_XOR || idx->method == BMJ_SET) &&
                       (idx->b == 64 || idx->b == 128 || idx->b == 256);
     int rc = BMJ_OK;
@@ -492,9 +495,13 @@ int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
         (unsigned)std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, (items_ub + 7) / 8));
     const unsigned vblocks =
         (unsigned)std::min<int64_t>((int64_t)sms * 4, std::max<int64_t>(1, (s.win + 255) / 256));
-    // a batch of at most kFuseProbes probes verifies its survivors inside the
-    // filter (one launch fewer); larger ones keep the thread-per-survivor kernel
-    const bool inline_verify = nq <= kFuseProbes;
+    // a batch of at most kFuseProbes probes whose windows hold at most
+    // kInlineVerifyWindow pairs verifies its survivors inside the filter (one
+    // launch fewer): a lane merges the survivors it found while the rest of
+    // its warp waits, which is cheap while survivors are few per warp; larger
+    // batches and wide windows (many survivors at low thresholds) keep the
+    // thread-per-survivor kernel
+    const bool inline_verify = nq <= kFuseProbes && s.win <= kInlineVerifyWindow;
 #define BMJ_QUERY_FILTER(KW, KV)                                                               \
     BMJ_LAUNCH((k_query_filter<KW, KV>), fblocks, 256, 0, st, s.d_pbm, s.d_off, s.d_p, s.d_q,   \
                s.d_lo, s.d_hi, s.d_items, nq, idx->bm, idx->ssz, idx->W, s.d_queue, &s.d_ctr[0],  \

@@ -142,6 +142,20 @@ def test_full_served_workload_sampled():
     for x in rng.choice(4000, 24, replace=False):
         want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
         assert np.array_equal(res[x], want), x
+    # small batches at 1/2 whose windows are wide (millions of resident sets each):
+    # one probe (survivors verified inside the filter) and four (the window total
+    # is above the in-filter bound, so a verification kernel runs) give the oracle's ids
+    wide = np.nonzero((psz >= 8) & (psz <= 16))[0][:4]
+    for sel in (wide[:1], wide):
+        o2 = np.zeros(len(sel) + 1, np.int64)
+        o2[1:] = np.cumsum(psz[sel])
+        t2 = np.concatenate([qtok[qoff[x]:qoff[x + 1]] for x in sel])
+        half = np.ones(len(sel), np.uint32)
+        got, st2 = idx.query(o2, t2, half, 2 * half)
+        assert st2["window_pairs"] == O.rs_window_pairs(psz[sel], rsz, 1, 2) > 1_000_000 * len(sel)
+        for k, x in enumerate(sel):
+            want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, 1, 2)
+            assert np.array_equal(got[k], want), x
     idx.close()
 
 
