@@ -565,7 +565,7 @@ def run_million(args, dev):
             ev0.record(stream)
             for thr in THRESHOLDS_1M:
                 st = join(thr[0], thr[1], b, caps[thr], method=method)
-                for key in per[thr]:
+                for key in ("ms_total", "ms_filter", "ms_verify"):
                     per[thr][key] += st[key]
                 per[thr]["st"] = st
             ev1.record(stream)
