@@ -137,9 +137,12 @@ typedef struct {
     int32_t candidates;        /* bmj_self_join, bmj_rs_join: BMJ_CAND_WINDOW (default) filters
                                   every pair of the length window; BMJ_CAND_PREFIX filters only the window
                                   pairs whose prefixes share a token (prefix filter, Section 2.2)
-                                  -- fewer pairs at high thresholds, same result; it falls back
-                                  to the window when its candidates do not fit in memory, and
-                                  needs row_begin = row_end = 0 and cutoff = 0 */
+                                  -- fewer pairs at high thresholds, same result.  Its candidates
+                                  are expanded in ranges of at most queue_cap slots (0: a quarter
+                                  of the free device memory), each filtered and verified before
+                                  the next, so any number of them fits; it falls back to the
+                                  window only when the prefix index itself does not fit.  Needs
+                                  row_begin = row_end = 0 and cutoff = 0 */
     int32_t cutoff;            /* bmj_self_join, bmj_rs_join: the cutoff point of Section 3.5.
                                   0 (default) = none, every window pair meets the Bitmap Filter
                                   (the paper's GPU setting); n > 0 = a pair whose larger set has
@@ -175,7 +178,11 @@ typedef struct {
     float   reserved_f;
     int64_t candidates;     /* BMJ_CAND_PREFIX: distinct prefix-filter candidates, which the
                                Bitmap Filter then evaluated (survivors counts those passing it);
-                               0 in window mode; -1 when prefix mode fell back to the window */
+                               0 in window mode; -1 when prefix mode fell back to the window
+                               (only when the prefix index itself does not fit in memory) */
+    int64_t candidate_slots;/* BMJ_CAND_PREFIX: (rank, pair) slots the candidates were expanded
+                               from (a pair sharing k prefix tokens has k slots); they go
+                               through a buffer of fixed size in filter_passes ranges */
 } bmj_stats;
 
 /* Counters and stage times of one bmj_self_join_batch call. */

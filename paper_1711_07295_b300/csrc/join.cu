@@ -223,48 +223,105 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
         stl.window_pairs = hv[0];
         const int64_t n_items = hv[1];
 
-        // ---- candidates from the prefix filter (Section 2.2), if asked for ----
         uint64_t *keys = nullptr;
+        int64_t res_cap = 0;
+        // Appends r result keys from src to the growing result buffer.
+        auto append = [&](const uint64_t *src, int64_t r) -> int {
+            if (n_res + r > res_cap) {
+                const int64_t ncap = std::max(2 * res_cap, n_res + r);
+                uint64_t *grown = nullptr;
+                int rc = A.alloc(&grown, (size_t)ncap);
+                if (rc) return rc;
+                if (n_res)
+                    BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
+                                              cudaMemcpyDeviceToDevice, s));
+                if (keys) A.free_one(keys);
+                keys = grown;
+                res_cap = ncap;
+            }
+            if (r)
+                BMJ_CHECK(cudaMemcpyAsync(keys + n_res, src, r * sizeof(uint64_t),
+                                          cudaMemcpyDeviceToDevice, s));
+            n_res += r;
+            return BMJ_OK;
+        };
+
+        // ---- candidates from the prefix filter (Section 2.2), if asked for ----
+        // The index of every prefix is built once; its candidate slots are then
+        // expanded a range at a time into a buffer of fixed size (a quarter of the
+        // free memory, or opt.queue_cap slots), and each range's candidates pass
+        // Eq. 2 with the join's bitmaps and the merge before the next range.
         bool done = false;
         if (o.candidates == BMJ_CAND_PREFIX) {
             Arena PA(s);  // its buffers go once the candidates are verified
-            size_t free_b = 0, total_b = 0;
-            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
-            cudaGetLastError();
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
-            uint2 *cq = nullptr;
-            int64_t nc = 0, slots = 0;
-            int pst = prefix_candidates(ssz, soff, stok, n, d.ntok, rs ? n_sc : 0, win,
-                                        (int64_t)(free_b / 4 / sizeof(uint2)), PA, s, &cq, &nc,
-                                        &slots);
-            BMJ_CHECK(cudaEventRecord(ev.e[4], s));
-            if (pst == BMJ_OK) {
-                stl.candidates = nc;
-                stl.filter_passes = 1;
-                // Eq. 2 with the join's own bitmaps on every candidate, then the merge
-                st = A.alloc(&keys, (size_t)(nc > 0 ? nc : 1));
+            PrefixIndex px;
+            int pst = prefix_index(ssz, soff, stok, n, d.ntok, rs ? n_sc : 0, win, PA, s, &px);
+            if (pst == BMJ_ERR_OOM) {  // the index itself does not fit: the window instead
+                cudaGetLastError();
+                PA.release();
+                stl.candidates = -1;
+            } else if (pst) {
+                return pst;
+            } else {
+                float ms_index = 0.f;
+                BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+                BMJ_CHECK(cudaEventSynchronize(ev.e[4]));
+                ms_index = ev.ms(3, 4);
+                size_t free_b = 0, total_b = 0;
+                if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)8 << 30;
+                cudaGetLastError();
+                // a range's slots need 8 bytes of candidates and 8 of result keys each
+                int64_t chunk = o.queue_cap > 0 ? o.queue_cap
+                                                : std::max<int64_t>((int64_t)1 << 20,
+                                                                    (int64_t)(free_b / 4 / 16));
+                chunk = std::max<int64_t>(1, std::min(chunk, px.slots));
+                uint2 *cq = nullptr;
+                uint64_t *ckeys = nullptr;
+                unsigned long long *ccnt = nullptr;
+                st = PA.alloc(&cq, (size_t)chunk);
+                if (!st) st = PA.alloc(&ckeys, (size_t)chunk);
+                if (!st) st = PA.alloc(&ccnt, 1);
                 if (st) return st;
-                BMJ_CHECK(cudaEventRecord(ev.e[5], s));
-                if (nc > 0) {
-                    st = launch_verify(cq, nc, soff, stok, ssz, perm, need, lim, bm, W, keys, &ctr[3],
-                                       &ctr[4], nbits, sms, s, sim, p, q);
+                stl.candidates = 0;
+                stl.survivors = 0;
+                stl.verified = 0;
+                stl.filter_passes = 0;
+                float ms_expand = 0.f;
+                for (int64_t o0 = 0; o0 < px.slots; o0 += chunk) {
+                    const int64_t o1 = std::min(px.slots, o0 + chunk);
+                    BMJ_CHECK(cudaMemsetAsync(ccnt, 0, sizeof(unsigned long long), s));
+                    BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
+                    BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+                    st = prefix_expand(px, o0, o1, cq, ccnt, s);
+                    if (st) return st;
+                    BMJ_CHECK(cudaEventRecord(ev.e[4], s));
+                    int64_t nc = 0;
+                    BMJ_CHECK(cudaMemcpyAsync(&nc, ccnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                    BMJ_CHECK(cudaStreamSynchronize(s));
+                    ms_expand += ev.ms(3, 4);
+                    stl.candidates += nc;
+                    stl.filter_passes++;
+                    if (nc == 0) continue;
+                    // Eq. 2 with the join's own bitmaps on every candidate, then the merge
+                    BMJ_CHECK(cudaEventRecord(ev.e[5], s));
+                    st = launch_verify(cq, nc, soff, stok, ssz, perm, need, lim, bm, W, ckeys,
+                                       &ctr[3], &ctr[4], nbits, sms, s, sim, p, q);
+                    if (st) return st;
+                    BMJ_CHECK(cudaEventRecord(ev.e[6], s));
+                    int64_t hv2[2] = {0, 0};
+                    BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t),
+                                              cudaMemcpyDeviceToHost, s));
+                    BMJ_CHECK(cudaStreamSynchronize(s));
+                    stl.survivors += hv2[1];
+                    stl.verified += hv2[1];
+                    stl.ms_verify += ev.ms(5, 6);
+                    st = append(ckeys, hv2[0]);
                     if (st) return st;
                 }
-                BMJ_CHECK(cudaEventRecord(ev.e[6], s));
-                int64_t hv2[2] = {0, 0};
-                BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-                BMJ_CHECK(cudaStreamSynchronize(s));
-                n_res = hv2[0];
-                stl.survivors = hv2[1];
-                stl.verified = hv2[1];
-                stl.ms_filter = ev.ms(3, 4);
-                stl.ms_verify = ev.ms(5, 6);
+                stl.candidate_slots = px.slots;
+                stl.ms_filter = ms_index + ms_expand;
                 done = true;
-            } else if (pst == BMJ_ERR_OOM) {  // too many candidates: the window instead
-                cudaGetLastError();
-                stl.candidates = -1;
-            } else {
-                return pst;
             }
         }
         if (!done) {
@@ -366,27 +423,6 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                     banded = true;
                 }
             }
-            int64_t res_cap = 0;
-            // Appends r result keys from src to the growing result buffer.
-            auto append = [&](const uint64_t *src, int64_t r) -> int {
-                if (n_res + r > res_cap) {
-                    const int64_t ncap = std::max(2 * res_cap, n_res + r);
-                    uint64_t *grown = nullptr;
-                    int rc = A.alloc(&grown, (size_t)ncap);
-                    if (rc) return rc;
-                    if (n_res)
-                        BMJ_CHECK(cudaMemcpyAsync(grown, keys, n_res * sizeof(uint64_t),
-                                                  cudaMemcpyDeviceToDevice, s));
-                    if (keys) A.free_one(keys);
-                    keys = grown;
-                    res_cap = ncap;
-                }
-                if (r)
-                    BMJ_CHECK(cudaMemcpyAsync(keys + n_res, src, r * sizeof(uint64_t),
-                                              cudaMemcpyDeviceToDevice, s));
-                n_res += r;
-                return BMJ_OK;
-            };
             if (!banded && !fault.keys && A.alloc(&keys, (size_t)(n_surv > 0 ? n_surv : 1)) == BMJ_OK) {
                 st = run_verify(queue, n_surv, keys, &n_res);
                 if (st) return st;

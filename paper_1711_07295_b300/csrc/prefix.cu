@@ -19,9 +19,12 @@
 //                                   2048); a sort of (set, rank) keys beyond
 //   index the prefixes              sort (rank, set) entries of every prefix
 //   count and expand candidates     per index entry, the earlier sets of its
-//                                   rank's list inside the window; one thread
-//                                   per candidate slot, kept when the entry's
-//                                   rank is the pair's lowest shared one
+//                                   rank's list inside the window (its slots);
+//                                   a slot is kept when the entry's rank is the
+//                                   pair's lowest shared one.  The slots are
+//                                   expanded in ranges (prefix_expand), so that
+//                                   any number of them goes through a buffer of
+//                                   fixed size, a range at a time
 #include <algorithm>
 
 #include "host_util.cuh"
@@ -327,70 +330,89 @@ __global__ void k_cand_count(const uint64_t *__restrict__ idx, int64_t P,
     }
 }
 
-// One candidate slot per thread: slot o belongs to entry k (cand_off[k] <= o <
-// cand_off[k+1]); the pair (i, j) is kept when no rank below the entry's is in
-// both prefixes (sorted ranks of a prefix: pref[pofs[x] ..]).  Kept pairs are
-// appended with one atomicAdd per warp.
+// Candidate slots [o0, o1) in tiles of 32 * kExpandPerLane consecutive slots
+// per warp.  The warp finds the entries owning its tile's first and last slots
+// (binary searches of cand_off over all entries), then each slot's entry by a
+// binary search between those two.  The pair (i, j) of a slot is kept when no
+// rank below the entry's is in both prefixes (sorted ranks of a prefix:
+// pref[pofs[x] ..]), so that a pair sharing several prefix tokens comes out
+// once.  Kept pairs are appended with one atomicAdd per warp and round.
+constexpr int kExpandPerLane = 8;
+
+__device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ cand_off, int64_t a,
+                                            int64_t b, int64_t o) {
+    // last k in [a, b) with cand_off[k] <= o (cand_off[a] <= o holds)
+    while (b - a > 1) {
+        const int64_t m = (a + b) >> 1;
+        if (cand_off[m] <= o) a = m;
+        else b = m;
+    }
+    return a;
+}
+
 __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                               const int64_t *__restrict__ cand_off, const int64_t *__restrict__ lo,
-                              int64_t C, const uint32_t *__restrict__ ssz,
+                              int64_t o0, int64_t o1, const uint32_t *__restrict__ ssz,
                               const int64_t *__restrict__ pofs, const uint32_t *__restrict__ pref,
                               SimWindow win, int rshift, uint2 *__restrict__ out,
                               unsigned long long *__restrict__ count) {
+    constexpr int64_t kTile = 32 * kExpandPerLane;
     const int lane = threadIdx.x & 31;
     const uint64_t umask = (1ull << rshift) - 1;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (int64_t base = gw * 32; base < C; base += warps * 32) {
-        const int64_t o = base + lane;
-        bool keep = false;
-        uint32_t i = 0, j = 0;
-        if (o < C) {
-            int64_t a = 0, b = P;  // last k with cand_off[k] <= o
-            while (b - a > 1) {
-                const int64_t m = (a + b) >> 1;
-                if (cand_off[m] <= o) a = m;
-                else b = m;
-            }
-            const int64_t k = a;
-            const uint64_t key = idx[k];
-            const uint32_t r = (uint32_t)(key & umask);
-            i = (uint32_t)(key >> rshift);
-            j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
-            const uint32_t *pi = pref + pofs[i];
-            const uint32_t *pj = pref + pofs[j];
-            const int64_t ni = prefix_len(ssz[i], win), nj = prefix_len(ssz[j], win);
-            int64_t x = 0, y = 0;
-            keep = true;
-            while (x < ni && y < nj) {
-                const uint32_t rx = pi[x], ry = pj[y];
-                if (rx >= r || ry >= r) break;
-                if (rx == ry) {
-                    keep = false;
-                    break;
+    for (int64_t t0 = o0 + gw * kTile; t0 < o1; t0 += warps * kTile) {
+        const int64_t t1 = min(t0 + kTile, o1);
+        // lane 0: the first slot's entry, lane 1: the last slot's
+        int64_t kb = 0;
+        if (lane < 2) kb = owner_of(cand_off, 0, P, lane == 0 ? t0 : t1 - 1);
+        const int64_t ka = __shfl_sync(kFullP, kb, 0);
+        const int64_t kz = __shfl_sync(kFullP, kb, 1) + 1;
+        for (int m = 0; m < kExpandPerLane; m++) {
+            const int64_t o = t0 + m * 32 + lane;
+            bool keep = false;
+            uint32_t i = 0, j = 0;
+            if (o < t1) {
+                const int64_t k = owner_of(cand_off, ka, kz, o);
+                const uint64_t key = idx[k];
+                const uint32_t r = (uint32_t)(key & umask);
+                i = (uint32_t)(key >> rshift);
+                j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
+                const uint32_t *pi = pref + pofs[i];
+                const uint32_t *pj = pref + pofs[j];
+                const int64_t ni = prefix_len(ssz[i], win), nj = prefix_len(ssz[j], win);
+                int64_t x = 0, y = 0;
+                keep = true;
+                while (x < ni && y < nj) {
+                    const uint32_t rx = pi[x], ry = pj[y];
+                    if (rx >= r || ry >= r) break;
+                    if (rx == ry) {
+                        keep = false;
+                        break;
+                    }
+                    if (rx < ry) x++;
+                    else y++;
                 }
-                if (rx < ry) x++;
-                else y++;
             }
-        }
-        const unsigned ball = __ballot_sync(kFullP, keep);
-        if (ball) {
-            unsigned long long pos = 0;
-            if (lane == 0) pos = atomicAdd(count, (unsigned long long)__popc(ball));
-            pos = __shfl_sync(kFullP, pos, 0);
-            if (keep) out[pos + __popc(ball & ((1u << lane) - 1u))] = make_uint2(i, j);
+            const unsigned ball = __ballot_sync(kFullP, keep);
+            if (ball) {
+                unsigned long long pos = 0;
+                if (lane == 0) pos = atomicAdd(count, (unsigned long long)__popc(ball));
+                pos = __shfl_sync(kFullP, pos, 0);
+                if (keep) out[pos + __popc(ball & ((1u << lane) - 1u))] = make_uint2(i, j);
+            }
         }
     }
 }
 
 }  // namespace
 
-int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, int64_t n,
-                      int64_t ntok, int64_t n_cols, SimWindow win, int64_t max_cand, Arena &A,
-                      cudaStream_t s, uint2 **cand, int64_t *n_cand, int64_t *n_slots) {
-    *cand = nullptr;
-    *n_cand = 0;
-    *n_slots = 0;
+int prefix_index(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, int64_t n,
+                 int64_t ntok, int64_t n_cols, SimWindow win, Arena &A, cudaStream_t s,
+                 PrefixIndex *out) {
+    *out = PrefixIndex{};
+    out->ssz = ssz;
+    out->win = win;
     if (n < 2 || ntok <= 0) return BMJ_OK;
     if (ntok >= ((int64_t)1 << 32)) return BMJ_ERR_TOO_LARGE;  // counts and ranks are 32-bit
     // ---- rank the distinct tokens: (occurrences, token value), rarest first ----
@@ -466,7 +488,7 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     BMJ_CHECK(cudaMemcpyAsync(&hv[1], bounds, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
     const int64_t P = hv[0];
-    if (P == 0) return BMJ_OK;
+    if (P == 0) return BMJ_OK;  // (no set has a prefix: no candidate)
     // ---- every set's prefix in rank order, per run of sets in size order (one
     //      run for a self-join; S's run and R's run for an RS-join) ----
     uint32_t *pref = nullptr;
@@ -534,22 +556,24 @@ int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *s
     int64_t C = 0;
     BMJ_CHECK(cudaMemcpyAsync(&C, coff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
-    *n_slots = C;
-    if (C == 0) return BMJ_OK;
-    if (max_cand > 0 && C > max_cand) return BMJ_ERR_OOM;  // more slots than the caller allows
-    uint2 *out = nullptr;
-    unsigned long long *cnt2 = nullptr;
-    rc = A.alloc(&out, (size_t)C);
-    if (!rc) rc = A.alloc(&cnt2, 1);
-    if (rc) return rc;
-    BMJ_CHECK(cudaMemsetAsync(cnt2, 0, sizeof(unsigned long long), s));
-    BMJ_LAUNCH(k_cand_expand, grid_p(C, 256, 148 * 16), 256, 0, s, idx, P, coff, lo, C, ssz, pofs,
-               pref, win, rshift, out, cnt2);
-    unsigned long long nc = 0;
-    BMJ_CHECK(cudaMemcpyAsync(&nc, cnt2, sizeof(nc), cudaMemcpyDeviceToHost, s));
-    BMJ_CHECK(cudaStreamSynchronize(s));
-    *cand = out;
-    *n_cand = (int64_t)nc;
+    out->idx = idx;
+    out->lo = lo;
+    out->cand_off = coff;
+    out->pofs = pofs;
+    out->pref = pref;
+    out->P = P;
+    out->slots = C;
+    out->rshift = rshift;
+    return BMJ_OK;
+}
+
+int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, uint2 *out,
+                  unsigned long long *count, cudaStream_t s) {
+    if (o1 <= o0 || ix.P == 0) return BMJ_OK;
+    constexpr int64_t kTile = 32 * kExpandPerLane;
+    BMJ_LAUNCH(k_cand_expand, grid_p((o1 - o0 + kTile - 1) / kTile, 8, 148 * 64), 256, 0, s, ix.idx,
+               ix.P, ix.cand_off, ix.lo, o0, o1, ix.ssz, ix.pofs, ix.pref, ix.win, ix.rshift, out,
+               count);
     return BMJ_OK;
 }
 

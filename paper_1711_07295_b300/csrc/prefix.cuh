@@ -6,15 +6,40 @@
 
 namespace bmj {
 
-// Candidates of the prefix filter (Section 2.2, prefix.cu): the pairs (i, j),
-// j < i in size order inside the window, whose prefixes share a token, each
-// once.  On the size-sorted collection (sizes, sorted CSR).  RS-join
-// (n_cols > 0): S's sets at positions [0, n_cols) and R's after them, each run
-// in size order; the pairs are (i in R, j in S) inside both window bounds.
-// *n_slots is the number of (rank, pair) slots examined; BMJ_ERR_OOM when they
-// exceed max_cand (> 0) or do not fit.
-int prefix_candidates(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, int64_t n,
-                      int64_t ntok, int64_t n_cols, SimWindow win, int64_t max_cand, Arena &A,
-                      cudaStream_t s, uint2 **cand, int64_t *n_cand, int64_t *n_slots);
+// The prefix index of a size-sorted collection: every set's prefix (its
+// lowest-ranked tokens, tokens ranked by (frequency, value)), the (rank, set)
+// entries of all prefixes sorted by rank (each rank's list in size order), and
+// per entry the run of earlier entries of its list inside the set's window.
+// Candidate slot o belongs to entry k when cand_off[k] <= o < cand_off[k+1];
+// its pair is (the entry's set, the (o - cand_off[k])-th set of that run).
+// The buffers live in the Arena given to prefix_index.
+struct PrefixIndex {
+    const uint64_t *idx = nullptr;      // P entries: (set << rshift) | rank, sorted by rank
+    const int64_t *lo = nullptr;        // per entry: first entry of its run of partners
+    const int64_t *cand_off = nullptr;  // P + 1: exclusive scan of the run lengths
+    const int64_t *pofs = nullptr;      // per set: offset of its prefix in pref
+    const uint32_t *pref = nullptr;     // every prefix, ranks ascending
+    const uint32_t *ssz = nullptr;      // set sizes in size order
+    int64_t P = 0;                      // index entries
+    int64_t slots = 0;                  // candidate slots, = cand_off[P]
+    int rshift = 0;
+    SimWindow win{};
+};
+
+// Builds the index on the size-sorted collection (sizes, sorted CSR).
+// RS-join (n_cols > 0): S's sets at positions [0, n_cols) and R's after them,
+// each run in size order; an entry of R owns the entries of S in its rank's
+// list inside both window bounds, an entry of S owns none.
+int prefix_index(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, int64_t n,
+                 int64_t ntok, int64_t n_cols, SimWindow win, Arena &A, cudaStream_t s,
+                 PrefixIndex *out);
+
+// Candidates of the slots [o0, o1): the pairs (i, j), j < i in size order
+// (RS: i in R, j in S) inside the window whose prefixes share a token, kept
+// at the slot of their lowest shared rank so that every pair appears once over
+// all slots.  Appends them to out (room for o1 - o0 pairs) and adds their
+// number to *count (device).
+int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, uint2 *out,
+                  unsigned long long *count, cudaStream_t s);
 
 }  // namespace bmj

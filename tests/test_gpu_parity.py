@@ -410,6 +410,15 @@ def test_ten_million_sets_row_sampled(ten_million, p, q):
     assert np.all(a < bb)
     key = a.astype(np.uint64) << np.uint64(32) | bb.astype(np.uint64)
     assert np.all(key[1:] > key[:-1])
+    # prefix-filter candidates (Section 2.2): the same pair list, from fewer pairs
+    xp, _, sx = _bmj.bmj_self_join(off_d, tok_d, p, q, b=128, output_on_device=True,
+                                   candidates=_bmj.BMJ_CAND_PREFIX)
+    xa = xp.a.cpu().numpy().view(np.uint32)
+    xb = xp.b.cpu().numpy().view(np.uint32)
+    xp.release()
+    assert sx["candidates"] >= 0 and sx["results"] == st["results"]
+    assert np.array_equal(xa, a) and np.array_equal(xb, bb)
+    assert sx["candidates"] < st["window_pairs"] // 100
 
 
 def test_measured_popc_rate_matches_the_unit_count():
@@ -441,6 +450,25 @@ def test_prefix_filter_candidates(sim, p, q, b):
     assert st["window_pairs"] == w and c <= w
 
 
+@pytest.mark.parametrize("cap", [1, 97, 5000])
+@pytest.mark.parametrize("sim,p,q", [(_bmj.BMJ_JACCARD, 1, 2), (_bmj.BMJ_JACCARD, 4, 5),
+                                     (_bmj.BMJ_DICE, 3, 4)])
+def test_prefix_filter_candidates_in_ranges(sim, p, q, cap):
+    # The candidate slots expanded in ranges of at most `cap` slots (a tiny budget
+    # forces many ranges, each filtered and verified before the next): candidates,
+    # survivors, results and the pair list are the oracle's, whatever the ranges.
+    off, tok = I.random_collection(3001, 2000, 1, 50, seed=400 + cap + p, zipf_s=1.0,
+                                   planted_frac=0.15)
+    a, bb, st = gpu_join(off, tok, p, q, b=64, sim=sim, candidates=_bmj.BMJ_CAND_PREFIX,
+                         queue_cap=cap)
+    ra, rb = O.self_join(off, tok, p, q, sim=sim)
+    assert np.array_equal(a, ra) and np.array_equal(bb, rb)
+    c, s, r = O.prefix_counts(off, tok, p, q, 64, O.XOR, sim=sim)
+    assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r)
+    assert st["candidate_slots"] >= st["candidates"]
+    assert st["filter_passes"] == max(1, -(-st["candidate_slots"] // cap))
+
+
 @pytest.mark.parametrize("large_values", [False, True])
 def test_prefix_filter_large_sets_and_token_values(large_values):
     # sets of 2,049 to 6,000 tokens among small ones (their prefixes are ordered by a
@@ -466,15 +494,17 @@ def test_prefix_filter_large_sets_and_token_values(large_values):
 
 
 def test_prefix_filter_on_the_million_set_workload(million):
-    # 1M sets at 9/10 and 19/20: the same pairs as the window-mode join, far fewer pairs
-    # through the Bitmap Filter.
+    # 1M sets at every threshold of the workload: the same pairs as the window-mode
+    # join, fewer pairs through the Bitmap Filter (at 1/2 its billions of candidate
+    # slots may go through the buffer in several ranges).
     off, tok = million
     off_d, tok_d = dev(off, tok)
-    for p, q in ((9, 10), (19, 20)):
+    for p, q in ((1, 2), (3, 4), (9, 10), (19, 20)):
         w_pairs, _, st_w = _bmj.bmj_self_join(off_d, tok_d, p, q, b=64, output_on_device=True)
         x_pairs, _, st_x = _bmj.bmj_self_join(off_d, tok_d, p, q, b=64, output_on_device=True,
                                               candidates=_bmj.BMJ_CAND_PREFIX)
         assert torch.equal(w_pairs.a, x_pairs.a) and torch.equal(w_pairs.b, x_pairs.b)
         assert st_x["results"] == st_w["results"] and 0 < st_x["candidates"] < st_w["window_pairs"] // 10
+        assert st_x["candidate_slots"] >= st_x["candidates"] and st_x["filter_passes"] >= 1
         w_pairs.release()
         x_pairs.release()
