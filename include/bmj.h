@@ -61,6 +61,7 @@ extern "C" {
 #define BMJ_ERR_TIMEOUT         (-7)  /* a bounded device-side wait gave up */
 #define BMJ_ERR_CUDA            (-8)  /* a CUDA runtime call failed */
 #define BMJ_ERR_TOO_LARGE       (-9)  /* more than 2^31 - 1 sets, or a set of 2^24 tokens or more */
+#define BMJ_PENDING              1    /* bmj_serve_poll: not completed yet (not an error) */
 
 /* ---- bitmap generation methods (Section 3.2) ---------------------------- */
 #define BMJ_XOR      0   /* Alg. 3b: toggle bit h(t); the paper's GPU default */
@@ -316,7 +317,9 @@ typedef struct {
     int64_t max_batch_queries;     /* queries per batch (default 4096) */
     int64_t max_batch_window_pairs;/* memory admission: window pairs per batch (default 2^25);
                                       raised to the largest single query's window */
-    int64_t reserved[4];
+    int64_t max_probe_tokens;      /* bmj_serve_open: largest probe a submission may hold
+                                      (default 4096); bmj_serve sizes it from its queries */
+    int64_t reserved[3];
 } bmj_serve_options;
 
 typedef struct {
@@ -383,6 +386,61 @@ int bmj_index_query(bmj_index *idx, const bmj_collection *probes, const uint32_t
 int bmj_serve(bmj_index *idx, const bmj_collection *queries, const double *arrival_s,
               const uint32_t *p, const uint32_t *q, const bmj_serve_options *opt,
               bmj_id_lists *out, double *latency_ms, bmj_serve_stats *stats);
+
+/* ---- live serving: queries submitted while other batches run ------------ */
+
+/* A request loop over an index (its own host thread and stream slots). */
+typedef struct bmj_server bmj_server;
+
+/*
+ * Opens a live server on idx (no counterpart in the paper; the arithmetic of
+ * every query is the one of bmj_index_query).  opt as for bmj_serve (NULL =
+ * defaults): n_slots batches in flight, at most max_batch_queries queries and
+ * max_batch_window_pairs window pairs per batch (raised to the index's size,
+ * the largest window a single query can have), probes of at most
+ * max_probe_tokens tokens.  The server allocates its slots (stream, pinned and
+ * device buffers) once, here, and starts its loop thread: queries submitted
+ * from any thread are admitted into free slots by the exact window-pair count
+ * of the batch (memory admission) while earlier batches are on the device,
+ * and several batches overlap.  idx must outlive the server.
+ * Errors: BMJ_ERR_INVALID_ARG, BMJ_ERR_OOM, BMJ_ERR_CUDA, or the index's
+ * sticky status.
+ */
+int bmj_serve_open(bmj_index *idx, const bmj_serve_options *opt, bmj_server **out);
+
+/*
+ * Submits one probe set: tokens[0 .. n_tokens-1] (host memory, strictly
+ * increasing, non-negative; copied, so the caller may reuse the buffer) with
+ * threshold p/q for the index's similarity function.  *ticket receives the
+ * query's ticket (0, 1, 2, ... in submission order).  Thread-safe.
+ * Errors: BMJ_ERR_INVALID_ARG (NULL, bad threshold, or after
+ * bmj_serve_close began), BMJ_ERR_EMPTY_SET, BMJ_ERR_UNSORTED,
+ * BMJ_ERR_NEG_TOKEN, BMJ_ERR_TOO_LARGE (more than max_probe_tokens), or a
+ * device failure of the server's loop (sticky).
+ */
+int bmj_serve_submit(bmj_server *srv, const int32_t *tokens, int64_t n_tokens, uint32_t p,
+                     uint32_t q, int64_t *ticket);
+
+/*
+ * The result of a submitted query: BMJ_OK with out filled (one list: the
+ * resident ids s with sim(x, s) >= p/q, ascending; free with
+ * bmj_id_lists_free) and *latency_ms (optional) = completion - submission;
+ * BMJ_PENDING when the query has not completed within wait_ms milliseconds
+ * (0 = do not wait); a negative status when its batch failed.  A result is
+ * handed out once: a second poll of the same ticket, like an unknown ticket,
+ * gives BMJ_ERR_INVALID_ARG.  Thread-safe.
+ */
+int bmj_serve_poll(bmj_server *srv, int64_t ticket, int32_t wait_ms, bmj_id_lists *out,
+                   double *latency_ms);
+
+/*
+ * Finishes every submitted query, stops the loop and frees the server;
+ * results not yet polled are dropped.  stats (optional): the queries
+ * completed, batches, window pairs, survivors, results, p50/p99/max latency
+ * (completion - submission) and qps over the time from open to the last
+ * completion.  Returns the loop's device failure, if any (BMJ_OK otherwise).
+ */
+int bmj_serve_close(bmj_server *srv, bmj_serve_stats *stats);
 
 void bmj_id_lists_free(bmj_id_lists *lists);
 

@@ -26,6 +26,7 @@ BMJ_ERR_OUTPUT_OVERFLOW = -6
 BMJ_ERR_TIMEOUT = -7
 BMJ_ERR_CUDA = -8
 BMJ_ERR_TOO_LARGE = -9
+BMJ_PENDING = 1   # bmj_serve_poll: the query has not completed yet (not an error)
 
 BMJ_XOR, BMJ_SET, BMJ_NEXT, BMJ_COMBINED = 0, 1, 2, 3
 BMJ_JACCARD, BMJ_COSINE, BMJ_DICE, BMJ_OVERLAP = 0, 1, 2, 3   # similarity functions (Table 1)
@@ -109,7 +110,7 @@ class bmj_id_lists(C.Structure):
 class bmj_serve_options(C.Structure):
     _fields_ = [("n_slots", C.c_int32), ("reserved0", C.c_int32),
                 ("max_batch_queries", C.c_int64), ("max_batch_window_pairs", C.c_int64),
-                ("reserved", C.c_int64 * 4)]
+                ("max_probe_tokens", C.c_int64), ("reserved", C.c_int64 * 3)]
 
 
 class bmj_serve_stats(C.Structure):
@@ -159,6 +160,12 @@ SIGNATURES = {
                             C.c_void_p, C.POINTER(bmj_serve_options), C.POINTER(bmj_id_lists),
                             C.c_void_p, C.POINTER(bmj_serve_stats)]),
     "bmj_id_lists_free": (None, [C.POINTER(bmj_id_lists)]),
+    "bmj_serve_open": (C.c_int, [C.c_void_p, C.POINTER(bmj_serve_options), C.POINTER(C.c_void_p)]),
+    "bmj_serve_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_uint32, C.c_uint32,
+                                   C.POINTER(C.c_int64)]),
+    "bmj_serve_poll": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(bmj_id_lists),
+                                 C.POINTER(C.c_double)]),
+    "bmj_serve_close": (C.c_int, [C.c_void_p, C.POINTER(bmj_serve_stats)]),
     "bmj_kernel_launches": (C.c_int64, []),
     "bmj_host_pool_trim": (C.c_int64, []),
     "bmj_measure_popc_rate": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -530,3 +537,61 @@ class Index:
         if st != BMJ_OK:
             raise BmjError(st, "bmj_serve")
         return (_take_id_lists(out) if want_results else None), lat, st_.as_dict()
+
+
+class Server:
+    """A live request loop over an index (bmj_serve_open / _submit / _poll /
+    _close): queries submitted from any thread while other batches run."""
+
+    def __init__(self, index: Index, n_slots: int = 4, max_batch_queries: int = 4096,
+                 max_batch_window_pairs: int = 1 << 25, max_probe_tokens: int = 4096):
+        so = bmj_serve_options()
+        lib().bmj_default_serve_options(C.byref(so))
+        so.n_slots = int(n_slots)
+        so.max_batch_queries = int(max_batch_queries)
+        so.max_batch_window_pairs = int(max_batch_window_pairs)
+        so.max_probe_tokens = int(max_probe_tokens)
+        h = C.c_void_p()
+        st = lib().bmj_serve_open(index._h, C.byref(so), C.byref(h))
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_serve_open")
+        self._h = h
+        self._index = index   # the index must outlive the server
+
+    def submit(self, tokens, p: int, q: int) -> int:
+        """Returns the query's ticket."""
+        t = np.ascontiguousarray(tokens, dtype=np.int32)
+        ticket = C.c_int64(-1)
+        st = lib().bmj_serve_submit(self._h, _ptr(t), len(t), C.c_uint32(int(p)),
+                                    C.c_uint32(int(q)), C.byref(ticket))
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_serve_submit")
+        return int(ticket.value)
+
+    def poll(self, ticket: int, wait_ms: int = 0):
+        """(ids ascending, latency_ms) when the query has completed, else None."""
+        out = bmj_id_lists()
+        lat = C.c_double(0.0)
+        st = lib().bmj_serve_poll(self._h, int(ticket), int(wait_ms), C.byref(out), C.byref(lat))
+        if st == BMJ_PENDING:
+            return None
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_serve_poll")
+        return _take_id_lists(out)[0], float(lat.value)
+
+    def close(self):
+        """Finishes every submitted query; returns the stats dict."""
+        if self._h is None:
+            return None
+        st_ = bmj_serve_stats()
+        st = lib().bmj_serve_close(self._h, C.byref(st_))
+        self._h = None
+        if st != BMJ_OK:
+            raise BmjError(st, "bmj_serve_close")
+        return st_.as_dict()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

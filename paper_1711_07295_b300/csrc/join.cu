@@ -621,7 +621,8 @@ const char *bmj_strerror(int status) {
         case BMJ_ERR_OUTPUT_OVERFLOW: return "output buffer too small";
         case BMJ_ERR_TIMEOUT: return "bounded device wait timed out";
         case BMJ_ERR_CUDA: return "CUDA runtime error";
-        case BMJ_ERR_TOO_LARGE: return "collection too large (n_sets >= 2^31 or a set of >= 2^24 tokens)";
+        case BMJ_ERR_TOO_LARGE: return "too large (n_sets >= 2^31, a set of >= 2^24 tokens, or a probe above the server's limit)";
+        case BMJ_PENDING: return "pending: the query has not completed yet";
         default: return "unknown status";
     }
 }

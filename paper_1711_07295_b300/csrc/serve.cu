@@ -20,11 +20,22 @@
 // count (from a host histogram of resident sizes) fits the slot's buffers,
 // which bounds every buffer of the batch (survivors and results cannot
 // exceed window pairs).  Latency of a query = completion - arrival.
+//
+// bmj_serve_open / _submit / _poll / _close run the same slots live: a
+// server owns a host thread that admits the queries submitted so far (from
+// any thread, while other batches are on the device) into free slots by the
+// same window-pair budget, completes batches as their events fire and files
+// every result under its ticket until it is polled.  Latency of a query =
+// completion - submission.
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "host_util.cuh"
@@ -573,10 +584,10 @@ int launch_phase2(Slot &s) {
     return BMJ_OK;
 }
 
-// Stages queries ids[0..m) of a host query collection into a slot.
-void stage(Slot &s, const bmj_collection *qc, const uint32_t *p, const uint32_t *q,
-           const int64_t *ids, int64_t m) {
-    s.ids.assign(ids, ids + m);
+// Stages m queries into a slot.  get(k, &tokens, &n_tokens, &p, &q) gives
+// the k-th query of the batch.
+template <class Get>
+void stage_with(Slot &s, int64_t m, Get get) {
     s.nq = m;
     // packed layout: offsets (m + 1 int64), p (m), q (m), then the tokens
     const size_t o_p = (size_t)(m + 1) * sizeof(int64_t), o_q = o_p + m * sizeof(uint32_t),
@@ -592,16 +603,28 @@ void stage(Slot &s, const bmj_collection *qc, const uint32_t *p, const uint32_t 
     s.h_off[0] = 0;
     int64_t t = 0;
     for (int64_t k = 0; k < m; k++) {
-        const int64_t x = ids[k];
-        const int64_t a = qc->offsets[x], b = qc->offsets[x + 1];
-        memcpy(s.h_tok + t, qc->tokens + a, (b - a) * sizeof(int32_t));
-        t += b - a;
+        const int32_t *tk = nullptr;
+        int64_t nt = 0;
+        get(k, &tk, &nt, &s.h_p[k], &s.h_q[k]);
+        memcpy(s.h_tok + t, tk, nt * sizeof(int32_t));
+        t += nt;
         s.h_off[k + 1] = t;
-        s.h_p[k] = p[x];
-        s.h_q[k] = q[x];
     }
     s.ntok = t;
     s.in_bytes = (int64_t)(o_t + t * sizeof(int32_t));
+}
+
+// Stages queries ids[0..m) of a host query collection into a slot.
+void stage(Slot &s, const bmj_collection *qc, const uint32_t *p, const uint32_t *q,
+           const int64_t *ids, int64_t m) {
+    s.ids.assign(ids, ids + m);
+    stage_with(s, m, [&](int64_t k, const int32_t **tk, int64_t *nt, uint32_t *pk, uint32_t *qk) {
+        const int64_t x = ids[k];
+        *tk = qc->tokens + qc->offsets[x];
+        *nt = qc->offsets[x + 1] - qc->offsets[x];
+        *pk = p[x];
+        *qk = q[x];
+    });
 }
 
 }  // namespace
@@ -918,6 +941,7 @@ extern "C" void bmj_default_serve_options(bmj_serve_options *so) {
     so->n_slots = 4;
     so->max_batch_queries = 4096;
     so->max_batch_window_pairs = (int64_t)1 << 25;
+    so->max_probe_tokens = 4096;
 }
 
 // A device-level failure (CUDA runtime error, bounded wait given up) leaves the
@@ -982,4 +1006,375 @@ extern "C" int bmj_serve(bmj_index *idx, const bmj_collection *queries, const do
         cudaGetLastError();
     }
     return stick(idx, st);
+}
+
+// ============================================================================
+// Live serving: a request loop that accepts queries while batches run.
+// ============================================================================
+namespace {
+
+struct LiveQuery {
+    std::vector<int32_t> tok;
+    uint32_t p = 0, q = 0;
+    int64_t win = 0;
+    std::chrono::steady_clock::time_point t_submit;
+};
+
+struct LiveResult {
+    int status = BMJ_OK;
+    std::vector<int64_t> ids;
+    double latency_ms = 0.0;
+};
+
+}  // namespace
+
+struct bmj_server {
+    bmj_index *idx = nullptr;
+    int64_t max_q = 0, tok_cap = 0, pair_budget = 0, max_probe = 0;
+    std::vector<bmj::Slot> slots;
+    std::thread loop;
+    std::mutex mu;
+    std::condition_variable cv_work;   // the loop waits here for submissions
+    std::condition_variable cv_done;   // pollers wait here for results
+    std::deque<int64_t> pending;       // submitted, not yet in a batch (ticket order)
+    std::unordered_map<int64_t, LiveQuery> queries;   // submitted, not yet completed
+    std::unordered_map<int64_t, LiveResult> results;  // completed, not yet polled
+    int64_t next_ticket = 0;
+    bool closing = false;
+    int error = BMJ_OK;
+    // totals (written by the loop under mu)
+    std::vector<double> latencies;
+    int64_t batches = 0, window_pairs = 0, survivors = 0, n_results = 0;
+    std::chrono::steady_clock::time_point t_open, t_last;
+};
+
+namespace {
+
+// The request loop of a live server (its own host thread, the index's device
+// current).  Slots are touched by this thread only; the queues and result
+// table are shared with submitters and pollers under srv->mu.
+void live_loop(bmj_server *srv) {
+    using clk = std::chrono::steady_clock;
+    bmj_index *idx = srv->idx;
+    if (cudaSetDevice(idx->device) != cudaSuccess) {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->error = BMJ_ERR_CUDA;
+    }
+    const int sms = bmj::num_sms(idx->device);
+    // per slot: the queries of its batch (pointers stay valid: node-based map,
+    // entries erased by this thread only)
+    std::vector<std::vector<const LiveQuery *>> batch_q(srv->slots.size());
+    auto last_activity = clk::now();
+    int rc = BMJ_OK;
+    for (;;) {
+        bool progressed = false;
+        bool in_flight = false;
+        // 1. finished phases
+        for (size_t si = 0; si < srv->slots.size() && !rc; si++) {
+            bmj::Slot &s = srv->slots[si];
+            if (s.phase == 0) continue;
+            const cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaErrorNotReady) {
+                in_flight = true;
+                continue;
+            }
+            if (e != cudaSuccess) {
+                rc = bmj::status_of(e);
+                break;
+            }
+            progressed = true;
+            bool finished = s.phase == 2;
+            if (s.phase == 1) {
+                if (bmj::finish_on_host(s)) {
+                    finished = true;
+                } else {
+                    rc = bmj::launch_phase2(s);
+                    s.phase = 2;
+                    in_flight = true;
+                }
+            }
+            if (finished) {
+                const auto t_done = clk::now();
+                std::vector<LiveResult> out(s.nq);
+                for (int64_t k = 0; k < s.nq; k++) {
+                    const int64_t lo = s.h_bounds[k], hi = s.h_bounds[k + 1];
+                    out[k].ids.resize(hi - lo);
+                    for (int64_t r = lo; r < hi; r++)
+                        out[k].ids[r - lo] = (int64_t)(s.h_keys[r] & 0xffffffffu);
+                    out[k].latency_ms = std::chrono::duration<double, std::milli>(
+                                            t_done - batch_q[si][k]->t_submit).count();
+                }
+                {
+                    std::lock_guard<std::mutex> g(srv->mu);
+                    srv->survivors += (int64_t)s.h_ctr[0];
+                    srv->n_results += (int64_t)s.h_ctr[1];
+                    for (int64_t k = 0; k < s.nq; k++) {
+                        srv->latencies.push_back(out[k].latency_ms);
+                        srv->results[s.ids[k]] = std::move(out[k]);
+                        srv->queries.erase(s.ids[k]);
+                    }
+                    srv->t_last = t_done;
+                }
+                srv->cv_done.notify_all();
+                batch_q[si].clear();
+                s.phase = 0;
+            }
+        }
+        if (rc) break;
+        // 2. admission: submitted queries into free slots, bounded by the slot's
+        //    query, token and window-pair capacities
+        bool closing = false, waiting = false;
+        for (size_t si = 0; si < srv->slots.size() && !rc; si++) {
+            bmj::Slot &s = srv->slots[si];
+            if (s.phase != 0) continue;
+            std::vector<int64_t> take;
+            std::vector<const LiveQuery *> qs;
+            int64_t w = 0, t = 0;
+            {
+                std::lock_guard<std::mutex> g(srv->mu);
+                while (!srv->pending.empty() && (int64_t)take.size() < srv->max_q) {
+                    const int64_t x = srv->pending.front();
+                    const LiveQuery &lq = srv->queries.at(x);
+                    const int64_t sx = (int64_t)lq.tok.size();
+                    if (!take.empty() && (w + lq.win > srv->pair_budget || t + sx > srv->tok_cap))
+                        break;
+                    take.push_back(x);
+                    qs.push_back(&lq);
+                    w += lq.win;
+                    t += sx;
+                    srv->pending.pop_front();
+                }
+                if (!take.empty()) {
+                    srv->batches++;
+                    srv->window_pairs += w;
+                }
+            }
+            if (take.empty()) break;
+            s.ids = take;
+            bmj::stage_with(s, (int64_t)take.size(),
+                            [&](int64_t k, const int32_t **tk, int64_t *nt, uint32_t *pk,
+                                uint32_t *qk) {
+                                *tk = qs[k]->tok.data();
+                                *nt = (int64_t)qs[k]->tok.size();
+                                *pk = qs[k]->p;
+                                *qk = qs[k]->q;
+                            });
+            s.win = w;
+            batch_q[si] = std::move(qs);
+            rc = bmj::launch_phase1(idx, s, sms);
+            if (rc) break;
+            s.phase = 1;
+            in_flight = true;
+            progressed = true;
+        }
+        if (rc) break;
+        {
+            std::lock_guard<std::mutex> g(srv->mu);
+            closing = srv->closing;
+            waiting = !srv->pending.empty();
+        }
+        if (!in_flight && !waiting && closing) break;  // drained
+        if (progressed) {
+            last_activity = clk::now();
+        } else if (!in_flight && !waiting) {
+            // idle: poll for a millisecond (a wake-up from a sleep can come tens of
+            // microseconds late), then block until a submission or close
+            if (clk::now() - last_activity < std::chrono::milliseconds(1)) {
+                std::this_thread::yield();
+            } else {
+                std::unique_lock<std::mutex> lk(srv->mu);
+                srv->cv_work.wait(lk, [&] { return srv->closing || !srv->pending.empty(); });
+                last_activity = clk::now();
+            }
+        } else {
+            std::this_thread::yield();
+        }
+    }
+    if (rc) {
+        // a device-level failure: every query not yet completed fails with it
+        for (auto &s : srv->slots)
+            if (s.stream) cudaStreamSynchronize(s.stream);
+        cudaGetLastError();
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->error = rc;
+        for (auto &kv : srv->queries) {
+            LiveResult r;
+            r.status = rc;
+            srv->results[kv.first] = std::move(r);
+        }
+        srv->queries.clear();
+        srv->pending.clear();
+        if (rc == BMJ_ERR_CUDA || rc == BMJ_ERR_TIMEOUT) idx->sticky = rc;
+    }
+    srv->cv_done.notify_all();
+}
+
+void destroy_server(bmj_server *srv) {
+    for (auto &s : srv->slots) bmj::free_slot(s);
+    delete srv;
+}
+
+}  // namespace
+
+extern "C" int bmj_serve_open(bmj_index *idx, const bmj_serve_options *opt, bmj_server **out) {
+    if (!out) return BMJ_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!idx) return BMJ_ERR_INVALID_ARG;
+    if (idx->sticky) return idx->sticky;
+    bmj_serve_options so;
+    if (opt) so = *opt;
+    else bmj_default_serve_options(&so);
+    if (so.n_slots < 1 || so.max_batch_queries < 0 || so.max_batch_window_pairs < 0 ||
+        so.max_probe_tokens < 0)
+        return BMJ_ERR_INVALID_ARG;
+    bmj_server *srv = new (std::nothrow) bmj_server();
+    if (!srv) return BMJ_ERR_OOM;
+    srv->idx = idx;
+    srv->max_q = so.max_batch_queries > 0 ? so.max_batch_queries : 4096;
+    srv->max_probe = so.max_probe_tokens > 0 ? so.max_probe_tokens : 4096;
+    srv->tok_cap = std::max<int64_t>(srv->max_probe,
+                                     std::min<int64_t>(srv->max_q * srv->max_probe, (int64_t)1 << 22));
+    // a single query's window holds at most every resident set: it always fits a slot
+    srv->pair_budget = std::max<int64_t>(
+        so.max_batch_window_pairs > 0 ? so.max_batch_window_pairs : ((int64_t)1 << 25),
+        std::max<int64_t>(idx->n, 1));
+    int dev_prev = 0;
+    cudaGetDevice(&dev_prev);
+    if (cudaSetDevice(idx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete srv;
+        return BMJ_ERR_CUDA;
+    }
+    srv->slots.resize(so.n_slots);
+    int rc = BMJ_OK;
+    for (auto &s : srv->slots) {
+        rc = bmj::alloc_slot(s, srv->max_q, srv->tok_cap, srv->pair_budget, idx->W);
+        if (rc) break;
+    }
+    cudaSetDevice(dev_prev);
+    if (rc) {
+        destroy_server(srv);
+        return rc;
+    }
+    srv->t_open = srv->t_last = std::chrono::steady_clock::now();
+    try {
+        srv->loop = std::thread(live_loop, srv);
+    } catch (...) {
+        destroy_server(srv);
+        return BMJ_ERR_OOM;
+    }
+    *out = srv;
+    return BMJ_OK;
+}
+
+extern "C" int bmj_serve_submit(bmj_server *srv, const int32_t *tokens, int64_t n_tokens,
+                                uint32_t p, uint32_t q, int64_t *ticket) {
+    if (!srv || !ticket || n_tokens < 0 || (n_tokens > 0 && !tokens)) return BMJ_ERR_INVALID_ARG;
+    *ticket = -1;
+    if (!sim_valid(srv->idx->sim, p, q)) return BMJ_ERR_INVALID_ARG;
+    if (n_tokens == 0) return BMJ_ERR_EMPTY_SET;
+    if (n_tokens > srv->max_probe) return BMJ_ERR_TOO_LARGE;
+    if (tokens[0] < 0) return BMJ_ERR_NEG_TOKEN;
+    for (int64_t k = 1; k < n_tokens; k++)
+        if (tokens[k] <= tokens[k - 1]) return BMJ_ERR_UNSORTED;
+    LiveQuery lq;
+    try {
+        lq.tok.assign(tokens, tokens + n_tokens);
+    } catch (...) {
+        return BMJ_ERR_OOM;
+    }
+    lq.p = p;
+    lq.q = q;
+    lq.win = window_of(srv->idx, n_tokens, p, q);
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        if (srv->error) return srv->error;
+        if (srv->closing) return BMJ_ERR_INVALID_ARG;
+        lq.t_submit = std::chrono::steady_clock::now();
+        const int64_t t = srv->next_ticket++;
+        try {
+            srv->queries.emplace(t, std::move(lq));
+            srv->pending.push_back(t);
+        } catch (...) {
+            srv->queries.erase(t);
+            return BMJ_ERR_OOM;
+        }
+        *ticket = t;
+    }
+    srv->cv_work.notify_one();
+    return BMJ_OK;
+}
+
+extern "C" int bmj_serve_poll(bmj_server *srv, int64_t ticket, int32_t wait_ms,
+                              bmj_id_lists *out, double *latency_ms) {
+    if (!srv || !out) return BMJ_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    std::unique_lock<std::mutex> lk(srv->mu);
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::milliseconds(std::max<int32_t>(wait_ms, 0));
+    for (;;) {
+        auto it = srv->results.find(ticket);
+        if (it != srv->results.end()) {
+            LiveResult r = std::move(it->second);
+            srv->results.erase(it);
+            lk.unlock();
+            if (r.status) return r.status;
+            out->n_queries = 1;
+            out->offsets = (int64_t *)malloc(2 * sizeof(int64_t));
+            out->ids = (int64_t *)malloc(std::max<size_t>(r.ids.size(), 1) * sizeof(int64_t));
+            if (!out->offsets || !out->ids) {
+                id_lists_free_impl(out);
+                return BMJ_ERR_OOM;
+            }
+            out->offsets[0] = 0;
+            out->offsets[1] = (int64_t)r.ids.size();
+            if (!r.ids.empty()) memcpy(out->ids, r.ids.data(), r.ids.size() * sizeof(int64_t));
+            if (latency_ms) *latency_ms = r.latency_ms;
+            return BMJ_OK;
+        }
+        if (srv->queries.find(ticket) == srv->queries.end())
+            return BMJ_ERR_INVALID_ARG;  // never submitted, or already polled
+        if (wait_ms <= 0) return BMJ_PENDING;
+        if (srv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+            srv->results.find(ticket) == srv->results.end())
+            return BMJ_PENDING;
+    }
+}
+
+extern "C" int bmj_serve_close(bmj_server *srv, bmj_serve_stats *stats) {
+    if (!srv) return BMJ_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> g(srv->mu);
+        srv->closing = true;
+    }
+    srv->cv_work.notify_all();
+    if (srv->loop.joinable()) srv->loop.join();
+    const int err = srv->error;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        std::vector<double> lat = srv->latencies;
+        std::sort(lat.begin(), lat.end());
+        auto pct = [&](double f) {
+            if (lat.empty()) return 0.0;
+            size_t k = (size_t)std::min<double>((double)lat.size() - 1, f * (double)lat.size());
+            return lat[k];
+        };
+        stats->n_queries = (int64_t)lat.size();
+        stats->batches = srv->batches;
+        stats->window_pairs = srv->window_pairs;
+        stats->survivors = srv->survivors;
+        stats->results = srv->n_results;
+        stats->wall_s = std::chrono::duration<double>(srv->t_last - srv->t_open).count();
+        stats->qps = stats->wall_s > 0 ? (double)lat.size() / stats->wall_s : 0.0;
+        stats->p50_ms = pct(0.50);
+        stats->p99_ms = pct(0.99);
+        stats->max_ms = lat.empty() ? 0.0 : lat.back();
+    }
+    int dev_prev = 0;
+    cudaGetDevice(&dev_prev);
+    cudaSetDevice(srv->idx->device);
+    destroy_server(srv);
+    cudaSetDevice(dev_prev);
+    cudaGetLastError();
+    return err;
 }

@@ -182,3 +182,81 @@ def test_index_other_similarity_functions(sim):
             idx.query(qoff[:2], qtok[:int(qoff[1])], np.array([5], np.uint32), np.array([4], np.uint32))
         assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
     idx.close()
+
+
+def test_live_server_submissions_while_batches_run():
+    # bmj_serve_open / submit / poll / close: a second host thread submits queries
+    # while earlier batches are on the device and the main thread polls; every result
+    # equals the oracle's search, in that mix and alone (one query in flight at a time).
+    import threading
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=41, nq=300)
+    idx = _bmj.Index(torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda(), b=64)
+    srv = _bmj.Server(idx, n_slots=3, max_batch_queries=16, max_probe_tokens=64)
+    tickets = [None] * len(p)
+    done = threading.Event()
+
+    def producer():
+        for x in range(len(p)):
+            tickets[x] = srv.submit(qtok[qoff[x]:qoff[x + 1]], int(p[x]), int(q[x]))
+            if x % 16 == 15:
+                done.wait(0.0003)   # let some batches start before the next submissions
+    th = threading.Thread(target=producer)
+    th.start()
+    got = {}
+    while len(got) < len(p):
+        for x in range(len(p)):
+            if x not in got and tickets[x] is not None:
+                r = srv.poll(tickets[x])
+                if r is not None:
+                    got[x] = r
+    th.join()
+    st = srv.close()
+    assert st["n_queries"] == len(p) and 1 <= st["batches"] <= len(p)
+    assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+    psz, rsz = np.diff(qoff), np.diff(off)
+    assert st["window_pairs"] == sum(
+        O.rs_window_pairs(psz[(p == pk) & (q == qk)], rsz, int(pk), int(qk))
+        for pk, qk in set(zip(p.tolist(), q.tolist())))
+    alone = _bmj.Server(idx, n_slots=1)
+    nonempty = 0
+    for x in range(len(p)):
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
+        assert np.array_equal(got[x][0], want), x
+        assert got[x][1] > 0
+        nonempty += len(want) > 0
+        if x < 60:
+            t = alone.submit(qtok[qoff[x]:qoff[x + 1]], int(p[x]), int(q[x]))
+            ids, _ = alone.poll(t, wait_ms=20_000)
+            assert np.array_equal(ids, want), x
+    assert nonempty > 30
+    alone.close()
+    idx.close()
+
+
+def test_live_server_errors():
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=43, nq=10)
+    idx = _bmj.Index(off, tok, b=64)
+    srv = _bmj.Server(idx, n_slots=2, max_probe_tokens=8)
+    with pytest.raises(_bmj.BmjError) as e:
+        srv.submit(np.array([3, 2, 5]), 1, 2)
+    assert e.value.status == _bmj.BMJ_ERR_UNSORTED
+    with pytest.raises(_bmj.BmjError) as e:
+        srv.submit(np.arange(9), 1, 2)            # above max_probe_tokens
+    assert e.value.status == _bmj.BMJ_ERR_TOO_LARGE
+    with pytest.raises(_bmj.BmjError) as e:
+        srv.submit(np.array([1, 2]), 3, 2)        # p > q
+    assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
+    with pytest.raises(_bmj.BmjError) as e:
+        srv.submit(np.zeros(0, np.int32), 1, 2)
+    assert e.value.status == _bmj.BMJ_ERR_EMPTY_SET
+    t = srv.submit(tok[off[5]:off[6]], 1, 2)
+    ids, lat = srv.poll(t, wait_ms=20_000)
+    assert np.array_equal(ids, O.search(tok[off[5]:off[6]], off, tok, 1, 2)) and 5 in ids.tolist()
+    with pytest.raises(_bmj.BmjError) as e:     # a result is handed out once
+        srv.poll(t)
+    assert e.value.status == _bmj.BMJ_ERR_INVALID_ARG
+    # close finishes what was submitted; nothing can be submitted after it
+    last = [srv.submit(qtok[qoff[x]:qoff[x + 1]][:8], 1, 2) for x in range(5)]
+    st = srv.close()
+    assert st["n_queries"] == 6 and len(last) == 5
+    idx.close()
