@@ -440,6 +440,24 @@ def run_ours(args):
         host_coll.clear()
         _bmj.bmj_host_pool_trim()
 
+    # ---- bands: the one exchange of a sharded join, gathering the pair lists ----
+    gather = None
+    if bands:
+        from paper_1711_07295_b300 import shard
+        gather = []
+        for (p, q) in THRESHOLDS:
+            r0, r1 = bands[(p, q)]
+            a, bb, _ = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, row_begin=r0, row_end=r1,
+                                          stream=stream.cuda_stream)
+            dist.barrier()
+            t0 = time.perf_counter()
+            got = shard.gather_pairs(a, bb, dst=0)
+            dt = time.perf_counter() - t0
+            if rank == 0:
+                gather.append({"threshold": f"{p}/{q}", "pairs": int(len(got[0])),
+                               "gather_ms": round(dt * 1e3, 2)})
+            del a, bb, got
+
     out = None
     if rank == 0:
         joins = []
@@ -468,6 +486,10 @@ def run_ours(args):
                "verify": {"survivors_per_s": round(surv * args.steps / (ver_ms / 1e3)),
                           "ms_per_step": round(ver_ms / args.steps, 3)},
                "generation_s": round(gen_s, 2)}
+        if gather:
+            out["band_gather"] = {"how": "counts, then int64 keys padded to the largest count, "
+                                         "one torch.distributed gather to rank 0, merged there",
+                                  "joins": gather}
 
     # ---- extras: the same 10M collection with prefix-filter candidates and the cutoff ----
     if rank == 0 and world == 1:

@@ -59,13 +59,47 @@ def merge_pairs(parts):
     return a[order], b[order]
 
 
-def gather_pairs(a, b, group=None):
-    """Gather every rank's pair list (torch.distributed, any backend) and merge."""
+def gather_pairs(a, b, group=None, dst=None):
+    """Gather every rank's pair list as fixed-dtype tensors and merge.
+
+    The counts go first (one all_gather of an int64 each); then every rank's
+    pairs travel as int64 keys (a << 32 | b), padded to the largest count, in
+    one all_gather (dst None: every rank gets the merged list) or one gather
+    to rank dst (the others get None).  Tensors live on the CPU for gloo and
+    on the current CUDA device for NCCL.  Each rank's list is sorted and the
+    bands are disjoint, so the merge is a stable sort of the concatenated runs.
+    """
+    import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)
-    out = [None] * world
-    dist.all_gather_object(out, (np.asarray(a, np.uint32), np.asarray(b, np.uint32)), group=group)
-    return merge_pairs(out)
+    rank = dist.get_rank(group)
+    dev = (torch.device("cuda", torch.cuda.current_device())
+           if dist.get_backend(group) == "nccl" else torch.device("cpu"))
+    a = np.asarray(a, np.uint32).astype(np.int64)
+    b = np.asarray(b, np.uint32).astype(np.int64)
+    mine = torch.from_numpy((a << 32) | b).to(dev)
+    cnt = torch.tensor([mine.numel()], dtype=torch.int64, device=dev)
+    counts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(counts, cnt, group=group)
+    counts = [int(c.item()) for c in counts]
+    m = max(counts) if counts else 0
+    if m == 0:
+        empty = (np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+        return empty if dst is None or rank == dst else None
+    padded = torch.zeros(m, dtype=torch.int64, device=dev)
+    padded[:mine.numel()] = mine
+    if dst is None:
+        bufs = [torch.empty(m, dtype=torch.int64, device=dev) for _ in range(world)]
+        dist.all_gather(bufs, padded, group=group)
+    else:
+        bufs = [torch.empty(m, dtype=torch.int64, device=dev) for _ in range(world)] \
+            if rank == dst else None
+        dist.gather(padded, bufs, dst=dst, group=group)
+        if rank != dst:
+            return None
+    keys = np.concatenate([bufs[r][:counts[r]].cpu().numpy() for r in range(world)])
+    keys = np.sort(keys, kind="stable")
+    return (keys >> 32).astype(np.uint32), (keys & 0xffffffff).astype(np.uint32)
 
 
 def sharded_self_join(offsets, tokens, p: int, q: int, rank: int, world: int, **kw):

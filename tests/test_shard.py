@@ -112,6 +112,47 @@ def _gloo_worker(rank, world, port, result_path):
     dist.destroy_process_group()
 
 
+def _gloo_big_worker(rank, world, port, result_path):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # 1,700 copies of one set (C(1700, 2) = 1,444,150 similar pairs) among random sets
+    off, tok = I.random_collection(1200, 300, 1, 25, seed=19, planted_frac=0.2)
+    sets = [tok[off[i]:off[i + 1]] for i in range(len(off) - 1)]
+    sets += [np.array([4, 9, 17], np.int32)] * 1700
+    off = np.zeros(len(sets) + 1, np.int64)
+    off[1:] = np.cumsum([len(x) for x in sets])
+    tok = np.concatenate(sets).astype(np.int32)
+    full_a, full_b = O.self_join(off, tok, 3, 5)
+    r0, r1 = shard.band_split(off, 3, 5, world)[rank]
+    a, b = _band_of_pairs(off, full_a, full_b, r0, r1)
+    ma, mb = shard.gather_pairs(a, b)                 # every rank gets the merged list
+    ok = len(full_a) > 1_000_000 and np.array_equal(ma, full_a) and np.array_equal(mb, full_b)
+    got = shard.gather_pairs(a, b, dst=0)             # rank 0 only
+    if rank == 0:
+        ok = ok and np.array_equal(got[0], full_a) and np.array_equal(got[1], full_b)
+    else:
+        ok = ok and got is None
+    oks = [None] * world
+    dist.all_gather_object(oks, ok)
+    if rank == 0:
+        with open(result_path, "w") as f:
+            f.write("ok" if all(oks) else "mismatch")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_two_ranks_gather_a_million_pairs(tmp_path):
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    path = str(tmp_path / "result.txt")
+    mp.spawn(_gloo_big_worker, args=(2, port, path), nprocs=2, join=True)
+    assert open(path).read() == "ok"
+
+
 def test_gloo_two_ranks_gather(tmp_path):
     import torch.multiprocessing as mp
     with socket.socket() as s:
