@@ -5,7 +5,9 @@
 
 The collection is the 1,000,000-set workload shape (Zipf(s=1.1) tokens over
 200,000, sizes lognormal(2.3, 0.6) in [1, 500]) truncated or extended to
---sets sets (seed 0).  The join runs --repeat times with the survivor queue
+--sets sets (seed 0); --shape 10m takes the 10,000,000-set workload's shape
+instead (Zipf(s=1.0) over 1,000,000, sizes lognormal(2.0, 0.8) in [1, 1000],
+drawn on the device).  The join runs --repeat times with the survivor queue
 sized from a first call, so that a profiler sees steady-state launches.
 With --rs-sets N the join is an RS-join against a second collection of the
 same shape with N sets (seed 1).
@@ -34,14 +36,18 @@ def main():
     ap.add_argument("--cutoff", type=int, default=0, help="cutoff point (-1: from Eq. 4-6)")
     ap.add_argument("--rs-sets", type=int, default=0, help="RS-join against this many sets")
     ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--shape", default="1m", choices=("1m", "10m"))
     args = ap.parse_args()
 
     import torch
     from paper_1711_07295_b300 import _bmj, inputs
-    spec = inputs.spec_1m(seed=0)
+    spec = inputs.spec_1m(seed=0) if args.shape == "1m" else inputs.spec_10m(seed=0)
     spec = inputs.CollectionSpec(args.sets, spec.universe, spec.zipf_s, spec.size_dist, seed=0)
-    off, tok = inputs.gen_collection(spec)
-    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    if args.shape == "10m":
+        d_off, d_tok = inputs.gen_collection_device(spec)
+    else:
+        off, tok = inputs.gen_collection(spec)
+        d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
     m = _bmj.METHODS[args.method]
     sim = {"jaccard": _bmj.BMJ_JACCARD, "cosine": _bmj.BMJ_COSINE, "dice": _bmj.BMJ_DICE,
            "overlap": _bmj.BMJ_OVERLAP}[args.sim]
