@@ -123,7 +123,13 @@ typedef struct {
                                   survivors fit, each verified before the next
                                   (stats.filter_passes counts the passes) */
     void   *stream;            /* cudaStream_t; NULL = legacy default stream */
-    int32_t rows_per_thread;   /* filter register blocking: 0 = automatic */
+    int32_t rows_per_thread;   /* bmj_self_join_batch: rows per lane of the filter's row tile.
+                                  0 (default) = per job, the width's default tile (as in
+                                  bmj_self_join) or a small one (a quarter or fewer of the
+                                  rows) where the default tile's diagonal would waste a large
+                                  share of a small job's window (cost model in the tuner);
+                                  a value below the width's default forces the small tile,
+                                  any other value the default */
     int32_t use_graph;         /* bmj_self_join_batch: run the execute stage as a CUDA graph */
     int32_t cascade_b;         /* bmj_self_join, bmj_rs_join: width of a second Bitmap Filter
                                   applied to the survivors before merging (0 = automatic: 256
@@ -184,6 +190,9 @@ typedef struct {
     int64_t candidate_slots;/* BMJ_CAND_PREFIX: (rank, pair) slots the candidates were expanded
                                from (a pair sharing k prefix tokens has k slots); they go
                                through a buffer of fixed size in filter_passes ranges */
+    int32_t tile_rows;      /* bmj_self_join_batch job stats: rows of the job's filter tile
+                               (32 x rows per lane) */
+    int32_t chunk_cols;     /* ... and columns per filter work item */
 } bmj_stats;
 
 /* Counters and stage times of one bmj_self_join_batch call. */

@@ -86,7 +86,7 @@ class bmj_stats(C.Structure):
                 ("cascade_b", C.c_int32), ("cutoff", C.c_int32), ("ms_prepare", C.c_float),
                 ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
                 ("ms_total", C.c_float), ("reserved_f", C.c_float), ("candidates", C.c_int64),
-                ("candidate_slots", C.c_int64)]
+                ("candidate_slots", C.c_int64), ("tile_rows", C.c_int32), ("chunk_cols", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -404,11 +404,13 @@ def bmj_rs_join(r_offsets, r_tokens, s_offsets, s_tokens, p: int, q: int, b: int
 def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int = BMJ_XOR,
                         output_on_device: bool = False, queue_cap: int = 0,
                         validate: bool = True, use_graph: bool = False, stream=None,
-                        sim: int = BMJ_JACCARD, cascade_b: int = 0):
+                        sim: int = BMJ_JACCARD, cascade_b: int = 0, rows_per_thread: int = 0):
     """Independent self-joins of the jobs ``job_sets`` of one concatenated collection.
 
     ``job_sets`` int64[n_jobs+1] set boundaries, ``p``/``q`` per-job thresholds;
-    ``b = 0`` autotunes b per job.  Returns ``(pairs, job_stats, batch_stats)``
+    ``b = 0`` autotunes b per job; ``rows_per_thread`` 0 picks each job's row
+    tile, a value below a width's default forces the small tile.  Returns
+    ``(pairs, job_stats, batch_stats)``
     where ``pairs[k]`` is ``(a, b)`` numpy uint32 arrays in job-local ids.
     """
     coll, keep = make_collection(offsets, tokens)
@@ -426,6 +428,7 @@ def bmj_self_join_batch(offsets, tokens, job_sets, p, q, b: int = 0, method: int
     o.queue_cap = int(queue_cap)
     o.use_graph = 1 if use_graph else 0
     o.cascade_b = int(cascade_b)
+    o.rows_per_thread = int(rows_per_thread)
     o.stream = _stream_of(stream, coll.on_device)
     outs = (bmj_pairs * max(n_jobs, 1))()
     jst = (bmj_stats * max(n_jobs, 1))()

@@ -33,6 +33,19 @@ namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
+// Rows per lane of the small row tile of each width (the default tile is the
+// single join's: kTmaR1, kTmaR2, kTmaR4), the tile classes (three widths, two
+// tiles each, then every other width) and the counters of a plan.
+constexpr int kSmallR1 = 2, kSmallR2 = 1, kSmallR4 = 1;
+constexpr int kClasses = 7;
+constexpr int kCounters = 3 + kClasses;
+#ifndef BMJ_SMALL_COST
+#define BMJ_SMALL_COST 1.3, 1.3, 1.3
+#endif
+constexpr double kSmallCosts[3] = {BMJ_SMALL_COST};
+constexpr double kSmallCost1 = kSmallCosts[0], kSmallCost2 = kSmallCosts[1],
+                 kSmallCost4 = kSmallCosts[2];
+
 struct JobDesc {
     const uint64_t *bm;  // bitmap array of the job's width (indexed by global sorted position)
     const uint64_t *bm2; // cascade bitmaps (256 bits) checked before a merge, or null
@@ -220,6 +233,10 @@ struct BatchFilterArgs {
 // one row in eight at b = 64 (249.7 against 251.6 ms for the 512-job batch).
 template <int W>
 constexpr int kBatchAlu = W == 1 ? kAluRowsW1 : 0;
+// ... in tiles of the default height only (one row in eight): a small tile keeps
+// every row on POPC
+template <int W, int R>
+constexpr int kBatchAluR = R >= 8 ? kBatchAlu<W> : 0;
 
 // Resident 4-warp blocks per SM of the batched filter at b = 64: eight (64
 // registers, 8 bytes spilled) ran the 512-job execute stage in 248.2 ms against
@@ -253,7 +270,7 @@ __global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS 
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
         const SimArgs sa{jd.win, jd.p, jd.q, 0xffffffffu, a.one};
-        filter_item_tma<W, R, CS, kBatchAlu<W>, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0,
+        filter_item_tma<W, R, CS, kBatchAluR<W, R>, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0,
                                                       c0, c1, sa, sink, stg);
         if (!stg.ok) {
             drain_stage(stg);
@@ -396,8 +413,9 @@ struct Plan {
     int64_t n_tiles = 0;
     int32_t *tile_job = nullptr;
     int64_t *tile_i0 = nullptr, *tile_c0 = nullptr, *tile_off = nullptr;
-    // tile ranges of the width classes (b = 64, 128, 256, other), in tile order
-    int64_t class_t0[4] = {0, 0, 0, 0}, class_t1[4] = {0, 0, 0, 0};
+    // tile ranges of the tile classes (tile_class: b = 64, 128, 256 each with its
+    // default and its small row tile, then other widths), in tile order
+    int64_t class_t0[kClasses] = {0}, class_t1[kClasses] = {0};
     // counters: [1] survivors, [2] results, [3 + c] item counter of class c
     unsigned long long *ctr = nullptr;
     unsigned long long *job_surv = nullptr;
@@ -466,7 +484,26 @@ int upload_jobs(Plan &P, Arena &A, cudaStream_t s) {
     return BMJ_OK;
 }
 
-int width_class(int W) { return W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : 3; }
+// Tile class of a job: its width and its rows per lane (the default of the
+// single join, or the small tile for jobs whose diagonal tiles would waste a
+// large share of their window; see the tuner).
+int tile_class(int W, int tile_rows) {
+    switch (W) {
+        case 1: return tile_rows == 32 * kTmaR1 ? 0 : 1;
+        case 2: return tile_rows == 32 * kTmaR2 ? 2 : 3;
+        case 4: return tile_rows == 32 * kTmaR4 ? 4 : 5;
+        default: return 6;
+    }
+}
+int default_tile_rows(int W) {
+    return W == 1 ? 32 * kTmaR1 : W == 2 ? 32 * kTmaR2 : W == 4 ? 32 * kTmaR4 : 32;
+}
+int small_tile_rows(int W) {
+    return W == 1 ? 32 * kSmallR1 : W == 2 ? 32 * kSmallR2 : W == 4 ? 32 * kSmallR4 : 32;
+}
+// Filter time per evaluated pair in the small tile relative to the default
+// tile of the width (measured on a B300 with large jobs forced to each tile).
+double small_tile_cost(int W) { return W == 1 ? kSmallCost1 : W == 2 ? kSmallCost2 : kSmallCost4; }
 
 template <int W, int R, int CS, bool kCos>
 int launch_class_c(const BatchFilterArgs &fa, int64_t t0, int64_t t1, unsigned long long *counter,
@@ -506,15 +543,18 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
     fa.job_surv = P.job_surv;
     fa.qcap = P.qcap;
     fa.err = P.err;
-    for (int c = 0; c < 4; c++) {
+    for (int c = 0; c < kClasses; c++) {
         const int64_t t0 = P.class_t0[c], t1 = P.class_t1[c];
         if (t1 <= t0) continue;
         unsigned long long *counter = &P.ctr[3 + c];
         int st = BMJ_OK;
         switch (c) {
             case 0: st = launch_class<1, kTmaR1, 256>(fa, t0, t1, counter, sms, s); break;
-            case 1: st = launch_class<2, kTmaR2, 256>(fa, t0, t1, counter, sms, s); break;
-            case 2: st = launch_class<4, kTmaR4, 128>(fa, t0, t1, counter, sms, s); break;
+            case 1: st = launch_class<1, kSmallR1, 256>(fa, t0, t1, counter, sms, s); break;
+            case 2: st = launch_class<2, kTmaR2, 256>(fa, t0, t1, counter, sms, s); break;
+            case 3: st = launch_class<2, kSmallR2, 256>(fa, t0, t1, counter, sms, s); break;
+            case 4: st = launch_class<4, kTmaR4, 128>(fa, t0, t1, counter, sms, s); break;
+            case 5: st = launch_class<4, kSmallR4, 128>(fa, t0, t1, counter, sms, s); break;
             default: {
                 int per_sm = 0;
                 BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_generic,
@@ -532,7 +572,7 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
 // The execute stage: clear counters, filter every job, verify every survivor.
 // No allocation and no host read: capturable into a CUDA graph.
 int enqueue_execute(const Plan &P, int sms, cudaStream_t s) {
-    BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 8 * sizeof(unsigned long long), s));
+    BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, kCounters * sizeof(unsigned long long), s));
     BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, P.n_jobs * sizeof(unsigned long long), s));
     int st = enqueue_filter(P, sms, s);
     if (st) return st;
@@ -598,6 +638,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
     std::vector<int64_t> result_bounds(n_jobs + 1, 0);
     std::vector<uint32_t> res_a, res_b;
     std::vector<int> job_b(n_jobs, o.b > 0 ? o.b : 64), job_method(n_jobs, o.method);
+    std::vector<char> job_small(n_jobs, 0);  // 1: the job's tiles are the small row tile
     for (int64_t k = 0; k < n_jobs; k++)
         if (o.method == BMJ_COMBINED) job_method[k] = combined_method(sim, hp[k], hq[k]);
     std::vector<unsigned long long> job_win(n_jobs, 0), job_sv(n_jobs, 0);
@@ -644,7 +685,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         if (!st) st = A.alloc(&P.lim, (size_t)(P.n_s * n_jobs));
         if (!st) st = A.alloc(&jp, (size_t)n_jobs);
         if (!st) st = A.alloc(&jq, (size_t)n_jobs);
-        if (!st) st = A.alloc(&P.ctr, 8);
+        if (!st) st = A.alloc(&P.ctr, kCounters);
         if (!st) st = A.alloc(&P.job_surv, (size_t)n_jobs);
         if (!st) st = A.alloc(&P.err, 1);
         if (st) return st;
@@ -724,9 +765,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 jd.sim = sim;
                 jd.win = sim_window(sim, hp[k], hq[k]);
                 jd.W = jb[k] / 64;
-                jd.tile_rows = jd.W == 1 ? 32 * kTmaR1
-                               : jd.W == 2 ? 32 * kTmaR2
-                               : jd.W == 4 ? 32 * kTmaR4 : 32;
+                jd.tile_rows = job_small[k] ? small_tile_rows(jd.W) : default_tile_rows(jd.W);
                 jd.chunk_cols = 4096;
             }
         };
@@ -766,7 +805,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
             }
             auto sample_tiles = [&](int width, std::vector<int32_t> &tj, std::vector<int64_t> &tl) {
                 const int wq = width / 64;
-                const int tr = wq == 1 ? 32 * kTmaR1 : wq == 2 ? 32 * kTmaR2 : wq == 4 ? 32 * kTmaR4 : 32;
+                const int tr = default_tile_rows(wq);
                 tj.clear();
                 tl.clear();
                 for (size_t r = 0; r < s_rows_job.size(); r++) {
@@ -796,13 +835,14 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 sample_tiles(widths[wi], tj, tl);
                 unsigned long long *twin = nullptr;
                 st = build_tiles(P, tj, tl, false, {}, {}, A, s, &twin);
-                for (int c = 0; c < 4; c++) P.class_t0[c] = P.class_t1[c] = 0;
-                P.class_t1[width_class(widths[wi] / 64)] = P.n_tiles;
+                for (int c = 0; c < kClasses; c++) P.class_t0[c] = P.class_t1[c] = 0;
+                P.class_t1[tile_class(widths[wi] / 64, default_tile_rows(widths[wi] / 64))] =
+                    P.n_tiles;
                 if (st) return st;
                 std::vector<unsigned long long> h_twin(P.n_tiles);
                 BMJ_CHECK(cudaMemcpyAsync(h_twin.data(), twin, P.n_tiles * sizeof(unsigned long long),
                                           cudaMemcpyDeviceToHost, s));
-                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, 8 * sizeof(unsigned long long), s));
+                BMJ_CHECK(cudaMemsetAsync(P.ctr, 0, kCounters * sizeof(unsigned long long), s));
                 BMJ_CHECK(cudaMemsetAsync(P.job_surv, 0, n_jobs * sizeof(unsigned long long), s));
                 st = enqueue_filter(P, sms, s);
                 if (st) return st;
@@ -871,25 +911,48 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         }
         BMJ_CHECK(cudaEventRecord(ev.e[4], s));
 
+        // ---- row tile per job ----
+        // A tile of T rows evaluates every pair of its column range, also the
+        // T(T-1)/2 pairs at or above the diagonal (masked out), so a job of N
+        // sets in tiles of T rows evaluates about its window plus N*T/2 pairs.
+        // The small tile wastes less of a small job's window but costs more
+        // per evaluated pair (fewer rows share each staged column); per job the
+        // cheaper of the two is taken, or the caller's choice.
+        for (int64_t k = 0; k < n_jobs; k++) {
+            const int W = job_b[k] / 64;
+            const double nk = (double)(job_sets[k + 1] - job_sets[k]);
+            const double cost_d = (double)job_win[k] + nk * default_tile_rows(W) / 2.0;
+            const double cost_s =
+                ((double)job_win[k] + nk * small_tile_rows(W) / 2.0) * small_tile_cost(W);
+            if (o.rows_per_thread > 0)
+                job_small[k] = o.rows_per_thread * 32 < default_tile_rows(W) ? 1 : 0;
+            else
+                job_small[k] = (W == 1 || W == 2 || W == 4) && cost_s < cost_d ? 1 : 0;
+        }
+        set_jobs(job_b);
+        st = upload_jobs(P, A, s);
+        if (st) return st;
+
         // ---- tiles of every job ----
-        // jobs grouped by width class, so that each class is one tile range
+        // jobs grouped by tile class, so that each class is one tile range
         std::vector<int32_t> order(n_jobs);
         for (int64_t k = 0; k < n_jobs; k++) order[k] = (int32_t)k;
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
-            return width_class(P.jobs[a].W) < width_class(P.jobs[c].W);
+            return tile_class(P.jobs[a].W, P.jobs[a].tile_rows) <
+                   tile_class(P.jobs[c].W, P.jobs[c].tile_rows);
         });
         std::vector<int64_t> job_tile0(n_jobs + 1, 0);
-        for (int c = 0; c < 4; c++) P.class_t0[c] = P.class_t1[c] = 0;
+        for (int c = 0; c < kClasses; c++) P.class_t0[c] = P.class_t1[c] = 0;
         for (int64_t pos = 0; pos < n_jobs; pos++) {
             const int64_t k = order[pos];
             const int64_t nk = job_sets[k + 1] - job_sets[k];
             job_tile0[pos + 1] =
                 job_tile0[pos] + (nk >= 2 ? (nk + P.jobs[k].tile_rows - 1) / P.jobs[k].tile_rows : 0);
         }
-        for (int c = 0; c < 4; c++) {
+        for (int c = 0; c < kClasses; c++) {
             int64_t lo = -1, hi = -1;
             for (int64_t pos = 0; pos < n_jobs; pos++)
-                if (width_class(P.jobs[order[pos]].W) == c) {
+                if (tile_class(P.jobs[order[pos]].W, P.jobs[order[pos]].tile_rows) == c) {
                     if (lo < 0) lo = job_tile0[pos];
                     hi = job_tile0[pos + 1];
                 }
@@ -1022,6 +1085,8 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
             js.filter_passes = bs.filter_passes;
             js.b = job_b[k];
             js.method = job_method[k];
+            js.tile_rows = P.jobs.empty() ? 0 : P.jobs[k].tile_rows;
+            js.chunk_cols = P.jobs.empty() ? 0 : P.jobs[k].chunk_cols;
         }
     }
     bs.n_launches = (int32_t)(launches() - launches0);

@@ -66,6 +66,30 @@ def test_batch_matches_oracle(b):
     assert bst["results"] == sum(len(x[0]) for x in pairs)
 
 
+@pytest.mark.parametrize("b,rows", [(0, 0), (0, 1), (64, 1), (128, 1), (256, 1), (64, 8)])
+def test_batch_row_tiles(b, rows):
+    # The row tile per job: chosen by the tuner's cost model (rows = 0), the small tile
+    # forced for every job (rows below the width's default) or the default tile.  Pairs
+    # and counts are the oracle's whatever the tile, and the job stats record it.
+    jobs = make_batch(18, seed=60 + b + rows, lo=30, hi=4000)
+    off, tok, js, p, q = concat(jobs)
+    d_off, d_tok = torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda()
+    pairs, jst, bst = _bmj.bmj_self_join_batch(d_off, d_tok, js, p, q, b=b, rows_per_thread=rows,
+                                               use_graph=True)
+    check(jobs, pairs, jst)
+    default = {64: 256, 128: 128, 256: 128}
+    small = {64: 64, 128: 32, 256: 32}
+    for k, st in enumerate(jst):
+        assert st["tile_rows"] in (default[st["b"]], small[st["b"]]) and st["chunk_cols"] > 0
+        if rows == 1:
+            assert st["tile_rows"] == small[st["b"]]
+        if rows == 8:
+            assert st["tile_rows"] == default[st["b"]]
+    if rows == 0:   # jobs of a few dozen sets take the small tile, the largest the default
+        sizes = np.diff(js)
+        assert jst[int(np.argmin(sizes))]["tile_rows"] == small[jst[int(np.argmin(sizes))]["b"]]
+
+
 def test_batch_combined_method_and_host_input():
     jobs = make_batch(12, seed=7)
     off, tok, js, p, q = concat(jobs)
