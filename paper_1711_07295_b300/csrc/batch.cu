@@ -223,7 +223,6 @@ struct BatchFilterArgs {
     int64_t qcap;
     int *err;                      // set when a bounded wait on a copy gave up
     int sim;                       // similarity function of every job
-    int one = 1;                   // the constant 1 as a kernel argument (SimArgs::one)
 };
 
 // The Bitmap Filter over the work items of every job of one bitmap width:
@@ -269,7 +268,7 @@ __global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS 
         const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
-        const SimArgs sa{jd.win, jd.p, jd.q, 0xffffffffu, a.one};
+        const SimArgs sa{jd.win, jd.p, jd.q};
         filter_item_tma<W, R, CS, kBatchAluR<W, R>, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0,
                                                       c0, c1, sa, sink, stg);
         if (!stg.ok) {
@@ -300,7 +299,7 @@ __global__ void __launch_bounds__(256) k_filter_batch_generic(const BatchFilterA
         const int64_t c_end = min(i0 + (int64_t)jd.tile_rows, jd.end) - 1;
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
-        const SimArgs sa{jd.win, jd.p, jd.q, 0xffffffffu, a.one};
+        const SimArgs sa{jd.win, jd.p, jd.q};
         if (jd.sim == BMJ_COSINE)
             filter_item_generic<true>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, sa,
                                       jd.W, sink);

@@ -20,7 +20,7 @@ template <int W, int R, bool kCos>
 __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
     const int lane = threadIdx.x & 31;
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut, a.one};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs a) {
 __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int W) {
     const int lane = threadIdx.x & 31;
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut, a.one};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterAr
         st.skip_copy = (blockIdx.x == 0 && threadIdx.x < 32) ? 1 : 0;
     }
     const SurvivorSink sink{a.queue, a.qcount, nullptr, a.qcap};
-    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut, a.one};
+    const SimArgs sa{sim_window(a.sim, a.p, a.q), a.p, a.q, a.cut};
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(a.item_counter, 1ull);

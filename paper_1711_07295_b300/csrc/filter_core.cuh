@@ -50,9 +50,6 @@ struct SimArgs {
     SimWindow win;
     uint32_t p, q;
     uint32_t cut = 0xffffffffu;  // cutoff point: a pair whose larger size exceeds it skips Eq. 2
-    // 1, passed in from the host: multiples of it are integer multiply-adds the
-    // compiler cannot fold into shifts, so that they run on the FMA pipe
-    int one = 1;
 };
 
 // Eq. 2 limit of a pair of sizes: from the table indexed by |x|+|y| (Jaccard,
@@ -330,21 +327,7 @@ struct PopcHS<2> {
 
 template <>
 struct PopcHS<4> {
-    // 8 words: four carry-save adders -> 4 POPC.  t(): the popcount plus nlim,
-    // the weighted sums as multiply-adds by two and four (FMA pipe: the ALU
-    // pipe, which carries the xors and carry-save adders, is the bound here).
-    __device__ __forceinline__ static int t(const uint32_t *x, int nlim, int two, int four) {
-        const uint32_t s1 = x[0] ^ x[1] ^ x[2];
-        const uint32_t c1 = (x[0] & x[1]) | (x[2] & (x[0] ^ x[1]));
-        const uint32_t s2 = x[3] ^ x[4] ^ x[5];
-        const uint32_t c2 = (x[3] & x[4]) | (x[5] & (x[3] ^ x[4]));
-        const uint32_t s3 = s1 ^ s2 ^ x[6];
-        const uint32_t c3 = (s1 & s2) | (x[6] & (s1 ^ s2));
-        const uint32_t s4 = c1 ^ c2 ^ c3;
-        const uint32_t c4 = (c1 & c2) | (c3 & (c1 ^ c2));
-        const int t0 = __popc(s3) + __popc(x[7]) + nlim;
-        return four * __popc(c4) + (two * __popc(s4) + t0);
-    }
+    // 8 words: four carry-save adders -> 4 POPC.
     __device__ __forceinline__ static int h(const uint32_t *x) {
         const uint32_t s1 = x[0] ^ x[1] ^ x[2];
         const uint32_t c1 = (x[0] & x[1]) | (x[2] & (x[0] ^ x[1]));
@@ -357,13 +340,6 @@ struct PopcHS<4> {
         return __popc(s3) + __popc(x[7]) + 2 * __popc(s4) + 4 * __popc(c4);
     }
 };
-
-// At b = 256: 0 = the weighted popcount sums and the survive bit on the ALU
-// pipe; 1 = the sums as multiply-adds (FMA pipe); 2 = the survive bit too.
-#ifndef BMJ_W4_FMA
-#define BMJ_W4_FMA 0
-#endif
-constexpr int kW4Fma = BMJ_W4_FMA;
 
 // Shared-memory layout of one warp's column buffers.
 template <int W, int CS>
@@ -537,7 +513,6 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
 #pragma unroll
     for (int k = 0; k < R; k++) nlim[k] = 0;
     uint32_t prev_cs = 0xffffffffu;
-    const int two = sa.one + sa.one, four = two + two;
 
     const int64_t n_chunks = (c1 - c0 + CS - 1) / CS;
     // prefetch chunk 0 into slot 0
@@ -593,17 +568,11 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                     uint32_t x[2 * W];
 #pragma unroll
                     for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
-                    int t;
-                    if (W == 1 && kAluRows > 0 && k >= R - kAluRows)
-                        t = popc64_alu(x[0], x[1]) + nlim[k];
-                    else if (W == 4 && kW4Fma >= 1)
-                        t = PopcHS<4>::t(x, nlim[k], two, four);
-                    else
-                        t = PopcHS<W>::h(x) + nlim[k];
-                    if (W == 4 && kW4Fma >= 2)  // the survive bit (sign of t) by multiply-adds
-                        mask[k] = mask[k] * (uint32_t)two + __umulhi((uint32_t)t, (uint32_t)two);
-                    else
-                        mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);
+                    int h;
+                    if (W == 1 && kAluRows > 0 && k >= R - kAluRows) h = popc64_alu(x[0], x[1]);
+                    else h = PopcHS<W>::h(x);
+                    const int t = h + nlim[k];
+                    mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);
                 }
             }
             // bit (gj-1-cc) of mask[k] is column g+cc; keep only columns j < i

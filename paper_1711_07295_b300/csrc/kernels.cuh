@@ -85,7 +85,6 @@ struct FilterArgs {
     uint32_t p, q;
     int sim = BMJ_JACCARD;  // similarity function of the threshold p/q
     uint32_t cut = 0xffffffffu;  // cutoff point (Section 3.5); all ones: none
-    int one = 1;            // the constant 1 as a kernel argument (SimArgs::one)
     const int64_t *tile_item_off;  // [n_tiles + 1], exclusive scan of items per tile
     const int32_t *tile_c0;
     const int32_t *tile_c1 = nullptr;  // RS-join: end of each tile's columns (else the diagonal)
