@@ -39,12 +39,17 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kSmallR1 = 2, kSmallR2 = 1, kSmallR4 = 1;
 constexpr int kClasses = 7;
 constexpr int kCounters = 3 + kClasses;
-#ifndef BMJ_SMALL_COST
-#define BMJ_SMALL_COST 1.3, 1.3, 1.3
+#ifndef BMJ_SMALL_COST1
+#define BMJ_SMALL_COST1 1.3
 #endif
-constexpr double kSmallCosts[3] = {BMJ_SMALL_COST};
-constexpr double kSmallCost1 = kSmallCosts[0], kSmallCost2 = kSmallCosts[1],
-                 kSmallCost4 = kSmallCosts[2];
+#ifndef BMJ_SMALL_COST2
+#define BMJ_SMALL_COST2 1.3
+#endif
+#ifndef BMJ_SMALL_COST4
+#define BMJ_SMALL_COST4 1.3
+#endif
+constexpr double kSmallCost1 = BMJ_SMALL_COST1, kSmallCost2 = BMJ_SMALL_COST2,
+                 kSmallCost4 = BMJ_SMALL_COST4;
 
 struct JobDesc {
     const uint64_t *bm;  // bitmap array of the job's width (indexed by global sorted position)
@@ -548,12 +553,12 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
         unsigned long long *counter = &P.ctr[3 + c];
         int st = BMJ_OK;
         switch (c) {
-            case 0: st = launch_class<1, kTmaR1, 256>(fa, t0, t1, counter, sms, s); break;
-            case 1: st = launch_class<1, kSmallR1, 256>(fa, t0, t1, counter, sms, s); break;
-            case 2: st = launch_class<2, kTmaR2, 256>(fa, t0, t1, counter, sms, s); break;
-            case 3: st = launch_class<2, kSmallR2, 256>(fa, t0, t1, counter, sms, s); break;
-            case 4: st = launch_class<4, kTmaR4, 128>(fa, t0, t1, counter, sms, s); break;
-            case 5: st = launch_class<4, kSmallR4, 128>(fa, t0, t1, counter, sms, s); break;
+            case 0: st = launch_class<1, kTmaR1, kTmaCS1>(fa, t0, t1, counter, sms, s); break;
+            case 1: st = launch_class<1, kSmallR1, kTmaCS1>(fa, t0, t1, counter, sms, s); break;
+            case 2: st = launch_class<2, kTmaR2, kTmaCS2>(fa, t0, t1, counter, sms, s); break;
+            case 3: st = launch_class<2, kSmallR2, kTmaCS2>(fa, t0, t1, counter, sms, s); break;
+            case 4: st = launch_class<4, kTmaR4, kTmaCS4>(fa, t0, t1, counter, sms, s); break;
+            case 5: st = launch_class<4, kSmallR4, kTmaCS4>(fa, t0, t1, counter, sms, s); break;
             default: {
                 int per_sm = 0;
                 BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_generic,

@@ -195,9 +195,9 @@ int filter_tma_tile_rows(int W) {
 int launch_filter_tma(const FilterArgs &a, int W, int *err, int num_sms, cudaStream_t s) {
     if (a.n_items <= 0) return BMJ_OK;
     switch (W) {
-        case 1: return launch_filter_tma_t<1, kTmaR1, 256>(a, err, num_sms, s);
-        case 2: return launch_filter_tma_t<2, kTmaR2, 256>(a, err, num_sms, s);
-        case 4: return launch_filter_tma_t<4, kTmaR4, 128>(a, err, num_sms, s);
+        case 1: return launch_filter_tma_t<1, kTmaR1, kTmaCS1>(a, err, num_sms, s);
+        case 2: return launch_filter_tma_t<2, kTmaR2, kTmaCS2>(a, err, num_sms, s);
+        case 4: return launch_filter_tma_t<4, kTmaR4, kTmaCS4>(a, err, num_sms, s);
         default: return launch_filter(a, W, num_sms, s);
     }
 }
