@@ -281,8 +281,19 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                 unsigned long long *ccnt = nullptr;
                 st = PA.alloc(&cq, (size_t)chunk);
                 if (!st) st = PA.alloc(&ckeys, (size_t)chunk);
-                if (!st) st = PA.alloc(&ccnt, 1);
+                if (!st) st = PA.alloc(&ccnt, 2);  // [0] passed Eq. 2, [1] candidates
                 if (st) return st;
+                // The Bitmap Filter runs inside the expansion (only survivors are written)
+                // where the limit depends on |x|+|y| alone and b is 64, 128 or 256; the
+                // survivors then take the cascade check and the merge of the window path.
+                // Otherwise every candidate is written and verification applies Eq. 2.
+                PrefixTest test;
+                const bool fused = sim != BMJ_COSINE && (W == 1 || W == 2 || W == 4);
+                if (fused) {
+                    test.bm = bm;
+                    test.lim = lim;
+                    test.W = W;
+                }
                 stl.candidates = 0;
                 stl.survivors = 0;
                 stl.verified = 0;
@@ -290,31 +301,40 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                 float ms_expand = 0.f;
                 for (int64_t o0 = 0; o0 < px.slots; o0 += chunk) {
                     const int64_t o1 = std::min(px.slots, o0 + chunk);
-                    BMJ_CHECK(cudaMemsetAsync(ccnt, 0, sizeof(unsigned long long), s));
+                    BMJ_CHECK(cudaMemsetAsync(ccnt, 0, 2 * sizeof(unsigned long long), s));
                     BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
                     BMJ_CHECK(cudaEventRecord(ev.e[3], s));
-                    st = prefix_expand(px, o0, o1, cq, ccnt, s);
+                    st = prefix_expand(px, o0, o1, test, cq, &ccnt[0], &ccnt[1], s);
                     if (st) return st;
                     BMJ_CHECK(cudaEventRecord(ev.e[4], s));
-                    int64_t nc = 0;
-                    BMJ_CHECK(cudaMemcpyAsync(&nc, ccnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                    int64_t hc[2] = {0, 0};  // written pairs, candidates
+                    BMJ_CHECK(cudaMemcpyAsync(hc, ccnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
                     BMJ_CHECK(cudaStreamSynchronize(s));
                     ms_expand += ev.ms(3, 4);
-                    stl.candidates += nc;
+                    stl.candidates += hc[1];
                     stl.filter_passes++;
-                    if (nc == 0) continue;
-                    // Eq. 2 with the join's own bitmaps on every candidate, then the merge
+                    if (fused) stl.survivors += hc[0];
+                    if (hc[0] == 0) continue;
+                    // fused: the cascade check (if any) and the merge on the survivors;
+                    // otherwise Eq. 2 with the join's bitmaps on every candidate, then the merge
                     BMJ_CHECK(cudaEventRecord(ev.e[5], s));
-                    st = launch_verify(cq, nc, soff, stok, ssz, perm, need, lim, bm, W, ckeys,
-                                       &ctr[3], &ctr[4], nbits, sms, s, sim, p, q);
+                    st = fused ? launch_verify(cq, hc[0], soff, stok, ssz, perm, need, lim, bm2, W2,
+                                               ckeys, &ctr[3], bm2 ? &ctr[4] : nullptr, nbits, sms,
+                                               s, sim, p, q)
+                               : launch_verify(cq, hc[0], soff, stok, ssz, perm, need, lim, bm, W,
+                                               ckeys, &ctr[3], &ctr[4], nbits, sms, s, sim, p, q);
                     if (st) return st;
                     BMJ_CHECK(cudaEventRecord(ev.e[6], s));
                     int64_t hv2[2] = {0, 0};
                     BMJ_CHECK(cudaMemcpyAsync(hv2, &ctr[3], 2 * sizeof(int64_t),
                                               cudaMemcpyDeviceToHost, s));
                     BMJ_CHECK(cudaStreamSynchronize(s));
-                    stl.survivors += hv2[1];
-                    stl.verified += hv2[1];
+                    if (fused) {
+                        stl.verified += bm2 ? hv2[1] : hc[0];
+                    } else {
+                        stl.survivors += hv2[1];
+                        stl.verified += hv2[1];
+                    }
                     stl.ms_verify += ev.ms(5, 6);
                     st = append(ckeys, hv2[0]);
                     if (st) return st;

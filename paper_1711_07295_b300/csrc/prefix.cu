@@ -350,12 +350,15 @@ __device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ cand_off
     return a;
 }
 
+template <int W>
 __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                               const int64_t *__restrict__ cand_off, const int64_t *__restrict__ lo,
                               int64_t o0, int64_t o1, const uint32_t *__restrict__ ssz,
                               const int64_t *__restrict__ pofs, const uint32_t *__restrict__ pref,
-                              SimWindow win, int rshift, uint2 *__restrict__ out,
-                              unsigned long long *__restrict__ count) {
+                              SimWindow win, int rshift, const uint64_t *__restrict__ bm,
+                              const int32_t *__restrict__ lim, uint2 *__restrict__ out,
+                              unsigned long long *__restrict__ count,
+                              unsigned long long *__restrict__ n_cand) {
     constexpr int64_t kTile = 32 * kExpandPerLane;
     const int lane = threadIdx.x & 31;
     const uint64_t umask = (1ull << rshift) - 1;
@@ -394,12 +397,22 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                     else y++;
                 }
             }
-            const unsigned ball = __ballot_sync(kFullP, keep);
+            // the Bitmap Filter (Eq. 2) on the candidate, inside the window by construction
+            bool pass = keep;
+            if (W > 0 && keep) {
+                int h = 0;
+#pragma unroll
+                for (int w = 0; w < W; w++) h += __popcll(bm[(size_t)i * W + w] ^ bm[(size_t)j * W + w]);
+                pass = h <= lim[ssz[i] + ssz[j]];
+            }
+            const unsigned cball = __ballot_sync(kFullP, keep);
+            const unsigned ball = __ballot_sync(kFullP, pass);
+            if (lane == 0 && cball) atomicAdd(n_cand, (unsigned long long)__popc(cball));
             if (ball) {
                 unsigned long long pos = 0;
                 if (lane == 0) pos = atomicAdd(count, (unsigned long long)__popc(ball));
                 pos = __shfl_sync(kFullP, pos, 0);
-                if (keep) out[pos + __popc(ball & ((1u << lane) - 1u))] = make_uint2(i, j);
+                if (pass) out[pos + __popc(ball & ((1u << lane) - 1u))] = make_uint2(i, j);
             }
         }
     }
@@ -567,13 +580,22 @@ int prefix_index(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, 
     return BMJ_OK;
 }
 
-int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, uint2 *out,
-                  unsigned long long *count, cudaStream_t s) {
+int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, const PrefixTest &test,
+                  uint2 *out, unsigned long long *count, unsigned long long *n_cand,
+                  cudaStream_t s) {
     if (o1 <= o0 || ix.P == 0) return BMJ_OK;
     constexpr int64_t kTile = 32 * kExpandPerLane;
-    BMJ_LAUNCH(k_cand_expand, grid_p((o1 - o0 + kTile - 1) / kTile, 8, 148 * 64), 256, 0, s, ix.idx,
-               ix.P, ix.cand_off, ix.lo, o0, o1, ix.ssz, ix.pofs, ix.pref, ix.win, ix.rshift, out,
-               count);
+    const unsigned grid = grid_p((o1 - o0 + kTile - 1) / kTile, 8, 148 * 64);
+#define BMJ_EXPAND(KW)                                                                            \
+    BMJ_LAUNCH(k_cand_expand<KW>, grid, 256, 0, s, ix.idx, ix.P, ix.cand_off, ix.lo, o0, o1,       \
+               ix.ssz, ix.pofs, ix.pref, ix.win, ix.rshift, test.bm, test.lim, out, count, n_cand)
+    switch (test.bm ? test.W : 0) {
+        case 1: BMJ_EXPAND(1); break;
+        case 2: BMJ_EXPAND(2); break;
+        case 4: BMJ_EXPAND(4); break;
+        default: BMJ_EXPAND(0); break;
+    }
+#undef BMJ_EXPAND
     return BMJ_OK;
 }
 

@@ -34,12 +34,24 @@ int prefix_index(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, 
                  int64_t ntok, int64_t n_cols, SimWindow win, Arena &A, cudaStream_t s,
                  PrefixIndex *out);
 
+// The Bitmap Filter applied to the candidates as they are expanded: W words
+// per set (1, 2 or 4) in size order, and lim[|x|+|y|] of Eq. 2 against the
+// threshold (for the functions whose limit depends on the size sum alone).
+// W = 0: no test, every candidate is emitted.
+struct PrefixTest {
+    const uint64_t *bm = nullptr;
+    const int32_t *lim = nullptr;
+    int W = 0;
+};
+
 // Candidates of the slots [o0, o1): the pairs (i, j), j < i in size order
 // (RS: i in R, j in S) inside the window whose prefixes share a token, kept
 // at the slot of their lowest shared rank so that every pair appears once over
-// all slots.  Appends them to out (room for o1 - o0 pairs) and adds their
-// number to *count (device).
-int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, uint2 *out,
-                  unsigned long long *count, cudaStream_t s);
+// all slots.  Adds their number to *n_cand (device); appends to out (room for
+// o1 - o0 pairs) those that pass the test (all of them when test.W = 0) and
+// adds their number to *count (device).
+int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, const PrefixTest &test,
+                  uint2 *out, unsigned long long *count, unsigned long long *n_cand,
+                  cudaStream_t s);
 
 }  // namespace bmj
