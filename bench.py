@@ -504,7 +504,8 @@ def run_ours(args):
                     r.release()
                 wj = per_thr[(p, q)]["ms_total"] / args.steps
                 rows.append({"threshold": f"{p}/{q}", "candidates": st["candidates"],
-                             "candidate_passes": st.get("candidate_passes", 1),
+                             "candidate_slots": st["candidate_slots"],
+                             "candidate_ranges": st["filter_passes"],
                              "survivors": st["survivors"], "results": st["results"],
                              "join_ms": round(st["ms_total"], 2),
                              "candidate_ms": round(st["ms_filter"], 2),
@@ -659,7 +660,8 @@ def run_million(args, dev):
             wj = step64[f"{p}/{q}"]["join_ms"]
             rows.append({"threshold": f"{p}/{q}", "window_pairs": st["window_pairs"],
                          "candidates": st["candidates"],
-                         "candidate_passes": st.get("candidate_passes", 1),
+                         "candidate_slots": st["candidate_slots"],
+                         "candidate_ranges": st["filter_passes"],
                          "survivors": st["survivors"],
                          "results": st["results"], "join_ms": round(st["ms_total"], 3),
                          "candidate_ms": round(st["ms_filter"], 3), "window_join_ms": wj,
@@ -864,6 +866,8 @@ def run_live(idx, arr, qoff, qtok, p, q):
             "max_ms": round(float(lat.max()), 4), "qps": round(st["qps"], 1),
             "batches": int(st["batches"]), "results": int(n_res.sum()),
             "submit_lateness_p99_ms": round(float(np.percentile(late, 99)) * 1e3, 4),
+            "submit_lateness_max_ms": round(float(late.max()) * 1e3, 4),
+            "submit_lateness_worst_at_s": round(float(arr[int(np.argmax(late))]), 4),
             "how": "bmj_serve_submit at each arrival time and bmj_serve_poll between arrivals "
                    "from one host thread, the server's loop thread batching; latency = "
                    "completion - submission (library clock)"}

@@ -113,9 +113,18 @@ int filter_tile_rows(int W);
 #ifndef BMJ_TMA_CS2
 #define BMJ_TMA_CS2 256
 #endif
-constexpr int kTmaR1 = BMJ_TMA_R1, kTmaR2 = BMJ_TMA_R2, kTmaR4 = 4;
+#ifndef BMJ_TMA_CS1
+#define BMJ_TMA_CS1 256
+#endif
+#ifndef BMJ_TMA_CS4
+#define BMJ_TMA_CS4 128
+#endif
+#ifndef BMJ_TMA_R4
+#define BMJ_TMA_R4 4
+#endif
+constexpr int kTmaR1 = BMJ_TMA_R1, kTmaR2 = BMJ_TMA_R2, kTmaR4 = BMJ_TMA_R4;
 // Columns per staged chunk (one TMA bulk copy of bitmaps, one of sizes) per width.
-constexpr int kTmaCS1 = 256, kTmaCS2 = BMJ_TMA_CS2, kTmaCS4 = 128;
+constexpr int kTmaCS1 = BMJ_TMA_CS1, kTmaCS2 = BMJ_TMA_CS2, kTmaCS4 = BMJ_TMA_CS4;
 // At b = 64, rows per lane whose popcount runs on the ALU instead of POPC.
 #ifndef BMJ_ALU_ROWS_W1
 #define BMJ_ALU_ROWS_W1 1
