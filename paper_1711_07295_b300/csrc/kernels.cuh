@@ -110,14 +110,18 @@ int filter_tile_rows(int W);
 #ifndef BMJ_TMA_R2
 #define BMJ_TMA_R2 4
 #endif
+// Chunks of 128 columns at b = 128 and 64 at b = 256 (half the shared memory of
+// 256 and 128: more resident warps) measured 3.4% faster each; 128 at b = 64
+// and 64 at b = 128 were slower, as were 3 rows per lane at b = 128 and 2 at
+// b = 256 (1M workload and 2M sets of the 10M shape).
 #ifndef BMJ_TMA_CS2
-#define BMJ_TMA_CS2 256
+#define BMJ_TMA_CS2 128
 #endif
 #ifndef BMJ_TMA_CS1
 #define BMJ_TMA_CS1 256
 #endif
 #ifndef BMJ_TMA_CS4
-#define BMJ_TMA_CS4 128
+#define BMJ_TMA_CS4 64
 #endif
 #ifndef BMJ_TMA_R4
 #define BMJ_TMA_R4 4

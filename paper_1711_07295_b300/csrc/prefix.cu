@@ -336,7 +336,9 @@ __global__ void k_cand_count(const uint64_t *__restrict__ idx, int64_t P,
 // binary search between those two.  The pair (i, j) of a slot is kept when no
 // rank below the entry's is in both prefixes (sorted ranks of a prefix:
 // pref[pofs[x] ..]), so that a pair sharing several prefix tokens comes out
-// once.  Kept pairs are appended with one atomicAdd per warp and round.
+// once.  With W > 0 the pair then meets Eq. 2 with its W-word bitmaps.  The
+// pairs kept in a tile are appended with one atomicAdd per warp and tile; the
+// candidates are counted with one atomicAdd per warp.
 constexpr int kExpandPerLane = 8;
 
 __device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ cand_off, int64_t a,
@@ -364,6 +366,7 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
     const uint64_t umask = (1ull << rshift) - 1;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    unsigned n_keep = 0;  // this lane's candidates (fewer than 2^32 per lane)
     for (int64_t t0 = o0 + gw * kTile; t0 < o1; t0 += warps * kTile) {
         const int64_t t1 = min(t0 + kTile, o1);
         // lane 0: the first slot's entry, lane 1: the last slot's
@@ -371,19 +374,35 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
         if (lane < 2) kb = owner_of(cand_off, 0, P, lane == 0 ? t0 : t1 - 1);
         const int64_t ka = __shfl_sync(kFullP, kb, 0);
         const int64_t kz = __shfl_sync(kFullP, kb, 1) + 1;
+        // every round's kept pairs stay in registers; the tile reserves its
+        // output slots with one atomicAdd (same-address atomics per round were
+        // the bottleneck with billions of candidates)
+        uint32_t ii[kExpandPerLane], jj[kExpandPerLane];
+        uint32_t pmask = 0;
+#pragma unroll
         for (int m = 0; m < kExpandPerLane; m++) {
             const int64_t o = t0 + m * 32 + lane;
             bool keep = false;
-            uint32_t i = 0, j = 0;
+            uint32_t i = 0, j = 0, si = 0, sj = 0;
+            uint64_t bwi[W > 0 ? W : 1], bwj[W > 0 ? W : 1];
             if (o < t1) {
                 const int64_t k = owner_of(cand_off, ka, kz, o);
                 const uint64_t key = idx[k];
                 const uint32_t r = (uint32_t)(key & umask);
                 i = (uint32_t)(key >> rshift);
                 j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
+                // the bitmap words are loaded before the prefix merge, so that their
+                // latency overlaps it
+#pragma unroll
+                for (int w = 0; w < W; w++) {
+                    bwi[w] = bm[(size_t)i * W + w];
+                    bwj[w] = bm[(size_t)j * W + w];
+                }
+                si = ssz[i];
+                sj = ssz[j];
                 const uint32_t *pi = pref + pofs[i];
                 const uint32_t *pj = pref + pofs[j];
-                const int64_t ni = prefix_len(ssz[i], win), nj = prefix_len(ssz[j], win);
+                const int64_t ni = prefix_len(si, win), nj = prefix_len(sj, win);
                 int64_t x = 0, y = 0;
                 keep = true;
                 while (x < ni && y < nj) {
@@ -402,20 +421,35 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
             if (W > 0 && keep) {
                 int h = 0;
 #pragma unroll
-                for (int w = 0; w < W; w++) h += __popcll(bm[(size_t)i * W + w] ^ bm[(size_t)j * W + w]);
-                pass = h <= lim[ssz[i] + ssz[j]];
+                for (int w = 0; w < W; w++) h += __popcll(bwi[w] ^ bwj[w]);
+                pass = h <= lim[si + sj];
             }
-            const unsigned cball = __ballot_sync(kFullP, keep);
-            const unsigned ball = __ballot_sync(kFullP, pass);
-            if (lane == 0 && cball) atomicAdd(n_cand, (unsigned long long)__popc(cball));
-            if (ball) {
-                unsigned long long pos = 0;
-                if (lane == 0) pos = atomicAdd(count, (unsigned long long)__popc(ball));
-                pos = __shfl_sync(kFullP, pos, 0);
-                if (pass) out[pos + __popc(ball & ((1u << lane) - 1u))] = make_uint2(i, j);
+            n_keep += keep ? 1u : 0u;
+            ii[m] = i;
+            jj[m] = j;
+            pmask |= pass ? (1u << m) : 0u;
+        }
+        const int c = __popc(pmask);
+        const int total = __reduce_add_sync(kFullP, c);
+        if (total) {
+            int excl = c;  // exclusive scan of c over the lanes
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int u = __shfl_up_sync(kFullP, excl, d);
+                if (lane >= d) excl += u;
             }
+            excl -= c;
+            unsigned long long pos = 0;
+            if (lane == 0) pos = atomicAdd(count, (unsigned long long)total);
+            pos = __shfl_sync(kFullP, pos, 0) + excl;
+#pragma unroll
+            for (int m = 0; m < kExpandPerLane; m++)
+                if (pmask & (1u << m)) out[pos++] = make_uint2(ii[m], jj[m]);
         }
     }
+    // candidates: one atomicAdd per warp for its whole share
+    const unsigned tot_keep = __reduce_add_sync(kFullP, n_keep);
+    if (lane == 0 && tot_keep) atomicAdd(n_cand, (unsigned long long)tot_keep);
 }
 
 }  // namespace
