@@ -17,13 +17,7 @@
 #include "host_util.cuh"
 #include "prefix.cuh"
 
-#ifndef BMJ_PREFIX_FUSED
-#define BMJ_PREFIX_FUSED 1
-#endif
-
 namespace bmj {
-// 1: the Bitmap Filter runs inside the prefix-candidate expansion (see below).
-constexpr bool kPrefixFused = BMJ_PREFIX_FUSED != 0;
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -294,7 +288,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                 // survivors then take the cascade check and the merge of the window path.
                 // Otherwise every candidate is written and verification applies Eq. 2.
                 PrefixTest test;
-                const bool fused = kPrefixFused && sim != BMJ_COSINE && (W == 1 || W == 2 || W == 4);
+                const bool fused = sim != BMJ_COSINE && (W == 1 || W == 2 || W == 4);
                 if (fused) {
                     test.bm = bm;
                     test.lim = lim;
