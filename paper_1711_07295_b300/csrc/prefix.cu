@@ -352,6 +352,68 @@ __device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ cand_off
     return a;
 }
 
+// One candidate slot of the expansion: its entry and pair (fetch), the
+// partner data (load: sizes, prefix offsets and, with W > 0, bitmaps), the
+// prefix test (lowest_shared: no rank below the entry's in both prefixes) and
+// Eq. 2 (passes).
+template <int W>
+struct SlotLoad {
+    bool valid = false;
+    uint32_t i = 0, j = 0, r = 0, si = 0, sj = 0;
+    int64_t poi = 0, poj = 0;
+    uint64_t bwi[W > 0 ? W : 1], bwj[W > 0 ? W : 1];
+
+    __device__ __forceinline__ void fetch(int64_t o, int64_t t1, int64_t ka, int64_t kz,
+                                          const uint64_t *__restrict__ idx,
+                                          const int64_t *__restrict__ cand_off,
+                                          const int64_t *__restrict__ lo, uint64_t umask,
+                                          int rshift) {
+        valid = o < t1;
+        if (!valid) return;
+        const int64_t k = owner_of(cand_off, ka, kz, o);
+        const uint64_t key = idx[k];
+        r = (uint32_t)(key & umask);
+        i = (uint32_t)(key >> rshift);
+        j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
+    }
+    __device__ __forceinline__ void load(const uint32_t *__restrict__ ssz,
+                                         const int64_t *__restrict__ pofs,
+                                         const uint64_t *__restrict__ bm) {
+        if (!valid) return;
+        si = ssz[i];
+        sj = ssz[j];
+        poi = pofs[i];
+        poj = pofs[j];
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            bwi[w] = bm[(size_t)i * W + w];
+            bwj[w] = bm[(size_t)j * W + w];
+        }
+    }
+    __device__ __forceinline__ bool lowest_shared(const uint32_t *__restrict__ pref,
+                                                  SimWindow win) const {
+        const uint32_t *pi = pref + poi;
+        const uint32_t *pj = pref + poj;
+        const int64_t ni = prefix_len(si, win), nj = prefix_len(sj, win);
+        int64_t x = 0, y = 0;
+        while (x < ni && y < nj) {
+            const uint32_t rx = pi[x], ry = pj[y];
+            if (rx >= r || ry >= r) break;
+            if (rx == ry) return false;
+            if (rx < ry) x++;
+            else y++;
+        }
+        return true;
+    }
+    __device__ __forceinline__ bool passes(const int32_t *__restrict__ lim) const {
+        if (W == 0) return true;
+        int h = 0;
+#pragma unroll
+        for (int w = 0; w < W; w++) h += __popcll(bwi[w] ^ bwj[w]);
+        return h <= lim[si + sj];
+    }
+};
+
 template <int W>
 __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                               const int64_t *__restrict__ cand_off, const int64_t *__restrict__ lo,
@@ -379,55 +441,26 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
         // the bottleneck with billions of candidates)
         uint32_t ii[kExpandPerLane], jj[kExpandPerLane];
         uint32_t pmask = 0;
+        // two slots per lane in flight: every load of both is issued before
+        // either prefix merge, so that their latencies overlap
 #pragma unroll
-        for (int m = 0; m < kExpandPerLane; m++) {
-            const int64_t o = t0 + m * 32 + lane;
-            bool keep = false;
-            uint32_t i = 0, j = 0, si = 0, sj = 0;
-            uint64_t bwi[W > 0 ? W : 1], bwj[W > 0 ? W : 1];
-            if (o < t1) {
-                const int64_t k = owner_of(cand_off, ka, kz, o);
-                const uint64_t key = idx[k];
-                const uint32_t r = (uint32_t)(key & umask);
-                i = (uint32_t)(key >> rshift);
-                j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
-                // the bitmap words are loaded before the prefix merge, so that their
-                // latency overlaps it
-#pragma unroll
-                for (int w = 0; w < W; w++) {
-                    bwi[w] = bm[(size_t)i * W + w];
-                    bwj[w] = bm[(size_t)j * W + w];
-                }
-                si = ssz[i];
-                sj = ssz[j];
-                const uint32_t *pi = pref + pofs[i];
-                const uint32_t *pj = pref + pofs[j];
-                const int64_t ni = prefix_len(si, win), nj = prefix_len(sj, win);
-                int64_t x = 0, y = 0;
-                keep = true;
-                while (x < ni && y < nj) {
-                    const uint32_t rx = pi[x], ry = pj[y];
-                    if (rx >= r || ry >= r) break;
-                    if (rx == ry) {
-                        keep = false;
-                        break;
-                    }
-                    if (rx < ry) x++;
-                    else y++;
-                }
-            }
+        for (int m = 0; m < kExpandPerLane; m += 2) {
+            SlotLoad<W> a, b;
+            a.fetch(t0 + m * 32 + lane, t1, ka, kz, idx, cand_off, lo, umask, rshift);
+            b.fetch(t0 + (m + 1) * 32 + lane, t1, ka, kz, idx, cand_off, lo, umask, rshift);
+            a.load(ssz, pofs, bm);
+            b.load(ssz, pofs, bm);
+            const bool ka_ = a.valid && a.lowest_shared(pref, win);
+            const bool kb_ = b.valid && b.lowest_shared(pref, win);
             // the Bitmap Filter (Eq. 2) on the candidate, inside the window by construction
-            bool pass = keep;
-            if (W > 0 && keep) {
-                int h = 0;
-#pragma unroll
-                for (int w = 0; w < W; w++) h += __popcll(bwi[w] ^ bwj[w]);
-                pass = h <= lim[si + sj];
-            }
-            n_keep += keep ? 1u : 0u;
-            ii[m] = i;
-            jj[m] = j;
-            pmask |= pass ? (1u << m) : 0u;
+            const bool pa = ka_ && a.passes(lim);
+            const bool pb = kb_ && b.passes(lim);
+            n_keep += (ka_ ? 1u : 0u) + (kb_ ? 1u : 0u);
+            ii[m] = a.i;
+            jj[m] = a.j;
+            ii[m + 1] = b.i;
+            jj[m + 1] = b.j;
+            pmask |= (pa ? (1u << m) : 0u) | (pb ? (2u << m) : 0u);
         }
         const int c = __popc(pmask);
         const int total = __reduce_add_sync(kFullP, c);
