@@ -148,20 +148,25 @@ typedef struct {
                                   are expanded in ranges of at most queue_cap slots (0: a quarter
                                   of the free device memory), each filtered and verified before
                                   the next, so any number of them fits; it falls back to the
-                                  window only when the prefix index itself does not fit.  Needs
-                                  row_begin = row_end = 0 and cutoff = 0 */
+                                  window only when the prefix index itself does not fit.
+                                  BMJ_CAND_AUTO builds the prefix index and takes the prefix
+                                  filter or the window, whichever its slot count says is faster.
+                                  Both need row_begin = row_end = 0 and cutoff = 0 */
     int32_t cutoff;            /* bmj_self_join, bmj_rs_join: the cutoff point of Section 3.5.
                                   0 (default) = none, every window pair meets the Bitmap Filter
                                   (the paper's GPU setting); n > 0 = a pair whose larger set has
                                   more than n tokens skips the filter and is verified directly;
                                   BMJ_CUTOFF_AUTO = n from Eq. 4-6 for b, the method used and the
                                   normalised threshold (Jaccard 2p/(p+q), Dice and Cosine p/q;
-                                  none for Overlap).  With BMJ_CAND_PREFIX it must be 0. */
+                                  none for Overlap).  With BMJ_CAND_PREFIX or AUTO it must be 0. */
 } bmj_options;
 
 #define BMJ_CUTOFF_AUTO (-1)
 #define BMJ_CAND_WINDOW 0
 #define BMJ_CAND_PREFIX 1
+#define BMJ_CAND_AUTO   2   /* the prefix filter when its candidate slots are few enough for the
+                               expansion to beat the whole window (a per-width cost ratio
+                               measured on a B300), else the window */
 
 /* Counters and stage times of one join.  Pair counts are exact and do not
  * depend on the launch configuration. */
@@ -186,8 +191,9 @@ typedef struct {
     int64_t candidates;     /* BMJ_CAND_PREFIX: distinct prefix-filter candidates, which the
                                Bitmap Filter then evaluated (survivors counts those passing it);
                                0 in window mode; -1 when prefix mode fell back to the window
-                               (only when the prefix index itself does not fit in memory) */
-    int64_t candidate_slots;/* BMJ_CAND_PREFIX: (rank, pair) slots the candidates were expanded
+                               (only when the prefix index itself does not fit in memory); -2
+                               when BMJ_CAND_AUTO chose the window */
+    int64_t candidate_slots;/* BMJ_CAND_PREFIX / AUTO: (rank, pair) slots the candidates were expanded
                                from (a pair sharing k prefix tokens has k slots); they go
                                through a buffer of fixed size in filter_passes ranges */
     int32_t tile_rows;      /* bmj_self_join_batch job stats: rows of the job's filter tile

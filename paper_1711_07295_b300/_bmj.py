@@ -31,6 +31,7 @@ BMJ_PENDING = 1   # bmj_serve_poll: the query has not completed yet (not an erro
 BMJ_XOR, BMJ_SET, BMJ_NEXT, BMJ_COMBINED = 0, 1, 2, 3
 BMJ_JACCARD, BMJ_COSINE, BMJ_DICE, BMJ_OVERLAP = 0, 1, 2, 3   # similarity functions (Table 1)
 BMJ_CAND_WINDOW, BMJ_CAND_PREFIX = 0, 1   # candidate pairs: the whole window, or the prefix filter
+BMJ_CAND_AUTO = 2   # the prefix filter or the window, whichever the slot count says is faster
 BMJ_CUTOFF_AUTO = -1   # bmj_options.cutoff: the cutoff point from Eq. 4-6 (Section 3.5)
 METHODS = {"xor": BMJ_XOR, "set": BMJ_SET, "next": BMJ_NEXT, "combined": BMJ_COMBINED}
 

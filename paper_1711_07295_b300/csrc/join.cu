@@ -19,6 +19,15 @@
 
 namespace bmj {
 
+// Time of one prefix-candidate slot (expansion, Eq. 2, its share of the
+// verification) in window pairs of the Bitmap Filter at W words, measured on a
+// B300: about 35 ps per slot against 0.42, 0.65 and 1.15 ps per window pair at
+// b = 64, 128, 256 (BMJ_CAND_AUTO takes the prefix filter when
+// slots x this < window pairs).
+static double slot_cost_in_pairs(int W) {
+    return W == 1 ? 80.0 : W == 2 ? 55.0 : W == 4 ? 30.0 : 80.0 / W;
+}
+
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
@@ -252,7 +261,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
         // free memory, or opt.queue_cap slots), and each range's candidates pass
         // Eq. 2 with the join's bitmaps and the merge before the next range.
         bool done = false;
-        if (o.candidates == BMJ_CAND_PREFIX) {
+        if (o.candidates == BMJ_CAND_PREFIX || o.candidates == BMJ_CAND_AUTO) {
             Arena PA(s);  // its buffers go once the candidates are verified
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
             PrefixIndex px;
@@ -263,6 +272,12 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                 stl.candidates = -1;
             } else if (pst) {
                 return pst;
+            } else if (o.candidates == BMJ_CAND_AUTO &&
+                       (double)px.slots * slot_cost_in_pairs(W) >= (double)stl.window_pairs) {
+                // the whole window is cheaper than expanding this many slots
+                PA.release();
+                stl.candidates = -2;
+                stl.candidate_slots = px.slots;
             } else {
                 float ms_index = 0.f;
                 BMJ_CHECK(cudaEventRecord(ev.e[4], s));
@@ -688,8 +703,10 @@ int bmj_self_join(const bmj_collection *coll, int sim, uint32_t p, uint32_t q,
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     if (o.row_begin < 0 || o.row_end < 0 || o.row_end < o.row_begin) return BMJ_ERR_INVALID_ARG;
-    if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX) return BMJ_ERR_INVALID_ARG;
-    if (o.candidates == BMJ_CAND_PREFIX && (o.row_begin != 0 || o.row_end != 0 || o.cutoff != 0))
+    if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX &&
+        o.candidates != BMJ_CAND_AUTO)
+        return BMJ_ERR_INVALID_ARG;
+    if (o.candidates != BMJ_CAND_WINDOW && (o.row_begin != 0 || o.row_end != 0 || o.cutoff != 0))
         return BMJ_ERR_INVALID_ARG;
     if (o.cutoff < BMJ_CUTOFF_AUTO) return BMJ_ERR_INVALID_ARG;
     if ((o.row_begin != 0 || o.row_end != 0) && o.row_end > coll->n_sets) return BMJ_ERR_INVALID_ARG;
@@ -724,9 +741,11 @@ int bmj_rs_join(const bmj_collection *r, const bmj_collection *s, int sim, uint3
     if (o.queue_cap < 0) return BMJ_ERR_INVALID_ARG;
     if (o.cascade_b != 0 && o.cascade_b != -1 && !bmj::valid_b(o.cascade_b)) return BMJ_ERR_INVALID_ARG;
     if (o.row_begin != 0 || o.row_end != 0) return BMJ_ERR_INVALID_ARG;
-    if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates != BMJ_CAND_WINDOW && o.candidates != BMJ_CAND_PREFIX &&
+        o.candidates != BMJ_CAND_AUTO)
+        return BMJ_ERR_INVALID_ARG;
     if (o.cutoff < BMJ_CUTOFF_AUTO) return BMJ_ERR_INVALID_ARG;
-    if (o.candidates == BMJ_CAND_PREFIX && o.cutoff != 0) return BMJ_ERR_INVALID_ARG;
+    if (o.candidates != BMJ_CAND_WINDOW && o.cutoff != 0) return BMJ_ERR_INVALID_ARG;
     try {
         st = bmj::self_join_impl(r, s, sim, p, q, o, out, stats);
     } catch (...) {

@@ -493,6 +493,38 @@ def test_prefix_filter_large_sets_and_token_values(large_values):
         assert (st["candidates"], st["survivors"], st["results"]) == (c, s, r) and r > 0
 
 
+@pytest.mark.parametrize("p,q", [(1, 2), (4, 5), (19, 20)])
+def test_automatic_candidates_small(p, q):
+    # BMJ_CAND_AUTO takes the prefix filter or the window; either way the pair list is the
+    # oracle's, and the counts are those of the mode it took
+    off, tok = I.random_collection(4001, 3000, 1, 60, seed=500 + p, zipf_s=1.0, planted_frac=0.15)
+    a, bb, st = gpu_join(off, tok, p, q, b=64, candidates=_bmj.BMJ_CAND_AUTO)
+    ra, rb = O.self_join(off, tok, p, q)
+    assert np.array_equal(a, ra) and np.array_equal(bb, rb)
+    assert st["candidate_slots"] > 0
+    if st["candidates"] == -2:   # the window
+        assert (st["window_pairs"], st["survivors"], st["results"]) == \
+            O.filter_counts(off, tok, p, q, 64, O.XOR)
+    else:
+        assert (st["candidates"], st["survivors"], st["results"]) == \
+            O.prefix_counts(off, tok, p, q, 64, O.XOR)
+
+
+def test_automatic_candidates_on_the_million_set_workload(million):
+    # 1M sets: at 1/2 the 6e9 candidate slots cost more than the window (the automatic mode
+    # keeps the window), at 9/10 far less (it takes the prefix filter); same pairs either way
+    off, tok = million
+    off_d, tok_d = dev(off, tok)
+    for (p, q), mode in (((1, 2), "window"), ((9, 10), "prefix")):
+        w_pairs, _, st_w = _bmj.bmj_self_join(off_d, tok_d, p, q, b=64, output_on_device=True)
+        x_pairs, _, st_x = _bmj.bmj_self_join(off_d, tok_d, p, q, b=64, output_on_device=True,
+                                              candidates=_bmj.BMJ_CAND_AUTO)
+        assert torch.equal(w_pairs.a, x_pairs.a) and torch.equal(w_pairs.b, x_pairs.b)
+        assert (st_x["candidates"] == -2) == (mode == "window"), (p, q, st_x["candidates"])
+        w_pairs.release()
+        x_pairs.release()
+
+
 def test_prefix_filter_on_the_million_set_workload(million):
     # 1M sets at every threshold of the workload: the same pairs as the window-mode
     # join, fewer pairs through the Bitmap Filter (at 1/2 its billions of candidate
