@@ -503,7 +503,14 @@ def run_ours(args):
                                                   stream=stream.cuda_stream)
                     r.release()
                 wj = per_thr[(p, q)]["ms_total"] / args.steps
-                rows.append({"threshold": f"{p}/{q}", "candidates": st["candidates"],
+                r, _, sa = _bmj.bmj_self_join(d_off, d_tok, p, q, b=b, output_on_device=True,
+                                              candidates=_bmj.BMJ_CAND_AUTO,
+                                              stream=stream.cuda_stream)
+                r.release()
+                rows.append({"threshold": f"{p}/{q}",
+                             "automatic": {"took": "window" if sa["candidates"] == -2 else "prefix",
+                                           "join_ms": round(sa["ms_total"], 2)},
+                             "candidates": st["candidates"],
                              "candidate_slots": st["candidate_slots"],
                              "candidate_ranges": st["filter_passes"],
                              "survivors": st["survivors"], "results": st["results"],
@@ -657,8 +664,11 @@ def run_million(args, dev):
         for (p, q) in THRESHOLDS_1M:
             join(p, q, 64, candidates=_bmj.BMJ_CAND_PREFIX)
             st = join(p, q, 64, candidates=_bmj.BMJ_CAND_PREFIX)
+            sa = join(p, q, 64, candidates=_bmj.BMJ_CAND_AUTO)
             wj = step64[f"{p}/{q}"]["join_ms"]
             rows.append({"threshold": f"{p}/{q}", "window_pairs": st["window_pairs"],
+                         "automatic": {"took": "window" if sa["candidates"] == -2 else "prefix",
+                                       "join_ms": round(sa["ms_total"], 3)},
                          "candidates": st["candidates"],
                          "candidate_slots": st["candidate_slots"],
                          "candidate_ranges": st["filter_passes"],
