@@ -28,6 +28,7 @@
 // every result under its ticket until it is polled.  Latency of a query =
 // completion - submission.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
@@ -1037,6 +1038,8 @@ struct bmj_server {
     std::condition_variable cv_work;   // the loop waits here for submissions
     std::condition_variable cv_done;   // pollers wait here for results
     std::deque<int64_t> pending;       // submitted, not yet in a batch (ticket order)
+    std::atomic<int64_t> n_pending{0}; // its length, read by the loop without the lock
+    std::atomic<bool> closing_flag{false};
     std::unordered_map<int64_t, LiveQuery> queries;   // submitted, not yet completed
     std::unordered_map<int64_t, LiveResult> results;  // completed, not yet polled
     int64_t next_ticket = 0;
@@ -1130,6 +1133,7 @@ void live_loop(bmj_server *srv) {
             std::vector<int64_t> take;
             std::vector<const LiveQuery *> qs;
             int64_t w = 0, t = 0;
+            if (srv->n_pending.load(std::memory_order_acquire) == 0) break;
             {
                 std::lock_guard<std::mutex> g(srv->mu);
                 while (!srv->pending.empty() && (int64_t)take.size() < srv->max_q) {
@@ -1144,6 +1148,7 @@ void live_loop(bmj_server *srv) {
                     t += sx;
                     srv->pending.pop_front();
                 }
+                srv->n_pending.fetch_sub((int64_t)take.size(), std::memory_order_release);
                 if (!take.empty()) {
                     srv->batches++;
                     srv->window_pairs += w;
@@ -1168,11 +1173,8 @@ void live_loop(bmj_server *srv) {
             progressed = true;
         }
         if (rc) break;
-        {
-            std::lock_guard<std::mutex> g(srv->mu);
-            closing = srv->closing;
-            waiting = !srv->pending.empty();
-        }
+        closing = srv->closing_flag.load(std::memory_order_acquire);
+        waiting = srv->n_pending.load(std::memory_order_acquire) > 0;
         if (!in_flight && !waiting && closing) break;  // drained
         if (progressed) {
             last_activity = clk::now();
@@ -1204,6 +1206,7 @@ void live_loop(bmj_server *srv) {
         }
         srv->queries.clear();
         srv->pending.clear();
+        srv->n_pending.store(0);
         if (rc == BMJ_ERR_CUDA || rc == BMJ_ERR_TIMEOUT) idx->sticky = rc;
     }
     srv->cv_done.notify_all();
@@ -1295,6 +1298,7 @@ extern "C" int bmj_serve_submit(bmj_server *srv, const int32_t *tokens, int64_t 
         try {
             srv->queries.emplace(t, std::move(lq));
             srv->pending.push_back(t);
+            srv->n_pending.fetch_add(1, std::memory_order_release);
         } catch (...) {
             srv->queries.erase(t);
             return BMJ_ERR_OOM;
@@ -1346,6 +1350,7 @@ extern "C" int bmj_serve_close(bmj_server *srv, bmj_serve_stats *stats) {
     {
         std::lock_guard<std::mutex> g(srv->mu);
         srv->closing = true;
+        srv->closing_flag.store(true, std::memory_order_release);
     }
     srv->cv_work.notify_all();
     if (srv->loop.joinable()) srv->loop.join();
