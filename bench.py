@@ -413,7 +413,8 @@ def run_ours(args):
         pinned = (torch.from_numpy(off).pin_memory(), torch.from_numpy(tok).pin_memory())
         host_coll["off"], host_coll["tok"] = pinned[0].numpy(), pinned[1].numpy()
         e_steps = max(1, min(args.e2e_steps, args.steps))
-        join(9, 10, caps[(9, 10)], host=True)   # warms the host-side pools
+        for thr in THRESHOLDS:   # one untimed step warms the page-locked result pool
+            join(thr[0], thr[1], caps[thr], host=True)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
