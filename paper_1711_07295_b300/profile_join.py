@@ -67,9 +67,11 @@ def main():
             return _bmj.bmj_self_join(d_off, d_tok, args.p, args.q, **kw, **extra)
     res, _, st = join()
     res.release()
-    cap = max(1, st["survivors"])
+    # window mode: the survivor queue sized from the first call; prefix mode sizes
+    # its candidate ranges itself (a queue_cap there would cut them to that many slots)
+    extra = {"queue_cap": max(1, st["survivors"])} if cand == _bmj.BMJ_CAND_WINDOW else {}
     for _ in range(args.repeat):
-        res, _, st = join(queue_cap=cap)
+        res, _, st = join(**extra)
         res.release()
     torch.cuda.synchronize()
     print(json.dumps({"sets": args.sets, "rs_sets": args.rs_sets,
