@@ -162,3 +162,32 @@ def test_rs_join_arguments_rejected_on_host():
     assert _join_status(off, tok, 1, 2, cutoff=-2) == _bmj.BMJ_ERR_INVALID_ARG
     assert _join_status(off, tok, 1, 2, cutoff=3, candidates=_bmj.BMJ_CAND_PREFIX) == \
         _bmj.BMJ_ERR_INVALID_ARG
+
+
+STRUCTS = ("bmj_collection", "bmj_pairs", "bmj_options", "bmj_stats", "bmj_batch_stats",
+           "bmj_id_lists", "bmj_serve_options", "bmj_serve_stats")
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # Every struct the binding marshals has the size and field offsets that a C compiler
+    # gives the header's declaration (gcc, the host ABI the library is built for).
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bmj.h"', 'int main(void) {']
+    for name in STRUCTS:
+        cls = getattr(_bmj, name)
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                   check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for name in STRUCTS:
+        cls = getattr(_bmj, name)
+        assert int(got[name]) == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
