@@ -586,6 +586,7 @@ int enqueue_execute(const Plan &P, int sms, cudaStream_t s) {
 }
 
 int run_execute(const Plan &P, int sms, cudaStream_t s, bool use_graph, int *graphed) {
+    NvtxRange nv("bmj.batch_execute");
     *graphed = 0;
     if (!use_graph) return enqueue_execute(P, sms, s);
     cudaStream_t cs = nullptr;
@@ -617,6 +618,7 @@ int run_execute(const Plan &P, int sms, cudaStream_t s, bool use_graph, int *gra
 int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_sets, int sim,
                const uint32_t *hp, const uint32_t *hq, const bmj_options &o, bmj_pairs *outs,
                bmj_stats *job_stats, bmj_batch_stats *bst) {
+    NvtxRange nv_call("bmj_self_join_batch");
     cudaStream_t s = (cudaStream_t)o.stream;
     const int64_t launches0 = launches();
     int dev = 0;

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 
 namespace bmj {
@@ -96,6 +98,16 @@ inline int flags_to_status(int flags) {
 }
 
 inline bool valid_b(int b) { return b >= 64 && b <= 4096 && (b % 64) == 0; }
+
+// A named NVTX range over a host scope (a call or a stage): profilers (ncu
+// --nvtx, nsys) see the library's stages; without a tool attached a range
+// costs a few nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Device-resident view of a collection (copied in when it is host memory).
 struct DevColl {

@@ -89,6 +89,7 @@ static int64_t auto_queue_cap(int64_t window) {
 static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll_s, int sim,
                           uint32_t p, uint32_t q, const bmj_options &o, bmj_pairs *out,
                           bmj_stats *stats) {
+    NvtxRange nv_call(coll_s ? "bmj_rs_join" : "bmj_self_join");
     cudaStream_t s = (cudaStream_t)o.stream;
     const int64_t launches0 = launches();
     const FaultPlan fault = read_fault_plan();
@@ -265,7 +266,9 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
             Arena PA(s);  // its buffers go once the candidates are verified
             BMJ_CHECK(cudaEventRecord(ev.e[3], s));
             PrefixIndex px;
+            nvtxRangePushA("bmj.prefix_index");
             int pst = prefix_index(ssz, soff, stok, n, d.ntok, rs ? n_sc : 0, win, PA, s, &px);
+            nvtxRangePop();
             if (pst == BMJ_ERR_OOM) {  // the index itself does not fit: the window instead
                 cudaGetLastError();
                 PA.release();
@@ -319,6 +322,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                     BMJ_CHECK(cudaMemsetAsync(ccnt, 0, 2 * sizeof(unsigned long long), s));
                     BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
                     BMJ_CHECK(cudaEventRecord(ev.e[3], s));
+                    NvtxRange nv_range("bmj.prefix_range");
                     st = prefix_expand(px, o0, o1, test, cq, &ccnt[0], &ccnt[1], s);
                     if (st) return st;
                     BMJ_CHECK(cudaEventRecord(ev.e[4], s));
@@ -404,6 +408,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
             }
             // Filters work items [lo, hi) into the queue; *count = their survivors.
             auto run_filter = [&](int64_t lo, int64_t hi, int64_t *count) -> int {
+                NvtxRange nv("bmj.filter");
                 const unsigned long long init[2] = {0ull, (unsigned long long)lo};
                 BMJ_CHECK(cudaMemcpyAsync(&ctr[1], init, sizeof(init), cudaMemcpyHostToDevice, s));
                 fa.n_items = hi;
@@ -423,6 +428,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
             // Verifies the m survivors at qptr into out_keys (*n_out results).
             auto run_verify = [&](const uint2 *qptr, int64_t m, uint64_t *out_keys,
                                   int64_t *n_out) -> int {
+                NvtxRange nv("bmj.verify");
                 BMJ_CHECK(cudaMemsetAsync(&ctr[3], 0, 2 * sizeof(unsigned long long), s));
                 BMJ_CHECK(cudaEventRecord(ev.e[5], s));
                 int rc = launch_verify(qptr, m, soff, stok, ssz, perm, need, lim, bm2, W2, out_keys,
@@ -522,6 +528,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
 
         // ---- canonical order ----
         if (n_res > 0) {
+            NvtxRange nv("bmj.result_sort");
             st = A.alloc(&keys_sorted, (size_t)n_res);
             if (!st) st = radix_sort_u64(keys, keys_sorted, n_res, 2 * nbits, A, s);
             if (st) return st;
@@ -534,6 +541,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
     stl.results = n_res;
 
     // ---- output ----
+    NvtxRange nv_out("bmj.output");
     bmj_pairs res;
     memset(&res, 0, sizeof(res));
     res.on_device = o.output_on_device ? 1 : 0;

@@ -470,6 +470,7 @@ int64_t window_of(const bmj_index *idx, int64_t sx, uint32_t p, uint32_t q) {
 // Phase 1 of a staged batch: copy in, bitmaps, windows, filter, verification,
 // result count back to pinned memory.
 int launch_phase1(const bmj_index *idx, Slot &s, int sms) {
+    NvtxRange nv("bmj.serve_batch");
     cudaStream_t st = s.stream;
     const int64_t nq = s.nq;
     BMJ_CHECK(cudaMemcpyAsync(s.d_in, s.h_in, s.in_bytes, cudaMemcpyHostToDevice, st));
