@@ -61,8 +61,8 @@ LOP_PER_CLK_PER_SM = 64       # 32-bit logic operations (ALU pipe) per SM per cl
 # compression of those words allows (2 words: 2 POPC; 4 words: one carry-save
 # adder, 2 LOP3, 3 POPC; 8 words: four carry-save adders, 8 LOP3, 4 POPC).
 FILTER_MIX = {64: (2, 2), 128: (3, 6), 256: (4, 16)}   # b -> (POPC, LOP3) per pair
-FILTER_KERNEL = {64: "k_filter_tma<1,8,256>", 128: "k_filter_tma<2,4,256>",
-                 256: "k_filter_tma<4,4,128>"}
+FILTER_KERNEL = {64: "k_filter_tma<1,8,256>", 128: "k_filter_tma<2,4,128>",
+                 256: "k_filter_tma<4,4,64>"}
 FLUSH_BYTES = 256 << 20       # > 126 MB L2
 
 
