@@ -312,6 +312,8 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                     test.lim = lim;
                     test.W = W;
                 }
+                st = prefix_records(px, test, PA, s);
+                if (st) return st;
                 stl.candidates = 0;
                 stl.survivors = 0;
                 stl.verified = 0;

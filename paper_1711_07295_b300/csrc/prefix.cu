@@ -356,6 +356,23 @@ __device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ cand_off
 // partner data (load: sizes, prefix offsets and, with W > 0, bitmaps), the
 // prefix test (lowest_shared: no rank below the entry's in both prefixes) and
 // Eq. 2 (passes).
+// 64-bit words of a set's record for the expansion: its size, its prefix
+// offset and its W bitmap words, padded to 16, 32 or 64 bytes.
+__host__ __device__ constexpr int rec_words(int W) { return W == 0 ? 2 : W <= 2 ? 4 : 8; }
+
+__global__ void k_pack_records(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ pofs,
+                               const uint64_t *__restrict__ bm, int W, int K, int64_t n,
+                               uint64_t *__restrict__ rec) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        uint64_t *r = rec + (size_t)x * K;
+        r[0] = ssz[x];
+        r[1] = (uint64_t)pofs[x];
+        for (int w = 0; w < W; w++) r[2 + w] = bm[(size_t)x * W + w];
+        for (int w = 2 + W; w < K; w++) r[w] = 0;
+    }
+}
+
 template <int W>
 struct SlotLoad {
     bool valid = false;
@@ -376,18 +393,30 @@ struct SlotLoad {
         i = (uint32_t)(key >> rshift);
         j = (uint32_t)(idx[lo[k] + (o - cand_off[k])] >> rshift);
     }
-    __device__ __forceinline__ void load(const uint32_t *__restrict__ ssz,
-                                         const int64_t *__restrict__ pofs,
-                                         const uint64_t *__restrict__ bm) {
+    // the two sets' records (size, prefix offset, bitmap): one or two aligned
+    // 16-byte loads per record, so a partner costs one random sector or two
+    __device__ __forceinline__ void load(const uint64_t *__restrict__ rec) {
         if (!valid) return;
-        si = ssz[i];
-        sj = ssz[j];
-        poi = pofs[i];
-        poj = pofs[j];
+        constexpr int K = rec_words(W);
+        uint64_t a[K], b[K];
+        const ulonglong2 *ra = reinterpret_cast<const ulonglong2 *>(rec + (size_t)i * K);
+        const ulonglong2 *rb = reinterpret_cast<const ulonglong2 *>(rec + (size_t)j * K);
+#pragma unroll
+        for (int v = 0; v < K / 2; v++) {
+            const ulonglong2 x = ra[v], y = rb[v];
+            a[2 * v] = x.x;
+            a[2 * v + 1] = x.y;
+            b[2 * v] = y.x;
+            b[2 * v + 1] = y.y;
+        }
+        si = (uint32_t)a[0];
+        sj = (uint32_t)b[0];
+        poi = (int64_t)a[1];
+        poj = (int64_t)b[1];
 #pragma unroll
         for (int w = 0; w < W; w++) {
-            bwi[w] = bm[(size_t)i * W + w];
-            bwj[w] = bm[(size_t)j * W + w];
+            bwi[w] = a[2 + w];
+            bwj[w] = b[2 + w];
         }
     }
     __device__ __forceinline__ bool lowest_shared(const uint32_t *__restrict__ pref,
@@ -417,9 +446,8 @@ struct SlotLoad {
 template <int W>
 __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
                               const int64_t *__restrict__ cand_off, const int64_t *__restrict__ lo,
-                              int64_t o0, int64_t o1, const uint32_t *__restrict__ ssz,
-                              const int64_t *__restrict__ pofs, const uint32_t *__restrict__ pref,
-                              SimWindow win, int rshift, const uint64_t *__restrict__ bm,
+                              int64_t o0, int64_t o1, const uint64_t *__restrict__ rec,
+                              const uint32_t *__restrict__ pref, SimWindow win, int rshift,
                               const int32_t *__restrict__ lim, uint2 *__restrict__ out,
                               unsigned long long *__restrict__ count,
                               unsigned long long *__restrict__ n_cand) {
@@ -448,8 +476,8 @@ __global__ void k_cand_expand(const uint64_t *__restrict__ idx, int64_t P,
             SlotLoad<W> a, b;
             a.fetch(t0 + m * 32 + lane, t1, ka, kz, idx, cand_off, lo, umask, rshift);
             b.fetch(t0 + (m + 1) * 32 + lane, t1, ka, kz, idx, cand_off, lo, umask, rshift);
-            a.load(ssz, pofs, bm);
-            b.load(ssz, pofs, bm);
+            a.load(rec);
+            b.load(rec);
             const bool ka_ = a.valid && a.lowest_shared(pref, win);
             const bool kb_ = b.valid && b.lowest_shared(pref, win);
             // the Bitmap Filter (Eq. 2) on the candidate, inside the window by construction
@@ -636,6 +664,7 @@ int prefix_index(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, 
     int64_t C = 0;
     BMJ_CHECK(cudaMemcpyAsync(&C, coff + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BMJ_CHECK(cudaStreamSynchronize(s));
+    out->n = n;
     out->idx = idx;
     out->lo = lo;
     out->cand_off = coff;
@@ -647,15 +676,30 @@ int prefix_index(const uint32_t *ssz, const int64_t *soff, const int32_t *stok, 
     return BMJ_OK;
 }
 
+int prefix_records(const PrefixIndex &ix, PrefixTest &test, Arena &A, cudaStream_t s) {
+    test.rec = nullptr;
+    if (ix.P == 0) return BMJ_OK;
+    const int W = test.bm ? test.W : 0;
+    const int K = rec_words(W);
+    const int64_t n = ix.n;
+    uint64_t *rec = nullptr;
+    int rc = A.alloc(&rec, (size_t)std::max<int64_t>(n, 1) * K);
+    if (rc) return rc;
+    BMJ_LAUNCH(k_pack_records, grid_p(n, 256), 256, 0, s, ix.ssz, ix.pofs, test.bm, W, K, n, rec);
+    test.rec = rec;
+    return BMJ_OK;
+}
+
 int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, const PrefixTest &test,
                   uint2 *out, unsigned long long *count, unsigned long long *n_cand,
                   cudaStream_t s) {
     if (o1 <= o0 || ix.P == 0) return BMJ_OK;
+    if (!test.rec) return BMJ_ERR_INVALID_ARG;  // prefix_records first
     constexpr int64_t kTile = 32 * kExpandPerLane;
     const unsigned grid = grid_p((o1 - o0 + kTile - 1) / kTile, 8, 148 * 64);
 #define BMJ_EXPAND(KW)                                                                            \
     BMJ_LAUNCH(k_cand_expand<KW>, grid, 256, 0, s, ix.idx, ix.P, ix.cand_off, ix.lo, o0, o1,       \
-               ix.ssz, ix.pofs, ix.pref, ix.win, ix.rshift, test.bm, test.lim, out, count, n_cand)
+               test.rec, ix.pref, ix.win, ix.rshift, test.lim, out, count, n_cand)
     switch (test.bm ? test.W : 0) {
         case 1: BMJ_EXPAND(1); break;
         case 2: BMJ_EXPAND(2); break;

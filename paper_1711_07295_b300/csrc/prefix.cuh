@@ -20,6 +20,7 @@ struct PrefixIndex {
     const int64_t *pofs = nullptr;      // per set: offset of its prefix in pref
     const uint32_t *pref = nullptr;     // every prefix, ranks ascending
     const uint32_t *ssz = nullptr;      // set sizes in size order
+    int64_t n = 0;                      // sets
     int64_t P = 0;                      // index entries
     int64_t slots = 0;                  // candidate slots, = cand_off[P]
     int rshift = 0;
@@ -42,14 +43,20 @@ struct PrefixTest {
     const uint64_t *bm = nullptr;
     const int32_t *lim = nullptr;
     int W = 0;
+    const uint64_t *rec = nullptr;  // per set: size, prefix offset, bitmap (prefix_records)
 };
+
+// Packs every set's size, prefix offset and (with a test) bitmap into one
+// aligned record, so that the expansion reads a random partner in one or two
+// sectors instead of three separate arrays; sets test.rec (memory from A).
+int prefix_records(const PrefixIndex &ix, PrefixTest &test, Arena &A, cudaStream_t s);
 
 // Candidates of the slots [o0, o1): the pairs (i, j), j < i in size order
 // (RS: i in R, j in S) inside the window whose prefixes share a token, kept
 // at the slot of their lowest shared rank so that every pair appears once over
 // all slots.  Adds their number to *n_cand (device); appends to out (room for
 // o1 - o0 pairs) those that pass the test (all of them when test.W = 0) and
-// adds their number to *count (device).
+// adds their number to *count (device).  test.rec must come from prefix_records.
 int prefix_expand(const PrefixIndex &ix, int64_t o0, int64_t o1, const PrefixTest &test,
                   uint2 *out, unsigned long long *count, unsigned long long *n_cand,
                   cudaStream_t s);
