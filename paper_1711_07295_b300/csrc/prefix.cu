@@ -356,44 +356,29 @@ __device__ __forceinline__ int64_t owner_of(const int64_t *__restrict__ cand_off
 // partner data (load: sizes, prefix offsets and, with W > 0, bitmaps), the
 // prefix test (lowest_shared: no rank below the entry's in both prefixes) and
 // Eq. 2 (passes).
-// A set's record for the expansion, in 64-bit words: word 0 = its size
-// (low half) and prefix offset (high half; prefixes hold fewer than 2^32 tokens),
-// words 2 .. 1+W = its bitmap, and every other word two of the first ranks of
-// its prefix (in order; 0xffffffff past its end).  16, 32 or 64 bytes: a
-// partner's size, bitmap and first 2 (W = 2), 4 (W = 0, 1) or 6 (W = 4) prefix
-// ranks come in one or two sectors, and most prefix merges end within them.
+// 64-bit words of a set's record for the expansion: its size, its prefix
+// offset and its W bitmap words, padded to 16, 32 or 64 bytes.
 __host__ __device__ constexpr int rec_words(int W) { return W == 0 ? 2 : W <= 2 ? 4 : 8; }
-__host__ __device__ constexpr int rec_ranks(int W) { return 2 * (rec_words(W) - 1 - W); }
-// word of inline rank pair k (ranks 2k, 2k+1)
-__host__ __device__ constexpr int rec_rank_word(int W, int k) { return k == 0 ? 1 : 1 + W + k; }
 
 __global__ void k_pack_records(const uint32_t *__restrict__ ssz, const int64_t *__restrict__ pofs,
-                               const uint32_t *__restrict__ pref, SimWindow win,
-                               const uint64_t *__restrict__ bm, int W, int64_t n,
+                               const uint64_t *__restrict__ bm, int W, int K, int64_t n,
                                uint64_t *__restrict__ rec) {
-    const int K = rec_words(W), NR = rec_ranks(W);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
         uint64_t *r = rec + (size_t)x * K;
-        const int64_t po = pofs[x], len = prefix_len(ssz[x], win);
-        r[0] = (uint64_t)ssz[x] | ((uint64_t)po << 32);
+        r[0] = ssz[x];
+        r[1] = (uint64_t)pofs[x];
         for (int w = 0; w < W; w++) r[2 + w] = bm[(size_t)x * W + w];
-        for (int k = 0; 2 * k < NR; k++) {
-            const uint32_t lo = 2 * k < len ? pref[po + 2 * k] : 0xffffffffu;
-            const uint32_t hi = 2 * k + 1 < len ? pref[po + 2 * k + 1] : 0xffffffffu;
-            r[rec_rank_word(W, k)] = (uint64_t)lo | ((uint64_t)hi << 32);
-        }
+        for (int w = 2 + W; w < K; w++) r[w] = 0;
     }
 }
 
 template <int W>
 struct SlotLoad {
-    static constexpr int NR = rec_ranks(W);
     bool valid = false;
     uint32_t i = 0, j = 0, r = 0, si = 0, sj = 0;
     int64_t poi = 0, poj = 0;
     uint64_t bwi[W > 0 ? W : 1], bwj[W > 0 ? W : 1];
-    uint32_t fi[NR], fj[NR];  // the first prefix ranks of the two sets
 
     __device__ __forceinline__ void fetch(int64_t o, int64_t t1, int64_t ka, int64_t kz,
                                           const uint64_t *__restrict__ idx,
@@ -426,20 +411,12 @@ struct SlotLoad {
         }
         si = (uint32_t)a[0];
         sj = (uint32_t)b[0];
-        poi = (int64_t)(a[0] >> 32);
-        poj = (int64_t)(b[0] >> 32);
+        poi = (int64_t)a[1];
+        poj = (int64_t)b[1];
 #pragma unroll
         for (int w = 0; w < W; w++) {
             bwi[w] = a[2 + w];
             bwj[w] = b[2 + w];
-        }
-#pragma unroll
-        for (int k = 0; 2 * k < NR; k++) {
-            const uint64_t u = a[rec_rank_word(W, k)], v = b[rec_rank_word(W, k)];
-            fi[2 * k] = (uint32_t)u;
-            fi[2 * k + 1] = (uint32_t)(u >> 32);
-            fj[2 * k] = (uint32_t)v;
-            fj[2 * k + 1] = (uint32_t)(v >> 32);
         }
     }
     __device__ __forceinline__ bool lowest_shared(const uint32_t *__restrict__ pref,
@@ -449,22 +426,13 @@ struct SlotLoad {
         const int64_t ni = prefix_len(si, win), nj = prefix_len(sj, win);
         int64_t x = 0, y = 0;
         while (x < ni && y < nj) {
-            // the first NR ranks from the records, the rest from the prefixes
-            const uint32_t rx = x < NR ? pick(fi, (int)x) : pi[x];
-            const uint32_t ry = y < NR ? pick(fj, (int)y) : pj[y];
+            const uint32_t rx = pi[x], ry = pj[y];
             if (rx >= r || ry >= r) break;
             if (rx == ry) return false;
             if (rx < ry) x++;
             else y++;
         }
         return true;
-    }
-    // f[k] with a register-resident array and a run-time k (a select chain)
-    __device__ __forceinline__ static uint32_t pick(const uint32_t (&f)[NR], int k) {
-        uint32_t v = f[0];
-#pragma unroll
-        for (int t = 1; t < NR; t++) v = k == t ? f[t] : v;
-        return v;
     }
     __device__ __forceinline__ bool passes(const int32_t *__restrict__ lim) const {
         if (W == 0) return true;
@@ -717,8 +685,7 @@ int prefix_records(const PrefixIndex &ix, PrefixTest &test, Arena &A, cudaStream
     uint64_t *rec = nullptr;
     int rc = A.alloc(&rec, (size_t)std::max<int64_t>(n, 1) * K);
     if (rc) return rc;
-    BMJ_LAUNCH(k_pack_records, grid_p(n, 256), 256, 0, s, ix.ssz, ix.pofs, ix.pref, ix.win, test.bm,
-               W, n, rec);
+    BMJ_LAUNCH(k_pack_records, grid_p(n, 256), 256, 0, s, ix.ssz, ix.pofs, test.bm, W, K, n, rec);
     test.rec = rec;
     return BMJ_OK;
 }
