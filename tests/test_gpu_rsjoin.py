@@ -191,8 +191,14 @@ def test_rs_join_of_two_million_set_collections_row_sampled():
         key = a.astype(np.uint64) << np.uint64(32) | bb.astype(np.uint64)
         assert np.all(np.diff(key.astype(np.int64)) > 0)
         assert st["results"] == len(a) <= st["survivors"] <= st["window_pairs"]
+        # the window pairs of R x S at full size, from the oracle's two size histograms
+        assert st["window_pairs"] == O.rs_window_pairs(sizes, np.diff(so), p, q)
         x, y = sizes[a], np.diff(so)[bb]
         assert np.all(q * np.minimum(x, y) >= p * np.maximum(x, y))
+        # the automatic candidate mode gives the same pairs
+        xa, xb, sx = _bmj.bmj_rs_join(*dev(ro, rt), *dev(so, st_), p, q, b=b,
+                                      candidates=_bmj.BMJ_CAND_AUTO)
+        assert np.array_equal(xa, a) and np.array_equal(xb, bb) and sx["candidate_slots"] > 0
 
 
 @pytest.mark.parametrize("b", [64, 128, 256])
