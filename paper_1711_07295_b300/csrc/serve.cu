@@ -1060,17 +1060,14 @@ namespace {
 void live_loop(bmj_server *srv) {
     using clk = std::chrono::steady_clock;
     bmj_index *idx = srv->idx;
-    if (cudaSetDevice(idx->device) != cudaSuccess) {
-        std::lock_guard<std::mutex> g(srv->mu);
-        srv->error = BMJ_ERR_CUDA;
-    }
+    // a device that cannot be made current fails every query (below)
+    int rc = cudaSetDevice(idx->device) == cudaSuccess ? BMJ_OK : BMJ_ERR_CUDA;
     const int sms = bmj::num_sms(idx->device);
     // per slot: the queries of its batch (pointers stay valid: node-based map,
     // entries erased by this thread only)
     std::vector<std::vector<const LiveQuery *>> batch_q(srv->slots.size());
     auto last_activity = clk::now();
-    int rc = BMJ_OK;
-    for (;;) {
+    while (!rc) {
         bool progressed = false;
         bool in_flight = false;
         // 1. finished phases
