@@ -1045,6 +1045,7 @@ struct bmj_server {
     std::unordered_map<int64_t, LiveResult> results;  // completed, not yet polled
     int64_t next_ticket = 0;
     bool closing = false;
+    bool fault_serve = false;  // host fault injection: the first batch fails as a CUDA error would
     int error = BMJ_OK;
     // totals (written by the loop under mu)
     std::vector<double> latencies;
@@ -1164,6 +1165,10 @@ void live_loop(bmj_server *srv) {
                             });
             s.win = w;
             batch_q[si] = std::move(qs);
+            if (srv->fault_serve) {  // (BMJ_FAULT=serve at open: nothing is launched)
+                rc = BMJ_ERR_CUDA;
+                break;
+            }
             rc = bmj::launch_phase1(idx, s, sms);
             if (rc) break;
             s.phase = 1;
@@ -1231,6 +1236,7 @@ extern "C" int bmj_serve_open(bmj_index *idx, const bmj_serve_options *opt, bmj_
     bmj_server *srv = new (std::nothrow) bmj_server();
     if (!srv) return BMJ_ERR_OOM;
     srv->idx = idx;
+    srv->fault_serve = bmj::read_fault_plan().serve;
     srv->max_q = so.max_batch_queries > 0 ? so.max_batch_queries : 4096;
     srv->max_probe = so.max_probe_tokens > 0 ? so.max_probe_tokens : 4096;
     srv->tok_cap = std::max<int64_t>(srv->max_probe,

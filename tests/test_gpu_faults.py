@@ -81,3 +81,34 @@ def test_device_failures_stick_to_an_index(monkeypatch):
     assert fresh.status() == _bmj.BMJ_OK
     assert len(got) == len(want) and all(np.array_equal(x, y) for x, y in zip(got, want))
     fresh.close()
+
+
+def test_live_server_device_failure_fails_its_queries(monkeypatch):
+    # A live server whose first batch fails as a CUDA runtime error would (injected on
+    # the host at open: nothing is launched): every submitted query comes back with that
+    # status, later submissions are refused with it, close reports it, and it sticks to
+    # the index; a fresh index serves the same queries correctly.
+    off, tok = I.random_collection(5000, 1000, 1, 30, seed=79, planted_frac=0.1)
+    idx = _bmj.Index(off, tok, b=64)
+    monkeypatch.setenv("BMJ_FAULT", "serve")
+    srv = _bmj.Server(idx, n_slots=2)
+    monkeypatch.delenv("BMJ_FAULT")
+    tickets = [srv.submit(tok[off[x]:off[x + 1]], 1, 2) for x in range(5)]
+    for t in tickets:
+        with pytest.raises(_bmj.BmjError) as e:
+            srv.poll(t, wait_ms=20_000)
+        assert e.value.status == _bmj.BMJ_ERR_CUDA
+    with pytest.raises(_bmj.BmjError) as e:
+        srv.submit(tok[off[0]:off[1]], 1, 2)
+    assert e.value.status == _bmj.BMJ_ERR_CUDA
+    with pytest.raises(_bmj.BmjError) as e:
+        srv.close()
+    assert e.value.status == _bmj.BMJ_ERR_CUDA
+    assert idx.status() == _bmj.BMJ_ERR_CUDA
+    idx.close()
+    fresh = _bmj.Index(off, tok, b=64)
+    srv = _bmj.Server(fresh, n_slots=2)
+    ids, _ = srv.poll(srv.submit(tok[off[3]:off[4]], 1, 2), wait_ms=20_000)
+    assert np.array_equal(ids, O.search(tok[off[3]:off[4]], off, tok, 1, 2))
+    srv.close()
+    fresh.close()
