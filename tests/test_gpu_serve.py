@@ -261,3 +261,45 @@ def test_live_server_errors():
     st = srv.close()
     assert st["n_queries"] == 6 and len(last) == 5
     idx.close()
+
+
+def test_live_server_many_submitters_and_pollers():
+    # Four host threads submit concurrently and four others poll their tickets with
+    # waits: every ticket is unique, every result equals the oracle's search.
+    import threading
+    off, tok, arr, qoff, qtok, p, q = small_setup(seed=47, nq=240)
+    idx = _bmj.Index(torch.from_numpy(off).cuda(), torch.from_numpy(tok).cuda(), b=128)
+    srv = _bmj.Server(idx, n_slots=4, max_batch_queries=8, max_probe_tokens=64)
+    tickets = {}
+    lock = threading.Lock()
+    got = {}
+
+    def submitter(part):
+        for x in range(part, len(p), 4):
+            t = srv.submit(qtok[qoff[x]:qoff[x + 1]], int(p[x]), int(q[x]))
+            with lock:
+                tickets[x] = t
+
+    def poller(part):
+        for x in range(part, len(p), 4):
+            while True:
+                with lock:
+                    t = tickets.get(x)
+                if t is not None:
+                    break
+            r = srv.poll(t, wait_ms=20_000)
+            assert r is not None
+            got[x] = r[0]
+
+    threads = [threading.Thread(target=f, args=(k,)) for f in (submitter, poller) for k in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    st = srv.close()
+    assert st["n_queries"] == len(p)
+    assert sorted(tickets.values()) == list(range(len(p)))
+    for x in range(len(p)):
+        want = O.search(qtok[qoff[x]:qoff[x + 1]], off, tok, int(p[x]), int(q[x]))
+        assert np.array_equal(got[x], want), x
+    idx.close()
