@@ -839,7 +839,10 @@ def run_live(idx, arr, qoff, qtok, p, q):
     submits every query at its arrival time (bmj_serve_submit) and, between
     arrivals, polls the oldest tickets (bmj_serve_poll, no wait) while the
     server's own loop thread batches and runs them; latency = completion -
-    submission, measured by the library."""
+    submission, measured by the library.  Python's cyclic garbage collector is
+    paused over the stream: a full collection of the interpreter's objects
+    stalls the submitting thread for tens of milliseconds."""
+    import gc
     import numpy as np
     from paper_1711_07295_b300 import _bmj
     warm = _bmj.Server(idx, n_slots=4, max_batch_queries=4096, max_probe_tokens=512)
@@ -863,14 +866,19 @@ def run_live(idx, arr, qoff, qtok, p, q):
             n_res[head] = len(r[0])
             lat[head] = r[1]
             head += 1
-    t0 = time.perf_counter()
-    for x in range(n):
-        while time.perf_counter() - t0 < arr[x]:
-            poll_some(0)
-        late[x] = time.perf_counter() - t0 - arr[x]
-        tickets[x] = srv.submit(qtok[qoff[x]:qoff[x + 1]], int(p[x]), int(q[x]))
-    while head < n:
-        poll_some(100)
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for x in range(n):
+            while time.perf_counter() - t0 < arr[x]:
+                poll_some(0)
+            late[x] = time.perf_counter() - t0 - arr[x]
+            tickets[x] = srv.submit(qtok[qoff[x]:qoff[x + 1]], int(p[x]), int(q[x]))
+        while head < n:
+            poll_some(100)
+    finally:
+        gc.enable()
     st = srv.close()
     return {"p50_ms": round(float(np.percentile(lat, 50)), 4),
             "p99_ms": round(float(np.percentile(lat, 99)), 4),

@@ -233,14 +233,13 @@ struct BatchFilterArgs {
 // The Bitmap Filter over the work items of every job of one bitmap width:
 // tiles [t0, t1) (the jobs of that width are contiguous in the tile list),
 // items pulled from a per-class counter.  Columns are staged by TMA.
-// Rows per lane counted on the ALU in the batched filter: as in the single join,
-// one row in eight at b = 64 (249.7 against 251.6 ms for the 512-job batch).
-template <int W>
-constexpr int kBatchAlu = W == 1 ? kAluRowsW1 : 0;
-// ... in tiles of the default height only (one row in eight): a small tile keeps
-// every row on POPC
+// Rows per lane that take the width's second popcount form in the batched
+// filter, as in the single join: one row in eight counted on the ALU at b = 64
+// (249.7 against 251.6 ms for the 512-job batch), two rows in four reduced to
+// 5 POPC at b = 256; in tiles of the default height only (a small tile keeps
+// every row on the first form).
 template <int W, int R>
-constexpr int kBatchAluR = R >= 8 ? kBatchAlu<W> : 0;
+constexpr int kBatchAltR = (W == 1 && R >= 8) || (W == 4 && R >= 4) ? kAltRows<W> : 0;
 
 // Resident 4-warp blocks per SM of the batched filter at b = 64: eight (64
 // registers, 8 bytes spilled) ran the 512-job execute stage in 248.2 ms against
@@ -274,7 +273,7 @@ __global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS 
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
         const SimArgs sa{jd.win, jd.p, jd.q};
-        filter_item_tma<W, R, CS, kBatchAluR<W, R>, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0,
+        filter_item_tma<W, R, CS, kBatchAltR<W, R>, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0,
                                                       c0, c1, sa, sink, stg);
         if (!stg.ok) {
             drain_stage(stg);

@@ -341,6 +341,21 @@ struct PopcHS<4> {
     }
 };
 
+// The second form at b = 256, used for some rows so that part of the work
+// moves from the ALU to POPC: three carry-save adders and 5 POPC (one POPC
+// more and two LOP3 fewer than PopcHS<4>).
+struct PopcAlt4 {
+    __device__ __forceinline__ static int h(const uint32_t *x) {
+        const uint32_t s1 = x[0] ^ x[1] ^ x[2];
+        const uint32_t c1 = (x[0] & x[1]) | (x[2] & (x[0] ^ x[1]));
+        const uint32_t s2 = x[3] ^ x[4] ^ x[5];
+        const uint32_t c2 = (x[3] & x[4]) | (x[5] & (x[3] ^ x[4]));
+        const uint32_t s3 = s1 ^ s2 ^ x[6];
+        const uint32_t c3 = (s1 & s2) | (x[6] & (s1 ^ s2));
+        return __popc(s3) + __popc(x[7]) + 2 * (__popc(c1) + __popc(c2) + __popc(c3));
+    }
+};
+
 // Shared-memory layout of one warp's column buffers.
 template <int W, int CS>
 struct ColStage {
@@ -476,7 +491,7 @@ __device__ __forceinline__ void flush_masks(const uint32_t (&mask)[R], const int
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
 // arrays must be readable up to 3 entries past the last column (padded).
-template <int W, int R, int CS, int kAluRows = 0, bool kCos = false, bool kCut = false>
+template <int W, int R, int CS, int kAltRows = 0, bool kCos = false, bool kCut = false>
 __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                                                 const uint32_t *__restrict__ ssz,
                                                 const int32_t *__restrict__ lim_tab,
@@ -568,8 +583,11 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                     uint32_t x[2 * W];
 #pragma unroll
                     for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
+                    // rows R - kAltRows .. R - 1 take the width's second form
+                    const bool alt = kAltRows > 0 && k >= R - kAltRows;
                     int h;
-                    if (W == 1 && kAluRows > 0 && k >= R - kAluRows) h = popc64_alu(x[0], x[1]);
+                    if constexpr (W == 1) h = alt ? popc64_alu(x[0], x[1]) : PopcHS<1>::h(x);
+                    else if constexpr (W == 4) h = alt ? PopcAlt4::h(x) : PopcHS<4>::h(x);
                     else h = PopcHS<W>::h(x);
                     const int t = h + nlim[k];
                     mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);

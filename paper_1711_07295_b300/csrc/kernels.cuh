@@ -134,6 +134,16 @@ constexpr int kTmaCS1 = BMJ_TMA_CS1, kTmaCS2 = BMJ_TMA_CS2, kTmaCS4 = BMJ_TMA_CS
 #define BMJ_ALU_ROWS_W1 1
 #endif
 constexpr int kAluRowsW1 = BMJ_ALU_ROWS_W1;
+// At b = 256, rows per lane (of four) reduced by three carry-save adders and
+// 5 POPC (PopcAlt4) instead of four and 4 POPC: two rows took the 1M-set
+// filter from 0.840 to 0.871e12 pairs/s (one row 0.870, three 0.870).
+#ifndef BMJ_ALT_ROWS_W4
+#define BMJ_ALT_ROWS_W4 2
+#endif
+// Rows per lane that take the second popcount form of width W (popc64_alu at
+// b = 64, PopcAlt4 at b = 256).
+template <int W>
+constexpr int kAltRows = W == 1 ? kAluRowsW1 : W == 4 ? BMJ_ALT_ROWS_W4 : 0;
 
 // The Bitmap Filter with column chunks staged in shared memory by TMA bulk
 // copies (b in {64, 128, 256}; other widths fall back to launch_filter).  The
