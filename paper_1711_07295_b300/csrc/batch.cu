@@ -236,20 +236,24 @@ struct BatchFilterArgs {
 // Rows per lane that take the width's second popcount form in the batched
 // filter, as in the single join: one row in eight counted on the ALU at b = 64
 // (249.7 against 251.6 ms for the 512-job batch), two rows in four reduced to
-// 5 POPC at b = 256; in tiles of the default height only (a small tile keeps
-// every row on the first form).
+// 5 POPC at b = 256 (242.8 against 243.3 ms); in tiles of the default height
+// only (a small tile keeps every row on the first form).
 template <int W, int R>
 constexpr int kBatchAltR = (W == 1 && R >= 8) || (W == 4 && R >= 4) ? kAltRows<W> : 0;
 
 // Resident 4-warp blocks per SM of the batched filter at b = 64: eight (64
 // registers, 8 bytes spilled) ran the 512-job execute stage in 248.2 ms against
-// 249.6 ms with seven.
+// 249.6 ms with seven.  At b = 256 seven (72 registers): eight, within 64
+// registers, took it from 242.8 to 250.1 ms.
 #ifndef BMJ_BATCH_W1_BLOCKS
 #define BMJ_BATCH_W1_BLOCKS 8
 #endif
+#ifndef BMJ_BATCH_W4_BLOCKS
+#define BMJ_BATCH_W4_BLOCKS 7
+#endif
 
 template <int W, int R, int CS, bool kCos>
-__global__ void __launch_bounds__(128, kCos ? 6 : (W == 1 ? BMJ_BATCH_W1_BLOCKS : 7))
+__global__ void __launch_bounds__(128, kCos ? 6 : W == 1 ? BMJ_BATCH_W1_BLOCKS : W == 4 ? BMJ_BATCH_W4_BLOCKS : 7)
     k_filter_batch_w(const BatchFilterArgs a, int64_t t0, int64_t t1,
                      unsigned long long *counter) {
     extern __shared__ __align__(128) unsigned char smem[];
