@@ -840,8 +840,9 @@ def run_live(idx, arr, qoff, qtok, p, q):
     arrivals, polls the oldest tickets (bmj_serve_poll, no wait) while the
     server's own loop thread batches and runs them; latency = completion -
     submission, measured by the library.  Python's cyclic garbage collector is
-    paused over the stream: a full collection of the interpreter's objects
-    stalls the submitting thread for tens of milliseconds."""
+    paused over the stream and each turn polls at most eight tickets, so that
+    neither a collection nor a large finished batch keeps the submitting thread
+    from the next arrival."""
     import gc
     import numpy as np
     from paper_1711_07295_b300 import _bmj
@@ -857,26 +858,30 @@ def run_live(idx, arr, qoff, qtok, p, q):
     n_res = np.zeros(n, np.int64)
     head = 0   # oldest ticket not yet polled
 
-    def poll_some(wait_ms):
+    def poll_some(wait_ms, limit):
+        # at most `limit` completed tickets per call, so that a large finished
+        # batch does not hold the thread past the next arrival
         nonlocal head
-        while head < n and tickets[head] >= 0:
+        done = 0
+        while head < n and tickets[head] >= 0 and done < limit:
             r = srv.poll(int(tickets[head]), wait_ms=wait_ms)
             if r is None:
                 return
             n_res[head] = len(r[0])
             lat[head] = r[1]
             head += 1
+            done += 1
     gc.collect()
     gc.disable()
     try:
         t0 = time.perf_counter()
         for x in range(n):
             while time.perf_counter() - t0 < arr[x]:
-                poll_some(0)
+                poll_some(0, 8)
             late[x] = time.perf_counter() - t0 - arr[x]
             tickets[x] = srv.submit(qtok[qoff[x]:qoff[x + 1]], int(p[x]), int(q[x]))
         while head < n:
-            poll_some(100)
+            poll_some(100, n)
     finally:
         gc.enable()
     st = srv.close()

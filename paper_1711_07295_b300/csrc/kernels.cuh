@@ -136,7 +136,7 @@ constexpr int kTmaCS1 = BMJ_TMA_CS1, kTmaCS2 = BMJ_TMA_CS2, kTmaCS4 = BMJ_TMA_CS
 constexpr int kAluRowsW1 = BMJ_ALU_ROWS_W1;
 // At b = 256, rows per lane (of four) reduced by three carry-save adders and
 // 5 POPC (PopcAlt4) instead of four and 4 POPC: two rows took the 1M-set
-// filter from 0.840 to 0.871e12 pairs/s (one row 0.870, three 0.870).
+// filter from 0.874 to 0.882e12 pairs/s (one or three rows within 0.3% of two).
 #ifndef BMJ_ALT_ROWS_W4
 #define BMJ_ALT_ROWS_W4 2
 #endif
