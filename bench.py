@@ -790,7 +790,9 @@ def run_batched(args, dev):
 def run_served(args, dev):
     """A Poisson stream of 20,000 queries/s against a resident index of
     2,000,000 sets: continuous batching (4 slots) against one query per
-    launch (1 slot, batches of 1), same arrivals."""
+    launch (1 slot, batches of 1), same arrivals; the saturated capacity
+    (three runs, the median reported), with the SM clocks sampled over the
+    whole section."""
     import numpy as np
     import torch
     from paper_1711_07295_b300 import _bmj, inputs
@@ -802,15 +804,21 @@ def run_served(args, dev):
     arr, qoff, qtok, p, q = inputs.gen_queries(qs, spec, off, tok)
     gen_s = time.perf_counter() - t0
     idx = _bmj.Index(off_d, tok_d, b=64)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
     idx.serve(qoff[:201], qtok[:int(qoff[200])], arr[:200], p[:200], q[:200])   # warm-up
     _, lat, st = idx.serve(qoff, qtok, arr, p, q, n_slots=4, max_batch_queries=4096,
                            want_results=False)
     _, lat1, st1 = idx.serve(qoff, qtok, arr, p, q, n_slots=1, max_batch_queries=1,
                              want_results=False)
     # capacity: the same queries all waiting at time 0
-    _, lat0, st0 = idx.serve(qoff, qtok, np.zeros_like(arr), p, q, n_slots=4,
-                             max_batch_queries=4096, want_results=False)
+    sat = []
+    for _ in range(3):
+        sat.append(idx.serve(qoff, qtok, np.zeros_like(arr), p, q, n_slots=4,
+                             max_batch_queries=4096, want_results=False)[2])
+    st0 = sorted(sat, key=lambda x: x["qps"])[1]
     live = run_live(idx, arr, qoff, qtok, p, q)
+    clk = clocks.stop()
     idx.close()
     return {"workload": "resident index of 2,000,000 sets (Zipf(s=1.1) over 300,000, sizes "
                         "lognormal(2.3,0.6) in [1,500]); Poisson arrivals at 20,000 queries/s, "
@@ -829,8 +837,10 @@ def run_served(args, dev):
                                      "qps": round(st1["qps"], 1), "batches": int(st1["batches"])},
             "saturated": {"qps": round(st0["qps"], 1), "p50_ms": round(st0["p50_ms"], 4),
                           "p99_ms": round(st0["p99_ms"], 4), "batches": int(st0["batches"]),
-                          "arrivals": "all 20,000 queries at time 0"},
+                          "qps_runs": [round(x["qps"], 1) for x in sat],
+                          "arrivals": "all 20,000 queries at time 0 (median of three runs)"},
             "live_submit_poll": live,
+            "clocks": clk,
             "generation_s": round(gen_s, 2)}
 
 
