@@ -172,12 +172,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments, each run of whitespace one blank:
+    what the compiler sees, so that a comment edit keeps the digest."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":  # string or character literal, copied whole
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def filter_source_digest() -> str:
-    """sha256[:16] of the sources the filter kernel is built from."""
+    """sha256[:16] of the code (comments and layout stripped) of the sources
+    the filter kernel is built from."""
     h = hashlib.sha256()
     for name in ("filter_core.cuh", "kernels.cuh", "filter.cu"):
-        with open(os.path.join(ROOT, "paper_1711_07295_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1711_07295_b300", "csrc", name)) as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 
