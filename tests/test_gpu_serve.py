@@ -121,15 +121,17 @@ def test_invalid_probes_and_empty_batch():
     idx.close()
 
 
-def test_full_served_workload_sampled():
+@pytest.mark.parametrize("b", [64, 128])
+def test_full_served_workload_sampled(b):
     # 2,000,000 resident sets (Zipf 1.1 over 300,000, lognormal(2.3, 0.6)); a Poisson
-    # stream at 20,000 queries/s of probes of size 2..300 (half edited resident copies).
+    # stream at 20,000 queries/s of probes of size 2..300 (half edited resident copies);
+    # the index at 128 bits (the width the bench serves at) and at 64.
     spec = I.spec_resident_2m()
     off_d, tok_d = I.gen_collection_device(spec)
     off, tok = off_d.cpu().numpy(), tok_d.cpu().numpy()
     qs = I.QuerySpec(n_queries=4000)
     arr, qoff, qtok, p, q = I.gen_queries(qs, spec, off, tok)
-    idx = _bmj.Index(off_d, tok_d, b=64)
+    idx = _bmj.Index(off_d, tok_d, b=b)
     res, lat, st = idx.serve(qoff, qtok, arr, p, q)
     assert st["n_queries"] == 4000 and st["p99_ms"] > 0
     # window pairs = every (probe, resident set) pair inside Table 2's two-sided window,
