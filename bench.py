@@ -62,8 +62,8 @@ LOP_PER_CLK_PER_SM = 64       # 32-bit logic operations (ALU pipe) per SM per cl
 # adder, 2 LOP3, 3 POPC; 8 words: four carry-save adders, 8 LOP3, 4 POPC).
 FILTER_MIX = {64: (2, 2), 128: (3, 6), 256: (4, 16)}   # b -> (POPC, LOP3) per pair
 # Bitmap width of the served index: at 128 bits the 20,000 q/s stream had p50 0.032 / p99 0.077 ms
-# against 0.034 / 0.079-0.087 at 64 bits (15x fewer survivors to merge) at the same saturated
-# capacity; at 256 bits p99 0.068 ms, but the capacity fell from 9.5e5 to 5.5e5 queries/s.
+# against 0.034 / 0.079-0.087 at 64 bits (15x fewer survivors to merge) and a saturated capacity of
+# 1.0e6 queries/s; at 256 bits p99 0.068-0.072 ms, but the capacity is 6.7e5 queries/s.
 SERVE_B = 128
 FILTER_KERNEL = {64: "k_filter_tma<1,8,256>", 128: "k_filter_tma<2,4,128>",
                  256: "k_filter_tma<4,4,64>"}

@@ -39,6 +39,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "filter_core.cuh"
 #include "host_util.cuh"
 
 struct bmj_index {
@@ -239,8 +240,18 @@ __global__ void __launch_bounds__(256)
             for (int u = 0; u < U; u++) {  // all loads of the step first
                 const int64_t j = j0 + u * 32 + lane;
                 cs[u] = j < c1 ? ssz[j] : 0u;
+                if constexpr (kW == 2 || kW == 4) {  // 16-byte loads (a bitmap row is 16 or 32 bytes)
+                    const ulonglong2 *b2 = reinterpret_cast<const ulonglong2 *>(bm) + j * (kW / 2);
 #pragma unroll
-                for (int w = 0; w < kW; w++) cb[u][w] = j < c1 ? bm[j * kW + w] : 0ull;
+                    for (int w = 0; w < kW / 2; w++) {
+                        const ulonglong2 v = j < c1 ? b2[w] : make_ulonglong2(0ull, 0ull);
+                        cb[u][2 * w] = v.x;
+                        cb[u][2 * w + 1] = v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int w = 0; w < kW; w++) cb[u][w] = j < c1 ? bm[j * kW + w] : 0ull;
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; u++) {
@@ -248,7 +259,18 @@ __global__ void __launch_bounds__(256)
                 bool sv = false;
                 if (j < c1) {
                     int h = 0;
-                    if (kW > 0) {
+                    if constexpr (kW == 2 || kW == 4) {
+                        // the carry-save popcount of the join's filter (3 or 4 POPC
+                        // for 4 or 8 words instead of 4 or 8)
+                        uint32_t xw[2 * kW];
+#pragma unroll
+                        for (int w = 0; w < kW; w++) {
+                            const uint64_t d = pb[w] ^ cb[u][w];
+                            xw[2 * w] = (uint32_t)d;
+                            xw[2 * w + 1] = (uint32_t)(d >> 32);
+                        }
+                        h = PopcHS<kW>::h(xw);
+                    } else if (kW > 0) {
 #pragma unroll
                         for (int w = 0; w < kW; w++) h += __popcll(pb[w] ^ cb[u][w]);
                     } else {
