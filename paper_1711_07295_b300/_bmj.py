@@ -87,7 +87,8 @@ class bmj_stats(C.Structure):
                 ("cascade_b", C.c_int32), ("cutoff", C.c_int32), ("ms_prepare", C.c_float),
                 ("ms_filter", C.c_float), ("ms_verify", C.c_float), ("ms_output", C.c_float),
                 ("ms_total", C.c_float), ("reserved_f", C.c_float), ("candidates", C.c_int64),
-                ("candidate_slots", C.c_int64), ("tile_rows", C.c_int32), ("chunk_cols", C.c_int32)]
+                ("candidate_slots", C.c_int64), ("tile_rows", C.c_int32), ("chunk_cols", C.c_int32),
+                ("fold_steps", C.c_int64), ("fold_full_steps", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

@@ -37,7 +37,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // single join's: kTmaR1, kTmaR2, kTmaR4), the tile classes (three widths, two
 // tiles each, then every other width) and the counters of a plan.
 constexpr int kSmallR1 = 2, kSmallR2 = 1, kSmallR4 = 1;
-constexpr int kClasses = 7;
+constexpr int kClasses = 8;
 constexpr int kCounters = 3 + kClasses;
 #ifndef BMJ_SMALL_COST1
 #define BMJ_SMALL_COST1 1.3
@@ -64,7 +64,7 @@ struct JobDesc {
     int32_t chunk_cols;
     int32_t sim;         // similarity function of the threshold p/q
     SimWindow win;       // its length window (Table 2)
-    int32_t pad;
+    int32_t fold;        // b = 128: the folded 64-bit test before the 128-bit one
 };
 
 __device__ __forceinline__ int64_t lower_bound_range(const uint32_t *a, int64_t lo, int64_t hi,
@@ -245,6 +245,14 @@ constexpr int kBatchAltR = (W == 1 && R >= 8) || (W == 4 && R >= 4) ? kAltRows<W
 // registers, 8 bytes spilled) ran the 512-job execute stage in 248.2 ms against
 // 249.6 ms with seven.  At b = 256 seven (72 registers): eight, within 64
 // registers, took it from 242.8 to 250.1 ms.
+// The batched b = 128 filter takes the folded test (as the single join does) in
+// jobs whose sampled 64-bit survivor rate is at most this (from the autotuner;
+// every b = 128 job of default-height tiles when the width is given).
+#ifndef BMJ_BATCH_FOLD_RATE
+#define BMJ_BATCH_FOLD_RATE 2e-3
+#endif
+constexpr double kBatchFoldMaxRate64 = BMJ_BATCH_FOLD_RATE;
+
 #ifndef BMJ_BATCH_W1_BLOCKS
 #define BMJ_BATCH_W1_BLOCKS 8
 #endif
@@ -252,7 +260,7 @@ constexpr int kBatchAltR = (W == 1 && R >= 8) || (W == 4 && R >= 4) ? kAltRows<W
 #define BMJ_BATCH_W4_BLOCKS 7
 #endif
 
-template <int W, int R, int CS, bool kCos>
+template <int W, int R, int CS, bool kCos, bool kFold>
 __global__ void __launch_bounds__(128, kCos ? 6 : W == 1 ? BMJ_BATCH_W1_BLOCKS : W == 4 ? BMJ_BATCH_W4_BLOCKS : 7)
     k_filter_batch_w(const BatchFilterArgs a, int64_t t0, int64_t t1,
                      unsigned long long *counter) {
@@ -277,8 +285,8 @@ __global__ void __launch_bounds__(128, kCos ? 6 : W == 1 ? BMJ_BATCH_W1_BLOCKS :
         const int64_t c1 = min(c0 + (int64_t)jd.chunk_cols, c_end);
         const SurvivorSink sink{a.queue, a.qcount, a.job_surv ? &a.job_surv[k] : nullptr, a.qcap};
         const SimArgs sa{jd.win, jd.p, jd.q};
-        filter_item_tma<W, R, CS, kBatchAltR<W, R>, kCos>(jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0,
-                                                      c0, c1, sa, sink, stg);
+        filter_item_tma<W, R, CS, kBatchAltR<W, R>, kCos, false, kFold>(
+            jd.bm, a.ssz, a.lim + jd.lim_off, jd.end, i0, c0, c1, sa, sink, stg);
         if (!stg.ok) {
             drain_stage(stg);
             if (lane == 0) atomicOr(a.err, 1);
@@ -494,10 +502,10 @@ int upload_jobs(Plan &P, Arena &A, cudaStream_t s) {
 // Tile class of a job: its width and its rows per lane (the default of the
 // single join, or the small tile for jobs whose diagonal tiles would waste a
 // large share of their window; see the tuner).
-int tile_class(int W, int tile_rows) {
+int tile_class(int W, int tile_rows, int fold = 0) {
     switch (W) {
         case 1: return tile_rows == 32 * kTmaR1 ? 0 : 1;
-        case 2: return tile_rows == 32 * kTmaR2 ? 2 : 3;
+        case 2: return tile_rows == 32 * kTmaR2 ? (fold ? 7 : 2) : 3;
         case 4: return tile_rows == 32 * kTmaR4 ? 4 : 5;
         default: return 6;
     }
@@ -512,24 +520,24 @@ int small_tile_rows(int W) {
 // tile of the width (measured on a B300 with large jobs forced to each tile).
 double small_tile_cost(int W) { return W == 1 ? kSmallCost1 : W == 2 ? kSmallCost2 : kSmallCost4; }
 
-template <int W, int R, int CS, bool kCos>
+template <int W, int R, int CS, bool kCos, bool kFold>
 int launch_class_c(const BatchFilterArgs &fa, int64_t t0, int64_t t1, unsigned long long *counter,
                    int sms, cudaStream_t s) {
     const int smem = 4 * ColStage<W, CS>::kWarpBytes;
     int per_sm = 0;
-    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_w<W, R, CS, kCos>,
-                                                            128, smem));
+    BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_filter_batch_w<W, R, CS, kCos, kFold>, 128, smem));
     if (per_sm < 1) per_sm = 1;
-    BMJ_LAUNCH((k_filter_batch_w<W, R, CS, kCos>), (unsigned)(sms * per_sm), 128, smem, s, fa, t0,
-               t1, counter);
+    BMJ_LAUNCH((k_filter_batch_w<W, R, CS, kCos, kFold>), (unsigned)(sms * per_sm), 128, smem, s,
+               fa, t0, t1, counter);
     return BMJ_OK;
 }
 
-template <int W, int R, int CS>
+template <int W, int R, int CS, bool kFold = false>
 int launch_class(const BatchFilterArgs &fa, int64_t t0, int64_t t1, unsigned long long *counter,
                  int sms, cudaStream_t s) {
-    return fa.sim == BMJ_COSINE ? launch_class_c<W, R, CS, true>(fa, t0, t1, counter, sms, s)
-                                : launch_class_c<W, R, CS, false>(fa, t0, t1, counter, sms, s);
+    return fa.sim == BMJ_COSINE ? launch_class_c<W, R, CS, true, kFold>(fa, t0, t1, counter, sms, s)
+                                : launch_class_c<W, R, CS, false, kFold>(fa, t0, t1, counter, sms, s);
 }
 
 // Filter over the planned items into the plan's queue (cap may be 0: count
@@ -562,6 +570,7 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
             case 3: st = launch_class<2, kSmallR2, kTmaCS2>(fa, t0, t1, counter, sms, s); break;
             case 4: st = launch_class<4, kTmaR4, kTmaCS4>(fa, t0, t1, counter, sms, s); break;
             case 5: st = launch_class<4, kSmallR4, kTmaCS4>(fa, t0, t1, counter, sms, s); break;
+            case 7: st = launch_class<2, kTmaR2, kTmaCS2, true>(fa, t0, t1, counter, sms, s); break;
             default: {
                 int per_sm = 0;
                 BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_generic,
@@ -648,6 +657,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
     std::vector<uint32_t> res_a, res_b;
     std::vector<int> job_b(n_jobs, o.b > 0 ? o.b : 64), job_method(n_jobs, o.method);
     std::vector<char> job_small(n_jobs, 0);  // 1: the job's tiles are the small row tile
+    std::vector<char> job_fold(n_jobs, 1);   // b = 128 jobs: 1 = the folded test first
     for (int64_t k = 0; k < n_jobs; k++)
         if (o.method == BMJ_COMBINED) job_method[k] = combined_method(sim, hp[k], hq[k]);
     std::vector<unsigned long long> job_win(n_jobs, 0), job_sv(n_jobs, 0);
@@ -776,6 +786,7 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                 jd.W = jb[k] / 64;
                 jd.tile_rows = job_small[k] ? small_tile_rows(jd.W) : default_tile_rows(jd.W);
                 jd.chunk_cols = 4096;
+                jd.fold = jd.W == 2 && !job_small[k] && job_fold[k] ? 1 : 0;
             }
         };
         set_jobs(job_b);
@@ -913,6 +924,10 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
                     }
                 }
                 est_surv += best_surv;
+                // the folded test pays where few pairs pass the 64-bit filter (a column
+                // step of 128 pairs then rarely needs the 128-bit test)
+                const double r64 = samp_win[0][k] > 0 ? (double)samp_surv[0][k] / samp_win[0][k] : 0.0;
+                job_fold[k] = widths[0] == 64 && r64 > kBatchFoldMaxRate64 ? 0 : 1;
             }
             set_jobs(job_b);
             st = upload_jobs(P, A, s);
@@ -947,8 +962,8 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         std::vector<int32_t> order(n_jobs);
         for (int64_t k = 0; k < n_jobs; k++) order[k] = (int32_t)k;
         std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) {
-            return tile_class(P.jobs[a].W, P.jobs[a].tile_rows) <
-                   tile_class(P.jobs[c].W, P.jobs[c].tile_rows);
+            return tile_class(P.jobs[a].W, P.jobs[a].tile_rows, P.jobs[a].fold) <
+                   tile_class(P.jobs[c].W, P.jobs[c].tile_rows, P.jobs[c].fold);
         });
         std::vector<int64_t> job_tile0(n_jobs + 1, 0);
         for (int c = 0; c < kClasses; c++) P.class_t0[c] = P.class_t1[c] = 0;
@@ -961,7 +976,8 @@ int batch_impl(const bmj_collection *coll, int64_t n_jobs, const int64_t *job_se
         for (int c = 0; c < kClasses; c++) {
             int64_t lo = -1, hi = -1;
             for (int64_t pos = 0; pos < n_jobs; pos++)
-                if (tile_class(P.jobs[order[pos]].W, P.jobs[order[pos]].tile_rows) == c) {
+                if (tile_class(P.jobs[order[pos]].W, P.jobs[order[pos]].tile_rows,
+                               P.jobs[order[pos]].fold) == c) {
                     if (lo < 0) lo = job_tile0[pos];
                     hi = job_tile0[pos + 1];
                 }

@@ -94,8 +94,12 @@ __global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterAr
         const int64_t c_end =
             a.tile_c1 ? (int64_t)a.tile_c1[t] : min(i0 + (int64_t)a.tile_rows, row_end) - 1;
         const int64_t c1 = min(c0 + (int64_t)a.chunk_cols, c_end);
-        filter_item_tma<W, R, CS, kAltRows<W>, kCos, kCut>(a.bm, a.ssz, a.lim, row_end, i0, c0,
-                                                            c1, sa, sink, st);
+        filter_item_tma<W, R, CS, kAltRows<W>, kCos, kCut, kFoldW<W>>(a.bm, a.ssz, a.lim, row_end,
+                                                                       i0, c0, c1, sa, sink, st);
+        if (kFoldW<W> && a.steps && lane == 0 && c1 > c0) {
+            atomicAdd(&a.steps[0], (unsigned long long)(c1 - c0));
+            atomicAdd(&a.steps[1], (unsigned long long)st.n_full);
+        }
         if (!st.ok) {
             drain_stage(st);
             if (lane == 0) atomicOr(err, 1);

@@ -379,6 +379,8 @@ struct StageState {
     int pending;          // after a failed wait: 1 + slot of a copy still in flight, or 0
     int wait_limit;       // polls before a wait gives up
     int skip_copy;        // fault injection: issue no copy for the next fill (then 0)
+    uint32_t n_full;      // filter_item_tma with kFold: column steps of the last item that
+                          // took the 128-bit test
 };
 
 // After a failed wait: waits (bounded) for the copy still in flight, so that
@@ -400,6 +402,7 @@ __device__ __forceinline__ void init_stage(StageState &st, unsigned char *region
     st.pending = 0;
     st.wait_limit = 1 << 22;
     st.skip_copy = 0;
+    st.n_full = 0;
     if ((threadIdx.x & 31) == 0) {
         mbar_init(&st.bar[0], 1);
         mbar_init(&st.bar[1], 1);
@@ -491,7 +494,13 @@ __device__ __forceinline__ void flush_masks(const uint32_t (&mask)[R], const int
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
 // arrays must be readable up to 3 entries past the last column (padded).
-template <int W, int R, int CS, int kAltRows = 0, bool kCos = false, bool kCut = false>
+// kFold (b = 128): every pair first meets Eq. 2 with the two 64-bit halves of
+// the xor folded onto each other; popc(x0 ^ x1) <= popc(x0) + popc(x1), so a
+// pair that fails this test fails the 128-bit one too, and a warp runs the
+// 128-bit test on a column only when one of its 32 x R pairs passes the folded
+// one (the survivors are the same).
+template <int W, int R, int CS, int kAltRows = 0, bool kCos = false, bool kCut = false,
+          bool kFold = false>
 __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                                                 const uint32_t *__restrict__ ssz,
                                                 const int32_t *__restrict__ lim_tab,
@@ -501,6 +510,7 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
     using L = ColStage<W, CS>;
     constexpr unsigned kFull = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    st.n_full = 0;
     if (c1 <= c0) return;
     // rows in registers, as 32-bit words
     uint32_t rb[R][2 * W];
@@ -524,6 +534,8 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
             for (int w = 0; w < 2 * W; w++) rb[k][w] = 0;
         }
     }
+    static_assert(!kFold || W == 2, "the folded test is for b = 128");
+    uint32_t n_full = 0;  // kFold: column steps that took the 128-bit test (left in st.n_full)
     int nlim[R];
 #pragma unroll
     for (int k = 0; k < R; k++) nlim[k] = 0;
@@ -578,19 +590,42 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                 uint32_t cw[2 * W];
 #pragma unroll
                 for (int w = 0; w < 2 * W; w++) cw[w] = colw[col * 2 * W + w];
+                if constexpr (kFold) {
+                    // the column's fold; each row's fold is taken inside the same
+                    // three-input xor
+                    const uint32_t f0 = cw[0] ^ cw[2], f1 = cw[1] ^ cw[3];
+                    int any = 0;  // sign bit: some row passes the folded test
 #pragma unroll
-                for (int k = 0; k < R; k++) {
-                    uint32_t x[2 * W];
+                    for (int k = 0; k < R; k++)
+                        any |= __popc(rb[k][0] ^ rb[k][2] ^ f0) + __popc(rb[k][1] ^ rb[k][3] ^ f1) +
+                               nlim[k];
+                    if (__builtin_expect(__any_sync(kFull, any < 0), 0)) {
+                        n_full++;
+                        const int sh = gj - 1 - cc;  // bit of this column in the masks
 #pragma unroll
-                    for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
-                    // rows R - kAltRows .. R - 1 take the width's second form
-                    const bool alt = kAltRows > 0 && k >= R - kAltRows;
-                    int h;
-                    if constexpr (W == 1) h = alt ? popc64_alu(x[0], x[1]) : PopcHS<1>::h(x);
-                    else if constexpr (W == 4) h = alt ? PopcAlt4::h(x) : PopcHS<4>::h(x);
-                    else h = PopcHS<W>::h(x);
-                    const int t = h + nlim[k];
-                    mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);
+                        for (int k = 0; k < R; k++) {
+                            uint32_t x[2 * W];
+#pragma unroll
+                            for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
+                            const int t = PopcHS<W>::h(x) + nlim[k];
+                            mask[k] |= ((uint32_t)t >> 31) << sh;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < R; k++) {
+                        uint32_t x[2 * W];
+#pragma unroll
+                        for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
+                        // rows R - kAltRows .. R - 1 take the width's second form
+                        const bool alt = kAltRows > 0 && k >= R - kAltRows;
+                        int h;
+                        if constexpr (W == 1) h = alt ? popc64_alu(x[0], x[1]) : PopcHS<1>::h(x);
+                        else if constexpr (W == 4) h = alt ? PopcAlt4::h(x) : PopcHS<4>::h(x);
+                        else h = PopcHS<W>::h(x);
+                        const int t = h + nlim[k];
+                        mask[k] = __funnelshift_l((uint32_t)t, mask[k], 1);
+                    }
                 }
             }
             // bit (gj-1-cc) of mask[k] is column g+cc; keep only columns j < i
@@ -607,6 +642,7 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
         }
         __syncwarp();  // every lane is done with this slot before it is refilled
     }
+    st.n_full = n_full;
 }
 
 }  // namespace bmj

@@ -198,7 +198,8 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
         int32_t *tile_c0 = nullptr, *tile_c1 = nullptr;
         int64_t *tile_off = nullptr;
         // [0] window, [1] queue count, [2] item counter, [3] results, [4] verified,
-        // [5] first-level survivors (cascade)
+        // [5] first-level survivors (cascade), [6] [7] the filter's folded-test column
+        // steps and those of them that took the full test (b = 128)
         unsigned long long *ctr = nullptr;
         int *err = nullptr;
         st = A.alloc(&need, (size_t)n_s);
@@ -206,10 +207,10 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
         if (!st) st = A.alloc(&tile_c0, (size_t)(n_tiles > 0 ? n_tiles : 1));
         if (!st) st = A.alloc(&tile_off, (size_t)n_tiles + 1);
         if (!st && rs) st = A.alloc(&tile_c1, (size_t)(n_tiles > 0 ? n_tiles : 1));
-        if (!st) st = A.alloc(&ctr, 6);
+        if (!st) st = A.alloc(&ctr, 8);
         if (!st) st = A.alloc(&err, 1);
         if (st) return st;
-        BMJ_CHECK(cudaMemsetAsync(ctr, 0, 6 * sizeof(unsigned long long), s));
+        BMJ_CHECK(cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned long long), s));
         BMJ_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
         BMJ_CHECK(cudaMemsetAsync(ssz + n, 0, 4 * sizeof(uint32_t), s));
         BMJ_CHECK(cudaMemsetAsync(bm + (size_t)n * W, 0, 4 * W * sizeof(uint64_t), s));
@@ -404,11 +405,15 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
             fa.qcount = &ctr[1];
             fa.qcap = qcap;
             fa.item_counter = &ctr[2];
+            fa.steps = &ctr[6];
             if (fault.timeout) {
                 fa.fault_skip_copy = 1;
                 fa.wait_limit = 1 << 12;
             }
-            // Filters work items [lo, hi) into the queue; *count = their survivors.
+            // Filters work items [lo, hi) into the queue; *count = their survivors.  The
+            // folded-test step counts are taken from the first pass (every item once).
+            int64_t fold_steps[2] = {0, 0};
+            bool fold_read = false;
             auto run_filter = [&](int64_t lo, int64_t hi, int64_t *count) -> int {
                 NvtxRange nv("bmj.filter");
                 const unsigned long long init[2] = {0ull, (unsigned long long)lo};
@@ -421,8 +426,17 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                 int herr = 0;
                 BMJ_CHECK(cudaMemcpyAsync(count, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
                 BMJ_CHECK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+                const bool read_steps = !fold_read && W == 2;
+                if (read_steps)
+                    BMJ_CHECK(cudaMemcpyAsync(fold_steps, &ctr[6], 2 * sizeof(int64_t),
+                                              cudaMemcpyDeviceToHost, s));
                 BMJ_CHECK(cudaStreamSynchronize(s));
                 if (herr) return BMJ_ERR_TIMEOUT;
+                if (read_steps) {
+                    fold_read = true;
+                    stl.fold_steps = fold_steps[0];
+                    stl.fold_full_steps = fold_steps[1];
+                }
                 stl.filter_passes++;
                 stl.ms_filter += ev.ms(3, 4);
                 return BMJ_OK;

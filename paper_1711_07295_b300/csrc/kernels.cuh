@@ -96,6 +96,9 @@ struct FilterArgs {
     unsigned long long *qcount;
     int64_t qcap;
     unsigned long long *item_counter;
+    // [2] (may be null): at b = 128, warp column steps of the folded test and
+    // those that took the 128-bit test
+    unsigned long long *steps = nullptr;
 };
 
 // The Bitmap Filter over every window pair (persistent, warp-level work items;
@@ -140,6 +143,12 @@ constexpr int kAluRowsW1 = BMJ_ALU_ROWS_W1;
 #ifndef BMJ_ALT_ROWS_W4
 #define BMJ_ALT_ROWS_W4 2
 #endif
+// At b = 128, the folded 64-bit test before the 128-bit one (filter_item_tma's kFold).
+#ifndef BMJ_FOLD_W2
+#define BMJ_FOLD_W2 1
+#endif
+template <int W>
+constexpr bool kFoldW = W == 2 && BMJ_FOLD_W2;
 // Rows per lane that take the second popcount form of width W (popc64_alu at
 // b = 64, PopcAlt4 at b = 256).
 template <int W>

@@ -22,6 +22,24 @@ def test_filter_bound_per_width():
     assert 16 / popc == 64 / lop
 
 
+def test_folded_filter_bound():
+    # b = 128 with the folded test: (2 + 3f) POPC and (2.5 + 6f) LOP3 per pair for a
+    # fraction f of full-test steps; XU-bound for every f in [0, 1]
+    assert bench.filter_mix(128, 0.0) == (2, 2.5)
+    assert bench.filter_mix(128, 1.0) == (5, 8.5)
+    assert bench.filter_mix(128) == bench.FILTER_MIX[128]
+    assert bench.filter_mix(64, 0.5) == bench.FILTER_MIX[64]
+    assert bench.filter_bound(128, 148, 2032.0, 0.0) == pytest.approx(148 * 8 * 2032e6)
+    assert bench.filter_bound(128, 148, 2032.0, 1.0) == pytest.approx(148 * 16 / 5 * 2032e6)
+    f = 0.046
+    assert bench.filter_bound(128, 148, 2032.0, f) == pytest.approx(148 * 16 / (2 + 3 * f) * 2032e6)
+    r = bench.filter_roofline(128, 1.0e12, 500.0, 148, 2032.0, full_frac=f)
+    assert r["achieved"] == pytest.approx(2.0, abs=1e-4)
+    assert r["frac"] == pytest.approx(2.0e12 / bench.filter_bound(128, 148, 2032.0, f), abs=1e-4)
+    assert r["frac_of_full_test_bound"] == pytest.approx(2.0e12 / bench.filter_bound(128, 148, 2032.0),
+                                                         abs=1e-4)
+
+
 def test_strip_comments_keeps_code_and_literals():
     src = ('int a = 1; // one\n'
            'const char *s = "x // not a comment /* nor this */";\n'

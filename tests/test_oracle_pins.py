@@ -869,3 +869,23 @@ def test_rs_window_pairs_from_the_size_histograms(sim, p, q):
     w, _, _ = O.rs_filter_counts(ro, rt, so, st, p, q, 64, O.XOR, sim=sim)
     assert w == brute
     assert O.rs_window_pairs([], ss, p, q, sim) == 0 == O.rs_window_pairs(sr, [], p, q, sim)
+
+
+def test_folded_bitmap_distance_bounds_the_full_one():
+    # The b = 128 filter's first test folds the two 64-bit halves of the xor onto each
+    # other.  For Xor bitmaps (h(t) = t mod b) the fold of a 128-bit bitmap is the 64-bit
+    # Xor bitmap of the same set, and for every method the folded distance is at most
+    # the 128-bit one, so Eq. 2 on the fold never rejects a pair the 128-bit test keeps.
+    rng = np.random.default_rng(5)
+    for _ in range(300):
+        n1, n2 = rng.integers(1, 300, size=2)
+        x = np.unique(rng.integers(0, 1 << 31, size=n1)).astype(np.int32)
+        y = np.unique(rng.integers(0, 1 << 31, size=n2)).astype(np.int32)
+        assert np.array_equal(O.bitmap(x, 128, O.XOR)[0] ^ O.bitmap(x, 128, O.XOR)[1],
+                              O.bitmap(x, 64, O.XOR)[0])
+        for m in (O.XOR, O.SET, O.NEXT):
+            bx, by = O.bitmap(x, 128, m), O.bitmap(y, 128, m)
+            h_fold = O.hamming(np.array([bx[0] ^ bx[1]]), np.array([by[0] ^ by[1]]))
+            h_full = O.hamming(bx, by)
+            assert h_fold <= h_full
+            assert O.upper_bound(len(x), len(y), h_fold) >= O.upper_bound(len(x), len(y), h_full)
