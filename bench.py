@@ -69,7 +69,7 @@ FOLD_MIX = (2, 2.5)
 # against 0.034 / 0.079-0.087 at 64 bits (15x fewer survivors to merge) and a saturated capacity of
 # 1.0e6 queries/s; at 256 bits p99 0.068-0.072 ms, but the capacity is 6.7e5 queries/s.
 SERVE_B = 128
-FILTER_KERNEL = {64: "k_filter_tma<1,8,256>", 128: "k_filter_tma<2,4,128>",
+FILTER_KERNEL = {64: "k_filter_tma<1,8,256>", 128: "k_filter_tma<2,5,128>",
                  256: "k_filter_tma<4,4,64>"}
 FLUSH_BYTES = 256 << 20       # > 126 MB L2
 

@@ -196,11 +196,12 @@ typedef struct {
     int64_t candidate_slots;/* BMJ_CAND_PREFIX / AUTO: (rank, pair) slots the candidates were expanded
                                from (a pair sharing k prefix tokens has k slots); they go
                                through a buffer of fixed size in filter_passes ranges */
-    int32_t tile_rows;      /* bmj_self_join_batch job stats: rows of the job's filter tile
-                               (32 x rows per lane) */
+    int32_t tile_rows;      /* rows of the filter's tile (32 x rows per lane), of the job's tile in
+                               bmj_self_join_batch job stats */
     int32_t chunk_cols;     /* ... and columns per filter work item */
-    int64_t fold_steps;     /* b = 128: warp column steps of the filter (32 x 4 rows against one
-                               column each), every one first tested with the two 64-bit halves
+    int64_t fold_steps;     /* b = 128: warp column steps of the filter (the tile_rows rows of a
+                               warp's tile against one column each), every one first tested
+                               with the two 64-bit halves
                                of the xor folded onto each other (fewer differing bits than the
                                128-bit xor, so a pair that fails it fails Eq. 2); counted over
                                the first filter pass, 0 at other widths */

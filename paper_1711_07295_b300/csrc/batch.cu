@@ -34,9 +34,12 @@ namespace {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 // Rows per lane of the small row tile of each width (the default tile is the
-// single join's: kTmaR1, kTmaR2, kTmaR4), the tile classes (three widths, two
-// tiles each, then every other width) and the counters of a plan.
+// single join's at b = 64 and 256, kTmaR1 and kTmaR4, and 4 rows at b = 128,
+// the batch's measured configuration), the tile classes (three widths, two
+// tiles each, every other width, then b = 128 default tiles with the folded
+// test) and the counters of a plan.
 constexpr int kSmallR1 = 2, kSmallR2 = 1, kSmallR4 = 1;
+constexpr int kBatchR2 = 4;
 constexpr int kClasses = 8;
 constexpr int kCounters = 3 + kClasses;
 #ifndef BMJ_SMALL_COST1
@@ -505,13 +508,13 @@ int upload_jobs(Plan &P, Arena &A, cudaStream_t s) {
 int tile_class(int W, int tile_rows, int fold = 0) {
     switch (W) {
         case 1: return tile_rows == 32 * kTmaR1 ? 0 : 1;
-        case 2: return tile_rows == 32 * kTmaR2 ? (fold ? 7 : 2) : 3;
+        case 2: return tile_rows == 32 * kBatchR2 ? (fold ? 7 : 2) : 3;
         case 4: return tile_rows == 32 * kTmaR4 ? 4 : 5;
         default: return 6;
     }
 }
 int default_tile_rows(int W) {
-    return W == 1 ? 32 * kTmaR1 : W == 2 ? 32 * kTmaR2 : W == 4 ? 32 * kTmaR4 : 32;
+    return W == 1 ? 32 * kTmaR1 : W == 2 ? 32 * kBatchR2 : W == 4 ? 32 * kTmaR4 : 32;
 }
 int small_tile_rows(int W) {
     return W == 1 ? 32 * kSmallR1 : W == 2 ? 32 * kSmallR2 : W == 4 ? 32 * kSmallR4 : 32;
@@ -566,11 +569,11 @@ int enqueue_filter(const Plan &P, int sms, cudaStream_t s) {
         switch (c) {
             case 0: st = launch_class<1, kTmaR1, kTmaCS1>(fa, t0, t1, counter, sms, s); break;
             case 1: st = launch_class<1, kSmallR1, kTmaCS1>(fa, t0, t1, counter, sms, s); break;
-            case 2: st = launch_class<2, kTmaR2, kTmaCS2>(fa, t0, t1, counter, sms, s); break;
+            case 2: st = launch_class<2, kBatchR2, kTmaCS2>(fa, t0, t1, counter, sms, s); break;
             case 3: st = launch_class<2, kSmallR2, kTmaCS2>(fa, t0, t1, counter, sms, s); break;
             case 4: st = launch_class<4, kTmaR4, kTmaCS4>(fa, t0, t1, counter, sms, s); break;
             case 5: st = launch_class<4, kSmallR4, kTmaCS4>(fa, t0, t1, counter, sms, s); break;
-            case 7: st = launch_class<2, kTmaR2, kTmaCS2, true>(fa, t0, t1, counter, sms, s); break;
+            case 7: st = launch_class<2, kBatchR2, kTmaCS2, true>(fa, t0, t1, counter, sms, s); break;
             default: {
                 int per_sm = 0;
                 BMJ_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_batch_generic,

@@ -68,8 +68,13 @@ __global__ void __launch_bounds__(256) k_filter_generic(const FilterArgs a, int 
 // Eight 4-warp blocks per SM (64 registers) for the production variants; the
 // Cosine variant's per-pair limit needs more registers.  kCut: pairs whose
 // larger set is above the cutoff point skip Eq. 2 (Section 3.5).
+// Resident blocks per SM at b = 128 (the register bound follows: 56 at nine).
+#ifndef BMJ_TMA_MINB2
+#define BMJ_TMA_MINB2 9
+#endif
 template <int W, int R, int CS, bool kFault, bool kCos, bool kCut>
-__global__ void __launch_bounds__(128, kCos ? 6 : 8) k_filter_tma(const FilterArgs a, int *err) {
+__global__ void __launch_bounds__(128, kCos ? 6 : W == 2 ? BMJ_TMA_MINB2 : 8)
+    k_filter_tma(const FilterArgs a, int *err) {
     extern __shared__ __align__(128) unsigned char smem[];
     using L = ColStage<W, CS>;
     const int lane = threadIdx.x & 31;

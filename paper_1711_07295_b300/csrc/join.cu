@@ -190,6 +190,8 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
         int32_t *need = nullptr, *lim = nullptr;
         const int tile_rows = filter_tma_tile_rows(W);
         const int chunk_cols = W <= 4 ? 4096 : 2048;
+        stl.tile_rows = tile_rows;
+        stl.chunk_cols = chunk_cols;
         // rows joined: size-order positions [r0, r1) (all rows unless a band is given)
         const int64_t r0 = rs ? n_sc : (o.row_begin == 0 && o.row_end == 0) ? 0 : o.row_begin;
         const int64_t r1 = rs ? n : (o.row_begin == 0 && o.row_end == 0) ? n : o.row_end;

@@ -110,8 +110,13 @@ int filter_tile_rows(int W);
 #ifndef BMJ_TMA_R1
 #define BMJ_TMA_R1 8
 #endif
+// At b = 128, with the folded test, 5 rows per lane and nine blocks per SM
+// (56 registers) ran 4M sets of the 10M shape at 2.071 / 2.191e12 pairs/s
+// (3/5, 9/10) against 1.962 / 2.058 with 4 rows and eight blocks, 2.039 / 2.140
+// with 4 rows and nine, 2.044 / 2.176 with 6 rows and eight, 2.013 / 2.144 with
+// 6 rows and nine (spilling); 8 rows spill.
 #ifndef BMJ_TMA_R2
-#define BMJ_TMA_R2 4
+#define BMJ_TMA_R2 5
 #endif
 // Chunks of 128 columns at b = 128 and 64 at b = 256 (half the shared memory of
 // 256 and 128: more resident warps) measured 3.4% faster each; 128 at b = 64

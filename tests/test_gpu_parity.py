@@ -56,13 +56,16 @@ def check_join(off, tok, p, q, b=64, method=_bmj.BMJ_XOR, counts=True, sim=_bmj.
 def test_folded_test_keeps_the_survivors(method, sim, p, q):
     # b = 128 runs the 128-bit test only in the warp column steps where some pair
     # passes the folded 64-bit test; survivors and results stay the oracle's, and
-    # the step counters are consistent with the pairs: a step covers at most 32 x 4
-    # window pairs, and every survivor lies in a step that took the full test
+    # the step counters are consistent with the pairs: a step covers at most one
+    # tile's rows (32 x rows per lane) of window pairs, and every survivor lies in a
+    # step that took the full test
     off, tok = I.random_collection(6000, 3000, 1, 60, seed=11, planted_frac=0.15)
     st = check_join(off, tok, p, q, b=128, method=method, sim=sim)
+    rows = st["tile_rows"]
+    assert rows % 32 == 0 and 32 <= rows <= 256
     assert 0 <= st["fold_full_steps"] <= st["fold_steps"]
-    assert st["window_pairs"] <= 128 * st["fold_steps"]
-    assert st["survivors"] <= 128 * st["fold_full_steps"]
+    assert st["window_pairs"] <= rows * st["fold_steps"]
+    assert st["survivors"] <= rows * st["fold_full_steps"]
     assert st["survivors"] > 0
     # with a queue too small for the survivors (reruns in item ranges) nothing changes
     check_join(off, tok, p, q, b=128, method=method, sim=sim, queue_cap=97)
