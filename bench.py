@@ -61,10 +61,11 @@ LOP_PER_CLK_PER_SM = 64       # 32-bit logic operations (ALU pipe) per SM per cl
 # compression of those words allows (2 words: 2 POPC; 4 words: one carry-save
 # adder, 2 LOP3, 3 POPC; 8 words: four carry-save adders, 8 LOP3, 4 POPC).
 FILTER_MIX = {64: (2, 2), 128: (3, 6), 256: (4, 16)}   # b -> (POPC, LOP3) per pair
-# b = 128: the folded test every pair meets first (the two 64-bit halves of the xor folded onto
-# each other: 2 POPC, 2 three-input xors and a quarter of the column's two-word fold), before the
-# 128-bit test of FILTER_MIX[128] in the column steps where some pair passes it
-FOLD_MIX = (2, 2.5)
+# b = 128 and 256: the folded test every pair meets first (the two halves of the xor folded onto
+# each other, 64 or 128 bits: 2 POPC and 2 three-input xors, or 3 POPC, 4 three-input xors and a
+# carry-save adder; plus the row's share of the column's fold, 2 words over 5 rows or 4 over 4),
+# before the full-width test of FILTER_MIX[b] in the column steps where some pair passes it
+FOLD_MIX = {128: (2, 2.4), 256: (3, 7)}
 # Bitmap width of the served index: at 128 bits the 20,000 q/s stream had p50 0.032 / p99 0.077 ms
 # against 0.034 / 0.079-0.087 at 64 bits (15x fewer survivors to merge) and a saturated capacity of
 # 1.0e6 queries/s; at 256 bits p99 0.068-0.072 ms, but the capacity is 6.7e5 queries/s.
@@ -232,12 +233,12 @@ def profile_traffic(name: str):
 
 
 def filter_mix(b: int, full_frac=None):
-    """(POPC, LOP3) per window pair: FILTER_MIX[b], or at b = 128 with the folded
-    test, FOLD_MIX plus the full test's mix for the fraction of column steps
-    that took it (counted by the kernel)."""
-    if b == 128 and full_frac is not None:
-        return (FOLD_MIX[0] + full_frac * FILTER_MIX[128][0],
-                FOLD_MIX[1] + full_frac * FILTER_MIX[128][1])
+    """(POPC, LOP3) per window pair: FILTER_MIX[b], or with the folded test
+    (b = 128, 256), FOLD_MIX[b] plus the full test's mix for the fraction of
+    column steps that took it (counted by the kernel)."""
+    if b in FOLD_MIX and full_frac is not None:
+        return (FOLD_MIX[b][0] + full_frac * FILTER_MIX[b][0],
+                FOLD_MIX[b][1] + full_frac * FILTER_MIX[b][1])
     return FILTER_MIX[b]
 
 
@@ -259,20 +260,21 @@ def filter_roofline(b, pairs, filter_ms, sms, mhz, median_mhz=None, popc_measure
     r = {"bound": "alu", "achieved": round(achieved / 1e12, 4), "peak": round(peak / 1e12, 4),
          "unit": "Tpairs/s", "frac": round(achieved / peak, 4),
          "kernel": f"{FILTER_KERNEL[b]} (Bitmap Filter, b = {b}, TMA-staged columns"
-                   + (", folded 64-bit test first)" if full_frac is not None and b == 128 else ")"),
+                   + (f", folded {b // 2}-bit test first)" if full_frac is not None and b in FOLD_MIX
+                      else ")"),
          "work_per_pair": {"popc32": round(popc, 4), "lop3": round(lop, 4), "bits_compared": b},
          "peak_derivation": (f"{sms} SMs x {mhz:.0f} MHz (max SM clock) x min({POPC_PER_CLK_PER_SM}"
                              f" POPC/clk/SM / {popc:.4g}, {LOP_PER_CLK_PER_SM} LOP3/clk/SM / "
                              f"{lop:.4g}) pairs; binding pipe {binding}"),
          "frac_of_popc_only": round(achieved * (b // 32) /
                                     (sms * POPC_PER_CLK_PER_SM * mhz * 1e6), 4)}
-    if full_frac is not None and b == 128:
+    if full_frac is not None and b in FOLD_MIX:
         r["full_test_step_frac"] = round(full_frac, 5)
         r["work_per_pair_note"] = (
-            f"every window pair meets the folded 64-bit test ({FOLD_MIX[0]} POPC, {FOLD_MIX[1]} "
-            f"LOP3); the {full_frac:.2%} of warp column steps in which some pair passes it also "
-            f"run the 128-bit test ({FILTER_MIX[128][0]} POPC, {FILTER_MIX[128][1]} LOP3)")
-        r["frac_of_full_test_bound"] = round(achieved / filter_bound(128, sms, mhz), 4)
+            f"every window pair meets the folded {b // 2}-bit test ({FOLD_MIX[b][0]} POPC, "
+            f"{FOLD_MIX[b][1]} LOP3); the {full_frac:.2%} of warp column steps in which some pair "
+            f"passes it also run the {b}-bit test ({FILTER_MIX[b][0]} POPC, {FILTER_MIX[b][1]} LOP3)")
+        r["frac_of_full_test_bound"] = round(achieved / filter_bound(b, sms, mhz), 4)
     if median_mhz:
         r["frac_at_median_clock"] = round(achieved / filter_bound(b, sms, median_mhz, full_frac), 4)
     if popc_measured:

@@ -199,14 +199,14 @@ typedef struct {
     int32_t tile_rows;      /* rows of the filter's tile (32 x rows per lane), of the job's tile in
                                bmj_self_join_batch job stats */
     int32_t chunk_cols;     /* ... and columns per filter work item */
-    int64_t fold_steps;     /* b = 128: warp column steps of the filter (the tile_rows rows of a
-                               warp's tile against one column each), every one first tested
-                               with the two 64-bit halves
-                               of the xor folded onto each other (fewer differing bits than the
-                               128-bit xor, so a pair that fails it fails Eq. 2); counted over
-                               the first filter pass, 0 at other widths */
+    int64_t fold_steps;     /* b = 128 and 256: warp column steps of the filter (the tile_rows
+                               rows of a warp's tile against one column each), every one first
+                               tested with the two halves of the xor folded onto each other
+                               (64 or 128 bits; no more differing bits than the full xor, so a
+                               pair that fails it fails Eq. 2); counted over the first filter
+                               pass, 0 at other widths */
     int64_t fold_full_steps;/* ... those in which some pair passed the folded test, so that the
-                               warp ran the 128-bit test */
+                               warp ran the full-width test */
 } bmj_stats;
 
 /* Counters and stage times of one bmj_self_join_batch call. */

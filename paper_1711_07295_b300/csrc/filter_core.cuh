@@ -494,11 +494,11 @@ __device__ __forceinline__ void flush_masks(const uint32_t (&mask)[R], const int
 
 // Filter over one work item with TMA-staged columns.  The bitmap and size
 // arrays must be readable up to 3 entries past the last column (padded).
-// kFold (b = 128): every pair first meets Eq. 2 with the two 64-bit halves of
-// the xor folded onto each other; popc(x0 ^ x1) <= popc(x0) + popc(x1), so a
-// pair that fails this test fails the 128-bit one too, and a warp runs the
-// 128-bit test on a column only when one of its 32 x R pairs passes the folded
-// one (the survivors are the same).
+// kFold (b = 128 and 256): every pair first meets Eq. 2 with the two halves of
+// the xor folded onto each other (64 or 128 bits); popc(x0 ^ x1) <= popc(x0) +
+// popc(x1), so a pair that fails this test fails the full-width one too, and a
+// warp runs the full-width test on a column only when one of its 32 x R pairs
+// passes the folded one (the survivors are the same).
 template <int W, int R, int CS, int kAltRows = 0, bool kCos = false, bool kCut = false,
           bool kFold = false>
 __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
@@ -534,7 +534,7 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
             for (int w = 0; w < 2 * W; w++) rb[k][w] = 0;
         }
     }
-    static_assert(!kFold || W == 2, "the folded test is for b = 128");
+    static_assert(!kFold || W == 2 || W == 4, "the folded test is for b = 128 and 256");
     uint32_t n_full = 0;  // kFold: column steps that took the 128-bit test (left in st.n_full)
     int nlim[R];
 #pragma unroll
@@ -591,14 +591,19 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
 #pragma unroll
                 for (int w = 0; w < 2 * W; w++) cw[w] = colw[col * 2 * W + w];
                 if constexpr (kFold) {
-                    // the column's fold; each row's fold is taken inside the same
-                    // three-input xor
-                    const uint32_t f0 = cw[0] ^ cw[2], f1 = cw[1] ^ cw[3];
+                    // the column's fold (its 32-bit word w xored with word w + W);
+                    // each row's fold is taken inside the same three-input xor
+                    uint32_t f[W];
+#pragma unroll
+                    for (int w = 0; w < W; w++) f[w] = cw[w] ^ cw[w + W];
                     int any = 0;  // sign bit: some row passes the folded test
 #pragma unroll
-                    for (int k = 0; k < R; k++)
-                        any |= __popc(rb[k][0] ^ rb[k][2] ^ f0) + __popc(rb[k][1] ^ rb[k][3] ^ f1) +
-                               nlim[k];
+                    for (int k = 0; k < R; k++) {
+                        uint32_t y[W];
+#pragma unroll
+                        for (int w = 0; w < W; w++) y[w] = rb[k][w] ^ rb[k][w + W] ^ f[w];
+                        any |= PopcHS<W / 2>::h(y) + nlim[k];
+                    }
                     if (__builtin_expect(__any_sync(kFull, any < 0), 0)) {
                         n_full++;
                         const int sh = gj - 1 - cc;  // bit of this column in the masks
@@ -607,7 +612,11 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
                             uint32_t x[2 * W];
 #pragma unroll
                             for (int w = 0; w < 2 * W; w++) x[w] = rb[k][w] ^ cw[w];
-                            const int t = PopcHS<W>::h(x) + nlim[k];
+                            const bool alt = W == 4 && kAltRows > 0 && k >= R - kAltRows;
+                            int h;
+                            if constexpr (W == 4) h = alt ? PopcAlt4::h(x) : PopcHS<4>::h(x);
+                            else h = PopcHS<W>::h(x);
+                            const int t = h + nlim[k];
                             mask[k] |= ((uint32_t)t >> 31) << sh;
                         }
                     }

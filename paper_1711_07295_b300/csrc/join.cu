@@ -428,7 +428,7 @@ static int self_join_impl(const bmj_collection *coll, const bmj_collection *coll
                 int herr = 0;
                 BMJ_CHECK(cudaMemcpyAsync(count, &ctr[1], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
                 BMJ_CHECK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-                const bool read_steps = !fold_read && W == 2;
+                const bool read_steps = !fold_read && (W == 2 || W == 4);
                 if (read_steps)
                     BMJ_CHECK(cudaMemcpyAsync(fold_steps, &ctr[6], 2 * sizeof(int64_t),
                                               cudaMemcpyDeviceToHost, s));

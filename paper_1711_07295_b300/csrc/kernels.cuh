@@ -148,12 +148,16 @@ constexpr int kAluRowsW1 = BMJ_ALU_ROWS_W1;
 #ifndef BMJ_ALT_ROWS_W4
 #define BMJ_ALT_ROWS_W4 2
 #endif
-// At b = 128, the folded 64-bit test before the 128-bit one (filter_item_tma's kFold).
+// At b = 128 and 256, the folded test (64 and 128 bits) before the full-width one
+// (filter_item_tma's kFold).
 #ifndef BMJ_FOLD_W2
 #define BMJ_FOLD_W2 1
 #endif
+#ifndef BMJ_FOLD_W4
+#define BMJ_FOLD_W4 1
+#endif
 template <int W>
-constexpr bool kFoldW = W == 2 && BMJ_FOLD_W2;
+constexpr bool kFoldW = (W == 2 && BMJ_FOLD_W2) || (W == 4 && BMJ_FOLD_W4);
 // Rows per lane that take the second popcount form of width W (popc64_alu at
 // b = 64, PopcAlt4 at b = 256).
 template <int W>

@@ -23,10 +23,12 @@ def test_filter_bound_per_width():
 
 
 def test_folded_filter_bound():
-    # b = 128 with the folded test: (2 + 3f) POPC and (2.5 + 6f) LOP3 per pair for a
-    # fraction f of full-test steps; XU-bound for every f in [0, 1]
-    assert bench.filter_mix(128, 0.0) == (2, 2.5)
-    assert bench.filter_mix(128, 1.0) == (5, 8.5)
+    # b = 128 with the folded test: (2 + 3f) POPC and (2.4 + 6f) LOP3 per pair for a
+    # fraction f of full-test steps; XU-bound for every f in [0, 1]; b = 256: (3 + 4f,
+    # 7 + 16f)
+    assert bench.filter_mix(128, 0.0) == (2, 2.4)
+    assert bench.filter_mix(128, 1.0) == (5, 8.4)
+    assert bench.filter_mix(256, 0.5) == (5, 15)
     assert bench.filter_mix(128) == bench.FILTER_MIX[128]
     assert bench.filter_mix(64, 0.5) == bench.FILTER_MIX[64]
     assert bench.filter_bound(128, 148, 2032.0, 0.0) == pytest.approx(148 * 8 * 2032e6)

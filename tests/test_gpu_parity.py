@@ -50,17 +50,18 @@ def check_join(off, tok, p, q, b=64, method=_bmj.BMJ_XOR, counts=True, sim=_bmj.
 
 
 # ------------------------------------------- folded test of the b = 128 filter
+@pytest.mark.parametrize("b", [128, 256])
 @pytest.mark.parametrize("method", [_bmj.BMJ_XOR, _bmj.BMJ_SET, _bmj.BMJ_NEXT])
 @pytest.mark.parametrize("sim,p,q", [(_bmj.BMJ_JACCARD, 1, 2), (_bmj.BMJ_JACCARD, 4, 5),
                                      (_bmj.BMJ_COSINE, 3, 4), (_bmj.BMJ_DICE, 9, 10)])
-def test_folded_test_keeps_the_survivors(method, sim, p, q):
-    # b = 128 runs the 128-bit test only in the warp column steps where some pair
-    # passes the folded 64-bit test; survivors and results stay the oracle's, and
+def test_folded_test_keeps_the_survivors(b, method, sim, p, q):
+    # b = 128 and 256 run the full-width test only in the warp column steps where some
+    # pair passes the folded (64- or 128-bit) test; survivors and results stay the oracle's, and
     # the step counters are consistent with the pairs: a step covers at most one
     # tile's rows (32 x rows per lane) of window pairs, and every survivor lies in a
     # step that took the full test
     off, tok = I.random_collection(6000, 3000, 1, 60, seed=11, planted_frac=0.15)
-    st = check_join(off, tok, p, q, b=128, method=method, sim=sim)
+    st = check_join(off, tok, p, q, b=b, method=method, sim=sim)
     rows = st["tile_rows"]
     assert rows % 32 == 0 and 32 <= rows <= 256
     assert 0 <= st["fold_full_steps"] <= st["fold_steps"]
@@ -68,7 +69,7 @@ def test_folded_test_keeps_the_survivors(method, sim, p, q):
     assert st["survivors"] <= rows * st["fold_full_steps"]
     assert st["survivors"] > 0
     # with a queue too small for the survivors (reruns in item ranges) nothing changes
-    check_join(off, tok, p, q, b=128, method=method, sim=sim, queue_cap=97)
+    check_join(off, tok, p, q, b=b, method=method, sim=sim, queue_cap=97)
     # other widths do not fold
     st64 = check_join(off, tok, p, q, b=64, method=method, sim=sim)
     assert st64["fold_steps"] == 0 and st64["fold_full_steps"] == 0
