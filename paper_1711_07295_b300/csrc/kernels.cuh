@@ -149,12 +149,15 @@ constexpr int kAluRowsW1 = BMJ_ALU_ROWS_W1;
 #define BMJ_ALT_ROWS_W4 2
 #endif
 // At b = 128 and 256, the folded test (64 and 128 bits) before the full-width one
-// (filter_item_tma's kFold).
+// (filter_item_tma's kFold).  Off at b = 256: it took the 1M joins from 0.882 to
+// 1.157e12 pairs/s, but one join per call of the 512 batched jobs from 650-742 to
+// 865 ms, where the 128-bit filter passes many pairs and the folded test rarely
+// spares the full one.
 #ifndef BMJ_FOLD_W2
 #define BMJ_FOLD_W2 1
 #endif
 #ifndef BMJ_FOLD_W4
-#define BMJ_FOLD_W4 1
+#define BMJ_FOLD_W4 0
 #endif
 template <int W>
 constexpr bool kFoldW = (W == 2 && BMJ_FOLD_W2) || (W == 4 && BMJ_FOLD_W4);

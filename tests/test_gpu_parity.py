@@ -64,10 +64,11 @@ def test_folded_test_keeps_the_survivors(b, method, sim, p, q):
     st = check_join(off, tok, p, q, b=b, method=method, sim=sim)
     rows = st["tile_rows"]
     assert rows % 32 == 0 and 32 <= rows <= 256
-    assert 0 <= st["fold_full_steps"] <= st["fold_steps"]
-    assert st["window_pairs"] <= rows * st["fold_steps"]
-    assert st["survivors"] <= rows * st["fold_full_steps"]
     assert st["survivors"] > 0
+    assert 0 <= st["fold_full_steps"] <= st["fold_steps"]
+    if st["fold_steps"] or b == 128:  # b = 256 folds only in a build that enables it
+        assert st["window_pairs"] <= rows * st["fold_steps"]
+        assert st["survivors"] <= rows * st["fold_full_steps"]
     # with a queue too small for the survivors (reruns in item ranges) nothing changes
     check_join(off, tok, p, q, b=b, method=method, sim=sim, queue_cap=97)
     # other widths do not fold
