@@ -380,7 +380,7 @@ struct StageState {
     int wait_limit;       // polls before a wait gives up
     int skip_copy;        // fault injection: issue no copy for the next fill (then 0)
     uint32_t n_full;      // filter_item_tma with kFold: column steps of the last item that
-                          // took the 128-bit test
+                          // took the full-width test
 };
 
 // After a failed wait: waits (bounded) for the copy still in flight, so that
@@ -535,7 +535,7 @@ __device__ __forceinline__ void filter_item_tma(const uint64_t *__restrict__ bm,
         }
     }
     static_assert(!kFold || W == 2 || W == 4, "the folded test is for b = 128 and 256");
-    uint32_t n_full = 0;  // kFold: column steps that took the 128-bit test (left in st.n_full)
+    uint32_t n_full = 0;  // kFold: column steps that took the full-width test (left in st.n_full)
     int nlim[R];
 #pragma unroll
     for (int k = 0; k < R; k++) nlim[k] = 0;

@@ -96,8 +96,8 @@ struct FilterArgs {
     unsigned long long *qcount;
     int64_t qcap;
     unsigned long long *item_counter;
-    // [2] (may be null): at b = 128, warp column steps of the folded test and
-    // those that took the 128-bit test
+    // [2] (may be null): with the folded test (b = 128, and 256 where built),
+    // warp column steps of the folded test and those that took the full-width one
     unsigned long long *steps = nullptr;
 };
 
